@@ -1,0 +1,74 @@
+"""The oracle's pins have teeth: plausible mistakes planted in a copy of the
+oracle (a dropped term, a wrong modulus, sign, index or operand) must each
+make tests/test_oracle_pins.py fail.  Everything runs on the CPU; the planted
+copies are compiled into a temporary directory and never used elsewhere."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+MUTANTS = {
+    "9a_wrong_modulus": ("s = or_mulmod(a, s, p);", "s = or_mulmod(a, s, n);"),
+    "9b_dropped_m": ("m = (uint64_t)(((u128)m + s) % n);", "m = (uint64_t)(((u128)s) % n);"),
+    "9b_wrong_sign": ("m = (uint64_t)(((u128)m + s) % n);",
+                      "m = (uint64_t)(((u128)m + n - s % n) % n);"),
+    "9c_transposed": ("uint64_t c = or_powmod(m, e, n);", "uint64_t c = or_powmod(s, e, n);"),
+    "9d_dropped_plus1": ("return (double)(c + 1) / (double)(n + 1);",
+                         "return (double)(c) / (double)(n + 1);"),
+    "9d_wrong_denominator": ("return (double)(c + 1) / (double)(n + 1);",
+                             "return (double)(c + 1) / (double)(n);"),
+    "powmod_wrong_square": ("base = or_mulmod(base, base, n);",
+                            "base = or_mulmod(base, result, n);"),
+    "mulmod_off_by_one": ("return (x * y) % n;", "return (x * y + 1) % n;"),
+    "skip_dropped_cycle_term": ("st[0] = (uint64_t)(((u128)m + add + sum % n) % n);",
+                                "st[0] = (uint64_t)(((u128)m + sum % n) % n);"),
+    "skip_wrong_cycle_length": ("uint64_t q = k / (p - 1), r = k % (p - 1);",
+                                "uint64_t q = k / p, r = k % p;"),
+    "state_at_wrap_index": ("+ or_pref(p, a, table, stride, hi - (p - 1));",
+                            "+ or_pref(p, a, table, stride, hi - p);"),
+    "state_at_s_index": ("st_out[1] = or_powmod(a, L0 + r, p);",
+                         "st_out[1] = or_powmod(a, L0 + r + 1, p);"),
+    "table_entry": ("if (i % stride == 0) table[j++] = sum;",
+                    "if (i % stride == 0) table[j++] = sum - x;"),
+    "pref_tail_index": ("for (uint64_t i = j * stride + 1; i <= t; ++i) {",
+                        "for (uint64_t i = j * stride + 1; i < t; ++i) {"),
+    "stats_square": ("Y += v * v;", "Y += v * (v - 1);"),
+    "stats_hist_scale": ("int b = (int)(R * 256.0);", "int b = (int)(R * 255.0);"),
+    "stats_var_N": ("u128 num = (u128)N * Y - X * X;", "u128 num = (u128)(N - 1) * Y - X * X;"),
+    "corr_transposed": ("Z += ((u128)ca[k] + 1) * ((u128)cb[k] + 1);",
+                        "Z += ((u128)ca[k] + 1) * ((u128)ca[k] + 1);"),
+    "dlog_index": ("L_out[q] = (i * M + val[h]) % order;", "L_out[q] = (i * M + val[h] + 1) % order;"),
+}
+
+
+def _run_pins(so_path):
+    env = dict(os.environ, PHPRNG_ORACLE_SO=so_path)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        "-m", "not slow and not gpu",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    return r.returncode, r.stdout[-2000:]
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_mistake_is_caught(tmp_path, name):
+    old, new = MUTANTS[name]
+    src = open(oracle._SRC).read()
+    assert src.count(old) >= 1, "mutation anchor missing: " + old
+    mutated = src.replace(old, new, 1)
+    c_path = tmp_path / "mutant.c"
+    c_path.write_text(mutated)
+    so = oracle.build(force=True, src=str(c_path), out=str(tmp_path / "mutant.so"))
+    rc, out = _run_pins(so)
+    assert rc != 0, "pins did not catch mutant %s:\n%s" % (name, out)
+
+
+def test_unmutated_copy_passes(tmp_path):
+    so = oracle.build(force=True, src=oracle._SRC, out=str(tmp_path / "clean.so"))
+    rc, out = _run_pins(so)
+    assert rc == 0, out

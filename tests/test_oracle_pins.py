@@ -1,0 +1,336 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: Python's
+own big-integer pow and exact rational division, brute force on tiny
+moduli, closed forms, theorems the paper states (Fermat, Eq. 2 decryption,
+the period n(p-1) and the (p-1)-fold multiplicity of every ciphertext), and
+printed values (Fig. 2, Fig. 3, a hand-worked Eq. 9 table).
+"""
+import math
+import random
+import struct
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from conftest import read_golden
+
+P31, A31 = 2147483647, 784588716
+
+
+def bits(x):
+    return struct.unpack("<Q", struct.pack("<d", x))[0]
+
+
+def primitive_root(p):
+    phi = p - 1
+    fac, x, d = set(), phi, 2
+    while d * d <= x:
+        while x % d == 0:
+            fac.add(d)
+            x //= d
+        d += 1
+    if x > 1:
+        fac.add(x)
+    for g in range(2, p):
+        if all(pow(g, phi // q, p) != 1 for q in fac):
+            return g
+    return 1  # p = 2
+
+
+def small_primes(lo, hi):
+    return [q for q in range(max(lo, 2), hi) if all(q % d for d in range(2, int(q ** 0.5) + 1))]
+
+
+# ------------------------------------------------------------ modular arithmetic
+def test_mulmod_powmod_match_python_pow(oracle_mod):
+    rng = random.Random(1)
+    for bits_n in (5, 16, 31, 32, 33, 48, 63, 64):
+        for _ in range(300):
+            n = rng.randrange(2, 1 << bits_n) | 1
+            x, y = rng.randrange(n), rng.randrange(n)
+            e = rng.randrange(1 << rng.randrange(1, 65))
+            assert oracle_mod.mulmod(x, y, n) == x * y % n
+            assert oracle_mod.powmod(x, e, n) == pow(x, e, n)
+    assert oracle_mod.powmod(5, 0, 7) == 1
+
+
+def test_fermat_little_theorem(oracle_mod):
+    """For prime n and m in (Z/nZ)*: m^(n-1) mod n = 1 (Introduction, Eq. 2)."""
+    rng = random.Random(2)
+    for n in (23, 4294967087, 4294967291, 18446744073709551557):
+        for _ in range(200):
+            m = rng.randrange(1, n)
+            assert oracle_mod.powmod(m, n - 1, n) == 1
+
+
+def test_fig3_key_decrypts(oracle_mod):
+    """Eq. 2 with the Fig. 3 key: c^d mod n recovers every message."""
+    h, _ = read_golden("fig3_key.txt")
+    n, e, d = int(h["n"]), int(h["e"]), int(h["d"])
+    assert (d * e) % (n - 1) == 1
+    rng = random.Random(3)
+    for m in [0, 1, 2, n - 2, n - 1] + [rng.randrange(n) for _ in range(2000)]:
+        c = oracle_mod.powmod(m, e, n)
+        assert oracle_mod.powmod(c, d, n) == m
+
+
+def test_decryption_random_64bit_keys(oracle_mod):
+    rng = random.Random(4)
+    for n in (18446744073709551557, 9223372036854775837):
+        for _ in range(50):
+            e = rng.randrange(3, n - 1)
+            if math.gcd(e, n - 1) != 1:
+                continue
+            d = pow(e, -1, n - 1)
+            m = rng.randrange(n)
+            assert oracle_mod.powmod(oracle_mod.powmod(m, e, n), d, n) == m
+
+
+def test_encryption_is_a_bijection_on_tiny_primes(oracle_mod):
+    """x -> x^e mod n permutes Z/nZ for every allowed e (Introduction)."""
+    for n in small_primes(5, 90):
+        for e in range(3, n - 1):
+            images = {oracle_mod.powmod(x, e, n) for x in range(n)}
+            if math.gcd(e, n - 1) == 1:
+                assert images == set(range(n)), (n, e)
+            else:
+                assert len(images) < n, (n, e)
+
+
+def test_reflection_symmetry(oracle_mod):
+    """(n-m)^e mod n = n - (m^e mod n) for odd e (Message skipping algorithms)."""
+    rng = random.Random(5)
+    for n in (4294967087, 2147483659, 18446744073709551557):
+        for _ in range(300):
+            e = rng.randrange(3, n - 1) | 1
+            m = rng.randrange(1, n)
+            assert oracle_mod.powmod(n - m, e, n) == n - oracle_mod.powmod(m, e, n)
+
+
+def test_constant_skip_identity(oracle_mod):
+    """Eq. 4: (k b)^e mod n = ((b^e mod n)(k^e mod n)) mod n."""
+    rng = random.Random(6)
+    n = 4294967087
+    for _ in range(300):
+        b, k, e = rng.randrange(2, n - 1), rng.randrange(n), rng.randrange(3, n - 1)
+        lhs = oracle_mod.powmod(oracle_mod.mulmod(k, b, n), e, n)
+        rhs = oracle_mod.mulmod(oracle_mod.powmod(b, e, n), oracle_mod.powmod(k, e, n), n)
+        assert lhs == rhs
+
+
+# ------------------------------------------------------------ Eq. 9 generator
+def test_hand_worked_eq9_table(oracle_mod):
+    h, rows = read_golden("tiny_n23_eq9.txt")
+    n, e, p, a = (int(h[k]) for k in ("n", "e", "p", "a"))
+    m, s = int(h["m0"]), int(h["s0"])
+    for k, sk, mk, ck, num, den in rows:
+        c, r, (m, s) = oracle_mod.generate(n, e, p, a, m, s, 1)
+        assert (s, m, int(c[0])) == (sk, mk, ck), k
+        assert r[0] == num / den
+        assert bits(r[0]) == bits(float(Fraction(num, den)))
+
+
+def test_fig2_unit_skip_cribs(oracle_mod):
+    """Unit skip s_k = 1 is the skip generator with p = 2, a = 1 (s = 1*1 mod 2)."""
+    h, rows = read_golden("fig2_unit_skip.txt")
+    n, e = int(h["n"]), int(h["e"])
+    c, _, _ = oracle_mod.generate(n, e, 2, 1, n - 1, 1, len(rows))   # m_1 = 0
+    assert [int(x) for x in c] == [row[1] for row in rows]
+
+
+TINY = [  # (n, p, e): p < n, both prime
+    (23, 11, 3), (47, 23, 5), (59, 29, 3), (83, 41, 13), (107, 53, 5), (29, 13, 3),
+    (37, 31, 5), (101, 97, 3), (13, 11, 5), (11, 7, 3),
+]
+
+
+@pytest.mark.parametrize("n,p,e", TINY)
+def test_period_and_uniform_full_period(oracle_mod, n, p, e):
+    """Period P = n(p-1); over it every ciphertext appears exactly p-1 times
+    (Message skipping algorithms, proof after Eq. 6)."""
+    assert math.gcd(e, n - 1) == 1
+    a = primitive_root(p)
+    rng = random.Random(n * 1000 + p)
+    m0, s0 = rng.randrange(n), rng.randrange(1, p)
+    P = n * (p - 1)
+    # walk the state and find the first return
+    m, s = m0, s0
+    first_return = None
+    c_all = []
+    for k in range(1, P + 1):
+        c, _, (m, s) = oracle_mod.generate(n, e, p, a, m, s, 1)
+        c_all.append(int(c[0]))
+        if (m, s) == (m0, s0) and first_return is None:
+            first_return = k
+    assert first_return == P
+    counts = np.bincount(np.array(c_all), minlength=n)
+    assert np.all(counts == p - 1)
+    # bulk call gives the same stream
+    c_bulk, _, st = oracle_mod.generate(n, e, p, a, m0, s0, P)
+    assert [int(x) for x in c_bulk] == c_all and st == (m0, s0)
+
+
+def test_real_32bit_is_correctly_rounded(oracle_mod):
+    rng = random.Random(7)
+    ns = [4294967291, 4294967087, 2147483659, 23, 3, 5, 8191]
+    for n in ns:
+        cs = [0, 1, n - 1, n - 2, (n - 1) // 2] + [rng.randrange(n) for _ in range(2000)]
+        cs += [(1 << j) - 1 for j in range(1, 32) if (1 << j) - 1 < n]
+        for c in cs:
+            r = oracle_mod.real(c, n)
+            assert bits(r) == bits(float(Fraction(c + 1, n + 1)))
+            assert 0.0 < r < 1.0
+
+
+def test_real_64bit_reading(oracle_mod):
+    """64-bit n: RN(RN(c+1) / RN(n+1)) -- each operand rounded to double first."""
+    rng = random.Random(8)
+    n = 18446744073709551557
+    differs = 0
+    for _ in range(5000):
+        c = rng.randrange(n)
+        r = oracle_mod.real(c, n)
+        assert bits(r) == bits(float(c + 1) / float(n + 1))
+        differs += bits(r) != bits(float(Fraction(c + 1, n + 1)))
+    assert differs > 0            # the reading is not the exact-rational rounding
+    assert oracle_mod.real(n - 1, n) == 1.0   # R can reach 1.0 for 64-bit n
+
+
+# ------------------------------------------------------------ Eq. 7 skip-ahead
+@pytest.mark.parametrize("n,p,e", TINY[:5])
+def test_skip_stepping_matches_generation_tiny(oracle_mod, n, p, e):
+    a = primitive_root(p)
+    rng = random.Random(p)
+    for _ in range(40):
+        m, s = rng.randrange(n), rng.randrange(1, p)
+        k = rng.randrange(0, 5 * n * (p - 1))
+        _, _, st = oracle_mod.generate(n, e, p, a, m, s, k)
+        assert oracle_mod.skip_stepping(n, p, a, m, s, k) == st
+
+
+def test_skip_stepping_matches_generation_32bit(oracle_mod):
+    rng = random.Random(9)
+    n, e = 4294967087, 9
+    for _ in range(20):
+        m, s = rng.randrange(n), rng.randrange(1, P31)
+        k = rng.randrange(0, 200000)
+        _, _, st = oracle_mod.generate(n, e, P31, A31, m, s, k)
+        assert oracle_mod.skip_stepping(n, P31, A31, m, s, k) == st
+
+
+@pytest.mark.parametrize("p", [11, 13, 23, 29, 101, 257])
+def test_prefix_table_tiny(oracle_mod, p):
+    a = primitive_root(p)
+    for stride in (1, 2, 3, 5, p - 1):
+        T = oracle_mod.PrefixTable(p, a, stride)
+        brute = [0]
+        for i in range(1, p):
+            brute.append(brute[-1] + pow(a, i, p))
+        assert brute[-1] == p * (p - 1) // 2
+        for t in range(p):
+            assert T.pref(t) == brute[t]
+
+
+@pytest.mark.parametrize("n,p,e", TINY[:6])
+def test_state_at_matches_stepping_tiny(oracle_mod, n, p, e):
+    a = primitive_root(p)
+    rng = random.Random(n + p)
+    T = oracle_mod.PrefixTable(p, a, 3)
+    for _ in range(60):
+        m0, L0 = rng.randrange(n), rng.randrange(p - 1)
+        s0 = pow(a, L0, p)
+        t = rng.randrange(0, 4 * n * (p - 1))
+        _, _, st = oracle_mod.generate(n, e, p, a, m0, s0, t)
+        assert T.state_at(n, m0, L0, t) == st
+
+
+def test_dlog_places_seeds_on_the_cycle(oracle_mod):
+    rng = random.Random(10)
+    s = [1, A31, P31 - 1] + [rng.randrange(1, P31) for _ in range(200)]
+    L = oracle_mod.dlog(P31, A31, s)
+    for si, li in zip(s, L):
+        assert 0 <= int(li) < P31 - 1 and pow(A31, int(li), P31) == si
+
+
+@pytest.mark.slow
+def test_default_skip_cycle_sum_and_state_at(oracle_mod):
+    """Full cycle of (p, a) = (2^31-1, 784588716): Pref(p-1) = p(p-1)/2, and
+    Eq. 7 from a seed agrees with Eq. 7 by stepping at offsets past one cycle."""
+    T = oracle_mod.PrefixTable(P31, A31, 1 << 16)
+    assert T.pref(P31 - 1) == P31 * (P31 - 1) // 2
+    rng = random.Random(11)
+    n = 4294967087
+    for _ in range(6):
+        m0, s0 = rng.randrange(n), rng.randrange(1, P31)
+        L0 = int(oracle_mod.dlog(P31, A31, [s0])[0])
+        t = rng.randrange(0, 1 << 40)
+        k_small = rng.randrange(0, 3000)
+        st = T.state_at(n, m0, L0, t)
+        # stepping agrees after a further k_small steps
+        _, _, st2 = oracle_mod.generate(n, 9, P31, A31, st[0], st[1], k_small)
+        assert T.state_at(n, m0, L0, t + k_small) == st2
+        # and the q-cycle term matches Eq. 7 by stepping for offsets q(p-1)+r
+        r = rng.randrange(0, 5000)
+        t2 = (t // (P31 - 1)) * (P31 - 1) + r
+        assert T.state_at(n, m0, L0, t2) == oracle_mod.skip_stepping(n, P31, A31, m0, s0, t2)
+
+
+# ------------------------------------------------------------ fused statistics
+@pytest.mark.parametrize("n,p,e", TINY[:6])
+def test_stats_full_period_closed_forms(oracle_mod, n, p, e):
+    a = primitive_root(p)
+    P = n * (p - 1)
+    c, _, _ = oracle_mod.generate(n, e, p, a, 3 % n, 1, P)
+    X, Y, hist, mean, var = oracle_mod.stats(c, n)
+    assert X == (p - 1) * n * (n + 1) // 2
+    assert Y == (p - 1) * n * (n + 1) * (2 * n + 1) // 6
+    expect = np.zeros(256, dtype=np.int64)
+    for cc in range(n):
+        expect[(256 * (cc + 1)) // (n + 1)] += p - 1
+    assert np.array_equal(hist.astype(np.int64), expect)
+    assert mean == float(X) / float(P * (n + 1))
+    assert var == float(P * Y - X * X) / float(P * (P - 1) * (n + 1) ** 2)
+    # mean of (c+1)/(n+1) over a uniform full period is 1/2 exactly
+    assert Fraction(X, P * (n + 1)) == Fraction(1, 2)
+
+
+def test_corr_pins(oracle_mod):
+    rng = random.Random(12)
+    n1, n2 = 4294967087, 4294967291
+    c1, _, _ = oracle_mod.generate(n1, 9, P31, A31, rng.randrange(n1), 5, 3000)
+    c2, _, _ = oracle_mod.generate(n2, 17, P31, A31, rng.randrange(n2), 7, 3000)
+    X1, Y1, *_ = oracle_mod.stats(c1, n1)
+    X2, Y2, *_ = oracle_mod.stats(c2, n2)
+    Z11, _ = oracle_mod.corr(c1, c1, n1, n1)
+    assert Z11 == Y1                                  # identical streams
+    Z12, corr = oracle_mod.corr(c1, c2, n1, n2)
+    assert Z12 * Z12 <= Y1 * Y2                       # Cauchy-Schwarz
+    assert corr == float(Z12) / float(3000 * (n1 + 1) * (n2 + 1))
+    assert abs(corr - 0.25) < 0.02                    # independent uniforms
+
+
+def test_u128_conversion_in_stats_is_correctly_rounded(oracle_mod):
+    """Large accumulators: mean and var use RN conversions of 128-bit integers."""
+    n = 4294967291
+    rng = random.Random(13)
+    c = np.array([rng.randrange(n) for _ in range(4097)], dtype=np.uint64)
+    X, Y, _, mean, var = oracle_mod.stats(c, n)
+    N = c.size
+    assert X == sum(int(x) + 1 for x in c)
+    assert Y == sum((int(x) + 1) ** 2 for x in c)
+    assert bits(mean) == bits(float(X) / float(N * (n + 1)))
+    assert bits(var) == bits(float(N * Y - X * X) / float(N * (N - 1) * (n + 1) ** 2))
+
+
+def test_generate_many_matches_generate(oracle_mod):
+    from paper_1411_2484_gb300 import workloads
+    inst = workloads.draw_instances(7, seed=99)
+    rows = workloads.instance_rows(inst)
+    c, r, st, _ = oracle_mod.generate_many(rows, 333, threads=3)
+    for i in range(7):
+        n, e, p, a, m, s = (int(x) for x in rows[i])
+        ci, ri, sti = oracle_mod.generate(n, e, p, a, m, s, 333)
+        assert np.array_equal(c[i], ci) and np.array_equal(r[i].view(np.uint64), ri.view(np.uint64))
+        assert tuple(int(x) for x in st[i]) == sti
