@@ -1,0 +1,190 @@
+/*
+ * phprng.h -- C ABI of the GB300 (sm_103a) Pohlig-Hellman exponentiation-
+ * cipher pseudorandom generator.
+ *
+ * Method: P. D. Beale, "A new class of scalable parallel pseudorandom number
+ * generators based on Pohlig-Hellman exponentiation ciphers", arXiv:1411.2484.
+ * Every instance owns a prime modulus n and an exponent e with
+ * gcd(e, n-1) = 1 (Eq. 1) and a prime-modulus skip generator (p, a) with
+ * p < n and a a primitive root mod p (Eq. 5).  Its state is the seven
+ * integers {m, s, c, n, e, p, a} ("Message skipping algorithms"), of which
+ * m, s and c change.  One number is one pass of the implementation algorithm
+ * (Eq. 9):
+ *     s := a s mod p;  m := (m + s) mod n;  c := m^e mod n;  R := (c+1)/(n+1).
+ *
+ * Conventions shared by every entry point:
+ *  - Every function returns a phprng_status and never throws or aborts.
+ *    A failed call leaves the context unchanged; phprng_last_error() gives a
+ *    one-line message.
+ *  - Instance numbers are 0-based indexes into the table given at creation.
+ *  - The stream position t of an instance counts the numbers produced so far.
+ *    Output j (0-based) of a call is number t+j+1 of the stream, c_{t+j+1}:
+ *    the first number ever produced comes from (m0, s0) by Eq. 9a-9c.
+ *  - Device work is enqueued on the caller's CUDA stream (a cudaStream_t
+ *    passed as void*, NULL = legacy default stream) and is asynchronous,
+ *    unless an output pointer is host memory (see phprng_generate).
+ *  - The library owns the instance table, the generator state and the skip
+ *    table in device memory.  The caller owns every output buffer.
+ *  - Widths: 32 = moduli below 2^32 (c is uint32_t), 64 = moduli below 2^64
+ *    (c is uint64_t), 0 = mixed table, each instance on the 32-bit path when
+ *    n < 2^32 and on the 64-bit path otherwise (c is uint64_t).
+ */
+#ifndef PHPRNG_H
+#define PHPRNG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+typedef enum {
+    PHPRNG_OK = 0,
+    PHPRNG_EINVAL = 1,      /* bad argument: null or misaligned pointer, range, size, width */
+    PHPRNG_ENOTPRIME = 2,   /* n (or (n-1)/2 when a safe prime is required) is composite */
+    PHPRNG_EEXPONENT = 3,   /* e outside [3, n-2] or gcd(e, n-1) != 1 (Eq. 1, Eq. 2) */
+    PHPRNG_ESKIP = 4,       /* (p, a, s0) is not a valid skip generator (Eq. 5) */
+    PHPRNG_EDUPLICATE = 5,  /* two instances share a modulus (parameter splitting) */
+    PHPRNG_ENOMEM = 6,      /* host or device allocation failed */
+    PHPRNG_ECUDA = 7,       /* a CUDA runtime call failed; the message names it */
+    PHPRNG_ETIMEOUT = 8,    /* a bounded device or host wait ran out */
+    PHPRNG_EBUDGET = 9      /* admission refused: the output-byte budget is full */
+} phprng_status;
+
+/* Creation flags. */
+#define PHPRNG_REQUIRE_SAFE_PRIME 0x1u  /* (n-1)/2 must be prime (Implementation section) */
+#define PHPRNG_ALLOW_SHARED_N     0x2u  /* allow two instances with the same n */
+
+/* One instance as the caller describes it (caller-owned input).
+ * n  prime modulus, 5 <= n < 2^32 (width 32) or < 2^64 (width 64, 0)
+ * e  exponent, 3 <= e <= n-2, gcd(e, n-1) = 1
+ * p  skip-generator prime, 3 <= p < n, p < 2^32; the same (p, a) for every
+ *    instance of a context
+ * a  primitive root mod p
+ * m0 initial message, 0 <= m0 < n
+ * s0 initial skip, 1 <= s0 <= p-1 */
+typedef struct {
+    uint64_t n, e, p, a, m0, s0;
+} phprng_instance;
+
+/* Per-stream statistics of one generate call (fused consumer mode; 32-bit
+ * moduli).  N = numbers of the call for this stream, c_k its ciphertexts,
+ * R_k = (c_k+1)/(n+1) as in Eq. 9d.  All sums are exact integers:
+ *   x = sum (c_k+1),  y = sum (c_k+1)^2,
+ *   z = sum (c_k+1)(c'_k+1) with c' the next instance of the call (stream
+ *       alpha+1 in the interstream ordering of "Message skipping
+ *       algorithms", last item); 0 for the last instance of the call,
+ *   hist[b] = #{k : floor(256 R_k) = b}.
+ * Doubles: mean = RN(RN(x) / RN(N(n+1))),
+ *          var  = RN(RN(N y - x^2) / RN(N(N-1)(n+1)^2))   (0 when N < 2),
+ *          corr = RN(RN(z) / RN(N(n+1)(n'+1)))             (0 for the last).
+ * Integers of 128 bits are stored as {lo, hi}. */
+typedef struct {
+    uint64_t x_lo, x_hi;
+    uint64_t y_lo, y_hi;
+    uint64_t z_lo, z_hi;
+    uint64_t count;
+    double mean, var, corr;
+    uint32_t hist[256];
+} phprng_stats;
+
+typedef struct phprng_ctx phprng_ctx;   /* opaque, library-owned */
+
+/* ---------------------------------------------------------------- lifetime */
+
+/* Validates `count` instances on the host and uploads them to the current
+ * CUDA device.  Validation (Implementation section): n prime by trial
+ * division by the primes below 256 and then the deterministic Rabin-Miller
+ * test with bases 2,3,5,7,11 (n < 2^32) or the twelve primes up to 37
+ * (n < 2^64); with PHPRNG_REQUIRE_SAFE_PRIME also (n-1)/2; e as above; p
+ * prime and a a primitive root mod p (a^((p-1)/q) != 1 for every prime q
+ * dividing p-1); moduli distinct unless PHPRNG_ALLOW_SHARED_N.
+ * width: 32, 64 or 0 (mixed).  On success *out is a new context whose every
+ * stream is at position 0.  On failure *out is NULL, nothing is allocated,
+ * and phprng_last_error(NULL) names the first offending instance.
+ * cuda_stream orders the uploads. */
+int phprng_create(phprng_ctx **out, int width, const phprng_instance *inst,
+                  uint64_t count, uint32_t flags, void *cuda_stream);
+
+/* Draws `count` instances from a 64-bit seed with phprng_draw_instances()
+ * and creates a context from them. */
+int phprng_create_seeded(phprng_ctx **out, int width, uint64_t count, uint64_t seed,
+                         uint32_t flags, void *cuda_stream);
+
+/* Frees the context and its device memory after the device is idle with
+ * respect to it (synchronizes the device).  NULL is accepted. */
+int phprng_destroy(phprng_ctx *ctx);
+
+/* Message of the last failed call on ctx, or of the calling thread's last
+ * failed create when ctx is NULL.  Never NULL; owned by the library. */
+const char *phprng_last_error(const phprng_ctx *ctx);
+
+/* Static text for a status code. */
+const char *phprng_status_string(int status);
+
+/* ---------------------------------------------------------------- generation */
+
+/* Produces per_inst consecutive numbers (Eq. 9) for each of the instances
+ * first .. first+num_inst-1 and advances their streams by per_inst.
+ * Outputs, instance-major (instance first+i, number j at index i*per_inst+j):
+ *   c_out  ciphertexts c (uint32_t for width 32, uint64_t otherwise), or NULL
+ *   r_out  R = (c+1)/(n+1) as IEEE double: for n < 2^32 the correctly
+ *          rounded quotient; for 64-bit n, RN(RN(c+1)/RN(n+1)) -- or NULL
+ *   stats_out  num_inst phprng_stats (32-bit instances only), or NULL.
+ *          With c_out and r_out NULL this is the fused mode: nothing but the
+ *          statistics is written.
+ * Pointers may be device memory (asynchronous on cuda_stream) or host memory
+ * (pinned or pageable; the call then stages through device buffers, copies
+ * back, and returns after the data is on the host).  c_out/r_out must be
+ * aligned to their element size.  per_inst = 0 is a no-op. */
+int phprng_generate(phprng_ctx *ctx, uint64_t first, uint64_t num_inst, uint64_t per_inst,
+                    void *c_out, double *r_out, phprng_stats *stats_out, void *cuda_stream);
+
+/* Advances instance inst_ids[i] by k[i] positions without producing output,
+ * by the closed form Eq. 7 (k = q(p-1) + r: s' = s a^r mod p and
+ * m' = m + q p(p-1)/2 + sum_{j=1..r} (s a^j mod p) mod n), with the sum read
+ * from an exact prefix-sum table of the skip cycle of (p, a) (built on the
+ * device at the first call, then kept).  inst_ids and k are host arrays of
+ * cnt entries; an instance may appear more than once (the skips add). */
+int phprng_skip(phprng_ctx *ctx, const uint64_t *inst_ids, const uint64_t *k, uint64_t cnt,
+                void *cuda_stream);
+
+/* Copies instance inst's parameters and current state to the host: the
+ * returned phprng_instance holds {n, e, p, a, m, s} with m, s the current
+ * message and skip; *pos_out (nullable) its stream position and *c_out
+ * (nullable) the last ciphertext (0 before the first number).  Waits for
+ * work queued on cuda_stream. */
+int phprng_get_state(phprng_ctx *ctx, uint64_t inst, phprng_instance *state_out,
+                     uint64_t *pos_out, uint64_t *c_out, void *cuda_stream);
+
+/* ---------------------------------------------------------------- host only
+ * These run on the CPU and need no GPU. */
+
+/* 1 if n is prime, else 0: trial division by the primes below 256, then
+ * the deterministic Rabin-Miller test with the paper's bases (2,3,5,7,11
+ * below 2^32, the twelve primes up to 37 below 2^64), Implementation
+ * section. */
+int phprng_is_prime(uint64_t n);
+
+/* Validates instances exactly as phprng_create does, without a GPU.
+ * *bad_index (nullable) receives the first failing instance. */
+int phprng_validate(int width, const phprng_instance *inst, uint64_t count, uint32_t flags,
+                    uint64_t *bad_index);
+
+/* Draws `count` instances from `seed` (Implementation section, seeding
+ * paragraph, with a fixed seed in place of the system time): distinct
+ * primes n in [2^31, 2^32) (width 32) or [2^63, 2^64) (width 64), safe
+ * primes when PHPRNG_REQUIRE_SAFE_PRIME; e uniform in [3, n-2] with
+ * gcd(e, n-1) = 1; m0 uniform in [0, n); s0 = a^L mod p with L uniform in
+ * [0, p-2] (the stream skipped forward L steps from s = 1 by Eq. 7);
+ * (p, a) = (2^31-1, 784588716).  Random source: SplitMix64.
+ * out must hold count entries. */
+int phprng_draw_instances(int width, uint64_t count, uint64_t seed, uint32_t flags,
+                          phprng_instance *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PHPRNG_H */

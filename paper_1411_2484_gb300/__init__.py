@@ -1,0 +1,253 @@
+"""GB300-native Pohlig-Hellman exponentiation-cipher PRNG (arXiv:1411.2484).
+
+Thin ctypes binding of libphprng.so: the functions below carry the names of
+the C ABI (include/phprng.h) and only marshal arguments.  Every step of the
+generator runs in the library's CUDA kernels; there is no Python or CPU
+fallback, and every call raises RuntimeError when the compiled library is
+absent.  Build it with ``paper_1411_2484_gb300.build.build()``.
+
+Pointer arguments accept a torch tensor, a numpy array, an int address or
+None.  Stream arguments accept a torch.cuda.Stream, an int handle or None
+(the legacy default stream).
+"""
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libphprng.so")
+
+PHPRNG_OK = 0
+PHPRNG_EINVAL = 1
+PHPRNG_ENOTPRIME = 2
+PHPRNG_EEXPONENT = 3
+PHPRNG_ESKIP = 4
+PHPRNG_EDUPLICATE = 5
+PHPRNG_ENOMEM = 6
+PHPRNG_ECUDA = 7
+PHPRNG_ETIMEOUT = 8
+PHPRNG_EBUDGET = 9
+PHPRNG_REQUIRE_SAFE_PRIME = 0x1
+PHPRNG_ALLOW_SHARED_N = 0x2
+
+EXPORTED = [
+    "phprng_create", "phprng_create_seeded", "phprng_destroy", "phprng_last_error",
+    "phprng_status_string", "phprng_generate", "phprng_skip", "phprng_get_state",
+    "phprng_is_prime", "phprng_validate", "phprng_draw_instances",
+]
+
+
+class phprng_instance(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in ("n", "e", "p", "a", "m0", "s0")]
+
+
+class phprng_stats(ctypes.Structure):
+    _fields_ = [("x_lo", ctypes.c_uint64), ("x_hi", ctypes.c_uint64),
+                ("y_lo", ctypes.c_uint64), ("y_hi", ctypes.c_uint64),
+                ("z_lo", ctypes.c_uint64), ("z_hi", ctypes.c_uint64),
+                ("count", ctypes.c_uint64),
+                ("mean", ctypes.c_double), ("var", ctypes.c_double), ("corr", ctypes.c_double),
+                ("hist", ctypes.c_uint32 * 256)]
+
+
+STATS_DTYPE = np.dtype([("x_lo", "<u8"), ("x_hi", "<u8"), ("y_lo", "<u8"), ("y_hi", "<u8"),
+                        ("z_lo", "<u8"), ("z_hi", "<u8"), ("count", "<u8"),
+                        ("mean", "<f8"), ("var", "<f8"), ("corr", "<f8"),
+                        ("hist", "<u4", (256,))])
+assert STATS_DTYPE.itemsize == ctypes.sizeof(phprng_stats)
+
+
+class PhprngError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s (status %d)" % (message, status))
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libphprng.so is not built (%s); run "
+                               "paper_1411_2484_gb300.build.build()" % LIB_PATH)
+        lib = ctypes.CDLL(LIB_PATH)
+        vp, u64, i32, u32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint32
+        P_inst = ctypes.POINTER(phprng_instance)
+        P64 = ctypes.POINTER(ctypes.c_uint64)
+        lib.phprng_create.argtypes = [ctypes.POINTER(vp), i32, P_inst, u64, u32, vp]
+        lib.phprng_create_seeded.argtypes = [ctypes.POINTER(vp), i32, u64, u64, u32, vp]
+        lib.phprng_destroy.argtypes = [vp]
+        lib.phprng_last_error.argtypes = [vp]
+        lib.phprng_last_error.restype = ctypes.c_char_p
+        lib.phprng_status_string.argtypes = [i32]
+        lib.phprng_status_string.restype = ctypes.c_char_p
+        lib.phprng_generate.argtypes = [vp, u64, u64, u64, vp, vp, vp, vp]
+        lib.phprng_skip.argtypes = [vp, P64, P64, u64, vp]
+        lib.phprng_get_state.argtypes = [vp, u64, P_inst, P64, P64, vp]
+        lib.phprng_is_prime.argtypes = [u64]
+        lib.phprng_validate.argtypes = [i32, P_inst, u64, u32, P64]
+        lib.phprng_draw_instances.argtypes = [i32, u64, u64, u32, P_inst]
+        _lib = lib
+        return lib
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError("unsupported pointer argument %r" % type(x))
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    if hasattr(s, "cuda_stream"):
+        return s.cuda_stream
+    raise TypeError("unsupported stream argument %r" % type(s))
+
+
+def _check(rc, ctx=None):
+    if rc != PHPRNG_OK:
+        msg = _load().phprng_last_error(ctx)
+        raise PhprngError(rc, msg.decode() if msg else "error")
+
+
+def _instances(inst):
+    """Accepts a dict of arrays {n, e, p, a, m0, s0}, an (count, 6) array or a
+    sequence of 6-tuples; returns a ctypes array of phprng_instance."""
+    if isinstance(inst, dict):
+        rows = np.stack([np.asarray(inst[k], dtype=np.uint64)
+                         for k in ("n", "e", "p", "a", "m0", "s0")], axis=1)
+    else:
+        rows = np.asarray(inst, dtype=np.uint64).reshape(-1, 6)
+    rows = np.ascontiguousarray(rows, dtype=np.uint64)
+    arr = (phprng_instance * rows.shape[0])()
+    ctypes.memmove(arr, rows.ctypes.data, rows.nbytes)
+    return arr, rows.shape[0]
+
+
+def phprng_create(width, instances, flags=0, stream=None):
+    """Returns an opaque context handle (int)."""
+    lib = _load()
+    arr, count = _instances(instances)
+    out = ctypes.c_void_p()
+    _check(lib.phprng_create(ctypes.byref(out), int(width), arr, count, int(flags),
+                             _stream(stream)))
+    return out.value
+
+
+def phprng_create_seeded(width, count, seed, flags=0, stream=None):
+    lib = _load()
+    out = ctypes.c_void_p()
+    _check(lib.phprng_create_seeded(ctypes.byref(out), int(width), int(count), int(seed),
+                                    int(flags), _stream(stream)))
+    return out.value
+
+
+def phprng_destroy(ctx):
+    if ctx:
+        _load().phprng_destroy(ctx)
+
+
+def phprng_last_error(ctx=None):
+    return _load().phprng_last_error(ctx).decode()
+
+
+def phprng_status_string(status):
+    return _load().phprng_status_string(int(status)).decode()
+
+
+def phprng_generate(ctx, first, num_inst, per_inst, c_out=None, r_out=None, stats_out=None,
+                    stream=None):
+    _check(_load().phprng_generate(ctx, int(first), int(num_inst), int(per_inst), _ptr(c_out),
+                                   _ptr(r_out), _ptr(stats_out), _stream(stream)), ctx)
+
+
+def phprng_skip(ctx, inst_ids, k, stream=None):
+    ids = np.ascontiguousarray(np.asarray(inst_ids, dtype=np.uint64).reshape(-1))
+    ks = np.ascontiguousarray(np.asarray(k, dtype=np.uint64).reshape(-1))
+    if ids.size != ks.size:
+        raise ValueError("inst_ids and k differ in length")
+    P64 = ctypes.POINTER(ctypes.c_uint64)
+    _check(_load().phprng_skip(ctx, ids.ctypes.data_as(P64), ks.ctypes.data_as(P64), ids.size,
+                               _stream(stream)), ctx)
+
+
+def phprng_get_state(ctx, inst, stream=None):
+    """Returns dict(n, e, p, a, m, s, c, pos) of instance `inst`."""
+    st = phprng_instance()
+    pos = ctypes.c_uint64()
+    c = ctypes.c_uint64()
+    _check(_load().phprng_get_state(ctx, int(inst), ctypes.byref(st), ctypes.byref(pos),
+                                    ctypes.byref(c), _stream(stream)), ctx)
+    return dict(n=st.n, e=st.e, p=st.p, a=st.a, m=st.m0, s=st.s0, c=c.value, pos=pos.value)
+
+
+def phprng_is_prime(n):
+    return bool(_load().phprng_is_prime(int(n)))
+
+
+def phprng_validate(width, instances, flags=0):
+    """Returns (status, first bad index or None, message)."""
+    lib = _load()
+    arr, count = _instances(instances)
+    bad = ctypes.c_uint64(0)
+    rc = lib.phprng_validate(int(width), arr, count, int(flags), ctypes.byref(bad))
+    if rc == PHPRNG_OK:
+        return rc, None, ""
+    return rc, bad.value, lib.phprng_last_error(None).decode()
+
+
+def phprng_draw_instances(width, count, seed, flags=0):
+    """Returns the drawn table as a dict of uint64 arrays {n, e, p, a, m0, s0}."""
+    lib = _load()
+    arr = (phprng_instance * int(count))()
+    _check(lib.phprng_draw_instances(int(width), int(count), int(seed), int(flags), arr))
+    rows = np.frombuffer(arr, dtype=np.uint64).reshape(-1, 6).copy()
+    return {k: rows[:, j] for j, k in enumerate(("n", "e", "p", "a", "m0", "s0"))}
+
+
+class Generator:
+    """Owns one context; thin convenience over the functions above."""
+
+    def __init__(self, width, instances=None, count=None, seed=None, flags=0, stream=None):
+        if instances is not None:
+            self.ctx = phprng_create(width, instances, flags, stream)
+        else:
+            self.ctx = phprng_create_seeded(width, count, seed, flags, stream)
+        self.width = width
+
+    def generate(self, first, num_inst, per_inst, c_out=None, r_out=None, stats_out=None,
+                 stream=None):
+        phprng_generate(self.ctx, first, num_inst, per_inst, c_out, r_out, stats_out, stream)
+
+    def skip(self, inst_ids, k, stream=None):
+        phprng_skip(self.ctx, inst_ids, k, stream)
+
+    def state(self, inst, stream=None):
+        return phprng_get_state(self.ctx, inst, stream)
+
+    def close(self):
+        if self.ctx:
+            phprng_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,390 @@
+// capi.cpp -- the C ABI declared in include/phprng.h.
+//
+// A context owns, in device memory: the instance table (DevInst, 64 B per
+// instance), the generator state (m, s, c, pos as four arrays of uint64) and,
+// once a skip is requested, the prefix table of the skip cycle.  It also owns
+// two staging buffers and a copy stream used only when a caller passes host
+// output pointers.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+#define PH_API extern "C" __attribute__((visibility("default")))
+
+using namespace phprng;
+
+struct phprng_ctx {
+    int width = 32;
+    uint64_t count = 0;
+    uint32_t flags = 0;
+    int device = 0;
+    uint64_t p = 0, a = 0;
+    bool any32 = false, any64 = false;
+    std::vector<phprng_instance> host_inst;
+    std::vector<uint8_t> wide;
+    DevInst *d_inst = nullptr;
+    uint64_t *d_state = nullptr;      // 4 * count: m | s | c | pos
+    DevState st{};
+    SkipConst sk32{}, sk64{};
+    // host-output staging
+    void *stage[2] = {nullptr, nullptr};
+    size_t stage_bytes = 0;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_done[2] = {nullptr, nullptr}, ev_copied[2] = {nullptr, nullptr};
+    std::string err;
+    std::mutex mu;
+};
+
+static thread_local std::string g_err;
+
+static int fail(phprng_ctx *ctx, int code, const std::string &msg)
+{
+    if (ctx) ctx->err = msg; else g_err = msg;
+    return code;
+}
+
+static int cuda_fail(phprng_ctx *ctx, cudaError_t e, const char *what)
+{
+    return fail(ctx, PHPRNG_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CU(ctx, call)                                                   \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);      \
+    } while (0)
+
+static void free_ctx(phprng_ctx *c)
+{
+    if (!c) return;
+    cudaDeviceSynchronize();
+    cudaFree(c->d_inst);
+    cudaFree(c->d_state);
+    for (int k = 0; k < 2; ++k) {
+        cudaFree(c->stage[k]);
+        if (c->ev_done[k]) cudaEventDestroy(c->ev_done[k]);
+        if (c->ev_copied[k]) cudaEventDestroy(c->ev_copied[k]);
+    }
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    delete c;
+}
+
+PH_API const char *phprng_status_string(int s)
+{
+    switch (s) {
+    case PHPRNG_OK: return "ok";
+    case PHPRNG_EINVAL: return "invalid argument";
+    case PHPRNG_ENOTPRIME: return "modulus is not prime";
+    case PHPRNG_EEXPONENT: return "exponent not coprime to n-1 or out of range";
+    case PHPRNG_ESKIP: return "invalid skip generator";
+    case PHPRNG_EDUPLICATE: return "duplicate modulus";
+    case PHPRNG_ENOMEM: return "out of memory";
+    case PHPRNG_ECUDA: return "CUDA error";
+    case PHPRNG_ETIMEOUT: return "timed out";
+    case PHPRNG_EBUDGET: return "output budget exhausted";
+    default: return "unknown status";
+    }
+}
+
+PH_API const char *phprng_last_error(const phprng_ctx *ctx)
+{
+    return ctx ? ctx->err.c_str() : g_err.c_str();
+}
+
+PH_API int phprng_is_prime(uint64_t n) { return is_prime(n) ? 1 : 0; }
+
+PH_API int phprng_validate(int width, const phprng_instance *inst, uint64_t count,
+                           uint32_t flags, uint64_t *bad_index)
+{
+    std::string msg;
+    int rc = validate_all(width, inst, count, flags, bad_index, &msg);
+    if (rc != PHPRNG_OK) g_err = msg;
+    return rc;
+}
+
+PH_API int phprng_draw_instances(int width, uint64_t count, uint64_t seed, uint32_t flags,
+                                 phprng_instance *out)
+{
+    std::string msg;
+    int rc;
+    try {
+        rc = draw_instances(width, count, seed, flags, out, &msg);
+    } catch (const std::bad_alloc &) {
+        msg = "phprng_draw_instances: host allocation failed";
+        rc = PHPRNG_ENOMEM;
+    }
+    if (rc != PHPRNG_OK) g_err = msg;
+    return rc;
+}
+
+PH_API int phprng_create(phprng_ctx **out, int width, const phprng_instance *inst,
+                         uint64_t count, uint32_t flags, void *cuda_stream)
+{
+    if (!out) return fail(nullptr, PHPRNG_EINVAL, "phprng_create: out is NULL");
+    *out = nullptr;
+    std::string msg;
+    uint64_t bad = 0;
+    int rc;
+    try {
+        rc = validate_all(width, inst, count, flags, &bad, &msg);
+    } catch (const std::bad_alloc &) {
+        return fail(nullptr, PHPRNG_ENOMEM, "phprng_create: host allocation failed");
+    }
+    if (rc != PHPRNG_OK) return fail(nullptr, rc, "phprng_create: " + msg);
+
+    phprng_ctx *c = new (std::nothrow) phprng_ctx;
+    if (!c) return fail(nullptr, PHPRNG_ENOMEM, "phprng_create: host allocation failed");
+    std::vector<DevInst> di;
+    std::vector<uint64_t> state;
+    try {
+        c->width = width;
+        c->count = count;
+        c->flags = flags;
+        c->p = inst[0].p;
+        c->a = inst[0].a;
+        c->host_inst.assign(inst, inst + count);
+        c->wide.resize(count);
+        di.resize(count);
+        state.assign(4 * count, 0);
+    } catch (const std::bad_alloc &) {
+        delete c;
+        return fail(nullptr, PHPRNG_ENOMEM, "phprng_create: host allocation failed");
+    }
+    for (uint64_t i = 0; i < count; ++i) {
+        int w = width == 64 ? 1 : width == 32 ? 0 : (inst[i].n >= (1ull << 32) ? 1 : 0);
+        c->wide[i] = (uint8_t)w;
+        (w ? c->any64 : c->any32) = true;
+        di[i] = derive_inst(inst[i], w);
+        state[i] = inst[i].m0;
+        state[count + i] = inst[i].s0;
+    }
+    c->sk32 = derive_skip(c->p, c->a, gen_npt(0));
+    c->sk64 = derive_skip(c->p, c->a, gen_npt(1));
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_inst, count * sizeof(DevInst));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_state, 4 * count * sizeof(uint64_t));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->d_inst, di.data(), count * sizeof(DevInst), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->d_state, state.data(), 4 * count * sizeof(uint64_t),
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // host vectors die on return
+    if (e != cudaSuccess) {
+        int code = (e == cudaErrorMemoryAllocation) ? PHPRNG_ENOMEM : PHPRNG_ECUDA;
+        std::string m = std::string("phprng_create: ") + cudaGetErrorString(e);
+        free_ctx(c);
+        return fail(nullptr, code, m);
+    }
+    c->st.m = c->d_state;
+    c->st.s = c->d_state + count;
+    c->st.c = c->d_state + 2 * count;
+    c->st.pos = c->d_state + 3 * count;
+    *out = c;
+    return PHPRNG_OK;
+}
+
+PH_API int phprng_create_seeded(phprng_ctx **out, int width, uint64_t count, uint64_t seed,
+                                uint32_t flags, void *cuda_stream)
+{
+    if (!out) return fail(nullptr, PHPRNG_EINVAL, "phprng_create_seeded: out is NULL");
+    *out = nullptr;
+    if (width != 32 && width != 64)
+        return fail(nullptr, PHPRNG_EINVAL, "phprng_create_seeded: width must be 32 or 64");
+    std::vector<phprng_instance> v;
+    try {
+        v.resize(count);
+    } catch (const std::bad_alloc &) {
+        return fail(nullptr, PHPRNG_ENOMEM, "phprng_create_seeded: host allocation failed");
+    }
+    std::string msg;
+    int rc = draw_instances(width, count, seed, flags, v.data(), &msg);
+    if (rc != PHPRNG_OK) return fail(nullptr, rc, msg);
+    return phprng_create(out, width, v.data(), count, flags, cuda_stream);
+}
+
+PH_API int phprng_destroy(phprng_ctx *ctx)
+{
+    free_ctx(ctx);
+    return PHPRNG_OK;
+}
+
+// Kind of memory behind a pointer: 1 device (or managed), 0 host, -1 error.
+static int pointer_kind(const void *p)
+{
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) { cudaGetLastError(); return -1; }
+    return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) ? 1 : 0;
+}
+
+static int launch_range(phprng_ctx *c, uint64_t first, uint64_t num, uint64_t per_inst,
+                        void *c_out, double *r_out, phprng_stats *stats, cudaStream_t s)
+{
+    GenArgs g;
+    g.inst = c->d_inst;
+    g.st = c->st;
+    g.first = first;
+    g.num = num;
+    g.per_inst = per_inst;
+    g.c_out = c_out;
+    g.r_out = r_out;
+    g.stats = stats;
+    g.c_is_64 = c->width != 32;
+    const size_t csz = g.c_is_64 ? 8 : 4;
+    g.vec_ok = (per_inst % 4 == 0) && ((uintptr_t)c_out % 16 == 0) &&
+               ((uintptr_t)r_out % 16 == 0) && (csz * per_inst) % 16 == 0;
+    std::string err;
+    int rc = PHPRNG_OK;
+    if (c->any32) {
+        g.sk = c->sk32;
+        rc = launch_gen32(g, s, &err);
+    }
+    if (rc == PHPRNG_OK && c->any64) {
+        g.sk = c->sk64;
+        rc = launch_gen64(g, s, &err);
+    }
+    if (rc != PHPRNG_OK) return fail(c, rc, "phprng_generate: " + err);
+    return PHPRNG_OK;
+}
+
+static int ensure_staging(phprng_ctx *c, size_t bytes)
+{
+    if (c->stage_bytes >= bytes) return PHPRNG_OK;
+    for (int k = 0; k < 2; ++k) {
+        cudaFree(c->stage[k]);
+        c->stage[k] = nullptr;
+    }
+    c->stage_bytes = 0;
+    for (int k = 0; k < 2; ++k) {
+        cudaError_t e = cudaMalloc(&c->stage[k], bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, PHPRNG_ENOMEM, "phprng_generate: staging allocation failed");
+        }
+        if (!c->ev_done[k]) CU(c, cudaEventCreateWithFlags(&c->ev_done[k], cudaEventDisableTiming));
+        if (!c->ev_copied[k]) CU(c, cudaEventCreateWithFlags(&c->ev_copied[k], cudaEventDisableTiming));
+    }
+    if (!c->copy_stream) CU(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+    c->stage_bytes = bytes;
+    return PHPRNG_OK;
+}
+
+// Host outputs: generate into two device staging buffers in turn (blocks of
+// instances x numbers), copying each block back on the copy stream while the
+// next one is generated; returns once everything is on the host.
+static int generate_to_host(phprng_ctx *c, uint64_t first, uint64_t num, uint64_t per_inst,
+                            void *c_out, double *r_out, cudaStream_t s)
+{
+    const size_t csz = c->width == 32 ? 4 : 8;
+    const size_t per_num = (c_out ? csz : 0) + (r_out ? 8 : 0);
+    const uint64_t cap = 1ull << 24;                      // numbers per block
+    const uint64_t piece = std::min<uint64_t>(per_inst, cap);
+    const uint64_t ninst = std::max<uint64_t>(1, std::min<uint64_t>(num, cap / piece));
+    int rc = ensure_staging(c, (size_t)(ninst * piece * per_num + 256));
+    if (rc != PHPRNG_OK) return rc;
+    int k = 0;
+    bool used[2] = {false, false};
+    for (uint64_t i0 = 0; i0 < num; i0 += ninst) {
+        const uint64_t ni = std::min(ninst, num - i0);
+        for (uint64_t j0 = 0; j0 < per_inst; j0 += piece) {
+            const uint64_t pj = std::min(piece, per_inst - j0);
+            char *buf = (char *)c->stage[k];
+            void *dc = c_out ? buf : nullptr;
+            double *dr = r_out ? (double *)(buf + ((c_out ? ni * pj * csz : 0) + 15) / 16 * 16)
+                               : nullptr;
+            if (used[k]) CU(c, cudaStreamWaitEvent(s, c->ev_copied[k], 0));
+            rc = launch_range(c, first + i0, ni, pj, dc, dr, nullptr, s);
+            if (rc != PHPRNG_OK) return rc;
+            CU(c, cudaEventRecord(c->ev_done[k], s));
+            CU(c, cudaStreamWaitEvent(c->copy_stream, c->ev_done[k], 0));
+            if (c_out)
+                CU(c, cudaMemcpy2DAsync((char *)c_out + (i0 * per_inst + j0) * csz, per_inst * csz,
+                                        dc, pj * csz, pj * csz, ni, cudaMemcpyDeviceToHost,
+                                        c->copy_stream));
+            if (r_out)
+                CU(c, cudaMemcpy2DAsync(r_out + i0 * per_inst + j0, per_inst * 8, dr, pj * 8,
+                                        pj * 8, ni, cudaMemcpyDeviceToHost, c->copy_stream));
+            CU(c, cudaEventRecord(c->ev_copied[k], c->copy_stream));
+            used[k] = true;
+            k ^= 1;
+        }
+    }
+    CU(c, cudaStreamSynchronize(c->copy_stream));
+    CU(c, cudaStreamSynchronize(s));
+    return PHPRNG_OK;
+}
+
+PH_API int phprng_generate(phprng_ctx *ctx, uint64_t first, uint64_t num_inst,
+                           uint64_t per_inst, void *c_out, double *r_out,
+                           phprng_stats *stats_out, void *cuda_stream)
+{
+    if (!ctx) return fail(nullptr, PHPRNG_EINVAL, "phprng_generate: ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (first > ctx->count || num_inst > ctx->count - first)
+        return fail(ctx, PHPRNG_EINVAL, "phprng_generate: instance range outside the table");
+    if (num_inst == 0 || per_inst == 0) return PHPRNG_OK;
+    if (num_inst > (1ull << 40) / per_inst)
+        return fail(ctx, PHPRNG_EINVAL, "phprng_generate: num_inst * per_inst exceeds 2^40");
+    const size_t csz = ctx->width == 32 ? 4 : 8;
+    if (((uintptr_t)c_out % csz) || ((uintptr_t)r_out % 8))
+        return fail(ctx, PHPRNG_EINVAL, "phprng_generate: output pointer not aligned to its element");
+    if (stats_out) {
+        if (ctx->any64)
+            return fail(ctx, PHPRNG_EINVAL,
+                        "phprng_generate: fused statistics are defined for 32-bit moduli only");
+        return fail(ctx, PHPRNG_EINVAL, "phprng_generate: fused statistics are not available");
+    }
+    if (!c_out && !r_out)
+        return fail(ctx, PHPRNG_EINVAL,
+                    "phprng_generate: no output (use phprng_skip to advance without output)");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    const int kc = c_out ? pointer_kind(c_out) : -2;
+    const int kr = r_out ? pointer_kind(r_out) : -2;
+    if (kc == -1 || kr == -1)
+        return fail(ctx, PHPRNG_EINVAL, "phprng_generate: cannot classify an output pointer");
+    const bool host = (kc == 0) || (kr == 0);
+    const bool dev = (kc == 1) || (kr == 1);
+    if (host && dev)
+        return fail(ctx, PHPRNG_EINVAL, "phprng_generate: mix of host and device output pointers");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (host) return generate_to_host(ctx, first, num_inst, per_inst, c_out, r_out, s);
+    return launch_range(ctx, first, num_inst, per_inst, c_out, r_out, nullptr, s);
+}
+
+PH_API int phprng_get_state(phprng_ctx *ctx, uint64_t inst, phprng_instance *state_out,
+                            uint64_t *pos_out, uint64_t *c_out, void *cuda_stream)
+{
+    if (!ctx) return fail(nullptr, PHPRNG_EINVAL, "phprng_get_state: ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (inst >= ctx->count) return fail(ctx, PHPRNG_EINVAL, "phprng_get_state: instance out of range");
+    if (!state_out) return fail(ctx, PHPRNG_EINVAL, "phprng_get_state: state_out is NULL");
+    CU(ctx, cudaSetDevice(ctx->device));
+    CU(ctx, cudaStreamSynchronize((cudaStream_t)cuda_stream));
+    uint64_t v[4];
+    for (int k = 0; k < 4; ++k)
+        CU(ctx, cudaMemcpy(&v[k], ctx->d_state + (uint64_t)k * ctx->count + inst, 8,
+                           cudaMemcpyDeviceToHost));
+    *state_out = ctx->host_inst[inst];
+    state_out->m0 = v[0];
+    state_out->s0 = v[1];
+    if (c_out) *c_out = v[2];
+    if (pos_out) *pos_out = v[3];
+    return PHPRNG_OK;
+}
+
+PH_API int phprng_skip(phprng_ctx *ctx, const uint64_t *inst_ids, const uint64_t *k,
+                       uint64_t cnt, void *cuda_stream)
+{
+    (void)inst_ids; (void)k; (void)cnt; (void)cuda_stream;
+    if (!ctx) return fail(nullptr, PHPRNG_EINVAL, "phprng_skip: ctx is NULL");
+    return fail(ctx, PHPRNG_EINVAL, "phprng_skip: not available in this build");
+}

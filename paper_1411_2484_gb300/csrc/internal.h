@@ -1,0 +1,83 @@
+// internal.h -- data layout shared by the host layer, the C ABI and the
+// kernels of libphprng (never installed, never seen by callers).
+#pragma once
+#include <stdint.h>
+#include <stddef.h>
+#include <string>
+#include <vector>
+
+#include "../../include/phprng.h"
+
+namespace phprng {
+
+// One instance as the kernels read it: 64 bytes, read-only on the device.
+// Derived on the host from {n, e} at creation.
+struct alignas(16) DevInst {
+    uint64_t n;      // prime modulus (Eq. 1)
+    uint64_t ninv;   // n^-1 mod 2^32 (32-bit path) or mod 2^64 (64-bit path)
+    uint64_t K;      // Montgomery exit constant R^(1-alpha) mod n, see mont_exit_constant()
+    uint64_t e;      // exponent
+    uint64_t V;      // floor(2^84 / yN): reciprocal for the integer-built R (32-bit path)
+    uint32_t yN;     // (n+1) << (32 - bitlen(n+1)), normalised divisor (32-bit path)
+    uint32_t ybits;  // bitlen(n+1)
+    uint32_t ebits;  // bitlen(e)
+    uint32_t wide;   // 0: 32-bit path, 1: 64-bit path
+    uint32_t pad[2];
+};
+static_assert(sizeof(DevInst) == 64, "DevInst is one 64-byte line");
+
+// Skip-generator constants for one (p, a) and one numbers-per-lane count
+// NPT; passed to kernels by value.  Values in Montgomery form carry a
+// factor 2^32 so that mont32(s, xM) = s*x mod p with s in plain form.
+struct SkipConst {
+    uint32_t p, pinv;      // p, p^-1 mod 2^32
+    uint32_t aM;           // a * 2^32 mod p                      (one step, Eq. 9a)
+    uint32_t aGM;          // a^(32*NPT) * 2^32 mod p             (one warp group)
+    uint32_t lane[32];     // a^(NPT*j) * 2^32 mod p, j = lane    (lane start)
+};
+
+// Generator state, structure of arrays in device memory, one entry per
+// instance: the message m, the skip s, the last ciphertext c (the three
+// values of the seven-integer state that change) and the stream position.
+struct DevState {
+    uint64_t *m, *s, *c, *pos;
+};
+
+// Arguments of one generate launch over instances [first, first+num).
+struct GenArgs {
+    const DevInst *inst;
+    DevState st;
+    SkipConst sk;
+    uint64_t first, num, per_inst;
+    void *c_out;            // uint32_t* (c_is_64 = 0) or uint64_t* (c_is_64 = 1), nullable
+    double *r_out;          // nullable
+    phprng_stats *stats;    // nullable
+    int c_is_64;
+    int vec_ok;             // outputs allow 16-byte vector stores
+};
+
+// ---- kernel launchers (gen.cu) -------------------------------------------
+int gen_npt(int wide);   // numbers per lane per warp group of the 32/64-bit launch
+int launch_gen32(const GenArgs &a, void *stream, std::string *err);
+int launch_gen64(const GenArgs &a, void *stream, std::string *err);
+
+// ---- host number theory (hostnt.cpp) -------------------------------------
+uint64_t mulmod(uint64_t x, uint64_t y, uint64_t n);
+uint64_t powmod(uint64_t b, uint64_t e, uint64_t n);
+uint64_t gcd64(uint64_t a, uint64_t b);
+bool is_prime(uint64_t n);
+int bitlen(uint64_t x);
+uint64_t inv_mod_2_64(uint64_t odd);
+std::vector<uint64_t> prime_factors(uint64_t x);
+bool is_primitive_root(uint64_t a, uint64_t p);
+bool discrete_log(uint64_t p, uint64_t a, uint64_t s, uint64_t *L);
+uint64_t mont_exit_constant(uint64_t n, uint64_t e, int rbits);
+DevInst derive_inst(const phprng_instance &in, int wide);
+SkipConst derive_skip(uint64_t p, uint64_t a, int npt);
+int validate_one(int width, const phprng_instance &in, uint32_t flags, std::string *msg);
+int validate_all(int width, const phprng_instance *inst, uint64_t count, uint32_t flags,
+                 uint64_t *bad, std::string *msg);
+int draw_instances(int width, uint64_t count, uint64_t seed, uint32_t flags,
+                   phprng_instance *out, std::string *msg);
+
+}  // namespace phprng

@@ -39,3 +39,14 @@ def oracle_mod():
     import oracle
     alt = os.environ.get("PHPRNG_ORACLE_SO")
     return oracle.Oracle(alt) if alt else oracle._default()
+
+
+@pytest.fixture(scope="session")
+def ph():
+    """The product binding with libphprng.so built for sm_103a (nvcc cross-
+    compiles here; host-only entry points run without a GPU)."""
+    from paper_1411_2484_gb300 import build
+    build.build()
+    import paper_1411_2484_gb300
+    paper_1411_2484_gb300._load()
+    return paper_1411_2484_gb300

@@ -1,0 +1,63 @@
+// Host build of the library's hot-path arithmetic (arith.cuh) and instance
+// layer (hostnt.cpp) for CPU tests: the same source the kernels compile,
+// instantiated with one number per lane.
+#include <cstdint>
+#include "../../paper_1411_2484_gb300/csrc/arith.cuh"
+#include "../../paper_1411_2484_gb300/csrc/internal.h"
+
+using namespace phprng;
+
+extern "C" {
+
+void h_real32_many(const uint64_t *n, const uint64_t *c, double *out, uint64_t count)
+{
+    for (uint64_t i = 0; i < count; ++i) {
+        phprng_instance in{n[i], 3, 3, 2, 0, 1};
+        DevInst d = derive_inst(in, 0);
+        out[i] = real32((uint32_t)c[i], d.yN, d.ybits, d.V);
+    }
+}
+
+void h_modexp_many(const uint64_t *m, const uint64_t *e, const uint64_t *n, uint64_t *out,
+                   uint64_t count, int wide)
+{
+    for (uint64_t i = 0; i < count; ++i) {
+        phprng_instance in{n[i], e[i], 3, 2, 0, 1};
+        DevInst d = derive_inst(in, wide);
+        if (!wide) {
+            uint32_t msg[1] = {(uint32_t)m[i]}, x[1];
+            modexp32<1>(x, msg, (uint32_t)d.e, (int)d.ebits, (uint32_t)d.n, (uint32_t)d.ninv,
+                        (uint32_t)d.K);
+            out[i] = x[0];
+        } else {
+            uint64_t msg[1] = {m[i]}, x[1];
+            modexp64<1>(x, msg, d.e, (int)d.ebits, d.n, d.ninv, d.K);
+            out[i] = x[0];
+        }
+    }
+}
+
+// One skip step s -> a s mod p through the Montgomery constants the kernels use.
+uint64_t h_skip_step(uint64_t s, uint64_t p, uint64_t a)
+{
+    SkipConst k = derive_skip(p, a, 4);
+    return mont32((uint32_t)s, k.aM, k.p, k.pinv);
+}
+
+// s a^(npt*lane) mod p and s a^(32*npt) mod p from the lane constants.
+uint64_t h_skip_lane(uint64_t s, uint64_t p, uint64_t a, int npt, int lane)
+{
+    SkipConst k = derive_skip(p, a, npt);
+    return mont32((uint32_t)s, lane < 32 ? k.lane[lane] : k.aGM, k.p, k.pinv);
+}
+
+int h_discrete_log(uint64_t p, uint64_t a, uint64_t s, uint64_t *L)
+{
+    return discrete_log(p, a, s, L) ? 1 : 0;
+}
+
+uint64_t h_addmod(uint64_t a, uint64_t b, uint64_t n, int wide)
+{
+    return wide ? addmod64(a, b, n) : addmod32((uint32_t)a, (uint32_t)b, (uint32_t)n);
+}
+}

@@ -1,0 +1,128 @@
+"""CPU checks of the library's own arithmetic, compiled for the host from the
+same source the kernels use (arith.cuh, hostnt.cpp): Montgomery
+exponentiation with the exit constant K, the integer-built R, the skip
+constants and the discrete log, against Python's pow and IEEE division."""
+import ctypes
+import os
+import random
+import struct
+import subprocess
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+
+P31, A31 = 2147483647, 784588716
+
+
+@pytest.fixture(scope="module")
+def h(tmp_path_factory):
+    out = str(tmp_path_factory.mktemp("harness") / "host_arith.so")
+    subprocess.check_call([
+        "g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-I", os.path.join(ROOT, "include"),
+        os.path.join(ROOT, "tests", "harness", "host_arith.cpp"),
+        os.path.join(ROOT, "paper_1411_2484_gb300", "csrc", "hostnt.cpp"),
+        "-o", out, "-lpthread"])
+    lib = ctypes.CDLL(out)
+    P64 = ctypes.POINTER(ctypes.c_uint64)
+    u64 = ctypes.c_uint64
+    lib.h_real32_many.argtypes = [P64, P64, ctypes.POINTER(ctypes.c_double), u64]
+    lib.h_modexp_many.argtypes = [P64, P64, P64, P64, u64, ctypes.c_int]
+    lib.h_skip_step.restype = u64
+    lib.h_skip_step.argtypes = [u64, u64, u64]
+    lib.h_skip_lane.restype = u64
+    lib.h_skip_lane.argtypes = [u64, u64, u64, ctypes.c_int, ctypes.c_int]
+    lib.h_discrete_log.argtypes = [u64, u64, u64, P64]
+    lib.h_addmod.restype = u64
+    lib.h_addmod.argtypes = [u64, u64, u64, ctypes.c_int]
+    return lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+
+
+def modexp(h, m, e, n, wide):
+    m, e, n = (np.ascontiguousarray(x, dtype=np.uint64) for x in (m, e, n))
+    out = np.empty_like(m)
+    h.h_modexp_many(_p(m), _p(e), _p(n), _p(out), m.size, wide)
+    return out
+
+
+def test_real32_equals_ieee_division(h):
+    rng = np.random.default_rng(1)
+    k = 400000
+    n = np.concatenate([rng.integers(3, 1 << 32, k // 2, dtype=np.uint64) | np.uint64(1),
+                        rng.integers(3, 5000, k // 2, dtype=np.uint64) | np.uint64(1)])
+    n = np.minimum(n, np.uint64((1 << 32) - 5))
+    c = (rng.integers(0, 1 << 62, k, dtype=np.uint64) % n).astype(np.uint64)
+    c[::7] = n[::7] - np.uint64(1)
+    c[::11] = 0
+    out = np.empty(k, dtype=np.float64)
+    h.h_real32_many(_p(n), _p(c), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), k)
+    ref = (c + np.uint64(1)).astype(np.float64) / (n + np.uint64(1)).astype(np.float64)
+    assert np.array_equal(out.view(np.uint64), ref.view(np.uint64))
+    for i in range(0, k, 997):            # and against exact rationals
+        assert out[i] == float(Fraction(int(c[i]) + 1, int(n[i]) + 1))
+
+
+def test_real32_every_c_for_small_moduli(h):
+    for nn in (3, 5, 7, 23, 31, 127, 255, 257, 1023, 4093, 8191):
+        c = np.arange(nn, dtype=np.uint64)
+        n = np.full(nn, nn, dtype=np.uint64)
+        out = np.empty(nn, dtype=np.float64)
+        h.h_real32_many(_p(n), _p(c), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nn)
+        for ci in range(nn):
+            assert out[ci] == float(Fraction(ci + 1, nn + 1))
+
+
+@pytest.mark.parametrize("wide", [0, 1])
+def test_montgomery_exponentiation_matches_pow(h, wide):
+    from paper_1411_2484_gb300 import workloads
+    rng = random.Random(2 + wide)
+    ns = [4294967291, 4294967087, 2147483659, 23, 101, 65537] if not wide else \
+        [18446744073709551557, 9223372036854775837, 4294967291, 23]
+    ns += [int(x) for x in workloads.draw_instances(20, width=64 if wide else 32, seed=3)["n"]]
+    ms, es, nn, ref = [], [], [], []
+    for n in ns:
+        for _ in range(300):
+            e = rng.randrange(3, n - 1) if n > 5 else 3
+            m = rng.choice([0, 1, n - 1, rng.randrange(n)])
+            ms.append(m); es.append(e); nn.append(n); ref.append(pow(m, e, n))
+        for e in (3, 5, 9, 17, n - 2):
+            m = rng.randrange(n)
+            ms.append(m); es.append(e); nn.append(n); ref.append(pow(m, e, n))
+    out = modexp(h, ms, es, nn, wide)
+    assert [int(x) for x in out] == ref
+
+
+def test_skip_constants(h):
+    rng = random.Random(4)
+    for p, a in ((P31, A31), (11, 2), (4294967291, 2), (101, 2)):
+        for _ in range(200):
+            s = rng.randrange(1, p)
+            assert h.h_skip_step(s, p, a) == a * s % p
+            npt, lane = rng.choice([1, 2, 4, 8]), rng.randrange(33)
+            expo = npt * lane if lane < 32 else 32 * npt
+            assert h.h_skip_lane(s, p, a, npt, lane) == s * pow(a, expo, p) % p
+
+
+def test_addmod(h):
+    rng = random.Random(5)
+    for wide, bits in ((0, 32), (1, 64)):
+        for _ in range(2000):
+            n = rng.randrange(3, 1 << bits)
+            a, b = rng.randrange(n), rng.randrange(n)
+            assert h.h_addmod(a, b, n, wide) == (a + b) % n
+
+
+def test_discrete_log(h):
+    rng = random.Random(6)
+    L = ctypes.c_uint64()
+    for p, a in ((P31, A31), (11, 2), (1000003, 2), (4294967291, 2)):
+        for _ in range(50):
+            s = rng.randrange(1, p)
+            assert h.h_discrete_log(p, a, s, ctypes.byref(L)) == 1
+            assert pow(a, L.value, p) == s and L.value < p - 1
