@@ -158,6 +158,19 @@ int phprng_skip(phprng_ctx *ctx, const uint64_t *inst_ids, const uint64_t *k, ui
 int phprng_get_state(phprng_ctx *ctx, uint64_t inst, phprng_instance *state_out,
                      uint64_t *pos_out, uint64_t *c_out, void *cuda_stream);
 
+/* ---------------------------------------------------------------- measurement */
+
+/* Measures the current device's throughput for one instruction form and
+ * stores operations per second in *ops_per_s (eight independent chains per
+ * thread over a full-occupancy grid, timed with CUDA events on cuda_stream;
+ * the call synchronizes).  which: 0 mul.lo.u32, 1 mad.hi.u32, 2 mad.wide.u32
+ * (each 32-bit product half is the unit of the generator's roofline: forms
+ * 0 and 1 make one half, form 2 two), 3 the generator's Montgomery product
+ * mod a 32-bit prime, 4 fma.rn.f64.  Allocates and frees a small device
+ * buffer.  The paper has no counterpart: this is the measurement used to
+ * state the multiply-bound roofline of Eq. 9c. */
+int phprng_microbench(int which, double *ops_per_s, void *cuda_stream);
+
 /* ---------------------------------------------------------------- host only
  * These run on the CPU and need no GPU. */
 

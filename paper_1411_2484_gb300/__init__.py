@@ -35,7 +35,7 @@ PHPRNG_ALLOW_SHARED_N = 0x2
 EXPORTED = [
     "phprng_create", "phprng_create_seeded", "phprng_destroy", "phprng_last_error",
     "phprng_status_string", "phprng_generate", "phprng_skip", "phprng_get_state",
-    "phprng_is_prime", "phprng_validate", "phprng_draw_instances",
+    "phprng_is_prime", "phprng_validate", "phprng_draw_instances", "phprng_microbench",
 ]
 
 
@@ -94,6 +94,7 @@ def _load():
         lib.phprng_is_prime.argtypes = [u64]
         lib.phprng_validate.argtypes = [i32, P_inst, u64, u32, P64]
         lib.phprng_draw_instances.argtypes = [i32, u64, u64, u32, P_inst]
+        lib.phprng_microbench.argtypes = [i32, ctypes.POINTER(ctypes.c_double), vp]
         _lib = lib
         return lib
 
@@ -219,6 +220,13 @@ def phprng_draw_instances(width, count, seed, flags=0):
     _check(lib.phprng_draw_instances(int(width), int(count), int(seed), int(flags), arr))
     rows = np.frombuffer(arr, dtype=np.uint64).reshape(-1, 6).copy()
     return {k: rows[:, j] for j, k in enumerate(("n", "e", "p", "a", "m0", "s0"))}
+
+
+def phprng_microbench(which, stream=None):
+    """Operations per second of instruction form `which` on the current device."""
+    out = ctypes.c_double()
+    _check(_load().phprng_microbench(int(which), ctypes.byref(out), _stream(stream)))
+    return out.value
 
 
 class Generator:

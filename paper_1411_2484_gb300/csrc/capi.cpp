@@ -33,6 +33,12 @@ struct phprng_ctx {
     uint64_t *d_state = nullptr;      // 4 * count: m | s | c | pos
     DevState st{};
     SkipConst sk32{}, sk64{};
+    std::vector<uint64_t> pos_host;   // host mirror of the stream positions
+    // skip-ahead: cycle positions of the seeds and the prefix table (lazy)
+    uint64_t *d_L0 = nullptr, *d_T = nullptr;
+    uint32_t *d_P = nullptr;
+    SkipTable tbl{};
+    bool skip_ready = false;
     // host-output staging
     void *stage[2] = {nullptr, nullptr};
     size_t stage_bytes = 0;
@@ -67,6 +73,9 @@ static void free_ctx(phprng_ctx *c)
     cudaDeviceSynchronize();
     cudaFree(c->d_inst);
     cudaFree(c->d_state);
+    cudaFree(c->d_L0);
+    cudaFree(c->d_T);
+    cudaFree(c->d_P);
     for (int k = 0; k < 2; ++k) {
         cudaFree(c->stage[k]);
         if (c->ev_done[k]) cudaEventDestroy(c->ev_done[k]);
@@ -150,6 +159,7 @@ PH_API int phprng_create(phprng_ctx **out, int width, const phprng_instance *ins
         c->p = inst[0].p;
         c->a = inst[0].a;
         c->host_inst.assign(inst, inst + count);
+        c->pos_host.assign(count, 0);
         c->wide.resize(count);
         di.resize(count);
         state.assign(4 * count, 0);
@@ -356,8 +366,11 @@ PH_API int phprng_generate(phprng_ctx *ctx, uint64_t first, uint64_t num_inst,
     if (host && dev)
         return fail(ctx, PHPRNG_EINVAL, "phprng_generate: mix of host and device output pointers");
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    if (host) return generate_to_host(ctx, first, num_inst, per_inst, c_out, r_out, s);
-    return launch_range(ctx, first, num_inst, per_inst, c_out, r_out, nullptr, s);
+    int rc = host ? generate_to_host(ctx, first, num_inst, per_inst, c_out, r_out, s)
+                  : launch_range(ctx, first, num_inst, per_inst, c_out, r_out, nullptr, s);
+    if (rc == PHPRNG_OK)
+        for (uint64_t i = first; i < first + num_inst; ++i) ctx->pos_host[i] += per_inst;
+    return rc;
 }
 
 PH_API int phprng_get_state(phprng_ctx *ctx, uint64_t inst, phprng_instance *state_out,
@@ -381,10 +394,95 @@ PH_API int phprng_get_state(phprng_ctx *ctx, uint64_t inst, phprng_instance *sta
     return PHPRNG_OK;
 }
 
+// Builds, once per context, the cycle positions L0 of the seeds (discrete
+// logs on the host) and the prefix table of the skip cycle (on the device).
+static int ensure_skip(phprng_ctx *c, cudaStream_t s)
+{
+    if (c->skip_ready) return PHPRNG_OK;
+    std::vector<uint64_t> s0(c->count), L0(c->count);
+    for (uint64_t i = 0; i < c->count; ++i) s0[i] = c->host_inst[i].s0;
+    if (!discrete_logs(c->p, c->a, s0.data(), c->count, L0.data()))
+        return fail(c, PHPRNG_ESKIP, "phprng_skip: no discrete log for a seed s0 (a not a primitive root?)");
+    SkipTable tb = derive_skip_table(c->p, c->a);
+    uint64_t *seg = nullptr;
+    cudaError_t e = cudaMalloc(&c->d_L0, c->count * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_T, tb.nT * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_P, tb.nT * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&seg, tb.nT * 8);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->d_L0, L0.data(), c->count * 8, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) {
+        cudaFree(seg);
+        cudaFree(c->d_L0); cudaFree(c->d_T); cudaFree(c->d_P);
+        c->d_L0 = c->d_T = nullptr; c->d_P = nullptr;
+        return cuda_fail(c, e, "phprng_skip: table allocation");
+    }
+    std::string err;
+    int rc = launch_build_skip_table(c->p, c->a, c->d_T, c->d_P, seg, s, &err);
+    cudaError_t e2 = cudaStreamSynchronize(s);                 // L0 host copy, seg lifetime
+    cudaFree(seg);
+    if (rc != PHPRNG_OK) return fail(c, rc, "phprng_skip: " + err);
+    if (e2 != cudaSuccess) return cuda_fail(c, e2, "phprng_skip: table build");
+    tb.T = c->d_T;
+    tb.P = c->d_P;
+    c->tbl = tb;
+    c->skip_ready = true;
+    return PHPRNG_OK;
+}
+
 PH_API int phprng_skip(phprng_ctx *ctx, const uint64_t *inst_ids, const uint64_t *k,
                        uint64_t cnt, void *cuda_stream)
 {
-    (void)inst_ids; (void)k; (void)cnt; (void)cuda_stream;
     if (!ctx) return fail(nullptr, PHPRNG_EINVAL, "phprng_skip: ctx is NULL");
-    return fail(ctx, PHPRNG_EINVAL, "phprng_skip: not available in this build");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (cnt == 0) return PHPRNG_OK;
+    if (!inst_ids || !k) return fail(ctx, PHPRNG_EINVAL, "phprng_skip: NULL request arrays");
+    // merge repeated instances (their skips add) and check for overflow
+    std::vector<SkipReq> reqs;
+    std::vector<uint64_t> slot;
+    try {
+        reqs.reserve(cnt);
+        slot.assign(ctx->count, UINT64_MAX);
+    } catch (const std::bad_alloc &) {
+        return fail(ctx, PHPRNG_ENOMEM, "phprng_skip: host allocation failed");
+    }
+    for (uint64_t j = 0; j < cnt; ++j) {
+        const uint64_t i = inst_ids[j];
+        if (i >= ctx->count) return fail(ctx, PHPRNG_EINVAL, "phprng_skip: instance out of range");
+        if (slot[i] == UINT64_MAX) {
+            slot[i] = reqs.size();
+            reqs.push_back({i, 0});
+        }
+        SkipReq &r = reqs[slot[i]];
+        if (k[j] > UINT64_MAX - r.k || r.k + k[j] > UINT64_MAX - ctx->pos_host[i])
+            return fail(ctx, PHPRNG_EINVAL, "phprng_skip: stream position would exceed 2^64-1");
+        r.k += k[j];
+    }
+    CU(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    int rc = ensure_skip(ctx, s);
+    if (rc != PHPRNG_OK) return rc;
+    SkipReq *d_reqs = nullptr;
+    CU(ctx, cudaMallocAsync((void **)&d_reqs, reqs.size() * sizeof(SkipReq), s));
+    cudaError_t e = cudaMemcpyAsync(d_reqs, reqs.data(), reqs.size() * sizeof(SkipReq),
+                                    cudaMemcpyHostToDevice, s);
+    std::string err;
+    if (e == cudaSuccess)
+        rc = launch_skip(ctx->d_inst, ctx->st, ctx->d_L0, ctx->tbl, d_reqs, reqs.size(), s, &err);
+    cudaError_t e2 = cudaFreeAsync(d_reqs, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "phprng_skip: request upload");
+    if (rc != PHPRNG_OK) return fail(ctx, rc, "phprng_skip: " + err);
+    if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "phprng_skip: cudaFreeAsync");
+    // the pageable upload above completes before cudaMemcpyAsync returns
+    for (const SkipReq &r : reqs) ctx->pos_host[r.inst] += r.k;
+    return PHPRNG_OK;
+}
+
+PH_API int phprng_microbench(int which, double *ops_per_s, void *cuda_stream)
+{
+    if (!ops_per_s) return fail(nullptr, PHPRNG_EINVAL, "phprng_microbench: ops_per_s is NULL");
+    std::string err;
+    int rc = run_microbench(which, ops_per_s, cuda_stream, &err);
+    if (rc != PHPRNG_OK) return fail(nullptr, rc, err);
+    return PHPRNG_OK;
 }

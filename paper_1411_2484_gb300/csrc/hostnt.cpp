@@ -118,69 +118,106 @@ bool is_primitive_root(uint64_t a, uint64_t p)
     return true;
 }
 
-// Discrete log in the subgroup of prime order q generated by g (baby-step
-// giant-step); h must lie in that subgroup.
-static bool bsgs(uint64_t g, uint64_t h, uint64_t q, uint64_t p, uint64_t *x)
-{
-    uint64_t m = 1;
-    while (m * m < q) ++m;
-    std::unordered_map<uint64_t, uint64_t> baby;
-    baby.reserve(m * 2);
-    uint64_t v = 1;
-    for (uint64_t j = 0; j < m; ++j) {
-        baby.emplace(v, j);
-        v = mulmod(v, g, p);
-    }
-    uint64_t gm_inv = powmod(powmod(g, m, p), p - 2, p);
-    uint64_t y = h;
-    for (uint64_t i = 0; i <= m; ++i) {
-        auto it = baby.find(y);
-        if (it != baby.end()) { *x = (i * m + it->second) % q; return true; }
-        y = mulmod(y, gm_inv, p);
-    }
-    return false;
-}
+// Discrete logarithms base a modulo p (a a primitive root): the
+// Pohlig-Hellman reduction to the prime-order subgroups of (Z/pZ)*, digit by
+// digit, with Shanks' baby-step giant-step in each subgroup, then the Chinese
+// remainder theorem.  The baby-step tables depend only on (p, a), so one
+// solver serves every seed of a context.  Used to place seeds s0 on the skip
+// cycle so that Eq. 7 can be evaluated from the prefix table.
+struct DlogSolver {
+    struct Factor {
+        uint64_t q, qk;
+        int k;
+        uint64_t gq, m, gm_inv;
+        std::unordered_map<uint64_t, uint64_t> baby;
+    };
+    uint64_t p, a, N;
+    std::vector<Factor> f;
 
-// L in [0, p-2] with a^L = s mod p (Pohlig-Hellman reduction to prime-order
-// subgroups, digit by digit, then the Chinese remainder theorem).  Places a
-// seed s0 on the skip cycle so Eq. 7 can be evaluated from a prefix table.
+    DlogSolver(uint64_t p_, uint64_t a_) : p(p_), a(a_), N(p_ - 1)
+    {
+        uint64_t rest = N;
+        for (uint64_t q : prime_factors(N)) {
+            Factor F;
+            F.q = q; F.k = 0; F.qk = 1;
+            while (rest % q == 0) { rest /= q; F.qk *= q; ++F.k; }
+            F.gq = powmod(a, N / q, p);                   // generator of the order-q subgroup
+            F.m = 1;
+            while (F.m * F.m < q) ++F.m;
+            F.baby.reserve(F.m * 2);
+            uint64_t v = 1;
+            for (uint64_t j = 0; j < F.m; ++j) {
+                F.baby.emplace(v, j);
+                v = mulmod(v, F.gq, p);
+            }
+            F.gm_inv = powmod(powmod(F.gq, F.m, p), p - 2, p);
+            f.push_back(std::move(F));
+        }
+    }
+
+    bool solve(uint64_t s, uint64_t *L) const
+    {
+        s %= p;
+        if (s == 0) return false;
+        uint64_t x = 0, mod = 1;
+        for (const Factor &F : f) {
+            uint64_t xq = 0, qj = 1;
+            for (int j = 0; j < F.k; ++j) {
+                // h = (s a^-xq)^(N / q^(j+1)) lies in the order-q subgroup
+                uint64_t a_inv_xq = powmod(powmod(a, xq, p), p - 2, p);
+                uint64_t h = powmod(mulmod(s, a_inv_xq, p), N / (qj * F.q), p);
+                uint64_t y = h, d = UINT64_MAX;
+                for (uint64_t i = 0; i <= F.m; ++i) {
+                    auto it = F.baby.find(y);
+                    if (it != F.baby.end()) { d = (i * F.m + it->second) % F.q; break; }
+                    y = mulmod(y, F.gm_inv, p);
+                }
+                if (d == UINT64_MAX) return false;
+                xq += d * qj;
+                qj *= F.q;
+            }
+            // x = x (mod mod), x = xq (mod qk): inverse of mod modulo qk by the
+            // extended Euclidean algorithm
+            int64_t r0 = (int64_t)F.qk, r1 = (int64_t)(mod % F.qk), s0 = 0, s1 = 1;
+            while (r1) {
+                int64_t qq = r0 / r1, tmp = r0 - qq * r1;
+                r0 = r1; r1 = tmp;
+                tmp = s0 - qq * s1; s0 = s1; s1 = tmp;
+            }
+            uint64_t inv = (uint64_t)((s0 % (int64_t)F.qk + (int64_t)F.qk) % (int64_t)F.qk);
+            uint64_t t = (uint64_t)((u128)((xq + F.qk - x % F.qk) % F.qk) * inv % F.qk);
+            x += mod * t;
+            mod *= F.qk;
+        }
+        if (powmod(a, x, p) != s) return false;
+        *L = x % N;
+        return true;
+    }
+};
+
 bool discrete_log(uint64_t p, uint64_t a, uint64_t s, uint64_t *L)
 {
-    uint64_t N = p - 1;
-    s %= p;
-    if (s == 0) return false;
-    uint64_t x = 0, mod = 1;
-    uint64_t rest = N;
-    for (uint64_t q : prime_factors(N)) {
-        int k = 0;
-        uint64_t qk = 1;
-        while (rest % q == 0) { rest /= q; qk *= q; ++k; }
-        uint64_t gq = powmod(a, N / q, p);          // order q
-        uint64_t xq = 0, qj = 1;
-        for (int j = 0; j < k; ++j) {
-            // h = (s a^-xq)^(N / q^(j+1))
-            uint64_t a_inv_xq = powmod(powmod(a, xq, p), p - 2, p);
-            uint64_t h = powmod(mulmod(s, a_inv_xq, p), N / (qj * q), p);
-            uint64_t d;
-            if (!bsgs(gq, h, q, p, &d)) return false;
-            xq += d * qj;
-            qj *= q;
-        }
-        // CRT: x = x (mod mod), x = xq (mod qk); inverse of mod modulo qk by
-        // the extended Euclidean algorithm
-        int64_t r0 = (int64_t)qk, r1 = (int64_t)(mod % qk), s0 = 0, s1 = 1;
-        while (r1) {
-            int64_t qq = r0 / r1, tmp = r0 - qq * r1;
-            r0 = r1; r1 = tmp;
-            tmp = s0 - qq * s1; s0 = s1; s1 = tmp;
-        }
-        uint64_t inv = (uint64_t)((s0 % (int64_t)qk + (int64_t)qk) % (int64_t)qk);
-        uint64_t t = (uint64_t)((u128)((xq + qk - x % qk) % qk) * inv % qk);
-        x += mod * t;
-        mod *= qk;
+    DlogSolver d(p, a);
+    return d.solve(s, L);
+}
+
+bool discrete_logs(uint64_t p, uint64_t a, const uint64_t *s, uint64_t count, uint64_t *L)
+{
+    DlogSolver d(p, a);
+    unsigned nt = std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
+    if (count < 1024) nt = 1;
+    std::vector<int> ok(nt, 1);
+    auto work = [&](unsigned t) {
+        for (uint64_t i = count * t / nt; i < count * (t + 1) / nt; ++i)
+            if (!d.solve(s[i], &L[i])) { ok[t] = 0; return; }
+    };
+    if (nt == 1) work(0);
+    else {
+        std::vector<std::thread> th;
+        for (unsigned t = 0; t < nt; ++t) th.emplace_back(work, t);
+        for (auto &x : th) x.join();
     }
-    if (powmod(a, x, p) != s) return false;
-    *L = x % N;
+    for (int v : ok) if (!v) return false;
     return true;
 }
 
@@ -223,6 +260,8 @@ DevInst derive_inst(const phprng_instance &in, int wide)
     } else {
         d.ninv = inv_mod_2_64(in.n);
         d.K = mont_exit_constant(in.n, in.e, 64);
+        uint64_t r = (uint64_t)((((u128)1) << 64) % in.n);
+        d.r2 = mulmod(r, r, in.n);
     }
     return d;
 }
@@ -238,6 +277,22 @@ SkipConst derive_skip(uint64_t p, uint64_t a, int npt)
     for (int j = 0; j < 32; ++j)
         k.lane[j] = (uint32_t)mulmod(powmod(a, (uint64_t)npt * j, p), R, p);
     return k;
+}
+
+SkipTable derive_skip_table(uint64_t p, uint64_t a)
+{
+    SkipTable t;
+    memset(&t, 0, sizeof t);
+    uint64_t R = (1ull << 32) % p;
+    t.p = (uint32_t)p;
+    t.pinv = (uint32_t)inv_mod_2_64(p);
+    t.aM = (uint32_t)mulmod(a % p, R, p);
+    t.oneM = (uint32_t)R;
+    t.nT = (p - 1) / kSkipB + 1;
+    t.half = (uint64_t)(((u128)p * (p - 1)) / 2);
+    for (int l = 0; l < 32; ++l)
+        t.laneM[l] = (uint32_t)mulmod(powmod(a, 32ull * l, p), R, p);
+    return t;
 }
 
 static std::string fmt_inst(const char *what, const phprng_instance &in)

@@ -22,7 +22,7 @@ struct alignas(16) DevInst {
     uint32_t ybits;  // bitlen(n+1)
     uint32_t ebits;  // bitlen(e)
     uint32_t wide;   // 0: 32-bit path, 1: 64-bit path
-    uint32_t pad[2];
+    uint64_t r2;     // 2^128 mod n (64-bit path): x*y mod n = mont64(mont64(x, y), r2)
 };
 static_assert(sizeof(DevInst) == 64, "DevInst is one 64-byte line");
 
@@ -56,10 +56,43 @@ struct GenArgs {
     int vec_ok;             // outputs allow 16-byte vector stores
 };
 
+// Exact prefix table of the skip generator's cycle (Eq. 7): with
+// Pref(t) = sum_{i=1..t} (a^i mod p), the table holds T[j] = Pref(j*B) and
+// the checkpoint powers P[j] = a^(j*B) mod p for j = 0 .. (p-1)/B.  Built on
+// the device, shared by every instance (one (p, a) per context).
+static constexpr uint32_t kSkipLog2B = 10;
+static constexpr uint32_t kSkipB = 1u << kSkipLog2B;
+
+struct SkipTable {
+    const uint64_t *T;     // prefix sums (exact, < 2^64 because p < 2^32)
+    const uint32_t *P;     // checkpoint powers
+    uint64_t nT;           // entries: (p-1)/B + 1
+    uint64_t half;         // p(p-1)/2 = Pref(p-1), the sum over one cycle
+    uint32_t p, pinv;      // p, p^-1 mod 2^32
+    uint32_t aM;           // a * 2^32 mod p
+    uint32_t oneM;         // 2^32 mod p (1 in Montgomery form)
+    uint32_t laneM[32];    // a^(32*l) * 2^32 mod p: start of lane l's share of a tail
+};
+
+// One skip request after merging duplicates: advance instance `inst` by k.
+struct SkipReq {
+    uint64_t inst, k;
+};
+
 // ---- kernel launchers (gen.cu) -------------------------------------------
 int gen_npt(int wide);   // numbers per lane per warp group of the 32/64-bit launch
 int launch_gen32(const GenArgs &a, void *stream, std::string *err);
 int launch_gen64(const GenArgs &a, void *stream, std::string *err);
+
+// ---- skip-ahead (skip.cu) ------------------------------------------------
+SkipTable derive_skip_table(uint64_t p, uint64_t a);   // constants; T, P set by the caller
+int launch_build_skip_table(uint64_t p, uint64_t a, uint64_t *T, uint32_t *P, uint64_t *seg,
+                            void *stream, std::string *err);
+int launch_skip(const DevInst *inst, DevState st, const uint64_t *L0, SkipTable tbl,
+                const SkipReq *reqs, uint64_t cnt, void *stream, std::string *err);
+
+// ---- measurement (microbench.cu) ------------------------------------------
+int run_microbench(int which, double *ops_per_s, void *stream, std::string *err);
 
 // ---- host number theory (hostnt.cpp) -------------------------------------
 uint64_t mulmod(uint64_t x, uint64_t y, uint64_t n);
@@ -71,6 +104,7 @@ uint64_t inv_mod_2_64(uint64_t odd);
 std::vector<uint64_t> prime_factors(uint64_t x);
 bool is_primitive_root(uint64_t a, uint64_t p);
 bool discrete_log(uint64_t p, uint64_t a, uint64_t s, uint64_t *L);
+bool discrete_logs(uint64_t p, uint64_t a, const uint64_t *s, uint64_t count, uint64_t *L);
 uint64_t mont_exit_constant(uint64_t n, uint64_t e, int rbits);
 DevInst derive_inst(const phprng_instance &in, int wide);
 SkipConst derive_skip(uint64_t p, uint64_t a, int npt);

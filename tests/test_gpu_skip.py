@@ -1,0 +1,151 @@
+"""GPU tests of the Eq. 7 skip-ahead through the C ABI.
+
+The device builds its own prefix table of the skip cycle; the oracle checks
+it with a different table (stride 2^16, plain loop) and with plain stepping.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1411_2484_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+P31, A31 = 2147483647, 784588716
+THREADS = os.cpu_count() or 4
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available()
+    return t
+
+
+@pytest.fixture(scope="module")
+def table31():
+    return oracle.PrefixTable(P31, A31, 1 << 16)
+
+
+def gen(ph, torch, ctx, width, first, num, per):
+    cdt = torch.int32 if width == 32 else torch.int64
+    c = torch.empty(num * per, dtype=cdt, device="cuda")
+    r = torch.empty(num * per, dtype=torch.float64, device="cuda")
+    ph.phprng_generate(ctx, first, num, per, c, r)
+    torch.cuda.synchronize()
+    cn = c.cpu().numpy().view(np.uint32 if width == 32 else np.uint64).astype(np.uint64)
+    return cn.reshape(num, per), r.cpu().numpy().reshape(num, per)
+
+
+def test_skip_small_offsets_against_stepping(ph, torch):
+    inst = workloads.draw_instances(12, seed=41)
+    ctx = ph.phprng_create(32, inst, 0)
+    try:
+        ks = [0, 1, 2, 31, 32, 1023, 1024, 1025, 4095, 70000, 123457, 999999]
+        ph.phprng_skip(ctx, list(range(12)), ks)
+        for i, k in enumerate(ks):
+            n, e, p, a, m0, s0 = (int(inst[x][i]) for x in ("n", "e", "p", "a", "m0", "s0"))
+            _, _, st = oracle.generate(n, e, p, a, m0, s0, k)
+            s = ph.phprng_get_state(ctx, i)
+            assert (s["m"], s["s"], s["pos"]) == (st[0], st[1], k), i
+        # outputs after the skip continue the stream
+        c, r = gen(ph, torch, ctx, 32, 0, 12, 300)
+        for i, k in enumerate(ks):
+            n, e, p, a, m0, s0 = (int(inst[x][i]) for x in ("n", "e", "p", "a", "m0", "s0"))
+            cr, rr, _ = oracle.generate(n, e, p, a, m0, s0, k + 300)
+            assert np.array_equal(c[i], cr[k:]) and np.array_equal(r[i].view(np.uint64),
+                                                                    rr[k:].view(np.uint64))
+    finally:
+        ph.phprng_destroy(ctx)
+
+
+@pytest.mark.parametrize("width", [32, 64])
+def test_skip_large_offsets_against_oracle_table(ph, torch, table31, width):
+    inst = workloads.draw_instances(40, width=width, seed=42 + width)
+    ctx = ph.phprng_create(width, inst, 0)
+    try:
+        rng = np.random.default_rng(width)
+        ks = [int(x) for x in rng.integers(0, 1 << 40, 40)]
+        ks[0], ks[1] = (P31 - 1) * 7, (P31 - 1) * 3 + 5           # exact cycles, cycle + 5
+        ph.phprng_skip(ctx, list(range(40)), ks)
+        L0 = oracle.dlog(P31, A31, inst["s0"])
+        c, r = gen(ph, torch, ctx, width, 0, 40, 257)
+        for i, k in enumerate(ks):
+            n, e = int(inst["n"][i]), int(inst["e"][i])
+            m_k, s_k = table31.state_at(n, int(inst["m0"][i]), int(L0[i]), k)
+            s = ph.phprng_get_state(ctx, i)
+            assert s["pos"] == k + 257
+            cr, rr, st = oracle.generate(n, e, P31, A31, m_k, s_k, 257)
+            assert np.array_equal(c[i], cr), i
+            assert np.array_equal(r[i].view(np.uint64), rr.view(np.uint64)), i
+            assert (s["m"], s["s"]) == st
+    finally:
+        ph.phprng_destroy(ctx)
+
+
+@pytest.mark.parametrize("n,p", [(23, 11), (1019, 509), (4294967087, 13)])
+def test_skip_tiny_cycles(ph, torch, n, p):
+    """Skips spanning many cycles of a tiny skip generator (q large, r small)."""
+    from test_gpu_parity import primitive_root
+    a = primitive_root(p)
+    rng = np.random.default_rng(n)
+    count = 6
+    inst = {"n": [n] * count, "e": [3 if (n - 1) % 3 else 5] * count, "p": [p] * count,
+            "a": [a] * count, "m0": [int(x) for x in rng.integers(0, n, count)],
+            "s0": [int(x) for x in rng.integers(1, p, count)]}
+    ctx = ph.phprng_create(32, inst, ph.PHPRNG_ALLOW_SHARED_N)
+    try:
+        ks = [0, 1, p - 1, 5 * (p - 1) + 3, int(rng.integers(0, 1 << 40)),
+              int(rng.integers(0, 1 << 62))]
+        ph.phprng_skip(ctx, list(range(count)), ks)
+        for i, k in enumerate(ks):
+            st = oracle.skip_stepping(n, p, a, inst["m0"][i], inst["s0"][i], k)
+            s = ph.phprng_get_state(ctx, i)
+            assert (s["m"], s["s"], s["pos"]) == (st[0], st[1], k), (i, k)
+    finally:
+        ph.phprng_destroy(ctx)
+
+
+def test_repeated_instances_add_and_match_generation(ph, torch):
+    inst = workloads.draw_instances(4, seed=44)
+    a = ph.phprng_create(32, inst, 0)
+    b = ph.phprng_create(32, inst, 0)
+    try:
+        ph.phprng_skip(a, [2, 0, 2, 2], [1000, 5, 24, 3000])      # instance 2 by 4024
+        ph.phprng_skip(a, [1], [0])
+        ca, ra = gen(ph, torch, a, 32, 0, 4, 500)
+        cb, rb = gen(ph, torch, b, 32, 0, 4, 4024 + 500)
+        assert np.array_equal(ca[2], cb[2][4024:])
+        assert np.array_equal(ca[0], cb[0][5:505])
+        assert np.array_equal(ca[1], cb[1][:500]) and np.array_equal(ca[3], cb[3][:500])
+        assert ph.phprng_get_state(a, 2)["pos"] == 4524
+        with pytest.raises(ph.PhprngError):
+            ph.phprng_skip(a, [4], [1])                              # out of range
+        with pytest.raises(ph.PhprngError):
+            ph.phprng_skip(a, [0, 0], [2 ** 64 - 1, 2])              # position overflow
+    finally:
+        ph.phprng_destroy(a)
+        ph.phprng_destroy(b)
+
+
+def test_skip_after_generate_and_c_state(ph, torch):
+    """The state's last ciphertext after a skip is Eq. 7c at the new position."""
+    inst = workloads.draw_instances(5, seed=45)
+    ctx = ph.phprng_create(32, inst, 0)
+    try:
+        gen(ph, torch, ctx, 32, 0, 5, 77)
+        ph.phprng_skip(ctx, list(range(5)), [10 ** 9 + i for i in range(5)])
+        for i in range(5):
+            s = ph.phprng_get_state(ctx, i)
+            assert s["c"] == pow(s["m"], int(inst["e"][i]), int(inst["n"][i]))
+            assert s["pos"] == 77 + 10 ** 9 + i
+    finally:
+        ph.phprng_destroy(ctx)
+
+
+def test_microbench_rates(ph, torch):
+    rates = [ph.phprng_microbench(w) for w in range(5)]
+    assert all(r > 1e9 for r in rates), rates
+    print("mul.lo %.3g mad.hi %.3g mad.wide %.3g mont32 %.3g dfma %.3g per s" % tuple(rates))
