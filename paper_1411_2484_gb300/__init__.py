@@ -4,7 +4,8 @@ Thin ctypes binding of libphprng.so: the functions below carry the names of
 the C ABI (include/phprng.h) and only marshal arguments.  Every step of the
 generator runs in the library's CUDA kernels; there is no Python or CPU
 fallback, and every call raises RuntimeError when the compiled library is
-absent.  Build it with ``paper_1411_2484_gb300.build.build()``.
+absent.  Build it with ``paper_1411_2484_gb300.build.build()``; the
+environment variable PHPRNG_LIB selects another build of the same library.
 
 Pointer arguments accept a torch tensor, a numpy array, an int address or
 None.  Stream arguments accept a torch.cuda.Stream, an int handle or None
@@ -17,7 +18,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libphprng.so")
+LIB_PATH = os.environ.get("PHPRNG_LIB") or os.path.join(_HERE, "libphprng.so")
 
 PHPRNG_OK = 0
 PHPRNG_EINVAL = 1

@@ -39,35 +39,39 @@ def up_to_date():
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def _compile(src, ptxas_v):
-    obj = os.path.join(OBJ, os.path.basename(src) + ".o")
-    cmd = [NVCC] + ARCH + FLAGS + (["-Xptxas", "-v"] if ptxas_v else []) + ["-c", src, "-o", obj]
+def _compile(src, ptxas_v, extra=(), obj_dir=OBJ):
+    obj = os.path.join(obj_dir, os.path.basename(src) + ".o")
+    cmd = [NVCC] + ARCH + FLAGS + list(extra) + (["-Xptxas", "-v"] if ptxas_v else []) + \
+        ["-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, r.stdout, r.stderr))
     return obj, r.stderr
 
 
-def build(force=False, ptxas_v=False, verbose=False):
-    """Compile and link libphprng.so; returns its path."""
-    if not force and not ptxas_v and up_to_date():
+def build(force=False, ptxas_v=False, verbose=False, defines=(), out=None):
+    """Compile and link libphprng.so (or `out`, with extra -D `defines`)."""
+    lib = out or LIB
+    if not force and not ptxas_v and not defines and out is None and up_to_date():
         return LIB
-    os.makedirs(OBJ, exist_ok=True)
+    obj_dir = OBJ if out is None else out + ".objs"
+    os.makedirs(obj_dir, exist_ok=True)
     srcs = sources()
+    extra = ["-D" + d for d in defines]
     with ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        results = list(ex.map(lambda s: _compile(s, ptxas_v), srcs))
+        results = list(ex.map(lambda s: _compile(s, ptxas_v, extra, obj_dir), srcs))
     if ptxas_v or verbose:
         for (_, log), s in zip(results, srcs):
             if log.strip():
                 print("==", os.path.basename(s))
                 print(log)
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = lib + ".tmp%d" % os.getpid()
     cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results] + ["-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

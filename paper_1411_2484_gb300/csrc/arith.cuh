@@ -136,46 +136,152 @@ PH_HD double real32(uint32_t c, uint32_t yN, uint32_t ybits, uint64_t V)
     return bits_to_double(((uint64_t)(1022 + E) << 52) + Q);
 }
 
-// c_u = msg_u^e mod n for NPT independent messages (Eq. 9c): left-to-right
-// square-and-multiply over the ebits bits of e on Montgomery products started
-// from the plain messages, then one product with K = R^(1-alpha) mod n (the
-// host derives alpha, the net power of R^-1 the products leave behind).  The
-// bit test is uniform across a warp that shares e, and the NPT chains are
-// independent, which is the instruction-level parallelism of a lane.
-template <int NPT>
-PH_HD void modexp32(uint32_t (&x)[NPT], const uint32_t (&msg)[NPT], uint32_t e, int ebits,
-                    uint32_t n, uint32_t ninv, uint32_t K)
+// Exponentiation program: the left-to-right sliding-window decomposition of
+// one instance's exponent (Menezes, van Oorschot, Vanstone, Handbook of
+// Applied Cryptography, Algorithm 14.85), built on the host.  The table holds
+// the odd powers m, m^3, .., m^(2 tbl - 1); x starts as the table entry of the
+// first window, then each later window is `sq` squarings followed by one
+// product with its table entry, then `tail` squarings close the exponent.
+// One byte per window: sq in bits 0-5, table index in bits 6-7.
+struct alignas(16) ExpProg {
+    uint8_t nent;       // windows (>= 1)
+    uint8_t tail;       // squarings after the last window
+    uint8_t tbl;        // table entries: 1, 2 or 4
+    uint8_t pad;
+    uint8_t ent[28];
+};
+
+PH_HD uint32_t mont(uint32_t a, uint32_t b, uint32_t n, uint32_t ninv) { return mont32(a, b, n, ninv); }
+PH_HD uint64_t mont(uint64_t a, uint64_t b, uint64_t n, uint64_t ninv) { return mont64(a, b, n, ninv); }
+
+// x_u = MP(x_u, y_u) for every u.
+template <int NPT, typename W>
+PH_HD void mont_vec(W (&x)[NPT], const W (&y)[NPT], W n, W ninv)
 {
 #pragma unroll
-    for (int u = 0; u < NPT; ++u) x[u] = msg[u];
-    for (int b = ebits - 2; b >= 0; --b) {
-#pragma unroll
-        for (int u = 0; u < NPT; ++u) x[u] = mont32(x[u], x[u], n, ninv);
-        if ((e >> b) & 1u) {
-#pragma unroll
-            for (int u = 0; u < NPT; ++u) x[u] = mont32(x[u], msg[u], n, ninv);
-        }
-    }
-#pragma unroll
-    for (int u = 0; u < NPT; ++u) x[u] = mont32(x[u], K, n, ninv);
+    for (int u = 0; u < NPT; ++u) x[u] = mont(x[u], y[u], n, ninv);
 }
 
-template <int NPT>
-PH_HD void modexp64(uint64_t (&x)[NPT], const uint64_t (&msg)[NPT], uint64_t e, int ebits,
-                    uint64_t n, uint64_t ninv, uint64_t K)
+template <int NPT, typename W>
+PH_HD void mont_sqr_vec(W (&x)[NPT], W n, W ninv)
 {
 #pragma unroll
-    for (int u = 0; u < NPT; ++u) x[u] = msg[u];
-    for (int b = ebits - 2; b >= 0; --b) {
+    for (int u = 0; u < NPT; ++u) x[u] = mont(x[u], x[u], n, ninv);
+}
+
+// c_u = m_u^e mod n for NPT messages by the exponent's program (Eq. 9c with
+// fewer products than the binary method), closed by one product with the
+// exit constant K the host derived for that program.  All control flow
+// depends only on the program, so it is uniform across a warp that shares
+// the instance.
+template <int NPT, typename W>
+PH_HD void modexp_prog(W (&x)[NPT], const W (&m)[NPT], const ExpProg &pg, W n, W ninv, W K)
+{
+    W t3[NPT], t5[NPT], t7[NPT];
+    const int tbl = pg.tbl;
+    if (tbl >= 2) {
+        W m2[NPT];
 #pragma unroll
-        for (int u = 0; u < NPT; ++u) x[u] = mont64(x[u], x[u], n, ninv);
-        if ((e >> b) & 1ull) {
+        for (int u = 0; u < NPT; ++u) {
+            m2[u] = mont(m[u], m[u], n, ninv);
+            t3[u] = mont(m2[u], m[u], n, ninv);
+        }
+        if (tbl == 4) {
 #pragma unroll
-            for (int u = 0; u < NPT; ++u) x[u] = mont64(x[u], msg[u], n, ninv);
+            for (int u = 0; u < NPT; ++u) {
+                t5[u] = mont(t3[u], m2[u], n, ninv);
+                t7[u] = mont(t5[u], m2[u], n, ninv);
+            }
         }
     }
+    switch (pg.ent[0] >> 6) {
+    case 0:
 #pragma unroll
-    for (int u = 0; u < NPT; ++u) x[u] = mont64(x[u], K, n, ninv);
+        for (int u = 0; u < NPT; ++u) x[u] = m[u];
+        break;
+    case 1:
+#pragma unroll
+        for (int u = 0; u < NPT; ++u) x[u] = t3[u];
+        break;
+    case 2:
+#pragma unroll
+        for (int u = 0; u < NPT; ++u) x[u] = t5[u];
+        break;
+    default:
+#pragma unroll
+        for (int u = 0; u < NPT; ++u) x[u] = t7[u];
+        break;
+    }
+    const int nent = pg.nent;
+    for (int k = 1; k < nent; ++k) {
+        const int b = pg.ent[k];
+        int sq = b & 63;
+        for (; sq >= 2; sq -= 2) {
+            mont_sqr_vec<NPT>(x, n, ninv);
+            mont_sqr_vec<NPT>(x, n, ninv);
+        }
+        if (sq) mont_sqr_vec<NPT>(x, n, ninv);
+        switch (b >> 6) {
+        case 0: mont_vec<NPT>(x, m, n, ninv); break;
+        case 1: mont_vec<NPT>(x, t3, n, ninv); break;
+        case 2: mont_vec<NPT>(x, t5, n, ninv); break;
+        default: mont_vec<NPT>(x, t7, n, ninv); break;
+        }
+    }
+    for (int sq = pg.tail; sq > 0; --sq) mont_sqr_vec<NPT>(x, n, ninv);
+#pragma unroll
+    for (int u = 0; u < NPT; ++u) x[u] = mont(x[u], K, n, ninv);
+}
+
+PH_HD int clz64(uint64_t x)
+{
+#if defined(__CUDA_ARCH__)
+    return __clzll((long long)x);
+#else
+    return x ? __builtin_clzll(x) : 64;
+#endif
+}
+
+PH_HD double u64_to_double_rn(uint64_t x)
+{
+#if defined(__CUDA_ARCH__)
+    return __ull2double_rn(x);
+#else
+    return (double)x;
+#endif
+}
+
+// Round-to-nearest-even double of the 128-bit integer hi*2^64 + lo.  The top
+// 64 significant bits are converted with one RN conversion after the bits
+// shifted out are folded into bit 0 (a sticky bit: the conversion rounds at
+// bit 11, so only whether the discarded part is zero matters there); the
+// power-of-two scaling is exact.
+PH_HD double u128_to_double(uint64_t hi, uint64_t lo)
+{
+    if (hi == 0) return u64_to_double_rn(lo);
+    const int sh = 64 - clz64(hi);                       // 1 .. 64
+    const uint64_t top = sh == 64 ? hi : (hi << (64 - sh)) | (lo >> sh);
+    const uint64_t rest = sh == 64 ? lo : (lo << (64 - sh));
+    const double t = u64_to_double_rn(top | (rest != 0 ? 1u : 0u));
+    return t * bits_to_double((uint64_t)(1023 + sh) << 52);
+}
+
+// floor(256 R) for a double R in [0, 1] taken apart as integers: R =
+// sig 2^(ef-1075) with the implicit bit in sig, so 256 R = sig 2^(ef-1067).
+PH_HD uint32_t hist_bin256(double R)
+{
+    uint64_t b;
+#if defined(__CUDA_ARCH__)
+    b = (uint64_t)__double_as_longlong(R);
+#else
+    __builtin_memcpy(&b, &R, 8);
+#endif
+    const int ef = (int)(b >> 52);
+    if (ef == 0) return 0;
+    const uint64_t sig = (b & ((1ull << 52) - 1)) | (1ull << 52);
+    const int shift = 1067 - ef;
+    const uint32_t bin = shift >= 64 ? 0u : shift <= 0 ? 256u : (uint32_t)(sig >> shift);
+    return bin > 255u ? 255u : bin;
 }
 
 PH_HD double real64(uint64_t c, uint64_t n)

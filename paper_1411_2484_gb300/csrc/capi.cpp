@@ -30,6 +30,7 @@ struct phprng_ctx {
     std::vector<phprng_instance> host_inst;
     std::vector<uint8_t> wide;
     DevInst *d_inst = nullptr;
+    ExpProg *d_prog = nullptr;        // exponent programs, one per instance
     uint64_t *d_state = nullptr;      // 4 * count: m | s | c | pos
     DevState st{};
     SkipConst sk32{}, sk64{};
@@ -72,6 +73,7 @@ static void free_ctx(phprng_ctx *c)
     if (!c) return;
     cudaDeviceSynchronize();
     cudaFree(c->d_inst);
+    cudaFree(c->d_prog);
     cudaFree(c->d_state);
     cudaFree(c->d_L0);
     cudaFree(c->d_T);
@@ -151,6 +153,7 @@ PH_API int phprng_create(phprng_ctx **out, int width, const phprng_instance *ins
     phprng_ctx *c = new (std::nothrow) phprng_ctx;
     if (!c) return fail(nullptr, PHPRNG_ENOMEM, "phprng_create: host allocation failed");
     std::vector<DevInst> di;
+    std::vector<ExpProg> prog;
     std::vector<uint64_t> state;
     try {
         c->width = width;
@@ -162,6 +165,7 @@ PH_API int phprng_create(phprng_ctx **out, int width, const phprng_instance *ins
         c->pos_host.assign(count, 0);
         c->wide.resize(count);
         di.resize(count);
+        prog.resize(count);
         state.assign(4 * count, 0);
     } catch (const std::bad_alloc &) {
         delete c;
@@ -171,7 +175,7 @@ PH_API int phprng_create(phprng_ctx **out, int width, const phprng_instance *ins
         int w = width == 64 ? 1 : width == 32 ? 0 : (inst[i].n >= (1ull << 32) ? 1 : 0);
         c->wide[i] = (uint8_t)w;
         (w ? c->any64 : c->any32) = true;
-        di[i] = derive_inst(inst[i], w);
+        di[i] = derive_inst(inst[i], w, &prog[i]);
         state[i] = inst[i].m0;
         state[count + i] = inst[i].s0;
     }
@@ -180,7 +184,10 @@ PH_API int phprng_create(phprng_ctx **out, int width, const phprng_instance *ins
     cudaStream_t s = (cudaStream_t)cuda_stream;
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_inst, count * sizeof(DevInst));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_prog, count * sizeof(ExpProg));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_state, 4 * count * sizeof(uint64_t));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->d_prog, prog.data(), count * sizeof(ExpProg), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->d_inst, di.data(), count * sizeof(DevInst), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
@@ -240,6 +247,7 @@ static int launch_range(phprng_ctx *c, uint64_t first, uint64_t num, uint64_t pe
 {
     GenArgs g;
     g.inst = c->d_inst;
+    g.prog = c->d_prog;
     g.st = c->st;
     g.first = first;
     g.num = num;
@@ -247,16 +255,26 @@ static int launch_range(phprng_ctx *c, uint64_t first, uint64_t num, uint64_t pe
     g.c_out = c_out;
     g.r_out = r_out;
     g.stats = stats;
+    g.edge = nullptr;
     g.c_is_64 = c->width != 32;
     const size_t csz = g.c_is_64 ? 8 : 4;
     g.vec_ok = (per_inst % 4 == 0) && ((uintptr_t)c_out % 16 == 0) &&
                ((uintptr_t)r_out % 16 == 0) && (csz * per_inst) % 16 == 0;
     std::string err;
     int rc = PHPRNG_OK;
+    const uint64_t edge_words = stats ? gen32_edge_words(num, per_inst) : 0;
+    if (edge_words) {
+        cudaError_t e = cudaMallocAsync((void **)&g.edge, edge_words * 4, s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, PHPRNG_ENOMEM, "phprng_generate: statistics scratch allocation failed");
+        }
+    }
     if (c->any32) {
         g.sk = c->sk32;
         rc = launch_gen32(g, s, &err);
     }
+    if (g.edge) cudaFreeAsync(g.edge, s);
     if (rc == PHPRNG_OK && c->any64) {
         g.sk = c->sk64;
         rc = launch_gen64(g, s, &err);
@@ -350,9 +368,12 @@ PH_API int phprng_generate(phprng_ctx *ctx, uint64_t first, uint64_t num_inst,
         if (ctx->any64)
             return fail(ctx, PHPRNG_EINVAL,
                         "phprng_generate: fused statistics are defined for 32-bit moduli only");
-        return fail(ctx, PHPRNG_EINVAL, "phprng_generate: fused statistics are not available");
+        if (per_inst >= (1ull << 31))
+            return fail(ctx, PHPRNG_EINVAL, "phprng_generate: statistics need per_inst < 2^31");
+        if ((uintptr_t)stats_out % 8)
+            return fail(ctx, PHPRNG_EINVAL, "phprng_generate: stats_out not 8-byte aligned");
     }
-    if (!c_out && !r_out)
+    if (!c_out && !r_out && !stats_out)
         return fail(ctx, PHPRNG_EINVAL,
                     "phprng_generate: no output (use phprng_skip to advance without output)");
     cudaError_t e = cudaSetDevice(ctx->device);
@@ -366,8 +387,32 @@ PH_API int phprng_generate(phprng_ctx *ctx, uint64_t first, uint64_t num_inst,
     if (host && dev)
         return fail(ctx, PHPRNG_EINVAL, "phprng_generate: mix of host and device output pointers");
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    int rc = host ? generate_to_host(ctx, first, num_inst, per_inst, c_out, r_out, s)
+    int rc;
+    if (stats_out) {
+        if (host)
+            return fail(ctx, PHPRNG_EINVAL,
+                        "phprng_generate: with statistics, c_out/r_out must be device memory");
+        const int ks = pointer_kind(stats_out);
+        if (ks == -1)
+            return fail(ctx, PHPRNG_EINVAL, "phprng_generate: cannot classify stats_out");
+        if (ks == 1) {
+            rc = launch_range(ctx, first, num_inst, per_inst, c_out, r_out, stats_out, s);
+        } else {                                 // host statistics: stage, copy back, wait
+            phprng_stats *d = nullptr;
+            CU(ctx, cudaMallocAsync((void **)&d, num_inst * sizeof(phprng_stats), s));
+            rc = launch_range(ctx, first, num_inst, per_inst, c_out, r_out, d, s);
+            cudaError_t e = rc == PHPRNG_OK
+                ? cudaMemcpyAsync(stats_out, d, num_inst * sizeof(phprng_stats),
+                                  cudaMemcpyDeviceToHost, s)
+                : cudaSuccess;
+            cudaFreeAsync(d, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (rc == PHPRNG_OK && e != cudaSuccess) return cuda_fail(ctx, e, "phprng_generate: statistics copy");
+        }
+    } else {
+        rc = host ? generate_to_host(ctx, first, num_inst, per_inst, c_out, r_out, s)
                   : launch_range(ctx, first, num_inst, per_inst, c_out, r_out, nullptr, s);
+    }
     if (rc == PHPRNG_OK)
         for (uint64_t i = first; i < first + num_inst; ++i) ctx->pos_host[i] += per_inst;
     return rc;
@@ -468,7 +513,7 @@ PH_API int phprng_skip(phprng_ctx *ctx, const uint64_t *inst_ids, const uint64_t
                                     cudaMemcpyHostToDevice, s);
     std::string err;
     if (e == cudaSuccess)
-        rc = launch_skip(ctx->d_inst, ctx->st, ctx->d_L0, ctx->tbl, d_reqs, reqs.size(), s, &err);
+        rc = launch_skip(ctx->d_inst, ctx->d_prog, ctx->st, ctx->d_L0, ctx->tbl, d_reqs, reqs.size(), s, &err);
     cudaError_t e2 = cudaFreeAsync(d_reqs, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "phprng_skip: request upload");
     if (rc != PHPRNG_OK) return fail(ctx, rc, "phprng_skip: " + err);

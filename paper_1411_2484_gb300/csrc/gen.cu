@@ -14,9 +14,10 @@
 //   messages  m at lane j's u-th number = m_t + (sum of the skips before it),
 //           Eq. 6b, formed as an exclusive warp scan mod n of the lanes'
 //           skip sums plus the lane's own running sum (Eq. 9b);
-//   encrypt c = m^e mod n (Eq. 9c) by left-to-right square-and-multiply on
-//           Montgomery products started from the plain message, closed by
-//           one product with the per-instance constant K;
+//   encrypt c = m^e mod n (Eq. 9c) by the instance's sliding-window program
+//           (squarings and products with odd powers of m) on Montgomery
+//           products started from the plain message, closed by one product
+//           with the per-instance constant K;
 //   float   R = (c+1)/(n+1) (Eq. 9d): integer-built correctly rounded double
 //           for n < 2^32, hardware FP64 division of the rounded operands for
 //           64-bit n;
@@ -29,28 +30,63 @@
 
 namespace phprng {
 
-static constexpr int kNPT = 4;          // numbers per lane per group (32-bit path)
-static constexpr int kNPT64 = 2;        // numbers per lane per group (64-bit path)
+#ifndef PH_NPT32
+#define PH_NPT32 4
+#endif
+#ifndef PH_NPT64
+#define PH_NPT64 2
+#endif
+#ifndef PH_MINB32
+#define PH_MINB32 1
+#endif
+static constexpr int kNPT = PH_NPT32;     // numbers per lane per group (32-bit path)
+static constexpr int kNPT64 = PH_NPT64;   // numbers per lane per group (64-bit path)
 static constexpr int kWarpsPerBlock = 8;
 static constexpr unsigned kFull = 0xffffffffu;
 
 int gen_npt(int wide) { return wide ? kNPT64 : kNPT; }
 
-template <int NPT, typename CT>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
-gen32_kernel(const DevInst *__restrict__ inst, DevState st, SkipConst sk, uint64_t first,
-             uint64_t num, uint64_t per_inst, CT *__restrict__ c_out,
-             double *__restrict__ r_out, int vec_ok)
+typedef unsigned __int128 u128;
+
+__device__ __forceinline__ u128 warp_sum_u128(u128 v)
 {
-    const int lane = threadIdx.x & 31;
-    const uint64_t w = (uint64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-    if (w >= num) return;
-    const uint64_t i = first + w;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const uint64_t lo = __shfl_xor_sync(kFull, (uint64_t)v, off);
+        const uint64_t hi = __shfl_xor_sync(kFull, (uint64_t)(v >> 64), off);
+        v += ((u128)hi << 64) | lo;
+    }
+    return v;
+}
+
+__device__ __forceinline__ double u128d(u128 v) { return u128_to_double((uint64_t)(v >> 64), (uint64_t)v); }
+
+// STATS = false: the plain generator.  STATS = true: the fused consumer mode
+// -- the same numbers, plus per-stream exact sums X = sum(c+1),
+// Y = sum(c+1)^2, Z = sum(c+1)(c'+1) with the next instance of the call, and
+// a 256-bin histogram of floor(256 R), reduced on chip.  In that mode the
+// block's warps walk their groups in lockstep: each group's ciphertexts go to
+// a double-buffered shared array so a warp can pair them with the next warp's;
+// the first and last warp of a block also leave their ciphertexts in `edge`
+// so stats_edge_kernel can pair instances that straddle two blocks.
+template <int NPT, typename CT, bool STATS>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, STATS ? 1 : PH_MINB32)
+gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, DevState st,
+             SkipConst sk, uint64_t first,
+             uint64_t num, uint64_t per_inst, CT *__restrict__ c_out,
+             double *__restrict__ r_out, int vec_ok, phprng_stats *__restrict__ stats,
+             uint32_t *__restrict__ edge)
+{
+    extern __shared__ uint32_t smem[];   // STATS: cbuf[2][W][32*NPT] then hist[W][256]
+    constexpr int W = kWarpsPerBlock;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t w = (uint64_t)blockIdx.x * W + warp;
+    const bool active = w < num;
+    if (!STATS && !active) return;
+    const uint64_t i = first + (active ? w : 0);
     const DevInst P = inst[i];
-    if (P.wide) return;
+    if (!STATS && P.wide) return;
     const uint32_t n = (uint32_t)P.n, ninv = (uint32_t)P.ninv, K = (uint32_t)P.K;
-    const uint32_t e = (uint32_t)P.e;
-    const int ebits = (int)P.ebits;
     const uint32_t p = sk.p, pinv = sk.pinv, aM = sk.aM;
 
     uint32_t M = (uint32_t)st.m[i];
@@ -58,86 +94,178 @@ gen32_kernel(const DevInst *__restrict__ inst, DevState st, SkipConst sk, uint64
     const uint64_t base = w * per_inst;
     constexpr uint64_t G = 32 * NPT;
 
+    uint32_t *hist = smem + 2 * W * (32 * NPT) + warp * 256;
+    u128 X = 0, Y = 0, Z = 0;
+    const bool has_next = w + 1 < num;
+    const bool pair_in_block = has_next && warp + 1 < W;
+    if (STATS) {
+        for (int b = lane; b < 256; b += 32) hist[b] = 0;
+        __syncwarp();
+    }
+
     for (uint64_t g0 = 0; g0 < per_inst; g0 += G) {
         uint32_t sv[NPT], msg[NPT], x[NPT];
+        double rv[NPT];
         const uint64_t my0 = g0 + (uint64_t)NPT * lane;
-        uint32_t S = 0, t = sig;
+        if (active) {
+            uint32_t S = 0, t = sig;
 #pragma unroll
-        for (int u = 0; u < NPT; ++u) {
-            t = mont32(t, aM, p, pinv);                          // Eq. 9a
-            sv[u] = t;
-            if (my0 + u < per_inst) S = addmod32(S, t, n);
-        }
-        uint32_t incl = S;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            uint32_t y = __shfl_up_sync(kFull, incl, off);
-            if (lane >= off) incl = addmod32(incl, y, n);
-        }
-        const uint32_t total = __shfl_sync(kFull, incl, 31);
-        uint32_t mm = addmod32(M, submod32(incl, S, n), n);
-#pragma unroll
-        for (int u = 0; u < NPT; ++u) {
-            mm = addmod32(mm, sv[u], n);                          // Eq. 9b
-            msg[u] = mm;
-        }
-        modexp32<NPT>(x, msg, e, ebits, n, ninv, K);             // Eq. 9c
-
-        const bool full = my0 + NPT <= per_inst;
-        if (c_out) {
-            CT *dst = c_out + base + my0;
-            if (full && vec_ok && sizeof(CT) == 4 && NPT % 4 == 0) {
-#pragma unroll
-                for (int u = 0; u < NPT; u += 4)
-                    *reinterpret_cast<uint4 *>(dst + u) = make_uint4(x[u], x[u + 1], x[u + 2], x[u + 3]);
-            } else if (full && vec_ok && sizeof(CT) == 8 && NPT % 2 == 0) {
-#pragma unroll
-                for (int u = 0; u < NPT; u += 2)
-                    *reinterpret_cast<ulonglong2 *>(dst + u) = make_ulonglong2(x[u], x[u + 1]);
-            } else {
-#pragma unroll
-                for (int u = 0; u < NPT; ++u)
-                    if (my0 + u < per_inst) dst[u] = (CT)x[u];
+            for (int u = 0; u < NPT; ++u) {
+                t = mont32(t, aM, p, pinv);                      // Eq. 9a
+                sv[u] = t;
+                if (my0 + u < per_inst) S = addmod32(S, t, n);
             }
-        }
-        if (r_out) {
-            double *dst = r_out + base + my0;
-            double rv[NPT];
+            uint32_t incl = S;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                uint32_t y = __shfl_up_sync(kFull, incl, off);
+                if (lane >= off) incl = addmod32(incl, y, n);
+            }
+            const uint32_t total = __shfl_sync(kFull, incl, 31);
+            uint32_t mm = addmod32(M, submod32(incl, S, n), n);
+#pragma unroll
+            for (int u = 0; u < NPT; ++u) {
+                mm = addmod32(mm, sv[u], n);                      // Eq. 9b
+                msg[u] = mm;
+            }
+            modexp_prog<NPT, uint32_t>(x, msg, prog[i], n, ninv, K);   // Eq. 9c
 #pragma unroll
             for (int u = 0; u < NPT; ++u) rv[u] = real32(x[u], P.yN, P.ybits, P.V);   // Eq. 9d
-            if (full && vec_ok && NPT % 2 == 0) {
+
+            const bool full = my0 + NPT <= per_inst;
+            if (c_out) {
+                CT *dst = c_out + base + my0;
+                if (full && vec_ok && sizeof(CT) == 4 && NPT % 4 == 0) {
 #pragma unroll
-                for (int u = 0; u < NPT; u += 2)
-                    *reinterpret_cast<double2 *>(dst + u) = make_double2(rv[u], rv[u + 1]);
-            } else {
+                    for (int u = 0; u < NPT; u += 4)
+                        *reinterpret_cast<uint4 *>(dst + u) = make_uint4(x[u], x[u + 1], x[u + 2], x[u + 3]);
+                } else if (full && vec_ok && sizeof(CT) == 8 && NPT % 2 == 0) {
 #pragma unroll
-                for (int u = 0; u < NPT; ++u)
-                    if (my0 + u < per_inst) dst[u] = rv[u];
+                    for (int u = 0; u < NPT; u += 2)
+                        *reinterpret_cast<ulonglong2 *>(dst + u) = make_ulonglong2(x[u], x[u + 1]);
+                } else {
+#pragma unroll
+                    for (int u = 0; u < NPT; ++u)
+                        if (my0 + u < per_inst) dst[u] = (CT)x[u];
+                }
             }
+            if (r_out) {
+                double *dst = r_out + base + my0;
+                if (full && vec_ok && NPT % 2 == 0) {
+#pragma unroll
+                    for (int u = 0; u < NPT; u += 2)
+                        *reinterpret_cast<double2 *>(dst + u) = make_double2(rv[u], rv[u + 1]);
+                } else {
+#pragma unroll
+                    for (int u = 0; u < NPT; ++u)
+                        if (my0 + u < per_inst) dst[u] = rv[u];
+                }
+            }
+            if (g0 + G >= per_inst) {                            // state write-back
+                const uint64_t last = per_inst - 1 - g0;
+                if ((uint64_t)lane == last / NPT) {
+                    const int ul = (int)(last % NPT);
+#pragma unroll
+                    for (int u = 0; u < NPT; ++u) {
+                        if (u == ul) {
+                            st.m[i] = msg[u];
+                            st.s[i] = sv[u];
+                            st.c[i] = x[u];
+                        }
+                    }
+                    st.pos[i] += per_inst;
+                }
+            }
+            M = addmod32(M, total, n);
+            sig = mont32(sig, sk.aGM, p, pinv);
         }
-        if (g0 + G >= per_inst) {                                // state write-back
-            const uint64_t last = per_inst - 1 - g0;
-            if ((uint64_t)lane == last / NPT) {
-                const int ul = (int)(last % NPT);
+        if (STATS) {
+            uint32_t *cb = smem + ((int)((g0 / G) & 1) * W + warp) * (32 * NPT);
+            if (active) {
 #pragma unroll
                 for (int u = 0; u < NPT; ++u) {
-                    if (u == ul) {
-                        st.m[i] = msg[u];
-                        st.s[i] = sv[u];
-                        st.c[i] = x[u];
+                    cb[NPT * lane + u] = x[u];
+                    if (my0 + u < per_inst) {
+                        const uint64_t v = (uint64_t)x[u] + 1;
+                        X += v;
+                        Y += (u128)(v * v);
+                        atomicAdd(&hist[hist_bin256(rv[u])], 1u);
                     }
                 }
-                st.pos[i] += per_inst;
+                if (edge && ((warp == W - 1 && has_next) || (warp == 0 && blockIdx.x > 0))) {
+                    uint32_t *row = edge + (2 * (uint64_t)blockIdx.x + (warp == 0 ? 0 : 1)) * per_inst;
+#pragma unroll
+                    for (int u = 0; u < NPT; ++u)
+                        if (my0 + u < per_inst) row[my0 + u] = x[u];
+                }
+            }
+            __syncthreads();
+            if (active && pair_in_block) {
+                const uint32_t *cn = cb + 32 * NPT;              // next warp, same buffer
+#pragma unroll
+                for (int u = 0; u < NPT; ++u)
+                    if (my0 + u < per_inst)
+                        Z += (u128)(((uint64_t)x[u] + 1) * ((uint64_t)cn[NPT * lane + u] + 1));
             }
         }
-        M = addmod32(M, total, n);
-        sig = mont32(sig, sk.aGM, p, pinv);
+    }
+    if (STATS && active) {
+        X = warp_sum_u128(X);
+        Y = warp_sum_u128(Y);
+        Z = warp_sum_u128(Z);
+        __syncwarp();
+        phprng_stats *o = stats + w;
+        for (int b = lane; b < 256; b += 32) o->hist[b] = hist[b];
+        if (lane == 0) {
+            const u128 N = per_inst, n1 = (u128)n + 1;
+            o->x_lo = (uint64_t)X; o->x_hi = (uint64_t)(X >> 64);
+            o->y_lo = (uint64_t)Y; o->y_hi = (uint64_t)(Y >> 64);
+            o->z_lo = (uint64_t)Z; o->z_hi = (uint64_t)(Z >> 64);
+            o->count = per_inst;
+            o->mean = __ddiv_rn(u128d(X), u128d(N * n1));
+            o->var = per_inst >= 2 ? __ddiv_rn(u128d(N * Y - X * X), u128d(N * (N - 1) * n1 * n1)) : 0.0;
+            if (pair_in_block) {
+                const u128 nn1 = (u128)inst[i + 1].n + 1;
+                o->corr = __ddiv_rn(u128d(Z), u128d(N * n1 * nn1));
+            } else {
+                o->corr = 0.0;                                   // last of the call, or set by the edge kernel
+            }
+        }
+    }
+}
+
+// Pairs the last instance of block b with the first of block b+1 (one warp
+// per pair): Z and corr of that instance from the rows gen32_kernel left in
+// `edge`.
+__global__ void __launch_bounds__(256)
+stats_edge_kernel(const DevInst *__restrict__ inst, const uint32_t *__restrict__ edge,
+                  uint64_t first, uint64_t num, uint64_t per_inst, uint64_t nblocks,
+                  phprng_stats *__restrict__ stats)
+{
+    const uint64_t b = (uint64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (b + 1 >= nblocks) return;
+    const uint32_t *L = edge + (2 * b + 1) * per_inst;
+    const uint32_t *F = edge + (2 * (b + 1)) * per_inst;
+    u128 Z = 0;
+    for (uint64_t k = lane; k < per_inst; k += 32)
+        Z += (u128)(((uint64_t)L[k] + 1) * ((uint64_t)F[k] + 1));
+    Z = warp_sum_u128(Z);
+    if (lane == 0) {
+        const uint64_t w = b * kWarpsPerBlock + kWarpsPerBlock - 1;     // < num - 1
+        phprng_stats *o = stats + w;
+        const u128 N = per_inst;
+        const u128 n1 = (u128)inst[first + w].n + 1, nn1 = (u128)inst[first + w + 1].n + 1;
+        o->z_lo = (uint64_t)Z;
+        o->z_hi = (uint64_t)(Z >> 64);
+        o->corr = __ddiv_rn(u128d(Z), u128d(N * n1 * nn1));
     }
 }
 
 template <int NPT>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
-gen64_kernel(const DevInst *__restrict__ inst, DevState st, SkipConst sk, uint64_t first,
+gen64_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, DevState st,
+             SkipConst sk, uint64_t first,
              uint64_t num, uint64_t per_inst, uint64_t *__restrict__ c_out,
              double *__restrict__ r_out, int vec_ok)
 {
@@ -147,8 +275,7 @@ gen64_kernel(const DevInst *__restrict__ inst, DevState st, SkipConst sk, uint64
     const uint64_t i = first + w;
     const DevInst P = inst[i];
     if (!P.wide) return;
-    const uint64_t n = P.n, ninv = P.ninv, K = P.K, e = P.e;
-    const int ebits = (int)P.ebits;
+    const uint64_t n = P.n, ninv = P.ninv, K = P.K;
     const uint32_t p = sk.p, pinv = sk.pinv, aM = sk.aM;
 
     uint64_t M = st.m[i];
@@ -181,7 +308,7 @@ gen64_kernel(const DevInst *__restrict__ inst, DevState st, SkipConst sk, uint64
             mm = addmod64(mm, sv[u], n);                          // Eq. 9b
             msg[u] = mm;
         }
-        modexp64<NPT>(x, msg, e, ebits, n, ninv, K);             // Eq. 9c
+        modexp_prog<NPT, uint64_t>(x, msg, prog[i], n, ninv, K);     // Eq. 9c
 
         const bool full = my0 + NPT <= per_inst;
         if (c_out) {
@@ -246,13 +373,37 @@ int launch_gen32(const GenArgs &a, void *stream, std::string *err)
     if (a.num == 0 || a.per_inst == 0) return PHPRNG_OK;
     const uint64_t blocks = (a.num + kWarpsPerBlock - 1) / kWarpsPerBlock;
     cudaStream_t s = (cudaStream_t)stream;
+    if (a.stats) {
+        const size_t smem = (2 * kWarpsPerBlock * 32 * kNPT + kWarpsPerBlock * 256) * sizeof(uint32_t);
+        if (a.c_is_64)
+            gen32_kernel<kNPT, uint64_t, true><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(
+                a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, (uint64_t *)a.c_out, a.r_out,
+                a.vec_ok, a.stats, a.edge);
+        else
+            gen32_kernel<kNPT, uint32_t, true><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(
+                a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, (uint32_t *)a.c_out, a.r_out,
+                a.vec_ok, a.stats, a.edge);
+        int rc = check_launch(err, "gen32_kernel (statistics) launch");
+        if (rc != PHPRNG_OK || blocks < 2) return rc;
+        stats_edge_kernel<<<(unsigned)((blocks - 1 + 7) / 8), 256, 0, s>>>(
+            a.inst, a.edge, a.first, a.num, a.per_inst, blocks, a.stats);
+        return check_launch(err, "stats_edge_kernel launch");
+    }
     if (a.c_is_64)
-        gen32_kernel<kNPT, uint64_t><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(
-            a.inst, a.st, a.sk, a.first, a.num, a.per_inst, (uint64_t *)a.c_out, a.r_out, a.vec_ok);
+        gen32_kernel<kNPT, uint64_t, false><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(
+            a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, (uint64_t *)a.c_out, a.r_out, a.vec_ok,
+            nullptr, nullptr);
     else
-        gen32_kernel<kNPT, uint32_t><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(
-            a.inst, a.st, a.sk, a.first, a.num, a.per_inst, (uint32_t *)a.c_out, a.r_out, a.vec_ok);
+        gen32_kernel<kNPT, uint32_t, false><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(
+            a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, (uint32_t *)a.c_out, a.r_out, a.vec_ok,
+            nullptr, nullptr);
     return check_launch(err, "gen32_kernel launch");
+}
+
+uint64_t gen32_edge_words(uint64_t num, uint64_t per_inst)
+{
+    const uint64_t blocks = (num + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    return blocks < 2 ? 0 : 2 * blocks * per_inst;
 }
 
 int launch_gen64(const GenArgs &a, void *stream, std::string *err)
@@ -260,7 +411,7 @@ int launch_gen64(const GenArgs &a, void *stream, std::string *err)
     if (a.num == 0 || a.per_inst == 0) return PHPRNG_OK;
     const uint64_t blocks = (a.num + kWarpsPerBlock - 1) / kWarpsPerBlock;
     gen64_kernel<kNPT64><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, (cudaStream_t)stream>>>(
-        a.inst, a.st, a.sk, a.first, a.num, a.per_inst, (uint64_t *)a.c_out, a.r_out, a.vec_ok);
+        a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, (uint64_t *)a.c_out, a.r_out, a.vec_ok);
     return check_launch(err, "gen64_kernel launch");
 }
 

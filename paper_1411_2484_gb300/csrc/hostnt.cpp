@@ -13,6 +13,7 @@
 #include <unordered_map>
 #include <unordered_set>
 
+#include "arith.cuh"
 #include "internal.h"
 
 namespace phprng {
@@ -221,28 +222,83 @@ bool discrete_logs(uint64_t p, uint64_t a, const uint64_t *s, uint64_t count, ui
     return true;
 }
 
-// Left-to-right square-and-multiply started from the plain message m with
-// Montgomery products MP(x, y) = x y R^-1 (R = 2^rbits) leaves
-// x = m^e R^alpha, where alpha follows alpha -> 2 alpha - 1 per squaring and
-// alpha -> alpha - 1 per multiplication.  One more product with
-// K = R^(1-alpha) mod n returns m^e (R has order dividing n-1 mod prime n,
-// so alpha is tracked mod n-1).
-uint64_t mont_exit_constant(uint64_t n, uint64_t e, int rbits)
+// Sliding-window program of exponent e with windows of at most w bits:
+// scanning e from its top bit, a zero bit is one more squaring; a one bit
+// opens the longest window of <= w bits that ends in a one, and costs that
+// many squarings (none for the first window, which initialises x) plus one
+// product with the odd power m^v, v the window's value.  Returns the number of
+// Montgomery products, table included, or -1 if the program does not fit.
+static int build_program(uint64_t e, int w, ExpProg *pg)
 {
-    uint64_t ord = n - 1;
-    uint64_t alpha = 0;
-    int L = bitlen(e);
-    for (int i = L - 2; i >= 0; --i) {
-        alpha = (uint64_t)(((u128)alpha * 2 + ord - 1) % ord);
-        if ((e >> i) & 1) alpha = (uint64_t)(((u128)alpha + ord - 1) % ord);
+    memset(pg, 0, sizeof *pg);
+    const int L = bitlen(e);
+    int i = L - 1, pending = 0, nent = 0, maxidx = 0, products = 0;
+    while (i >= 0) {
+        if (((e >> i) & 1) == 0) {
+            ++pending;
+            --i;
+            continue;
+        }
+        int l = i - w + 1 < 0 ? 0 : i - w + 1;
+        while (((e >> l) & 1) == 0) ++l;
+        const int len = i - l + 1;
+        const uint64_t val = (e >> l) & ((1ull << len) - 1);
+        const int idx = (int)((val - 1) / 2);
+        const int sq = nent == 0 ? 0 : pending + len;
+        if (nent >= (int)sizeof pg->ent || sq > 63) return -1;
+        pg->ent[nent++] = (uint8_t)(sq | (idx << 6));
+        products += sq + (nent > 1 ? 1 : 0);
+        if (idx > maxidx) maxidx = idx;
+        pending = 0;
+        i = l - 1;
     }
-    uint64_t rmodn = rbits == 32 ? (uint64_t)((1ull << 32) % n)
-                                 : (uint64_t)((((u128)1) << 64) % n);
-    uint64_t ex = (uint64_t)(((u128)ord + 1 - alpha) % ord);
+    pg->nent = (uint8_t)nent;
+    pg->tail = (uint8_t)pending;
+    pg->tbl = (uint8_t)(maxidx == 0 ? 1 : maxidx == 1 ? 2 : 4);
+    products += pending + (pg->tbl == 1 ? 0 : pg->tbl == 2 ? 2 : 4);
+    return products;
+}
+
+// The cheapest program over window sizes 1..3.
+static ExpProg best_program(uint64_t e)
+{
+    ExpProg best, cand;
+    int best_cost = -1;
+    for (int w = 1; w <= 3; ++w) {
+        int c = build_program(e, w, &cand);
+        if (c >= 0 && (best_cost < 0 || c < best_cost)) {
+            best = cand;
+            best_cost = c;
+        }
+    }
+    return best;
+}
+
+// Every Montgomery product MP(x, y) = x y R^-1 (R = 2^rbits) multiplies the
+// R-powers its operands carry and adds one R^-1.  Started from the plain
+// message (power 0), the table holds m2 (power -1), m^3 = MP(m2, m) (-2),
+// m^5 = MP(m^3, m2) (-4), m^7 = MP(m^5, m2) (-6); the program leaves
+// x = m^e R^alpha, and one more product with K = R^(1-alpha) mod n returns
+// m^e.  R has order dividing n-1 mod the prime n, so alpha is tracked mod n-1.
+uint64_t mont_exit_constant(uint64_t n, const ExpProg &pg, int rbits)
+{
+    const uint64_t ord = n - 1;
+    auto sub = [&](uint64_t a, uint64_t k) { return (uint64_t)(((u128)a + ord - k % ord) % ord); };
+    const uint64_t tpow[4] = {0, sub(0, 2), sub(0, 4), sub(0, 6)};
+    uint64_t alpha = tpow[pg.ent[0] >> 6];
+    auto square = [&](uint64_t a) { return (uint64_t)(((u128)a * 2 + ord - 1) % ord); };
+    for (int k = 1; k < pg.nent; ++k) {
+        for (int q = 0; q < (pg.ent[k] & 63); ++q) alpha = square(alpha);
+        alpha = sub((uint64_t)(((u128)alpha + tpow[pg.ent[k] >> 6]) % ord), 1);
+    }
+    for (int q = 0; q < pg.tail; ++q) alpha = square(alpha);
+    const uint64_t rmodn = rbits == 32 ? (uint64_t)((1ull << 32) % n)
+                                       : (uint64_t)((((u128)1) << 64) % n);
+    const uint64_t ex = (uint64_t)(((u128)ord + 1 - alpha) % ord);
     return powmod(rmodn, ex, n);
 }
 
-DevInst derive_inst(const phprng_instance &in, int wide)
+DevInst derive_inst(const phprng_instance &in, int wide, ExpProg *prog)
 {
     DevInst d;
     memset(&d, 0, sizeof d);
@@ -250,16 +306,17 @@ DevInst derive_inst(const phprng_instance &in, int wide)
     d.e = in.e;
     d.ebits = (uint32_t)bitlen(in.e);
     d.wide = wide ? 1u : 0u;
+    *prog = best_program(in.e);
     if (!wide) {
         d.ninv = (uint32_t)inv_mod_2_64(in.n);
-        d.K = mont_exit_constant(in.n, in.e, 32);
+        d.K = mont_exit_constant(in.n, *prog, 32);
         uint64_t y = in.n + 1;
         d.ybits = (uint32_t)bitlen(y);
         d.yN = (uint32_t)(y << (32 - d.ybits));
         d.V = (uint64_t)((((u128)1) << 84) / d.yN);
     } else {
         d.ninv = inv_mod_2_64(in.n);
-        d.K = mont_exit_constant(in.n, in.e, 64);
+        d.K = mont_exit_constant(in.n, *prog, 64);
         uint64_t r = (uint64_t)((((u128)1) << 64) % in.n);
         d.r2 = mulmod(r, r, in.n);
     }

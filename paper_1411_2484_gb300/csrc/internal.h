@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "../../include/phprng.h"
+#include "arith.cuh"
 
 namespace phprng {
 
@@ -16,7 +17,7 @@ struct alignas(16) DevInst {
     uint64_t n;      // prime modulus (Eq. 1)
     uint64_t ninv;   // n^-1 mod 2^32 (32-bit path) or mod 2^64 (64-bit path)
     uint64_t K;      // Montgomery exit constant R^(1-alpha) mod n, see mont_exit_constant()
-    uint64_t e;      // exponent
+    uint64_t e;      // exponent (its sliding-window program is a separate ExpProg)
     uint64_t V;      // floor(2^84 / yN): reciprocal for the integer-built R (32-bit path)
     uint32_t yN;     // (n+1) << (32 - bitlen(n+1)), normalised divisor (32-bit path)
     uint32_t ybits;  // bitlen(n+1)
@@ -46,12 +47,14 @@ struct DevState {
 // Arguments of one generate launch over instances [first, first+num).
 struct GenArgs {
     const DevInst *inst;
+    const ExpProg *prog;    // per-instance exponent programs
     DevState st;
     SkipConst sk;
     uint64_t first, num, per_inst;
     void *c_out;            // uint32_t* (c_is_64 = 0) or uint64_t* (c_is_64 = 1), nullable
     double *r_out;          // nullable
     phprng_stats *stats;    // nullable
+    uint32_t *edge;         // statistics scratch: gen32_edge_words(num, per_inst) words
     int c_is_64;
     int vec_ok;             // outputs allow 16-byte vector stores
 };
@@ -82,14 +85,15 @@ struct SkipReq {
 // ---- kernel launchers (gen.cu) -------------------------------------------
 int gen_npt(int wide);   // numbers per lane per warp group of the 32/64-bit launch
 int launch_gen32(const GenArgs &a, void *stream, std::string *err);
+uint64_t gen32_edge_words(uint64_t num, uint64_t per_inst);
 int launch_gen64(const GenArgs &a, void *stream, std::string *err);
 
 // ---- skip-ahead (skip.cu) ------------------------------------------------
 SkipTable derive_skip_table(uint64_t p, uint64_t a);   // constants; T, P set by the caller
 int launch_build_skip_table(uint64_t p, uint64_t a, uint64_t *T, uint32_t *P, uint64_t *seg,
                             void *stream, std::string *err);
-int launch_skip(const DevInst *inst, DevState st, const uint64_t *L0, SkipTable tbl,
-                const SkipReq *reqs, uint64_t cnt, void *stream, std::string *err);
+int launch_skip(const DevInst *inst, const ExpProg *prog, DevState st, const uint64_t *L0,
+                SkipTable tbl, const SkipReq *reqs, uint64_t cnt, void *stream, std::string *err);
 
 // ---- measurement (microbench.cu) ------------------------------------------
 int run_microbench(int which, double *ops_per_s, void *stream, std::string *err);
@@ -105,8 +109,8 @@ std::vector<uint64_t> prime_factors(uint64_t x);
 bool is_primitive_root(uint64_t a, uint64_t p);
 bool discrete_log(uint64_t p, uint64_t a, uint64_t s, uint64_t *L);
 bool discrete_logs(uint64_t p, uint64_t a, const uint64_t *s, uint64_t count, uint64_t *L);
-uint64_t mont_exit_constant(uint64_t n, uint64_t e, int rbits);
-DevInst derive_inst(const phprng_instance &in, int wide);
+uint64_t mont_exit_constant(uint64_t n, const ExpProg &pg, int rbits);
+DevInst derive_inst(const phprng_instance &in, int wide, ExpProg *prog);
 SkipConst derive_skip(uint64_t p, uint64_t a, int npt);
 int validate_one(int width, const phprng_instance &in, uint32_t flags, std::string *msg);
 int validate_all(int width, const phprng_instance *inst, uint64_t count, uint32_t flags,

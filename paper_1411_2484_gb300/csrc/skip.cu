@@ -69,7 +69,8 @@ skip_table_scan(const uint64_t *seg, uint64_t nseg, uint64_t *T)
 }
 
 __global__ void __launch_bounds__(256)
-skip_kernel(const DevInst *__restrict__ inst, DevState st, const uint64_t *__restrict__ L0,
+skip_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, DevState st,
+            const uint64_t *__restrict__ L0,
             SkipTable tb, const SkipReq *__restrict__ reqs, uint64_t cnt)
 {
     const uint64_t w = (uint64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -89,12 +90,12 @@ skip_kernel(const DevInst *__restrict__ inst, DevState st, const uint64_t *__res
         uint64_t c;
         if (!P.wide) {
             uint32_t msg[1] = {(uint32_t)m}, x[1];
-            modexp32<1>(x, msg, (uint32_t)P.e, (int)P.ebits, (uint32_t)P.n, (uint32_t)P.ninv,
-                        (uint32_t)P.K);
+            modexp_prog<1, uint32_t>(x, msg, prog[i], (uint32_t)P.n, (uint32_t)P.ninv,
+                                     (uint32_t)P.K);
             c = x[0];
         } else {
             uint64_t msg[1] = {m}, x[1];
-            modexp64<1>(x, msg, P.e, (int)P.ebits, P.n, P.ninv, P.K);
+            modexp_prog<1, uint64_t>(x, msg, prog[i], P.n, P.ninv, P.K);
             c = x[0];
         }
         st.m[i] = m;
@@ -127,12 +128,12 @@ int launch_build_skip_table(uint64_t p, uint64_t a, uint64_t *T, uint32_t *P, ui
     return check(err, "skip_table_scan launch");
 }
 
-int launch_skip(const DevInst *inst, DevState st, const uint64_t *L0, SkipTable tbl,
-                const SkipReq *reqs, uint64_t cnt, void *stream, std::string *err)
+int launch_skip(const DevInst *inst, const ExpProg *prog, DevState st, const uint64_t *L0,
+                SkipTable tbl, const SkipReq *reqs, uint64_t cnt, void *stream, std::string *err)
 {
     if (cnt == 0) return PHPRNG_OK;
-    skip_kernel<<<(unsigned)((cnt + 7) / 8), 256, 0, (cudaStream_t)stream>>>(inst, st, L0, tbl,
-                                                                               reqs, cnt);
+    skip_kernel<<<(unsigned)((cnt + 7) / 8), 256, 0, (cudaStream_t)stream>>>(inst, prog, st, L0,
+                                                                               tbl, reqs, cnt);
     return check(err, "skip_kernel launch");
 }
 

@@ -2,7 +2,6 @@
 // layer (hostnt.cpp) for CPU tests: the same source the kernels compile,
 // instantiated with one number per lane.
 #include <cstdint>
-#include "../../paper_1411_2484_gb300/csrc/arith.cuh"
 #include "../../paper_1411_2484_gb300/csrc/internal.h"
 
 using namespace phprng;
@@ -13,7 +12,8 @@ void h_real32_many(const uint64_t *n, const uint64_t *c, double *out, uint64_t c
 {
     for (uint64_t i = 0; i < count; ++i) {
         phprng_instance in{n[i], 3, 3, 2, 0, 1};
-        DevInst d = derive_inst(in, 0);
+        ExpProg pg;
+        DevInst d = derive_inst(in, 0, &pg);
         out[i] = real32((uint32_t)c[i], d.yN, d.ybits, d.V);
     }
 }
@@ -23,15 +23,15 @@ void h_modexp_many(const uint64_t *m, const uint64_t *e, const uint64_t *n, uint
 {
     for (uint64_t i = 0; i < count; ++i) {
         phprng_instance in{n[i], e[i], 3, 2, 0, 1};
-        DevInst d = derive_inst(in, wide);
+        ExpProg pg;
+        DevInst d = derive_inst(in, wide, &pg);
         if (!wide) {
             uint32_t msg[1] = {(uint32_t)m[i]}, x[1];
-            modexp32<1>(x, msg, (uint32_t)d.e, (int)d.ebits, (uint32_t)d.n, (uint32_t)d.ninv,
-                        (uint32_t)d.K);
+            modexp_prog<1, uint32_t>(x, msg, pg, (uint32_t)d.n, (uint32_t)d.ninv, (uint32_t)d.K);
             out[i] = x[0];
         } else {
             uint64_t msg[1] = {m[i]}, x[1];
-            modexp64<1>(x, msg, d.e, (int)d.ebits, d.n, d.ninv, d.K);
+            modexp_prog<1, uint64_t>(x, msg, pg, d.n, d.ninv, d.K);
             out[i] = x[0];
         }
     }
@@ -59,5 +59,17 @@ int h_discrete_log(uint64_t p, uint64_t a, uint64_t s, uint64_t *L)
 uint64_t h_addmod(uint64_t a, uint64_t b, uint64_t n, int wide)
 {
     return wide ? addmod64(a, b, n) : addmod32((uint32_t)a, (uint32_t)b, (uint32_t)n);
+}
+}
+
+extern "C" {
+void h_u128_to_double_many(const uint64_t *hi, const uint64_t *lo, double *out, uint64_t count)
+{
+    for (uint64_t i = 0; i < count; ++i) out[i] = u128_to_double(hi[i], lo[i]);
+}
+
+void h_hist_bin_many(const double *r, uint32_t *out, uint64_t count)
+{
+    for (uint64_t i = 0; i < count; ++i) out[i] = hist_bin256(r[i]);
 }
 }

@@ -126,3 +126,40 @@ def test_discrete_log(h):
             s = rng.randrange(1, p)
             assert h.h_discrete_log(p, a, s, ctypes.byref(L)) == 1
             assert pow(a, L.value, p) == s and L.value < p - 1
+
+
+def test_u128_to_double_is_correctly_rounded(h):
+    h.h_u128_to_double_many.argtypes = [ctypes.POINTER(ctypes.c_uint64)] * 2 + [
+        ctypes.POINTER(ctypes.c_double), ctypes.c_uint64]
+    rng = random.Random(7)
+    vals = [0, 1, (1 << 64) - 1, 1 << 64, (1 << 128) - 1, (1 << 53) + 1, (1 << 117) + (1 << 64)]
+    for _ in range(20000):
+        bits = rng.randrange(1, 129)
+        v = rng.getrandbits(bits)
+        vals.append(v)
+        # halfway cases and their neighbours
+        if bits > 60:
+            k = bits - 54
+            base = (v >> k) << k
+            vals += [base + (1 << (k - 1)), base + (1 << (k - 1)) - 1, base + (1 << (k - 1)) + 1]
+    vals = [v for v in vals if v < (1 << 128)]
+    hi = np.array([v >> 64 for v in vals], dtype=np.uint64)
+    lo = np.array([v & ((1 << 64) - 1) for v in vals], dtype=np.uint64)
+    out = np.empty(len(vals), dtype=np.float64)
+    h.h_u128_to_double_many(_p(hi), _p(lo), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                            len(vals))
+    for v, o in zip(vals, out):
+        assert o == float(v), v          # Python int -> float rounds to nearest even
+
+
+def test_hist_bin_matches_floor(h):
+    h.h_hist_bin_many.argtypes = [ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.c_uint32), ctypes.c_uint64]
+    rng = np.random.default_rng(8)
+    r = np.concatenate([rng.random(100000), [0.0, 1.0, 0.5, 255 / 256, np.nextafter(1.0, 0.0),
+                                               1 / 256, np.nextafter(1 / 256, 0.0), 2.0 ** -60]])
+    out = np.empty(r.size, dtype=np.uint32)
+    h.h_hist_bin_many(r.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                      out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), r.size)
+    ref = np.minimum(np.floor(r * 256.0), 255).astype(np.uint32)
+    assert np.array_equal(out, ref)
