@@ -150,6 +150,68 @@ int phprng_generate(phprng_ctx *ctx, uint64_t first, uint64_t num_inst, uint64_t
 int phprng_skip(phprng_ctx *ctx, const uint64_t *inst_ids, const uint64_t *k, uint64_t cnt,
                 void *cuda_stream);
 
+/* ---------------------------------------------------------------- batches */
+
+/* One request of a batch: `len` consecutive numbers of instance `inst`,
+ * starting after stream position `offset` (the request's first output is
+ * number offset+1, reached by Eq. 7 without producing the numbers before it),
+ * or, with offset = PHPRNG_CONTINUE, right after the instance's previous
+ * request in the same batch (after its current position for the first one).
+ * Outputs go to c_base[c_off + j] and r_base[r_off + j], j < len. */
+#define PHPRNG_CONTINUE UINT64_MAX
+typedef struct {
+    uint64_t inst, offset, len, c_off, r_off;
+} phprng_request;
+
+typedef struct phprng_plan phprng_plan;   /* opaque, library-owned */
+
+/* Launch configuration of a plan: numbers per tile, numbers per lane per warp
+ * group of the 32-bit path (2 or 4), resident blocks per SM (0 = as many as
+ * fit), and the time the autotuner measured for it (ms, 0 if never timed). */
+typedef struct {
+    uint32_t tile;
+    int32_t npt;
+    int32_t blocks_per_sm;
+    float ms;
+} phprng_tuning;
+
+/* Resolves a batch of requests into tiles of at most `tile` numbers (0 = a
+ * default) and uploads them: the plan for one persistent launch that serves
+ * every request, whatever its instance width, length and start.  Start
+ * positions are fixed here (PHPRNG_CONTINUE is resolved against the context's
+ * positions now).  After every launch of the plan, each instance it touches
+ * is positioned at the end of its last request (in request order), with its
+ * state written back.  Builds the skip table on first use.  The plan keeps a
+ * pointer to ctx: destroy it before the context.  reqs is a host array. */
+int phprng_plan_create(phprng_ctx *ctx, const phprng_request *reqs, uint64_t nreq,
+                       uint32_t tile, phprng_plan **out, void *cuda_stream);
+
+/* One persistent launch of the plan on cuda_stream (a memset of the tile
+ * queue and one kernel; both may be captured in a CUDA graph).  c_base and
+ * r_base are device memory (either may be NULL); the caller sizes them for
+ * the largest c_off + len and r_off + len of the plan. */
+int phprng_plan_launch(phprng_plan *plan, void *c_base, double *r_base, void *cuda_stream);
+
+/* The same launch through a CUDA graph that the plan captures on first use
+ * for these output pointers and replays afterwards. */
+int phprng_plan_launch_graph(phprng_plan *plan, void *c_base, double *r_base, void *cuda_stream);
+
+/* Times plan launches over tile sizes, numbers per lane and blocks per SM
+ * (CUDA events on cuda_stream; the outputs are written each time with the
+ * same values), keeps the fastest configuration in the plan and returns it. */
+int phprng_plan_autotune(phprng_plan *plan, void *c_base, double *r_base,
+                         phprng_tuning *best, void *cuda_stream);
+
+/* Current configuration of the plan. */
+int phprng_plan_tuning(const phprng_plan *plan, phprng_tuning *out);
+
+/* Frees the plan (waits for the device).  NULL is accepted. */
+int phprng_plan_destroy(phprng_plan *plan);
+
+/* plan_create + plan_launch + plan_destroy for one batch. */
+int phprng_generate_batch(phprng_ctx *ctx, const phprng_request *reqs, uint64_t nreq,
+                          void *c_base, double *r_base, void *cuda_stream);
+
 /* Copies instance inst's parameters and current state to the host: the
  * returned phprng_instance holds {n, e, p, a, m, s} with m, s the current
  * message and skip; *pos_out (nullable) its stream position and *c_out

@@ -37,11 +37,26 @@ EXPORTED = [
     "phprng_create", "phprng_create_seeded", "phprng_destroy", "phprng_last_error",
     "phprng_status_string", "phprng_generate", "phprng_skip", "phprng_get_state",
     "phprng_is_prime", "phprng_validate", "phprng_draw_instances", "phprng_microbench",
+    "phprng_plan_create", "phprng_plan_launch", "phprng_plan_launch_graph",
+    "phprng_plan_autotune", "phprng_plan_tuning", "phprng_plan_destroy", "phprng_generate_batch",
 ]
+PHPRNG_CONTINUE = (1 << 64) - 1
 
 
 class phprng_instance(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint64) for k in ("n", "e", "p", "a", "m0", "s0")]
+
+
+class phprng_request(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in ("inst", "offset", "len", "c_off", "r_off")]
+
+
+class phprng_tuning(ctypes.Structure):
+    _fields_ = [("tile", ctypes.c_uint32), ("npt", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("ms", ctypes.c_float)]
+
+
+REQUEST_DTYPE = np.dtype([(k, "<u8") for k in ("inst", "offset", "len", "c_off", "r_off")])
 
 
 class phprng_stats(ctypes.Structure):
@@ -96,6 +111,14 @@ def _load():
         lib.phprng_validate.argtypes = [i32, P_inst, u64, u32, P64]
         lib.phprng_draw_instances.argtypes = [i32, u64, u64, u32, P_inst]
         lib.phprng_microbench.argtypes = [i32, ctypes.POINTER(ctypes.c_double), vp]
+        P_req = ctypes.POINTER(phprng_request)
+        lib.phprng_plan_create.argtypes = [vp, P_req, u64, u32, ctypes.POINTER(vp), vp]
+        lib.phprng_plan_launch.argtypes = [vp, vp, vp, vp]
+        lib.phprng_plan_launch_graph.argtypes = [vp, vp, vp, vp]
+        lib.phprng_plan_autotune.argtypes = [vp, vp, vp, ctypes.POINTER(phprng_tuning), vp]
+        lib.phprng_plan_tuning.argtypes = [vp, ctypes.POINTER(phprng_tuning)]
+        lib.phprng_plan_destroy.argtypes = [vp]
+        lib.phprng_generate_batch.argtypes = [vp, P_req, u64, vp, vp, vp]
         _lib = lib
         return lib
 
@@ -221,6 +244,62 @@ def phprng_draw_instances(width, count, seed, flags=0):
     _check(lib.phprng_draw_instances(int(width), int(count), int(seed), int(flags), arr))
     rows = np.frombuffer(arr, dtype=np.uint64).reshape(-1, 6).copy()
     return {k: rows[:, j] for j, k in enumerate(("n", "e", "p", "a", "m0", "s0"))}
+
+
+def _requests(reqs):
+    """Accepts a REQUEST_DTYPE array, an (n, 5) integer array or a sequence of
+    (inst, offset, len, c_off, r_off) tuples."""
+    a = np.asarray(reqs)
+    if a.dtype != REQUEST_DTYPE:
+        a = np.asarray(reqs, dtype=np.uint64).reshape(-1, 5)
+        a = np.ascontiguousarray(a).view(REQUEST_DTYPE).reshape(-1)
+    a = np.ascontiguousarray(a)
+    return a.ctypes.data_as(ctypes.POINTER(phprng_request)), a.size, a
+
+
+def _tuning_dict(t):
+    return dict(tile=t.tile, npt=t.npt, blocks_per_sm=t.blocks_per_sm, ms=t.ms)
+
+
+def phprng_plan_create(ctx, reqs, tile=0, stream=None):
+    ptr, n, _keep = _requests(reqs)
+    out = ctypes.c_void_p()
+    _check(_load().phprng_plan_create(ctx, ptr, n, int(tile), ctypes.byref(out),
+                                      _stream(stream)), ctx)
+    return out.value
+
+
+def phprng_plan_launch(plan, c_base=None, r_base=None, stream=None, ctx=None):
+    _check(_load().phprng_plan_launch(plan, _ptr(c_base), _ptr(r_base), _stream(stream)), ctx)
+
+
+def phprng_plan_launch_graph(plan, c_base=None, r_base=None, stream=None, ctx=None):
+    _check(_load().phprng_plan_launch_graph(plan, _ptr(c_base), _ptr(r_base), _stream(stream)),
+           ctx)
+
+
+def phprng_plan_autotune(plan, c_base=None, r_base=None, stream=None, ctx=None):
+    t = phprng_tuning()
+    _check(_load().phprng_plan_autotune(plan, _ptr(c_base), _ptr(r_base), ctypes.byref(t),
+                                        _stream(stream)), ctx)
+    return _tuning_dict(t)
+
+
+def phprng_plan_tuning(plan):
+    t = phprng_tuning()
+    _check(_load().phprng_plan_tuning(plan, ctypes.byref(t)))
+    return _tuning_dict(t)
+
+
+def phprng_plan_destroy(plan):
+    if plan:
+        _load().phprng_plan_destroy(plan)
+
+
+def phprng_generate_batch(ctx, reqs, c_base=None, r_base=None, stream=None):
+    ptr, n, _keep = _requests(reqs)
+    _check(_load().phprng_generate_batch(ctx, ptr, n, _ptr(c_base), _ptr(r_base),
+                                         _stream(stream)), ctx)
 
 
 def phprng_microbench(which, stream=None):

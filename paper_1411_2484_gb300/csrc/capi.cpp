@@ -33,10 +33,10 @@ struct phprng_ctx {
     ExpProg *d_prog = nullptr;        // exponent programs, one per instance
     uint64_t *d_state = nullptr;      // 4 * count: m | s | c | pos
     DevState st{};
-    SkipConst sk32{}, sk64{};
+    SkipConst sk32{}, sk64{}, sk32_4{}, sk32_2{};
     std::vector<uint64_t> pos_host;   // host mirror of the stream positions
     // skip-ahead: cycle positions of the seeds and the prefix table (lazy)
-    uint64_t *d_L0 = nullptr, *d_T = nullptr;
+    uint64_t *d_L0 = nullptr, *d_m0 = nullptr, *d_T = nullptr;
     uint32_t *d_P = nullptr;
     SkipTable tbl{};
     bool skip_ready = false;
@@ -76,6 +76,7 @@ static void free_ctx(phprng_ctx *c)
     cudaFree(c->d_prog);
     cudaFree(c->d_state);
     cudaFree(c->d_L0);
+    cudaFree(c->d_m0);
     cudaFree(c->d_T);
     cudaFree(c->d_P);
     for (int k = 0; k < 2; ++k) {
@@ -181,6 +182,8 @@ PH_API int phprng_create(phprng_ctx **out, int width, const phprng_instance *ins
     }
     c->sk32 = derive_skip(c->p, c->a, gen_npt(0));
     c->sk64 = derive_skip(c->p, c->a, gen_npt(1));
+    c->sk32_4 = derive_skip(c->p, c->a, 4);
+    c->sk32_2 = derive_skip(c->p, c->a, 2);
     cudaStream_t s = (cudaStream_t)cuda_stream;
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_inst, count * sizeof(DevInst));
@@ -444,27 +447,33 @@ PH_API int phprng_get_state(phprng_ctx *ctx, uint64_t inst, phprng_instance *sta
 static int ensure_skip(phprng_ctx *c, cudaStream_t s)
 {
     if (c->skip_ready) return PHPRNG_OK;
-    std::vector<uint64_t> s0(c->count), L0(c->count);
-    for (uint64_t i = 0; i < c->count; ++i) s0[i] = c->host_inst[i].s0;
+    std::vector<uint64_t> s0(c->count), L0(c->count), m0(c->count);
+    for (uint64_t i = 0; i < c->count; ++i) {
+        s0[i] = c->host_inst[i].s0;
+        m0[i] = c->host_inst[i].m0;
+    }
     if (!discrete_logs(c->p, c->a, s0.data(), c->count, L0.data()))
         return fail(c, PHPRNG_ESKIP, "phprng_skip: no discrete log for a seed s0 (a not a primitive root?)");
     SkipTable tb = derive_skip_table(c->p, c->a);
     uint64_t *seg = nullptr;
     cudaError_t e = cudaMalloc(&c->d_L0, c->count * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_m0, c->count * 8);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_T, tb.nT * 8);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_P, tb.nT * 4);
     if (e == cudaSuccess) e = cudaMalloc(&seg, tb.nT * 8);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->d_L0, L0.data(), c->count * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->d_m0, m0.data(), c->count * 8, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) {
         cudaFree(seg);
-        cudaFree(c->d_L0); cudaFree(c->d_T); cudaFree(c->d_P);
-        c->d_L0 = c->d_T = nullptr; c->d_P = nullptr;
+        cudaFree(c->d_L0); cudaFree(c->d_m0); cudaFree(c->d_T); cudaFree(c->d_P);
+        c->d_L0 = c->d_m0 = c->d_T = nullptr; c->d_P = nullptr;
         return cuda_fail(c, e, "phprng_skip: table allocation");
     }
     std::string err;
     int rc = launch_build_skip_table(c->p, c->a, c->d_T, c->d_P, seg, s, &err);
-    cudaError_t e2 = cudaStreamSynchronize(s);                 // L0 host copy, seg lifetime
+    cudaError_t e2 = cudaStreamSynchronize(s);                 // host copies, seg lifetime
     cudaFree(seg);
     if (rc != PHPRNG_OK) return fail(c, rc, "phprng_skip: " + err);
     if (e2 != cudaSuccess) return cuda_fail(c, e2, "phprng_skip: table build");
@@ -530,4 +539,304 @@ PH_API int phprng_microbench(int which, double *ops_per_s, void *cuda_stream)
     int rc = run_microbench(which, ops_per_s, cuda_stream, &err);
     if (rc != PHPRNG_OK) return fail(nullptr, rc, err);
     return PHPRNG_OK;
+}
+
+// ---- batches ----------------------------------------------------------------
+
+struct phprng_plan {
+    struct Req {
+        uint64_t inst, start, len, c_off, r_off;
+        bool last;                         // last request of its instance
+    };
+    phprng_ctx *ctx = nullptr;
+    std::vector<Req> reqs;
+    std::vector<std::pair<uint64_t, uint64_t>> final_pos;   // (instance, position after)
+    Tile *d_tiles = nullptr;
+    size_t tiles_cap = 0;
+    uint64_t ntiles = 0;
+    unsigned long long *d_counter = nullptr;
+    phprng_tuning tune{};
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    void *g_c = nullptr;
+    double *g_r = nullptr;
+};
+
+static const uint32_t kDefaultTile = 16384;
+
+static void free_plan(phprng_plan *pl)
+{
+    if (!pl) return;
+    cudaDeviceSynchronize();
+    if (pl->gexec) cudaGraphExecDestroy(pl->gexec);
+    if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
+    cudaFree(pl->d_tiles);
+    cudaFree(pl->d_counter);
+    delete pl;
+}
+
+// Cuts the resolved requests into tiles, heaviest first, and uploads them.
+static int build_tiles(phprng_plan *pl, uint32_t tile)
+{
+    phprng_ctx *c = pl->ctx;
+    std::vector<Tile> t;
+    for (const auto &r : pl->reqs) {
+        const uint32_t wide = c->wide[r.inst] ? kTileWide : 0u;
+        for (uint64_t k = 0; k < r.len; k += tile) {
+            Tile x;
+            x.len = (uint32_t)std::min<uint64_t>(tile, r.len - k);
+            x.inst = (uint32_t)r.inst | wide | ((r.last && k + x.len == r.len) ? kTileWriteBack : 0u);
+            x.start = r.start + k;
+            x.c_off = r.c_off + k;
+            x.r_off = r.r_off + k;
+            t.push_back(x);
+        }
+    }
+    std::stable_sort(t.begin(), t.end(), [](const Tile &a, const Tile &b) {
+        const bool wa = (a.inst & kTileWide) != 0, wb = (b.inst & kTileWide) != 0;
+        if (wa != wb) return wa;
+        return a.len > b.len;
+    });
+    if (t.size() > pl->tiles_cap) {
+        cudaFree(pl->d_tiles);
+        pl->d_tiles = nullptr;
+        pl->tiles_cap = 0;
+        cudaError_t e = cudaMalloc(&pl->d_tiles, t.size() * sizeof(Tile));
+        if (e != cudaSuccess) return cuda_fail(c, e, "phprng_plan: tile list allocation");
+        pl->tiles_cap = t.size();
+    }
+    if (!t.empty())
+        CU(c, cudaMemcpy(pl->d_tiles, t.data(), t.size() * sizeof(Tile), cudaMemcpyHostToDevice));
+    pl->ntiles = t.size();
+    pl->tune.tile = tile;
+    if (pl->gexec) {                                  // the captured graph names the old list
+        cudaGraphExecDestroy(pl->gexec);
+        pl->gexec = nullptr;
+    }
+    return PHPRNG_OK;
+}
+
+static BatchArgs batch_args(phprng_plan *pl, void *c_base, double *r_base)
+{
+    phprng_ctx *c = pl->ctx;
+    BatchArgs a;
+    a.inst = c->d_inst;
+    a.prog = c->d_prog;
+    a.st = c->st;
+    a.m0 = c->d_m0;
+    a.L0 = c->d_L0;
+    a.tb = c->tbl;
+    a.sk32_4 = c->sk32_4;
+    a.sk32_2 = c->sk32_2;
+    a.sk64 = c->sk64;
+    a.tiles = pl->d_tiles;
+    a.ntiles = pl->ntiles;
+    a.counter = pl->d_counter;
+    a.c_base = c_base;
+    a.r_base = r_base;
+    a.c_is_64 = c->width != 32;
+    a.vec_ok = ((uintptr_t)c_base % 16 == 0) && ((uintptr_t)r_base % 16 == 0);
+    return a;
+}
+
+PH_API int phprng_plan_create(phprng_ctx *ctx, const phprng_request *reqs, uint64_t nreq,
+                              uint32_t tile, phprng_plan **out, void *cuda_stream)
+{
+    if (!out) return fail(ctx, PHPRNG_EINVAL, "phprng_plan_create: out is NULL");
+    *out = nullptr;
+    if (!ctx) return fail(nullptr, PHPRNG_EINVAL, "phprng_plan_create: ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (nreq && !reqs) return fail(ctx, PHPRNG_EINVAL, "phprng_plan_create: reqs is NULL");
+    if (tile == 0) tile = kDefaultTile;
+    if (tile > (1u << 30)) return fail(ctx, PHPRNG_EINVAL, "phprng_plan_create: tile above 2^30");
+    if (ctx->count > kTileInstMask)
+        return fail(ctx, PHPRNG_EINVAL, "phprng_plan_create: more than 2^30 instances");
+    phprng_plan *pl = new (std::nothrow) phprng_plan;
+    if (!pl) return fail(ctx, PHPRNG_ENOMEM, "phprng_plan_create: host allocation failed");
+    pl->ctx = ctx;
+    pl->tune.npt = 4;
+    pl->tune.blocks_per_sm = 0;
+    try {
+        std::vector<uint64_t> cursor(ctx->pos_host);
+        std::vector<int64_t> lastreq(ctx->count, -1);
+        pl->reqs.reserve(nreq);
+        for (uint64_t j = 0; j < nreq; ++j) {
+            const phprng_request &r = reqs[j];
+            if (r.inst >= ctx->count) {
+                delete pl;
+                return fail(ctx, PHPRNG_EINVAL, "phprng_plan_create: request " + std::to_string(j) +
+                                                    ": instance out of range");
+            }
+            const uint64_t start = r.offset == PHPRNG_CONTINUE ? cursor[r.inst] : r.offset;
+            if (r.len > UINT64_MAX - start || r.len > UINT64_MAX - r.c_off ||
+                r.len > UINT64_MAX - r.r_off) {
+                delete pl;
+                return fail(ctx, PHPRNG_EINVAL, "phprng_plan_create: request " + std::to_string(j) +
+                                                    ": position or offset overflow");
+            }
+            cursor[r.inst] = start + r.len;
+            if (r.len == 0) continue;
+            lastreq[r.inst] = (int64_t)pl->reqs.size();
+            pl->reqs.push_back({r.inst, start, r.len, r.c_off, r.r_off, false});
+        }
+        for (uint64_t i = 0; i < ctx->count; ++i) {
+            if (lastreq[i] >= 0) {
+                pl->reqs[lastreq[i]].last = true;
+                pl->final_pos.push_back({i, cursor[i]});
+            }
+        }
+    } catch (const std::bad_alloc &) {
+        delete pl;
+        return fail(ctx, PHPRNG_ENOMEM, "phprng_plan_create: host allocation failed");
+    }
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) { delete pl; return cuda_fail(ctx, e, "cudaSetDevice"); }
+    int rc = ensure_skip(ctx, (cudaStream_t)cuda_stream);
+    if (rc != PHPRNG_OK) { delete pl; return rc; }
+    e = cudaMalloc(&pl->d_counter, sizeof(unsigned long long));
+    if (e != cudaSuccess) { free_plan(pl); return cuda_fail(ctx, e, "phprng_plan_create: counter"); }
+    rc = build_tiles(pl, tile);
+    if (rc != PHPRNG_OK) { free_plan(pl); return rc; }
+    *out = pl;
+    return PHPRNG_OK;
+}
+
+static int plan_launch_locked(phprng_plan *pl, void *c_base, double *r_base, cudaStream_t s)
+{
+    phprng_ctx *c = pl->ctx;
+    const size_t csz = c->width == 32 ? 4 : 8;
+    if ((uintptr_t)c_base % csz || (uintptr_t)r_base % 8)
+        return fail(c, PHPRNG_EINVAL, "phprng_plan_launch: output base not aligned to its element");
+    std::string err;
+    int rc = launch_batch(batch_args(pl, c_base, r_base), pl->tune.npt, pl->tune.blocks_per_sm, s, &err);
+    if (rc != PHPRNG_OK) return fail(c, rc, "phprng_plan_launch: " + err);
+    for (const auto &fp : pl->final_pos) c->pos_host[fp.first] = fp.second;
+    return PHPRNG_OK;
+}
+
+PH_API int phprng_plan_launch(phprng_plan *plan, void *c_base, double *r_base, void *cuda_stream)
+{
+    if (!plan) return fail(nullptr, PHPRNG_EINVAL, "phprng_plan_launch: plan is NULL");
+    std::lock_guard<std::mutex> lk(plan->ctx->mu);
+    CU(plan->ctx, cudaSetDevice(plan->ctx->device));
+    return plan_launch_locked(plan, c_base, r_base, (cudaStream_t)cuda_stream);
+}
+
+PH_API int phprng_plan_launch_graph(phprng_plan *plan, void *c_base, double *r_base,
+                                    void *cuda_stream)
+{
+    if (!plan) return fail(nullptr, PHPRNG_EINVAL, "phprng_plan_launch_graph: plan is NULL");
+    phprng_ctx *c = plan->ctx;
+    std::lock_guard<std::mutex> lk(c->mu);
+    CU(c, cudaSetDevice(c->device));
+    if (!plan->gexec || plan->g_c != c_base || plan->g_r != r_base) {
+        if (plan->gexec) {
+            cudaGraphExecDestroy(plan->gexec);
+            plan->gexec = nullptr;
+        }
+        if (!plan->cap_stream)
+            CU(c, cudaStreamCreateWithFlags(&plan->cap_stream, cudaStreamNonBlocking));
+        CU(c, cudaStreamBeginCapture(plan->cap_stream, cudaStreamCaptureModeThreadLocal));
+        int rc = plan_launch_locked(plan, c_base, r_base, plan->cap_stream);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(plan->cap_stream, &g);
+        if (rc != PHPRNG_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(c, e, "phprng_plan_launch_graph: capture");
+        e = cudaGraphInstantiate(&plan->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            plan->gexec = nullptr;
+            return cuda_fail(c, e, "phprng_plan_launch_graph: instantiate");
+        }
+        plan->g_c = c_base;
+        plan->g_r = r_base;
+    }
+    CU(c, cudaGraphLaunch(plan->gexec, (cudaStream_t)cuda_stream));
+    for (const auto &fp : plan->final_pos) c->pos_host[fp.first] = fp.second;
+    return PHPRNG_OK;
+}
+
+PH_API int phprng_plan_autotune(phprng_plan *plan, void *c_base, double *r_base,
+                                phprng_tuning *best, void *cuda_stream)
+{
+    if (!plan) return fail(nullptr, PHPRNG_EINVAL, "phprng_plan_autotune: plan is NULL");
+    phprng_ctx *c = plan->ctx;
+    std::lock_guard<std::mutex> lk(c->mu);
+    CU(c, cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const uint32_t tiles[] = {4096, 16384, 65536};
+    const int npts[] = {4, 2};
+    cudaEvent_t e0, e1;
+    CU(c, cudaEventCreate(&e0));
+    CU(c, cudaEventCreate(&e1));
+    phprng_tuning bestt = plan->tune;
+    bestt.ms = -1.f;
+    int rc = PHPRNG_OK;
+    for (uint32_t tile : tiles) {
+        rc = build_tiles(plan, tile);
+        if (rc != PHPRNG_OK) break;
+        for (int npt : npts) {
+            const int maxb = batch_max_blocks_per_sm(npt, c->width != 32);
+            for (int b = 1; b <= maxb && rc == PHPRNG_OK; ++b) {
+                plan->tune.npt = npt;
+                plan->tune.blocks_per_sm = b;
+                rc = plan_launch_locked(plan, c_base, r_base, s);           // warm-up
+                if (rc != PHPRNG_OK) break;
+                cudaEventRecord(e0, s);
+                for (int r = 0; r < 2 && rc == PHPRNG_OK; ++r)
+                    rc = plan_launch_locked(plan, c_base, r_base, s);
+                cudaEventRecord(e1, s);
+                cudaError_t e = cudaEventSynchronize(e1);
+                if (e != cudaSuccess) { rc = cuda_fail(c, e, "phprng_plan_autotune"); break; }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                ms /= 2.f;
+                if (bestt.ms < 0.f || ms < bestt.ms) {
+                    bestt = plan->tune;
+                    bestt.ms = ms;
+                }
+            }
+            if (rc != PHPRNG_OK) break;
+        }
+        if (rc != PHPRNG_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != PHPRNG_OK) return rc;
+    rc = build_tiles(plan, bestt.tile);
+    if (rc != PHPRNG_OK) return rc;
+    plan->tune = bestt;
+    if (best) *best = bestt;
+    return PHPRNG_OK;
+}
+
+PH_API int phprng_plan_tuning(const phprng_plan *plan, phprng_tuning *out)
+{
+    if (!plan || !out) return fail(nullptr, PHPRNG_EINVAL, "phprng_plan_tuning: NULL argument");
+    *out = plan->tune;
+    return PHPRNG_OK;
+}
+
+PH_API int phprng_plan_destroy(phprng_plan *plan)
+{
+    free_plan(plan);
+    return PHPRNG_OK;
+}
+
+PH_API int phprng_generate_batch(phprng_ctx *ctx, const phprng_request *reqs, uint64_t nreq,
+                                 void *c_base, double *r_base, void *cuda_stream)
+{
+    phprng_plan *pl = nullptr;
+    int rc = phprng_plan_create(ctx, reqs, nreq, 0, &pl, cuda_stream);
+    if (rc != PHPRNG_OK) return rc;
+    rc = phprng_plan_launch(pl, c_base, r_base, cuda_stream);
+    if (rc == PHPRNG_OK) {
+        cudaError_t e = cudaStreamSynchronize((cudaStream_t)cuda_stream);
+        if (e != cudaSuccess) rc = cuda_fail(ctx, e, "phprng_generate_batch");
+    }
+    free_plan(pl);
+    return rc;
 }

@@ -1,32 +1,14 @@
 // gen.cu -- generator kernels: Eq. 9 for many independent instances.
 //
-// Work split.  One warp owns one instance (its exponent e is then uniform
-// across the warp, so the square-and-multiply loop has no divergence).  The
-// warp walks the instance's stream in groups of G = 32*NPT numbers; in a
-// group lane j owns the NPT consecutive numbers G*g + NPT*j + 1 .. + NPT,
-// which makes a lane's outputs contiguous and a group's outputs one
-// contiguous run of G values.
-//
-// Per group (position t before the group, state m_t, s_t):
-//   skips   lane j keeps sigma_j = s at the position just before its run and
-//           steps it NPT times with Eq. 9a (Montgomery product mod p);
-//           sigma_j advances by a^G per group (Eq. 6a: s_k = s_0 a^k mod p);
-//   messages  m at lane j's u-th number = m_t + (sum of the skips before it),
-//           Eq. 6b, formed as an exclusive warp scan mod n of the lanes'
-//           skip sums plus the lane's own running sum (Eq. 9b);
-//   encrypt c = m^e mod n (Eq. 9c) by the instance's sliding-window program
-//           (squarings and products with odd powers of m) on Montgomery
-//           products started from the plain message, closed by one product
-//           with the per-instance constant K;
-//   float   R = (c+1)/(n+1) (Eq. 9d): integer-built correctly rounded double
-//           for n < 2^32, hardware FP64 division of the rounded operands for
-//           64-bit n;
-//   store   c and/or R; 16-byte vector stores when aligned.
-// The lane that owns the last number writes the state back (m, s, c, pos).
+// One warp owns one instance, so the exponent -- and with it every branch of
+// the square-and-multiply program -- is uniform across the warp.  The warp
+// walks the instance's stream in groups of 32*NPT numbers (gencore.cuh: skip
+// steps, warp scan of the messages, encryption, integer-built R); a group's
+// outputs are one contiguous run, so every lane stores 16-byte vectors.  The
+// lane that owns the call's last number writes the state back (m, s, c, pos).
 #include <cuda_runtime.h>
 
-#include "arith.cuh"
-#include "internal.h"
+#include "gencore.cuh"
 
 namespace phprng {
 
@@ -42,7 +24,7 @@ namespace phprng {
 static constexpr int kNPT = PH_NPT32;     // numbers per lane per group (32-bit path)
 static constexpr int kNPT64 = PH_NPT64;   // numbers per lane per group (64-bit path)
 static constexpr int kWarpsPerBlock = 8;
-static constexpr unsigned kFull = 0xffffffffu;
+static constexpr unsigned kFull = kFullMask;
 
 int gen_npt(int wide) { return wide ? kNPT64 : kNPT; }
 
@@ -72,13 +54,13 @@ __device__ __forceinline__ double u128d(u128 v) { return u128_to_double((uint64_
 template <int NPT, typename CT, bool STATS>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, STATS ? 1 : PH_MINB32)
 gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, DevState st,
-             SkipConst sk, uint64_t first,
-             uint64_t num, uint64_t per_inst, CT *__restrict__ c_out,
-             double *__restrict__ r_out, int vec_ok, phprng_stats *__restrict__ stats,
-             uint32_t *__restrict__ edge)
+             SkipConst sk, uint64_t first, uint64_t num, uint64_t per_inst,
+             CT *__restrict__ c_out, double *__restrict__ r_out, int vec_ok,
+             phprng_stats *__restrict__ stats, uint32_t *__restrict__ edge)
 {
     extern __shared__ uint32_t smem[];   // STATS: cbuf[2][W][32*NPT] then hist[W][256]
     constexpr int W = kWarpsPerBlock;
+    constexpr uint64_t G = 32 * NPT;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint64_t w = (uint64_t)blockIdx.x * W + warp;
     const bool active = w < num;
@@ -86,13 +68,13 @@ gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
     const uint64_t i = first + (active ? w : 0);
     const DevInst P = inst[i];
     if (!STATS && P.wide) return;
-    const uint32_t n = (uint32_t)P.n, ninv = (uint32_t)P.ninv, K = (uint32_t)P.K;
-    const uint32_t p = sk.p, pinv = sk.pinv, aM = sk.aM;
+    const ExpProg &pg = prog[i];
 
     uint32_t M = (uint32_t)st.m[i];
-    uint32_t sig = mont32((uint32_t)st.s[i], sk.lane[lane], p, pinv);
-    const uint64_t base = w * per_inst;
-    constexpr uint64_t G = 32 * NPT;
+    uint32_t sig = mont32((uint32_t)st.s[i], sk.lane[lane], sk.p, sk.pinv);
+    const uint64_t pos_after = st.pos[i] + per_inst;
+    CT *cdst = c_out ? c_out + w * per_inst : nullptr;
+    double *rdst = r_out ? r_out + w * per_inst : nullptr;
 
     uint32_t *hist = smem + 2 * W * (32 * NPT) + warp * 256;
     u128 X = 0, Y = 0, Z = 0;
@@ -105,79 +87,12 @@ gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
 
     for (uint64_t g0 = 0; g0 < per_inst; g0 += G) {
         uint32_t sv[NPT], msg[NPT], x[NPT];
-        double rv[NPT];
         const uint64_t my0 = g0 + (uint64_t)NPT * lane;
         if (active) {
-            uint32_t S = 0, t = sig;
-#pragma unroll
-            for (int u = 0; u < NPT; ++u) {
-                t = mont32(t, aM, p, pinv);                      // Eq. 9a
-                sv[u] = t;
-                if (my0 + u < per_inst) S = addmod32(S, t, n);
-            }
-            uint32_t incl = S;
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                uint32_t y = __shfl_up_sync(kFull, incl, off);
-                if (lane >= off) incl = addmod32(incl, y, n);
-            }
-            const uint32_t total = __shfl_sync(kFull, incl, 31);
-            uint32_t mm = addmod32(M, submod32(incl, S, n), n);
-#pragma unroll
-            for (int u = 0; u < NPT; ++u) {
-                mm = addmod32(mm, sv[u], n);                      // Eq. 9b
-                msg[u] = mm;
-            }
-            modexp_prog<NPT, uint32_t>(x, msg, prog[i], n, ninv, K);   // Eq. 9c
-#pragma unroll
-            for (int u = 0; u < NPT; ++u) rv[u] = real32(x[u], P.yN, P.ybits, P.V);   // Eq. 9d
-
-            const bool full = my0 + NPT <= per_inst;
-            if (c_out) {
-                CT *dst = c_out + base + my0;
-                if (full && vec_ok && sizeof(CT) == 4 && NPT % 4 == 0) {
-#pragma unroll
-                    for (int u = 0; u < NPT; u += 4)
-                        *reinterpret_cast<uint4 *>(dst + u) = make_uint4(x[u], x[u + 1], x[u + 2], x[u + 3]);
-                } else if (full && vec_ok && sizeof(CT) == 8 && NPT % 2 == 0) {
-#pragma unroll
-                    for (int u = 0; u < NPT; u += 2)
-                        *reinterpret_cast<ulonglong2 *>(dst + u) = make_ulonglong2(x[u], x[u + 1]);
-                } else {
-#pragma unroll
-                    for (int u = 0; u < NPT; ++u)
-                        if (my0 + u < per_inst) dst[u] = (CT)x[u];
-                }
-            }
-            if (r_out) {
-                double *dst = r_out + base + my0;
-                if (full && vec_ok && NPT % 2 == 0) {
-#pragma unroll
-                    for (int u = 0; u < NPT; u += 2)
-                        *reinterpret_cast<double2 *>(dst + u) = make_double2(rv[u], rv[u + 1]);
-                } else {
-#pragma unroll
-                    for (int u = 0; u < NPT; ++u)
-                        if (my0 + u < per_inst) dst[u] = rv[u];
-                }
-            }
-            if (g0 + G >= per_inst) {                            // state write-back
-                const uint64_t last = per_inst - 1 - g0;
-                if ((uint64_t)lane == last / NPT) {
-                    const int ul = (int)(last % NPT);
-#pragma unroll
-                    for (int u = 0; u < NPT; ++u) {
-                        if (u == ul) {
-                            st.m[i] = msg[u];
-                            st.s[i] = sv[u];
-                            st.c[i] = x[u];
-                        }
-                    }
-                    st.pos[i] += per_inst;
-                }
-            }
-            M = addmod32(M, total, n);
-            sig = mont32(sig, sk.aGM, p, pinv);
+            group32<NPT>(P, pg, sk, lane, my0, per_inst, M, sig, sv, msg, x);
+            store_group<NPT, CT, uint32_t>(P, cdst, rdst, my0, per_inst, vec_ok, x);
+            writeback_if_last<NPT, uint32_t, uint32_t>(st, i, lane, g0, per_inst, pos_after, sv,
+                                                       msg, x);
         }
         if (STATS) {
             uint32_t *cb = smem + ((int)((g0 / G) & 1) * W + warp) * (32 * NPT);
@@ -189,7 +104,7 @@ gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
                         const uint64_t v = (uint64_t)x[u] + 1;
                         X += v;
                         Y += (u128)(v * v);
-                        atomicAdd(&hist[hist_bin256(rv[u])], 1u);
+                        atomicAdd(&hist[hist_bin256(real_of(P, x[u]))], 1u);
                     }
                 }
                 if (edge && ((warp == W - 1 && has_next) || (warp == 0 && blockIdx.x > 0))) {
@@ -217,7 +132,7 @@ gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
         phprng_stats *o = stats + w;
         for (int b = lane; b < 256; b += 32) o->hist[b] = hist[b];
         if (lane == 0) {
-            const u128 N = per_inst, n1 = (u128)n + 1;
+            const u128 N = per_inst, n1 = P.n + 1;
             o->x_lo = (uint64_t)X; o->x_hi = (uint64_t)(X >> 64);
             o->y_lo = (uint64_t)Y; o->y_hi = (uint64_t)(Y >> 64);
             o->z_lo = (uint64_t)Z; o->z_hi = (uint64_t)(Z >> 64);
@@ -265,96 +180,29 @@ stats_edge_kernel(const DevInst *__restrict__ inst, const uint32_t *__restrict__
 template <int NPT>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 gen64_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, DevState st,
-             SkipConst sk, uint64_t first,
-             uint64_t num, uint64_t per_inst, uint64_t *__restrict__ c_out,
-             double *__restrict__ r_out, int vec_ok)
+             SkipConst sk, uint64_t first, uint64_t num, uint64_t per_inst,
+             uint64_t *__restrict__ c_out, double *__restrict__ r_out, int vec_ok)
 {
+    constexpr uint64_t G = 32 * NPT;
     const int lane = threadIdx.x & 31;
     const uint64_t w = (uint64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     if (w >= num) return;
     const uint64_t i = first + w;
     const DevInst P = inst[i];
     if (!P.wide) return;
-    const uint64_t n = P.n, ninv = P.ninv, K = P.K;
-    const uint32_t p = sk.p, pinv = sk.pinv, aM = sk.aM;
-
+    const ExpProg &pg = prog[i];
     uint64_t M = st.m[i];
-    uint32_t sig = mont32((uint32_t)st.s[i], sk.lane[lane], p, pinv);
-    const uint64_t base = w * per_inst;
-    constexpr uint64_t G = 32 * NPT;
-
+    uint32_t sig = mont32((uint32_t)st.s[i], sk.lane[lane], sk.p, sk.pinv);
+    const uint64_t pos_after = st.pos[i] + per_inst;
+    uint64_t *cdst = c_out ? c_out + w * per_inst : nullptr;
+    double *rdst = r_out ? r_out + w * per_inst : nullptr;
     for (uint64_t g0 = 0; g0 < per_inst; g0 += G) {
         uint32_t sv[NPT];
         uint64_t msg[NPT], x[NPT];
         const uint64_t my0 = g0 + (uint64_t)NPT * lane;
-        uint64_t S = 0;
-        uint32_t t = sig;
-#pragma unroll
-        for (int u = 0; u < NPT; ++u) {
-            t = mont32(t, aM, p, pinv);
-            sv[u] = t;
-            if (my0 + u < per_inst) S = addmod64(S, t, n);
-        }
-        uint64_t incl = S;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            uint64_t y = __shfl_up_sync(kFull, incl, off);
-            if (lane >= off) incl = addmod64(incl, y, n);
-        }
-        const uint64_t total = __shfl_sync(kFull, incl, 31);
-        uint64_t mm = addmod64(M, incl >= S ? incl - S : incl - S + n, n);
-#pragma unroll
-        for (int u = 0; u < NPT; ++u) {
-            mm = addmod64(mm, sv[u], n);                          // Eq. 9b
-            msg[u] = mm;
-        }
-        modexp_prog<NPT, uint64_t>(x, msg, prog[i], n, ninv, K);     // Eq. 9c
-
-        const bool full = my0 + NPT <= per_inst;
-        if (c_out) {
-            uint64_t *dst = c_out + base + my0;
-            if (full && vec_ok && NPT % 2 == 0) {
-#pragma unroll
-                for (int u = 0; u < NPT; u += 2)
-                    *reinterpret_cast<ulonglong2 *>(dst + u) = make_ulonglong2(x[u], x[u + 1]);
-            } else {
-#pragma unroll
-                for (int u = 0; u < NPT; ++u)
-                    if (my0 + u < per_inst) dst[u] = x[u];
-            }
-        }
-        if (r_out) {
-            double *dst = r_out + base + my0;
-            double rv[NPT];
-#pragma unroll
-            for (int u = 0; u < NPT; ++u) rv[u] = real64(x[u], n);
-            if (full && vec_ok && NPT % 2 == 0) {
-#pragma unroll
-                for (int u = 0; u < NPT; u += 2)
-                    *reinterpret_cast<double2 *>(dst + u) = make_double2(rv[u], rv[u + 1]);
-            } else {
-#pragma unroll
-                for (int u = 0; u < NPT; ++u)
-                    if (my0 + u < per_inst) dst[u] = rv[u];
-            }
-        }
-        if (g0 + G >= per_inst) {
-            const uint64_t last = per_inst - 1 - g0;
-            if ((uint64_t)lane == last / NPT) {
-                const int ul = (int)(last % NPT);
-#pragma unroll
-                for (int u = 0; u < NPT; ++u) {
-                    if (u == ul) {
-                        st.m[i] = msg[u];
-                        st.s[i] = sv[u];
-                        st.c[i] = x[u];
-                    }
-                }
-                st.pos[i] += per_inst;
-            }
-        }
-        M = addmod64(M, total, n);
-        sig = mont32(sig, sk.aGM, p, pinv);
+        group64<NPT>(P, pg, sk, lane, my0, per_inst, M, sig, sv, msg, x);
+        store_group<NPT, uint64_t, uint64_t>(P, cdst, rdst, my0, per_inst, vec_ok, x);
+        writeback_if_last<NPT, uint64_t, uint64_t>(st, i, lane, g0, per_inst, pos_after, sv, msg, x);
     }
 }
 

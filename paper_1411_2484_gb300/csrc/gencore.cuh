@@ -1,0 +1,162 @@
+// gencore.cuh -- one warp group of Eq. 9, shared by the plain, fused and
+// batched kernels.
+//
+// A warp owns one instance and walks its stream in groups of G = 32*NPT
+// numbers; in a group lane j owns the NPT consecutive numbers my0 + 1 ..
+// my0 + NPT (my0 = g0 + NPT*j, counted from the start of the run).  Entering
+// a group the warp holds M = the message before the group and, per lane,
+// sig = the skip just before the lane's first number.  The group:
+//   skips     sv_u = sig a^u mod p, u = 1..NPT                      (Eq. 9a)
+//   messages  msg_u = M + (skips of lower lanes) + sv_1 + .. + sv_u  (Eq. 6b, 9b)
+//             -- the lower-lane sum is an exclusive warp scan mod n
+//   encrypt   x_u = msg_u^e mod n by the instance's program          (Eq. 9c)
+// and leaves M and sig ready for the next group; R = (x_u+1)/(n+1) (Eq. 9d)
+// is formed where it is stored or consumed (real_of).  Numbers past `len` are
+// computed but excluded from the sums that carry into later numbers.
+#pragma once
+#include "arith.cuh"
+#include "internal.h"
+
+namespace phprng {
+
+static constexpr unsigned kFullMask = 0xffffffffu;
+
+template <int NPT>
+__device__ __forceinline__ void group32(const DevInst &P, const ExpProg &pg, const SkipConst &sk,
+                                        int lane, uint64_t my0, uint64_t len, uint32_t &M,
+                                        uint32_t &sig, uint32_t (&sv)[NPT], uint32_t (&msg)[NPT],
+                                        uint32_t (&x)[NPT])
+{
+    const uint32_t n = (uint32_t)P.n, p = sk.p, pinv = sk.pinv;
+    uint32_t S = 0, t = sig;
+#pragma unroll
+    for (int u = 0; u < NPT; ++u) {
+        t = mont32(t, sk.aM, p, pinv);                           // Eq. 9a
+        sv[u] = t;
+        if (my0 + u < len) S = addmod32(S, t, n);
+    }
+    uint32_t incl = S;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFullMask, incl, off);
+        if (lane >= off) incl = addmod32(incl, y, n);
+    }
+    const uint32_t total = __shfl_sync(kFullMask, incl, 31);
+    uint32_t mm = addmod32(M, submod32(incl, S, n), n);
+#pragma unroll
+    for (int u = 0; u < NPT; ++u) {
+        mm = addmod32(mm, sv[u], n);                              // Eq. 9b
+        msg[u] = mm;
+    }
+    modexp_prog<NPT, uint32_t>(x, msg, pg, n, (uint32_t)P.ninv, (uint32_t)P.K);   // Eq. 9c
+    M = addmod32(M, total, n);
+    sig = mont32(sig, sk.aGM, p, pinv);
+}
+
+template <int NPT>
+__device__ __forceinline__ void group64(const DevInst &P, const ExpProg &pg, const SkipConst &sk,
+                                        int lane, uint64_t my0, uint64_t len, uint64_t &M,
+                                        uint32_t &sig, uint32_t (&sv)[NPT], uint64_t (&msg)[NPT],
+                                        uint64_t (&x)[NPT])
+{
+    const uint64_t n = P.n;
+    const uint32_t p = sk.p, pinv = sk.pinv;
+    uint64_t S = 0;
+    uint32_t t = sig;
+#pragma unroll
+    for (int u = 0; u < NPT; ++u) {
+        t = mont32(t, sk.aM, p, pinv);
+        sv[u] = t;
+        if (my0 + u < len) S = addmod64(S, t, n);
+    }
+    uint64_t incl = S;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint64_t y = __shfl_up_sync(kFullMask, incl, off);
+        if (lane >= off) incl = addmod64(incl, y, n);
+    }
+    const uint64_t total = __shfl_sync(kFullMask, incl, 31);
+    uint64_t mm = addmod64(M, incl >= S ? incl - S : incl - S + n, n);
+#pragma unroll
+    for (int u = 0; u < NPT; ++u) {
+        mm = addmod64(mm, sv[u], n);
+        msg[u] = mm;
+    }
+    modexp_prog<NPT, uint64_t>(x, msg, pg, n, P.ninv, P.K);
+    M = addmod64(M, total, n);
+    sig = mont32(sig, sk.aGM, p, pinv);
+}
+
+// R = (c+1)/(n+1) (Eq. 9d): integer-built and correctly rounded for 32-bit
+// n, RN(RN(c+1)/RN(n+1)) by the FP64 unit for 64-bit n.
+__device__ __forceinline__ double real_of(const DevInst &P, uint32_t c)
+{
+    return real32(c, P.yN, P.ybits, P.V);
+}
+__device__ __forceinline__ double real_of(const DevInst &P, uint64_t c) { return real64(c, P.n); }
+
+// Stores a lane's NPT outputs (16-byte vectors when the whole run of the
+// lane is inside `len` and vec_ok says the addresses are aligned).
+template <int NPT, typename CT, typename XT>
+__device__ __forceinline__ void store_group(const DevInst &P, CT *c_dst, double *r_dst,
+                                            uint64_t my0, uint64_t len, bool vec_ok,
+                                            const XT (&x)[NPT])
+{
+    const bool full = my0 + NPT <= len;
+    if (c_dst) {
+        CT *dst = c_dst + my0;
+        if (full && vec_ok && sizeof(CT) == 4 && NPT % 4 == 0) {
+#pragma unroll
+            for (int u = 0; u < NPT; u += 4)
+                *reinterpret_cast<uint4 *>(dst + u) =
+                    make_uint4((uint32_t)x[u], (uint32_t)x[u + 1], (uint32_t)x[u + 2], (uint32_t)x[u + 3]);
+        } else if (full && vec_ok && sizeof(CT) == 8 && NPT % 2 == 0) {
+#pragma unroll
+            for (int u = 0; u < NPT; u += 2)
+                *reinterpret_cast<ulonglong2 *>(dst + u) = make_ulonglong2(x[u], x[u + 1]);
+        } else {
+#pragma unroll
+            for (int u = 0; u < NPT; ++u)
+                if (my0 + u < len) dst[u] = (CT)x[u];
+        }
+    }
+    if (r_dst) {
+        double *dst = r_dst + my0;
+        if (full && vec_ok && NPT % 2 == 0) {
+#pragma unroll
+            for (int u = 0; u < NPT; u += 2)
+                *reinterpret_cast<double2 *>(dst + u) =
+                    make_double2(real_of(P, x[u]), real_of(P, x[u + 1]));
+        } else {
+#pragma unroll
+            for (int u = 0; u < NPT; ++u)
+                if (my0 + u < len) dst[u] = real_of(P, x[u]);
+        }
+    }
+}
+
+// The lane that owns number `len` of the run (g0 the group's first index)
+// writes the state after it: message, skip, ciphertext and position.
+template <int NPT, typename MT, typename XT>
+__device__ __forceinline__ void writeback_if_last(DevState st, uint64_t i, int lane, uint64_t g0,
+                                                  uint64_t len, uint64_t pos_after,
+                                                  const uint32_t (&sv)[NPT], const MT (&msg)[NPT],
+                                                  const XT (&x)[NPT])
+{
+    constexpr uint64_t G = 32 * NPT;
+    if (g0 + G < len) return;
+    const uint64_t last = len - 1 - g0;
+    if ((uint64_t)lane != last / NPT) return;
+    const int ul = (int)(last % NPT);
+#pragma unroll
+    for (int u = 0; u < NPT; ++u) {
+        if (u == ul) {
+            st.m[i] = msg[u];
+            st.s[i] = sv[u];
+            st.c[i] = x[u];
+        }
+    }
+    st.pos[i] = pos_after;
+}
+
+}  // namespace phprng

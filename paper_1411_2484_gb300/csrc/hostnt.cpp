@@ -259,12 +259,17 @@ static int build_program(uint64_t e, int w, ExpProg *pg)
     return products;
 }
 
-// The cheapest program over window sizes 1..3.
+#ifndef PH_MAX_WINDOW
+#define PH_MAX_WINDOW 3
+#endif
+
+// The cheapest program over window sizes 1..PH_MAX_WINDOW (at most 3: the
+// table holds up to four odd powers).
 static ExpProg best_program(uint64_t e)
 {
     ExpProg best, cand;
     int best_cost = -1;
-    for (int w = 1; w <= 3; ++w) {
+    for (int w = 1; w <= PH_MAX_WINDOW && w <= 3; ++w) {
         int c = build_program(e, w, &cand);
         if (c >= 0 && (best_cost < 0 || c < best_cost)) {
             best = cand;

@@ -82,6 +82,37 @@ struct SkipReq {
     uint64_t inst, k;
 };
 
+// ---- batched persistent launch (batch.cu) ----------------------------------
+// One tile: `len` consecutive numbers of one instance starting after stream
+// position `start`, written at element offsets c_off / r_off of the outputs.
+static constexpr uint32_t kTileInstMask = 0x3fffffffu;   // instance index
+static constexpr uint32_t kTileWide = 0x40000000u;       // 64-bit path
+static constexpr uint32_t kTileWriteBack = 0x80000000u;  // ends the instance's last request
+struct Tile {
+    uint32_t inst;
+    uint32_t len;
+    uint64_t start, c_off, r_off;
+};
+static_assert(sizeof(Tile) == 32, "Tile is 32 bytes");
+
+struct BatchArgs {
+    const DevInst *inst;
+    const ExpProg *prog;
+    DevState st;
+    const uint64_t *m0, *L0;        // seed message and the seed skip's cycle position
+    SkipTable tb;
+    SkipConst sk32_4, sk32_2, sk64; // lane constants for NPT = 4, 2 (32-bit) and 2 (64-bit)
+    const Tile *tiles;
+    uint64_t ntiles;
+    unsigned long long *counter;    // tile queue head, zeroed before each launch
+    void *c_base;
+    double *r_base;
+    int c_is_64;
+    int vec_ok;                     // c_base / r_base are 16-byte aligned
+};
+int launch_batch(const BatchArgs &a, int npt32, int blocks_per_sm, void *stream, std::string *err);
+int batch_max_blocks_per_sm(int npt32, int c_is_64);
+
 // ---- kernel launchers (gen.cu) -------------------------------------------
 int gen_npt(int wide);   // numbers per lane per warp group of the 32/64-bit launch
 int launch_gen32(const GenArgs &a, void *stream, std::string *err);

@@ -213,6 +213,27 @@ WORKLOADS = {
 }
 
 
+def batched_requests(instances32, instances64, max_len=1 << 20, max_offset=1 << 40, seed=7):
+    """Requests for the batched workload: one per instance (32-bit instances
+    first, then 64-bit), length floor(exp(U ln max_len)) in [1, max_len]
+    (log-uniform), start offset uniform in [0, max_offset), outputs packed
+    one after another (c and R at the same element offsets)."""
+    rng = SplitMix64(seed)
+    total = instances32 + instances64
+    reqs = np.zeros(total, dtype=[(k, "<u8") for k in ("inst", "offset", "len", "c_off", "r_off")])
+    off = 0
+    for i in range(total):
+        length = int(math.floor(math.exp(rng.uniform01() * math.log(max_len))))
+        length = min(max(length, 1), max_len)
+        reqs[i] = (i, rng.below(max_offset), length, off, off)
+        off += length
+    return reqs
+
+
+WORKLOADS["batched_20000_mixed"] = dict(instances32=16000, instances64=4000, max_len=1 << 20,
+                                        max_offset=1 << 40, seed=0x5EED0003)
+
+
 def workload_instances(name, count=None):
     """Instance table of a named workload (optionally only its first `count`)."""
     w = WORKLOADS[name]
