@@ -157,7 +157,8 @@ int phprng_skip(phprng_ctx *ctx, const uint64_t *inst_ids, const uint64_t *k, ui
  * number offset+1, reached by Eq. 7 without producing the numbers before it),
  * or, with offset = PHPRNG_CONTINUE, right after the instance's previous
  * request in the same batch (after its current position for the first one).
- * Outputs go to c_base[c_off + j] and r_base[r_off + j], j < len. */
+ * Outputs go to c_base[c_off + j] and r_base[r_off + j], j < len.  Requests
+ * with len = 0 are ignored (they move no position). */
 #define PHPRNG_CONTINUE UINT64_MAX
 typedef struct {
     uint64_t inst, offset, len, c_off, r_off;
@@ -211,6 +212,84 @@ int phprng_plan_destroy(phprng_plan *plan);
 /* plan_create + plan_launch + plan_destroy for one batch. */
 int phprng_generate_batch(phprng_ctx *ctx, const phprng_request *reqs, uint64_t nreq,
                           void *c_base, double *r_base, void *cuda_stream);
+
+/* ---------------------------------------------------------------- serving */
+
+/* A request loop over every stream of a context, kept in device memory
+ * (continuous batching).  Requests arrive through phprng_server_submit, now
+ * or at a stated future time on the phprng_clock_ns() clock (an open-loop
+ * arrival schedule is replayed exactly).  A scheduler thread admits arrived
+ * requests in FIFO order while their outputs fit in the output arena of
+ * output_budget_bytes (the admission bound; a request then starts right
+ * after the previous request of its stream), and whenever one of `inflight`
+ * CUDA streams is free launches one batched persistent launch for everything
+ * admitted since -- requests that arrive while others run join the next
+ * launch and overlap them on the device.  Finished requests are handed back
+ * by phprng_server_poll with their arrival and completion times; their
+ * outputs stay in the arena until phprng_server_release.  While a server
+ * runs, the context's other calls return PHPRNG_EINVAL. */
+typedef struct phprng_server phprng_server;   /* opaque, library-owned */
+
+typedef struct {
+    uint64_t output_budget_bytes;  /* arena size: the admission bound on outstanding outputs */
+    uint32_t max_batch;            /* requests per launch (0 = 4096) */
+    uint32_t inflight;             /* launches in flight, one CUDA stream each (0 = 2, max 16) */
+    uint32_t tile;                 /* numbers per tile (0 = 4096) */
+    uint32_t want_c;               /* nonzero: also store ciphertexts after each request's R */
+} phprng_server_config;
+
+typedef struct {
+    uint64_t id, tag, inst;        /* request id (from submit), caller tag, stream */
+    uint64_t start, len;           /* the request produced numbers start+1 .. start+len */
+    const double *r;               /* device pointer to its R values (Eq. 9d) */
+    const void *c;                 /* device pointer to its ciphertexts, or NULL */
+    int64_t arrival_ns, done_ns;   /* arrival and completion on phprng_clock_ns() */
+} phprng_completion;
+
+typedef struct {
+    uint64_t submitted, admitted, completed, batches, tiles, numbers;
+    uint64_t max_waiting;          /* most requests seen waiting for admission at once */
+    uint64_t waiting;              /* submitted and not yet admitted, now */
+    uint64_t outstanding_bytes;    /* arena bytes held by admitted or unreleased requests */
+} phprng_server_stats;
+
+/* Monotonic clock of the server (CLOCK_MONOTONIC), nanoseconds. */
+int64_t phprng_clock_ns(void);
+
+/* Allocates the output arena (device), builds the skip table if needed and
+ * starts the scheduler thread. */
+int phprng_server_create(phprng_ctx *ctx, const phprng_server_config *cfg,
+                         phprng_server **out);
+
+/* Submits count requests (host arrays): stream inst[j], len[j] numbers
+ * (1 <= len <= 2^32 and at most 65,536 tiles), optional tag[j] and optional
+ * arrival_ns[j] (NULL:
+ * now).  *first_id (nullable) receives the id of the first; ids are
+ * consecutive.  PHPRNG_EBUDGET if one request alone exceeds the arena. */
+int phprng_server_submit(phprng_server *srv, const uint64_t *inst, const uint64_t *len,
+                         const uint64_t *tag, const int64_t *arrival_ns, uint64_t count,
+                         uint64_t *first_id);
+
+/* Moves up to max finished requests into out (waiting up to timeout_ns for
+ * the first) and stores their number in *count. */
+int phprng_server_poll(phprng_server *srv, phprng_completion *out, uint64_t max,
+                       uint64_t *count, int64_t timeout_ns);
+
+/* Copies finished request id's outputs (len doubles to r_dst, len
+ * ciphertexts to c_dst; either NULL) into caller memory, host or device,
+ * before it is released.  Synchronous. */
+int phprng_server_copy(phprng_server *srv, uint64_t id, double *r_dst, void *c_dst);
+
+/* Returns the output memory of finished requests to the arena. */
+int phprng_server_release(phprng_server *srv, const uint64_t *ids, uint64_t count);
+
+/* Counters of the server so far. */
+int phprng_server_stats_get(phprng_server *srv, phprng_server_stats *out);
+
+/* Stops the server: requests not yet admitted are dropped, admitted ones
+ * finish; the streams' stored states are advanced to their served positions
+ * (Eq. 7); the arena is freed.  NULL is accepted. */
+int phprng_server_destroy(phprng_server *srv);
 
 /* Copies instance inst's parameters and current state to the host: the
  * returned phprng_instance holds {n, e, p, a, m, s} with m, s the current

@@ -39,6 +39,9 @@ EXPORTED = [
     "phprng_is_prime", "phprng_validate", "phprng_draw_instances", "phprng_microbench",
     "phprng_plan_create", "phprng_plan_launch", "phprng_plan_launch_graph",
     "phprng_plan_autotune", "phprng_plan_tuning", "phprng_plan_destroy", "phprng_generate_batch",
+    "phprng_clock_ns", "phprng_server_create", "phprng_server_submit", "phprng_server_poll",
+    "phprng_server_release", "phprng_server_stats_get", "phprng_server_destroy",
+    "phprng_server_copy",
 ]
 PHPRNG_CONTINUE = (1 << 64) - 1
 
@@ -56,6 +59,28 @@ class phprng_tuning(ctypes.Structure):
                 ("blocks_per_sm", ctypes.c_int32), ("ms", ctypes.c_float)]
 
 
+class phprng_server_config(ctypes.Structure):
+    _fields_ = [("output_budget_bytes", ctypes.c_uint64), ("max_batch", ctypes.c_uint32),
+                ("inflight", ctypes.c_uint32), ("tile", ctypes.c_uint32),
+                ("want_c", ctypes.c_uint32)]
+
+
+class phprng_completion(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("tag", ctypes.c_uint64), ("inst", ctypes.c_uint64),
+                ("start", ctypes.c_uint64), ("len", ctypes.c_uint64),
+                ("r", ctypes.c_void_p), ("c", ctypes.c_void_p),
+                ("arrival_ns", ctypes.c_int64), ("done_ns", ctypes.c_int64)]
+
+
+class phprng_server_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in (
+        "submitted", "admitted", "completed", "batches", "tiles", "numbers", "max_waiting",
+        "waiting", "outstanding_bytes")]
+
+
+COMPLETION_DTYPE = np.dtype([("id", "<u8"), ("tag", "<u8"), ("inst", "<u8"), ("start", "<u8"),
+                             ("len", "<u8"), ("r", "<u8"), ("c", "<u8"),
+                             ("arrival_ns", "<i8"), ("done_ns", "<i8")])
 REQUEST_DTYPE = np.dtype([(k, "<u8") for k in ("inst", "offset", "len", "c_off", "r_off")])
 
 
@@ -119,6 +144,17 @@ def _load():
         lib.phprng_plan_tuning.argtypes = [vp, ctypes.POINTER(phprng_tuning)]
         lib.phprng_plan_destroy.argtypes = [vp]
         lib.phprng_generate_batch.argtypes = [vp, P_req, u64, vp, vp, vp]
+        PI64 = ctypes.POINTER(ctypes.c_int64)
+        lib.phprng_clock_ns.argtypes = []
+        lib.phprng_clock_ns.restype = ctypes.c_int64
+        lib.phprng_server_create.argtypes = [vp, ctypes.POINTER(phprng_server_config),
+                                             ctypes.POINTER(vp)]
+        lib.phprng_server_submit.argtypes = [vp, P64, P64, P64, PI64, u64, P64]
+        lib.phprng_server_poll.argtypes = [vp, vp, u64, P64, ctypes.c_int64]
+        lib.phprng_server_release.argtypes = [vp, P64, u64]
+        lib.phprng_server_stats_get.argtypes = [vp, ctypes.POINTER(phprng_server_stats)]
+        lib.phprng_server_destroy.argtypes = [vp]
+        lib.phprng_server_copy.argtypes = [vp, u64, vp, vp]
         _lib = lib
         return lib
 
@@ -300,6 +336,68 @@ def phprng_generate_batch(ctx, reqs, c_base=None, r_base=None, stream=None):
     ptr, n, _keep = _requests(reqs)
     _check(_load().phprng_generate_batch(ctx, ptr, n, _ptr(c_base), _ptr(r_base),
                                          _stream(stream)), ctx)
+
+
+def phprng_clock_ns():
+    return int(_load().phprng_clock_ns())
+
+
+def phprng_server_create(ctx, output_budget_bytes, max_batch=0, inflight=0, tile=0, want_c=0):
+    cfg = phprng_server_config(int(output_budget_bytes), int(max_batch), int(inflight), int(tile),
+                               int(want_c))
+    out = ctypes.c_void_p()
+    _check(_load().phprng_server_create(ctx, ctypes.byref(cfg), ctypes.byref(out)), ctx)
+    return out.value
+
+
+def _u64arr(x):
+    return np.ascontiguousarray(np.asarray(x, dtype=np.uint64).reshape(-1))
+
+
+def phprng_server_submit(srv, inst, length, tag=None, arrival_ns=None):
+    """Submits requests (arrays or scalars); returns the id of the first."""
+    P64 = ctypes.POINTER(ctypes.c_uint64)
+    inst, length = _u64arr(inst), _u64arr(length)
+    tag = _u64arr(tag) if tag is not None else None
+    arr = (np.ascontiguousarray(np.asarray(arrival_ns, dtype=np.int64).reshape(-1))
+           if arrival_ns is not None else None)
+    first = ctypes.c_uint64()
+    _check(_load().phprng_server_submit(
+        srv, inst.ctypes.data_as(P64), length.ctypes.data_as(P64),
+        tag.ctypes.data_as(P64) if tag is not None else None,
+        arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)) if arr is not None else None,
+        inst.size, ctypes.byref(first)))
+    return first.value
+
+
+def phprng_server_poll(srv, max_items=4096, timeout_ns=0):
+    """Returns a COMPLETION_DTYPE array of finished requests."""
+    out = np.zeros(int(max_items), dtype=COMPLETION_DTYPE)
+    n = ctypes.c_uint64()
+    _check(_load().phprng_server_poll(srv, out.ctypes.data, int(max_items), ctypes.byref(n),
+                                      int(timeout_ns)))
+    return out[:n.value]
+
+
+def phprng_server_release(srv, ids):
+    ids = _u64arr(ids)
+    _check(_load().phprng_server_release(srv, ids.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                         ids.size))
+
+
+def phprng_server_copy(srv, req_id, r_dst=None, c_dst=None):
+    _check(_load().phprng_server_copy(srv, int(req_id), _ptr(r_dst), _ptr(c_dst)))
+
+
+def phprng_server_stats_get(srv):
+    st = phprng_server_stats()
+    _check(_load().phprng_server_stats_get(srv, ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in phprng_server_stats._fields_}
+
+
+def phprng_server_destroy(srv):
+    if srv:
+        _check(_load().phprng_server_destroy(srv))
 
 
 def phprng_microbench(which, stream=None):

@@ -14,59 +14,22 @@
 #include <string>
 #include <vector>
 
-#include "internal.h"
-
-#define PH_API extern "C" __attribute__((visibility("default")))
+#include "ctx.h"
 
 using namespace phprng;
 
-struct phprng_ctx {
-    int width = 32;
-    uint64_t count = 0;
-    uint32_t flags = 0;
-    int device = 0;
-    uint64_t p = 0, a = 0;
-    bool any32 = false, any64 = false;
-    std::vector<phprng_instance> host_inst;
-    std::vector<uint8_t> wide;
-    DevInst *d_inst = nullptr;
-    ExpProg *d_prog = nullptr;        // exponent programs, one per instance
-    uint64_t *d_state = nullptr;      // 4 * count: m | s | c | pos
-    DevState st{};
-    SkipConst sk32{}, sk64{}, sk32_4{}, sk32_2{};
-    std::vector<uint64_t> pos_host;   // host mirror of the stream positions
-    // skip-ahead: cycle positions of the seeds and the prefix table (lazy)
-    uint64_t *d_L0 = nullptr, *d_m0 = nullptr, *d_T = nullptr;
-    uint32_t *d_P = nullptr;
-    SkipTable tbl{};
-    bool skip_ready = false;
-    // host-output staging
-    void *stage[2] = {nullptr, nullptr};
-    size_t stage_bytes = 0;
-    cudaStream_t copy_stream = nullptr;
-    cudaEvent_t ev_done[2] = {nullptr, nullptr}, ev_copied[2] = {nullptr, nullptr};
-    std::string err;
-    std::mutex mu;
-};
-
 static thread_local std::string g_err;
 
-static int fail(phprng_ctx *ctx, int code, const std::string &msg)
+int fail(phprng_ctx *ctx, int code, const std::string &msg)
 {
     if (ctx) ctx->err = msg; else g_err = msg;
     return code;
 }
 
-static int cuda_fail(phprng_ctx *ctx, cudaError_t e, const char *what)
+int cuda_fail(phprng_ctx *ctx, cudaError_t e, const char *what)
 {
     return fail(ctx, PHPRNG_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
-
-#define CU(ctx, call)                                                   \
-    do {                                                                \
-        cudaError_t e_ = (call);                                        \
-        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);      \
-    } while (0)
 
 static void free_ctx(phprng_ctx *c)
 {
@@ -232,6 +195,8 @@ PH_API int phprng_create_seeded(phprng_ctx **out, int width, uint64_t count, uin
 
 PH_API int phprng_destroy(phprng_ctx *ctx)
 {
+    if (ctx && ctx->serving)
+        return fail(ctx, PHPRNG_EINVAL, "phprng_destroy: destroy the server first");
     free_ctx(ctx);
     return PHPRNG_OK;
 }
@@ -359,6 +324,7 @@ PH_API int phprng_generate(phprng_ctx *ctx, uint64_t first, uint64_t num_inst,
 {
     if (!ctx) return fail(nullptr, PHPRNG_EINVAL, "phprng_generate: ctx is NULL");
     std::lock_guard<std::mutex> lk(ctx->mu);
+    if (ctx->serving) return fail(ctx, PHPRNG_EINVAL, "phprng_generate: a server owns the context");
     if (first > ctx->count || num_inst > ctx->count - first)
         return fail(ctx, PHPRNG_EINVAL, "phprng_generate: instance range outside the table");
     if (num_inst == 0 || per_inst == 0) return PHPRNG_OK;
@@ -444,7 +410,7 @@ PH_API int phprng_get_state(phprng_ctx *ctx, uint64_t inst, phprng_instance *sta
 
 // Builds, once per context, the cycle positions L0 of the seeds (discrete
 // logs on the host) and the prefix table of the skip cycle (on the device).
-static int ensure_skip(phprng_ctx *c, cudaStream_t s)
+int ensure_skip(phprng_ctx *c, cudaStream_t s)
 {
     if (c->skip_ready) return PHPRNG_OK;
     std::vector<uint64_t> s0(c->count), L0(c->count), m0(c->count);
@@ -489,6 +455,7 @@ PH_API int phprng_skip(phprng_ctx *ctx, const uint64_t *inst_ids, const uint64_t
 {
     if (!ctx) return fail(nullptr, PHPRNG_EINVAL, "phprng_skip: ctx is NULL");
     std::lock_guard<std::mutex> lk(ctx->mu);
+    if (ctx->serving) return fail(ctx, PHPRNG_EINVAL, "phprng_skip: a server owns the context");
     if (cnt == 0) return PHPRNG_OK;
     if (!inst_ids || !k) return fail(ctx, PHPRNG_EINVAL, "phprng_skip: NULL request arrays");
     // merge repeated instances (their skips add) and check for overflow
@@ -646,6 +613,7 @@ PH_API int phprng_plan_create(phprng_ctx *ctx, const phprng_request *reqs, uint6
     *out = nullptr;
     if (!ctx) return fail(nullptr, PHPRNG_EINVAL, "phprng_plan_create: ctx is NULL");
     std::lock_guard<std::mutex> lk(ctx->mu);
+    if (ctx->serving) return fail(ctx, PHPRNG_EINVAL, "phprng_plan_create: a server owns the context");
     if (nreq && !reqs) return fail(ctx, PHPRNG_EINVAL, "phprng_plan_create: reqs is NULL");
     if (tile == 0) tile = kDefaultTile;
     if (tile > (1u << 30)) return fail(ctx, PHPRNG_EINVAL, "phprng_plan_create: tile above 2^30");
@@ -667,6 +635,7 @@ PH_API int phprng_plan_create(phprng_ctx *ctx, const phprng_request *reqs, uint6
                 return fail(ctx, PHPRNG_EINVAL, "phprng_plan_create: request " + std::to_string(j) +
                                                     ": instance out of range");
             }
+            if (r.len == 0) continue;                        // ignored entirely
             const uint64_t start = r.offset == PHPRNG_CONTINUE ? cursor[r.inst] : r.offset;
             if (r.len > UINT64_MAX - start || r.len > UINT64_MAX - r.c_off ||
                 r.len > UINT64_MAX - r.r_off) {
@@ -675,7 +644,6 @@ PH_API int phprng_plan_create(phprng_ctx *ctx, const phprng_request *reqs, uint6
                                                     ": position or offset overflow");
             }
             cursor[r.inst] = start + r.len;
-            if (r.len == 0) continue;
             lastreq[r.inst] = (int64_t)pl->reqs.size();
             pl->reqs.push_back({r.inst, start, r.len, r.c_off, r.r_off, false});
         }

@@ -1,0 +1,61 @@
+// ctx.h -- the context object behind the opaque phprng_ctx handle, shared by
+// the C ABI (capi.cpp) and the serving loop (serve.cpp).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+#define PH_API extern "C" __attribute__((visibility("default")))
+
+using phprng::DevInst;
+using phprng::DevState;
+using phprng::ExpProg;
+using phprng::SkipConst;
+using phprng::SkipTable;
+
+struct phprng_ctx {
+    int width = 32;
+    uint64_t count = 0;
+    uint32_t flags = 0;
+    int device = 0;
+    uint64_t p = 0, a = 0;
+    bool any32 = false, any64 = false;
+    std::vector<phprng_instance> host_inst;
+    std::vector<uint8_t> wide;
+    DevInst *d_inst = nullptr;
+    ExpProg *d_prog = nullptr;        // exponent programs, one per instance
+    uint64_t *d_state = nullptr;      // 4 * count: m | s | c | pos
+    DevState st{};
+    SkipConst sk32{}, sk64{}, sk32_4{}, sk32_2{};
+    std::vector<uint64_t> pos_host;   // host mirror of the stream positions
+    // skip-ahead: cycle positions of the seeds and the prefix table (lazy)
+    uint64_t *d_L0 = nullptr, *d_m0 = nullptr, *d_T = nullptr;
+    uint32_t *d_P = nullptr;
+    SkipTable tbl{};
+    bool skip_ready = false;
+    // host-output staging
+    void *stage[2] = {nullptr, nullptr};
+    size_t stage_bytes = 0;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_done[2] = {nullptr, nullptr}, ev_copied[2] = {nullptr, nullptr};
+    bool serving = false;             // a phprng_server owns the context
+    std::string err;
+    std::mutex mu;
+};
+
+
+// Records the message for phprng_last_error and returns code.
+int fail(phprng_ctx *ctx, int code, const std::string &msg);
+int cuda_fail(phprng_ctx *ctx, cudaError_t e, const char *what);
+// Builds the seeds' cycle positions and the skip prefix table once.
+int ensure_skip(phprng_ctx *c, cudaStream_t s);
+
+#define CU(ctx, call)                                                   \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);      \
+    } while (0)

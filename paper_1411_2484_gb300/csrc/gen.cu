@@ -21,9 +21,12 @@ namespace phprng {
 #ifndef PH_MINB32
 #define PH_MINB32 1
 #endif
+#ifndef PH_WPB
+#define PH_WPB 8
+#endif
 static constexpr int kNPT = PH_NPT32;     // numbers per lane per group (32-bit path)
 static constexpr int kNPT64 = PH_NPT64;   // numbers per lane per group (64-bit path)
-static constexpr int kWarpsPerBlock = 8;
+static constexpr int kWarpsPerBlock = PH_WPB;
 static constexpr unsigned kFull = kFullMask;
 
 int gen_npt(int wide) { return wide ? kNPT64 : kNPT; }
