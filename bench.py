@@ -23,6 +23,8 @@ import subprocess
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -42,6 +44,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=64)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--modes", default="fused,wide64,batched,served",
+                    help="comma-separated extra measurements after the headline, or 'none'")
     return ap.parse_args()
 
 
@@ -147,6 +151,164 @@ def cpu_baseline(inst, per_inst, target_s=12.0):
     return {"value": count * per_inst / dt, "unit": "PRNs/s", "cores": cores, "kind": "oracle",
             "sample": "first %d of the %d instances x %d numbers (R stored), %.1f s"
                       % (count, len(rows), per_inst, dt)}
+
+
+def muls_per_number(e, wide):
+    """32-bit product halves per number (SURVEY-style algorithmic count): the
+    binary method's squarings and multiplications of Eq. 9c plus the skip
+    product of Eq. 9a; 4 halves per 32-bit Montgomery product, 20 per 64-bit
+    one (full 128-bit product 8, low word of q 4, high word of q n 8)."""
+    e = int(e)
+    mulmods = (e.bit_length() - 1) + (bin(e).count("1") - 1)
+    return 20 * mulmods + 4 if wide else 4 * (mulmods + 1)
+
+
+def timed(torch, stream, fn, steps, warmup=2):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def mode_fused(ph, torch, ctx, N, per, stream, steps):
+    """The same workload in fused mode: per-stream statistics, no R stores."""
+    sb = torch.empty(N * ph.STATS_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    ms = timed(torch, stream, lambda: ph.phprng_generate(ctx, 0, N, per, None, None, sb, stream),
+               steps)
+    return {"value": N * per / ms * 1e3, "unit": "PRNs/s", "ms_per_call": ms,
+            "workload": "plain32 65,536 x 4,096, statistics only (72 MB/call)"}
+
+
+def mode_wide64(ph, torch, stream, peak):
+    from paper_1411_2484_gb300 import workloads
+    inst = workloads.workload_instances("wide64_4096x2^20")
+    N, per = 4096, 1 << 16
+    ctx = ph.phprng_create(64, inst, ph.PHPRNG_REQUIRE_SAFE_PRIME, stream)
+    try:
+        r = torch.empty(N * per, dtype=torch.float64, device="cuda")
+        ms = timed(torch, stream, lambda: ph.phprng_generate(ctx, 0, N, per, None, r, None, stream),
+                   4, warmup=1)
+    finally:
+        ph.phprng_destroy(ctx)
+    muls = sum(muls_per_number(e, True) for e in inst["e"]) * per
+    achieved = muls / (ms * 1e-3) / 1e12
+    return {"value": N * per / ms * 1e3, "unit": "PRNs/s", "ms_per_call": ms,
+            "workload": "4,096 64-bit safe primes x 2^16 numbers per call (R, 2 GiB)",
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T mul32/s",
+                         "frac": achieved / peak}}
+
+
+def mode_batched(ph, torch, stream):
+    """20,000 instances (16,000 32-bit, 4,000 64-bit), log-uniform lengths in
+    [1, 2^20], offsets in [0, 2^40): one graph-replayed persistent launch
+    (autotuned) against one skip+generate launch pair per request."""
+    from paper_1411_2484_gb300 import workloads
+    w = workloads.WORKLOADS["batched_20000_mixed"]
+    i32 = ph.phprng_draw_instances(32, w["instances32"], w["seed"], ph.PHPRNG_REQUIRE_SAFE_PRIME)
+    i64 = ph.phprng_draw_instances(64, w["instances64"], w["seed"] + 1, ph.PHPRNG_REQUIRE_SAFE_PRIME)
+    inst = workloads.concat_instances(i32, i64)
+    reqs = workloads.batched_requests(w["instances32"], w["instances64"], w["max_len"],
+                                      w["max_offset"], w["seed"] + 2)
+    total = int(reqs["len"].sum())
+    ctx = ph.phprng_create(0, inst, 0, stream)
+    out = {}
+    try:
+        r = torch.empty(total, dtype=torch.float64, device="cuda")
+        plan = ph.phprng_plan_create(ctx, reqs, 0, stream)
+        try:
+            tune = ph.phprng_plan_autotune(plan, None, r, stream, ctx=ctx)
+            ms = timed(torch, stream, lambda: ph.phprng_plan_launch_graph(plan, None, r, stream,
+                                                                          ctx=ctx), 5)
+        finally:
+            ph.phprng_plan_destroy(plan)
+        out = {"value": total / ms * 1e3, "unit": "PRNs/s", "ms_per_launch": ms,
+               "numbers": total, "requests": len(reqs), "tuning": tune,
+               "latency_ms": {"p50": ms, "p99": ms,
+                              "note": "all requests are submitted together and complete "
+                                      "within the one launch"}}
+    finally:
+        ph.phprng_destroy(ctx)
+    # one launch per request (skip to the offset, then generate), first 300 requests
+    ctx = ph.phprng_create(0, inst, 0, stream)
+    try:
+        k = 300
+        sub = reqs[:k]
+        r = torch.empty(int(sub["len"].max()), dtype=torch.float64, device="cuda")
+        done = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for (i, off, ln, _, _) in sub:
+            ph.phprng_skip(ctx, [int(i)], [int(off)], stream)
+            ph.phprng_generate(ctx, int(i), 1, int(ln), None, r, None, stream)
+            torch.cuda.synchronize()
+            done.append(time.perf_counter() - t0)
+        dt = time.perf_counter() - t0
+        lat = np.array(done) * 1e3
+        out["per_instance_launches"] = {
+            "value": float(sub["len"].sum()) / dt, "unit": "PRNs/s", "requests": k,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "note": "first 300 requests, skip + generate per request, issued back to back"}
+    finally:
+        ph.phprng_destroy(ctx)
+    return out
+
+
+def mode_served(ph, torch, duration_s=10.0, warm_s=1.0, rate=50000.0):
+    """1,000,000 32-bit streams, open-loop Poisson arrivals at 50k requests/s,
+    sizes min(round(lognormal(ln 4096, 2)), 2^22), admission bounded by 16 GiB
+    of outputs; PRNs/s and p50/p99 latency from arrival to completion."""
+    rng = np.random.default_rng(4096)
+    ctx = ph.phprng_create_seeded(32, 1_000_000, 0x5EED0004, ph.PHPRNG_REQUIRE_SAFE_PRIME)
+    srv = None
+    try:
+        srv = ph.phprng_server_create(ctx, 16 << 30, max_batch=4096, inflight=4, tile=4096)
+        span = warm_s + duration_s
+        n = int(rate * span * 1.05) + 100
+        gaps = rng.exponential(1.0 / rate, n)
+        t = np.cumsum(gaps)
+        t = t[t < span]
+        n = t.size
+        sizes = np.minimum(np.maximum(np.round(rng.lognormal(np.log(4096), 2.0, n)), 1),
+                           1 << 22).astype(np.int64)
+        streams = rng.integers(0, 1_000_000, n)
+        t0 = ph.phprng_clock_ns() + 200_000_000
+        arrivals = t0 + (t * 1e9).astype(np.int64)
+        ph.phprng_server_submit(srv, streams, sizes, np.arange(n), arrivals)
+        lat = np.zeros(n, dtype=np.int64)
+        arr = np.zeros(n, dtype=np.int64)
+        got = 0
+        deadline = time.time() + span + 60
+        while got < n and time.time() < deadline:
+            comp = ph.phprng_server_poll(srv, 65536, 50_000_000)
+            if len(comp):
+                tags = comp["tag"].astype(np.int64)
+                lat[tags] = comp["done_ns"] - comp["arrival_ns"]
+                arr[tags] = comp["arrival_ns"]
+                got += len(comp)
+                ph.phprng_server_release(srv, comp["id"])
+        st = ph.phprng_server_stats_get(srv)
+    finally:
+        if srv:
+            ph.phprng_server_destroy(srv)
+        ph.phprng_destroy(ctx)
+    meas = (arrivals >= t0 + int(warm_s * 1e9))
+    l_ms = lat[meas] / 1e6
+    numbers = int(sizes[meas].sum())
+    return {"value": numbers / duration_s, "unit": "PRNs/s",
+            "requests": int(meas.sum()), "completed": int(got),
+            "latency_ms": {"p50": float(np.percentile(l_ms, 50)),
+                           "p99": float(np.percentile(l_ms, 99)),
+                           "max": float(l_ms.max())},
+            "offered_rate_req_s": rate, "batches": st["batches"],
+            "max_waiting": st["max_waiting"],
+            "workload": "1,000,000 32-bit streams, Poisson 50k req/s, lognormal(ln 4096, 2) "
+                        "sizes capped at 2^22, 16 GiB admission, R only"}
 
 
 def run_reference(args, rank):
@@ -282,6 +444,26 @@ def main():
     }
     if world == 1:
         out["cpu_baseline"] = cpu_baseline(inst, per)
+        modes = {}
+        wanted = [] if args.modes == "none" else args.modes.split(",")
+        for name, fn in (("fused", lambda: mode_fused(ph, torch, ctx2, N, per, stream, 8)),
+                         ("wide64", lambda: mode_wide64(ph, torch, stream, PEAK_TMULS)),
+                         ("batched", lambda: mode_batched(ph, torch, stream)),
+                         ("served", lambda: mode_served(ph, torch))):
+            if name not in wanted:
+                continue
+            try:
+                if name == "fused":
+                    ctx2 = ph.phprng_create(32, inst, ph.PHPRNG_REQUIRE_SAFE_PRIME, stream)
+                    try:
+                        modes[name] = fn()
+                    finally:
+                        ph.phprng_destroy(ctx2)
+                else:
+                    modes[name] = fn()
+            except Exception as exc:                   # a mode never hides the headline
+                modes[name] = {"error": repr(exc)[:300]}
+        out["modes"] = modes
     print(json.dumps(out), flush=True)
 
 

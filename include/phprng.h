@@ -167,7 +167,7 @@ typedef struct {
 typedef struct phprng_plan phprng_plan;   /* opaque, library-owned */
 
 /* Launch configuration of a plan: numbers per tile, numbers per lane per warp
- * group of the 32-bit path (2 or 4), resident blocks per SM (0 = as many as
+ * group of the 32-bit path (4 or 8), resident blocks per SM (0 = as many as
  * fit), and the time the autotuner measured for it (ms, 0 if never timed). */
 typedef struct {
     uint32_t tile;

@@ -29,7 +29,7 @@ __device__ __forceinline__ void run_tile32(const BatchArgs &a, const DevInst &P,
                                            const Tile &T, bool wb, bool vec_ok)
 {
     constexpr uint64_t G = 32 * NPT;
-    const SkipConst &sk = NPT == 4 ? a.sk32_4 : a.sk32_2;
+    const SkipConst &sk = NPT == 8 ? a.sk32_8 : a.sk32_4;
     uint32_t M = m;
     uint32_t sig = mont32(s, sk.lane[lane], sk.p, sk.pinv);
     CT *cdst = a.c_base ? (CT *)a.c_base + T.c_off : nullptr;
@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(256, PH_BATCH_MINB) batch_kernel(BatchArgs a)
         if (!wide)
             run_tile32<NPT32, CT>(a, P, a.prog[i], i, lane, (uint32_t)m, s, T, wb, vec_ok);
         else
-            run_tile64<2>(a, P, a.prog[i], i, lane, m, s, T, wb,
+            run_tile64<PH_NPT64>(a, P, a.prog[i], i, lane, m, s, T, wb,
                           a.vec_ok && (T.c_off % 2 == 0) && (T.r_off % 2 == 0));
     }
 }
@@ -124,10 +124,10 @@ int launch_batch(const BatchArgs &a, int npt32, int blocks_per_sm, void *stream,
 {
     if (a.ntiles == 0) return PHPRNG_OK;
     if (a.c_is_64)
-        return npt32 == 2 ? launch_one<2, uint64_t>(a, blocks_per_sm, stream, err)
-                          : launch_one<4, uint64_t>(a, blocks_per_sm, stream, err);
-    return npt32 == 2 ? launch_one<2, uint32_t>(a, blocks_per_sm, stream, err)
-                      : launch_one<4, uint32_t>(a, blocks_per_sm, stream, err);
+        return npt32 == 4 ? launch_one<4, uint64_t>(a, blocks_per_sm, stream, err)
+                          : launch_one<8, uint64_t>(a, blocks_per_sm, stream, err);
+    return npt32 == 4 ? launch_one<4, uint32_t>(a, blocks_per_sm, stream, err)
+                      : launch_one<8, uint32_t>(a, blocks_per_sm, stream, err);
 }
 
 int batch_max_blocks_per_sm(int npt32, int c_is_64)
@@ -135,10 +135,10 @@ int batch_max_blocks_per_sm(int npt32, int c_is_64)
     int maxb = 0;
     if (c_is_64)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &maxb, npt32 == 2 ? batch_kernel<2, uint64_t> : batch_kernel<4, uint64_t>, 256, 0);
+            &maxb, npt32 == 4 ? batch_kernel<4, uint64_t> : batch_kernel<8, uint64_t>, 256, 0);
     else
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &maxb, npt32 == 2 ? batch_kernel<2, uint32_t> : batch_kernel<4, uint32_t>, 256, 0);
+            &maxb, npt32 == 4 ? batch_kernel<4, uint32_t> : batch_kernel<8, uint32_t>, 256, 0);
     return maxb;
 }
 

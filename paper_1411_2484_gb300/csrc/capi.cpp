@@ -145,8 +145,8 @@ PH_API int phprng_create(phprng_ctx **out, int width, const phprng_instance *ins
     }
     c->sk32 = derive_skip(c->p, c->a, gen_npt(0));
     c->sk64 = derive_skip(c->p, c->a, gen_npt(1));
+    c->sk32_8 = derive_skip(c->p, c->a, 8);
     c->sk32_4 = derive_skip(c->p, c->a, 4);
-    c->sk32_2 = derive_skip(c->p, c->a, 2);
     cudaStream_t s = (cudaStream_t)cuda_stream;
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_inst, count * sizeof(DevInst));
@@ -593,8 +593,8 @@ static BatchArgs batch_args(phprng_plan *pl, void *c_base, double *r_base)
     a.m0 = c->d_m0;
     a.L0 = c->d_L0;
     a.tb = c->tbl;
+    a.sk32_8 = c->sk32_8;
     a.sk32_4 = c->sk32_4;
-    a.sk32_2 = c->sk32_2;
     a.sk64 = c->sk64;
     a.tiles = pl->d_tiles;
     a.ntiles = pl->ntiles;
@@ -622,7 +622,7 @@ PH_API int phprng_plan_create(phprng_ctx *ctx, const phprng_request *reqs, uint6
     phprng_plan *pl = new (std::nothrow) phprng_plan;
     if (!pl) return fail(ctx, PHPRNG_ENOMEM, "phprng_plan_create: host allocation failed");
     pl->ctx = ctx;
-    pl->tune.npt = 4;
+    pl->tune.npt = 8;
     pl->tune.blocks_per_sm = 0;
     try {
         std::vector<uint64_t> cursor(ctx->pos_host);
@@ -736,7 +736,7 @@ PH_API int phprng_plan_autotune(phprng_plan *plan, void *c_base, double *r_base,
     CU(c, cudaSetDevice(c->device));
     cudaStream_t s = (cudaStream_t)cuda_stream;
     const uint32_t tiles[] = {4096, 16384, 65536};
-    const int npts[] = {4, 2};
+    const int npts[] = {8, 4};
     cudaEvent_t e0, e1;
     CU(c, cudaEventCreate(&e0));
     CU(c, cudaEventCreate(&e1));

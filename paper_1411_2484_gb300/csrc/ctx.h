@@ -30,7 +30,7 @@ struct phprng_ctx {
     ExpProg *d_prog = nullptr;        // exponent programs, one per instance
     uint64_t *d_state = nullptr;      // 4 * count: m | s | c | pos
     DevState st{};
-    SkipConst sk32{}, sk64{}, sk32_4{}, sk32_2{};
+    SkipConst sk32{}, sk64{}, sk32_8{}, sk32_4{};
     std::vector<uint64_t> pos_host;   // host mirror of the stream positions
     // skip-ahead: cycle positions of the seeds and the prefix table (lazy)
     uint64_t *d_L0 = nullptr, *d_m0 = nullptr, *d_T = nullptr;

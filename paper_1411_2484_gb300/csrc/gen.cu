@@ -12,14 +12,8 @@
 
 namespace phprng {
 
-#ifndef PH_NPT32
-#define PH_NPT32 4
-#endif
-#ifndef PH_NPT64
-#define PH_NPT64 2
-#endif
 #ifndef PH_MINB32
-#define PH_MINB32 1
+#define PH_MINB32 2
 #endif
 #ifndef PH_WPB
 #define PH_WPB 8

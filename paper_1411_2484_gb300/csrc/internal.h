@@ -9,6 +9,15 @@
 #include "../../include/phprng.h"
 #include "arith.cuh"
 
+// Numbers per lane per warp group of the 32-bit and 64-bit generators (the
+// unit of instruction-level parallelism of a lane; tuned on GB300: 8 and 4).
+#ifndef PH_NPT32
+#define PH_NPT32 8
+#endif
+#ifndef PH_NPT64
+#define PH_NPT64 4
+#endif
+
 namespace phprng {
 
 // One instance as the kernels read it: 64 bytes, read-only on the device.
@@ -101,7 +110,7 @@ struct BatchArgs {
     DevState st;
     const uint64_t *m0, *L0;        // seed message and the seed skip's cycle position
     SkipTable tb;
-    SkipConst sk32_4, sk32_2, sk64; // lane constants for NPT = 4, 2 (32-bit) and 2 (64-bit)
+    SkipConst sk32_8, sk32_4, sk64; // lane constants for NPT = 8, 4 (32-bit), PH_NPT64 (64-bit)
     const Tile *tiles;
     uint64_t ntiles;
     unsigned long long *counter;    // tile queue head, zeroed before each launch

@@ -173,8 +173,8 @@ static int launch_slot(phprng_server *s, Slot &sl)
     a.m0 = c->d_m0;
     a.L0 = c->d_L0;
     a.tb = c->tbl;
+    a.sk32_8 = c->sk32_8;
     a.sk32_4 = c->sk32_4;
-    a.sk32_2 = c->sk32_2;
     a.sk64 = c->sk64;
     a.tiles = sl.d_tiles;
     a.ntiles = nt;
@@ -184,7 +184,7 @@ static int launch_slot(phprng_server *s, Slot &sl)
     a.c_is_64 = c->width != 32;
     a.vec_ok = 1;
     std::string err;
-    int rc = launch_batch(a, 4, 0, sl.stream, &err);
+    int rc = launch_batch(a, 8, 0, sl.stream, &err);
     if (rc == PHPRNG_OK) {
         e = cudaEventRecord(sl.ev, sl.stream);
         if (e != cudaSuccess) {
