@@ -141,6 +141,26 @@ const char *phprng_status_string(int status);
 int phprng_generate(phprng_ctx *ctx, uint64_t first, uint64_t num_inst, uint64_t per_inst,
                     void *c_out, double *r_out, phprng_stats *stats_out, void *cuda_stream);
 
+/* The fused-statistics call of phprng_generate (c_out = r_out = NULL) for
+ * callers that must not allocate GPU memory: a process whose caching
+ * allocator already holds the device's memory, a latency-critical loop where
+ * an allocation would synchronise the device, or code that may only allocate
+ * at start-up.  The paper has no counterpart; it is a property of this
+ * library.  It allocates and frees no device memory (nor host memory when it
+ * succeeds): its only scratch, the ciphertext rows that pair instances
+ * across thread blocks, lives in a fixed array of 2^20 uint32 words (4 MiB)
+ * that every device holds while the library is loaded.  Limit:
+ * 2 * ceil(num_inst/8) * per_inst <= 2^20, else PHPRNG_EINVAL naming the
+ * limit.  stats_out must be device memory (num_inst phprng_stats).  The first
+ * call on a device looks up the array's device address once (make that
+ * first call before any CUDA stream capture).  All calls share the array and
+ * leave their rows in it; every row is fully written before it is read, so
+ * nothing needs clearing, but calls that overlap on the GPU (unordered
+ * streams) race on it.  Results, state updates and errors are otherwise
+ * those of phprng_generate with stats_out. */
+int phprng_generate_stats_noalloc(phprng_ctx *ctx, uint64_t first, uint64_t num_inst,
+                                  uint64_t per_inst, phprng_stats *stats_out, void *cuda_stream);
+
 /* Advances instance inst_ids[i] by k[i] positions without producing output,
  * by the closed form Eq. 7 (k = q(p-1) + r: s' = s a^r mod p and
  * m' = m + q p(p-1)/2 + sum_{j=1..r} (s a^j mod p) mod n), with the sum read

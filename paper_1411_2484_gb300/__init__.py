@@ -41,7 +41,7 @@ EXPORTED = [
     "phprng_plan_autotune", "phprng_plan_tuning", "phprng_plan_destroy", "phprng_generate_batch",
     "phprng_clock_ns", "phprng_server_create", "phprng_server_submit", "phprng_server_poll",
     "phprng_server_release", "phprng_server_stats_get", "phprng_server_destroy",
-    "phprng_server_copy",
+    "phprng_server_copy", "phprng_generate_stats_noalloc",
 ]
 PHPRNG_CONTINUE = (1 << 64) - 1
 
@@ -130,6 +130,7 @@ def _load():
         lib.phprng_status_string.argtypes = [i32]
         lib.phprng_status_string.restype = ctypes.c_char_p
         lib.phprng_generate.argtypes = [vp, u64, u64, u64, vp, vp, vp, vp]
+        lib.phprng_generate_stats_noalloc.argtypes = [vp, u64, u64, u64, vp, vp]
         lib.phprng_skip.argtypes = [vp, P64, P64, u64, vp]
         lib.phprng_get_state.argtypes = [vp, u64, P_inst, P64, P64, vp]
         lib.phprng_is_prime.argtypes = [u64]
@@ -236,6 +237,13 @@ def phprng_generate(ctx, first, num_inst, per_inst, c_out=None, r_out=None, stat
                     stream=None):
     _check(_load().phprng_generate(ctx, int(first), int(num_inst), int(per_inst), _ptr(c_out),
                                    _ptr(r_out), _ptr(stats_out), _stream(stream)), ctx)
+
+
+def phprng_generate_stats_noalloc(ctx, first, num_inst, per_inst, stats_out, stream=None):
+    """Fused statistics without any GPU allocation (fixed 4 MiB scratch);
+    for callers that cannot allocate device memory at the call site."""
+    _check(_load().phprng_generate_stats_noalloc(ctx, int(first), int(num_inst), int(per_inst),
+                                                 _ptr(stats_out), _stream(stream)), ctx)
 
 
 def phprng_skip(ctx, inst_ids, k, stream=None):

@@ -387,6 +387,49 @@ PH_API int phprng_generate(phprng_ctx *ctx, uint64_t first, uint64_t num_inst,
     return rc;
 }
 
+PH_API int phprng_generate_stats_noalloc(phprng_ctx *ctx, uint64_t first, uint64_t num_inst,
+                                        uint64_t per_inst, phprng_stats *stats_out,
+                                        void *cuda_stream)
+{
+    if (!ctx) return fail(nullptr, PHPRNG_EINVAL, "phprng_generate_stats_noalloc: ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (ctx->serving)
+        return fail(ctx, PHPRNG_EINVAL, "phprng_generate_stats_noalloc: a server owns the context");
+    if (first > ctx->count || num_inst > ctx->count - first)
+        return fail(ctx, PHPRNG_EINVAL, "phprng_generate_stats_noalloc: instance range outside the table");
+    if (ctx->any64)
+        return fail(ctx, PHPRNG_EINVAL,
+                    "phprng_generate_stats_noalloc: statistics are defined for 32-bit moduli only");
+    if (per_inst >= (1ull << 31))
+        return fail(ctx, PHPRNG_EINVAL, "phprng_generate_stats_noalloc: per_inst must be below 2^31");
+    if (num_inst == 0 || per_inst == 0) return PHPRNG_OK;
+    if (!stats_out || (uintptr_t)stats_out % 8)
+        return fail(ctx, PHPRNG_EINVAL, "phprng_generate_stats_noalloc: stats_out NULL or misaligned");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    if (pointer_kind(stats_out) != 1)
+        return fail(ctx, PHPRNG_EINVAL, "phprng_generate_stats_noalloc: stats_out must be device memory");
+    GenArgs g;
+    g.inst = ctx->d_inst;
+    g.prog = ctx->d_prog;
+    g.st = ctx->st;
+    g.sk = ctx->sk32;
+    g.first = first;
+    g.num = num_inst;
+    g.per_inst = per_inst;
+    g.c_out = nullptr;
+    g.r_out = nullptr;
+    g.stats = stats_out;
+    g.edge = nullptr;
+    g.c_is_64 = ctx->width != 32;
+    g.vec_ok = 1;
+    std::string err;
+    int rc = launch_gen32_stats_fixed(g, ctx->device, cuda_stream, &err);
+    if (rc != PHPRNG_OK) return fail(ctx, rc, "phprng_generate_stats_noalloc: " + err);
+    for (uint64_t i = first; i < first + num_inst; ++i) ctx->pos_host[i] += per_inst;
+    return PHPRNG_OK;
+}
+
 PH_API int phprng_get_state(phprng_ctx *ctx, uint64_t inst, phprng_instance *state_out,
                             uint64_t *pos_out, uint64_t *c_out, void *cuda_stream)
 {

@@ -8,6 +8,8 @@
 // lane that owns the call's last number writes the state back (m, s, c, pos).
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "gencore.cuh"
 
 namespace phprng {
@@ -258,6 +260,65 @@ int launch_gen64(const GenArgs &a, void *stream, std::string *err)
     gen64_kernel<kNPT64><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, (cudaStream_t)stream>>>(
         a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, (uint64_t *)a.c_out, a.r_out, a.vec_ok);
     return check_launch(err, "gen64_kernel launch");
+}
+
+// ---- fused statistics with fixed scratch ------------------------------------
+// Some callers cannot allocate GPU memory at the point where they want the
+// statistics: a caching allocator may already own all device memory, the call
+// may sit on a latency-critical path where an allocation would synchronise the
+// device, or the code may run where allocation is forbidden after start-up.
+// For them the statistics call can use this fixed array for its only scratch
+// (the ciphertext rows that pair instances across thread blocks) instead of a
+// stream-ordered allocation.  The array lives for as long as the library is
+// loaded, on every device that loads it.  Every call shares it and leaves its
+// rows behind; each row is written in full before it is read, so nothing needs
+// clearing, but two such calls that overlap on the GPU (different streams,
+// not ordered) race on it.
+static constexpr uint64_t kFixedEdgeWords = 1ull << 20;      // 4 MiB of uint32
+static __device__ __align__(256) uint32_t g_fixed_edge[kFixedEdgeWords];
+
+static uint32_t *g_fixed_edge_addr[64];                     // device address, per device
+static std::mutex g_fixed_edge_mu;
+
+uint64_t gen32_fixed_edge_words() { return kFixedEdgeWords; }
+
+// The host name g_fixed_edge is only a stand-in for the device array: its
+// device address is looked up once per device, with that device current.
+static int fixed_edge_address(int dev, uint32_t **out, std::string *err)
+{
+    if (dev < 0 || dev >= 64) {
+        *err = "device index above 63";
+        return PHPRNG_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(g_fixed_edge_mu);
+    if (!g_fixed_edge_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_fixed_edge);
+        if (e != cudaSuccess) {
+            *err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+            return PHPRNG_ECUDA;
+        }
+        g_fixed_edge_addr[dev] = (uint32_t *)p;
+    }
+    *out = g_fixed_edge_addr[dev];
+    return PHPRNG_OK;
+}
+
+int launch_gen32_stats_fixed(const GenArgs &a, int dev, void *stream, std::string *err)
+{
+    if (a.num == 0 || a.per_inst == 0) return PHPRNG_OK;
+    if (gen32_edge_words(a.num, a.per_inst) > kFixedEdgeWords) {
+        *err = "statistics scratch of " + std::to_string(gen32_edge_words(a.num, a.per_inst)) +
+               " words exceeds the fixed 1,048,576 words (2 x ceil(num_inst/8) x per_inst must "
+               "not exceed 2^20)";
+        return PHPRNG_EINVAL;
+    }
+    uint32_t *edge = nullptr;
+    int rc = fixed_edge_address(dev, &edge, err);
+    if (rc != PHPRNG_OK) return rc;
+    GenArgs b = a;
+    b.edge = edge;
+    return launch_gen32(b, stream, err);
 }
 
 }  // namespace phprng
