@@ -154,7 +154,42 @@ struct alignas(16) ExpProg {
 PH_HD uint32_t mont(uint32_t a, uint32_t b, uint32_t n, uint32_t ninv) { return mont32(a, b, n, ninv); }
 PH_HD uint64_t mont(uint64_t a, uint64_t b, uint64_t n, uint64_t ninv) { return mont64(a, b, n, ninv); }
 
-// x_u = MP(x_u, y_u) for every u.
+// x_u = MP(x_u, y_u) for every u.  The 32-bit form is written phase by phase
+// across the NPT independent products (all full products, then all q, then
+// all high halves, then the corrections), so that consecutive multiplies never
+// wait on each other.
+#ifndef PH_MONT_INTERLEAVE
+#define PH_MONT_INTERLEAVE 1
+#endif
+#ifndef PH_SQ_SWITCH
+#define PH_SQ_SWITCH 0
+#endif
+template <int NPT>
+PH_HD void mont32_vec(uint32_t (&x)[NPT], const uint32_t (&y)[NPT], uint32_t n, uint32_t ninv)
+{
+#if PH_MONT_INTERLEAVE
+    uint32_t lo[NPT], hi[NPT];
+#pragma unroll
+    for (int u = 0; u < NPT; ++u) {
+        const uint64_t T = (uint64_t)x[u] * y[u];
+        lo[u] = (uint32_t)T;
+        hi[u] = (uint32_t)(T >> 32);
+    }
+#pragma unroll
+    for (int u = 0; u < NPT; ++u) lo[u] *= ninv;                 // q
+#pragma unroll
+    for (int u = 0; u < NPT; ++u) lo[u] = umulhi32(lo[u], n);    // hi(q n)
+#pragma unroll
+    for (int u = 0; u < NPT; ++u) {
+        const uint32_t t = hi[u] - lo[u];
+        x[u] = hi[u] < lo[u] ? t + n : t;
+    }
+#else
+#pragma unroll
+    for (int u = 0; u < NPT; ++u) x[u] = mont32(x[u], y[u], n, ninv);
+#endif
+}
+
 template <int NPT, typename W>
 PH_HD void mont_vec(W (&x)[NPT], const W (&y)[NPT], W n, W ninv)
 {
@@ -162,11 +197,23 @@ PH_HD void mont_vec(W (&x)[NPT], const W (&y)[NPT], W n, W ninv)
     for (int u = 0; u < NPT; ++u) x[u] = mont(x[u], y[u], n, ninv);
 }
 
+template <int NPT>
+PH_HD void mont_vec(uint32_t (&x)[NPT], const uint32_t (&y)[NPT], uint32_t n, uint32_t ninv)
+{
+    mont32_vec<NPT>(x, y, n, ninv);
+}
+
 template <int NPT, typename W>
 PH_HD void mont_sqr_vec(W (&x)[NPT], W n, W ninv)
 {
 #pragma unroll
     for (int u = 0; u < NPT; ++u) x[u] = mont(x[u], x[u], n, ninv);
+}
+
+template <int NPT>
+PH_HD void mont_sqr_vec(uint32_t (&x)[NPT], uint32_t n, uint32_t ninv)
+{
+    mont32_vec<NPT>(x, x, n, ninv);
 }
 
 // c_u = m_u^e mod n for NPT messages by the exponent's program (Eq. 9c with
@@ -216,11 +263,26 @@ PH_HD void modexp_prog(W (&x)[NPT], const W (&m)[NPT], const ExpProg &pg, W n, W
     for (int k = 1; k < nent; ++k) {
         const int b = pg.ent[k];
         int sq = b & 63;
+#if PH_SQ_SWITCH
+        for (; sq >= 4; sq -= 4) {
+            mont_sqr_vec<NPT>(x, n, ninv);
+            mont_sqr_vec<NPT>(x, n, ninv);
+            mont_sqr_vec<NPT>(x, n, ninv);
+            mont_sqr_vec<NPT>(x, n, ninv);
+        }
+        switch (sq) {                                   // the remaining 0..3 squarings
+        case 3: mont_sqr_vec<NPT>(x, n, ninv); /* fall through */
+        case 2: mont_sqr_vec<NPT>(x, n, ninv); /* fall through */
+        case 1: mont_sqr_vec<NPT>(x, n, ninv); /* fall through */
+        default: break;
+        }
+#else
         for (; sq >= 2; sq -= 2) {
             mont_sqr_vec<NPT>(x, n, ninv);
             mont_sqr_vec<NPT>(x, n, ninv);
         }
         if (sq) mont_sqr_vec<NPT>(x, n, ninv);
+#endif
         switch (b >> 6) {
         case 0: mont_vec<NPT>(x, m, n, ninv); break;
         case 1: mont_vec<NPT>(x, t3, n, ninv); break;

@@ -42,12 +42,12 @@ static void free_ctx(phprng_ctx *c)
     cudaFree(c->d_m0);
     cudaFree(c->d_T);
     cudaFree(c->d_P);
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < phprng_ctx::kStages; ++k) {
         cudaFree(c->stage[k]);
         if (c->ev_done[k]) cudaEventDestroy(c->ev_done[k]);
         if (c->ev_copied[k]) cudaEventDestroy(c->ev_copied[k]);
+        if (c->copy_stream[k]) cudaStreamDestroy(c->copy_stream[k]);
     }
-    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     delete c;
 }
 
@@ -253,13 +253,14 @@ static int launch_range(phprng_ctx *c, uint64_t first, uint64_t num, uint64_t pe
 
 static int ensure_staging(phprng_ctx *c, size_t bytes)
 {
+    const int S = phprng_ctx::kStages;
     if (c->stage_bytes >= bytes) return PHPRNG_OK;
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < S; ++k) {
         cudaFree(c->stage[k]);
         c->stage[k] = nullptr;
     }
     c->stage_bytes = 0;
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < S; ++k) {
         cudaError_t e = cudaMalloc(&c->stage[k], bytes);
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -267,27 +268,31 @@ static int ensure_staging(phprng_ctx *c, size_t bytes)
         }
         if (!c->ev_done[k]) CU(c, cudaEventCreateWithFlags(&c->ev_done[k], cudaEventDisableTiming));
         if (!c->ev_copied[k]) CU(c, cudaEventCreateWithFlags(&c->ev_copied[k], cudaEventDisableTiming));
+        if (!c->copy_stream[k])
+            CU(c, cudaStreamCreateWithFlags(&c->copy_stream[k], cudaStreamNonBlocking));
     }
-    if (!c->copy_stream) CU(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
     c->stage_bytes = bytes;
     return PHPRNG_OK;
 }
 
-// Host outputs: generate into two device staging buffers in turn (blocks of
-// instances x numbers), copying each block back on the copy stream while the
-// next one is generated; returns once everything is on the host.
+// Host outputs: generate blocks (instances x numbers) into kStages device
+// staging buffers in turn and copy each block back on that buffer's own copy
+// stream while later blocks are generated (several copy engines can run at
+// once); a block that covers whole instances is one contiguous copy.  Returns
+// once everything is on the host.
 static int generate_to_host(phprng_ctx *c, uint64_t first, uint64_t num, uint64_t per_inst,
                             void *c_out, double *r_out, cudaStream_t s)
 {
+    const int S = phprng_ctx::kStages;
     const size_t csz = c->width == 32 ? 4 : 8;
     const size_t per_num = (c_out ? csz : 0) + (r_out ? 8 : 0);
-    const uint64_t cap = 1ull << 24;                      // numbers per block
+    const uint64_t cap = 1ull << 25;                      // numbers per block
     const uint64_t piece = std::min<uint64_t>(per_inst, cap);
     const uint64_t ninst = std::max<uint64_t>(1, std::min<uint64_t>(num, cap / piece));
     int rc = ensure_staging(c, (size_t)(ninst * piece * per_num + 256));
     if (rc != PHPRNG_OK) return rc;
     int k = 0;
-    bool used[2] = {false, false};
+    bool used[phprng_ctx::kStages] = {};
     for (uint64_t i0 = 0; i0 < num; i0 += ninst) {
         const uint64_t ni = std::min(ninst, num - i0);
         for (uint64_t j0 = 0; j0 < per_inst; j0 += piece) {
@@ -300,20 +305,32 @@ static int generate_to_host(phprng_ctx *c, uint64_t first, uint64_t num, uint64_
             rc = launch_range(c, first + i0, ni, pj, dc, dr, nullptr, s);
             if (rc != PHPRNG_OK) return rc;
             CU(c, cudaEventRecord(c->ev_done[k], s));
-            CU(c, cudaStreamWaitEvent(c->copy_stream, c->ev_done[k], 0));
-            if (c_out)
-                CU(c, cudaMemcpy2DAsync((char *)c_out + (i0 * per_inst + j0) * csz, per_inst * csz,
-                                        dc, pj * csz, pj * csz, ni, cudaMemcpyDeviceToHost,
-                                        c->copy_stream));
-            if (r_out)
-                CU(c, cudaMemcpy2DAsync(r_out + i0 * per_inst + j0, per_inst * 8, dr, pj * 8,
-                                        pj * 8, ni, cudaMemcpyDeviceToHost, c->copy_stream));
-            CU(c, cudaEventRecord(c->ev_copied[k], c->copy_stream));
+            cudaStream_t cs = c->copy_stream[k];
+            CU(c, cudaStreamWaitEvent(cs, c->ev_done[k], 0));
+            const bool whole = pj == per_inst;                  // rows are contiguous on the host
+            if (c_out) {
+                char *dst = (char *)c_out + (i0 * per_inst + j0) * csz;
+                if (whole)
+                    CU(c, cudaMemcpyAsync(dst, dc, ni * pj * csz, cudaMemcpyDeviceToHost, cs));
+                else
+                    CU(c, cudaMemcpy2DAsync(dst, per_inst * csz, dc, pj * csz, pj * csz, ni,
+                                            cudaMemcpyDeviceToHost, cs));
+            }
+            if (r_out) {
+                double *dst = r_out + i0 * per_inst + j0;
+                if (whole)
+                    CU(c, cudaMemcpyAsync(dst, dr, ni * pj * 8, cudaMemcpyDeviceToHost, cs));
+                else
+                    CU(c, cudaMemcpy2DAsync(dst, per_inst * 8, dr, pj * 8, pj * 8, ni,
+                                            cudaMemcpyDeviceToHost, cs));
+            }
+            CU(c, cudaEventRecord(c->ev_copied[k], cs));
             used[k] = true;
-            k ^= 1;
+            k = (k + 1) % S;
         }
     }
-    CU(c, cudaStreamSynchronize(c->copy_stream));
+    for (int j = 0; j < S; ++j)
+        if (used[j]) CU(c, cudaStreamSynchronize(c->copy_stream[j]));
     CU(c, cudaStreamSynchronize(s));
     return PHPRNG_OK;
 }

@@ -37,11 +37,12 @@ struct phprng_ctx {
     uint32_t *d_P = nullptr;
     SkipTable tbl{};
     bool skip_ready = false;
-    // host-output staging
-    void *stage[2] = {nullptr, nullptr};
+    // host-output staging: kStages device buffers, each with its own copy stream
+    static constexpr int kStages = 3;
+    void *stage[kStages] = {};
     size_t stage_bytes = 0;
-    cudaStream_t copy_stream = nullptr;
-    cudaEvent_t ev_done[2] = {nullptr, nullptr}, ev_copied[2] = {nullptr, nullptr};
+    cudaStream_t copy_stream[kStages] = {};
+    cudaEvent_t ev_done[kStages] = {}, ev_copied[kStages] = {};
     bool serving = false;             // a phprng_server owns the context
     std::string err;
     std::mutex mu;

@@ -46,12 +46,17 @@ __device__ __forceinline__ double u128d(u128 v) { return u128_to_double((uint64_
 // -- the same numbers, plus per-stream exact sums X = sum(c+1),
 // Y = sum(c+1)^2, Z = sum(c+1)(c'+1) with the next instance of the call, and
 // a 256-bin histogram of floor(256 R), reduced on chip.  In that mode the
-// block's warps walk their groups in lockstep: each group's ciphertexts go to
-// a double-buffered shared array so a warp can pair them with the next warp's;
-// the first and last warp of a block also leave their ciphertexts in `edge`
-// so stats_edge_kernel can pair instances that straddle two blocks.
+// block's warps walk their groups in lockstep (one block barrier per group):
+// each group's ciphertexts go to a double-buffered shared array so a warp can
+// pair them with the next warp's; the first and last warp of a block also
+// leave their ciphertexts in `edge` so stats_edge_kernel can pair instances
+// that straddle two blocks.
+#ifndef PH_MINB_STATS
+#define PH_MINB_STATS 2
+#endif
+
 template <int NPT, typename CT, bool STATS>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, STATS ? 1 : PH_MINB32)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, STATS ? PH_MINB_STATS : PH_MINB32)
 gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, DevState st,
              SkipConst sk, uint64_t first, uint64_t num, uint64_t per_inst,
              CT *__restrict__ c_out, double *__restrict__ r_out, int vec_ok,
@@ -76,7 +81,8 @@ gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
     double *rdst = r_out ? r_out + w * per_inst : nullptr;
 
     uint32_t *hist = smem + 2 * W * (32 * NPT) + warp * 256;
-    u128 X = 0, Y = 0, Z = 0;
+    uint64_t X = 0;      // < 2^63: per_inst < 2^31 numbers of at most 2^32 each
+    u128 Y = 0, Z = 0;
     const bool has_next = w + 1 < num;
     const bool pair_in_block = has_next && warp + 1 < W;
     if (STATS) {
@@ -113,6 +119,8 @@ gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
                         if (my0 + u < per_inst) row[my0 + u] = x[u];
                 }
             }
+            // every thread of the block runs the same number of groups, so
+            // all of them reach this barrier once per group
             __syncthreads();
             if (active && pair_in_block) {
                 const uint32_t *cn = cb + 32 * NPT;              // next warp, same buffer
@@ -124,7 +132,8 @@ gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
         }
     }
     if (STATS && active) {
-        X = warp_sum_u128(X);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) X += __shfl_xor_sync(kFull, X, off);
         Y = warp_sum_u128(Y);
         Z = warp_sum_u128(Z);
         __syncwarp();
@@ -132,12 +141,13 @@ gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
         for (int b = lane; b < 256; b += 32) o->hist[b] = hist[b];
         if (lane == 0) {
             const u128 N = per_inst, n1 = P.n + 1;
-            o->x_lo = (uint64_t)X; o->x_hi = (uint64_t)(X >> 64);
+            o->x_lo = X; o->x_hi = 0;
             o->y_lo = (uint64_t)Y; o->y_hi = (uint64_t)(Y >> 64);
             o->z_lo = (uint64_t)Z; o->z_hi = (uint64_t)(Z >> 64);
             o->count = per_inst;
             o->mean = __ddiv_rn(u128d(X), u128d(N * n1));
-            o->var = per_inst >= 2 ? __ddiv_rn(u128d(N * Y - X * X), u128d(N * (N - 1) * n1 * n1)) : 0.0;
+            o->var = per_inst >= 2 ? __ddiv_rn(u128d(N * Y - (u128)X * X), u128d(N * (N - 1) * n1 * n1))
+                                   : 0.0;
             if (pair_in_block) {
                 const u128 nn1 = (u128)inst[i + 1].n + 1;
                 o->corr = __ddiv_rn(u128d(Z), u128d(N * n1 * nn1));

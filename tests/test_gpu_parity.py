@@ -230,25 +230,29 @@ def test_64bit_small_and_mixed_context(ph, torch):
 
 
 def test_host_output_buffers(ph, torch):
-    """Host pointers (pageable numpy, pinned torch) stage through the device,
-    across more than one staging block (> 2^24 numbers)."""
-    inst = workloads.draw_instances(300, seed=31)
-    a = ph.phprng_create(32, inst, 0)
-    b = ph.phprng_create(32, inst, 0)
-    try:
-        per = 65536
-        c_h = np.empty(300 * per, dtype=np.uint32)
-        r_h = torch.empty(300 * per, dtype=torch.float64, pin_memory=True)
-        ph.phprng_generate(a, 0, 300, per, c_h, r_h, None)
-        c_d, r_d = generate(ph, torch, b, 32, 0, 300, per)
-        assert np.array_equal(c_h.reshape(300, per).astype(np.uint64), c_d)
-        assert np.array_equal(r_h.numpy().reshape(300, per).view(np.uint64), r_d.view(np.uint64))
-        orc = OracleStreams(inst)
-        cr, rr = orc.next(0, 8, per)
-        assert_same(c_d[:8], r_d[:8], cr, rr)
-    finally:
-        ph.phprng_destroy(a)
-        ph.phprng_destroy(b)
+    """Host pointers (pageable numpy, pinned torch) stage through the device:
+    several staging blocks of whole instances (> 2^25 numbers), and instances
+    longer than one block (split rows, strided copies)."""
+    for count, per in ((600, 65536), (2, (1 << 25) + 1000)):
+        inst = workloads.draw_instances(count, seed=31 + count)
+        a = ph.phprng_create(32, inst, 0)
+        b = ph.phprng_create(32, inst, 0)
+        try:
+            c_h = np.empty(count * per, dtype=np.uint32)
+            r_h = torch.empty(count * per, dtype=torch.float64, pin_memory=True)
+            ph.phprng_generate(a, 0, count, per, c_h, r_h, None)
+            c_d, r_d = generate(ph, torch, b, 32, 0, count, per)
+            assert np.array_equal(c_h.reshape(count, per).astype(np.uint64), c_d)
+            assert np.array_equal(r_h.numpy().reshape(count, per).view(np.uint64),
+                                  r_d.view(np.uint64))
+            orc = OracleStreams(inst)
+            k = min(count, 4)
+            cr, rr = orc.next(0, k, min(per, 70000))
+            assert_same(c_d[:k, :cr.shape[1]], r_d[:k, :cr.shape[1]], cr, rr)
+            del c_h, r_h, c_d, r_d
+        finally:
+            ph.phprng_destroy(a)
+            ph.phprng_destroy(b)
 
 
 def test_plain32_full_size_first_call_and_64_calls(ph, torch):
