@@ -278,8 +278,8 @@ static int ensure_staging(phprng_ctx *c, size_t bytes)
 // Host outputs: generate blocks (instances x numbers) into kStages device
 // staging buffers in turn and copy each block back on that buffer's own copy
 // stream while later blocks are generated (several copy engines can run at
-// once); a block that covers whole instances is one contiguous copy.  Returns
-// once everything is on the host.
+// once); every block is one contiguous copy.  Returns once everything is on
+// the host.
 static int generate_to_host(phprng_ctx *c, uint64_t first, uint64_t num, uint64_t per_inst,
                             void *c_out, double *r_out, cudaStream_t s)
 {
@@ -307,23 +307,14 @@ static int generate_to_host(phprng_ctx *c, uint64_t first, uint64_t num, uint64_
             CU(c, cudaEventRecord(c->ev_done[k], s));
             cudaStream_t cs = c->copy_stream[k];
             CU(c, cudaStreamWaitEvent(cs, c->ev_done[k], 0));
-            const bool whole = pj == per_inst;                  // rows are contiguous on the host
-            if (c_out) {
-                char *dst = (char *)c_out + (i0 * per_inst + j0) * csz;
-                if (whole)
-                    CU(c, cudaMemcpyAsync(dst, dc, ni * pj * csz, cudaMemcpyDeviceToHost, cs));
-                else
-                    CU(c, cudaMemcpy2DAsync(dst, per_inst * csz, dc, pj * csz, pj * csz, ni,
-                                            cudaMemcpyDeviceToHost, cs));
-            }
-            if (r_out) {
-                double *dst = r_out + i0 * per_inst + j0;
-                if (whole)
-                    CU(c, cudaMemcpyAsync(dst, dr, ni * pj * 8, cudaMemcpyDeviceToHost, cs));
-                else
-                    CU(c, cudaMemcpy2DAsync(dst, per_inst * 8, dr, pj * 8, pj * 8, ni,
-                                            cudaMemcpyDeviceToHost, cs));
-            }
+            // A block is either whole instances (pj == per_inst) or a piece of a
+            // single instance (ni == 1), so its host image is one contiguous run.
+            if (c_out)
+                CU(c, cudaMemcpyAsync((char *)c_out + (i0 * per_inst + j0) * csz, dc, ni * pj * csz,
+                                      cudaMemcpyDeviceToHost, cs));
+            if (r_out)
+                CU(c, cudaMemcpyAsync(r_out + i0 * per_inst + j0, dr, ni * pj * 8,
+                                      cudaMemcpyDeviceToHost, cs));
             CU(c, cudaEventRecord(c->ev_copied[k], cs));
             used[k] = true;
             k = (k + 1) % S;

@@ -1,0 +1,78 @@
+"""Single launches of each kernel on fixed, moderately sized cases, for ncu.
+
+    python -m paper_1411_2484_gb300.profile_cases CASE [--repeat N]
+
+CASE is one of
+  plain32   65,536 instances x 4,096 numbers, R to HBM (2 GiB)     gen32_kernel
+  fused32   the same instances, statistics only                      gen32_kernel (STATS)
+  wide64    4,096 64-bit instances x 4,096 numbers, R (128 MiB)      gen64_kernel
+  batched   2,000 instances (80 % 32-bit), lengths log-uniform in
+            [1, 2^18], offsets in [0, 2^40), R (about 0.4 GiB)       batch_kernel
+Each case warms up once, then launches its kernel N times (default 3) and
+prints the CUDA-event time per launch.  Inputs are the seeded workloads of
+paper_1411_2484_gb300.workloads.
+"""
+import argparse
+import json
+
+import torch
+
+import paper_1411_2484_gb300 as ph
+from paper_1411_2484_gb300 import workloads
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case", choices=["plain32", "fused32", "wide64", "batched"])
+    ap.add_argument("--repeat", type=int, default=3)
+    args = ap.parse_args()
+    s = torch.cuda.current_stream()
+    ctx, plan = None, None
+    if args.case in ("plain32", "fused32"):
+        inst = workloads.workload_instances("plain32_65536x4096x64")
+        N, per = 65536, 4096
+        ctx = ph.phprng_create(32, inst, ph.PHPRNG_REQUIRE_SAFE_PRIME, s)
+        if args.case == "plain32":
+            r = torch.empty(N * per, dtype=torch.float64, device="cuda")
+            run = lambda: ph.phprng_generate(ctx, 0, N, per, None, r, None, s)
+        else:
+            sb = torch.empty(N * ph.STATS_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+            run = lambda: ph.phprng_generate(ctx, 0, N, per, None, None, sb, s)
+        numbers = N * per
+    elif args.case == "wide64":
+        inst = workloads.workload_instances("wide64_4096x2^20")
+        N, per = 4096, 4096
+        ctx = ph.phprng_create(64, inst, ph.PHPRNG_REQUIRE_SAFE_PRIME, s)
+        r = torch.empty(N * per, dtype=torch.float64, device="cuda")
+        run = lambda: ph.phprng_generate(ctx, 0, N, per, None, r, None, s)
+        numbers = N * per
+    else:
+        i32 = workloads.draw_instances(1600, seed=0x5EED0005)
+        i64 = workloads.draw_instances(400, width=64, seed=0x5EED0006)
+        inst = workloads.concat_instances(i32, i64)
+        reqs = workloads.batched_requests(1600, 400, max_len=1 << 18, seed=0x5EED0007)
+        numbers = int(reqs["len"].sum())
+        ctx = ph.phprng_create(0, inst, 0, s)
+        r = torch.empty(numbers, dtype=torch.float64, device="cuda")
+        plan = ph.phprng_plan_create(ctx, reqs, 0, s)
+        run = lambda: ph.phprng_plan_launch(plan, None, r, s, ctx=ctx)
+    try:
+        run()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(args.repeat):
+            run()
+        e1.record(s)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.repeat
+        print(json.dumps({"case": args.case, "numbers": numbers, "ms_per_launch": ms,
+                          "prn_s": numbers / ms * 1e3}))
+    finally:
+        if plan:
+            ph.phprng_plan_destroy(plan)
+        ph.phprng_destroy(ctx)
+
+
+if __name__ == "__main__":
+    main()

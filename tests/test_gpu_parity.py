@@ -229,11 +229,13 @@ def test_64bit_small_and_mixed_context(ph, torch):
         ph.phprng_destroy(ctxm)
 
 
-def test_host_output_buffers(ph, torch):
+@pytest.mark.parametrize("count,per", [(600, 65536), (2, (1 << 25) + 1000)],
+                         ids=["whole_instances", "split_instances"])
+def test_host_output_buffers(ph, torch, count, per):
     """Host pointers (pageable numpy, pinned torch) stage through the device:
     several staging blocks of whole instances (> 2^25 numbers), and instances
-    longer than one block (split rows, strided copies)."""
-    for count, per in ((600, 65536), (2, (1 << 25) + 1000)):
+    longer than one block (each split over blocks)."""
+    if True:
         inst = workloads.draw_instances(count, seed=31 + count)
         a = ph.phprng_create(32, inst, 0)
         b = ph.phprng_create(32, inst, 0)
