@@ -164,6 +164,9 @@ PH_HD uint64_t mont(uint64_t a, uint64_t b, uint64_t n, uint64_t ninv) { return 
 #ifndef PH_SQ_SWITCH
 #define PH_SQ_SWITCH 0
 #endif
+#ifndef PH_PROG_PREFETCH
+#define PH_PROG_PREFETCH 1
+#endif
 template <int NPT>
 PH_HD void mont32_vec(uint32_t (&x)[NPT], const uint32_t (&y)[NPT], uint32_t n, uint32_t ninv)
 {
@@ -260,8 +263,15 @@ PH_HD void modexp_prog(W (&x)[NPT], const W (&m)[NPT], const ExpProg &pg, W n, W
         break;
     }
     const int nent = pg.nent;
+#if PH_PROG_PREFETCH
+    int bnext = pg.ent[1];
+    for (int k = 1; k < nent; ++k) {
+        const int b = bnext;
+        bnext = pg.ent[k + 1 < (int)sizeof pg.ent ? k + 1 : k];   // next entry, loaded early
+#else
     for (int k = 1; k < nent; ++k) {
         const int b = pg.ent[k];
+#endif
         int sq = b & 63;
 #if PH_SQ_SWITCH
         for (; sq >= 4; sq -= 4) {
@@ -344,6 +354,36 @@ PH_HD uint32_t hist_bin256(double R)
     const int shift = 1067 - ef;
     const uint32_t bin = shift >= 64 ? 0u : shift <= 0 ? 256u : (uint32_t)(sig >> shift);
     return bin > 255u ? 255u : bin;
+}
+
+// The same double, deciding the rounding from an 11-bit fraction: with
+// W = floor((2^95 - 1) / yN), Xf = floor(A W / 2^(32-extra)) is the exact
+// quotient X = A 2^(52+extra) / yN scaled by 2^11 (so Xf < 2^64) and short of
+// it by less than 3 units of its last bit, because W is short of 2^95/yN by
+// at most 1, A < 2^32, and the floor drops less than 1.  Ties are impossible
+// (X is an integer or not dyadic, as yN < 2^32), so X rounds up exactly when
+// its fraction exceeds 1/2; the 11-bit fraction f of Xf decides that unless
+// 1021 <= f < 1024, where the exact remainder of floor(X) = floor(Xf / 2^11)
+// decides it (about 1 number in 700).
+PH_HD double real32_fast(uint32_t c, uint32_t yN, uint32_t ybits, uint64_t W)
+{
+    uint32_t x = c + 1;
+    int xb = 32 - clz32(x);
+    uint32_t A = x << (32 - xb);
+    uint32_t extra = A < yN ? 1u : 0u;
+    int E = xb - (int)ybits - (int)extra;
+    const uint64_t P = (uint64_t)A * (uint32_t)W;             // A * w0
+    const uint64_t H = (uint64_t)A * (uint32_t)(W >> 32);     // A * w1
+    const uint64_t Xf = (H << extra) + (P >> (32 - extra));
+    uint64_t Q = Xf >> 11;
+    const uint32_t f = (uint32_t)Xf & 0x7FFu;
+    if (f >= 1024u) {
+        ++Q;
+    } else if (f >= 1021u) {
+        const uint64_t r = ((uint64_t)A << (52 + extra)) - Q * (uint64_t)yN;   // exact, < yN
+        Q += (r << 1) > yN ? 1u : 0u;
+    }
+    return bits_to_double(((uint64_t)(1022 + E) << 52) + Q);
 }
 
 PH_HD double real64(uint64_t c, uint64_t n)

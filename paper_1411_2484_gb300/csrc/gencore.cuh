@@ -21,17 +21,30 @@ namespace phprng {
 
 static constexpr unsigned kFullMask = 0xffffffffu;
 
+#ifndef PH_R_FAST
+#define PH_R_FAST 1
+#endif
+
+// One skip step s -> a s mod p (group = false) or one warp group's advance
+// s -> a^(32 NPT) s mod p (group = true), as a Montgomery product with the
+// constant in Montgomery form.  (A Mersenne fold for p = 2^31 - 1 was measured
+// slower on GB300: it trades two multiplier slots for three ALU operations.)
+__device__ __forceinline__ uint32_t skip_step(const SkipConst &sk, uint32_t s, bool group)
+{
+    return mont32(s, group ? sk.aGM : sk.aM, sk.p, sk.pinv);
+}
+
 template <int NPT>
 __device__ __forceinline__ void group32(const DevInst &P, const ExpProg &pg, const SkipConst &sk,
                                         int lane, uint64_t my0, uint64_t len, uint32_t &M,
                                         uint32_t &sig, uint32_t (&sv)[NPT], uint32_t (&msg)[NPT],
                                         uint32_t (&x)[NPT])
 {
-    const uint32_t n = (uint32_t)P.n, p = sk.p, pinv = sk.pinv;
+    const uint32_t n = (uint32_t)P.n;
     uint32_t S = 0, t = sig;
 #pragma unroll
     for (int u = 0; u < NPT; ++u) {
-        t = mont32(t, sk.aM, p, pinv);                           // Eq. 9a
+        t = skip_step(sk, t, false);                             // Eq. 9a
         sv[u] = t;
         if (my0 + u < len) S = addmod32(S, t, n);
     }
@@ -50,7 +63,7 @@ __device__ __forceinline__ void group32(const DevInst &P, const ExpProg &pg, con
     }
     modexp_prog<NPT, uint32_t>(x, msg, pg, n, (uint32_t)P.ninv, (uint32_t)P.K);   // Eq. 9c
     M = addmod32(M, total, n);
-    sig = mont32(sig, sk.aGM, p, pinv);
+    sig = skip_step(sk, sig, true);
 }
 
 template <int NPT>
@@ -60,12 +73,11 @@ __device__ __forceinline__ void group64(const DevInst &P, const ExpProg &pg, con
                                         uint64_t (&x)[NPT])
 {
     const uint64_t n = P.n;
-    const uint32_t p = sk.p, pinv = sk.pinv;
     uint64_t S = 0;
     uint32_t t = sig;
 #pragma unroll
     for (int u = 0; u < NPT; ++u) {
-        t = mont32(t, sk.aM, p, pinv);
+        t = skip_step(sk, t, false);
         sv[u] = t;
         if (my0 + u < len) S = addmod64(S, t, n);
     }
@@ -84,14 +96,18 @@ __device__ __forceinline__ void group64(const DevInst &P, const ExpProg &pg, con
     }
     modexp_prog<NPT, uint64_t>(x, msg, pg, n, P.ninv, P.K);
     M = addmod64(M, total, n);
-    sig = mont32(sig, sk.aGM, p, pinv);
+    sig = skip_step(sk, sig, true);
 }
 
 // R = (c+1)/(n+1) (Eq. 9d): integer-built and correctly rounded for 32-bit
 // n, RN(RN(c+1)/RN(n+1)) by the FP64 unit for 64-bit n.
 __device__ __forceinline__ double real_of(const DevInst &P, uint32_t c)
 {
+#if PH_R_FAST
+    return real32_fast(c, P.yN, P.ybits, P.aux);
+#else
     return real32(c, P.yN, P.ybits, P.V);
+#endif
 }
 __device__ __forceinline__ double real_of(const DevInst &P, uint64_t c) { return real64(c, P.n); }
 

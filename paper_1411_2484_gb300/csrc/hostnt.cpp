@@ -319,11 +319,12 @@ DevInst derive_inst(const phprng_instance &in, int wide, ExpProg *prog)
         d.ybits = (uint32_t)bitlen(y);
         d.yN = (uint32_t)(y << (32 - d.ybits));
         d.V = (uint64_t)((((u128)1) << 84) / d.yN);
+        d.aux = (uint64_t)(((((u128)1) << 95) - 1) / d.yN);
     } else {
         d.ninv = inv_mod_2_64(in.n);
         d.K = mont_exit_constant(in.n, *prog, 64);
         uint64_t r = (uint64_t)((((u128)1) << 64) % in.n);
-        d.r2 = mulmod(r, r, in.n);
+        d.aux = mulmod(r, r, in.n);
     }
     return d;
 }

@@ -32,7 +32,8 @@ struct alignas(16) DevInst {
     uint32_t ybits;  // bitlen(n+1)
     uint32_t ebits;  // bitlen(e)
     uint32_t wide;   // 0: 32-bit path, 1: 64-bit path
-    uint64_t r2;     // 2^128 mod n (64-bit path): x*y mod n = mont64(mont64(x, y), r2)
+    uint64_t aux;    // 64-bit path: 2^128 mod n, so x*y mod n = mont64(mont64(x, y), aux);
+                     // 32-bit path: floor((2^95 - 1) / yN), the reciprocal of real32_fast
 };
 static_assert(sizeof(DevInst) == 64, "DevInst is one 64-byte line");
 

@@ -88,7 +88,7 @@ __device__ __forceinline__ void skip_state_warp(const SkipTable &tb, const DevIn
         *m_out = (m + add) % n;
     } else {
         const uint64_t t = mont64(q % n, tb.half % n, n, P.ninv);   // q*half*R^-1
-        add = mont64(t, P.r2, n, P.ninv);                          // q*half mod n
+        add = mont64(t, P.aux, n, P.ninv);                         // q*half mod n
         add = addmod64(add, W % n, n);
         *m_out = addmod64(m, add, n);
     }

@@ -18,6 +18,33 @@ void h_real32_many(const uint64_t *n, const uint64_t *c, double *out, uint64_t c
     }
 }
 
+void h_real32_fast_many(const uint64_t *n, const uint64_t *c, double *out, uint64_t count)
+{
+    for (uint64_t i = 0; i < count; ++i) {
+        phprng_instance in{n[i], 3, 3, 2, 0, 1};
+        ExpProg pg;
+        DevInst d = derive_inst(in, 0, &pg);
+        out[i] = real32_fast((uint32_t)c[i], d.yN, d.ybits, d.aux);
+    }
+}
+
+// fraction bits f of the fast quotient estimate, to find inputs in the band
+// where real32_fast falls back to the exact remainder
+uint32_t h_real32_fast_frac(uint64_t n, uint64_t c)
+{
+    phprng_instance in{n, 3, 3, 2, 0, 1};
+    ExpProg pg;
+    DevInst d = derive_inst(in, 0, &pg);
+    uint32_t x = (uint32_t)c + 1;
+    int xb = 32 - clz32(x);
+    uint32_t A = x << (32 - xb);
+    uint32_t extra = A < d.yN ? 1u : 0u;
+    const uint64_t P = (uint64_t)A * (uint32_t)d.aux;
+    const uint64_t H = (uint64_t)A * (uint32_t)(d.aux >> 32);
+    const uint64_t Xf = (H << extra) + (P >> (32 - extra));
+    return (uint32_t)Xf & 0x7FFu;
+}
+
 void h_modexp_many(const uint64_t *m, const uint64_t *e, const uint64_t *n, uint64_t *out,
                    uint64_t count, int wide)
 {

@@ -37,6 +37,9 @@ def h(tmp_path_factory):
     lib.h_discrete_log.argtypes = [u64, u64, u64, P64]
     lib.h_addmod.restype = u64
     lib.h_addmod.argtypes = [u64, u64, u64, ctypes.c_int]
+    lib.h_real32_fast_many.argtypes = [P64, P64, ctypes.POINTER(ctypes.c_double), u64]
+    lib.h_real32_fast_frac.restype = ctypes.c_uint32
+    lib.h_real32_fast_frac.argtypes = [u64, u64]
     return lib
 
 
@@ -163,3 +166,41 @@ def test_hist_bin_matches_floor(h):
                       out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), r.size)
     ref = np.minimum(np.floor(r * 256.0), 255).astype(np.uint32)
     assert np.array_equal(out, ref)
+
+
+def test_real32_fast_equals_ieee_division(h):
+    """The fast rounding decision, and its exact fallback band (forced)."""
+    rng = np.random.default_rng(11)
+    k = 600000
+    n = np.concatenate([rng.integers(3, 1 << 32, k // 2, dtype=np.uint64) | np.uint64(1),
+                        rng.integers(3, 5000, k // 2, dtype=np.uint64) | np.uint64(1)])
+    n = np.minimum(n, np.uint64((1 << 32) - 5))
+    c = (rng.integers(0, 1 << 62, k, dtype=np.uint64) % n).astype(np.uint64)
+    c[::7] = n[::7] - np.uint64(1)
+    c[::11] = 0
+    # add inputs whose estimate lands in the fallback band 1021 <= f < 1024
+    band_n, band_c = [], []
+    rr = random.Random(12)
+    while len(band_n) < 3000:
+        nn = rr.randrange(3, (1 << 32) - 5) | 1
+        cc = rr.randrange(nn)
+        if 1018 <= h.h_real32_fast_frac(nn, cc) < 1028:
+            band_n.append(nn)
+            band_c.append(cc)
+    n = np.concatenate([n, np.array(band_n, dtype=np.uint64)])
+    c = np.concatenate([c, np.array(band_c, dtype=np.uint64)])
+    out = np.empty(n.size, dtype=np.float64)
+    h.h_real32_fast_many(_p(n), _p(c), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n.size)
+    ref = (c + np.uint64(1)).astype(np.float64) / (n + np.uint64(1)).astype(np.float64)
+    assert np.array_equal(out.view(np.uint64), ref.view(np.uint64))
+    for nn in (3, 5, 7, 23, 31, 127, 255, 257, 4093, 8191, 2147483647):   # every c, small n
+        if nn > 10000:
+            cs = np.array([0, 1, nn - 2, nn - 1] + [rr.randrange(nn) for _ in range(5000)],
+                          dtype=np.uint64)
+        else:
+            cs = np.arange(nn, dtype=np.uint64)
+        ns = np.full(cs.size, nn, dtype=np.uint64)
+        o = np.empty(cs.size, dtype=np.float64)
+        h.h_real32_fast_many(_p(ns), _p(cs), o.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                             cs.size)
+        assert all(o[i] == float(Fraction(int(cs[i]) + 1, nn + 1)) for i in range(cs.size))
