@@ -327,8 +327,10 @@ int phprng_get_state(phprng_ctx *ctx, uint64_t inst, phprng_instance *state_out,
  * the call synchronizes).  which: 0 mul.lo.u32, 1 mad.hi.u32, 2 mad.wide.u32
  * (each 32-bit product half is the unit of the generator's roofline: forms
  * 0 and 1 make one half, form 2 two), 3 the generator's Montgomery product
- * mod a 32-bit prime, 4 fma.rn.f64.  Allocates and frees a small device
- * buffer.  The paper has no counterpart: this is the measurement used to
+ * mod a 32-bit prime, 4 fma.rn.f64, 5 the generator's window exponent
+ * programs alone on 65,536 seeded 32-bit instances (Montgomery products per
+ * second; draws the instances on the host first).  Allocates and frees small
+ * device buffers.  The paper has no counterpart: this is the measurement used to
  * state the multiply-bound roofline of Eq. 9c. */
 int phprng_microbench(int which, double *ops_per_s, void *cuda_stream);
 

@@ -38,10 +38,11 @@ __device__ __forceinline__ void run_tile32(const BatchArgs &a, const DevInst &P,
     for (uint64_t g0 = 0; g0 < len; g0 += G) {
         uint32_t sv[NPT], msg[NPT], x[NPT];
         const uint64_t my0 = g0 + (uint64_t)NPT * lane;
-        group32<NPT>(P, pg, sk, lane, my0, len, M, sig, sv, msg, x);
+        messages32<NPT>(P, sk, lane, my0, len, M, sig, sv, msg);
+        if (wb) write_ms_if_last<NPT, uint32_t>(a.st, i, lane, g0, len, T.start + len, sv, msg);
+        encrypt32<NPT>(P, pg, msg, x);
         store_group<NPT, CT, uint32_t>(P, cdst, rdst, my0, len, vec_ok, x);
-        if (wb) writeback_if_last<NPT, uint32_t, uint32_t>(a.st, i, lane, g0, len, T.start + len,
-                                                           sv, msg, x);
+        if (wb) write_c_if_last<NPT, uint32_t>(a.st, i, lane, g0, len, x);
     }
 }
 
@@ -61,10 +62,11 @@ __device__ __forceinline__ void run_tile64(const BatchArgs &a, const DevInst &P,
         uint32_t sv[NPT];
         uint64_t msg[NPT], x[NPT];
         const uint64_t my0 = g0 + (uint64_t)NPT * lane;
-        group64<NPT>(P, pg, sk, lane, my0, len, M, sig, sv, msg, x);
+        messages64<NPT>(P, sk, lane, my0, len, M, sig, sv, msg);
+        if (wb) write_ms_if_last<NPT, uint64_t>(a.st, i, lane, g0, len, T.start + len, sv, msg);
+        encrypt64<NPT>(P, pg, msg, x);
         store_group<NPT, uint64_t, uint64_t>(P, cdst, rdst, my0, len, vec_ok, x);
-        if (wb) writeback_if_last<NPT, uint64_t, uint64_t>(a.st, i, lane, g0, len, T.start + len,
-                                                           sv, msg, x);
+        if (wb) write_c_if_last<NPT, uint64_t>(a.st, i, lane, g0, len, x);
     }
 }
 

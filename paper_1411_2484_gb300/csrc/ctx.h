@@ -32,6 +32,12 @@ struct phprng_ctx {
     DevState st{};
     SkipConst sk32{}, sk64{}, sk32_8{}, sk32_4{};
     std::vector<uint64_t> pos_host;   // host mirror of the stream positions
+    // launch order: key[i] = 256*wide + 255 - products of instance i's program
+    // (clamped); d_order[first ..] holds the order of the last range sorted
+    // (indices relative to its first instance), ord_first/ord_num name it.
+    std::vector<uint16_t> key;
+    uint32_t *d_order = nullptr;
+    uint64_t ord_first = 0, ord_num = 0;
     // skip-ahead: cycle positions of the seeds and the prefix table (lazy)
     uint64_t *d_L0 = nullptr, *d_m0 = nullptr, *d_T = nullptr;
     uint32_t *d_P = nullptr;

@@ -60,7 +60,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, STATS ? PH_MINB_STATS : P
 gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, DevState st,
              SkipConst sk, uint64_t first, uint64_t num, uint64_t per_inst,
              CT *__restrict__ c_out, double *__restrict__ r_out, int vec_ok,
-             phprng_stats *__restrict__ stats, uint32_t *__restrict__ edge)
+             phprng_stats *__restrict__ stats, uint32_t *__restrict__ edge,
+             const uint32_t *__restrict__ order)
 {
     extern __shared__ uint32_t smem[];   // STATS: cbuf[2][W][32*NPT] then hist[W][256]
     constexpr int W = kWarpsPerBlock;
@@ -69,7 +70,9 @@ gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
     const uint64_t w = (uint64_t)blockIdx.x * W + warp;
     const bool active = w < num;
     if (!STATS && !active) return;
-    const uint64_t i = first + (active ? w : 0);
+    // the instance this warp runs, relative to `first` (statistics: always w)
+    const uint64_t j = !active ? 0 : (!STATS && order) ? order[w] : w;
+    const uint64_t i = first + j;
     const DevInst P = inst[i];
     if (!STATS && P.wide) return;
     const ExpProg &pg = prog[i];
@@ -77,8 +80,8 @@ gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
     uint32_t M = (uint32_t)st.m[i];
     uint32_t sig = mont32((uint32_t)st.s[i], sk.lane[lane], sk.p, sk.pinv);
     const uint64_t pos_after = st.pos[i] + per_inst;
-    CT *cdst = c_out ? c_out + w * per_inst : nullptr;
-    double *rdst = r_out ? r_out + w * per_inst : nullptr;
+    CT *cdst = c_out ? c_out + j * per_inst : nullptr;
+    double *rdst = r_out ? r_out + j * per_inst : nullptr;
 
     uint32_t *hist = smem + 2 * W * (32 * NPT) + warp * 256;
     uint64_t X = 0;      // < 2^63: per_inst < 2^31 numbers of at most 2^32 each
@@ -94,10 +97,11 @@ gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
         uint32_t sv[NPT], msg[NPT], x[NPT];
         const uint64_t my0 = g0 + (uint64_t)NPT * lane;
         if (active) {
-            group32<NPT>(P, pg, sk, lane, my0, per_inst, M, sig, sv, msg, x);
+            messages32<NPT>(P, sk, lane, my0, per_inst, M, sig, sv, msg);
+            write_ms_if_last<NPT, uint32_t>(st, i, lane, g0, per_inst, pos_after, sv, msg);
+            encrypt32<NPT>(P, pg, msg, x);
             store_group<NPT, CT, uint32_t>(P, cdst, rdst, my0, per_inst, vec_ok, x);
-            writeback_if_last<NPT, uint32_t, uint32_t>(st, i, lane, g0, per_inst, pos_after, sv,
-                                                       msg, x);
+            write_c_if_last<NPT, uint32_t>(st, i, lane, g0, per_inst, x);
         }
         if (STATS) {
             uint32_t *cb = smem + ((int)((g0 / G) & 1) * W + warp) * (32 * NPT);
@@ -190,28 +194,32 @@ template <int NPT>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 gen64_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, DevState st,
              SkipConst sk, uint64_t first, uint64_t num, uint64_t per_inst,
-             uint64_t *__restrict__ c_out, double *__restrict__ r_out, int vec_ok)
+             uint64_t *__restrict__ c_out, double *__restrict__ r_out, int vec_ok,
+             const uint32_t *__restrict__ order)
 {
     constexpr uint64_t G = 32 * NPT;
     const int lane = threadIdx.x & 31;
     const uint64_t w = (uint64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     if (w >= num) return;
-    const uint64_t i = first + w;
+    const uint64_t j = order ? order[w] : w;          // instance first + j
+    const uint64_t i = first + j;
     const DevInst P = inst[i];
     if (!P.wide) return;
     const ExpProg &pg = prog[i];
     uint64_t M = st.m[i];
     uint32_t sig = mont32((uint32_t)st.s[i], sk.lane[lane], sk.p, sk.pinv);
     const uint64_t pos_after = st.pos[i] + per_inst;
-    uint64_t *cdst = c_out ? c_out + w * per_inst : nullptr;
-    double *rdst = r_out ? r_out + w * per_inst : nullptr;
+    uint64_t *cdst = c_out ? c_out + j * per_inst : nullptr;
+    double *rdst = r_out ? r_out + j * per_inst : nullptr;
     for (uint64_t g0 = 0; g0 < per_inst; g0 += G) {
         uint32_t sv[NPT];
         uint64_t msg[NPT], x[NPT];
         const uint64_t my0 = g0 + (uint64_t)NPT * lane;
-        group64<NPT>(P, pg, sk, lane, my0, per_inst, M, sig, sv, msg, x);
+        messages64<NPT>(P, sk, lane, my0, per_inst, M, sig, sv, msg);
+        write_ms_if_last<NPT, uint64_t>(st, i, lane, g0, per_inst, pos_after, sv, msg);
+        encrypt64<NPT>(P, pg, msg, x);
         store_group<NPT, uint64_t, uint64_t>(P, cdst, rdst, my0, per_inst, vec_ok, x);
-        writeback_if_last<NPT, uint64_t, uint64_t>(st, i, lane, g0, per_inst, pos_after, sv, msg, x);
+        write_c_if_last<NPT, uint64_t>(st, i, lane, g0, per_inst, x);
     }
 }
 
@@ -235,11 +243,11 @@ int launch_gen32(const GenArgs &a, void *stream, std::string *err)
         if (a.c_is_64)
             gen32_kernel<kNPT, uint64_t, true><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(
                 a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, (uint64_t *)a.c_out, a.r_out,
-                a.vec_ok, a.stats, a.edge);
+                a.vec_ok, a.stats, a.edge, nullptr);
         else
             gen32_kernel<kNPT, uint32_t, true><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(
                 a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, (uint32_t *)a.c_out, a.r_out,
-                a.vec_ok, a.stats, a.edge);
+                a.vec_ok, a.stats, a.edge, nullptr);
         int rc = check_launch(err, "gen32_kernel (statistics) launch");
         if (rc != PHPRNG_OK || blocks < 2) return rc;
         stats_edge_kernel<<<(unsigned)((blocks - 1 + 7) / 8), 256, 0, s>>>(
@@ -249,11 +257,11 @@ int launch_gen32(const GenArgs &a, void *stream, std::string *err)
     if (a.c_is_64)
         gen32_kernel<kNPT, uint64_t, false><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(
             a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, (uint64_t *)a.c_out, a.r_out, a.vec_ok,
-            nullptr, nullptr);
+            nullptr, nullptr, a.order);
     else
         gen32_kernel<kNPT, uint32_t, false><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(
             a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, (uint32_t *)a.c_out, a.r_out, a.vec_ok,
-            nullptr, nullptr);
+            nullptr, nullptr, a.order);
     return check_launch(err, "gen32_kernel launch");
 }
 
@@ -268,7 +276,8 @@ int launch_gen64(const GenArgs &a, void *stream, std::string *err)
     if (a.num == 0 || a.per_inst == 0) return PHPRNG_OK;
     const uint64_t blocks = (a.num + kWarpsPerBlock - 1) / kWarpsPerBlock;
     gen64_kernel<kNPT64><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, (cudaStream_t)stream>>>(
-        a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, (uint64_t *)a.c_out, a.r_out, a.vec_ok);
+        a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, (uint64_t *)a.c_out, a.r_out, a.vec_ok,
+        a.order);
     return check_launch(err, "gen64_kernel launch");
 }
 

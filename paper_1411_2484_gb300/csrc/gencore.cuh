@@ -13,6 +13,11 @@
 // and leaves M and sig ready for the next group; R = (x_u+1)/(n+1) (Eq. 9d)
 // is formed where it is stored or consumed (real_of).  Numbers past `len` are
 // computed but excluded from the sums that carry into later numbers.
+//
+// The kernels call messages32/64, then (when the run ends in this group) let
+// the owning lane record m and s of the last number, then encrypt: so the
+// skips and messages need not stay in registers through the exponentiation,
+// and only the ciphertext of the last number is written after it.
 #pragma once
 #include "arith.cuh"
 #include "internal.h"
@@ -35,10 +40,9 @@ __device__ __forceinline__ uint32_t skip_step(const SkipConst &sk, uint32_t s, b
 }
 
 template <int NPT>
-__device__ __forceinline__ void group32(const DevInst &P, const ExpProg &pg, const SkipConst &sk,
-                                        int lane, uint64_t my0, uint64_t len, uint32_t &M,
-                                        uint32_t &sig, uint32_t (&sv)[NPT], uint32_t (&msg)[NPT],
-                                        uint32_t (&x)[NPT])
+__device__ __forceinline__ void messages32(const DevInst &P, const SkipConst &sk, int lane,
+                                           uint64_t my0, uint64_t len, uint32_t &M, uint32_t &sig,
+                                           uint32_t (&sv)[NPT], uint32_t (&msg)[NPT])
 {
     const uint32_t n = (uint32_t)P.n;
     uint32_t S = 0, t = sig;
@@ -61,16 +65,14 @@ __device__ __forceinline__ void group32(const DevInst &P, const ExpProg &pg, con
         mm = addmod32(mm, sv[u], n);                              // Eq. 9b
         msg[u] = mm;
     }
-    modexp_prog<NPT, uint32_t>(x, msg, pg, n, (uint32_t)P.ninv, (uint32_t)P.K);   // Eq. 9c
     M = addmod32(M, total, n);
     sig = skip_step(sk, sig, true);
 }
 
 template <int NPT>
-__device__ __forceinline__ void group64(const DevInst &P, const ExpProg &pg, const SkipConst &sk,
-                                        int lane, uint64_t my0, uint64_t len, uint64_t &M,
-                                        uint32_t &sig, uint32_t (&sv)[NPT], uint64_t (&msg)[NPT],
-                                        uint64_t (&x)[NPT])
+__device__ __forceinline__ void messages64(const DevInst &P, const SkipConst &sk, int lane,
+                                           uint64_t my0, uint64_t len, uint64_t &M, uint32_t &sig,
+                                           uint32_t (&sv)[NPT], uint64_t (&msg)[NPT])
 {
     const uint64_t n = P.n;
     uint64_t S = 0;
@@ -94,9 +96,22 @@ __device__ __forceinline__ void group64(const DevInst &P, const ExpProg &pg, con
         mm = addmod64(mm, sv[u], n);
         msg[u] = mm;
     }
-    modexp_prog<NPT, uint64_t>(x, msg, pg, n, P.ninv, P.K);
     M = addmod64(M, total, n);
     sig = skip_step(sk, sig, true);
+}
+
+// Eq. 9c for the lane's NPT messages.
+template <int NPT>
+__device__ __forceinline__ void encrypt32(const DevInst &P, const ExpProg &pg, const uint32_t (&msg)[NPT],
+                                          uint32_t (&x)[NPT])
+{
+    modexp_prog<NPT, uint32_t>(x, msg, pg, (uint32_t)P.n, (uint32_t)P.ninv, (uint32_t)P.K);
+}
+template <int NPT>
+__device__ __forceinline__ void encrypt64(const DevInst &P, const ExpProg &pg, const uint64_t (&msg)[NPT],
+                                          uint64_t (&x)[NPT])
+{
+    modexp_prog<NPT, uint64_t>(x, msg, pg, P.n, P.ninv, P.K);
 }
 
 // R = (c+1)/(n+1) (Eq. 9d): integer-built and correctly rounded for 32-bit
@@ -151,28 +166,47 @@ __device__ __forceinline__ void store_group(const DevInst &P, CT *c_dst, double 
     }
 }
 
-// The lane that owns number `len` of the run (g0 the group's first index)
-// writes the state after it: message, skip, ciphertext and position.
-template <int NPT, typename MT, typename XT>
-__device__ __forceinline__ void writeback_if_last(DevState st, uint64_t i, int lane, uint64_t g0,
-                                                  uint64_t len, uint64_t pos_after,
-                                                  const uint32_t (&sv)[NPT], const MT (&msg)[NPT],
-                                                  const XT (&x)[NPT])
+// The lane that owns number `len` of the run (g0 the group's first index),
+// or -1 in the other lanes and groups; u_out = its slot.
+template <int NPT>
+__device__ __forceinline__ bool owns_last(int lane, uint64_t g0, uint64_t len, int *u_out)
 {
     constexpr uint64_t G = 32 * NPT;
-    if (g0 + G < len) return;
+    if (g0 + G < len) return false;
     const uint64_t last = len - 1 - g0;
-    if ((uint64_t)lane != last / NPT) return;
-    const int ul = (int)(last % NPT);
+    if ((uint64_t)lane != last / NPT) return false;
+    *u_out = (int)(last % NPT);
+    return true;
+}
+
+// State after the run, before the encryption: message, skip and position.
+template <int NPT, typename MT>
+__device__ __forceinline__ void write_ms_if_last(DevState st, uint64_t i, int lane, uint64_t g0,
+                                                 uint64_t len, uint64_t pos_after,
+                                                 const uint32_t (&sv)[NPT], const MT (&msg)[NPT])
+{
+    int ul;
+    if (!owns_last<NPT>(lane, g0, len, &ul)) return;
 #pragma unroll
     for (int u = 0; u < NPT; ++u) {
         if (u == ul) {
             st.m[i] = msg[u];
             st.s[i] = sv[u];
-            st.c[i] = x[u];
         }
     }
     st.pos[i] = pos_after;
+}
+
+// ... and the last ciphertext, after it.
+template <int NPT, typename XT>
+__device__ __forceinline__ void write_c_if_last(DevState st, uint64_t i, int lane, uint64_t g0,
+                                                uint64_t len, const XT (&x)[NPT])
+{
+    int ul;
+    if (!owns_last<NPT>(lane, g0, len, &ul)) return;
+#pragma unroll
+    for (int u = 0; u < NPT; ++u)
+        if (u == ul) st.c[i] = x[u];
 }
 
 }  // namespace phprng

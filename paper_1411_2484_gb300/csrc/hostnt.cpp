@@ -279,6 +279,13 @@ static ExpProg best_program(uint64_t e)
     return best;
 }
 
+int program_products(const ExpProg &pg)
+{
+    int p = (pg.tbl == 1 ? 0 : pg.tbl == 2 ? 2 : 4) + pg.tail + 1;
+    for (int k = 1; k < pg.nent; ++k) p += (pg.ent[k] & 63) + 1;
+    return p;
+}
+
 // Every Montgomery product MP(x, y) = x y R^-1 (R = 2^rbits) multiplies the
 // R-powers its operands carry and adds one R^-1.  Started from the plain
 // message (power 0), the table holds m2 (power -1), m^3 = MP(m2, m) (-2),

@@ -67,6 +67,10 @@ struct GenArgs {
     uint32_t *edge;         // statistics scratch: gen32_edge_words(num, per_inst) words
     int c_is_64;
     int vec_ok;             // outputs allow 16-byte vector stores
+    // nullable: warp w of the launch runs instance first + order[w] (a
+    // permutation of 0 .. num-1, heaviest programs first); NULL = identity.
+    // Never used with statistics, whose pairs need adjacent instances.
+    const uint32_t *order = nullptr;
 };
 
 // Exact prefix table of the skip generator's cycle (Eq. 7): with
@@ -154,6 +158,7 @@ bool discrete_log(uint64_t p, uint64_t a, uint64_t s, uint64_t *L);
 bool discrete_logs(uint64_t p, uint64_t a, const uint64_t *s, uint64_t count, uint64_t *L);
 uint64_t mont_exit_constant(uint64_t n, const ExpProg &pg, int rbits);
 DevInst derive_inst(const phprng_instance &in, int wide, ExpProg *prog);
+int program_products(const ExpProg &pg);   // Montgomery products of one run, K included
 SkipConst derive_skip(uint64_t p, uint64_t a, int npt);
 int validate_one(int width, const phprng_instance &in, uint32_t flags, std::string *msg);
 int validate_all(int width, const phprng_instance *inst, uint64_t count, uint32_t flags,

@@ -9,7 +9,14 @@
 //   2  mad.wide.u32            two halves per operation
 //   3  Montgomery product mod a 32-bit prime (the generator's mulmod)
 //   4  fma.rn.f64              FP64 fused multiply-add
+//   5  the generator's window exponent programs alone (Eq. 9c without the
+//      skips, scan, R and stores): 65,536 seeded 32-bit instances (safe
+//      primes, random exponents), one warp per instance, 8 messages per
+//      lane, 16 exponentiations back to back; the rate counts Montgomery
+//      products (table, windows, squarings and the exit product).
 #include <cuda_runtime.h>
+
+#include <vector>
 
 #include "arith.cuh"
 #include "internal.h"
@@ -103,6 +110,80 @@ static int run_one(double *ops_per_s, cudaStream_t s, std::string *err)
     return PHPRNG_OK;
 }
 
+// Form 5: each warp runs its instance's program on 8 messages per lane and
+// feeds the results back as the next messages (so no exponentiation can be
+// skipped); the XOR of all results goes to sink only if it hits a constant.
+__global__ void __launch_bounds__(256, 2) exp_kernel(const DevInst *inst, const ExpProg *prog,
+                                                     int reps, uint32_t *sink)
+{
+    constexpr int NPT = 8;
+    const int lane = threadIdx.x & 31;
+    const uint64_t w = (uint64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    const DevInst P = inst[w];
+    const ExpProg &pg = prog[w];
+    const uint32_t n = (uint32_t)P.n;
+    uint32_t msg[NPT], x[NPT], acc = 0;
+#pragma unroll
+    for (int u = 0; u < NPT; ++u) msg[u] = (uint32_t)((w * 977 + lane * 131 + u * 7919) % n);
+    for (int r = 0; r < reps; ++r) {
+        modexp_prog<NPT, uint32_t>(x, msg, pg, n, (uint32_t)P.ninv, (uint32_t)P.K);
+#pragma unroll
+        for (int u = 0; u < NPT; ++u) {
+            msg[u] = x[u];
+            acc ^= x[u];
+        }
+    }
+    if (acc == 0x9E3779B9u) sink[w * 32 + lane] = acc;
+}
+
+static int run_exp(double *ops_per_s, cudaStream_t s, std::string *err)
+{
+    const uint64_t count = 65536;
+    const int reps = 16;
+    std::vector<phprng_instance> in(count);
+    int rc = draw_instances(32, count, 0x5EED0001, PHPRNG_REQUIRE_SAFE_PRIME, in.data(), err);
+    if (rc != PHPRNG_OK) return rc;
+    std::vector<DevInst> di(count);
+    std::vector<ExpProg> pg(count);
+    double products = 0;
+    for (uint64_t i = 0; i < count; ++i) {
+        di[i] = derive_inst(in[i], 0, &pg[i]);
+        products += program_products(pg[i]);
+    }
+    DevInst *d_i = nullptr;
+    ExpProg *d_p = nullptr;
+    uint32_t *sink = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float ms = 0.f;
+    cudaError_t e = cudaMalloc(&d_i, count * sizeof(DevInst));
+    if (e == cudaSuccess) e = cudaMalloc(&d_p, count * sizeof(ExpProg));
+    if (e == cudaSuccess) e = cudaMalloc(&sink, count * 32 * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_i, di.data(), count * sizeof(DevInst), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_p, pg.data(), count * sizeof(ExpProg), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {     // two warm-ups, one timed
+        cudaEventRecord(e0, s);
+        exp_kernel<<<(unsigned)(count / 8), 256, 0, s>>>(d_i, d_p, reps, sink);
+        cudaEventRecord(e1, s);
+        e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(d_i);
+    cudaFree(d_p);
+    cudaFree(sink);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *err = std::string("microbench (exponentiation): ") + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? PHPRNG_ENOMEM : PHPRNG_ECUDA;
+    }
+    *ops_per_s = products * 32.0 * 8.0 * reps / (ms * 1e-3);
+    return PHPRNG_OK;
+}
+
 int run_microbench(int which, double *ops_per_s, void *stream, std::string *err)
 {
     cudaStream_t s = (cudaStream_t)stream;
@@ -112,6 +193,7 @@ int run_microbench(int which, double *ops_per_s, void *stream, std::string *err)
     case 2: return run_one<2>(ops_per_s, s, err);
     case 3: return run_one<3>(ops_per_s, s, err);
     case 4: return run_one<4>(ops_per_s, s, err);
+    case 5: return run_exp(ops_per_s, s, err);
     default:
         *err = "microbench: unknown form";
         return PHPRNG_EINVAL;

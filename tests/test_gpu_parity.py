@@ -257,6 +257,60 @@ def test_host_output_buffers(ph, torch, count, per):
             ph.phprng_destroy(b)
 
 
+@pytest.mark.parametrize("width,count,per,want_c", [(32, 1500, 4096, True), (32, 37, 1001, True),
+                                                    (32, 64, 777, False), (64, 20, 513, True)],
+                         ids=["whole_vec", "ragged", "r_only_ragged", "wide64"])
+def test_pinned_host_outputs(ph, torch, width, count, per, want_c):
+    """Pinned host outputs only: same bytes as device outputs, ragged lengths
+    included, and the streams continue from there."""
+    inst = workloads.draw_instances(count, width=width, seed=77 + count)
+    a = ph.phprng_create(width, inst, 0)
+    b = ph.phprng_create(width, inst, 0)
+    try:
+        cdt = torch.int32 if width == 32 else torch.int64
+        for _ in range(2):
+            c_h = torch.zeros(count * per, dtype=cdt, pin_memory=True) if want_c else None
+            r_h = torch.zeros(count * per, dtype=torch.float64, pin_memory=True)
+            ph.phprng_generate(a, 0, count, per, c_h, r_h, None)
+            c_d, r_d = generate(ph, torch, b, width, 0, count, per)
+            if want_c:
+                got = c_h.numpy().view(np.uint32 if width == 32 else np.uint64)
+                assert np.array_equal(got.reshape(count, per).astype(np.uint64), c_d)
+            assert np.array_equal(r_h.numpy().reshape(count, per).view(np.uint64),
+                                  r_d.view(np.uint64))
+        orc = OracleStreams(inst)
+        k = min(count, 3)
+        cr, rr = orc.next(0, k, 2 * per)
+        assert_same(c_d[:k], r_d[:k], cr[:, per:], rr[:, per:])
+    finally:
+        ph.phprng_destroy(a)
+        ph.phprng_destroy(b)
+
+
+def test_launch_order_over_ranges(ph, torch):
+    """Launches of 1,024 instances or more run them heaviest program first
+    (32-bit before 64-bit): outputs stay instance-major and states right over
+    whole-table, sub-range, repeated and short ranges of a shuffled mixed
+    table."""
+    i32 = workloads.draw_instances(2600, seed=91)
+    i64 = workloads.draw_instances(500, width=64, seed=92)
+    cat = workloads.concat_instances(i32, i64)
+    perm = np.random.default_rng(93).permutation(3100)
+    mixed = {k: v[perm] for k, v in cat.items()}
+    ctx = ph.phprng_create(0, mixed, 0)
+    try:
+        orc = OracleStreams(mixed)
+        pos = np.zeros(3100, dtype=np.int64)
+        for first, num, per in [(0, 3100, 40), (300, 2600, 33), (300, 2600, 5), (0, 1024, 8),
+                                (0, 3100, 17), (5, 100, 9), (2000, 1100, 12)]:
+            c, r = generate(ph, torch, ctx, 0, first, num, per)
+            assert_same(c, r, *orc.next(first, num, per))
+            pos[first:first + num] += per
+        check_state(ph, ctx, orc, 0, 3100, pos)
+    finally:
+        ph.phprng_destroy(ctx)
+
+
 def test_plain32_full_size_first_call_and_64_calls(ph, torch):
     """65,536 instances x 4,096 numbers per call, the benchmark's launch:
     the whole first call against the oracle, then 63 more R-only calls and

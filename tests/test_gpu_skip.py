@@ -146,6 +146,11 @@ def test_skip_after_generate_and_c_state(ph, torch):
 
 
 def test_microbench_rates(ph, torch):
-    rates = [ph.phprng_microbench(w) for w in range(5)]
+    rates = [ph.phprng_microbench(w) for w in range(6)]
     assert all(r > 1e9 for r in rates), rates
-    print("mul.lo %.3g mad.hi %.3g mad.wide %.3g mont32 %.3g dfma %.3g per s" % tuple(rates))
+    # the exponent programs run Montgomery products no faster than a bare chain
+    assert rates[5] < 1.05 * rates[3], rates
+    print("mul.lo %.3g mad.hi %.3g mad.wide %.3g mont32 %.3g dfma %.3g programs %.3g per s"
+          % tuple(rates))
+    with pytest.raises(ph.PhprngError):
+        ph.phprng_microbench(6)
