@@ -137,7 +137,14 @@ const char *phprng_status_string(int status);
  * Pointers may be device memory (asynchronous on cuda_stream) or host memory
  * (pinned or pageable; the call then stages through device buffers, copies
  * back, and returns after the data is on the host).  c_out/r_out must be
- * aligned to their element size.  per_inst = 0 is a no-op. */
+ * aligned to their element size.  per_inst = 0 is a no-op.
+ * Work layout (results do not depend on it): a call of 1,024 instances or
+ * more runs them heaviest exponent first; a call with too few instances to
+ * fill the GPU cuts each instance's numbers into chunks (Eq. 6 over chunks:
+ * a pre-pass kernel sums each chunk's skips) and then takes a stream-ordered
+ * scratch of num_inst*(K+1) uint64 (K <= 4096 chunks) for the duration of
+ * the call.  Calls on overlapping instance ranges must be ordered on the
+ * device (they share the stored states). */
 int phprng_generate(phprng_ctx *ctx, uint64_t first, uint64_t num_inst, uint64_t per_inst,
                     void *c_out, double *r_out, phprng_stats *stats_out, void *cuda_stream);
 

@@ -263,6 +263,48 @@ static int pointer_kind(const void *p)
     return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) ? 1 : 0;
 }
 
+// Split launches (SplitArgs): a call with fewer instances than about eight
+// times the warps the GPU keeps resident cuts each instance into K chunks
+// (K a power of two, at most kMaxSplit, chunks of at least kMinChunk numbers)
+// so the grid still fills the GPU; the chunk starts cost one extra skip product
+// per number (the pre-pass) and a short sum per warp.
+static constexpr uint32_t kMaxSplit = 4096;
+static constexpr uint64_t kMinChunk = 1024;
+
+static int prepare_split(phprng_ctx *c, uint64_t num, uint64_t per_inst, GenArgs *g, cudaStream_t s)
+{
+    const uint64_t target = 8 * gen_resident_warps();
+    uint32_t K = 1, lg = 0;
+    while (K < kMaxSplit && num * K < target && per_inst >= 2ull * K * kMinChunk) {
+        K *= 2;
+        ++lg;
+    }
+    if (K == 1) return PHPRNG_OK;
+    SplitArgs &sp = g->sp;
+    sp.K = K;
+    sp.log2K = lg;
+    sp.Lc = ((per_inst + K - 1) / K + 255) / 256 * 256;
+    const uint64_t R = (1ull << 32) % c->p;
+    sp.oneM = (uint32_t)R;
+    sp.aLcM = (uint32_t)mulmod(powmod(c->a, sp.Lc, c->p), R, c->p);
+    uint64_t *scr = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&scr, num * (K + 1) * sizeof(uint64_t), s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        sp = SplitArgs();
+        return fail(c, PHPRNG_ENOMEM, "phprng_generate: split scratch allocation failed");
+    }
+    sp.scratch = scr;
+    std::string err;
+    int rc = launch_chunk_sums(*g, c->sk32_8, s, &err);
+    if (rc != PHPRNG_OK) {
+        cudaFreeAsync(scr, s);
+        sp = SplitArgs();
+        return fail(c, rc, "phprng_generate: " + err);
+    }
+    return PHPRNG_OK;
+}
+
 static int launch_range(phprng_ctx *c, uint64_t first, uint64_t num, uint64_t per_inst,
                         void *c_out, double *r_out, phprng_stats *stats, cudaStream_t s,
                         bool ordered = false)
@@ -289,6 +331,10 @@ static int launch_range(phprng_ctx *c, uint64_t first, uint64_t num, uint64_t pe
                ((uintptr_t)r_out % 16 == 0) && (csz * per_inst) % 16 == 0;
     std::string err;
     int rc = PHPRNG_OK;
+    if (!stats) {
+        rc = prepare_split(c, num, per_inst, &g, s);
+        if (rc != PHPRNG_OK) return rc;
+    }
     const uint64_t edge_words = stats ? gen32_edge_words(num, per_inst) : 0;
     if (edge_words) {
         cudaError_t e = cudaMallocAsync((void **)&g.edge, edge_words * 4, s);
@@ -306,6 +352,7 @@ static int launch_range(phprng_ctx *c, uint64_t first, uint64_t num, uint64_t pe
         g.sk = c->sk64;
         rc = launch_gen64(g, s, &err);
     }
+    if (g.sp.scratch) cudaFreeAsync((void *)g.sp.scratch, s);
     if (rc != PHPRNG_OK) return fail(c, rc, "phprng_generate: " + err);
     return PHPRNG_OK;
 }

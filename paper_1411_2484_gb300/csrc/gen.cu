@@ -61,27 +61,41 @@ gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
              SkipConst sk, uint64_t first, uint64_t num, uint64_t per_inst,
              CT *__restrict__ c_out, double *__restrict__ r_out, int vec_ok,
              phprng_stats *__restrict__ stats, uint32_t *__restrict__ edge,
-             const uint32_t *__restrict__ order)
+             const uint32_t *__restrict__ order, SplitArgs sp)
 {
     extern __shared__ uint32_t smem[];   // STATS: cbuf[2][W][32*NPT] then hist[W][256]
     constexpr int W = kWarpsPerBlock;
     constexpr uint64_t G = 32 * NPT;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint64_t w = (uint64_t)blockIdx.x * W + warp;
-    const bool active = w < num;
+    // statistics launches are never split (sp.K = 1)
+    const bool active = w < (num << sp.log2K);
     if (!STATS && !active) return;
+    const uint64_t q = w >> sp.log2K;                  // instance slot
+    const uint32_t cidx = (uint32_t)(w & (sp.K - 1));   // chunk of it
     // the instance this warp runs, relative to `first` (statistics: always w)
-    const uint64_t j = !active ? 0 : (!STATS && order) ? order[w] : w;
+    const uint64_t j = !active ? 0 : (!STATS && order) ? order[q] : q;
     const uint64_t i = first + j;
     const DevInst P = inst[i];
     if (!STATS && P.wide) return;
     const ExpProg &pg = prog[i];
+    const uint64_t b0 = (uint64_t)cidx * sp.Lc;       // first number of the chunk
+    if (!STATS && b0 >= per_inst) return;             // empty trailing chunk
+    const uint64_t len = sp.K == 1 ? per_inst : min(sp.Lc, per_inst - b0);
+    const bool wb = b0 + len == per_inst;             // the chunk that ends the call
 
-    uint32_t M = (uint32_t)st.m[i];
-    uint32_t sig = mont32((uint32_t)st.s[i], sk.lane[lane], sk.p, sk.pinv);
-    const uint64_t pos_after = st.pos[i] + per_inst;
-    CT *cdst = c_out ? c_out + j * per_inst : nullptr;
-    double *rdst = r_out ? r_out + j * per_inst : nullptr;
+    uint32_t M, sig;
+    if (sp.K == 1) {
+        M = (uint32_t)st.m[i];
+        sig = (uint32_t)st.s[i];
+    } else {
+        M = (uint32_t)chunk_message(sp, q, cidx, P.n, lane);
+        sig = skip_chunk(sk, sp, (uint32_t)sp.scratch[q * (sp.K + 1) + 1], cidx);
+    }
+    sig = mont32(sig, sk.lane[lane], sk.p, sk.pinv);
+    const uint64_t pos_after = wb ? st.pos[i] + per_inst : 0;
+    CT *cdst = c_out ? c_out + j * per_inst + b0 : nullptr;
+    double *rdst = r_out ? r_out + j * per_inst + b0 : nullptr;
 
     uint32_t *hist = smem + 2 * W * (32 * NPT) + warp * 256;
     uint64_t X = 0;      // < 2^63: per_inst < 2^31 numbers of at most 2^32 each
@@ -93,15 +107,15 @@ gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
         __syncwarp();
     }
 
-    for (uint64_t g0 = 0; g0 < per_inst; g0 += G) {
+    for (uint64_t g0 = 0; g0 < len; g0 += G) {
         uint32_t sv[NPT], msg[NPT], x[NPT];
         const uint64_t my0 = g0 + (uint64_t)NPT * lane;
         if (active) {
-            messages32<NPT>(P, sk, lane, my0, per_inst, M, sig, sv, msg);
-            write_ms_if_last<NPT, uint32_t>(st, i, lane, g0, per_inst, pos_after, sv, msg);
+            messages32<NPT>(P, sk, lane, my0, len, M, sig, sv, msg);
+            if (wb) write_ms_if_last<NPT, uint32_t>(st, i, lane, g0, len, pos_after, sv, msg);
             encrypt32<NPT>(P, pg, msg, x);
-            store_group<NPT, CT, uint32_t>(P, cdst, rdst, my0, per_inst, vec_ok, x);
-            write_c_if_last<NPT, uint32_t>(st, i, lane, g0, per_inst, x);
+            store_group<NPT, CT, uint32_t>(P, cdst, rdst, my0, len, vec_ok, x);
+            if (wb) write_c_if_last<NPT, uint32_t>(st, i, lane, g0, len, x);
         }
         if (STATS) {
             uint32_t *cb = smem + ((int)((g0 / G) & 1) * W + warp) * (32 * NPT);
@@ -195,32 +209,90 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 gen64_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, DevState st,
              SkipConst sk, uint64_t first, uint64_t num, uint64_t per_inst,
              uint64_t *__restrict__ c_out, double *__restrict__ r_out, int vec_ok,
-             const uint32_t *__restrict__ order)
+             const uint32_t *__restrict__ order, SplitArgs sp)
 {
     constexpr uint64_t G = 32 * NPT;
     const int lane = threadIdx.x & 31;
     const uint64_t w = (uint64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-    if (w >= num) return;
-    const uint64_t j = order ? order[w] : w;          // instance first + j
+    if (w >= (num << sp.log2K)) return;
+    const uint64_t q = w >> sp.log2K;
+    const uint32_t cidx = (uint32_t)(w & (sp.K - 1));
+    const uint64_t j = order ? order[q] : q;          // instance first + j
     const uint64_t i = first + j;
     const DevInst P = inst[i];
     if (!P.wide) return;
     const ExpProg &pg = prog[i];
-    uint64_t M = st.m[i];
-    uint32_t sig = mont32((uint32_t)st.s[i], sk.lane[lane], sk.p, sk.pinv);
-    const uint64_t pos_after = st.pos[i] + per_inst;
-    uint64_t *cdst = c_out ? c_out + j * per_inst : nullptr;
-    double *rdst = r_out ? r_out + j * per_inst : nullptr;
-    for (uint64_t g0 = 0; g0 < per_inst; g0 += G) {
+    const uint64_t b0 = (uint64_t)cidx * sp.Lc;
+    if (b0 >= per_inst) return;
+    const uint64_t len = sp.K == 1 ? per_inst : min(sp.Lc, per_inst - b0);
+    const bool wb = b0 + len == per_inst;
+    uint64_t M;
+    uint32_t sig;
+    if (sp.K == 1) {
+        M = st.m[i];
+        sig = (uint32_t)st.s[i];
+    } else {
+        M = chunk_message(sp, q, cidx, P.n, lane);
+        sig = skip_chunk(sk, sp, (uint32_t)sp.scratch[q * (sp.K + 1) + 1], cidx);
+    }
+    sig = mont32(sig, sk.lane[lane], sk.p, sk.pinv);
+    const uint64_t pos_after = wb ? st.pos[i] + per_inst : 0;
+    uint64_t *cdst = c_out ? c_out + j * per_inst + b0 : nullptr;
+    double *rdst = r_out ? r_out + j * per_inst + b0 : nullptr;
+    for (uint64_t g0 = 0; g0 < len; g0 += G) {
         uint32_t sv[NPT];
         uint64_t msg[NPT], x[NPT];
         const uint64_t my0 = g0 + (uint64_t)NPT * lane;
-        messages64<NPT>(P, sk, lane, my0, per_inst, M, sig, sv, msg);
-        write_ms_if_last<NPT, uint64_t>(st, i, lane, g0, per_inst, pos_after, sv, msg);
+        messages64<NPT>(P, sk, lane, my0, len, M, sig, sv, msg);
+        if (wb) write_ms_if_last<NPT, uint64_t>(st, i, lane, g0, len, pos_after, sv, msg);
         encrypt64<NPT>(P, pg, msg, x);
-        store_group<NPT, uint64_t, uint64_t>(P, cdst, rdst, my0, per_inst, vec_ok, x);
-        write_c_if_last<NPT, uint64_t>(st, i, lane, g0, per_inst, x);
+        store_group<NPT, uint64_t, uint64_t>(P, cdst, rdst, my0, len, vec_ok, x);
+        if (wb) write_c_if_last<NPT, uint64_t>(st, i, lane, g0, len, x);
     }
+}
+
+// Pre-pass of a split launch: warp w sums the skips of chunk w % K of slot
+// w / K (mod that instance's n; every chunk but the last), and the first warp
+// of each slot records the slot's start message and skip (see SplitArgs).
+// sk holds the constants of 8 numbers per lane.
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+chunk_sums_kernel(const DevInst *__restrict__ inst, DevState st, SkipConst sk, uint64_t first,
+                  uint64_t num, uint64_t per_inst, const uint32_t *__restrict__ order, SplitArgs sp,
+                  uint64_t *__restrict__ scratch)
+{
+    constexpr int NPT = 8;
+    constexpr uint64_t G = 32 * NPT;
+    const int lane = threadIdx.x & 31;
+    const uint64_t w = (uint64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (w >= (num << sp.log2K)) return;
+    const uint64_t q = w >> sp.log2K;
+    const uint32_t cidx = (uint32_t)(w & (sp.K - 1));
+    const uint64_t i = first + (order ? order[q] : q);
+    uint64_t *h = scratch + q * (sp.K + 1);
+    const uint32_t s = (uint32_t)st.s[i];
+    if (cidx == 0 && lane == 0) {
+        h[0] = st.m[i];
+        h[1] = s;
+    }
+    if (cidx + 1 == sp.K) return;                     // no chunk starts after the last
+    const uint64_t n = inst[i].n;
+    const uint64_t b0 = (uint64_t)cidx * sp.Lc;
+    const uint64_t len = b0 >= per_inst ? 0 : min(sp.Lc, per_inst - b0);
+    uint32_t sig = mont32(skip_chunk(sk, sp, s, cidx), sk.lane[lane], sk.p, sk.pinv);
+    uint64_t S = 0;
+    for (uint64_t g0 = 0; g0 < len; g0 += G) {
+        const uint64_t my0 = g0 + (uint64_t)NPT * lane;
+        uint32_t t = sig;
+#pragma unroll
+        for (int u = 0; u < NPT; ++u) {
+            t = skip_step(sk, t, false);                  // Eq. 9a
+            if (my0 + u < len) S = addmod64(S, t, n);
+        }
+        sig = skip_step(sk, sig, true);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) S = addmod64(S, __shfl_xor_sync(kFull, S, off), n);
+    if (lane == 0) h[2 + cidx] = S;
 }
 
 static int check_launch(std::string *err, const char *what)
@@ -236,18 +308,22 @@ static int check_launch(std::string *err, const char *what)
 int launch_gen32(const GenArgs &a, void *stream, std::string *err)
 {
     if (a.num == 0 || a.per_inst == 0) return PHPRNG_OK;
-    const uint64_t blocks = (a.num + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    if (a.stats && a.sp.K != 1) {
+        *err = "gen32_kernel: statistics launches are never split";
+        return PHPRNG_EINVAL;
+    }
+    const uint64_t blocks = ((a.num << a.sp.log2K) + kWarpsPerBlock - 1) / kWarpsPerBlock;
     cudaStream_t s = (cudaStream_t)stream;
     if (a.stats) {
         const size_t smem = (2 * kWarpsPerBlock * 32 * kNPT + kWarpsPerBlock * 256) * sizeof(uint32_t);
         if (a.c_is_64)
             gen32_kernel<kNPT, uint64_t, true><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(
                 a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, (uint64_t *)a.c_out, a.r_out,
-                a.vec_ok, a.stats, a.edge, nullptr);
+                a.vec_ok, a.stats, a.edge, nullptr, a.sp);
         else
             gen32_kernel<kNPT, uint32_t, true><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(
                 a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, (uint32_t *)a.c_out, a.r_out,
-                a.vec_ok, a.stats, a.edge, nullptr);
+                a.vec_ok, a.stats, a.edge, nullptr, a.sp);
         int rc = check_launch(err, "gen32_kernel (statistics) launch");
         if (rc != PHPRNG_OK || blocks < 2) return rc;
         stats_edge_kernel<<<(unsigned)((blocks - 1 + 7) / 8), 256, 0, s>>>(
@@ -257,11 +333,11 @@ int launch_gen32(const GenArgs &a, void *stream, std::string *err)
     if (a.c_is_64)
         gen32_kernel<kNPT, uint64_t, false><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(
             a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, (uint64_t *)a.c_out, a.r_out, a.vec_ok,
-            nullptr, nullptr, a.order);
+            nullptr, nullptr, a.order, a.sp);
     else
         gen32_kernel<kNPT, uint32_t, false><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(
             a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, (uint32_t *)a.c_out, a.r_out, a.vec_ok,
-            nullptr, nullptr, a.order);
+            nullptr, nullptr, a.order, a.sp);
     return check_launch(err, "gen32_kernel launch");
 }
 
@@ -274,11 +350,38 @@ uint64_t gen32_edge_words(uint64_t num, uint64_t per_inst)
 int launch_gen64(const GenArgs &a, void *stream, std::string *err)
 {
     if (a.num == 0 || a.per_inst == 0) return PHPRNG_OK;
-    const uint64_t blocks = (a.num + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    const uint64_t blocks = ((a.num << a.sp.log2K) + kWarpsPerBlock - 1) / kWarpsPerBlock;
     gen64_kernel<kNPT64><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, (cudaStream_t)stream>>>(
         a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, (uint64_t *)a.c_out, a.r_out, a.vec_ok,
-        a.order);
+        a.order, a.sp);
     return check_launch(err, "gen64_kernel launch");
+}
+
+int launch_chunk_sums(const GenArgs &a, const SkipConst &sk8, void *stream, std::string *err)
+{
+    if (a.num == 0 || a.per_inst == 0 || a.sp.K < 2) return PHPRNG_OK;
+    const uint64_t blocks = ((a.num << a.sp.log2K) + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    chunk_sums_kernel<<<(unsigned)blocks, kWarpsPerBlock * 32, 0, (cudaStream_t)stream>>>(
+        a.inst, a.st, sk8, a.first, a.num, a.per_inst, a.order, a.sp, (uint64_t *)a.sp.scratch);
+    return check_launch(err, "chunk_sums_kernel launch");
+}
+
+uint64_t gen_resident_warps()
+{
+    static std::mutex mu;
+    static uint64_t cached[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!cached[dev]) {
+        int sms = 0, b = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, gen32_kernel<kNPT, uint32_t, false>,
+                                                      kWarpsPerBlock * 32, 0);
+        cached[dev] = (uint64_t)(sms > 0 ? sms : 1) * (b > 0 ? b : 1) * kWarpsPerBlock;
+    }
+    return cached[dev];
 }
 
 // ---- fused statistics with fixed scratch ------------------------------------

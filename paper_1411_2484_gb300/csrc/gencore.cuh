@@ -39,6 +39,32 @@ __device__ __forceinline__ uint32_t skip_step(const SkipConst &sk, uint32_t s, b
     return mont32(s, group ? sk.aGM : sk.aM, sk.p, sk.pinv);
 }
 
+// s * a^(c Lc) mod p for a plain skip s: the start skip of chunk c of a
+// split launch (square-and-multiply on a^Lc in Montgomery form).
+__device__ __forceinline__ uint32_t skip_chunk(const SkipConst &sk, const SplitArgs &sp, uint32_t s,
+                                               uint32_t c)
+{
+    uint32_t r = sp.oneM, b = sp.aLcM;
+    for (; c; c >>= 1) {
+        if (c & 1) r = mont32(r, b, sk.p, sk.pinv);
+        b = mont32(b, b, sk.p, sk.pinv);
+    }
+    return mont32(s, r, sk.p, sk.pinv);
+}
+
+// Start message of chunk c of slot q: the slot's start message plus the skip
+// sums of chunks 0 .. c-1, mod n (every lane gets it).
+__device__ __forceinline__ uint64_t chunk_message(const SplitArgs &sp, uint64_t q, uint32_t c,
+                                                  uint64_t n, int lane)
+{
+    const uint64_t *h = sp.scratch + q * (sp.K + 1);
+    uint64_t S = 0;
+    for (uint32_t k = lane; k < c; k += 32) S = addmod64(S, h[2 + k], n);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) S = addmod64(S, __shfl_xor_sync(kFullMask, S, off), n);
+    return addmod64(h[0], S, n);
+}
+
 template <int NPT>
 __device__ __forceinline__ void messages32(const DevInst &P, const SkipConst &sk, int lane,
                                            uint64_t my0, uint64_t len, uint32_t &M, uint32_t &sig,

@@ -55,6 +55,21 @@ struct DevState {
 };
 
 // Arguments of one generate launch over instances [first, first+num).
+// Split launch, for calls with too few instances to fill the GPU: every
+// instance is cut into K chunks of Lc numbers (the last chunk shorter, or
+// empty), and warp w runs chunk w % K of instance slot w / K.  A pre-pass
+// (chunk_sums_kernel) leaves per slot q, at scratch[q*(K+1)]: the start
+// message, the start skip, and the skip sums mod n of chunks 0 .. K-2; chunk
+// c then starts from message m + (sums of chunks before it) and skip
+// s a^(c Lc) (Eq. 6 over chunks).  K = 1 is the plain launch.
+struct SplitArgs {
+    uint32_t K = 1, log2K = 0;
+    uint64_t Lc = 0;                   // a multiple of 256
+    uint32_t aLcM = 0;                 // a^Lc * 2^32 mod p
+    uint32_t oneM = 0;                 // 2^32 mod p
+    const uint64_t *scratch = nullptr;
+};
+
 struct GenArgs {
     const DevInst *inst;
     const ExpProg *prog;    // per-instance exponent programs
@@ -71,6 +86,7 @@ struct GenArgs {
     // permutation of 0 .. num-1, heaviest programs first); NULL = identity.
     // Never used with statistics, whose pairs need adjacent instances.
     const uint32_t *order = nullptr;
+    SplitArgs sp;                      // K = 1: no split
 };
 
 // Exact prefix table of the skip generator's cycle (Eq. 7): with
@@ -134,6 +150,10 @@ uint64_t gen32_edge_words(uint64_t num, uint64_t per_inst);
 uint64_t gen32_fixed_edge_words();
 int launch_gen32_stats_fixed(const GenArgs &a, int dev, void *stream, std::string *err);
 int launch_gen64(const GenArgs &a, void *stream, std::string *err);
+// Split launches: the pre-pass (sk8 = the NPT 8 skip constants) and the
+// number of warps the 32-bit generator keeps resident on the current device.
+int launch_chunk_sums(const GenArgs &a, const SkipConst &sk8, void *stream, std::string *err);
+uint64_t gen_resident_warps();
 
 // ---- skip-ahead (skip.cu) ------------------------------------------------
 SkipTable derive_skip_table(uint64_t p, uint64_t a);   // constants; T, P set by the caller

@@ -311,6 +311,31 @@ def test_launch_order_over_ranges(ph, torch):
         ph.phprng_destroy(ctx)
 
 
+@pytest.mark.parametrize("n32,n64,calls", [(3, 0, [100003, 5000, 2048, 2047]),
+                                            (2, 2, [50001, 4096, 1]),
+                                            (1, 0, [1 << 22])],
+                         ids=["32bit_ragged", "mixed", "one_instance_4M"])
+def test_split_launches(ph, torch, n32, n64, calls):
+    """Calls with few instances cut every instance into chunks whose start
+    message comes from a pre-pass of skip sums: outputs, continuation and
+    states equal the oracle's stream, for ragged and chunk-sized lengths."""
+    tables = [workloads.draw_instances(n32, seed=501 + n32)]
+    if n64:
+        tables.append(workloads.draw_instances(n64, width=64, seed=601 + n64))
+    inst = workloads.concat_instances(*tables)
+    count = n32 + n64
+    width = 32 if n64 == 0 else 0
+    ctx = ph.phprng_create(width, inst, 0)
+    try:
+        orc = OracleStreams(inst)
+        for per in calls:
+            c, r = generate(ph, torch, ctx, width, 0, count, per)
+            assert_same(c, r, *orc.next(0, count, per))
+        check_state(ph, ctx, orc, 0, count, [sum(calls)] * count)
+    finally:
+        ph.phprng_destroy(ctx)
+
+
 def test_plain32_full_size_first_call_and_64_calls(ph, torch):
     """65,536 instances x 4,096 numbers per call, the benchmark's launch:
     the whole first call against the oracle, then 63 more R-only calls and
