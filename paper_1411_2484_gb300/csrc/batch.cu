@@ -35,15 +35,19 @@ __device__ __forceinline__ void run_tile32(const BatchArgs &a, const DevInst &P,
     CT *cdst = a.c_base ? (CT *)a.c_base + T.c_off : nullptr;
     double *rdst = a.r_base ? a.r_base + T.r_off : nullptr;
     const uint64_t len = T.len;
+    uint32_t x[NPT], sig_last = sig;
+    uint64_t g_last = 0;
     for (uint64_t g0 = 0; g0 < len; g0 += G) {
-        uint32_t sv[NPT], msg[NPT], x[NPT];
+        uint32_t sv[NPT], msg[NPT];
         const uint64_t my0 = g0 + (uint64_t)NPT * lane;
+        sig_last = sig;
+        g_last = g0;
         messages32<NPT>(P, sk, lane, my0, len, M, sig, sv, msg);
-        if (wb) write_ms_if_last<NPT, uint32_t>(a.st, i, lane, g0, len, T.start + len, sv, msg);
         encrypt32<NPT>(P, pg, msg, x);
         store_group<NPT, CT, uint32_t>(P, cdst, rdst, my0, len, vec_ok, x);
-        if (wb) write_c_if_last<NPT, uint32_t>(a.st, i, lane, g0, len, x);
     }
+    if (wb) write_state_after<NPT, uint32_t, uint32_t>(a.st, sk, i, lane, g_last, len, T.start + len, M,
+                                                       sig_last, x);
 }
 
 template <int NPT>
@@ -58,16 +62,21 @@ __device__ __forceinline__ void run_tile64(const BatchArgs &a, const DevInst &P,
     uint64_t *cdst = a.c_base ? (uint64_t *)a.c_base + T.c_off : nullptr;
     double *rdst = a.r_base ? a.r_base + T.r_off : nullptr;
     const uint64_t len = T.len;
+    uint64_t x[NPT];
+    uint32_t sig_last = sig;
+    uint64_t g_last = 0;
     for (uint64_t g0 = 0; g0 < len; g0 += G) {
         uint32_t sv[NPT];
-        uint64_t msg[NPT], x[NPT];
+        uint64_t msg[NPT];
         const uint64_t my0 = g0 + (uint64_t)NPT * lane;
+        sig_last = sig;
+        g_last = g0;
         messages64<NPT>(P, sk, lane, my0, len, M, sig, sv, msg);
-        if (wb) write_ms_if_last<NPT, uint64_t>(a.st, i, lane, g0, len, T.start + len, sv, msg);
         encrypt64<NPT>(P, pg, msg, x);
         store_group<NPT, uint64_t, uint64_t>(P, cdst, rdst, my0, len, vec_ok, x);
-        if (wb) write_c_if_last<NPT, uint64_t>(a.st, i, lane, g0, len, x);
     }
+    if (wb) write_state_after<NPT, uint64_t, uint64_t>(a.st, sk, i, lane, g_last, len, T.start + len, M,
+                                                       sig_last, x);
 }
 
 template <int NPT32, typename CT>

@@ -107,6 +107,25 @@ gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
         __syncwarp();
     }
 
+    if (!STATS) {
+        // The plain loop carries nothing but the group step and the stores;
+        // the lane that owns the call's last number writes the state after
+        // it, once, after the loop.
+        uint32_t x[NPT], sig_last = sig;
+        uint64_t g_last = 0;
+        for (uint64_t g0 = 0; g0 < len; g0 += G) {
+            uint32_t sv[NPT], msg[NPT];
+            const uint64_t my0 = g0 + (uint64_t)NPT * lane;
+            sig_last = sig;
+            g_last = g0;
+            messages32<NPT>(P, sk, lane, my0, len, M, sig, sv, msg);
+            encrypt32<NPT>(P, pg, msg, x);
+            store_group<NPT, CT, uint32_t>(P, cdst, rdst, my0, len, vec_ok, x);
+        }
+        if (wb) write_state_after<NPT, uint32_t, uint32_t>(st, sk, i, lane, g_last, len, pos_after, M,
+                                                           sig_last, x);
+        return;
+    }
     for (uint64_t g0 = 0; g0 < len; g0 += G) {
         uint32_t sv[NPT], msg[NPT], x[NPT];
         const uint64_t my0 = g0 + (uint64_t)NPT * lane;
@@ -239,16 +258,21 @@ gen64_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
     const uint64_t pos_after = wb ? st.pos[i] + per_inst : 0;
     uint64_t *cdst = c_out ? c_out + j * per_inst + b0 : nullptr;
     double *rdst = r_out ? r_out + j * per_inst + b0 : nullptr;
+    uint64_t x[NPT];
+    uint32_t sig_last = sig;
+    uint64_t g_last = 0;
     for (uint64_t g0 = 0; g0 < len; g0 += G) {
         uint32_t sv[NPT];
-        uint64_t msg[NPT], x[NPT];
+        uint64_t msg[NPT];
         const uint64_t my0 = g0 + (uint64_t)NPT * lane;
+        sig_last = sig;
+        g_last = g0;
         messages64<NPT>(P, sk, lane, my0, len, M, sig, sv, msg);
-        if (wb) write_ms_if_last<NPT, uint64_t>(st, i, lane, g0, len, pos_after, sv, msg);
         encrypt64<NPT>(P, pg, msg, x);
         store_group<NPT, uint64_t, uint64_t>(P, cdst, rdst, my0, len, vec_ok, x);
-        if (wb) write_c_if_last<NPT, uint64_t>(st, i, lane, g0, len, x);
     }
+    if (wb) write_state_after<NPT, uint64_t, uint64_t>(st, sk, i, lane, g_last, len, pos_after, M, sig_last,
+                                                       x);
 }
 
 // Pre-pass of a split launch: warp w sums the skips of chunk w % K of slot

@@ -14,10 +14,9 @@
 // is formed where it is stored or consumed (real_of).  Numbers past `len` are
 // computed but excluded from the sums that carry into later numbers.
 //
-// The kernels call messages32/64, then (when the run ends in this group) let
-// the owning lane record m and s of the last number, then encrypt: so the
-// skips and messages need not stay in registers through the exponentiation,
-// and only the ciphertext of the last number is written after it.
+// The kernels call messages32/64 and encrypt32/64 per group and write the
+// state after the run once, after the loop (write_state_after), so that no
+// skip or message has to stay in registers through the exponentiation.
 #pragma once
 #include "arith.cuh"
 #include "internal.h"
@@ -233,6 +232,29 @@ __device__ __forceinline__ void write_c_if_last(DevState st, uint64_t i, int lan
 #pragma unroll
     for (int u = 0; u < NPT; ++u)
         if (u == ul) st.c[i] = x[u];
+}
+
+// State after a run, written once after the group loop by the lane that owns
+// the run's last number: M (the message after the last group, which is the
+// last number's message), that number's skip -- sig_group (the lane's skip
+// entering the last group, g0) stepped ul+1 times -- and its ciphertext.
+template <int NPT, typename XT, typename MT>
+__device__ __forceinline__ void write_state_after(DevState st, const SkipConst &sk, uint64_t i, int lane,
+                                                  uint64_t g0, uint64_t len, uint64_t pos_after, MT M,
+                                                  uint32_t sig_group, const XT (&x)[NPT])
+{
+    int ul;
+    if (!owns_last<NPT>(lane, g0, len, &ul)) return;
+    uint32_t s = sig_group;
+    for (int u = 0; u <= ul; ++u) s = skip_step(sk, s, false);
+    XT c = x[0];
+#pragma unroll
+    for (int u = 1; u < NPT; ++u)
+        if (u == ul) c = x[u];
+    st.m[i] = M;
+    st.s[i] = s;
+    st.c[i] = c;
+    st.pos[i] = pos_after;
 }
 
 }  // namespace phprng
