@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=64)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--modes", default="fused,wide64,batched,served",
+    ap.add_argument("--modes", default="fused,small_e,wide64,batched,served",
                     help="comma-separated extra measurements after the headline, or 'none'")
     return ap.parse_args()
 
@@ -183,6 +183,42 @@ def mode_fused(ph, torch, ctx, N, per, stream, steps):
                steps)
     return {"value": N * per / ms * 1e3, "unit": "PRNs/s", "ms_per_call": ms,
             "workload": "plain32 65,536 x 4,096, statistics only (72 MB/call)"}
+
+
+def mode_small_e(ph, torch, stream, peak):
+    """The plain 32-bit scale with e = 9 for every instance (the paper's
+    recommended exponent): R to HBM, 2 GiB per call.  Few products per number,
+    so the roofline is the lower of the multiplier and the HBM write bound."""
+    from paper_1411_2484_gb300 import workloads
+    inst = workloads.workload_instances("plain32_e9_65536x4096")
+    N, per = 65536, 4096
+    ctx = ph.phprng_create(32, inst, ph.PHPRNG_REQUIRE_SAFE_PRIME, stream)
+    try:
+        r = torch.empty(N * per, dtype=torch.float64, device="cuda")
+        ms = timed(torch, stream, lambda: ph.phprng_generate(ctx, 0, N, per, None, r, None, stream),
+                   16, warmup=3)
+    finally:
+        ph.phprng_destroy(ctx)
+    prn_s = N * per / ms * 1e3
+    mul_bound = peak * 1e12 / muls_per_number(9, False)
+    hbm = measured_hbm_gbs()
+    hbm_bound = (hbm or 0) * 1e9 / 8
+    if hbm and hbm_bound < mul_bound:
+        roof = {"bound": "hbm", "achieved": prn_s * 8 / 1e9, "peak": hbm, "unit": "GB/s",
+                "frac": prn_s * 8 / 1e9 / hbm, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+    else:
+        roof = {"bound": "alu", "achieved": prn_s * muls_per_number(9, False) / 1e12, "peak": peak,
+                "unit": "T mul32/s", "frac": prn_s / mul_bound}
+    return {"value": prn_s, "unit": "PRNs/s", "ms_per_call": ms,
+            "workload": "65,536 safe 32-bit primes, e = 9, x 4,096 numbers per call (R, 2 GiB)",
+            "roofline": roof}
+
+
+def measured_hbm_gbs():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return None
 
 
 def mode_wide64(ph, torch, stream, peak):
@@ -447,6 +483,7 @@ def main():
         modes = {}
         wanted = [] if args.modes == "none" else args.modes.split(",")
         for name, fn in (("fused", lambda: mode_fused(ph, torch, ctx2, N, per, stream, 8)),
+                         ("small_e", lambda: mode_small_e(ph, torch, stream, PEAK_TMULS)),
                          ("wide64", lambda: mode_wide64(ph, torch, stream, PEAK_TMULS)),
                          ("batched", lambda: mode_batched(ph, torch, stream)),
                          ("served", lambda: mode_served(ph, torch))):

@@ -356,6 +356,21 @@ PH_HD uint32_t hist_bin256(double R)
     return bin > 255u ? 255u : bin;
 }
 
+// floor(256 (c+1)/(n+1)) from integers, for n < 2^32: with y = n+1
+// normalised to yN = y 2^(32-ybits) (top bit set) and vN = (c+1) 2^(32-ybits)
+// < yN, the estimate floor(vN r / 2^32) with r = floor(2^40 / yN) is the bin or
+// one below it (r is short of 2^40/yN by less than 1, and vN < 2^32), and one
+// exact comparison decides.  Equal to hist_bin256 of the correctly rounded R:
+// a rounding can only reach a multiple of 1/256 that R equals exactly, since
+// a nonzero |k/256 - (c+1)/(n+1)| is at least 2^-40, far above half an ulp.
+PH_HD uint32_t hist_bin256_int(uint32_t c, uint32_t yN, uint32_t ybits, uint32_t r)
+{
+    const uint32_t vN = (c + 1) << (32 - ybits);
+    uint32_t est = umulhi32(vN, r);
+    if ((uint64_t)(est + 1) * yN <= ((uint64_t)vN << 8)) ++est;
+    return est;
+}
+
 // The same double, deciding the rounding from an 11-bit fraction: with
 // W = floor((2^95 - 1) / yN), Xf = floor(A W / 2^(32-extra)) is the exact
 // quotient X = A 2^(52+extra) / yN scaled by 2^11 (so Xf < 2^64) and short of

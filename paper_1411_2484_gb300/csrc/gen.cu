@@ -100,6 +100,7 @@ gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
     uint32_t *hist = smem + 2 * W * (32 * NPT) + warp * 256;
     uint64_t X = 0;      // < 2^63: per_inst < 2^31 numbers of at most 2^32 each
     u128 Y = 0, Z = 0;
+    const uint32_t binr = (uint32_t)(P.V >> 44);      // floor(2^40 / yN), for the histogram
     const bool has_next = w + 1 < num;
     const bool pair_in_block = has_next && warp + 1 < W;
     if (STATS) {
@@ -146,7 +147,7 @@ gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
                         const uint64_t v = (uint64_t)x[u] + 1;
                         X += v;
                         Y += (u128)(v * v);
-                        atomicAdd(&hist[hist_bin256(real_of(P, x[u]))], 1u);
+                        atomicAdd(&hist[hist_bin256_int(x[u], P.yN, P.ybits, binr)], 1u);
                     }
                 }
                 if (edge && ((warp == W - 1 && has_next) || (warp == 0 && blockIdx.x > 0))) {

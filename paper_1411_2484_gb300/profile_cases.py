@@ -5,6 +5,7 @@
 CASE is one of
   plain32   65,536 instances x 4,096 numbers, R to HBM (2 GiB)     gen32_kernel
   fused32   the same instances, statistics only                      gen32_kernel (STATS)
+  small_e   65,536 instances with e = 9 x 4,096 numbers, R (2 GiB)   gen32_kernel
   wide64    4,096 64-bit instances x 4,096 numbers, R (128 MiB)      gen64_kernel
   batched   2,000 instances (80 % 32-bit), lengths log-uniform in
             [1, 2^18], offsets in [0, 2^40), R (about 0.4 GiB)       batch_kernel
@@ -23,7 +24,7 @@ from paper_1411_2484_gb300 import workloads
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["plain32", "fused32", "wide64", "batched"])
+    ap.add_argument("case", choices=["plain32", "fused32", "small_e", "wide64", "batched"])
     ap.add_argument("--repeat", type=int, default=3)
     args = ap.parse_args()
     s = torch.cuda.current_stream()
@@ -38,6 +39,13 @@ def main():
         else:
             sb = torch.empty(N * ph.STATS_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
             run = lambda: ph.phprng_generate(ctx, 0, N, per, None, None, sb, s)
+        numbers = N * per
+    elif args.case == "small_e":
+        inst = workloads.workload_instances("plain32_e9_65536x4096")
+        N, per = 65536, 4096
+        ctx = ph.phprng_create(32, inst, ph.PHPRNG_REQUIRE_SAFE_PRIME, s)
+        r = torch.empty(N * per, dtype=torch.float64, device="cuda")
+        run = lambda: ph.phprng_generate(ctx, 0, N, per, None, r, None, s)
         numbers = N * per
     elif args.case == "wide64":
         inst = workloads.workload_instances("wide64_4096x2^20")

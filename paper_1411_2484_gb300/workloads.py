@@ -207,6 +207,10 @@ WORKLOADS = {
     # 65,536 instances x 4,096 numbers per call, 64 calls via stored state.
     "plain32_65536x4096x64": dict(width=32, instances=65536, per_inst=4096, calls=64,
                                   seed=0x5EED0001),
+    # The same scale with the paper's small exponent e = 9 for every instance
+    # (its recommended setting; 4 products per encryption instead of ~40).
+    "plain32_e9_65536x4096": dict(width=32, instances=65536, per_inst=4096, calls=64,
+                                  seed=0x5EED0009, exponent=9),
     # 4,096 64-bit safe primes x 2^20 numbers each.
     "wide64_4096x2^20": dict(width=64, instances=4096, per_inst=1 << 20, calls=1,
                              seed=0x5EED0002),
@@ -237,4 +241,5 @@ WORKLOADS["batched_20000_mixed"] = dict(instances32=16000, instances64=4000, max
 def workload_instances(name, count=None):
     """Instance table of a named workload (optionally only its first `count`)."""
     w = WORKLOADS[name]
-    return draw_instances(count or w["instances"], width=w["width"], seed=w["seed"])
+    return draw_instances(count or w["instances"], width=w["width"], seed=w["seed"],
+                          exponent=w.get("exponent"))

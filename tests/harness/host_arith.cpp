@@ -99,4 +99,16 @@ void h_hist_bin_many(const double *r, uint32_t *out, uint64_t count)
 {
     for (uint64_t i = 0; i < count; ++i) out[i] = hist_bin256(r[i]);
 }
+
+// floor(256 (c+1)/(n+1)) the integer way, with the per-instance constants
+// derived as the library derives them.
+void h_hist_bin_int_many(const uint64_t *n, const uint64_t *c, uint32_t *out, uint64_t count)
+{
+    for (uint64_t i = 0; i < count; ++i) {
+        phprng_instance in{n[i], 3, 2, 1, 0, 1};
+        ExpProg pg;
+        const DevInst d = derive_inst(in, 0, &pg);
+        out[i] = hist_bin256_int((uint32_t)c[i], d.yN, d.ybits, (uint32_t)(d.V >> 44));
+    }
+}
 }

@@ -336,6 +336,44 @@ def test_split_launches(ph, torch, n32, n64, calls):
         ph.phprng_destroy(ctx)
 
 
+def test_small_exponents(ph, torch):
+    """The paper's small exponents (e = 3, 5, 9, 17) and 65537, mixed in one
+    table with random ones: ragged calls and continuation against the oracle."""
+    tables = [workloads.draw_instances(6, seed=700 + e, exponent=e) for e in (3, 5, 9, 17, 65537)]
+    tables.append(workloads.draw_instances(6, seed=799))
+    inst = workloads.concat_instances(*tables)
+    count = len(inst["n"])
+    ctx = ph.phprng_create(32, inst, 0)
+    try:
+        orc = OracleStreams(inst)
+        for per in (4096, 1001, 3):
+            c, r = generate(ph, torch, ctx, 32, 0, count, per)
+            assert_same(c, r, *orc.next(0, count, per))
+        check_state(ph, ctx, orc, 0, count, [5100] * count)
+    finally:
+        ph.phprng_destroy(ctx)
+
+
+def test_small_exponent_full_size_sampled(ph, torch):
+    """65,536 instances with e = 9 x 4,096 numbers (the small-exponent bench
+    launch): sampled instances against the oracle, R on every number."""
+    inst = workloads.workload_instances("plain32_e9_65536x4096")
+    N, per = 65536, 4096
+    assert np.all(inst["e"] == 9)
+    ctx = ph.phprng_create(32, inst, ph.PHPRNG_REQUIRE_SAFE_PRIME)
+    try:
+        c, r = generate(ph, torch, ctx, 32, 0, N, per)
+        sample = np.unique(np.concatenate([[0, 1, N - 1], np.random.default_rng(9).choice(N, 61)]))
+        rows = workloads.instance_rows(inst)[sample]
+        cr, rr, _, _ = oracle.generate_many(rows, per, threads=THREADS)
+        assert_same(c[sample], r[sample], cr, rr)
+        n1 = (inst["n"] + np.uint64(1)).astype(np.float64)[:, None]
+        ref = (c + np.uint64(1)).astype(np.float64) / n1     # both exact in double: RN quotient
+        assert np.array_equal(ref.view(np.uint64), r.view(np.uint64))
+    finally:
+        ph.phprng_destroy(ctx)
+
+
 def test_plain32_full_size_first_call_and_64_calls(ph, torch):
     """65,536 instances x 4,096 numbers per call, the benchmark's launch:
     the whole first call against the oracle, then 63 more R-only calls and

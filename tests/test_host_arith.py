@@ -168,6 +168,45 @@ def test_hist_bin_matches_floor(h):
     assert np.array_equal(out, ref)
 
 
+def test_hist_bin_integer_equals_floor(h):
+    """The fused mode's integer bin equals floor(256 (c+1)/(n+1)), exact
+    multiples of 1/256 and tiny moduli included."""
+    h.h_hist_bin_int_many.argtypes = [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                                      ctypes.POINTER(ctypes.c_uint32), ctypes.c_uint64]
+    rng = np.random.default_rng(21)
+    k = 200000
+    n = np.concatenate([rng.integers(3, 1 << 32, k // 2, dtype=np.uint64) | np.uint64(1),
+                        rng.integers(3, 3000, k // 2, dtype=np.uint64) | np.uint64(1)])
+    n = np.minimum(n, np.uint64((1 << 32) - 5))
+    c = (rng.integers(0, 1 << 62, k, dtype=np.uint64) % n).astype(np.uint64)
+    c[::5] = n[::5] - np.uint64(1)
+    c[::9] = 0
+    # (c+1)/(n+1) exactly k'/256: n+1 = 256 t, c+1 = k' t
+    ex_n, ex_c = [], []
+    rr = random.Random(22)
+    while len(ex_n) < 4000:
+        t = rr.randrange(1, 1 << 24)
+        nn = 256 * t - 1
+        kk = rr.randrange(1, 256)
+        ex_n.append(nn)
+        ex_c.append(kk * t - 1)
+        ex_n.append(nn)
+        ex_c.append(kk * t - 2 if kk * t >= 2 else 0)
+    for nn in (3, 7, 31, 127, 8191, 131071, 524287):      # n + 1 a power of two
+        for cc in range(0, nn, max(1, nn // 300)):
+            ex_n.append(nn)
+            ex_c.append(cc)
+    n = np.concatenate([n, np.array(ex_n, dtype=np.uint64)])
+    c = np.concatenate([c, np.array(ex_c, dtype=np.uint64)])
+    out = np.empty(n.size, dtype=np.uint32)
+    P64 = ctypes.POINTER(ctypes.c_uint64)
+    h.h_hist_bin_int_many(n.ctypes.data_as(P64), c.ctypes.data_as(P64),
+                          out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), n.size)
+    ref = np.array([(256 * (int(ci) + 1)) // (int(ni) + 1) for ni, ci in zip(n, c)], dtype=np.uint32)
+    bad = np.flatnonzero(out != ref)
+    assert bad.size == 0, (n[bad[0]], c[bad[0]], out[bad[0]], ref[bad[0]])
+
+
 def test_real32_fast_equals_ieee_division(h):
     """The fast rounding decision, and its exact fallback band (forced)."""
     rng = np.random.default_rng(11)
