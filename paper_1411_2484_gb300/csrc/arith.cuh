@@ -382,14 +382,17 @@ PH_HD uint32_t hist_bin256_int(uint32_t c, uint32_t yN, uint32_t ybits, uint32_t
 // decides it (about 1 number in 700).
 PH_HD double real32_fast(uint32_t c, uint32_t yN, uint32_t ybits, uint64_t W)
 {
-    uint32_t x = c + 1;
-    int xb = 32 - clz32(x);
-    uint32_t A = x << (32 - xb);
-    uint32_t extra = A < yN ? 1u : 0u;
-    int E = xb - (int)ybits - (int)extra;
-    const uint64_t P = (uint64_t)A * (uint32_t)W;             // A * w0
-    const uint64_t H = (uint64_t)A * (uint32_t)(W >> 32);     // A * w1
-    const uint64_t Xf = (H << extra) + (P >> (32 - extra));
+    const uint32_t x = c + 1;
+    const int lz = clz32(x);
+    const uint32_t A = x << lz;
+    const uint32_t extra = A < yN ? 1u : 0u;
+    const int E = 32 - lz - (int)ybits - (int)extra;
+    // Xf = floor(A W / 2^(32 - extra)): H = A w1 + floor(A w0 / 2^32) (< 2^64,
+    // and < 2^63 when extra = 1, as A/yN < 1 then), shifted by extra with the
+    // next bit of A w0 shifted in.
+    const uint64_t P = (uint64_t)A * (uint32_t)W;                        // A * w0
+    const uint64_t H = (uint64_t)A * (uint32_t)(W >> 32) + (P >> 32);    // A * w1 + hi
+    const uint64_t Xf = (H << extra) | (uint64_t)(((uint32_t)P >> 31) & extra);
     uint64_t Q = Xf >> 11;
     const uint32_t f = (uint32_t)Xf & 0x7FFu;
     if (f >= 1024u) {

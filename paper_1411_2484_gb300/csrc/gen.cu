@@ -225,7 +225,7 @@ stats_edge_kernel(const DevInst *__restrict__ inst, const uint32_t *__restrict__
 }
 
 template <int NPT>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 2)
 gen64_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, DevState st,
              SkipConst sk, uint64_t first, uint64_t num, uint64_t per_inst,
              uint64_t *__restrict__ c_out, double *__restrict__ r_out, int vec_ok,

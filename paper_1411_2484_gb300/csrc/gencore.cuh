@@ -125,18 +125,37 @@ __device__ __forceinline__ void messages64(const DevInst &P, const SkipConst &sk
     sig = skip_step(sk, sig, true);
 }
 
-// Eq. 9c for the lane's NPT messages.
+// Eq. 9c for the lane's NPT messages.  Exponents e = 2^t + 1 (the paper's
+// recommended 9 and 17, also 3, 5, 65537) take a straight chain -- t
+// squarings and one product with m -- without reading a program; it is the
+// chain the host compiles for them, so the exit constant K is the same.
+template <int NPT, typename W>
+__device__ __forceinline__ void encrypt(const DevInst &P, const ExpProg &pg, const W (&msg)[NPT],
+                                        W (&x)[NPT])
+{
+    const W n = (W)P.n, ninv = (W)P.ninv, K = (W)P.K;
+    if (P.fermat) {
+#pragma unroll
+        for (int u = 0; u < NPT; ++u) x[u] = msg[u];
+        for (uint32_t q = P.fermat; q > 0; --q) mont_sqr_vec<NPT>(x, n, ninv);
+        mont_vec<NPT>(x, msg, n, ninv);
+#pragma unroll
+        for (int u = 0; u < NPT; ++u) x[u] = mont(x[u], K, n, ninv);
+        return;
+    }
+    modexp_prog<NPT, W>(x, msg, pg, n, ninv, K);
+}
 template <int NPT>
 __device__ __forceinline__ void encrypt32(const DevInst &P, const ExpProg &pg, const uint32_t (&msg)[NPT],
                                           uint32_t (&x)[NPT])
 {
-    modexp_prog<NPT, uint32_t>(x, msg, pg, (uint32_t)P.n, (uint32_t)P.ninv, (uint32_t)P.K);
+    encrypt<NPT, uint32_t>(P, pg, msg, x);
 }
 template <int NPT>
 __device__ __forceinline__ void encrypt64(const DevInst &P, const ExpProg &pg, const uint64_t (&msg)[NPT],
                                           uint64_t (&x)[NPT])
 {
-    modexp_prog<NPT, uint64_t>(x, msg, pg, P.n, P.ninv, P.K);
+    encrypt<NPT, uint64_t>(P, pg, msg, x);
 }
 
 // R = (c+1)/(n+1) (Eq. 9d): integer-built and correctly rounded for 32-bit

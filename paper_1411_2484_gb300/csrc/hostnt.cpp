@@ -316,9 +316,15 @@ DevInst derive_inst(const phprng_instance &in, int wide, ExpProg *prog)
     memset(&d, 0, sizeof d);
     d.n = in.n;
     d.e = in.e;
-    d.ebits = (uint32_t)bitlen(in.e);
+    // e = 2^t + 1: the kernels run the chain of t squarings and one product
+    // directly; its program (windows of one bit) has the same exit constant.
+    const bool fermat = in.e >= 3 && ((in.e - 1) & (in.e - 2)) == 0;
+    d.fermat = fermat ? (uint32_t)(bitlen(in.e - 1) - 1) : 0u;
     d.wide = wide ? 1u : 0u;
-    *prog = best_program(in.e);
+    if (fermat)
+        build_program(in.e, 1, prog);
+    else
+        *prog = best_program(in.e);
     if (!wide) {
         d.ninv = (uint32_t)inv_mod_2_64(in.n);
         d.K = mont_exit_constant(in.n, *prog, 32);

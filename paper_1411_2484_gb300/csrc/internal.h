@@ -30,7 +30,7 @@ struct alignas(16) DevInst {
     uint64_t V;      // floor(2^84 / yN): reciprocal for the integer-built R (32-bit path)
     uint32_t yN;     // (n+1) << (32 - bitlen(n+1)), normalised divisor (32-bit path)
     uint32_t ybits;  // bitlen(n+1)
-    uint32_t ebits;  // bitlen(e)
+    uint32_t fermat; // t when e = 2^t + 1 (straight chain of t squarings and one product), else 0
     uint32_t wide;   // 0: 32-bit path, 1: 64-bit path
     uint64_t aux;    // 64-bit path: 2^128 mod n, so x*y mod n = mont64(mont64(x, y), aux);
                      // 32-bit path: floor((2^95 - 1) / yN), the reciprocal of real32_fast

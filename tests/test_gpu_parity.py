@@ -352,6 +352,17 @@ def test_small_exponents(ph, torch):
         check_state(ph, ctx, orc, 0, count, [5100] * count)
     finally:
         ph.phprng_destroy(ctx)
+    tables = [workloads.draw_instances(3, width=64, seed=720 + e, exponent=e) for e in (3, 17, 65537)]
+    tables.append(workloads.draw_instances(3, width=64, seed=799))
+    inst = workloads.concat_instances(*tables)
+    ctx = ph.phprng_create(64, inst, 0)
+    try:
+        orc = OracleStreams(inst)
+        for per in (1000, 129):
+            c, r = generate(ph, torch, ctx, 64, 0, 12, per)
+            assert_same(c, r, *orc.next(0, 12, per))
+    finally:
+        ph.phprng_destroy(ctx)
 
 
 def test_small_exponent_full_size_sampled(ph, torch):
