@@ -177,6 +177,20 @@ int phprng_generate_stats_noalloc(phprng_ctx *ctx, uint64_t first, uint64_t num_
 int phprng_skip(phprng_ctx *ctx, const uint64_t *inst_ids, const uint64_t *k, uint64_t cnt,
                 void *cuda_stream);
 
+/* Moves instance inst_ids[i] to absolute stream position pos[i], forward or
+ * backward: afterwards its next number is number pos[i]+1 of the stream
+ * counted from its seed, and its state (m, s, c) is the one generation would
+ * have left there (c = 0 at position 0).  Both directions use Eq. 7 with the
+ * prefix table: backward by k from cycle position L, the earlier state sits at
+ * L' = L - k mod (p-1), with s' = a^L' and m' = m - (q p(p-1)/2 +
+ * sum_{j=1..r} a^(L'+j) mod p) mod n.  With phprng_get_state this saves and
+ * restores streams (save the position, seek back to it later).  inst_ids and
+ * pos are host arrays of cnt entries; when an instance appears more than once
+ * its last entry counts.  Asynchronous on cuda_stream; builds the prefix table
+ * at the first call as phprng_skip does. */
+int phprng_seek(phprng_ctx *ctx, const uint64_t *inst_ids, const uint64_t *pos, uint64_t cnt,
+                void *cuda_stream);
+
 /* ---------------------------------------------------------------- batches */
 
 /* One request of a batch: `len` consecutive numbers of instance `inst`,

@@ -35,7 +35,7 @@ PHPRNG_ALLOW_SHARED_N = 0x2
 
 EXPORTED = [
     "phprng_create", "phprng_create_seeded", "phprng_destroy", "phprng_last_error",
-    "phprng_status_string", "phprng_generate", "phprng_skip", "phprng_get_state",
+    "phprng_status_string", "phprng_generate", "phprng_skip", "phprng_seek", "phprng_get_state",
     "phprng_is_prime", "phprng_validate", "phprng_draw_instances", "phprng_microbench",
     "phprng_plan_create", "phprng_plan_launch", "phprng_plan_launch_graph",
     "phprng_plan_autotune", "phprng_plan_tuning", "phprng_plan_destroy", "phprng_generate_batch",
@@ -132,6 +132,7 @@ def _load():
         lib.phprng_generate.argtypes = [vp, u64, u64, u64, vp, vp, vp, vp]
         lib.phprng_generate_stats_noalloc.argtypes = [vp, u64, u64, u64, vp, vp]
         lib.phprng_skip.argtypes = [vp, P64, P64, u64, vp]
+        lib.phprng_seek.argtypes = [vp, P64, P64, u64, vp]
         lib.phprng_get_state.argtypes = [vp, u64, P_inst, P64, P64, vp]
         lib.phprng_is_prime.argtypes = [u64]
         lib.phprng_validate.argtypes = [i32, P_inst, u64, u32, P64]
@@ -253,6 +254,17 @@ def phprng_skip(ctx, inst_ids, k, stream=None):
         raise ValueError("inst_ids and k differ in length")
     P64 = ctypes.POINTER(ctypes.c_uint64)
     _check(_load().phprng_skip(ctx, ids.ctypes.data_as(P64), ks.ctypes.data_as(P64), ids.size,
+                               _stream(stream)), ctx)
+
+
+def phprng_seek(ctx, inst_ids, pos, stream=None):
+    """Moves the listed streams to absolute positions, forward or backward."""
+    ids = np.ascontiguousarray(np.asarray(inst_ids, dtype=np.uint64).reshape(-1))
+    ps = np.ascontiguousarray(np.asarray(pos, dtype=np.uint64).reshape(-1))
+    if ids.size != ps.size:
+        raise ValueError("inst_ids and pos differ in length")
+    P64 = ctypes.POINTER(ctypes.c_uint64)
+    _check(_load().phprng_seek(ctx, ids.ctypes.data_as(P64), ps.ctypes.data_as(P64), ids.size,
                                _stream(stream)), ctx)
 
 
@@ -431,6 +443,9 @@ class Generator:
 
     def skip(self, inst_ids, k, stream=None):
         phprng_skip(self.ctx, inst_ids, k, stream)
+
+    def seek(self, inst_ids, pos, stream=None):
+        phprng_seek(self.ctx, inst_ids, pos, stream)
 
     def state(self, inst, stream=None):
         return phprng_get_state(self.ctx, inst, stream)

@@ -632,7 +632,7 @@ PH_API int phprng_skip(phprng_ctx *ctx, const uint64_t *inst_ids, const uint64_t
         if (i >= ctx->count) return fail(ctx, PHPRNG_EINVAL, "phprng_skip: instance out of range");
         if (slot[i] == UINT64_MAX) {
             slot[i] = reqs.size();
-            reqs.push_back({i, 0});
+            reqs.push_back({i, 0, 0});
         }
         SkipReq &r = reqs[slot[i]];
         if (k[j] > UINT64_MAX - r.k || r.k + k[j] > UINT64_MAX - ctx->pos_host[i])
@@ -656,6 +656,57 @@ PH_API int phprng_skip(phprng_ctx *ctx, const uint64_t *inst_ids, const uint64_t
     if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "phprng_skip: cudaFreeAsync");
     // the pageable upload above completes before cudaMemcpyAsync returns
     for (const SkipReq &r : reqs) ctx->pos_host[r.inst] += r.k;
+    return PHPRNG_OK;
+}
+
+PH_API int phprng_seek(phprng_ctx *ctx, const uint64_t *inst_ids, const uint64_t *pos,
+                       uint64_t cnt, void *cuda_stream)
+{
+    if (!ctx) return fail(nullptr, PHPRNG_EINVAL, "phprng_seek: ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (ctx->serving) return fail(ctx, PHPRNG_EINVAL, "phprng_seek: a server owns the context");
+    if (cnt == 0) return PHPRNG_OK;
+    if (!inst_ids || !pos) return fail(ctx, PHPRNG_EINVAL, "phprng_seek: NULL request arrays");
+    std::vector<SkipReq> reqs;
+    std::vector<uint64_t> slot;
+    try {
+        reqs.reserve(cnt);
+        slot.assign(ctx->count, UINT64_MAX);
+    } catch (const std::bad_alloc &) {
+        return fail(ctx, PHPRNG_ENOMEM, "phprng_seek: host allocation failed");
+    }
+    std::vector<uint64_t> target;
+    for (uint64_t j = 0; j < cnt; ++j) {                // the last target of an instance wins
+        const uint64_t i = inst_ids[j];
+        if (i >= ctx->count) return fail(ctx, PHPRNG_EINVAL, "phprng_seek: instance out of range");
+        if (slot[i] == UINT64_MAX) {
+            slot[i] = reqs.size();
+            reqs.push_back({i, 0, 0});
+            target.push_back(0);
+        }
+        target[slot[i]] = pos[j];
+    }
+    for (size_t r = 0; r < reqs.size(); ++r) {
+        const uint64_t cur = ctx->pos_host[reqs[r].inst];
+        reqs[r].back = target[r] < cur ? 1 : 0;
+        reqs[r].k = target[r] < cur ? cur - target[r] : target[r] - cur;
+    }
+    CU(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    int rc = ensure_skip(ctx, s);
+    if (rc != PHPRNG_OK) return rc;
+    SkipReq *d_reqs = nullptr;
+    CU(ctx, cudaMallocAsync((void **)&d_reqs, reqs.size() * sizeof(SkipReq), s));
+    cudaError_t e = cudaMemcpyAsync(d_reqs, reqs.data(), reqs.size() * sizeof(SkipReq),
+                                    cudaMemcpyHostToDevice, s);
+    std::string err;
+    if (e == cudaSuccess)
+        rc = launch_skip(ctx->d_inst, ctx->d_prog, ctx->st, ctx->d_L0, ctx->tbl, d_reqs, reqs.size(), s, &err);
+    cudaError_t e2 = cudaFreeAsync(d_reqs, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "phprng_seek: request upload");
+    if (rc != PHPRNG_OK) return fail(ctx, rc, "phprng_seek: " + err);
+    if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "phprng_seek: cudaFreeAsync");
+    for (size_t r = 0; r < reqs.size(); ++r) ctx->pos_host[reqs[r].inst] = target[r];
     return PHPRNG_OK;
 }
 

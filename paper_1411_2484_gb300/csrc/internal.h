@@ -110,6 +110,7 @@ struct SkipTable {
 // One skip request after merging duplicates: advance instance `inst` by k.
 struct SkipReq {
     uint64_t inst, k;
+    uint64_t back;          // 0: forward by k; 1: backward by k (k <= position)
 };
 
 // ---- batched persistent launch (batch.cu) ----------------------------------

@@ -492,7 +492,7 @@ PH_API int phprng_server_destroy(phprng_server *s)
     // bring the stored states to the served positions (Eq. 7 skip kernel)
     std::vector<SkipReq> reqs;
     for (uint64_t i = 0; i < c->count; ++i)
-        if (s->cursor[i] != s->pos_at_start[i]) reqs.push_back({i, s->cursor[i] - s->pos_at_start[i]});
+        if (s->cursor[i] != s->pos_at_start[i]) reqs.push_back({i, s->cursor[i] - s->pos_at_start[i], 0});
     std::string err;
     if (!reqs.empty() && rc == PHPRNG_OK) {
         SkipReq *d = nullptr;

@@ -85,7 +85,22 @@ skip_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, 
     uint64_t m;
     uint32_t s;
     uint64_t Lnew;
-    skip_state_warp(tb, P, st.m[i], L, q.k, &m, &s, &Lnew);
+    if (!q.back) {
+        skip_state_warp(tb, P, st.m[i], L, q.k, &m, &s, &Lnew);
+    } else {
+        // Backward by k: the state k steps earlier sits at cycle position
+        // L' = L - k mod (p-1), and going forward k steps from it adds F =
+        // q p(p-1)/2 + (window sum from L') (Eq. 7), so m' = m - F mod n and
+        // s' = a^L'.
+        Lnew = (L + pm1 - q.k % pm1) % pm1;
+        uint64_t F, Lf, sumL;
+        uint32_t sf;
+        skip_state_warp(tb, P, 0, Lnew, q.k, &F, &sf, &Lf);
+        pref_warp(tb, Lnew, &sumL, &s);
+        const uint64_t mc = st.m[i];
+        m = mc >= F ? mc - F : mc + (P.n - F);
+    }
+    const uint64_t pos_new = q.back ? pos - q.k : pos + q.k;
     if ((threadIdx.x & 31) == 0) {
         uint64_t c;
         if (!P.wide) {
@@ -100,8 +115,8 @@ skip_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, 
         }
         st.m[i] = m;
         st.s[i] = s;
-        st.c[i] = c;                                   // Eq. 7c at the new position
-        st.pos[i] = pos + q.k;
+        st.c[i] = pos_new ? c : 0;                     // Eq. 7c at the new position (0 before
+        st.pos[i] = pos_new;                           // the first number)
     }
 }
 

@@ -154,3 +154,43 @@ def test_microbench_rates(ph, torch):
           % tuple(rates))
     with pytest.raises(ph.PhprngError):
         ph.phprng_microbench(6)
+
+
+@pytest.mark.parametrize("width", [32, 64])
+def test_seek_backward_and_forward(ph, torch, table31, width):
+    """phprng_seek to absolute positions in both directions (Eq. 7 backward:
+    cycle position L - k, message minus the forward window sum): states against
+    the oracle's own prefix table, outputs continue the stream, position 0
+    restores the seed (c = 0), and a saved position restores the saved state."""
+    inst = workloads.draw_instances(8, width=width, seed=46 + width)
+    ctx = ph.phprng_create(width, inst, 0)
+    try:
+        L0 = oracle.dlog(P31, A31, inst["s0"])
+        gen(ph, torch, ctx, width, 0, 8, 5000)
+        saved = [ph.phprng_get_state(ctx, i) for i in range(8)]
+        ph.phprng_skip(ctx, list(range(8)), [(P31 - 1) * 3 + 77] * 8)   # beyond three cycles
+        targets = [0, 1, 1234, 4999, 5000, 10 ** 9, (P31 - 1) * 2 + 11, 5000 + (P31 - 1) * 3 + 77]
+        ph.phprng_seek(ctx, list(range(8)), targets)
+        c, r = gen(ph, torch, ctx, width, 0, 8, 129)
+        for i, t in enumerate(targets):
+            n, e = int(inst["n"][i]), int(inst["e"][i])
+            m_t, s_t = table31.state_at(n, int(inst["m0"][i]), int(L0[i]), t)
+            cr, rr, st = oracle.generate(n, e, P31, A31, m_t, s_t, 129)
+            assert np.array_equal(c[i], cr), (i, t)
+            assert np.array_equal(r[i].view(np.uint64), rr.view(np.uint64)), (i, t)
+            s = ph.phprng_get_state(ctx, i)
+            assert (s["m"], s["s"], s["pos"]) == (st[0], st[1], t + 129), (i, t)
+        # back to the seed, then to the saved positions
+        ph.phprng_seek(ctx, list(range(8)), [0] * 8)
+        for i in range(8):
+            s = ph.phprng_get_state(ctx, i)
+            assert (s["m"], s["s"], s["c"], s["pos"]) == (int(inst["m0"][i]), int(inst["s0"][i]), 0, 0)
+        ph.phprng_seek(ctx, [3, 3, 5], [7, saved[3]["pos"], saved[5]["pos"]])   # last entry wins
+        for i in (3, 5):
+            s = ph.phprng_get_state(ctx, i)
+            assert {k: s[k] for k in ("m", "s", "c", "pos")} == \
+                {k: saved[i][k] for k in ("m", "s", "c", "pos")}
+        with pytest.raises(ph.PhprngError):
+            ph.phprng_seek(ctx, [8], [1])                                # out of range
+    finally:
+        ph.phprng_destroy(ctx)
