@@ -305,6 +305,26 @@ static int prepare_split(phprng_ctx *c, uint64_t num, uint64_t per_inst, GenArgs
     return PHPRNG_OK;
 }
 
+// Launches whose 32-bit instances average at most this many Montgomery
+// products per exponentiation (the paper's small exponents: 3 to 6) run the
+// generator's LIGHT instantiation.
+static constexpr double kLightProducts = 12.0;
+
+static bool light_range(phprng_ctx *c, uint64_t first, uint64_t num)
+{
+    if (c->lt_first == first && c->lt_num == num) return c->lt_light;
+    uint64_t sum = 0, cnt = 0;
+    for (uint64_t j = first; j < first + num; ++j) {
+        if (c->key[j] >= 256) continue;                  // 64-bit instance
+        sum += 255 - c->key[j];
+        ++cnt;
+    }
+    c->lt_first = first;
+    c->lt_num = num;
+    c->lt_light = cnt && (double)sum / (double)cnt <= kLightProducts;
+    return c->lt_light;
+}
+
 static int launch_range(phprng_ctx *c, uint64_t first, uint64_t num, uint64_t per_inst,
                         void *c_out, double *r_out, phprng_stats *stats, cudaStream_t s,
                         bool ordered = false)
@@ -345,6 +365,7 @@ static int launch_range(phprng_ctx *c, uint64_t first, uint64_t num, uint64_t pe
     }
     if (c->any32) {
         g.sk = c->sk32;
+        g.light = !stats && light_range(c, first, num);
         rc = launch_gen32(g, s, &err);
     }
     if (g.edge) cudaFreeAsync(g.edge, s);

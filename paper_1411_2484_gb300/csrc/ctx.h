@@ -38,6 +38,9 @@ struct phprng_ctx {
     std::vector<uint16_t> key;
     uint32_t *d_order = nullptr;
     uint64_t ord_first = 0, ord_num = 0;
+    // light-program decision of the last range launched (see launch_range)
+    uint64_t lt_first = UINT64_MAX, lt_num = 0;
+    bool lt_light = false;
     // skip-ahead: cycle positions of the seeds and the prefix table (lazy)
     uint64_t *d_L0 = nullptr, *d_m0 = nullptr, *d_T = nullptr;
     uint32_t *d_P = nullptr;

@@ -55,8 +55,18 @@ __device__ __forceinline__ double u128d(u128 v) { return u128_to_double((uint64_
 #define PH_MINB_STATS 2
 #endif
 
-template <int NPT, typename CT, bool STATS>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, STATS ? PH_MINB_STATS : PH_MINB32)
+#ifndef PH_MINB_LIGHT
+#define PH_MINB_LIGHT 3
+#endif
+
+// LIGHT: the instantiation for launches whose exponent programs are short
+// (the paper's small exponents): there the work besides the products (skip
+// sums, scan, R, stores) dominates, and three resident blocks per SM with
+// the stores of group g placed after group g+1's messages hide it better;
+// for long programs two blocks with in-order stores are faster.
+template <int NPT, typename CT, bool STATS, bool LIGHT>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32,
+                                  STATS ? PH_MINB_STATS : LIGHT ? PH_MINB_LIGHT : PH_MINB32)
 gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, DevState st,
              SkipConst sk, uint64_t first, uint64_t num, uint64_t per_inst,
              CT *__restrict__ c_out, double *__restrict__ r_out, int vec_ok,
@@ -114,14 +124,32 @@ gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
         // it, once, after the loop.
         uint32_t x[NPT], sig_last = sig;
         uint64_t g_last = 0;
-        for (uint64_t g0 = 0; g0 < len; g0 += G) {
-            uint32_t sv[NPT], msg[NPT];
-            const uint64_t my0 = g0 + (uint64_t)NPT * lane;
-            sig_last = sig;
-            g_last = g0;
-            messages32<NPT>(P, sk, lane, my0, len, M, sig, sv, msg);
-            encrypt32<NPT>(P, pg, msg, x);
-            store_group<NPT, CT, uint32_t>(P, cdst, rdst, my0, len, vec_ok, x);
+        if (LIGHT) {
+            uint32_t xp[NPT];
+            uint64_t myp = 0;
+            for (uint64_t g0 = 0; g0 < len; g0 += G) {
+                uint32_t sv[NPT], msg[NPT];
+                const uint64_t my0 = g0 + (uint64_t)NPT * lane;
+                sig_last = sig;
+                g_last = g0;
+                messages32<NPT>(P, sk, lane, my0, len, M, sig, sv, msg);
+                if (g0) store_group<NPT, CT, uint32_t>(P, cdst, rdst, myp, len, vec_ok, xp);
+                encrypt32<NPT>(P, pg, msg, x);
+#pragma unroll
+                for (int u = 0; u < NPT; ++u) xp[u] = x[u];
+                myp = my0;
+            }
+            store_group<NPT, CT, uint32_t>(P, cdst, rdst, myp, len, vec_ok, xp);
+        } else {
+            for (uint64_t g0 = 0; g0 < len; g0 += G) {
+                uint32_t sv[NPT], msg[NPT];
+                const uint64_t my0 = g0 + (uint64_t)NPT * lane;
+                sig_last = sig;
+                g_last = g0;
+                messages32<NPT>(P, sk, lane, my0, len, M, sig, sv, msg);
+                encrypt32<NPT>(P, pg, msg, x);
+                store_group<NPT, CT, uint32_t>(P, cdst, rdst, my0, len, vec_ok, x);
+            }
         }
         if (wb) write_state_after<NPT, uint32_t, uint32_t>(st, sk, i, lane, g_last, len, pos_after, M,
                                                            sig_last, x);
@@ -342,11 +370,11 @@ int launch_gen32(const GenArgs &a, void *stream, std::string *err)
     if (a.stats) {
         const size_t smem = (2 * kWarpsPerBlock * 32 * kNPT + kWarpsPerBlock * 256) * sizeof(uint32_t);
         if (a.c_is_64)
-            gen32_kernel<kNPT, uint64_t, true><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(
+            gen32_kernel<kNPT, uint64_t, true, false><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(
                 a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, (uint64_t *)a.c_out, a.r_out,
                 a.vec_ok, a.stats, a.edge, nullptr, a.sp);
         else
-            gen32_kernel<kNPT, uint32_t, true><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(
+            gen32_kernel<kNPT, uint32_t, true, false><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(
                 a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, (uint32_t *)a.c_out, a.r_out,
                 a.vec_ok, a.stats, a.edge, nullptr, a.sp);
         int rc = check_launch(err, "gen32_kernel (statistics) launch");
@@ -355,14 +383,18 @@ int launch_gen32(const GenArgs &a, void *stream, std::string *err)
             a.inst, a.edge, a.first, a.num, a.per_inst, blocks, a.stats);
         return check_launch(err, "stats_edge_kernel launch");
     }
-    if (a.c_is_64)
-        gen32_kernel<kNPT, uint64_t, false><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(
-            a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, (uint64_t *)a.c_out, a.r_out, a.vec_ok,
-            nullptr, nullptr, a.order, a.sp);
-    else
-        gen32_kernel<kNPT, uint32_t, false><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(
-            a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, (uint32_t *)a.c_out, a.r_out, a.vec_ok,
-            nullptr, nullptr, a.order, a.sp);
+#define PH_GEN32_PLAIN(CTY, LT)                                                                     \
+    gen32_kernel<kNPT, CTY, false, LT><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(            \
+        a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, (CTY *)a.c_out, a.r_out, a.vec_ok, \
+        nullptr, nullptr, a.order, a.sp)
+    if (a.c_is_64) {
+        if (a.light) PH_GEN32_PLAIN(uint64_t, true);
+        else PH_GEN32_PLAIN(uint64_t, false);
+    } else {
+        if (a.light) PH_GEN32_PLAIN(uint32_t, true);
+        else PH_GEN32_PLAIN(uint32_t, false);
+    }
+#undef PH_GEN32_PLAIN
     return check_launch(err, "gen32_kernel launch");
 }
 
@@ -402,7 +434,7 @@ uint64_t gen_resident_warps()
     if (!cached[dev]) {
         int sms = 0, b = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, gen32_kernel<kNPT, uint32_t, false>,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, gen32_kernel<kNPT, uint32_t, false, false>,
                                                       kWarpsPerBlock * 32, 0);
         cached[dev] = (uint64_t)(sms > 0 ? sms : 1) * (b > 0 ? b : 1) * kWarpsPerBlock;
     }

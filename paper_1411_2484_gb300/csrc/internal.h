@@ -87,6 +87,7 @@ struct GenArgs {
     // Never used with statistics, whose pairs need adjacent instances.
     const uint32_t *order = nullptr;
     SplitArgs sp;                      // K = 1: no split
+    int light = 0;                     // short exponent programs: the LIGHT instantiation
 };
 
 // Exact prefix table of the skip generator's cycle (Eq. 7): with

@@ -336,22 +336,28 @@ def test_split_launches(ph, torch, n32, n64, calls):
         ph.phprng_destroy(ctx)
 
 
-def test_small_exponents(ph, torch):
-    """The paper's small exponents (e = 3, 5, 9, 17) and 65537, mixed in one
-    table with random ones: ragged calls and continuation against the oracle."""
-    tables = [workloads.draw_instances(6, seed=700 + e, exponent=e) for e in (3, 5, 9, 17, 65537)]
-    tables.append(workloads.draw_instances(6, seed=799))
+@pytest.mark.parametrize("exps,calls", [((3, 5, 9, 17), (4096, 1001, 3, 100003)),
+                                        ((3, 5, 9, 17, 65537, None), (4096, 1001, 3))],
+                         ids=["light_programs", "mixed_with_random"])
+def test_small_exponents(ph, torch, exps, calls):
+    """The paper's small exponents (e = 3, 5, 9, 17), alone (the launches take
+    the light-program instantiation, the long call a split launch) and mixed
+    with 65537 and random exponents: ragged calls and continuation against
+    the oracle."""
+    tables = [workloads.draw_instances(6, seed=700 + (e or 99), exponent=e) for e in exps]
     inst = workloads.concat_instances(*tables)
     count = len(inst["n"])
     ctx = ph.phprng_create(32, inst, 0)
     try:
         orc = OracleStreams(inst)
-        for per in (4096, 1001, 3):
+        for per in calls:
             c, r = generate(ph, torch, ctx, 32, 0, count, per)
             assert_same(c, r, *orc.next(0, count, per))
-        check_state(ph, ctx, orc, 0, count, [5100] * count)
+        check_state(ph, ctx, orc, 0, count, [sum(calls)] * count)
     finally:
         ph.phprng_destroy(ctx)
+    if exps[-1] is not None:
+        return
     tables = [workloads.draw_instances(3, width=64, seed=720 + e, exponent=e) for e in (3, 17, 65537)]
     tables.append(workloads.draw_instances(3, width=64, seed=799))
     inst = workloads.concat_instances(*tables)
