@@ -84,7 +84,7 @@ def test_pr1_ref_4x2p20_full_compare(ph, torch):
         ph.phprng_destroy(ctx)
 
 
-@pytest.mark.parametrize("per", [1, 2, 3, 5, 31, 127, 128, 129, 255, 256, 1000, 4097])
+@pytest.mark.parametrize("per", [1, 2, 3, 5, 16, 31, 127, 128, 129, 255, 256, 272, 1000, 4097, 4112])
 def test_ragged_lengths_and_continuation(ph, torch, per):
     inst = workloads.draw_instances(9, seed=1000 + per)
     ctx = ph.phprng_create(32, inst, 0)
