@@ -81,6 +81,8 @@ class Oracle:
         lib.or_stats.argtypes = [P64, u64, u64, P64, P32, PD]
         lib.or_corr.restype = None
         lib.or_corr.argtypes = [P64, P64, u64, u64, u64, P64, PD]
+        lib.or_serial_hist.restype = None
+        lib.or_serial_hist.argtypes = [P64, u64, u64, ctypes.c_int, u64, P64]
         lib.or_generate_many.restype = u64
         lib.or_generate_many.argtypes = [P64, u64, u64, ctypes.c_int, P64, PD, P64]
         self.lib = lib
@@ -143,6 +145,16 @@ class Oracle:
         self.lib.or_corr(_p64(ca), _p64(cb), ca.size, na, nb, _p64(z),
                          out.ctypes.data_as(PD))
         return int(z[0]) | (int(z[1]) << 64), float(out[0])
+
+    def serial_hist(self, c, n, D, B, hist=None):
+        """Adds one stream's non-overlapping D-tuples (B bins per dimension)
+        to hist (uint64[B**D], created when None) and returns it."""
+        c = np.ascontiguousarray(c, dtype=np.uint64)
+        if hist is None:
+            hist = np.zeros(B ** D, dtype=np.uint64)
+        assert hist.dtype == np.uint64 and hist.size == B ** D and hist.flags.c_contiguous
+        self.lib.or_serial_hist(_p64(c), c.size, int(n), int(D), int(B), _p64(hist))
+        return hist
 
     def generate_many(self, params, per_inst, threads=1, want_c=True, want_r=True):
         """Eq. 9 for many independent instances on `threads` threads.
@@ -224,3 +236,7 @@ def corr(ca, cb, na, nb):
 
 def generate_many(params, per_inst, threads=1, want_c=True, want_r=True):
     return _default().generate_many(params, per_inst, threads, want_c, want_r)
+
+
+def serial_hist(c, n, D, B, hist=None):
+    return _default().serial_hist(c, n, D, B, hist)

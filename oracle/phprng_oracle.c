@@ -263,6 +263,34 @@ void or_corr(const uint64_t *ca, const uint64_t *cb, uint64_t N,
                     u128_to_double((u128)N * ((u128)na + 1) * ((u128)nb + 1)) : 0.0;
 }
 
+/* Serial-test histogram (Tests section, items 1-5: the one-dimensional
+ * frequency test and the two- to five-dimensional serial tests).  One
+ * stream's numbers R_k = or_real(c_k) in order, grouped into consecutive
+ * non-overlapping D-tuples (R_{tD+1}, ..., R_{tD+D}) for t = 0 ..
+ * floor(N/D)-1 (a shorter remainder is left out); each coordinate falls in bin
+ * floor(B R) of B bins per dimension (B - 1 for R = 1), and the tuple adds one
+ * to hist[b_0 + B b_1 + ... + B^(D-1) b_(D-1)] (hist has B^D entries and is
+ * added to, not cleared).
+ * Pinned by: the full-period one-dimensional histogram of tiny instances
+ * (every c appears p-1 times, bins counted with exact rationals); the tuple
+ * count floor(N/D); the marginal of a coordinate equal to the one-dimensional
+ * histogram of every D-th number; bins of exact multiples of 1/B. */
+void or_serial_hist(const uint64_t *c, uint64_t N, uint64_t n, int D, uint64_t B,
+                    uint64_t *hist)
+{
+    for (uint64_t t = 0; t < N / (uint64_t)D; ++t) {
+        uint64_t idx = 0, scale = 1;
+        for (int d = 0; d < D; ++d) {
+            double R = or_real(c[t * (uint64_t)D + (uint64_t)d], n);
+            uint64_t b = (uint64_t)(R * (double)B);
+            if (b >= B) b = B - 1;
+            idx += b * scale;
+            scale *= B;
+        }
+        hist[idx] += 1;
+    }
+}
+
 /* ---- threaded harness: many independent instances (parameter splitting,
  * Introduction: each process owns its own prime modulus) ------------------ */
 typedef struct {

@@ -42,6 +42,11 @@ MUTANTS = {
     "stats_var_N": ("u128 num = (u128)N * Y - X * X;", "u128 num = (u128)(N - 1) * Y - X * X;"),
     "corr_transposed": ("Z += ((u128)ca[k] + 1) * ((u128)cb[k] + 1);",
                         "Z += ((u128)ca[k] + 1) * ((u128)ca[k] + 1);"),
+    "serial_overlapping_tuples": ("double R = or_real(c[t * (uint64_t)D + (uint64_t)d], n);",
+                                  "double R = or_real(c[t + (uint64_t)d], n);"),
+    "serial_scale_order": ("scale *= B;", "scale *= B - 1;"),
+    "serial_bin_scale": ("uint64_t b = (uint64_t)(R * (double)B);",
+                         "uint64_t b = (uint64_t)(R * (double)(B - 1));"),
     "dlog_index": ("L_out[q] = (i * M + val[h]) % order;", "L_out[q] = (i * M + val[h] + 1) % order;"),
 }
 

@@ -334,3 +334,55 @@ def test_generate_many_matches_generate(oracle_mod):
         ci, ri, sti = oracle_mod.generate(n, e, p, a, m, s, 333)
         assert np.array_equal(c[i], ci) and np.array_equal(r[i].view(np.uint64), ri.view(np.uint64))
         assert tuple(int(x) for x in st[i]) == sti
+
+
+# ------------------------------------------------------------ serial tests
+@pytest.mark.parametrize("n,p,e", TINY[:6])
+@pytest.mark.parametrize("B", [3, 8, 100])
+def test_serial_1d_full_period(oracle_mod, n, p, e, B):
+    """One-dimensional frequency test over a full period: every c appears
+    p-1 times, so bin b holds p-1 times the count of c with floor(B (c+1)/(n+1))
+    = b (exact rationals)."""
+    a = primitive_root(p)
+    P = n * (p - 1)
+    c, _, _ = oracle_mod.generate(n, e, p, a, 2 % n, 1, P)
+    hist = oracle_mod.serial_hist(c, n, 1, B)
+    expect = np.zeros(B, dtype=np.int64)
+    for cc in range(n):
+        expect[(B * (cc + 1)) // (n + 1)] += p - 1
+    assert np.array_equal(hist.astype(np.int64), expect)
+
+
+@pytest.mark.parametrize("D,B", [(1, 1 << 20), (2, 1 << 10), (3, 100), (4, 32), (5, 16)])
+def test_serial_tuple_count_and_marginals(oracle_mod, D, B):
+    """The paper's bin counts per dimension: floor(N/D) tuples, and the
+    marginal of each coordinate equals the one-dimensional histogram of that
+    coordinate's numbers (every D-th number)."""
+    rng = random.Random(D * 7)
+    n = 4294967087
+    N = 5000 + rng.randrange(D)
+    c, _, _ = oracle_mod.generate(n, 9, P31, A31, rng.randrange(n), 5, N)
+    hist = oracle_mod.serial_hist(c, n, D, B)
+    ntup = N // D
+    assert int(hist.sum()) == ntup
+    shaped = hist.reshape((B,) * D)        # index b_0 + B b_1 + ...: axis D-1-d is coordinate d
+    for d in range(D):
+        axes = tuple(x for x in range(D) if x != D - 1 - d)
+        marg = shaped.sum(axis=axes)
+        ref = np.zeros(B, dtype=np.uint64)
+        for k in range(ntup):
+            ref[(B * (int(c[k * D + d]) + 1)) // (n + 1)] += 1
+        assert np.array_equal(marg, ref), d
+    # accumulation: a second stream adds to the same histogram
+    hist2 = oracle_mod.serial_hist(c, n, D, B, hist.copy())
+    assert np.array_equal(hist2, 2 * hist)
+
+
+def test_serial_bin_edges_exact_multiples(oracle_mod):
+    """(c+1)/(n+1) exactly k/B falls in bin k; just below it in bin k-1."""
+    n = 255 * 4096 + 4095                        # n + 1 = 2^20
+    for B in (2, 16, 1 << 10):
+        for k in (1, B // 2, B - 1):
+            v = k * ((n + 1) // B)
+            h = oracle_mod.serial_hist(np.array([v - 1, v - 2], dtype=np.uint64), n, 1, B)
+            assert h[k] == 1 and h[k - 1] == 1
