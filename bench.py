@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=64)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--modes", default="fused,small_e,wide64,batched,served",
+    ap.add_argument("--modes", default="fused,serial,small_e,wide64,batched,served",
                     help="comma-separated extra measurements after the headline, or 'none'")
     return ap.parse_args()
 
@@ -212,6 +212,22 @@ def mode_small_e(ph, torch, stream, peak):
     return {"value": prn_s, "unit": "PRNs/s", "ms_per_call": ms,
             "workload": "65,536 safe 32-bit primes, e = 9, x 4,096 numbers per call (R, 2 GiB)",
             "roofline": roof}
+
+
+def mode_serial(ph, torch, ctx, N, per, stream):
+    """The two-dimensional serial test of the Tests section (pairs into 2^20
+    bins) fused on the plain workload: nothing but the histogram is written."""
+    D, B = 2, 1 << 10
+    hist = torch.zeros(B ** D, dtype=torch.int64, device="cuda")
+    ms = timed(torch, stream, lambda: ph.phprng_serial_test(ctx, 0, N, per, D, B, hist, stream), 8)
+    torch.cuda.synchronize()
+    got = hist.cpu().numpy().astype(np.float64)
+    expect = got.sum() / B ** D
+    chi2 = float(((got - expect) ** 2).sum() / expect)
+    dof = B ** D - 1
+    return {"value": N * per / ms * 1e3, "unit": "PRNs/s", "ms_per_call": ms,
+            "workload": "plain32 65,536 x 4,096, pairs into 2^20 bins (8 MiB histogram)",
+            "chi2_z": (chi2 - dof) / (2 * dof) ** 0.5}
 
 
 def measured_hbm_gbs():
@@ -483,6 +499,7 @@ def main():
         modes = {}
         wanted = [] if args.modes == "none" else args.modes.split(",")
         for name, fn in (("fused", lambda: mode_fused(ph, torch, ctx2, N, per, stream, 8)),
+                         ("serial", lambda: mode_serial(ph, torch, ctx2, N, per, stream)),
                          ("small_e", lambda: mode_small_e(ph, torch, stream, PEAK_TMULS)),
                          ("wide64", lambda: mode_wide64(ph, torch, stream, PEAK_TMULS)),
                          ("batched", lambda: mode_batched(ph, torch, stream)),
@@ -490,7 +507,7 @@ def main():
             if name not in wanted:
                 continue
             try:
-                if name == "fused":
+                if name in ("fused", "serial"):
                     ctx2 = ph.phprng_create(32, inst, ph.PHPRNG_REQUIRE_SAFE_PRIME, stream)
                     try:
                         modes[name] = fn()

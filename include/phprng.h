@@ -177,6 +177,24 @@ int phprng_generate_stats_noalloc(phprng_ctx *ctx, uint64_t first, uint64_t num_
 int phprng_skip(phprng_ctx *ctx, const uint64_t *inst_ids, const uint64_t *k, uint64_t cnt,
                 void *cuda_stream);
 
+/* Serial-test consumer (Tests section, items 1-5: the one-dimensional
+ * frequency test and the two- to five-dimensional serial tests) for 32-bit
+ * moduli.  Generates per_inst numbers of each instance first ..
+ * first+num_inst-1 (advancing their streams exactly as phprng_generate does)
+ * without storing them: each stream's numbers of this call, in order, form
+ * consecutive non-overlapping D-tuples (R_{t+1}, ..., R_{t+D}) (a remainder of
+ * fewer than D numbers at the end of the call is left out); coordinate d falls
+ * in bin b_d = floor(B R) (equal to floor(B (c+1)/(n+1))), and each tuple adds
+ * one to hist[b_0 + B b_1 + ... + B^(D-1) b_(D-1)].  hist: device memory,
+ * B^D uint64 counters, added to (clear it first); all streams of the call
+ * share it.  The paper's sizes: D = 1, B = 2^20; D = 2, B = 2^10; D = 3,
+ * B = 100; D = 4, B = 32; D = 5, B = 16.  Limits: 1 <= D <= 8, B a power of
+ * two up to 2^20 or any B up to 2^16, B^D <= 2^24; else PHPRNG_EINVAL.  The
+ * chi-square against the uniform expectation is left to the caller.
+ * Asynchronous on cuda_stream. */
+int phprng_serial_test(phprng_ctx *ctx, uint64_t first, uint64_t num_inst, uint64_t per_inst,
+                       int D, uint32_t B, uint64_t *hist, void *cuda_stream);
+
 /* Moves instance inst_ids[i] to absolute stream position pos[i], forward or
  * backward: afterwards its next number is number pos[i]+1 of the stream
  * counted from its seed, and its state (m, s, c) is the one generation would

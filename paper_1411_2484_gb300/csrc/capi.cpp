@@ -680,6 +680,58 @@ PH_API int phprng_skip(phprng_ctx *ctx, const uint64_t *inst_ids, const uint64_t
     return PHPRNG_OK;
 }
 
+PH_API int phprng_serial_test(phprng_ctx *ctx, uint64_t first, uint64_t num_inst, uint64_t per_inst,
+                              int D, uint32_t B, uint64_t *hist, void *cuda_stream)
+{
+    if (!ctx) return fail(nullptr, PHPRNG_EINVAL, "phprng_serial_test: ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (ctx->serving) return fail(ctx, PHPRNG_EINVAL, "phprng_serial_test: a server owns the context");
+    if (first > ctx->count || num_inst > ctx->count - first)
+        return fail(ctx, PHPRNG_EINVAL, "phprng_serial_test: instance range outside the table");
+    if (D < 1 || D > 8) return fail(ctx, PHPRNG_EINVAL, "phprng_serial_test: D must be 1..8");
+    const bool pow2 = B && (B & (B - 1)) == 0;
+    if (B < 1 || (pow2 ? B > (1u << 20) : B > (1u << 16)))
+        return fail(ctx, PHPRNG_EINVAL,
+                    "phprng_serial_test: B must be a power of two up to 2^20 or at most 2^16");
+    uint64_t bins = 1;
+    for (int d = 0; d < D; ++d) bins *= B;
+    if (bins > (1ull << 24)) return fail(ctx, PHPRNG_EINVAL, "phprng_serial_test: B^D exceeds 2^24");
+    if (!hist || (uintptr_t)hist % 8)
+        return fail(ctx, PHPRNG_EINVAL, "phprng_serial_test: hist NULL or not 8-byte aligned");
+    if (num_inst == 0 || per_inst == 0) return PHPRNG_OK;
+    for (uint64_t i = first; i < first + num_inst; ++i)
+        if (ctx->wide[i])
+            return fail(ctx, PHPRNG_EINVAL, "phprng_serial_test: defined for 32-bit moduli only");
+    CU(ctx, cudaSetDevice(ctx->device));
+    if (pointer_kind(hist) != 1)
+        return fail(ctx, PHPRNG_EINVAL, "phprng_serial_test: hist must be device memory");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    GenArgs g;
+    g.inst = ctx->d_inst;
+    g.prog = ctx->d_prog;
+    g.st = ctx->st;
+    g.sk = ctx->sk32_8;
+    g.first = first;
+    g.num = num_inst;
+    g.per_inst = per_inst;
+    g.c_out = nullptr;
+    g.r_out = nullptr;
+    g.stats = nullptr;
+    g.edge = nullptr;
+    g.c_is_64 = 0;
+    g.vec_ok = 0;
+    if (num_inst >= kOrderMinInstances && num_inst < (1ull << 32)) {
+        int rc = PHPRNG_OK;
+        g.order = instance_order(ctx, first, num_inst, s, &rc);
+        if (rc != PHPRNG_OK) return rc;
+    }
+    std::string err;
+    int rc = launch_serial(g, D, B, (unsigned long long *)hist, s, &err);
+    if (rc != PHPRNG_OK) return fail(ctx, rc, "phprng_serial_test: " + err);
+    for (uint64_t i = first; i < first + num_inst; ++i) ctx->pos_host[i] += per_inst;
+    return PHPRNG_OK;
+}
+
 PH_API int phprng_seek(phprng_ctx *ctx, const uint64_t *inst_ids, const uint64_t *pos,
                        uint64_t cnt, void *cuda_stream)
 {

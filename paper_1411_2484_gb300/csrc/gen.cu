@@ -118,7 +118,7 @@ gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
         __syncwarp();
     }
 
-    if (!STATS) {
+    if constexpr (!STATS) {
         // The plain loop carries nothing but the group step and the stores;
         // the lane that owns the call's last number writes the state after
         // it, once, after the loop.
@@ -153,8 +153,7 @@ gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
         }
         if (wb) write_state_after<NPT, uint32_t, uint32_t>(st, sk, i, lane, g_last, len, pos_after, M,
                                                            sig_last, x);
-        return;
-    }
+    } else {
     for (uint64_t g0 = 0; g0 < len; g0 += G) {
         uint32_t sv[NPT], msg[NPT], x[NPT];
         const uint64_t my0 = g0 + (uint64_t)NPT * lane;
@@ -222,6 +221,7 @@ gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
             }
         }
     }
+    }   // STATS
 }
 
 // Pairs the last instance of block b with the first of block b+1 (one warp

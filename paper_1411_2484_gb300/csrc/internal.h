@@ -152,6 +152,10 @@ uint64_t gen32_edge_words(uint64_t num, uint64_t per_inst);
 uint64_t gen32_fixed_edge_words();
 int launch_gen32_stats_fixed(const GenArgs &a, int dev, void *stream, std::string *err);
 int launch_gen64(const GenArgs &a, void *stream, std::string *err);
+// Serial-test consumer (serial.cu): D-tuples of floor(B R) bins of the
+// launch's 32-bit streams added to hist[B^D]; sk for NPT 8.
+int launch_serial(const GenArgs &a, int D, uint32_t B, unsigned long long *hist, void *stream,
+                  std::string *err);
 // Split launches: the pre-pass (sk8 = the NPT 8 skip constants) and the
 // number of warps the 32-bit generator keeps resident on the current device.
 int launch_chunk_sums(const GenArgs &a, const SkipConst &sk8, void *stream, std::string *err);

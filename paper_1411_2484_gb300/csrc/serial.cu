@@ -1,0 +1,102 @@
+// serial.cu -- fused serial-test consumer (Tests section, items 1-5: the
+// one-dimensional frequency test and the two- to five-dimensional serial
+// tests) for 32-bit moduli.
+//
+// The numbers are generated exactly as by the plain kernels (gencore.cuh) and
+// never stored: each one's bin floor(B R) is formed from integers, the
+// stream's consecutive non-overlapping D-tuples of bins are assembled in
+// shared memory (a tuple may span lanes and warp groups), and each tuple adds
+// one to a histogram of B^D counters in device memory, pooled over the
+// launch's streams.  B^D is at most 2^24, so the histogram (<= 128 MiB of
+// 64-bit counters, 8 MiB at the paper's 2^20 bins) stays in or near L2 and
+// the additions are L2 reductions.
+#include <cuda_runtime.h>
+
+#include "gencore.cuh"
+
+namespace phprng {
+
+// floor(B (c+1)/(n+1)) for n < 2^32, from integers: with vN = (c+1)
+// 2^(32-ybits) < yN and r = floor(B 2^32 / yN), floor(vN r / 2^32) is the bin or
+// one below it (r is short of B 2^32 / yN by less than 1 and vN < 2^32), and
+// one exact comparison decides.
+__device__ __forceinline__ uint32_t serial_bin(uint32_t c, uint32_t yN, uint32_t ybits, uint32_t r,
+                                               uint32_t B)
+{
+    const uint32_t vN = (c + 1) << (32 - ybits);
+    uint32_t est = umulhi32(vN, r);
+    if ((uint64_t)(est + 1) * yN <= (uint64_t)vN * B) ++est;
+    return est;
+}
+
+template <int NPT>
+__global__ void __launch_bounds__(256, 2)
+serial_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, DevState st,
+              SkipConst sk, uint64_t first, uint64_t num, uint64_t per_inst, int D, uint32_t B,
+              unsigned long long *__restrict__ hist, const uint32_t *__restrict__ order)
+{
+    constexpr uint64_t G = 32 * NPT;
+    __shared__ uint32_t tb[8][32 * NPT + 8];   // per warp: a carried tuple start, then one group
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t w = (uint64_t)blockIdx.x * 8 + warp;
+    if (w >= num) return;
+    const uint64_t j = order ? order[w] : w;
+    const uint64_t i = first + j;
+    const DevInst P = inst[i];
+    const ExpProg &pg = prog[i];
+    const uint32_t r = (uint32_t)(((uint64_t)B << 32) / P.yN);
+    uint32_t M = (uint32_t)st.m[i];
+    uint32_t sig = mont32((uint32_t)st.s[i], sk.lane[lane], sk.p, sk.pinv);
+    const uint64_t pos_after = st.pos[i] + per_inst;
+    uint32_t *buf = tb[warp];
+    uint32_t carry = 0;                                   // bins waiting at buf[0 .. carry), < D
+    uint32_t x[NPT], sig_last = sig;
+    uint64_t g_last = 0;
+    for (uint64_t g0 = 0; g0 < per_inst; g0 += G) {
+        uint32_t sv[NPT], msg[NPT];
+        const uint64_t my0 = g0 + (uint64_t)NPT * lane;
+        sig_last = sig;
+        g_last = g0;
+        messages32<NPT>(P, sk, lane, my0, per_inst, M, sig, sv, msg);
+        encrypt32<NPT>(P, pg, msg, x);
+#pragma unroll
+        for (int u = 0; u < NPT; ++u)
+            if (my0 + u < per_inst) buf[carry + NPT * lane + u] = serial_bin(x[u], P.yN, P.ybits, r, B);
+        __syncwarp();
+        const uint32_t valid = per_inst - g0 < G ? (uint32_t)(per_inst - g0) : (uint32_t)G;
+        const uint32_t total = carry + valid, ntup = total / (uint32_t)D;
+        for (uint32_t t = lane; t < ntup; t += 32) {
+            uint32_t idx = 0, scale = 1;
+            for (int d = 0; d < D; ++d) {
+                idx += buf[t * D + d] * scale;
+                scale *= B;
+            }
+            atomicAdd(hist + idx, 1ull);
+        }
+        const uint32_t rem = total - ntup * (uint32_t)D;
+        const uint32_t keep = (uint32_t)lane < rem ? buf[ntup * D + lane] : 0u;
+        __syncwarp();
+        if ((uint32_t)lane < rem) buf[lane] = keep;
+        __syncwarp();
+        carry = rem;
+    }
+    write_state_after<NPT, uint32_t, uint32_t>(st, sk, i, lane, g_last, per_inst, pos_after, M, sig_last,
+                                               x);
+}
+
+int launch_serial(const GenArgs &a, int D, uint32_t B, unsigned long long *hist, void *stream,
+                  std::string *err)
+{
+    if (a.num == 0 || a.per_inst == 0) return PHPRNG_OK;
+    const uint64_t blocks = (a.num + 7) / 8;
+    serial_kernel<8><<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(
+        a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, D, B, hist, a.order);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        *err = std::string("serial_kernel launch: ") + cudaGetErrorString(e);
+        return PHPRNG_ECUDA;
+    }
+    return PHPRNG_OK;
+}
+
+}  // namespace phprng

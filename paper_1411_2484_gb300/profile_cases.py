@@ -6,6 +6,7 @@ CASE is one of
   plain32   65,536 instances x 4,096 numbers, R to HBM (2 GiB)     gen32_kernel
   fused32   the same instances, statistics only                      gen32_kernel (STATS)
   small_e   65,536 instances with e = 9 x 4,096 numbers, R (2 GiB)   gen32_kernel
+  serial2   plain32's instances, pairs into 2^20 bins (serial test)  serial_kernel
   wide64    4,096 64-bit instances x 4,096 numbers, R (128 MiB)      gen64_kernel
   batched   2,000 instances (80 % 32-bit), lengths log-uniform in
             [1, 2^18], offsets in [0, 2^40), R (about 0.4 GiB)       batch_kernel
@@ -24,12 +25,19 @@ from paper_1411_2484_gb300 import workloads
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["plain32", "fused32", "small_e", "wide64", "batched"])
+    ap.add_argument("case", choices=["plain32", "fused32", "small_e", "serial2", "wide64", "batched"])
     ap.add_argument("--repeat", type=int, default=3)
     args = ap.parse_args()
     s = torch.cuda.current_stream()
     ctx, plan = None, None
-    if args.case in ("plain32", "fused32"):
+    if args.case == "serial2":
+        inst = workloads.workload_instances("plain32_65536x4096x64")
+        N, per = 65536, 4096
+        ctx = ph.phprng_create(32, inst, ph.PHPRNG_REQUIRE_SAFE_PRIME, s)
+        hist = torch.zeros(1 << 20, dtype=torch.int64, device="cuda")
+        run = lambda: ph.phprng_serial_test(ctx, 0, N, per, 2, 1 << 10, hist, s)
+        numbers = N * per
+    elif args.case in ("plain32", "fused32"):
         inst = workloads.workload_instances("plain32_65536x4096x64")
         N, per = 65536, 4096
         ctx = ph.phprng_create(32, inst, ph.PHPRNG_REQUIRE_SAFE_PRIME, s)

@@ -1,0 +1,96 @@
+"""GPU tests of the serial-test consumer (Tests section, items 1-5) through the
+C ABI: the pooled D-tuple histograms must equal the oracle's exactly, and the
+streams must continue as after phprng_generate."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1411_2484_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+THREADS = os.cpu_count() or 4
+PAPER_SIZES = [(1, 1 << 20), (2, 1 << 10), (3, 100), (4, 32), (5, 16)]
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available()
+    return t
+
+
+def oracle_hist(_unused, start_rows, per, D, B):
+    """Histogram of per numbers of every stream from its current state."""
+    c, _, st, _ = oracle.generate_many(start_rows, per, threads=THREADS, want_r=False)
+    h = np.zeros(B ** D, dtype=np.uint64)
+    for k in range(len(start_rows)):
+        oracle.serial_hist(c[k], int(start_rows[k, 0]), D, B, h)
+    return h, st
+
+
+@pytest.mark.parametrize("D,B", PAPER_SIZES + [(7, 8), (3, 2)])
+def test_serial_histograms_match_oracle(ph, torch, D, B):
+    """Two consecutive calls (ragged lengths, tuples spanning lanes and warp
+    groups), histograms accumulated on the device, states continued."""
+    inst = workloads.draw_instances(37, seed=90 + D)
+    ctx = ph.phprng_create(32, inst, 0)
+    try:
+        rows = workloads.instance_rows(inst).copy()
+        hist = torch.zeros(B ** D, dtype=torch.int64, device="cuda")
+        want = np.zeros(B ** D, dtype=np.uint64)
+        for per in (1001, 4099):
+            ph.phprng_serial_test(ctx, 0, 37, per, D, B, hist)
+            h, st = oracle_hist(None, rows, per, D, B)
+            want += h
+            rows[:, 4:6] = st
+        torch.cuda.synchronize()
+        assert np.array_equal(hist.cpu().numpy().view(np.uint64), want)
+        for i in (0, 17, 36):
+            s = ph.phprng_get_state(ctx, i)
+            assert (s["m"], s["s"], s["pos"]) == (int(rows[i, 4]), int(rows[i, 5]), 5100)
+    finally:
+        ph.phprng_destroy(ctx)
+
+
+def test_serial_at_scale_and_chi_square(ph, torch):
+    """4,096 streams x 65,536 numbers, D = 2 and the paper's 2^20 bins: equal
+    to the oracle, and the chi-square of the pooled histogram is unremarkable
+    (|z| < 6 against the uniform expectation)."""
+    inst = workloads.draw_instances(4096, seed=93)
+    ctx = ph.phprng_create(32, inst, ph.PHPRNG_REQUIRE_SAFE_PRIME)
+    try:
+        D, B, per = 2, 1 << 10, 1 << 16
+        hist = torch.zeros(B ** D, dtype=torch.int64, device="cuda")
+        ph.phprng_serial_test(ctx, 0, 4096, per, D, B, hist)
+        torch.cuda.synchronize()
+        got = hist.cpu().numpy().view(np.uint64)
+        want, _ = oracle_hist(None, workloads.instance_rows(inst), per, D, B)
+        assert np.array_equal(got, want)
+        ntup = 4096 * (per // D)
+        expect = ntup / B ** D
+        chi2 = float(((got.astype(np.float64) - expect) ** 2).sum() / expect)
+        dof = B ** D - 1
+        assert abs(chi2 - dof) / np.sqrt(2 * dof) < 6, chi2
+    finally:
+        ph.phprng_destroy(ctx)
+
+
+def test_serial_argument_errors(ph, torch):
+    inst = workloads.draw_instances(4, seed=94)
+    ctx = ph.phprng_create(32, inst, 0)
+    wide = ph.phprng_create(64, workloads.draw_instances(2, width=64, seed=95), 0)
+    try:
+        h = torch.zeros(1 << 20, dtype=torch.int64, device="cuda")
+        for D, B in [(0, 16), (9, 2), (1, 0), (2, 70000), (5, 32), (1, (1 << 20) + 1)]:
+            with pytest.raises(ph.PhprngError):
+                ph.phprng_serial_test(ctx, 0, 4, 100, D, B, h)
+        with pytest.raises(ph.PhprngError):
+            ph.phprng_serial_test(ctx, 0, 4, 100, 1, 16, np.zeros(16, dtype=np.uint64))   # host memory
+        with pytest.raises(ph.PhprngError):
+            ph.phprng_serial_test(wide, 0, 2, 100, 1, 16, h)                              # 64-bit moduli
+        assert ph.phprng_get_state(ctx, 0)["pos"] == 0                                    # nothing ran
+    finally:
+        ph.phprng_destroy(ctx)
+        ph.phprng_destroy(wide)
