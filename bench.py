@@ -396,6 +396,28 @@ def run_reference(args, rank):
     }), flush=True)
 
 
+def rank_instances(workloads, w, rank, world):
+    """The instances of one rank: its own seeded draw of w["instances"] safe
+    primes from its own slice of [2^31, 2^32), so that moduli stay distinct
+    across ranks (parameter splitting) with no exchange between ranks.  One
+    rank draws exactly the single-GPU workload."""
+    lo, hi = 1 << 31, 1 << 32
+    span = (hi - lo) // world
+    top = hi if rank == world - 1 else lo + (rank + 1) * span
+    return workloads.draw_instances(w["instances"], width=32, seed=w["seed"] + 7919 * rank,
+                                    n_range=(lo + rank * span, top), exponent=w.get("exponent"))
+
+
+def max_over_ranks(x, dist, device):
+    """The largest of the ranks' values of x (all ranks get it)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def main():
     args = parse()
     assert args.warmup >= 3, "at least 3 warm-up steps"
@@ -422,7 +444,7 @@ def main():
 
     w = workloads.WORKLOADS[WORKLOAD]
     N, per = w["instances"], w["per_inst"]
-    inst = workloads.draw_instances(N, width=32, seed=w["seed"] + 7919 * rank)
+    inst = rank_instances(workloads, w, rank, world)
     stream = torch.cuda.current_stream()
     ctx = ph.phprng_create(32, inst, ph.PHPRNG_REQUIRE_SAFE_PRIME, stream)
     r = torch.empty(N * per, dtype=torch.float64, device="cuda")
@@ -444,11 +466,7 @@ def main():
     barrier()
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    ms = start.elapsed_time(end)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(start.elapsed_time(end), dist, "cuda")
     numbers = args.steps * N * per * world
     value = numbers / (ms / 1e3)
 
@@ -460,11 +478,7 @@ def main():
     t0 = time.perf_counter()
     for _ in range(steps_e2e):
         ph.phprng_generate(ctx, 0, N, per, None, r_host, None, stream)
-    dt = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([dt], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dt = float(t.item())
+    dt = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     e2e = {"value": steps_e2e * N * per * world / dt, "unit": "PRNs/s",
            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": N * per * 8,
            "steps": steps_e2e}
