@@ -83,6 +83,8 @@ class Oracle:
         lib.or_corr.argtypes = [P64, P64, u64, u64, u64, P64, PD]
         lib.or_serial_hist.restype = None
         lib.or_serial_hist.argtypes = [P64, u64, u64, ctypes.c_int, u64, P64]
+        lib.or_poker_hist.restype = None
+        lib.or_poker_hist.argtypes = [P64, u64, u64, P64]
         lib.or_generate_many.restype = u64
         lib.or_generate_many.argtypes = [P64, u64, u64, ctypes.c_int, P64, PD, P64]
         self.lib = lib
@@ -154,6 +156,15 @@ class Oracle:
             hist = np.zeros(B ** D, dtype=np.uint64)
         assert hist.dtype == np.uint64 and hist.size == B ** D and hist.flags.c_contiguous
         self.lib.or_serial_hist(_p64(c), c.size, int(n), int(D), int(B), _p64(hist))
+        return hist
+
+    def poker_hist(self, c, n, hist=None):
+        """Adds one stream's five-card hands (categories 0..6) to hist (uint64[7])."""
+        c = np.ascontiguousarray(c, dtype=np.uint64)
+        if hist is None:
+            hist = np.zeros(7, dtype=np.uint64)
+        assert hist.dtype == np.uint64 and hist.size == 7 and hist.flags.c_contiguous
+        self.lib.or_poker_hist(_p64(c), c.size, int(n), _p64(hist))
         return hist
 
     def generate_many(self, params, per_inst, threads=1, want_c=True, want_r=True):
@@ -240,3 +251,7 @@ def generate_many(params, per_inst, threads=1, want_c=True, want_r=True):
 
 def serial_hist(c, n, D, B, hist=None):
     return _default().serial_hist(c, n, D, B, hist)
+
+
+def poker_hist(c, n, hist=None):
+    return _default().poker_hist(c, n, hist)

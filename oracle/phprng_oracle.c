@@ -291,6 +291,43 @@ void or_serial_hist(const uint64_t *c, uint64_t N, uint64_t n, int D, uint64_t B
     }
 }
 
+/* Poker test (Tests section: five cards, ten denominations).  One stream's
+ * numbers in consecutive non-overlapping 5-tuples (a remainder of fewer than
+ * five is left out); card k of a hand has denomination floor(10 R_k); the
+ * hand adds one to hist[category] with categories 0 all different, 1 one
+ * pair, 2 two pairs, 3 three of a kind, 4 full house, 5 four of a kind,
+ * 6 five of a kind (hist has 7 entries and is added to).
+ * Pinned by: hands built from chosen denominations; the hand count floor(N/5);
+ * the category frequencies of a long stream against the exact probabilities
+ * (0.3024, 0.504, 0.108, 0.072, 0.009, 0.0045, 0.0001). */
+void or_poker_hist(const uint64_t *c, uint64_t N, uint64_t n, uint64_t *hist)
+{
+    for (uint64_t t = 0; t < N / 5; ++t) {
+        int count[10] = {0};
+        for (int k = 0; k < 5; ++k) {
+            int d = (int)(or_real(c[t * 5 + (uint64_t)k], n) * 10.0);
+            if (d > 9) d = 9;
+            count[d] += 1;
+        }
+        int pairs = 0, threes = 0, fours = 0, fives = 0;
+        for (int d = 0; d < 10; ++d) {
+            if (count[d] == 2) ++pairs;
+            if (count[d] == 3) ++threes;
+            if (count[d] == 4) ++fours;
+            if (count[d] == 5) ++fives;
+        }
+        int cat;
+        if (fives) cat = 6;
+        else if (fours) cat = 5;
+        else if (threes && pairs) cat = 4;
+        else if (threes) cat = 3;
+        else if (pairs == 2) cat = 2;
+        else if (pairs == 1) cat = 1;
+        else cat = 0;
+        hist[cat] += 1;
+    }
+}
+
 /* ---- threaded harness: many independent instances (parameter splitting,
  * Introduction: each process owns its own prime modulus) ------------------ */
 typedef struct {

@@ -47,6 +47,9 @@ MUTANTS = {
     "serial_scale_order": ("scale *= B;", "scale *= B - 1;"),
     "serial_bin_scale": ("uint64_t b = (uint64_t)(R * (double)B);",
                          "uint64_t b = (uint64_t)(R * (double)(B - 1));"),
+    "poker_full_house": ("else if (threes && pairs) cat = 4;", "else if (threes) cat = 4;"),
+    "poker_denominations": ("int d = (int)(or_real(c[t * 5 + (uint64_t)k], n) * 10.0);",
+                            "int d = (int)(or_real(c[t * 5 + (uint64_t)k], n) * 9.0);"),
     "dlog_index": ("L_out[q] = (i * M + val[h]) % order;", "L_out[q] = (i * M + val[h] + 1) % order;"),
 }
 

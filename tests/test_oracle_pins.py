@@ -386,3 +386,35 @@ def test_serial_bin_edges_exact_multiples(oracle_mod):
             v = k * ((n + 1) // B)
             h = oracle_mod.serial_hist(np.array([v - 1, v - 2], dtype=np.uint64), n, 1, B)
             assert h[k] == 1 and h[k - 1] == 1
+
+
+# ------------------------------------------------------------ poker test
+def test_poker_hands_from_chosen_denominations(oracle_mod):
+    """n + 1 = 10 t makes floor(10 (c+1)/(n+1)) = d for c = d t (d < 10):
+    hands of chosen denominations fall in their categories."""
+    t = 429496729
+    n = 10 * t - 1
+    hands = {0: [0, 1, 2, 3, 4], 1: [7, 7, 1, 2, 3], 2: [5, 5, 9, 9, 0], 3: [4, 4, 4, 8, 1],
+             4: [2, 2, 2, 6, 6], 5: [3, 3, 3, 3, 9], 6: [8, 8, 8, 8, 8]}
+    cs = []
+    for cat in range(7):
+        cs += [d * t for d in hands[cat]]
+    cs += [5 * t, 6 * t]                                   # a remainder of two is left out
+    h = oracle_mod.poker_hist(np.array(cs, dtype=np.uint64), n)
+    assert list(h) == [1] * 7
+    # a permuted hand is the same category; accumulation adds
+    h2 = oracle_mod.poker_hist(np.array([d * t for d in [6, 2, 6, 2, 2]], dtype=np.uint64), n, h.copy())
+    assert list(h2 - h) == [0, 0, 0, 0, 1, 0, 0]
+
+
+def test_poker_frequencies_of_a_long_stream(oracle_mod):
+    """Category frequencies of 400,000 hands against the exact probabilities
+    (each within 5 standard deviations)."""
+    n = 4294967087
+    c, _, _ = oracle_mod.generate(n, 9, P31, A31, 12345, 678, 2_000_000)
+    h = oracle_mod.poker_hist(c, n).astype(np.float64)
+    hands = 400_000
+    assert h.sum() == hands
+    prob = np.array([0.3024, 0.504, 0.108, 0.072, 0.009, 0.0045, 0.0001])
+    z = (h - hands * prob) / np.sqrt(hands * prob * (1 - prob))
+    assert np.all(np.abs(z) < 5), z
