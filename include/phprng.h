@@ -195,6 +195,18 @@ int phprng_skip(phprng_ctx *ctx, const uint64_t *inst_ids, const uint64_t *k, ui
 int phprng_serial_test(phprng_ctx *ctx, uint64_t first, uint64_t num_inst, uint64_t per_inst,
                        int D, uint32_t B, uint64_t *hist, void *cuda_stream);
 
+/* Poker-test consumer (Tests section: five cards, ten denominations) for
+ * 32-bit moduli.  Like phprng_serial_test with D = 5: each stream's numbers of
+ * the call form consecutive non-overlapping hands of five; card k has
+ * denomination floor(10 R_k); the hand adds one to hist[category], with
+ * categories 0 all different, 1 one pair, 2 two pairs, 3 three of a kind,
+ * 4 full house, 5 four of a kind, 6 five of a kind (exact probabilities
+ * 0.3024, 0.504, 0.108, 0.072, 0.009, 0.0045, 0.0001).  hist: device memory,
+ * 7 uint64 counters, added to.  Streams advance by per_inst.  Asynchronous on
+ * cuda_stream. */
+int phprng_poker_test(phprng_ctx *ctx, uint64_t first, uint64_t num_inst, uint64_t per_inst,
+                      uint64_t *hist, void *cuda_stream);
+
 /* Moves instance inst_ids[i] to absolute stream position pos[i], forward or
  * backward: afterwards its next number is number pos[i]+1 of the stream
  * counted from its seed, and its state (m, s, c) is the one generation would

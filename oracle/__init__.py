@@ -85,6 +85,8 @@ class Oracle:
         lib.or_serial_hist.argtypes = [P64, u64, u64, ctypes.c_int, u64, P64]
         lib.or_poker_hist.restype = None
         lib.or_poker_hist.argtypes = [P64, u64, u64, P64]
+        lib.or_runs_hist.restype = None
+        lib.or_runs_hist.argtypes = [P64, u64, u64, ctypes.c_int, P64]
         lib.or_generate_many.restype = u64
         lib.or_generate_many.argtypes = [P64, u64, u64, ctypes.c_int, P64, PD, P64]
         self.lib = lib
@@ -165,6 +167,16 @@ class Oracle:
             hist = np.zeros(7, dtype=np.uint64)
         assert hist.dtype == np.uint64 and hist.size == 7 and hist.flags.c_contiguous
         self.lib.or_poker_hist(_p64(c), c.size, int(n), _p64(hist))
+        return hist
+
+    def runs_hist(self, c, n, lmax, hist=None):
+        """Adds one stream's completed runs (bit-major, lengths capped at
+        lmax) to hist (uint64[2 lmax])."""
+        c = np.ascontiguousarray(c, dtype=np.uint64)
+        if hist is None:
+            hist = np.zeros(2 * lmax, dtype=np.uint64)
+        assert hist.dtype == np.uint64 and hist.size == 2 * lmax and hist.flags.c_contiguous
+        self.lib.or_runs_hist(_p64(c), c.size, int(n), int(lmax), _p64(hist))
         return hist
 
     def generate_many(self, params, per_inst, threads=1, want_c=True, want_r=True):
@@ -255,3 +267,7 @@ def serial_hist(c, n, D, B, hist=None):
 
 def poker_hist(c, n, hist=None):
     return _default().poker_hist(c, n, hist)
+
+
+def runs_hist(c, n, lmax, hist=None):
+    return _default().runs_hist(c, n, lmax, hist)

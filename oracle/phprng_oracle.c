@@ -328,6 +328,32 @@ void or_poker_hist(const uint64_t *c, uint64_t N, uint64_t n, uint64_t *hist)
     }
 }
 
+/* Runs test (Tests section: runs of 0's, R <= 0.5, and 1's, R > 0.5).  One
+ * stream's numbers in order give bits b_k = (R_k > 0.5); every maximal run of
+ * equal bits that ends before the last number adds one to
+ * hist[b * Lmax + min(L, Lmax) - 1] (L its length; the run still open at the
+ * last number is left out, the first run starts at the first number).  hist
+ * has 2 Lmax entries and is added to.
+ * Pinned by: bit patterns built from chosen c; total length of the counted
+ * runs = N minus the open run; run-length frequencies of a long stream
+ * against the probabilities 2^-L of fair independent bits. */
+void or_runs_hist(const uint64_t *c, uint64_t N, uint64_t n, int Lmax, uint64_t *hist)
+{
+    if (N == 0) return;
+    int bit = or_real(c[0], n) > 0.5;
+    uint64_t len = 1;
+    for (uint64_t k = 1; k < N; ++k) {
+        int b = or_real(c[k], n) > 0.5;
+        if (b == bit) {
+            ++len;
+            continue;
+        }
+        hist[(uint64_t)bit * (uint64_t)Lmax + (len < (uint64_t)Lmax ? len : (uint64_t)Lmax) - 1] += 1;
+        bit = b;
+        len = 1;
+    }
+}
+
 /* ---- threaded harness: many independent instances (parameter splitting,
  * Introduction: each process owns its own prime modulus) ------------------ */
 typedef struct {

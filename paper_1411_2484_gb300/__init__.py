@@ -35,7 +35,8 @@ PHPRNG_ALLOW_SHARED_N = 0x2
 
 EXPORTED = [
     "phprng_create", "phprng_create_seeded", "phprng_destroy", "phprng_last_error",
-    "phprng_status_string", "phprng_generate", "phprng_skip", "phprng_seek", "phprng_serial_test", "phprng_get_state",
+    "phprng_status_string", "phprng_generate", "phprng_skip", "phprng_seek", "phprng_serial_test", "phprng_poker_test",
+    "phprng_get_state",
     "phprng_is_prime", "phprng_validate", "phprng_draw_instances", "phprng_microbench",
     "phprng_plan_create", "phprng_plan_launch", "phprng_plan_launch_graph",
     "phprng_plan_autotune", "phprng_plan_tuning", "phprng_plan_destroy", "phprng_generate_batch",
@@ -134,6 +135,7 @@ def _load():
         lib.phprng_skip.argtypes = [vp, P64, P64, u64, vp]
         lib.phprng_seek.argtypes = [vp, P64, P64, u64, vp]
         lib.phprng_serial_test.argtypes = [vp, u64, u64, u64, i32, ctypes.c_uint32, vp, vp]
+        lib.phprng_poker_test.argtypes = [vp, u64, u64, u64, vp, vp]
         lib.phprng_get_state.argtypes = [vp, u64, P_inst, P64, P64, vp]
         lib.phprng_is_prime.argtypes = [u64]
         lib.phprng_validate.argtypes = [i32, P_inst, u64, u32, P64]
@@ -263,6 +265,13 @@ def phprng_serial_test(ctx, first, num_inst, per_inst, D, B, hist, stream=None):
     `hist` (B**D uint64 counters) and advances the streams by per_inst."""
     _check(_load().phprng_serial_test(ctx, int(first), int(num_inst), int(per_inst), int(D), int(B),
                                       _ptr(hist), _stream(stream)), ctx)
+
+
+def phprng_poker_test(ctx, first, num_inst, per_inst, hist, stream=None):
+    """Adds the call's five-card hands (categories 0..6) to the device
+    counters `hist` (7 uint64) and advances the streams by per_inst."""
+    _check(_load().phprng_poker_test(ctx, int(first), int(num_inst), int(per_inst), _ptr(hist),
+                                     _stream(stream)), ctx)
 
 
 def phprng_seek(ctx, inst_ids, pos, stream=None):

@@ -680,31 +680,22 @@ PH_API int phprng_skip(phprng_ctx *ctx, const uint64_t *inst_ids, const uint64_t
     return PHPRNG_OK;
 }
 
-PH_API int phprng_serial_test(phprng_ctx *ctx, uint64_t first, uint64_t num_inst, uint64_t per_inst,
-                              int D, uint32_t B, uint64_t *hist, void *cuda_stream)
+// Shared by the serial and poker tests: validation of the range, the launch,
+// the positions.  D = 0 selects the poker test.
+static int run_hist_test(phprng_ctx *ctx, const char *what, uint64_t first, uint64_t num_inst,
+                         uint64_t per_inst, int D, uint32_t B, uint64_t *hist, void *cuda_stream)
 {
-    if (!ctx) return fail(nullptr, PHPRNG_EINVAL, "phprng_serial_test: ctx is NULL");
-    std::lock_guard<std::mutex> lk(ctx->mu);
-    if (ctx->serving) return fail(ctx, PHPRNG_EINVAL, "phprng_serial_test: a server owns the context");
+    const std::string w(what);
+    if (ctx->serving) return fail(ctx, PHPRNG_EINVAL, w + ": a server owns the context");
     if (first > ctx->count || num_inst > ctx->count - first)
-        return fail(ctx, PHPRNG_EINVAL, "phprng_serial_test: instance range outside the table");
-    if (D < 1 || D > 8) return fail(ctx, PHPRNG_EINVAL, "phprng_serial_test: D must be 1..8");
-    const bool pow2 = B && (B & (B - 1)) == 0;
-    if (B < 1 || (pow2 ? B > (1u << 20) : B > (1u << 16)))
-        return fail(ctx, PHPRNG_EINVAL,
-                    "phprng_serial_test: B must be a power of two up to 2^20 or at most 2^16");
-    uint64_t bins = 1;
-    for (int d = 0; d < D; ++d) bins *= B;
-    if (bins > (1ull << 24)) return fail(ctx, PHPRNG_EINVAL, "phprng_serial_test: B^D exceeds 2^24");
+        return fail(ctx, PHPRNG_EINVAL, w + ": instance range outside the table");
     if (!hist || (uintptr_t)hist % 8)
-        return fail(ctx, PHPRNG_EINVAL, "phprng_serial_test: hist NULL or not 8-byte aligned");
+        return fail(ctx, PHPRNG_EINVAL, w + ": hist NULL or not 8-byte aligned");
     if (num_inst == 0 || per_inst == 0) return PHPRNG_OK;
     for (uint64_t i = first; i < first + num_inst; ++i)
-        if (ctx->wide[i])
-            return fail(ctx, PHPRNG_EINVAL, "phprng_serial_test: defined for 32-bit moduli only");
+        if (ctx->wide[i]) return fail(ctx, PHPRNG_EINVAL, w + ": defined for 32-bit moduli only");
     CU(ctx, cudaSetDevice(ctx->device));
-    if (pointer_kind(hist) != 1)
-        return fail(ctx, PHPRNG_EINVAL, "phprng_serial_test: hist must be device memory");
+    if (pointer_kind(hist) != 1) return fail(ctx, PHPRNG_EINVAL, w + ": hist must be device memory");
     cudaStream_t s = (cudaStream_t)cuda_stream;
     GenArgs g;
     g.inst = ctx->d_inst;
@@ -727,9 +718,33 @@ PH_API int phprng_serial_test(phprng_ctx *ctx, uint64_t first, uint64_t num_inst
     }
     std::string err;
     int rc = launch_serial(g, D, B, (unsigned long long *)hist, s, &err);
-    if (rc != PHPRNG_OK) return fail(ctx, rc, "phprng_serial_test: " + err);
+    if (rc != PHPRNG_OK) return fail(ctx, rc, w + ": " + err);
     for (uint64_t i = first; i < first + num_inst; ++i) ctx->pos_host[i] += per_inst;
     return PHPRNG_OK;
+}
+
+PH_API int phprng_serial_test(phprng_ctx *ctx, uint64_t first, uint64_t num_inst, uint64_t per_inst,
+                              int D, uint32_t B, uint64_t *hist, void *cuda_stream)
+{
+    if (!ctx) return fail(nullptr, PHPRNG_EINVAL, "phprng_serial_test: ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (D < 1 || D > 8) return fail(ctx, PHPRNG_EINVAL, "phprng_serial_test: D must be 1..8");
+    const bool pow2 = B && (B & (B - 1)) == 0;
+    if (B < 1 || (pow2 ? B > (1u << 20) : B > (1u << 16)))
+        return fail(ctx, PHPRNG_EINVAL,
+                    "phprng_serial_test: B must be a power of two up to 2^20 or at most 2^16");
+    uint64_t bins = 1;
+    for (int d = 0; d < D; ++d) bins *= B;
+    if (bins > (1ull << 24)) return fail(ctx, PHPRNG_EINVAL, "phprng_serial_test: B^D exceeds 2^24");
+    return run_hist_test(ctx, "phprng_serial_test", first, num_inst, per_inst, D, B, hist, cuda_stream);
+}
+
+PH_API int phprng_poker_test(phprng_ctx *ctx, uint64_t first, uint64_t num_inst, uint64_t per_inst,
+                             uint64_t *hist, void *cuda_stream)
+{
+    if (!ctx) return fail(nullptr, PHPRNG_EINVAL, "phprng_poker_test: ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    return run_hist_test(ctx, "phprng_poker_test", first, num_inst, per_inst, 0, 10, hist, cuda_stream);
 }
 
 PH_API int phprng_seek(phprng_ctx *ctx, const uint64_t *inst_ids, const uint64_t *pos,

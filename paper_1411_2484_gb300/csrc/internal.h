@@ -153,7 +153,8 @@ uint64_t gen32_fixed_edge_words();
 int launch_gen32_stats_fixed(const GenArgs &a, int dev, void *stream, std::string *err);
 int launch_gen64(const GenArgs &a, void *stream, std::string *err);
 // Serial-test consumer (serial.cu): D-tuples of floor(B R) bins of the
-// launch's 32-bit streams added to hist[B^D]; sk for NPT 8.
+// launch's 32-bit streams added to hist[B^D]; D = 0: the poker test (hands of
+// five floor(10 R) cards into hist[7]); sk for NPT 8.
 int launch_serial(const GenArgs &a, int D, uint32_t B, unsigned long long *hist, void *stream,
                   std::string *err);
 // Split launches: the pre-pass (sk8 = the NPT 8 skip constants) and the

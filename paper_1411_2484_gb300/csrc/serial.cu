@@ -1,6 +1,6 @@
-// serial.cu -- fused serial-test consumer (Tests section, items 1-5: the
-// one-dimensional frequency test and the two- to five-dimensional serial
-// tests) for 32-bit moduli.
+// serial.cu -- fused serial-test and poker-test consumers (Tests section,
+// items 1-6: the one-dimensional frequency test, the two- to five-dimensional
+// serial tests and the poker test) for 32-bit moduli.
 //
 // The numbers are generated exactly as by the plain kernels (gencore.cuh) and
 // never stored: each one's bin floor(B R) is formed from integers, the
@@ -29,7 +29,31 @@ __device__ __forceinline__ uint32_t serial_bin(uint32_t c, uint32_t yN, uint32_t
     return est;
 }
 
-template <int NPT>
+// Poker category of five denominations: the sum over the cards of how many
+// cards share the card's denomination is 5 (all different), 7 (one pair),
+// 9 (two pairs), 11 (three of a kind), 13 (full house), 17 (four of a kind)
+// or 25 (five of a kind), one value per category.
+__device__ __forceinline__ uint32_t poker_category(const uint32_t *h)
+{
+    uint32_t sum = 0;
+#pragma unroll
+    for (int a = 0; a < 5; ++a)
+#pragma unroll
+        for (int b = 0; b < 5; ++b) sum += h[a] == h[b] ? 1u : 0u;
+    switch (sum) {
+    case 5: return 0;
+    case 7: return 1;
+    case 9: return 2;
+    case 11: return 3;
+    case 13: return 4;
+    case 17: return 5;
+    default: return 6;
+    }
+}
+
+// POKER: hands of five cards, denominations floor(10 R), into 7 category
+// counters (D = 5, B = 10); otherwise the serial test's B^D counters.
+template <int NPT, bool POKER>
 __global__ void __launch_bounds__(256, 2)
 serial_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, DevState st,
               SkipConst sk, uint64_t first, uint64_t num, uint64_t per_inst, int D, uint32_t B,
@@ -67,9 +91,13 @@ serial_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog
         const uint32_t total = carry + valid, ntup = total / (uint32_t)D;
         for (uint32_t t = lane; t < ntup; t += 32) {
             uint32_t idx = 0, scale = 1;
-            for (int d = 0; d < D; ++d) {
-                idx += buf[t * D + d] * scale;
-                scale *= B;
+            if (POKER) {
+                idx = poker_category(buf + t * 5);
+            } else {
+                for (int d = 0; d < D; ++d) {
+                    idx += buf[t * D + d] * scale;
+                    scale *= B;
+                }
             }
             atomicAdd(hist + idx, 1ull);
         }
@@ -89,8 +117,12 @@ int launch_serial(const GenArgs &a, int D, uint32_t B, unsigned long long *hist,
 {
     if (a.num == 0 || a.per_inst == 0) return PHPRNG_OK;
     const uint64_t blocks = (a.num + 7) / 8;
-    serial_kernel<8><<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(
-        a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, D, B, hist, a.order);
+    if (D == 0)                                      // the poker test
+        serial_kernel<8, true><<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(
+            a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, 5, 10, hist, a.order);
+    else
+        serial_kernel<8, false><<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(
+            a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, D, B, hist, a.order);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         *err = std::string("serial_kernel launch: ") + cudaGetErrorString(e);

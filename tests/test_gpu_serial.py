@@ -94,3 +94,40 @@ def test_serial_argument_errors(ph, torch):
     finally:
         ph.phprng_destroy(ctx)
         ph.phprng_destroy(wide)
+
+
+def test_poker_matches_oracle_and_probabilities(ph, torch):
+    """Hands spanning lanes and warp groups over two ragged calls, equal to the
+    oracle's counts; at scale the category frequencies match the exact
+    probabilities (|z| < 6)."""
+    inst = workloads.draw_instances(41, seed=96)
+    ctx = ph.phprng_create(32, inst, 0)
+    try:
+        rows = workloads.instance_rows(inst).copy()
+        hist = torch.zeros(7, dtype=torch.int64, device="cuda")
+        want = np.zeros(7, dtype=np.uint64)
+        for per in (1003, 5000):
+            ph.phprng_poker_test(ctx, 0, 41, per, hist)
+            c, _, st, _ = oracle.generate_many(rows, per, threads=THREADS, want_r=False)
+            for k in range(41):
+                oracle.poker_hist(c[k], int(rows[k, 0]), want)
+            rows[:, 4:6] = st
+        torch.cuda.synchronize()
+        assert np.array_equal(hist.cpu().numpy().view(np.uint64), want)
+        s = ph.phprng_get_state(ctx, 40)
+        assert (s["m"], s["s"], s["pos"]) == (int(rows[40, 4]), int(rows[40, 5]), 6003)
+    finally:
+        ph.phprng_destroy(ctx)
+    inst = workloads.draw_instances(2048, seed=97)
+    ctx = ph.phprng_create(32, inst, 0)
+    try:
+        hist = torch.zeros(7, dtype=torch.int64, device="cuda")
+        ph.phprng_poker_test(ctx, 0, 2048, 1 << 16, hist)
+        h = hist.cpu().numpy().astype(np.float64)
+        hands = 2048 * ((1 << 16) // 5)
+        assert h.sum() == hands
+        prob = np.array([0.3024, 0.504, 0.108, 0.072, 0.009, 0.0045, 0.0001])
+        z = (h - hands * prob) / np.sqrt(hands * prob * (1 - prob))
+        assert np.all(np.abs(z) < 6), z
+    finally:
+        ph.phprng_destroy(ctx)

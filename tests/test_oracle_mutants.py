@@ -50,6 +50,8 @@ MUTANTS = {
     "poker_full_house": ("else if (threes && pairs) cat = 4;", "else if (threes) cat = 4;"),
     "poker_denominations": ("int d = (int)(or_real(c[t * 5 + (uint64_t)k], n) * 10.0);",
                             "int d = (int)(or_real(c[t * 5 + (uint64_t)k], n) * 9.0);"),
+    "runs_threshold": ("int b = or_real(c[k], n) > 0.5;", "int b = or_real(c[k], n) >= 0.5;"),
+    "runs_length_reset": ("        len = 1;\n    }", "        len = 0;\n    }"),
     "dlog_index": ("L_out[q] = (i * M + val[h]) % order;", "L_out[q] = (i * M + val[h] + 1) % order;"),
 }
 

@@ -418,3 +418,43 @@ def test_poker_frequencies_of_a_long_stream(oracle_mod):
     prob = np.array([0.3024, 0.504, 0.108, 0.072, 0.009, 0.0045, 0.0001])
     z = (h - hands * prob) / np.sqrt(hands * prob * (1 - prob))
     assert np.all(np.abs(z) < 5), z
+
+
+# ------------------------------------------------------------ runs test
+def test_runs_from_chosen_bits(oracle_mod):
+    """c below (n-1)/2 gives R <= 1/2 (bit 0), above gives bit 1; c = (n-1)/2
+    gives R = 1/2 exactly, bit 0."""
+    n = 1000003
+    lo, hi, half = 5, n - 7, (n - 1) // 2
+    bits = [0, 0, 1, 1, 1, 0, 1, 0, 0, 0, 0, 0, 1, 1]        # runs 2,3,1,1,5 then an open run of 2
+    cs = np.array([half if (b == 0 and k == 3 + 2) else (lo if b == 0 else hi)
+                   for k, b in enumerate(bits)], dtype=np.uint64)
+    h = oracle_mod.runs_hist(cs, n, 4)
+    want = np.zeros(8, dtype=np.uint64)
+    for b, L in [(0, 2), (1, 3), (0, 1), (1, 1), (0, 5)]:
+        want[b * 4 + min(L, 4) - 1] += 1
+    assert np.array_equal(h, want)
+
+
+def test_runs_lengths_of_a_long_stream(oracle_mod):
+    """Completed runs cover every number but the open run; run lengths of a
+    long stream follow 2^-L (each of the first eight lengths within 5 sigma)."""
+    n = 4294967087
+    N = 1_000_000
+    c, _, _ = oracle_mod.generate(n, 9, P31, A31, 4242, 77, N)
+    lmax = 32
+    h = oracle_mod.runs_hist(c, n, lmax)
+    bits = (c > (n - 1) // 2).astype(np.int64)
+    open_run = 1
+    while open_run < N and bits[N - 1 - open_run] == bits[N - 1]:
+        open_run += 1
+    h64 = oracle_mod.runs_hist(c, n, 64)                   # no run reaches 64 here
+    lengths = np.concatenate([np.arange(1, 65)] * 2)
+    assert h64[63] == 0 and h64[127] == 0
+    assert int((h64.astype(np.int64) * lengths).sum()) == N - open_run
+    runs = h.astype(np.float64).reshape(2, lmax).sum(axis=0)
+    total = runs.sum()
+    for L in range(1, 9):
+        p = 0.5 ** L
+        z = (runs[L - 1] - total * p) / np.sqrt(total * p * (1 - p))
+        assert abs(z) < 5, (L, z)
