@@ -207,6 +207,18 @@ int phprng_serial_test(phprng_ctx *ctx, uint64_t first, uint64_t num_inst, uint6
 int phprng_poker_test(phprng_ctx *ctx, uint64_t first, uint64_t num_inst, uint64_t per_inst,
                       uint64_t *hist, void *cuda_stream);
 
+/* Runs-test consumer (Tests section: runs of 0's, R <= 1/2, and 1's,
+ * R > 1/2) for 32-bit moduli.  Each stream's numbers of the call, in order,
+ * give bits b_k = (R_k > 1/2); every maximal run of equal bits that ends before
+ * the call's last number adds one to hist[b * lmax + min(L, lmax) - 1] (L its
+ * length; the first run starts at the call's first number, the run still
+ * open at the last number is left out).  For fair independent bits a
+ * completed run has length L with probability 2^-L.  hist: device memory,
+ * 2 lmax uint64 counters, added to; 1 <= lmax <= 64; per_inst < 2^32.
+ * Streams advance by per_inst.  Asynchronous on cuda_stream. */
+int phprng_runs_test(phprng_ctx *ctx, uint64_t first, uint64_t num_inst, uint64_t per_inst,
+                     int lmax, uint64_t *hist, void *cuda_stream);
+
 /* Moves instance inst_ids[i] to absolute stream position pos[i], forward or
  * backward: afterwards its next number is number pos[i]+1 of the stream
  * counted from its seed, and its state (m, s, c) is the one generation would

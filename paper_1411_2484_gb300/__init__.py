@@ -35,7 +35,7 @@ PHPRNG_ALLOW_SHARED_N = 0x2
 
 EXPORTED = [
     "phprng_create", "phprng_create_seeded", "phprng_destroy", "phprng_last_error",
-    "phprng_status_string", "phprng_generate", "phprng_skip", "phprng_seek", "phprng_serial_test", "phprng_poker_test",
+    "phprng_status_string", "phprng_generate", "phprng_skip", "phprng_seek", "phprng_serial_test", "phprng_poker_test", "phprng_runs_test",
     "phprng_get_state",
     "phprng_is_prime", "phprng_validate", "phprng_draw_instances", "phprng_microbench",
     "phprng_plan_create", "phprng_plan_launch", "phprng_plan_launch_graph",
@@ -136,6 +136,7 @@ def _load():
         lib.phprng_seek.argtypes = [vp, P64, P64, u64, vp]
         lib.phprng_serial_test.argtypes = [vp, u64, u64, u64, i32, ctypes.c_uint32, vp, vp]
         lib.phprng_poker_test.argtypes = [vp, u64, u64, u64, vp, vp]
+        lib.phprng_runs_test.argtypes = [vp, u64, u64, u64, i32, vp, vp]
         lib.phprng_get_state.argtypes = [vp, u64, P_inst, P64, P64, vp]
         lib.phprng_is_prime.argtypes = [u64]
         lib.phprng_validate.argtypes = [i32, P_inst, u64, u32, P64]
@@ -272,6 +273,13 @@ def phprng_poker_test(ctx, first, num_inst, per_inst, hist, stream=None):
     counters `hist` (7 uint64) and advances the streams by per_inst."""
     _check(_load().phprng_poker_test(ctx, int(first), int(num_inst), int(per_inst), _ptr(hist),
                                      _stream(stream)), ctx)
+
+
+def phprng_runs_test(ctx, first, num_inst, per_inst, lmax, hist, stream=None):
+    """Adds the call's completed runs (bit-major, lengths capped at lmax) to
+    the device counters `hist` (2*lmax uint64); streams advance by per_inst."""
+    _check(_load().phprng_runs_test(ctx, int(first), int(num_inst), int(per_inst), int(lmax),
+                                    _ptr(hist), _stream(stream)), ctx)
 
 
 def phprng_seek(ctx, inst_ids, pos, stream=None):

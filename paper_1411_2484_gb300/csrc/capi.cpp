@@ -680,8 +680,9 @@ PH_API int phprng_skip(phprng_ctx *ctx, const uint64_t *inst_ids, const uint64_t
     return PHPRNG_OK;
 }
 
-// Shared by the serial and poker tests: validation of the range, the launch,
-// the positions.  D = 0 selects the poker test.
+// Shared by the serial, poker and runs tests: validation of the range, the
+// launch, the positions.  D = 0 selects the poker test, D = -1 the runs test
+// (B = lmax).
 static int run_hist_test(phprng_ctx *ctx, const char *what, uint64_t first, uint64_t num_inst,
                          uint64_t per_inst, int D, uint32_t B, uint64_t *hist, void *cuda_stream)
 {
@@ -717,7 +718,8 @@ static int run_hist_test(phprng_ctx *ctx, const char *what, uint64_t first, uint
         if (rc != PHPRNG_OK) return rc;
     }
     std::string err;
-    int rc = launch_serial(g, D, B, (unsigned long long *)hist, s, &err);
+    int rc = D < 0 ? launch_runs(g, (int)B, (unsigned long long *)hist, s, &err)
+                   : launch_serial(g, D, B, (unsigned long long *)hist, s, &err);
     if (rc != PHPRNG_OK) return fail(ctx, rc, w + ": " + err);
     for (uint64_t i = first; i < first + num_inst; ++i) ctx->pos_host[i] += per_inst;
     return PHPRNG_OK;
@@ -745,6 +747,18 @@ PH_API int phprng_poker_test(phprng_ctx *ctx, uint64_t first, uint64_t num_inst,
     if (!ctx) return fail(nullptr, PHPRNG_EINVAL, "phprng_poker_test: ctx is NULL");
     std::lock_guard<std::mutex> lk(ctx->mu);
     return run_hist_test(ctx, "phprng_poker_test", first, num_inst, per_inst, 0, 10, hist, cuda_stream);
+}
+
+PH_API int phprng_runs_test(phprng_ctx *ctx, uint64_t first, uint64_t num_inst, uint64_t per_inst,
+                            int lmax, uint64_t *hist, void *cuda_stream)
+{
+    if (!ctx) return fail(nullptr, PHPRNG_EINVAL, "phprng_runs_test: ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (lmax < 1 || lmax > 64) return fail(ctx, PHPRNG_EINVAL, "phprng_runs_test: lmax must be 1..64");
+    if (per_inst >= (1ull << 32))
+        return fail(ctx, PHPRNG_EINVAL, "phprng_runs_test: per_inst must be below 2^32");
+    return run_hist_test(ctx, "phprng_runs_test", first, num_inst, per_inst, -1, (uint32_t)lmax, hist,
+                         cuda_stream);
 }
 
 PH_API int phprng_seek(phprng_ctx *ctx, const uint64_t *inst_ids, const uint64_t *pos,

@@ -157,6 +157,9 @@ int launch_gen64(const GenArgs &a, void *stream, std::string *err);
 // five floor(10 R) cards into hist[7]); sk for NPT 8.
 int launch_serial(const GenArgs &a, int D, uint32_t B, unsigned long long *hist, void *stream,
                   std::string *err);
+// Runs-test consumer (serial.cu): completed runs of R <= 1/2 and R > 1/2 by
+// length (capped at lmax <= 64) added to hist[2 lmax]; sk for NPT 8.
+int launch_runs(const GenArgs &a, int lmax, unsigned long long *hist, void *stream, std::string *err);
 // Split launches: the pre-pass (sk8 = the NPT 8 skip constants) and the
 // number of warps the 32-bit generator keeps resident on the current device.
 int launch_chunk_sums(const GenArgs &a, const SkipConst &sk8, void *stream, std::string *err);

@@ -112,6 +112,113 @@ serial_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog
                                                x);
 }
 
+// Runs test (Tests section): bits b_k = (R_k > 1/2), i.e. c > (n-1)/2 (R is
+// exactly 1/2 only for c = (n-1)/2, and no rounding crosses 1/2 since a
+// nonzero distance to it is at least 1/(2(n+1))).  Per warp group the 256
+// bits go to shared memory as 8 words (number k at bit k % 32 of word k / 32)
+// with the transition words T (T_k = b_k != b_(k-1); T_0 against the bit of the
+// run still open from the previous group).  A run ends at k when T_(k+1) is
+// set; its start is the highest transition at or below k, or, when there is
+// none, it began in an earlier group and adds the carried length.  The run
+// still open at the group's end is carried; the one open at the call's end is
+// not counted.  Counts go to a per-warp shared histogram, flushed at the end.
+template <int NPT>
+__global__ void __launch_bounds__(256, 2)
+runs_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, DevState st,
+            SkipConst sk, uint64_t first, uint64_t num, uint64_t per_inst, int lmax,
+            unsigned long long *__restrict__ hist, const uint32_t *__restrict__ order)
+{
+    constexpr uint64_t G = 32 * NPT;
+    constexpr int NW = (int)(G / 32);                    // words of bits per group
+    __shared__ uint32_t wb[8][NW], wt[8][NW];
+    __shared__ uint32_t wh[8][128];                      // 2 lmax <= 128 counters per warp
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t w = (uint64_t)blockIdx.x * 8 + warp;
+    if (w >= num) return;
+    const uint64_t j = order ? order[w] : w;
+    const uint64_t i = first + j;
+    const DevInst P = inst[i];
+    const ExpProg &pg = prog[i];
+    const uint32_t half = (uint32_t)((P.n - 1) / 2);
+    uint32_t M = (uint32_t)st.m[i];
+    uint32_t sig = mont32((uint32_t)st.s[i], sk.lane[lane], sk.p, sk.pinv);
+    const uint64_t pos_after = st.pos[i] + per_inst;
+    uint32_t *B = wb[warp], *T = wt[warp], *h = wh[warp];
+    for (int b = lane; b < 2 * lmax; b += 32) h[b] = 0;
+    uint32_t cur_bit = 0, cur_len = 0;                   // run open at the group's start (0: none)
+    uint32_t x[NPT], sig_last = sig;
+    uint64_t g_last = 0;
+    for (uint64_t g0 = 0; g0 < per_inst; g0 += G) {
+        uint32_t sv[NPT], msg[NPT];
+        const uint64_t my0 = g0 + (uint64_t)NPT * lane;
+        sig_last = sig;
+        g_last = g0;
+        messages32<NPT>(P, sk, lane, my0, per_inst, M, sig, sv, msg);
+        encrypt32<NPT>(P, pg, msg, x);
+        const uint32_t valid = per_inst - g0 < G ? (uint32_t)(per_inst - g0) : (uint32_t)G;
+        uint32_t byte = 0;
+#pragma unroll
+        for (int u = 0; u < NPT; ++u)
+            if (my0 + u < per_inst && x[u] > half) byte |= 1u << u;
+        uint32_t word = byte << (8 * (lane & 3));
+        word |= __shfl_xor_sync(kFullMask, word, 1);
+        word |= __shfl_xor_sync(kFullMask, word, 2);
+        if ((lane & 3) == 0) B[lane >> 2] = word;
+        __syncwarp();
+        if (lane < NW) {
+            const uint32_t prev = (B[lane] << 1) | (lane ? B[lane - 1] >> 31 : cur_bit);
+            uint32_t t = B[lane] ^ prev;
+            if (lane == 0 && cur_len == 0) t |= 1u;      // the call's first number starts a run
+            T[lane] = t;
+        }
+        __syncwarp();
+        if (lane == 0 && cur_len && (T[0] & 1u))         // the carried run ended before this group
+            atomicAdd(&h[cur_bit * lmax + min(cur_len, (uint32_t)lmax) - 1], 1u);
+#pragma unroll
+        for (int u = 0; u < NPT; ++u) {
+            const uint32_t k = NPT * lane + u;
+            if (k + 1 >= valid || !((T[(k + 1) >> 5] >> ((k + 1) & 31)) & 1u)) continue;
+            // a run ends at k: its start is the highest transition at or below k
+            int wi = (int)(k >> 5);
+            uint32_t m = T[wi] & (((k & 31) == 31) ? 0xffffffffu : ((2u << (k & 31)) - 1u));
+            while (!m && wi > 0) m = T[--wi];
+            const uint32_t L = m ? k - (32u * wi + 31u - (uint32_t)__clz(m)) + 1u : k + 1u + cur_len;
+            const uint32_t bit = (B[k >> 5] >> (k & 31)) & 1u;
+            atomicAdd(&h[bit * lmax + min(L, (uint32_t)lmax) - 1], 1u);
+        }
+        // carry the run open at the group's end (every lane computes the same)
+        {
+            const uint32_t last = valid - 1;
+            int wi = (int)(last >> 5);
+            uint32_t m = T[wi] & (((last & 31) == 31) ? 0xffffffffu : ((2u << (last & 31)) - 1u));
+            while (!m && wi > 0) m = T[--wi];
+            const uint32_t new_bit = (B[last >> 5] >> (last & 31)) & 1u;
+            cur_len = m ? last - (32u * wi + 31u - (uint32_t)__clz(m)) + 1u : cur_len + valid;
+            cur_bit = new_bit;
+        }
+        __syncwarp();
+    }
+    __syncwarp();
+    for (int b = lane; b < 2 * lmax; b += 32)
+        if (h[b]) atomicAdd(hist + b, (unsigned long long)h[b]);
+    write_state_after<NPT, uint32_t, uint32_t>(st, sk, i, lane, g_last, per_inst, pos_after, M, sig_last,
+                                               x);
+}
+
+int launch_runs(const GenArgs &a, int lmax, unsigned long long *hist, void *stream, std::string *err)
+{
+    if (a.num == 0 || a.per_inst == 0) return PHPRNG_OK;
+    const uint64_t blocks = (a.num + 7) / 8;
+    runs_kernel<8><<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(
+        a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, lmax, hist, a.order);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        *err = std::string("runs_kernel launch: ") + cudaGetErrorString(e);
+        return PHPRNG_ECUDA;
+    }
+    return PHPRNG_OK;
+}
+
 int launch_serial(const GenArgs &a, int D, uint32_t B, unsigned long long *hist, void *stream,
                   std::string *err)
 {

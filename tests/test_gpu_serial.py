@@ -131,3 +131,50 @@ def test_poker_matches_oracle_and_probabilities(ph, torch):
         assert np.all(np.abs(z) < 6), z
     finally:
         ph.phprng_destroy(ctx)
+
+
+@pytest.mark.parametrize("lmax", [4, 32, 64])
+def test_runs_match_oracle(ph, torch, lmax):
+    """Runs spanning lanes, words and warp groups, carried across groups and
+    left open at each call's end, over two ragged calls: equal to the oracle;
+    the states continue."""
+    inst = workloads.draw_instances(29, seed=98 + lmax)
+    ctx = ph.phprng_create(32, inst, 0)
+    try:
+        rows = workloads.instance_rows(inst).copy()
+        hist = torch.zeros(2 * lmax, dtype=torch.int64, device="cuda")
+        want = np.zeros(2 * lmax, dtype=np.uint64)
+        for per in (257, 3000, 1):
+            ph.phprng_runs_test(ctx, 0, 29, per, lmax, hist)
+            c, _, st, _ = oracle.generate_many(rows, per, threads=THREADS, want_r=False)
+            for k in range(29):
+                oracle.runs_hist(c[k], int(rows[k, 0]), lmax, want)
+            rows[:, 4:6] = st
+        torch.cuda.synchronize()
+        assert np.array_equal(hist.cpu().numpy().view(np.uint64), want)
+        s = ph.phprng_get_state(ctx, 28)
+        assert (s["m"], s["s"], s["pos"]) == (int(rows[28, 4]), int(rows[28, 5]), 3258)
+    finally:
+        ph.phprng_destroy(ctx)
+
+
+def test_runs_small_modulus_long_runs(ph, torch):
+    """A tiny modulus with a unit-like skip gives long runs (lengths above
+    lmax land in the last bin) -- equal to the oracle."""
+    from test_gpu_parity import primitive_root
+    n, p = 1019, 509
+    a = primitive_root(p)
+    inst = {"n": [n, 1031], "e": [3, 7], "p": [p, p], "a": [a, a], "m0": [5, 900], "s0": [1, 2]}
+    ctx = ph.phprng_create(32, inst, ph.PHPRNG_ALLOW_SHARED_N)
+    try:
+        rows = np.array([[n, 3, p, a, 5, 1], [1031, 7, p, a, 900, 2]], dtype=np.uint64)
+        hist = torch.zeros(2 * 8, dtype=torch.int64, device="cuda")
+        ph.phprng_runs_test(ctx, 0, 2, 20000, 8, hist)
+        c, _, _, _ = oracle.generate_many(rows, 20000, threads=2, want_r=False)
+        want = np.zeros(16, dtype=np.uint64)
+        for k in range(2):
+            oracle.runs_hist(c[k], int(rows[k, 0]), 8, want)
+        torch.cuda.synchronize()
+        assert np.array_equal(hist.cpu().numpy().view(np.uint64), want)
+    finally:
+        ph.phprng_destroy(ctx)
