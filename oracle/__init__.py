@@ -87,6 +87,8 @@ class Oracle:
         lib.or_poker_hist.argtypes = [P64, u64, u64, P64]
         lib.or_runs_hist.restype = None
         lib.or_runs_hist.argtypes = [P64, u64, u64, ctypes.c_int, P64]
+        lib.or_pattern_hist.restype = None
+        lib.or_pattern_hist.argtypes = [u64, u64, u64, u64, u64, u64, ctypes.c_int, u64, P64]
         lib.or_generate_many.restype = u64
         lib.or_generate_many.argtypes = [P64, u64, u64, ctypes.c_int, P64, PD, P64]
         self.lib = lib
@@ -177,6 +179,16 @@ class Oracle:
             hist = np.zeros(2 * lmax, dtype=np.uint64)
         assert hist.dtype == np.uint64 and hist.size == 2 * lmax and hist.flags.c_contiguous
         self.lib.or_runs_hist(_p64(c), c.size, int(n), int(lmax), _p64(hist))
+        return hist
+
+    def pattern_hist(self, n, e, p, a, c_lo, L0, D, nb, hist=None):
+        """Full-period pattern of the D-tuples starting at c0 in [c_lo, c_lo+L0)
+        (the O(p L0) enumeration), added to hist (uint64[nb**(D-1)])."""
+        if hist is None:
+            hist = np.zeros(nb ** (D - 1), dtype=np.uint64)
+        assert hist.dtype == np.uint64 and hist.size == nb ** (D - 1) and hist.flags.c_contiguous
+        self.lib.or_pattern_hist(int(n), int(e), int(p), int(a), int(c_lo), int(L0), int(D), int(nb),
+                                 _p64(hist))
         return hist
 
     def generate_many(self, params, per_inst, threads=1, want_c=True, want_r=True):
@@ -271,3 +283,7 @@ def poker_hist(c, n, hist=None):
 
 def runs_hist(c, n, lmax, hist=None):
     return _default().runs_hist(c, n, lmax, hist)
+
+
+def pattern_hist(n, e, p, a, c_lo, L0, D, nb, hist=None):
+    return _default().pattern_hist(n, e, p, a, c_lo, L0, D, nb, hist)

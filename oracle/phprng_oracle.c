@@ -354,6 +354,46 @@ void or_runs_hist(const uint64_t *c, uint64_t N, uint64_t n, int Lmax, uint64_t 
     }
 }
 
+/* Full-period D-dimensional pattern by enumeration (the O(p L0) method that
+ * follows Eq. 7): over the full period n(p-1), ciphertext c_k = c0 occurs
+ * p-1 times, once with each skip s_(k+1) = s in (Z/pZ)*, with message
+ * m = c0^d mod n (d = e^-1 mod n-1, Eq. 2); the succeeding points are
+ * c_(k+j) = (m + s + a s + ... + a^(j-1) s (each term mod p))^e mod n.  For every
+ * c0 in [c_lo, c_lo + L0) and every s in 1 .. p-1 the point (c_(k+1), ...,
+ * c_(k+D-1)) adds one to hist[b_1 + nb b_2 + ... + nb^(D-2) b_(D-1)] with
+ * b_j = floor(c_(k+j) / L1), L1 = ceil(n / nb) (hist has nb^(D-1) entries and is
+ * added to).
+ * Pinned by: the same histogram counted by brute force over a whole period
+ * of tiny instances (or_generate, every k with c_k in the range); for D = 2
+ * and the whole range of c0, each bin holds p-1 times its count of values. */
+void or_pattern_hist(uint64_t n, uint64_t e, uint64_t p, uint64_t a, uint64_t c_lo,
+                     uint64_t L0, int D, uint64_t nb, uint64_t *hist)
+{
+    /* d = e^-1 mod (n-1) by the extended Euclidean algorithm */
+    int64_t r0 = (int64_t)(n - 1), r1 = (int64_t)(e % (n - 1)), t0 = 0, t1 = 1;
+    while (r1) {
+        int64_t q = r0 / r1, tmp;
+        tmp = r0 - q * r1; r0 = r1; r1 = tmp;
+        tmp = t0 - q * t1; t0 = t1; t1 = tmp;
+    }
+    uint64_t d = (uint64_t)(t0 < 0 ? t0 + (int64_t)(n - 1) : t0);
+    uint64_t L1 = (n + nb - 1) / nb;
+    for (uint64_t c0 = c_lo; c0 < c_lo + L0; ++c0) {
+        uint64_t m = or_powmod(c0, d, n);
+        for (uint64_t s = 1; s < p; ++s) {
+            uint64_t acc = m, t = s, idx = 0, scale = 1;
+            for (int j = 1; j < D; ++j) {
+                acc = (uint64_t)(((u128)acc + t) % n);
+                uint64_t c = or_powmod(acc, e, n);
+                idx += (c / L1) * scale;
+                scale *= nb;
+                t = or_mulmod(a, t, p);
+            }
+            hist[idx] += 1;
+        }
+    }
+}
+
 /* ---- threaded harness: many independent instances (parameter splitting,
  * Introduction: each process owns its own prime modulus) ------------------ */
 typedef struct {

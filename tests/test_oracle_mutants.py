@@ -52,6 +52,8 @@ MUTANTS = {
                             "int d = (int)(or_real(c[t * 5 + (uint64_t)k], n) * 9.0);"),
     "runs_threshold": ("int b = or_real(c[k], n) > 0.5;", "int b = or_real(c[k], n) >= 0.5;"),
     "runs_length_reset": ("        len = 1;\n    }", "        len = 0;\n    }"),
+    "pattern_skip_modulus": ("                t = or_mulmod(a, t, p);", "                t = or_mulmod(a, t, n);"),
+    "pattern_encrypts_not_decrypts": ("uint64_t m = or_powmod(c0, d, n);", "uint64_t m = or_powmod(c0, e, n);"),
     "dlog_index": ("L_out[q] = (i * M + val[h]) % order;", "L_out[q] = (i * M + val[h] + 1) % order;"),
 }
 

@@ -458,3 +458,39 @@ def test_runs_lengths_of_a_long_stream(oracle_mod):
         p = 0.5 ** L
         z = (runs[L - 1] - total * p) / np.sqrt(total * p * (1 - p))
         assert abs(z) < 5, (L, z)
+
+
+# ------------------------------------------------------------ full-period pattern
+@pytest.mark.parametrize("n,p,e", [(23, 11, 3), (107, 53, 5), (1019, 509, 3), (1031, 103, 7)])
+@pytest.mark.parametrize("D,nb,c_lo,L0", [(2, 8, 0, None), (3, 5, 2, 9), (4, 3, 0, 40)])
+def test_pattern_equals_full_period_brute_force(oracle_mod, n, p, e, D, nb, c_lo, L0):
+    """The O(p L0) enumeration equals counting, over a whole period n(p-1) of
+    the generator, the D-tuples whose first number lies in [c_lo, c_lo+L0)."""
+    if L0 is None:
+        L0 = n - c_lo
+    L0 = min(L0, n - c_lo)
+    a = primitive_root(p)
+    P = n * (p - 1)
+    c, _, _ = oracle_mod.generate(n, e, p, a, 4 % n, 3 % p or 1, P)
+    L1 = -(-n // nb)
+    want = np.zeros(nb ** (D - 1), dtype=np.uint64)
+    for k in range(P):
+        if c_lo <= c[k] < c_lo + L0:
+            idx = 0
+            for j in range(1, D):
+                idx += (int(c[(k + j) % P]) // L1) * nb ** (j - 1)
+            want[idx] += 1
+    got = oracle_mod.pattern_hist(n, e, p, a, c_lo, L0, D, nb)
+    assert np.array_equal(got, want)
+
+
+def test_pattern_2d_whole_range_is_uniform(oracle_mod):
+    """D = 2 over every c0: each value c1 appears p-1 times."""
+    n, p, e = 1019, 509, 3
+    a = primitive_root(p)
+    nb = 7
+    got = oracle_mod.pattern_hist(n, e, p, a, 0, n, 2, nb)
+    L1 = -(-n // nb)
+    want = np.array([(p - 1) * len(range(b * L1, min((b + 1) * L1, n))) for b in range(nb)],
+                    dtype=np.uint64)
+    assert np.array_equal(got, want)
