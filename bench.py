@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=64)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--modes", default="fused,serial,small_e,wide64,batched,served",
+    ap.add_argument("--modes", default="fused,serial,small_e,pattern,wide64,batched,served",
                     help="comma-separated extra measurements after the headline, or 'none'")
     return ap.parse_args()
 
@@ -227,6 +227,28 @@ def mode_serial(ph, torch, ctx, N, per, stream):
     dof = B ** D - 1
     return {"value": N * per / ms * 1e3, "unit": "PRNs/s", "ms_per_call": ms,
             "workload": "plain32 65,536 x 4,096, pairs into 2^20 bins (8 MiB histogram)",
+            "chi2_z": (chi2 - dof) / (2 * dof) ** 0.5}
+
+
+def mode_pattern(ph, torch, stream, L0=128):
+    """The full-period three-dimensional pattern of the paper's instance
+    (n = 4294967087, p = 2^31-1, a = 784588716, e = 9) in 2^24 volumes of
+    L0 L1^2, L0 = 2^7, by the O(p L0) enumeration: L0 (p-1) points, two
+    exponentiations each; chi-square of the volumes against uniform."""
+    n, p, a, e, D, nb = 4294967087, 2147483647, 784588716, 9, 3, 4096
+    hist = torch.zeros(nb ** (D - 1), dtype=torch.int64, device="cuda")
+    ms = timed(torch, stream, lambda: ph.phprng_pattern(n, e, p, a, 0, L0, D, nb, hist, stream), 1,
+               warmup=0)
+    got = hist.cpu().numpy().astype(np.float64)
+    L1 = -(-n // nb)
+    widths = np.array([min(L1, n - b * L1) for b in range(nb)], dtype=np.float64) / n
+    expect = L0 * (p - 1) * np.outer(widths, widths).reshape(-1)
+    chi2 = float(((got - expect) ** 2 / expect).sum())
+    dof = nb ** (D - 1) - 1
+    points = L0 * (p - 1)
+    return {"value": points / ms * 1e3, "unit": "points/s", "ms": ms,
+            "exponentiations_per_s": 2 * points / ms * 1e3,
+            "workload": "paper's pattern instance, D = 3, L0 = 2^7, 2^24 volumes (2^38 points)",
             "chi2_z": (chi2 - dof) / (2 * dof) ** 0.5}
 
 
@@ -515,6 +537,7 @@ def main():
         for name, fn in (("fused", lambda: mode_fused(ph, torch, ctx2, N, per, stream, 8)),
                          ("serial", lambda: mode_serial(ph, torch, ctx2, N, per, stream)),
                          ("small_e", lambda: mode_small_e(ph, torch, stream, PEAK_TMULS)),
+                         ("pattern", lambda: mode_pattern(ph, torch, stream)),
                          ("wide64", lambda: mode_wide64(ph, torch, stream, PEAK_TMULS)),
                          ("batched", lambda: mode_batched(ph, torch, stream)),
                          ("served", lambda: mode_served(ph, torch))):

@@ -219,6 +219,25 @@ int phprng_poker_test(phprng_ctx *ctx, uint64_t first, uint64_t num_inst, uint64
 int phprng_runs_test(phprng_ctx *ctx, uint64_t first, uint64_t num_inst, uint64_t per_inst,
                      int lmax, uint64_t *hist, void *cuda_stream);
 
+/* Full-period D-dimensional pattern of one instance (32-bit n) by
+ * enumeration, as the paper derives after Eq. 7: over the whole period
+ * n(p-1) the value c0 occurs p-1 times, once with each next skip s in
+ * (Z/pZ)*, always with message m = c0^d mod n (d = e^-1 mod n-1, Eq. 2), so
+ * the tuples that start at c0 are c_(k+j) = (m + s + a s + ... + a^(j-1) s)^e
+ * mod n (skip terms mod p, sums mod n), j = 1 .. D-1.  For every c0 in
+ * [c_lo, c_lo + L0) and every s in 1 .. p-1 the point adds one to
+ * hist[b_1 + nb b_2 + ... + nb^(D-2) b_(D-1)], b_j = floor(c_(k+j) / L1) with
+ * L1 = ceil(n / nb): L0 (p-1) points and (D-1) L0 (p-1) exponentiations
+ * instead of n(p-1) steps.  The paper's volumes: L0 = 2^7 and nb^(D-1) = 2^24
+ * for D = 3, 4, 5 (expected count (p-1) L0 (L1/n)^(D-1) per volume).
+ * inst: validated like one instance of phprng_create (width 32, no flags);
+ * its m0 and s0 are not used.  Limits: 1 <= L0 <= 2^20, c_lo + L0 <= n,
+ * 2 <= D <= 8, nb^(D-1) <= 2^24.  hist: device memory, nb^(D-1) uint64
+ * counters, added to.  Needs no context; asynchronous on cuda_stream; errors
+ * are reported through phprng_last_error(NULL). */
+int phprng_pattern(const phprng_instance *inst, uint64_t c_lo, uint64_t L0, int D, uint32_t nb,
+                   uint64_t *hist, void *cuda_stream);
+
 /* Moves instance inst_ids[i] to absolute stream position pos[i], forward or
  * backward: afterwards its next number is number pos[i]+1 of the stream
  * counted from its seed, and its state (m, s, c) is the one generation would

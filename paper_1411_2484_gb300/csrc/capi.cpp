@@ -761,6 +761,74 @@ PH_API int phprng_runs_test(phprng_ctx *ctx, uint64_t first, uint64_t num_inst, 
                          cuda_stream);
 }
 
+// e^-1 mod m (gcd(e, m) = 1) by the extended Euclidean algorithm.
+static uint64_t inverse_mod(uint64_t e, uint64_t m)
+{
+    __int128 r0 = m, r1 = e % m, t0 = 0, t1 = 1;
+    while (r1) {
+        const __int128 q = r0 / r1;
+        __int128 tmp = r0 - q * r1;
+        r0 = r1;
+        r1 = tmp;
+        tmp = t0 - q * t1;
+        t0 = t1;
+        t1 = tmp;
+    }
+    return (uint64_t)(t0 < 0 ? t0 + m : t0);
+}
+
+PH_API int phprng_pattern(const phprng_instance *inst, uint64_t c_lo, uint64_t L0, int D, uint32_t nb,
+                          uint64_t *hist, void *cuda_stream)
+{
+    if (!inst) return fail(nullptr, PHPRNG_EINVAL, "phprng_pattern: inst is NULL");
+    phprng_instance in = *inst;
+    in.m0 = 0;                                               // the seeds play no part
+    in.s0 = 1;
+    std::string msg;
+    int rc = validate_one(32, in, 0, &msg);
+    if (rc != PHPRNG_OK) return fail(nullptr, rc, "phprng_pattern: " + msg);
+    inst = &in;
+    const uint64_t n = inst->n;
+    if (L0 < 1 || L0 > (1ull << 20) || c_lo >= n || L0 > n - c_lo)
+        return fail(nullptr, PHPRNG_EINVAL,
+                    "phprng_pattern: need 1 <= L0 <= 2^20 and c_lo + L0 <= n");
+    if (D < 2 || D > 8) return fail(nullptr, PHPRNG_EINVAL, "phprng_pattern: D must be 2..8");
+    uint64_t bins = 1;
+    for (int d = 1; d < D && bins <= (1ull << 24); ++d) bins *= nb;
+    if (nb < 1 || bins > (1ull << 24))
+        return fail(nullptr, PHPRNG_EINVAL, "phprng_pattern: nb^(D-1) must be 1 .. 2^24");
+    if (!hist || (uintptr_t)hist % 8)
+        return fail(nullptr, PHPRNG_EINVAL, "phprng_pattern: hist NULL or not 8-byte aligned");
+    if (pointer_kind(hist) != 1)
+        return fail(nullptr, PHPRNG_EINVAL, "phprng_pattern: hist must be device memory");
+    ExpProg pg;
+    const DevInst P = derive_inst(*inst, 0, &pg);
+    const SkipConst sk = derive_skip(inst->p, inst->a, 8);
+    const uint64_t d = inverse_mod(inst->e, n - 1);            // Eq. 2
+    std::vector<uint32_t> mtab;
+    try {
+        mtab.resize(L0);
+    } catch (const std::bad_alloc &) {
+        return fail(nullptr, PHPRNG_ENOMEM, "phprng_pattern: host allocation failed");
+    }
+    for (uint64_t q = 0; q < L0; ++q) mtab[q] = (uint32_t)powmod(c_lo + q, d, n);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    uint32_t *d_m = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&d_m, L0 * sizeof(uint32_t), s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(nullptr, PHPRNG_ENOMEM, "phprng_pattern: device allocation failed");
+    }
+    // from pageable memory: staged before the call returns, then ordered on s
+    e = cudaMemcpyAsync(d_m, mtab.data(), L0 * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
+    std::string err;
+    rc = e == cudaSuccess ? launch_pattern(P, pg, sk, d_m, L0, D, nb, hist, s, &err) : PHPRNG_ECUDA;
+    cudaFreeAsync(d_m, s);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "phprng_pattern: upload");
+    if (rc != PHPRNG_OK) return fail(nullptr, rc, "phprng_pattern: " + err);
+    return PHPRNG_OK;
+}
+
 PH_API int phprng_seek(phprng_ctx *ctx, const uint64_t *inst_ids, const uint64_t *pos,
                        uint64_t cnt, void *cuda_stream)
 {

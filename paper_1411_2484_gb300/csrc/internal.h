@@ -160,6 +160,10 @@ int launch_serial(const GenArgs &a, int D, uint32_t B, unsigned long long *hist,
 // Runs-test consumer (serial.cu): completed runs of R <= 1/2 and R > 1/2 by
 // length (capped at lmax <= 64) added to hist[2 lmax]; sk for NPT 8.
 int launch_runs(const GenArgs &a, int lmax, unsigned long long *hist, void *stream, std::string *err);
+// Full-period pattern by enumeration (pattern.cu): mtab[q] = (c_lo+q)^d mod n
+// for q < L0, sk for NPT 8; hist has nb^(D-1) uint64 counters.
+int launch_pattern(const DevInst &P, const ExpProg &pg, const SkipConst &sk, const uint32_t *mtab,
+                   uint64_t L0, int D, uint32_t nb, uint64_t *hist, void *stream, std::string *err);
 // Split launches: the pre-pass (sk8 = the NPT 8 skip constants) and the
 // number of warps the 32-bit generator keeps resident on the current device.
 int launch_chunk_sums(const GenArgs &a, const SkipConst &sk8, void *stream, std::string *err);

@@ -1,0 +1,96 @@
+// pattern.cu -- the full-period D-dimensional pattern of one 32-bit instance
+// by enumeration (the O(p L0) method that follows Eq. 7 in the paper).
+//
+// Over the full period n(p-1), the ciphertext value c0 occurs p-1 times, once
+// with each skip s = s_(k+1) in (Z/pZ)*, and always with the message
+// m = c0^d mod n (Eq. 2).  So the D-tuples (c0, c_(k+1), ..., c_(k+D-1)) of the
+// whole period with c0 in a range [c_lo, c_lo + L0) are the points
+//     c_(k+j) = (m + s + a s + ... + a^(j-1) s)^e mod n   (skips mod p, sum mod n)
+// for every c0 of the range and every s -- L0 (p-1) exponentiation chains
+// instead of a walk over n(p-1) numbers.  A thread takes NPT consecutive
+// skips of one c0 and runs them as NPT independent chains of the same
+// exponent program (gencore.cuh); each point adds one to a histogram of
+// nb^(D-1) counters (bin floor(c / L1) per coordinate, L1 = ceil(n / nb)).
+#include <cuda_runtime.h>
+
+#include "gencore.cuh"
+
+namespace phprng {
+
+// floor(x / L1) for L1 >= 2: with r = floor(2^32 / L1) the estimate
+// floor(x r / 2^32) is the quotient or one below it (r is short of 2^32 / L1 by
+// less than 1 and x < 2^32), and one comparison decides.
+__device__ __forceinline__ uint32_t div_by_width(uint32_t x, uint32_t L1, uint32_t r)
+{
+    uint32_t q = umulhi32(x, r);
+    if ((uint64_t)(q + 1) * L1 <= x) ++q;
+    return q;
+}
+
+template <int NPT>
+__global__ void __launch_bounds__(256, 2)
+pattern_kernel(DevInst P, ExpProg pg, SkipConst sk, const uint32_t *__restrict__ mtab, uint64_t L0,
+               int D, uint32_t nb, uint32_t L1, uint32_t rL1, unsigned long long *__restrict__ hist)
+{
+    const uint32_t p = sk.p, n = (uint32_t)P.n;
+    const uint64_t per_c0 = (p - 2 + NPT) / NPT;          // thread items per c0: skips 1 .. p-1
+    const uint64_t items = L0 * per_c0;
+    for (uint64_t it = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; it < items;
+         it += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t q = it / per_c0;
+        const uint32_t s0 = (uint32_t)((it - q * per_c0) * NPT) + 1;
+        const uint32_t m = mtab[q];
+        uint32_t t[NPT], acc[NPT], x[NPT], idx[NPT];
+#pragma unroll
+        for (int u = 0; u < NPT; ++u) {
+            // skips past p-1 (the last item of a c0) are computed and not counted
+            t[u] = s0 + u < p ? s0 + u : 1u;
+            acc[u] = m;
+            idx[u] = 0;
+        }
+        uint32_t scale = 1;
+        for (int j = 1; j < D; ++j) {
+#pragma unroll
+            for (int u = 0; u < NPT; ++u) acc[u] = addmod32(acc[u], t[u], n);
+            encrypt<NPT, uint32_t>(P, pg, acc, x);                     // Eq. 9c
+#pragma unroll
+            for (int u = 0; u < NPT; ++u)
+                idx[u] += (L1 == 1 ? x[u] : div_by_width(x[u], L1, rL1)) * scale;
+            scale *= nb;
+            if (j + 1 < D) {
+#pragma unroll
+                for (int u = 0; u < NPT; ++u) t[u] = mont32(t[u], sk.aM, p, sk.pinv);   // Eq. 9a
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < NPT; ++u)
+            if (s0 + u < p) atomicAdd(hist + idx[u], 1ull);
+    }
+}
+
+int launch_pattern(const DevInst &P, const ExpProg &pg, const SkipConst &sk, const uint32_t *mtab,
+                   uint64_t L0, int D, uint32_t nb, uint64_t *hist, void *stream, std::string *err)
+{
+    constexpr int NPT = 8;
+    const uint32_t n = (uint32_t)P.n;
+    const uint32_t L1 = (uint32_t)((n + (uint64_t)nb - 1) / nb);
+    const uint32_t rL1 = L1 >= 2 ? (uint32_t)((1ull << 32) / L1) : 0u;
+    int dev = 0, sms = 0, bps = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, pattern_kernel<NPT>, 256, 0);
+    const uint64_t items = L0 * ((sk.p - 2 + NPT) / NPT);
+    uint64_t grid = (items + 255) / 256;
+    const uint64_t cap = (uint64_t)(sms > 0 ? sms : 1) * (bps > 0 ? bps : 1) * 8;
+    if (grid > cap) grid = cap;
+    pattern_kernel<NPT><<<(unsigned)grid, 256, 0, (cudaStream_t)stream>>>(
+        P, pg, sk, mtab, L0, D, nb, L1, rL1, (unsigned long long *)hist);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        *err = std::string("pattern_kernel launch: ") + cudaGetErrorString(e);
+        return PHPRNG_ECUDA;
+    }
+    return PHPRNG_OK;
+}
+
+}  // namespace phprng

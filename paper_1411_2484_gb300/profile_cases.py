@@ -7,6 +7,8 @@ CASE is one of
   fused32   the same instances, statistics only                      gen32_kernel (STATS)
   small_e   65,536 instances with e = 9 x 4,096 numbers, R (2 GiB)   gen32_kernel
   serial2   plain32's instances, pairs into 2^20 bins (serial test)  serial_kernel
+  pattern3  the paper's pattern instance (n = 4294967087, p = 2^31-1,
+            e = 9), D = 3, 2^24 volumes, L0 = 4 (2^33 points)       pattern_kernel
   wide64    4,096 64-bit instances x 4,096 numbers, R (128 MiB)      gen64_kernel
   batched   2,000 instances (80 % 32-bit), lengths log-uniform in
             [1, 2^18], offsets in [0, 2^40), R (about 0.4 GiB)       batch_kernel
@@ -25,12 +27,16 @@ from paper_1411_2484_gb300 import workloads
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["plain32", "fused32", "small_e", "serial2", "wide64", "batched"])
+    ap.add_argument("case", choices=["plain32", "fused32", "small_e", "serial2", "pattern3", "wide64", "batched"])
     ap.add_argument("--repeat", type=int, default=3)
     args = ap.parse_args()
     s = torch.cuda.current_stream()
     ctx, plan = None, None
-    if args.case == "serial2":
+    if args.case == "pattern3":
+        hist = torch.zeros(1 << 24, dtype=torch.int64, device="cuda")
+        run = lambda: ph.phprng_pattern(4294967087, 9, 2147483647, 784588716, 1000, 4, 3, 4096, hist, s)
+        numbers = 4 * (2147483647 - 1) * 2                  # exponentiations
+    elif args.case == "serial2":
         inst = workloads.workload_instances("plain32_65536x4096x64")
         N, per = 65536, 4096
         ctx = ph.phprng_create(32, inst, ph.PHPRNG_REQUIRE_SAFE_PRIME, s)
@@ -87,7 +93,8 @@ def main():
     finally:
         if plan:
             ph.phprng_plan_destroy(plan)
-        ph.phprng_destroy(ctx)
+        if ctx:
+            ph.phprng_destroy(ctx)
 
 
 if __name__ == "__main__":

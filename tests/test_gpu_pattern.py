@@ -1,0 +1,63 @@
+"""GPU tests of the full-period pattern enumeration (phprng_pattern) through the
+C ABI: equal to the oracle's enumeration (itself pinned against brute-force
+counts over whole periods), and the paper's instance at scale."""
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available()
+    return t
+
+
+def run(ph, torch, n, e, p, a, c_lo, L0, D, nb):
+    hist = torch.zeros(nb ** (D - 1), dtype=torch.int64, device="cuda")
+    ph.phprng_pattern(n, e, p, a, c_lo, L0, D, nb, hist)
+    torch.cuda.synchronize()
+    return hist.cpu().numpy().view(np.uint64)
+
+
+@pytest.mark.parametrize("n,p,e", [(1019, 509, 3), (1031, 103, 7), (4294967087, 65537, 9),
+                                   (4294967087, 65537, 4294967085)])
+@pytest.mark.parametrize("D,nb", [(2, 8), (3, 16), (5, 4)])
+def test_pattern_matches_oracle(ph, torch, n, p, e, D, nb):
+    from test_gpu_parity import primitive_root
+    a = primitive_root(p)
+    c_lo, L0 = (0, n) if n < 5000 else (123456, 24)
+    got = run(ph, torch, n, e, p, a, c_lo, L0, D, nb)
+    want = oracle.pattern_hist(n, e, p, a, c_lo, L0, D, nb)
+    assert np.array_equal(got, want)
+
+
+def test_pattern_paper_instance_uniform(ph, torch):
+    """The instance of the paper's pattern figures (n = 4294967087, p = 2^31-1,
+    a = 784588716, e = 9): L0 (p-1) points, and over 4,096 volumes of a
+    three-dimensional pattern a chi-square consistent with uniform (|z| < 6)."""
+    n, p, a, e = 4294967087, 2147483647, 784588716, 9
+    D, nb, L0 = 3, 64, 2
+    got = run(ph, torch, n, e, p, a, 1000, L0, D, nb).astype(np.float64)
+    assert got.sum() == L0 * (p - 1)
+    L1 = -(-n // nb)
+    widths = np.array([min(L1, n - b * L1) for b in range(nb)], dtype=np.float64) / n
+    expect = L0 * (p - 1) * np.outer(widths, widths).reshape(-1)    # index b1 + nb b2
+    chi2 = float(((got - expect) ** 2 / expect).sum())
+    dof = nb ** (D - 1) - 1
+    assert abs(chi2 - dof) / np.sqrt(2 * dof) < 6, chi2
+
+
+def test_pattern_argument_errors(ph, torch):
+    h = torch.zeros(1 << 10, dtype=torch.int64, device="cuda")
+    n, p, a = 1019, 509, 2
+    for args in [(n, 3, p, a, 0, 0, 2, 8), (n, 3, p, a, 1000, 20, 2, 8), (n, 3, p, a, 0, 8, 1, 8),
+                 (n, 3, p, a, 0, 8, 9, 2), (n, 3, p, a, 0, 8, 3, 5000), (n, 4, p, a, 0, 8, 2, 8),
+                 (1021, 3, p, a, 0, 8, 2, 8)]:
+        with pytest.raises(ph.PhprngError):
+            ph.phprng_pattern(*args, h)
+    with pytest.raises(ph.PhprngError):
+        ph.phprng_pattern(n, 3, p, a, 0, 8, 2, 8, np.zeros(8, dtype=np.uint64))   # host memory
