@@ -27,10 +27,14 @@ __device__ __forceinline__ uint32_t div_by_width(uint32_t x, uint32_t L1, uint32
     return q;
 }
 
+// The counts go to 32-bit counters (nb^(D-1) <= 2^24: at most 64 MiB, which
+// L2 holds, where 64-bit counters spilled their reductions to DRAM); the
+// host runs chunks of c0 with fewer than 2^32 points each and folds the
+// 32-bit counters into the caller's 64-bit ones after every chunk.
 template <int NPT>
 __global__ void __launch_bounds__(256, 2)
 pattern_kernel(DevInst P, ExpProg pg, SkipConst sk, const uint32_t *__restrict__ mtab, uint64_t L0,
-               int D, uint32_t nb, uint32_t L1, uint32_t rL1, unsigned long long *__restrict__ hist)
+               int D, uint32_t nb, uint32_t L1, uint32_t rL1, unsigned int *__restrict__ hist)
 {
     const uint32_t p = sk.p, n = (uint32_t)P.n;
     const uint64_t per_c0 = (p - 2 + NPT) / NPT;          // thread items per c0: skips 1 .. p-1
@@ -64,7 +68,21 @@ pattern_kernel(DevInst P, ExpProg pg, SkipConst sk, const uint32_t *__restrict__
         }
 #pragma unroll
         for (int u = 0; u < NPT; ++u)
-            if (s0 + u < p) atomicAdd(hist + idx[u], 1ull);
+            if (s0 + u < p) atomicAdd(hist + idx[u], 1u);
+    }
+}
+
+// hist64[i] += hist32[i]; hist32[i] = 0.
+__global__ void __launch_bounds__(256)
+fold_counts_kernel(unsigned int *__restrict__ h32, unsigned long long *__restrict__ h64, uint64_t bins)
+{
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < bins;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const unsigned int v = h32[i];
+        if (v) {
+            h64[i] += v;
+            h32[i] = 0;
+        }
     }
 }
 
@@ -72,20 +90,40 @@ int launch_pattern(const DevInst &P, const ExpProg &pg, const SkipConst &sk, con
                    uint64_t L0, int D, uint32_t nb, uint64_t *hist, void *stream, std::string *err)
 {
     constexpr int NPT = 8;
+    cudaStream_t s = (cudaStream_t)stream;
     const uint32_t n = (uint32_t)P.n;
     const uint32_t L1 = (uint32_t)((n + (uint64_t)nb - 1) / nb);
     const uint32_t rL1 = L1 >= 2 ? (uint32_t)((1ull << 32) / L1) : 0u;
+    uint64_t bins = 1;
+    for (int d = 1; d < D; ++d) bins *= nb;
     int dev = 0, sms = 0, bps = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, pattern_kernel<NPT>, 256, 0);
-    const uint64_t items = L0 * ((sk.p - 2 + NPT) / NPT);
-    uint64_t grid = (items + 255) / 256;
     const uint64_t cap = (uint64_t)(sms > 0 ? sms : 1) * (bps > 0 ? bps : 1) * 8;
-    if (grid > cap) grid = cap;
-    pattern_kernel<NPT><<<(unsigned)grid, 256, 0, (cudaStream_t)stream>>>(
-        P, pg, sk, mtab, L0, D, nb, L1, rL1, (unsigned long long *)hist);
-    cudaError_t e = cudaGetLastError();
+    unsigned int *h32 = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&h32, bins * sizeof(unsigned int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h32, 0, bins * sizeof(unsigned int), s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (h32) cudaFreeAsync(h32, s);
+        *err = std::string("pattern counters: ") + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? PHPRNG_ENOMEM : PHPRNG_ECUDA;
+    }
+    // chunks of c0 with fewer than 2^32 points, so no 32-bit counter wraps
+    const uint64_t per_c0 = sk.p - 1;
+    const uint64_t chunk = ((1ull << 32) - 1) / per_c0 ? ((1ull << 32) - 1) / per_c0 : 1;
+    const uint64_t fold_grid = (bins + 255) / 256 < cap ? (bins + 255) / 256 : cap;
+    for (uint64_t q0 = 0; q0 < L0 && e == cudaSuccess; q0 += chunk) {
+        const uint64_t lq = L0 - q0 < chunk ? L0 - q0 : chunk;
+        const uint64_t items = lq * ((sk.p - 2 + NPT) / NPT);
+        uint64_t grid = (items + 255) / 256;
+        if (grid > cap) grid = cap;
+        pattern_kernel<NPT><<<(unsigned)grid, 256, 0, s>>>(P, pg, sk, mtab + q0, lq, D, nb, L1, rL1, h32);
+        fold_counts_kernel<<<(unsigned)fold_grid, 256, 0, s>>>(h32, (unsigned long long *)hist, bins);
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(h32, s);
     if (e != cudaSuccess) {
         *err = std::string("pattern_kernel launch: ") + cudaGetErrorString(e);
         return PHPRNG_ECUDA;
