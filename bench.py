@@ -333,7 +333,7 @@ def mode_batched(ph, torch, stream):
     return out
 
 
-def mode_served(ph, torch, duration_s=10.0, warm_s=1.0, rate=50000.0):
+def mode_served(ph, torch, duration_s=10.0, warm_s=1.0, rate=50000.0, tile=0):
     """1,000,000 32-bit streams, open-loop Poisson arrivals at 50k requests/s,
     sizes min(round(lognormal(ln 4096, 2)), 2^22), admission bounded by 16 GiB
     of outputs; PRNs/s and p50/p99 latency from arrival to completion."""
@@ -341,7 +341,7 @@ def mode_served(ph, torch, duration_s=10.0, warm_s=1.0, rate=50000.0):
     ctx = ph.phprng_create_seeded(32, 1_000_000, 0x5EED0004, ph.PHPRNG_REQUIRE_SAFE_PRIME)
     srv = None
     try:
-        srv = ph.phprng_server_create(ctx, 16 << 30, max_batch=4096, inflight=4, tile=4096)
+        srv = ph.phprng_server_create(ctx, 16 << 30, max_batch=4096, inflight=4, tile=tile)
         span = warm_s + duration_s
         n = int(rate * span * 1.05) + 100
         gaps = rng.exponential(1.0 / rate, n)
@@ -379,7 +379,7 @@ def mode_served(ph, torch, duration_s=10.0, warm_s=1.0, rate=50000.0):
             "latency_ms": {"p50": float(np.percentile(l_ms, 50)),
                            "p99": float(np.percentile(l_ms, 99)),
                            "max": float(l_ms.max())},
-            "offered_rate_req_s": rate, "batches": st["batches"],
+            "offered_rate_req_s": rate, "batches": st["batches"], "tile": tile,
             "max_waiting": st["max_waiting"],
             "workload": "1,000,000 32-bit streams, Poisson 50k req/s, lognormal(ln 4096, 2) "
                         "sizes capped at 2^22, 16 GiB admission, R only"}

@@ -336,7 +336,9 @@ typedef struct {
     uint64_t output_budget_bytes;  /* arena size: the admission bound on outstanding outputs */
     uint32_t max_batch;            /* requests per launch (0 = 4096) */
     uint32_t inflight;             /* launches in flight, one CUDA stream each (0 = 2, max 16) */
-    uint32_t tile;                 /* numbers per tile (0 = 4096) */
+    uint32_t tile;                 /* numbers per tile; 0 = sized per launch: about one tile
+                                      per resident warp, 256 to 4096 numbers (the lowest
+                                      latency at light load) */
     uint32_t want_c;               /* nonzero: also store ciphertexts after each request's R */
 } phprng_server_config;
 

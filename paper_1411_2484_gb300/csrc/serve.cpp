@@ -70,6 +70,8 @@ const uint64_t kAlign = 256;                    // arena slice alignment (bytes)
 struct phprng_server {
     phprng_ctx *ctx = nullptr;
     phprng_server_config cfg{};
+    bool auto_tile = false;                      // cfg.tile was 0: tiles sized per launch
+    uint64_t resident_warps = 1;                 // warps of batch_kernel the GPU keeps resident
     char *arena = nullptr;
     uint64_t arena_bytes = 0;
     std::map<uint64_t, uint64_t> free_list;     // offset -> size
@@ -146,7 +148,18 @@ static int launch_slot(phprng_server *s, Slot &sl)
 {
     phprng_ctx *c = s->ctx;
     uint64_t nt = 0;
-    const uint64_t tile = s->cfg.tile;
+    uint64_t tile = s->cfg.tile;
+    if (s->auto_tile) {
+        // about one tile per resident warp: a lightly loaded server finishes a
+        // launch in the time of one short tile; never more than kSlotTiles tiles
+        uint64_t total = 0;
+        for (const Req &r : sl.reqs) total += r.len;
+        const uint64_t round = 256;
+        uint64_t t = (total + s->resident_warps - 1) / s->resident_warps;
+        t = std::min<uint64_t>(std::max<uint64_t>((t + round - 1) / round * round, round), 4096);
+        const uint64_t cap_t = (total + (kSlotTiles - sl.reqs.size()) - 1) / (kSlotTiles - sl.reqs.size());
+        tile = std::max(t, (cap_t + round - 1) / round * round);
+    }
     for (const Req &r : sl.reqs) {
         const uint32_t wide = c->wide[r.inst] ? kTileWide : 0u;
         const uint64_t r_off = r.off / 8;
@@ -318,7 +331,14 @@ PH_API int phprng_server_create(phprng_ctx *ctx, const phprng_server_config *cfg
     s->cfg = *cfg;
     if (!s->cfg.max_batch) s->cfg.max_batch = 4096;
     if (!s->cfg.inflight) s->cfg.inflight = 2;
-    if (!s->cfg.tile) s->cfg.tile = 4096;
+    s->auto_tile = s->cfg.tile == 0;              // 0: sized per launch (launch_slot)
+    if (!s->cfg.tile) s->cfg.tile = 4096;         // the largest tile, for admission checks
+    {
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+        const int b = batch_max_blocks_per_sm(8, ctx->width != 32);
+        s->resident_warps = (uint64_t)(sms > 0 ? sms : 1) * (b > 0 ? b : 1) * 8;
+    }
     if (s->cfg.tile > (1u << 24) || s->cfg.inflight > 16) {
         delete s;
         return fail(ctx, PHPRNG_EINVAL, "phprng_server_create: tile or inflight out of range");

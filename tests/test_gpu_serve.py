@@ -48,11 +48,12 @@ def drain(ph, srv, total, copy=True, release=True, timeout=60.0):
     return got
 
 
-def test_served_requests_match_oracle_and_fifo(ph, torch, table31):
+@pytest.mark.parametrize("tile", [1024, 0], ids=["tile1024", "auto_tile"])
+def test_served_requests_match_oracle_and_fifo(ph, torch, table31, tile):
     inst = workloads.draw_instances(40, seed=601)
     L0 = oracle.dlog(P31, A31, inst["s0"])
     ctx = ph.phprng_create(32, inst, 0)
-    srv = ph.phprng_server_create(ctx, 64 << 20, inflight=3, tile=1024, want_c=1)
+    srv = ph.phprng_server_create(ctx, 64 << 20, inflight=3, tile=tile, want_c=1)
     try:
         rng = np.random.default_rng(3)
         n = 400
