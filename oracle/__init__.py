@@ -89,6 +89,8 @@ class Oracle:
         lib.or_runs_hist.argtypes = [P64, u64, u64, ctypes.c_int, P64]
         lib.or_pattern_hist.restype = None
         lib.or_pattern_hist.argtypes = [u64, u64, u64, u64, u64, u64, ctypes.c_int, u64, P64]
+        lib.or_collision_hist.restype = None
+        lib.or_collision_hist.argtypes = [P64, u64, u64, u64, u64, u64, P64]
         lib.or_generate_many.restype = u64
         lib.or_generate_many.argtypes = [P64, u64, u64, ctypes.c_int, P64, PD, P64]
         self.lib = lib
@@ -191,6 +193,16 @@ class Oracle:
                                  _p64(hist))
         return hist
 
+    def collision_hist(self, c, n, S, B, H, hist=None):
+        """Adds one stream's per-segment collision counts (segments of S numbers
+        into B bins, counts capped at H-1) to hist (uint64[H])."""
+        c = np.ascontiguousarray(c, dtype=np.uint64)
+        if hist is None:
+            hist = np.zeros(H, dtype=np.uint64)
+        assert hist.dtype == np.uint64 and hist.size == H and hist.flags.c_contiguous
+        self.lib.or_collision_hist(_p64(c), c.size, int(n), int(S), int(B), int(H), _p64(hist))
+        return hist
+
     def generate_many(self, params, per_inst, threads=1, want_c=True, want_r=True):
         """Eq. 9 for many independent instances on `threads` threads.
 
@@ -287,3 +299,7 @@ def runs_hist(c, n, lmax, hist=None):
 
 def pattern_hist(n, e, p, a, c_lo, L0, D, nb, hist=None):
     return _default().pattern_hist(n, e, p, a, c_lo, L0, D, nb, hist)
+
+
+def collision_hist(c, n, S, B, H, hist=None):
+    return _default().collision_hist(c, n, S, B, H, hist)

@@ -394,6 +394,37 @@ void or_pattern_hist(uint64_t n, uint64_t e, uint64_t p, uint64_t a, uint64_t c_
     }
 }
 
+/* Collision test (Tests section: 2^14 numbers into 2^20 bins).  One stream's
+ * numbers in consecutive non-overlapping segments of S (a remainder of fewer
+ * than S is left out); number k falls in bin floor(B R_k); a number is a
+ * collision when its bin already holds an earlier number of the segment;
+ * the segment's collision count C adds one to hist[min(C, H-1)] (hist has H
+ * entries and is added to).
+ * Pinned by: segments built from chosen bins; the mean collision count of a
+ * long stream against its exact expectation S - B (1 - (1 - 1/B)^S). */
+void or_collision_hist(const uint64_t *c, uint64_t N, uint64_t n, uint64_t S, uint64_t B,
+                       uint64_t H, uint64_t *hist)
+{
+    unsigned char *seen = (unsigned char *)calloc(B, 1);
+    if (!seen) return;
+    for (uint64_t g = 0; g + S <= N; g += S) {
+        uint64_t C = 0;
+        for (uint64_t k = g; k < g + S; ++k) {
+            uint64_t b = (uint64_t)(or_real(c[k], n) * (double)B);
+            if (b >= B) b = B - 1;
+            if (seen[b]) ++C;
+            seen[b] = 1;
+        }
+        hist[C < H ? C : H - 1] += 1;
+        for (uint64_t k = g; k < g + S; ++k) {
+            uint64_t b = (uint64_t)(or_real(c[k], n) * (double)B);
+            if (b >= B) b = B - 1;
+            seen[b] = 0;
+        }
+    }
+    free(seen);
+}
+
 /* ---- threaded harness: many independent instances (parameter splitting,
  * Introduction: each process owns its own prime modulus) ------------------ */
 typedef struct {

@@ -54,6 +54,8 @@ MUTANTS = {
     "runs_length_reset": ("        len = 1;\n    }", "        len = 0;\n    }"),
     "pattern_skip_modulus": ("                t = or_mulmod(a, t, p);", "                t = or_mulmod(a, t, n);"),
     "pattern_encrypts_not_decrypts": ("uint64_t m = or_powmod(c0, d, n);", "uint64_t m = or_powmod(c0, e, n);"),
+    "collision_counts_distinct": ("            if (seen[b]) ++C;", "            if (!seen[b]) ++C;"),
+    "collision_no_reset": ("            seen[b] = 0;\n", "            seen[b] = 1;\n"),
     "dlog_index": ("L_out[q] = (i * M + val[h]) % order;", "L_out[q] = (i * M + val[h] + 1) % order;"),
 }
 

@@ -494,3 +494,30 @@ def test_pattern_2d_whole_range_is_uniform(oracle_mod):
     want = np.array([(p - 1) * len(range(b * L1, min((b + 1) * L1, n))) for b in range(nb)],
                     dtype=np.uint64)
     assert np.array_equal(got, want)
+
+
+# ------------------------------------------------------------ collision test
+def test_collisions_from_chosen_bins(oracle_mod):
+    """n + 1 = 16 t makes floor(16 (c+1)/(n+1)) = b for c = b t: segments of
+    eight numbers into 16 bins with known collision counts."""
+    t = 268435453
+    n = 16 * t - 1
+    segs = [[0, 1, 2, 3, 4, 5, 6, 7],                   # 0 collisions
+            [3, 3, 3, 9, 9, 1, 2, 15],                  # 3
+            [5, 5, 5, 5, 5, 5, 5, 5]]                   # 7
+    cs = np.array([b * t for seg in segs for b in seg] + [1, 2, 3], dtype=np.uint64)   # remainder
+    h = oracle_mod.collision_hist(cs, n, 8, 16, 6)
+    assert list(h) == [1, 0, 0, 1, 0, 1]                # 7 collisions capped into the last counter
+
+
+def test_collision_mean_of_a_long_stream(oracle_mod):
+    """The paper's sizes (2^14 numbers into 2^20 bins): the mean collision count
+    over 120 segments within 5 standard errors of S - B (1 - (1 - 1/B)^S)."""
+    n = 4294967087
+    S, B, H = 1 << 14, 1 << 20, 512
+    c, _, _ = oracle_mod.generate(n, 9, P31, A31, 99, 12345, 120 * S + 17)
+    h = oracle_mod.collision_hist(c, n, S, B, H)
+    assert int(h.sum()) == 120
+    mean = float((h * np.arange(H)).sum()) / 120
+    expect = S - B * (1 - (1 - 1 / B) ** S)
+    assert abs(mean - expect) < 5 * np.sqrt(expect / 120), (mean, expect)
