@@ -207,6 +207,21 @@ int phprng_serial_test(phprng_ctx *ctx, uint64_t first, uint64_t num_inst, uint6
 int phprng_poker_test(phprng_ctx *ctx, uint64_t first, uint64_t num_inst, uint64_t per_inst,
                       uint64_t *hist, void *cuda_stream);
 
+/* Collision-test consumer (Tests section: 2^14 numbers into 2^20 bins) for
+ * 32-bit moduli.  Each stream's numbers of the call form consecutive
+ * segments of S numbers (a remainder of fewer than S is left out); in a
+ * segment, a number whose bin floor(B R) already holds an earlier number of
+ * the segment is a collision, and the segment's collision count C adds one to
+ * hist[min(C, H-1)].  Expected count per segment S - B (1 - (1 - 1/B)^S)
+ * (about 127.9 at the paper's S = 2^14, B = 2^20).  hist: device memory, H
+ * uint64 counters, added to.  Limits: S a multiple of 256 from 256 to 2^24;
+ * B a power of two up to 2^20 or any B up to 2^16; 1 <= H <= 2^16.  Takes a
+ * stream-ordered scratch of one B-bit bitmap per resident warp (311 MB at
+ * B = 2^20 on GB300) for the call.  Streams advance by per_inst.
+ * Asynchronous on cuda_stream. */
+int phprng_collision_test(phprng_ctx *ctx, uint64_t first, uint64_t num_inst, uint64_t per_inst,
+                          uint32_t S, uint32_t B, uint32_t H, uint64_t *hist, void *cuda_stream);
+
 /* Runs-test consumer (Tests section: runs of 0's, R <= 1/2, and 1's,
  * R > 1/2) for 32-bit moduli.  Each stream's numbers of the call, in order,
  * give bits b_k = (R_k > 1/2); every maximal run of equal bits that ends before

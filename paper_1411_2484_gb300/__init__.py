@@ -35,7 +35,8 @@ PHPRNG_ALLOW_SHARED_N = 0x2
 
 EXPORTED = [
     "phprng_create", "phprng_create_seeded", "phprng_destroy", "phprng_last_error",
-    "phprng_status_string", "phprng_generate", "phprng_skip", "phprng_seek", "phprng_serial_test", "phprng_poker_test", "phprng_runs_test", "phprng_pattern",
+    "phprng_status_string", "phprng_generate", "phprng_skip", "phprng_seek", "phprng_serial_test", "phprng_poker_test", "phprng_runs_test", "phprng_collision_test",
+    "phprng_pattern",
     "phprng_get_state",
     "phprng_is_prime", "phprng_validate", "phprng_draw_instances", "phprng_microbench",
     "phprng_plan_create", "phprng_plan_launch", "phprng_plan_launch_graph",
@@ -137,6 +138,8 @@ def _load():
         lib.phprng_serial_test.argtypes = [vp, u64, u64, u64, i32, ctypes.c_uint32, vp, vp]
         lib.phprng_poker_test.argtypes = [vp, u64, u64, u64, vp, vp]
         lib.phprng_runs_test.argtypes = [vp, u64, u64, u64, i32, vp, vp]
+        u32 = ctypes.c_uint32
+        lib.phprng_collision_test.argtypes = [vp, u64, u64, u64, u32, u32, u32, vp, vp]
         lib.phprng_pattern.argtypes = [ctypes.POINTER(phprng_instance), u64, u64, i32,
                                        ctypes.c_uint32, vp, vp]
         lib.phprng_get_state.argtypes = [vp, u64, P_inst, P64, P64, vp]
@@ -275,6 +278,13 @@ def phprng_poker_test(ctx, first, num_inst, per_inst, hist, stream=None):
     counters `hist` (7 uint64) and advances the streams by per_inst."""
     _check(_load().phprng_poker_test(ctx, int(first), int(num_inst), int(per_inst), _ptr(hist),
                                      _stream(stream)), ctx)
+
+
+def phprng_collision_test(ctx, first, num_inst, per_inst, S, B, H, hist, stream=None):
+    """Adds the call's per-segment collision counts (segments of S numbers into
+    B bins, counts capped at H-1) to the device counters `hist` (H uint64)."""
+    _check(_load().phprng_collision_test(ctx, int(first), int(num_inst), int(per_inst), int(S), int(B),
+                                         int(H), _ptr(hist), _stream(stream)), ctx)
 
 
 def phprng_runs_test(ctx, first, num_inst, per_inst, lmax, hist, stream=None):

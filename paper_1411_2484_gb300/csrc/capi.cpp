@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <functional>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -684,7 +685,9 @@ PH_API int phprng_skip(phprng_ctx *ctx, const uint64_t *inst_ids, const uint64_t
 // launch, the positions.  D = 0 selects the poker test, D = -1 the runs test
 // (B = lmax).
 static int run_hist_test(phprng_ctx *ctx, const char *what, uint64_t first, uint64_t num_inst,
-                         uint64_t per_inst, int D, uint32_t B, uint64_t *hist, void *cuda_stream)
+                         uint64_t per_inst, int D, uint32_t B, uint64_t *hist, void *cuda_stream,
+                         const std::function<int(const GenArgs &, cudaStream_t, std::string *)> &launch =
+                             nullptr)
 {
     const std::string w(what);
     if (ctx->serving) return fail(ctx, PHPRNG_EINVAL, w + ": a server owns the context");
@@ -718,8 +721,9 @@ static int run_hist_test(phprng_ctx *ctx, const char *what, uint64_t first, uint
         if (rc != PHPRNG_OK) return rc;
     }
     std::string err;
-    int rc = D < 0 ? launch_runs(g, (int)B, (unsigned long long *)hist, s, &err)
-                   : launch_serial(g, D, B, (unsigned long long *)hist, s, &err);
+    int rc = launch ? launch(g, s, &err)
+             : D < 0 ? launch_runs(g, (int)B, (unsigned long long *)hist, s, &err)
+                     : launch_serial(g, D, B, (unsigned long long *)hist, s, &err);
     if (rc != PHPRNG_OK) return fail(ctx, rc, w + ": " + err);
     for (uint64_t i = first; i < first + num_inst; ++i) ctx->pos_host[i] += per_inst;
     return PHPRNG_OK;
@@ -747,6 +751,39 @@ PH_API int phprng_poker_test(phprng_ctx *ctx, uint64_t first, uint64_t num_inst,
     if (!ctx) return fail(nullptr, PHPRNG_EINVAL, "phprng_poker_test: ctx is NULL");
     std::lock_guard<std::mutex> lk(ctx->mu);
     return run_hist_test(ctx, "phprng_poker_test", first, num_inst, per_inst, 0, 10, hist, cuda_stream);
+}
+
+PH_API int phprng_collision_test(phprng_ctx *ctx, uint64_t first, uint64_t num_inst, uint64_t per_inst,
+                                 uint32_t S, uint32_t B, uint32_t H, uint64_t *hist, void *cuda_stream)
+{
+    if (!ctx) return fail(nullptr, PHPRNG_EINVAL, "phprng_collision_test: ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (S < 256 || S % 256 || S > (1u << 24))
+        return fail(ctx, PHPRNG_EINVAL,
+                    "phprng_collision_test: S must be a multiple of 256 from 256 to 2^24");
+    const bool pow2 = B && (B & (B - 1)) == 0;
+    if (B < 1 || (pow2 ? B > (1u << 20) : B > (1u << 16)))
+        return fail(ctx, PHPRNG_EINVAL,
+                    "phprng_collision_test: B must be a power of two up to 2^20 or at most 2^16");
+    if (H < 1 || H > (1u << 16)) return fail(ctx, PHPRNG_EINVAL, "phprng_collision_test: H must be 1..2^16");
+    auto launch = [&](const GenArgs &g, cudaStream_t s, std::string *err) -> int {
+        const int warps = collision_grid_warps();
+        const size_t bytes = (size_t)warps * ((B + 31) / 32) * sizeof(uint32_t);
+        uint32_t *bm = nullptr;
+        cudaError_t e = cudaMallocAsync((void **)&bm, bytes, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(bm, 0, bytes, s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            if (bm) cudaFreeAsync(bm, s);
+            *err = std::string("collision bitmaps: ") + cudaGetErrorString(e);
+            return e == cudaErrorMemoryAllocation ? PHPRNG_ENOMEM : PHPRNG_ECUDA;
+        }
+        int rc = launch_collision(g, S, B, H, (unsigned long long *)hist, bm, warps, s, err);
+        cudaFreeAsync(bm, s);
+        return rc;
+    };
+    return run_hist_test(ctx, "phprng_collision_test", first, num_inst, per_inst, 1, 1, hist, cuda_stream,
+                         launch);
 }
 
 PH_API int phprng_runs_test(phprng_ctx *ctx, uint64_t first, uint64_t num_inst, uint64_t per_inst,

@@ -160,6 +160,12 @@ int launch_serial(const GenArgs &a, int D, uint32_t B, unsigned long long *hist,
 // Runs-test consumer (serial.cu): completed runs of R <= 1/2 and R > 1/2 by
 // length (capped at lmax <= 64) added to hist[2 lmax]; sk for NPT 8.
 int launch_runs(const GenArgs &a, int lmax, unsigned long long *hist, void *stream, std::string *err);
+// Collision-test consumer (serial.cu): segments of S numbers into B bins,
+// collision counts into hist[H]; a persistent grid of `warps` warps (from
+// collision_grid_warps()), each with a zeroed bitmap of ceil(B/32) words.
+int collision_grid_warps();
+int launch_collision(const GenArgs &a, uint32_t S, uint32_t B, uint32_t H, unsigned long long *hist,
+                     uint32_t *bitmaps, int warps, void *stream, std::string *err);
 // Full-period pattern by enumeration (pattern.cu): mtab[q] = (c_lo+q)^d mod n
 // for q < L0, sk for NPT 8; hist has nb^(D-1) uint64 counters.
 int launch_pattern(const DevInst &P, const ExpProg &pg, const SkipConst &sk, const uint32_t *mtab,

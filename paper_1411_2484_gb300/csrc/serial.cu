@@ -205,6 +205,91 @@ runs_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, 
                                                x);
 }
 
+// Collision test (Tests section): each stream's numbers of the call in
+// consecutive segments of S (a multiple of the 256-number warp group, so every
+// group lies in one segment); every number sets its bin floor(B R) in the
+// warp's own bitmap of B bits with an atomic OR, and is a collision when the
+// bit was already set.  The count of a segment is S minus its distinct bins,
+// whatever the order of the ORs.  At the end of a segment the warp adds one
+// to hist[min(C, H-1)] and clears its bitmap.  The grid is persistent (one
+// bitmap per resident warp, warps walk instances with a stride).
+template <int NPT>
+__global__ void __launch_bounds__(256, 2)
+collision_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, DevState st,
+                 SkipConst sk, uint64_t first, uint64_t num, uint64_t per_inst, uint32_t S, uint32_t B,
+                 uint32_t H, unsigned long long *__restrict__ hist, uint32_t *__restrict__ bitmaps,
+                 const uint32_t *__restrict__ order)
+{
+    constexpr uint64_t G = 32 * NPT;
+    const int lane = threadIdx.x & 31;
+    const uint64_t gw = (uint64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    const uint64_t nwarps = (uint64_t)gridDim.x * 8;
+    const uint32_t words = (B + 31) / 32;
+    uint32_t *bm = bitmaps + gw * words;
+    const uint64_t counted = per_inst / S * S;            // numbers in complete segments
+    for (uint64_t w = gw; w < num; w += nwarps) {
+        const uint64_t j = order ? order[w] : w;
+        const uint64_t i = first + j;
+        const DevInst P = inst[i];
+        const ExpProg &pg = prog[i];
+        const uint32_t r = (uint32_t)(((uint64_t)B << 32) / P.yN);
+        uint32_t M = (uint32_t)st.m[i];
+        uint32_t sig = mont32((uint32_t)st.s[i], sk.lane[lane], sk.p, sk.pinv);
+        const uint64_t pos_after = st.pos[i] + per_inst;
+        uint32_t x[NPT], sig_last = sig, C = 0;
+        uint64_t g_last = 0;
+        for (uint64_t g0 = 0; g0 < per_inst; g0 += G) {
+            uint32_t sv[NPT], msg[NPT];
+            const uint64_t my0 = g0 + (uint64_t)NPT * lane;
+            sig_last = sig;
+            g_last = g0;
+            messages32<NPT>(P, sk, lane, my0, per_inst, M, sig, sv, msg);
+            encrypt32<NPT>(P, pg, msg, x);
+            if (g0 >= counted) continue;                  // the incomplete last segment
+#pragma unroll
+            for (int u = 0; u < NPT; ++u) {
+                const uint32_t b = serial_bin(x[u], P.yN, P.ybits, r, B);
+                const uint32_t bit = 1u << (b & 31);
+                if (atomicOr(bm + (b >> 5), bit) & bit) ++C;
+            }
+            if ((g0 + G) % S == 0) {                      // the segment is complete
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) C += __shfl_xor_sync(kFullMask, C, off);
+                if (lane == 0) atomicAdd(hist + (C < H ? C : H - 1), 1ull);
+                C = 0;
+                __syncwarp();
+                for (uint32_t k = lane; k < words; k += 32) bm[k] = 0u;
+                __syncwarp();
+            }
+        }
+        write_state_after<NPT, uint32_t, uint32_t>(st, sk, i, lane, g_last, per_inst, pos_after, M,
+                                                   sig_last, x);
+    }
+}
+
+int collision_grid_warps()
+{
+    int dev = 0, sms = 0, b = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, collision_kernel<8>, 256, 0);
+    return (sms > 0 ? sms : 1) * (b > 0 ? b : 1) * 8;
+}
+
+int launch_collision(const GenArgs &a, uint32_t S, uint32_t B, uint32_t H, unsigned long long *hist,
+                     uint32_t *bitmaps, int warps, void *stream, std::string *err)
+{
+    if (a.num == 0 || a.per_inst == 0) return PHPRNG_OK;
+    collision_kernel<8><<<(unsigned)(warps / 8), 256, 0, (cudaStream_t)stream>>>(
+        a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, S, B, H, hist, bitmaps, a.order);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        *err = std::string("collision_kernel launch: ") + cudaGetErrorString(e);
+        return PHPRNG_ECUDA;
+    }
+    return PHPRNG_OK;
+}
+
 int launch_runs(const GenArgs &a, int lmax, unsigned long long *hist, void *stream, std::string *err)
 {
     if (a.num == 0 || a.per_inst == 0) return PHPRNG_OK;

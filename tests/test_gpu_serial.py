@@ -178,3 +178,48 @@ def test_runs_small_modulus_long_runs(ph, torch):
         assert np.array_equal(hist.cpu().numpy().view(np.uint64), want)
     finally:
         ph.phprng_destroy(ctx)
+
+
+@pytest.mark.parametrize("S,B,H", [(1 << 14, 1 << 20, 512), (256, 64, 300), (512, 1000, 64)])
+def test_collisions_match_oracle(ph, torch, S, B, H):
+    """Segments over two calls (a remainder of each call left out), counts equal
+    to the oracle's; the streams continue."""
+    inst = workloads.draw_instances(23, seed=120 + H)
+    ctx = ph.phprng_create(32, inst, 0)
+    try:
+        rows = workloads.instance_rows(inst).copy()
+        hist = torch.zeros(H, dtype=torch.int64, device="cuda")
+        want = np.zeros(H, dtype=np.uint64)
+        total = 0
+        for per in (3 * S + 1000, 2 * S):
+            ph.phprng_collision_test(ctx, 0, 23, per, S, B, H, hist)
+            c, _, st, _ = oracle.generate_many(rows, per, threads=THREADS, want_r=False)
+            for k in range(23):
+                oracle.collision_hist(c[k], int(rows[k, 0]), S, B, H, want)
+            rows[:, 4:6] = st
+            total += per
+        torch.cuda.synchronize()
+        assert np.array_equal(hist.cpu().numpy().view(np.uint64), want)
+        s = ph.phprng_get_state(ctx, 22)
+        assert (s["m"], s["s"], s["pos"]) == (int(rows[22, 4]), int(rows[22, 5]), total)
+    finally:
+        ph.phprng_destroy(ctx)
+
+
+def test_collision_mean_at_scale(ph, torch):
+    """4,096 streams x 2^16 numbers at the paper's sizes: the mean collision
+    count of 16,384 segments within 5 standard errors of its expectation."""
+    inst = workloads.draw_instances(4096, seed=125)
+    ctx = ph.phprng_create(32, inst, ph.PHPRNG_REQUIRE_SAFE_PRIME)
+    try:
+        S, B, H = 1 << 14, 1 << 20, 512
+        hist = torch.zeros(H, dtype=torch.int64, device="cuda")
+        ph.phprng_collision_test(ctx, 0, 4096, 1 << 16, S, B, H, hist)
+        h = hist.cpu().numpy().astype(np.float64)
+        segs = 4096 * 4
+        assert h.sum() == segs
+        mean = float((h * np.arange(H)).sum()) / segs
+        expect = S - B * (1 - (1 - 1 / B) ** S)
+        assert abs(mean - expect) < 5 * np.sqrt(expect / segs), (mean, expect)
+    finally:
+        ph.phprng_destroy(ctx)
