@@ -89,6 +89,8 @@ class Oracle:
         lib.or_runs_hist.argtypes = [P64, u64, u64, ctypes.c_int, P64]
         lib.or_pattern_hist.restype = None
         lib.or_pattern_hist.argtypes = [u64, u64, u64, u64, u64, u64, ctypes.c_int, u64, P64]
+        lib.or_pattern_const_hist.restype = None
+        lib.or_pattern_const_hist.argtypes = [u64, u64, u64, u64, u64, ctypes.c_int, u64, P64]
         lib.or_collision_hist.restype = None
         lib.or_collision_hist.argtypes = [P64, u64, u64, u64, u64, u64, P64]
         lib.or_generate_many.restype = u64
@@ -191,6 +193,16 @@ class Oracle:
         assert hist.dtype == np.uint64 and hist.size == nb ** (D - 1) and hist.flags.c_contiguous
         self.lib.or_pattern_hist(int(n), int(e), int(p), int(a), int(c_lo), int(L0), int(D), int(nb),
                                  _p64(hist))
+        return hist
+
+    def pattern_const_hist(self, n, e, b, c_lo, L0, D, nb, hist=None):
+        """Full-period pattern of the constant-skip generator (skip b; b = 1 is
+        the unit skip), added to hist (uint64[nb**(D-1)])."""
+        if hist is None:
+            hist = np.zeros(nb ** (D - 1), dtype=np.uint64)
+        assert hist.dtype == np.uint64 and hist.size == nb ** (D - 1) and hist.flags.c_contiguous
+        self.lib.or_pattern_const_hist(int(n), int(e), int(b), int(c_lo), int(L0), int(D), int(nb),
+                                       _p64(hist))
         return hist
 
     def collision_hist(self, c, n, S, B, H, hist=None):
@@ -303,3 +315,7 @@ def pattern_hist(n, e, p, a, c_lo, L0, D, nb, hist=None):
 
 def collision_hist(c, n, S, B, H, hist=None):
     return _default().collision_hist(c, n, S, B, H, hist)
+
+
+def pattern_const_hist(n, e, b, c_lo, L0, D, nb, hist=None):
+    return _default().pattern_const_hist(n, e, b, c_lo, L0, D, nb, hist)

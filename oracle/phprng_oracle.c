@@ -394,6 +394,36 @@ void or_pattern_hist(uint64_t n, uint64_t e, uint64_t p, uint64_t a, uint64_t c_
     }
 }
 
+/* Full-period pattern of the constant-skip generator ("Message skipping
+ * algorithms": s_k = b, so m_k = m_0 + k b mod n, period n; b = 1 is the unit
+ * skip, a block cipher in counter mode): every c0 occurs once per period, with
+ * message m = c0^d mod n, and the tuple that starts at c0 continues with
+ * c_(k+j) = (m + j b)^e mod n.  For every c0 in [c_lo, c_lo + L0) the point
+ * (c_(k+1), ..., c_(k+D-1)) adds one to hist[b_1 + nb b_2 + ...] with
+ * b_j = floor(c_(k+j) / L1), L1 = ceil(n / nb) (hist added to).
+ * Pinned by: brute-force counts over a whole period of m_k = m_0 + k b. */
+void or_pattern_const_hist(uint64_t n, uint64_t e, uint64_t b, uint64_t c_lo, uint64_t L0, int D,
+                           uint64_t nb, uint64_t *hist)
+{
+    int64_t r0 = (int64_t)(n - 1), r1 = (int64_t)(e % (n - 1)), t0 = 0, t1 = 1;
+    while (r1) {
+        int64_t q = r0 / r1, tmp;
+        tmp = r0 - q * r1; r0 = r1; r1 = tmp;
+        tmp = t0 - q * t1; t0 = t1; t1 = tmp;
+    }
+    uint64_t d = (uint64_t)(t0 < 0 ? t0 + (int64_t)(n - 1) : t0);
+    uint64_t L1 = (n + nb - 1) / nb;
+    for (uint64_t c0 = c_lo; c0 < c_lo + L0; ++c0) {
+        uint64_t m = or_powmod(c0, d, n), idx = 0, scale = 1;
+        for (int j = 1; j < D; ++j) {
+            uint64_t mj = (uint64_t)(((u128)m + (u128)j * (b % n)) % n);
+            idx += (or_powmod(mj, e, n) / L1) * scale;
+            scale *= nb;
+        }
+        hist[idx] += 1;
+    }
+}
+
 /* Collision test (Tests section: 2^14 numbers into 2^20 bins).  One stream's
  * numbers in consecutive non-overlapping segments of S (a remainder of fewer
  * than S is left out); number k falls in bin floor(B R_k); a number is a

@@ -56,6 +56,8 @@ MUTANTS = {
     "pattern_encrypts_not_decrypts": ("uint64_t m = or_powmod(c0, d, n);", "uint64_t m = or_powmod(c0, e, n);"),
     "collision_counts_distinct": ("            if (seen[b]) ++C;", "            if (!seen[b]) ++C;"),
     "collision_no_reset": ("            seen[b] = 0;\n", "            seen[b] = 1;\n"),
+    "pattern_const_offset": ("uint64_t mj = (uint64_t)(((u128)m + (u128)j * (b % n)) % n);",
+                             "uint64_t mj = (uint64_t)(((u128)m + (u128)(j + 1) * (b % n)) % n);"),
     "dlog_index": ("L_out[q] = (i * M + val[h]) % order;", "L_out[q] = (i * M + val[h] + 1) % order;"),
 }
 

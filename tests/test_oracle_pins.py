@@ -521,3 +521,23 @@ def test_collision_mean_of_a_long_stream(oracle_mod):
     mean = float((h * np.arange(H)).sum()) / 120
     expect = S - B * (1 - (1 - 1 / B) ** S)
     assert abs(mean - expect) < 5 * np.sqrt(expect / 120), (mean, expect)
+
+
+@pytest.mark.parametrize("n,e", [(23, 3), (1019, 3), (4099, 5)])
+@pytest.mark.parametrize("b", [1, 7])
+@pytest.mark.parametrize("D,nb,c_lo,L0", [(2, 8, 0, None), (3, 5, 3, 11), (4, 3, 0, 200)])
+def test_pattern_const_equals_full_period_brute_force(oracle_mod, n, e, b, D, nb, c_lo, L0):
+    """The constant-skip (b = 1: unit skip) pattern equals counting the D-tuples
+    of a whole period m_k = m_0 + k b, c_k = m_k^e mod n."""
+    L0 = min(n - c_lo if L0 is None else L0, n - c_lo)
+    c = [pow((5 + k * b) % n, e, n) for k in range(n)]
+    L1 = -(-n // nb)
+    want = np.zeros(nb ** (D - 1), dtype=np.uint64)
+    for k in range(n):
+        if c_lo <= c[k] < c_lo + L0:
+            idx = 0
+            for j in range(1, D):
+                idx += (c[(k + j) % n] // L1) * nb ** (j - 1)
+            want[idx] += 1
+    got = oracle_mod.pattern_const_hist(n, e, b, c_lo, L0, D, nb)
+    assert np.array_equal(got, want)
