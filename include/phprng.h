@@ -253,6 +253,20 @@ int phprng_runs_test(phprng_ctx *ctx, uint64_t first, uint64_t num_inst, uint64_
 int phprng_pattern(const phprng_instance *inst, uint64_t c_lo, uint64_t L0, int D, uint32_t nb,
                    uint64_t *hist, void *cuda_stream);
 
+/* Full-period D-dimensional pattern of the constant-skip generator of one
+ * instance ("Message skipping algorithms": s_k = b, m_k = m_0 + k b mod n,
+ * period n; b = 1 is the unit skip, encryption of a counter).  Each c0 occurs
+ * once per period, with message m = c0^d mod n (d = e^-1 mod n-1, Eq. 2), and
+ * the tuple that starts there continues with c_(k+j) = (m + j b)^e mod n: for
+ * every c0 in [c_lo, c_lo + L0) the point adds one to hist[b_1 + nb b_2 + ...
+ * + nb^(D-2) b_(D-1)], b_j = floor(c_(k+j) / L1), L1 = ceil(n / nb).  Uses n and
+ * e of inst (validated as for phprng_create, width 32).  Limits: 1 <= b < n,
+ * 1 <= L0, c_lo + L0 <= n (L0 = n, c_lo = 0 is the whole period), 2 <= D <= 8,
+ * nb^(D-1) <= 2^24.  hist: device memory, nb^(D-1) uint64 counters, added to.
+ * Asynchronous on cuda_stream; errors through phprng_last_error(NULL). */
+int phprng_pattern_const(const phprng_instance *inst, uint64_t b, uint64_t c_lo, uint64_t L0, int D,
+                         uint32_t nb, uint64_t *hist, void *cuda_stream);
+
 /* Moves instance inst_ids[i] to absolute stream position pos[i], forward or
  * backward: afterwards its next number is number pos[i]+1 of the stream
  * counted from its seed, and its state (m, s, c) is the one generation would

@@ -36,7 +36,7 @@ PHPRNG_ALLOW_SHARED_N = 0x2
 EXPORTED = [
     "phprng_create", "phprng_create_seeded", "phprng_destroy", "phprng_last_error",
     "phprng_status_string", "phprng_generate", "phprng_skip", "phprng_seek", "phprng_serial_test", "phprng_poker_test", "phprng_runs_test", "phprng_collision_test",
-    "phprng_pattern",
+    "phprng_pattern", "phprng_pattern_const",
     "phprng_get_state",
     "phprng_is_prime", "phprng_validate", "phprng_draw_instances", "phprng_microbench",
     "phprng_plan_create", "phprng_plan_launch", "phprng_plan_launch_graph",
@@ -142,6 +142,8 @@ def _load():
         lib.phprng_collision_test.argtypes = [vp, u64, u64, u64, u32, u32, u32, vp, vp]
         lib.phprng_pattern.argtypes = [ctypes.POINTER(phprng_instance), u64, u64, i32,
                                        ctypes.c_uint32, vp, vp]
+        lib.phprng_pattern_const.argtypes = [ctypes.POINTER(phprng_instance), u64, u64, u64, i32,
+                                             ctypes.c_uint32, vp, vp]
         lib.phprng_get_state.argtypes = [vp, u64, P_inst, P64, P64, vp]
         lib.phprng_is_prime.argtypes = [u64]
         lib.phprng_validate.argtypes = [i32, P_inst, u64, u32, P64]
@@ -301,6 +303,15 @@ def phprng_pattern(n, e, p, a, c_lo, L0, D, nb, hist, stream=None):
     inst = phprng_instance(int(n), int(e), int(p), int(a), 0, 1)
     _check(_load().phprng_pattern(ctypes.byref(inst), int(c_lo), int(L0), int(D), int(nb), _ptr(hist),
                                   _stream(stream)), None)
+
+
+def phprng_pattern_const(n, e, b, c_lo, L0, D, nb, hist, stream=None):
+    """Full-period D-dimensional pattern of the constant-skip generator
+    (skip b; b = 1 is the unit skip) of (n, e) for the tuples starting at c0 in
+    [c_lo, c_lo+L0), added to the device counters `hist` (nb**(D-1) uint64)."""
+    inst = phprng_instance(int(n), int(e), 2, 1, 0, 1)
+    _check(_load().phprng_pattern_const(ctypes.byref(inst), int(b), int(c_lo), int(L0), int(D), int(nb),
+                                        _ptr(hist), _stream(stream)), None)
 
 
 def phprng_seek(ctx, inst_ids, pos, stream=None):

@@ -866,6 +866,42 @@ PH_API int phprng_pattern(const phprng_instance *inst, uint64_t c_lo, uint64_t L
     return PHPRNG_OK;
 }
 
+PH_API int phprng_pattern_const(const phprng_instance *inst, uint64_t b, uint64_t c_lo, uint64_t L0,
+                                int D, uint32_t nb, uint64_t *hist, void *cuda_stream)
+{
+    if (!inst) return fail(nullptr, PHPRNG_EINVAL, "phprng_pattern_const: inst is NULL");
+    phprng_instance in = *inst;
+    in.p = 3;                                                // only n and e play a part:
+    in.a = 2;                                                // a valid stand-in skip generator
+    in.m0 = 0;
+    in.s0 = 1;
+    std::string msg;
+    int rc = validate_one(32, in, 0, &msg);
+    if (rc != PHPRNG_OK) return fail(nullptr, rc, "phprng_pattern_const: " + msg);
+    const uint64_t n = in.n;
+    if (b < 1 || b >= n) return fail(nullptr, PHPRNG_EINVAL, "phprng_pattern_const: need 1 <= b < n");
+    if (L0 < 1 || c_lo >= n || L0 > n - c_lo)
+        return fail(nullptr, PHPRNG_EINVAL, "phprng_pattern_const: need L0 >= 1 and c_lo + L0 <= n");
+    if (D < 2 || D > 8) return fail(nullptr, PHPRNG_EINVAL, "phprng_pattern_const: D must be 2..8");
+    uint64_t bins = 1;
+    for (int d = 1; d < D && bins <= (1ull << 24); ++d) bins *= nb;
+    if (nb < 1 || bins > (1ull << 24))
+        return fail(nullptr, PHPRNG_EINVAL, "phprng_pattern_const: nb^(D-1) must be 1 .. 2^24");
+    if (!hist || (uintptr_t)hist % 8)
+        return fail(nullptr, PHPRNG_EINVAL, "phprng_pattern_const: hist NULL or not 8-byte aligned");
+    if (pointer_kind(hist) != 1)
+        return fail(nullptr, PHPRNG_EINVAL, "phprng_pattern_const: hist must be device memory");
+    ExpProg pg, pgd;
+    const DevInst P = derive_inst(in, 0, &pg);
+    phprng_instance dec = in;
+    dec.e = inverse_mod(in.e, n - 1);                        // Eq. 2
+    const DevInst Pd = derive_inst(dec, 0, &pgd);
+    std::string err;
+    rc = launch_pattern_const(P, pg, Pd, pgd, (uint32_t)b, c_lo, L0, D, nb, hist, cuda_stream, &err);
+    if (rc != PHPRNG_OK) return fail(nullptr, rc, "phprng_pattern_const: " + err);
+    return PHPRNG_OK;
+}
+
 PH_API int phprng_seek(phprng_ctx *ctx, const uint64_t *inst_ids, const uint64_t *pos,
                        uint64_t cnt, void *cuda_stream)
 {

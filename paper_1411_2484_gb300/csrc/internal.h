@@ -160,6 +160,11 @@ int launch_serial(const GenArgs &a, int D, uint32_t B, unsigned long long *hist,
 // Runs-test consumer (serial.cu): completed runs of R <= 1/2 and R > 1/2 by
 // length (capped at lmax <= 64) added to hist[2 lmax]; sk for NPT 8.
 int launch_runs(const GenArgs &a, int lmax, unsigned long long *hist, void *stream, std::string *err);
+// Full-period pattern of the constant-skip generator (pattern.cu): P, pg for
+// e and Pd, pgd for d = e^-1 mod n-1; one point per c0 in [c_lo, c_lo+L0).
+int launch_pattern_const(const DevInst &P, const ExpProg &pg, const DevInst &Pd, const ExpProg &pgd,
+                         uint32_t b, uint64_t c_lo, uint64_t L0, int D, uint32_t nb, uint64_t *hist,
+                         void *stream, std::string *err);
 // Collision-test consumer (serial.cu): segments of S numbers into B bins,
 // collision counts into hist[H]; a persistent grid of `warps` warps (from
 // collision_grid_warps()), each with a zeroed bitmap of ceil(B/32) words.

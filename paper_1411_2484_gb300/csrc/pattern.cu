@@ -27,15 +27,26 @@ __device__ __forceinline__ uint32_t div_by_width(uint32_t x, uint32_t L1, uint32
     return q;
 }
 
+// SMEM: histograms of at most kSmemBins counters are gathered per block in
+// shared memory and added to the device counters once (few, hot counters
+// would otherwise serialise the device-wide reductions).
+static constexpr uint32_t kSmemBins = 8192;
+
 // The counts go to 32-bit counters (nb^(D-1) <= 2^24: at most 64 MiB, which
 // L2 holds, where 64-bit counters spilled their reductions to DRAM); the
 // host runs chunks of c0 with fewer than 2^32 points each and folds the
 // 32-bit counters into the caller's 64-bit ones after every chunk.
-template <int NPT>
+template <int NPT, bool SMEM>
 __global__ void __launch_bounds__(256, 2)
 pattern_kernel(DevInst P, ExpProg pg, SkipConst sk, const uint32_t *__restrict__ mtab, uint64_t L0,
-               int D, uint32_t nb, uint32_t L1, uint32_t rL1, unsigned int *__restrict__ hist)
+               int D, uint32_t nb, uint32_t L1, uint32_t rL1, uint32_t bins,
+               unsigned int *__restrict__ hist)
 {
+    extern __shared__ unsigned int sh[];
+    if (SMEM) {
+        for (uint32_t k = threadIdx.x; k < bins; k += blockDim.x) sh[k] = 0;
+        __syncthreads();
+    }
     const uint32_t p = sk.p, n = (uint32_t)P.n;
     const uint64_t per_c0 = (p - 2 + NPT) / NPT;          // thread items per c0: skips 1 .. p-1
     const uint64_t items = L0 * per_c0;
@@ -68,7 +79,12 @@ pattern_kernel(DevInst P, ExpProg pg, SkipConst sk, const uint32_t *__restrict__
         }
 #pragma unroll
         for (int u = 0; u < NPT; ++u)
-            if (s0 + u < p) atomicAdd(hist + idx[u], 1u);
+            if (s0 + u < p) atomicAdd((SMEM ? sh : hist) + idx[u], 1u);
+    }
+    if (SMEM) {
+        __syncthreads();
+        for (uint32_t k = threadIdx.x; k < bins; k += blockDim.x)
+            if (sh[k]) atomicAdd(hist + k, sh[k]);
     }
 }
 
@@ -86,6 +102,98 @@ fold_counts_kernel(unsigned int *__restrict__ h32, unsigned long long *__restric
     }
 }
 
+// The constant-skip generator (s_k = b; b = 1 is the unit skip, counter mode)
+// has period n and meets each c0 once, with message m = c0^d mod n, so its
+// full-period pattern has one point per c0: c_(k+j) = (m + j b)^e mod n.  A
+// thread takes NPT consecutive c0, decrypts them with the program of d
+// (Pd, pgd) and encrypts the D-1 successors with the program of e.
+template <int NPT, bool SMEM>
+__global__ void __launch_bounds__(256, 2)
+pattern_const_kernel(DevInst P, ExpProg pg, DevInst Pd, ExpProg pgd, uint32_t b, uint64_t c_lo,
+                     uint64_t L0, int D, uint32_t nb, uint32_t L1, uint32_t rL1, uint32_t bins,
+                     unsigned long long *__restrict__ hist)
+{
+    extern __shared__ unsigned int sh[];
+    if (SMEM) {
+        for (uint32_t k = threadIdx.x; k < bins; k += blockDim.x) sh[k] = 0;
+        __syncthreads();
+    }
+    const uint32_t n = (uint32_t)P.n;
+    const uint64_t items = (L0 + NPT - 1) / NPT;
+    for (uint64_t it = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; it < items;
+         it += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t q0 = it * NPT;
+        uint32_t c0[NPT], m[NPT], acc[NPT], x[NPT], idx[NPT];
+#pragma unroll
+        for (int u = 0; u < NPT; ++u) {
+            c0[u] = (uint32_t)(c_lo + (q0 + u < L0 ? q0 + u : 0));   // past L0: computed, not counted
+            idx[u] = 0;
+        }
+        encrypt<NPT, uint32_t>(Pd, pgd, c0, m);                       // m = c0^d (Eq. 2)
+        uint32_t scale = 1;
+#pragma unroll
+        for (int u = 0; u < NPT; ++u) acc[u] = m[u];
+        for (int j = 1; j < D; ++j) {
+#pragma unroll
+            for (int u = 0; u < NPT; ++u) acc[u] = addmod32(acc[u], b, n);
+            encrypt<NPT, uint32_t>(P, pg, acc, x);                      // Eq. 9c
+#pragma unroll
+            for (int u = 0; u < NPT; ++u)
+                idx[u] += (L1 == 1 ? x[u] : div_by_width(x[u], L1, rL1)) * scale;
+            scale *= nb;
+        }
+#pragma unroll
+        for (int u = 0; u < NPT; ++u) {
+            if (q0 + u >= L0) continue;
+            if (SMEM)
+                atomicAdd(sh + idx[u], 1u);
+            else
+                atomicAdd(hist + idx[u], 1ull);
+        }
+    }
+    if (SMEM) {
+        __syncthreads();
+        for (uint32_t k = threadIdx.x; k < bins; k += blockDim.x)
+            if (sh[k]) atomicAdd(hist + k, (unsigned long long)sh[k]);
+    }
+}
+
+int launch_pattern_const(const DevInst &P, const ExpProg &pg, const DevInst &Pd, const ExpProg &pgd,
+                         uint32_t b, uint64_t c_lo, uint64_t L0, int D, uint32_t nb, uint64_t *hist,
+                         void *stream, std::string *err)
+{
+    constexpr int NPT = 8;
+    const uint32_t n = (uint32_t)P.n;
+    const uint32_t L1 = (uint32_t)((n + (uint64_t)nb - 1) / nb);
+    const uint32_t rL1 = L1 >= 2 ? (uint32_t)((1ull << 32) / L1) : 0u;
+    uint32_t bins = 1;
+    for (int d = 1; d < D; ++d) bins *= nb;
+    const bool smem = bins <= kSmemBins;
+    int dev = 0, sms = 0, bps = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &bps, smem ? pattern_const_kernel<NPT, true> : pattern_const_kernel<NPT, false>, 256,
+        smem ? kSmemBins * 4 : 0);
+    const uint64_t items = (L0 + NPT - 1) / NPT;
+    uint64_t grid = (items + 255) / 256;
+    const uint64_t cap = (uint64_t)(sms > 0 ? sms : 1) * (bps > 0 ? bps : 1) * 8;
+    if (grid > cap) grid = cap;
+    if (grid == 0) return PHPRNG_OK;
+    if (smem)
+        pattern_const_kernel<NPT, true><<<(unsigned)grid, 256, bins * 4, (cudaStream_t)stream>>>(
+            P, pg, Pd, pgd, b, c_lo, L0, D, nb, L1, rL1, bins, (unsigned long long *)hist);
+    else
+        pattern_const_kernel<NPT, false><<<(unsigned)grid, 256, 0, (cudaStream_t)stream>>>(
+            P, pg, Pd, pgd, b, c_lo, L0, D, nb, L1, rL1, bins, (unsigned long long *)hist);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        *err = std::string("pattern_const_kernel launch: ") + cudaGetErrorString(e);
+        return PHPRNG_ECUDA;
+    }
+    return PHPRNG_OK;
+}
+
 int launch_pattern(const DevInst &P, const ExpProg &pg, const SkipConst &sk, const uint32_t *mtab,
                    uint64_t L0, int D, uint32_t nb, uint64_t *hist, void *stream, std::string *err)
 {
@@ -99,7 +207,10 @@ int launch_pattern(const DevInst &P, const ExpProg &pg, const SkipConst &sk, con
     int dev = 0, sms = 0, bps = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, pattern_kernel<NPT>, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, pattern_kernel<NPT, false>, 256, 0);
+    const bool smem = bins <= kSmemBins;
+    if (smem)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, pattern_kernel<NPT, true>, 256, kSmemBins * 4);
     const uint64_t cap = (uint64_t)(sms > 0 ? sms : 1) * (bps > 0 ? bps : 1) * 8;
     unsigned int *h32 = nullptr;
     cudaError_t e = cudaMallocAsync((void **)&h32, bins * sizeof(unsigned int), s);
@@ -119,7 +230,12 @@ int launch_pattern(const DevInst &P, const ExpProg &pg, const SkipConst &sk, con
         const uint64_t items = lq * ((sk.p - 2 + NPT) / NPT);
         uint64_t grid = (items + 255) / 256;
         if (grid > cap) grid = cap;
-        pattern_kernel<NPT><<<(unsigned)grid, 256, 0, s>>>(P, pg, sk, mtab + q0, lq, D, nb, L1, rL1, h32);
+        if (smem)
+            pattern_kernel<NPT, true><<<(unsigned)grid, 256, bins * 4, s>>>(P, pg, sk, mtab + q0, lq, D, nb,
+                                                                           L1, rL1, (uint32_t)bins, h32);
+        else
+            pattern_kernel<NPT, false><<<(unsigned)grid, 256, 0, s>>>(P, pg, sk, mtab + q0, lq, D, nb, L1,
+                                                                     rL1, (uint32_t)bins, h32);
         fold_counts_kernel<<<(unsigned)fold_grid, 256, 0, s>>>(h32, (unsigned long long *)hist, bins);
         e = cudaGetLastError();
     }

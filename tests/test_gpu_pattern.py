@@ -61,3 +61,32 @@ def test_pattern_argument_errors(ph, torch):
             ph.phprng_pattern(*args, h)
     with pytest.raises(ph.PhprngError):
         ph.phprng_pattern(n, 3, p, a, 0, 8, 2, 8, np.zeros(8, dtype=np.uint64))   # host memory
+
+
+@pytest.mark.parametrize("n,e", [(1019, 3), (4099, 5), (4294967087, 9), (4294967087, 4294967085)])
+@pytest.mark.parametrize("b", [1, 12345])
+@pytest.mark.parametrize("D,nb", [(2, 8), (3, 16), (4, 4)])
+def test_pattern_const_matches_oracle(ph, torch, n, e, b, D, nb):
+    """The constant-skip (b = 1: unit skip) full-period pattern equals the
+    oracle's (itself pinned against brute force over whole periods)."""
+    b = b % n or 1
+    c_lo, L0 = (0, n) if n < 5000 else (77, 100000)
+    hist = torch.zeros(nb ** (D - 1), dtype=torch.int64, device="cuda")
+    ph.phprng_pattern_const(n, e, b, c_lo, L0, D, nb, hist)
+    torch.cuda.synchronize()
+    want = oracle.pattern_const_hist(n, e, b, c_lo, L0, D, nb)
+    assert np.array_equal(hist.cpu().numpy().view(np.uint64), want)
+
+
+def test_pattern_const_whole_period_unit_skip(ph, torch):
+    """The unit skip over a whole 32-bit period (the paper's Fig. 2 generator,
+    n = 4294967087, e = 9): n points, and with D = 2 every column of the
+    pattern holds exactly as many points as values of c1 fall in it."""
+    n, e = 4294967087, 9
+    nb = 256
+    hist = torch.zeros(nb, dtype=torch.int64, device="cuda")
+    ph.phprng_pattern_const(n, e, 1, 0, n, 2, nb, hist)
+    h = hist.cpu().numpy().view(np.uint64)
+    L1 = -(-n // nb)
+    want = np.array([min(L1, n - k * L1) for k in range(nb)], dtype=np.uint64)
+    assert np.array_equal(h, want)
