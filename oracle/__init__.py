@@ -317,5 +317,39 @@ def collision_hist(c, n, S, B, H, hist=None):
     return _default().collision_hist(c, n, S, B, H, hist)
 
 
+# ---- Fourier test (Tests section) -------------------------------------------
+# numpy's FFT serves as the library primitive of this step; everything else is
+# the paper's definition written out.
+
+def fourier_coefficients(R, M):
+    """Fourier test coefficients of one stream's numbers R (in order): for each
+    consecutive sequence of M numbers (a remainder left out), with x_j = R_j -
+    1/2, xhat_k = M^(-1/2) sum_j x_j exp(+2 pi i j k / M) for k = 0 .. M/2-1.
+    Returns complex128[sequences, M/2]."""
+    R = np.asarray(R, dtype=np.float64)
+    seqs = R.size // M
+    x = R[: seqs * M].reshape(seqs, M) - 0.5
+    # sum_j x_j exp(+2 pi i j k / M) = M * ifft(x)_k
+    X = np.fft.ifft(x, axis=1) * M
+    return X[:, : M // 2] / np.sqrt(M)
+
+
+def fourier_bin(v, nbins, w):
+    """Histogram bin of a real or imaginary part v: floor((v + w) / (2 w) nbins),
+    clamped to the first and last bins outside [-w, w)."""
+    b = np.floor((np.asarray(v, dtype=np.float64) + w) / (2 * w) * nbins)
+    return np.clip(b, 0, nbins - 1).astype(np.int64)
+
+
+def fourier_hist(coefs, nbins, w, hist=None):
+    """Adds the real and imaginary parts of every coefficient to hist."""
+    if hist is None:
+        hist = np.zeros(nbins, dtype=np.uint64)
+    c = np.asarray(coefs).reshape(-1)
+    for part in (c.real, c.imag):
+        hist += np.bincount(fourier_bin(part, nbins, w), minlength=nbins).astype(np.uint64)
+    return hist
+
+
 def pattern_const_hist(n, e, b, c_lo, L0, D, nb, hist=None):
     return _default().pattern_const_hist(n, e, b, c_lo, L0, D, nb, hist)

@@ -541,3 +541,42 @@ def test_pattern_const_equals_full_period_brute_force(oracle_mod, n, e, b, D, nb
             want[idx] += 1
     got = oracle_mod.pattern_const_hist(n, e, b, c_lo, L0, D, nb)
     assert np.array_equal(got, want)
+
+
+# ------------------------------------------------------------ Fourier test
+def test_fourier_pure_tone_and_parseval(oracle_mod):
+    """A pure tone x_j = cos(2 pi j k0 / M) has xhat_k0 = sqrt(M)/2 and no other
+    coefficient in 1 .. M/2-1; Parseval: the coefficients of the full circle
+    carry sum x_j^2."""
+    import oracle as om
+    M, k0 = 4096, 37
+    j = np.arange(M)
+    R = 0.5 + np.cos(2 * np.pi * j * k0 / M)
+    X = om.fourier_coefficients(R, M)[0]
+    assert abs(X[k0] - np.sqrt(M) / 2) < 1e-9
+    others = np.delete(np.abs(X[1:]), k0 - 1)
+    assert others.max() < 1e-9
+    rng = np.random.default_rng(5)
+    R = rng.random(M)
+    X = om.fourier_coefficients(R, M)[0]
+    full = np.fft.fft(R - 0.5) / np.sqrt(M)              # the whole circle
+    assert abs(np.sum(np.abs(full) ** 2) - np.sum((R - 0.5) ** 2)) < 1e-9
+    # the kept half equals the conjugate-symmetric half of the full transform
+    assert np.allclose(X, np.conj(full[: M // 2]))
+
+
+def test_fourier_variance_one_over_24(oracle_mod):
+    """Coefficients of the generator's numbers: real and imaginary parts with
+    variance 1/24 (within 2 %), mean about zero."""
+    import oracle as om
+    n = 4294967087
+    M = 1 << 16
+    c, r, _ = oracle_mod.generate(n, 9, P31, A31, 31337, 4242, 4 * M)
+    X = om.fourier_coefficients(r, M)[:, 1:].reshape(-1)
+    for part in (X.real, X.imag):
+        assert abs(part.var() * 24 - 1) < 0.02
+        assert abs(part.mean()) < 0.01
+    h = om.fourier_hist(X, 64, 1.0)
+    assert int(h.sum()) == 2 * X.size
+    assert om.fourier_bin(-1.0, 64, 1.0) == 0 and om.fourier_bin(0.999999, 64, 1.0) == 63
+    assert om.fourier_bin(5.0, 64, 1.0) == 63 and om.fourier_bin(-5.0, 64, 1.0) == 0
