@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=64)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--modes", default="fused,serial,small_e,pattern,wide64,batched,served",
+    ap.add_argument("--modes", default="fused,serial,small_e,pattern,fourier,wide64,batched,served",
                     help="comma-separated extra measurements after the headline, or 'none'")
     return ap.parse_args()
 
@@ -257,6 +257,44 @@ def measured_hbm_gbs():
         return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
     except (OSError, ValueError, KeyError):
         return None
+
+
+FP64_FMA_PER_CLK_SM = 2      # GB300's FP64 unit: 2 fused multiply-adds per clock per SM
+
+
+def mode_fourier(ph, torch, stream, lgM=20):
+    """The Fourier test at the paper's M = 2^20: 256 streams x 2^20 numbers
+    (2^28 numbers, 256 sequences), real and imaginary parts into 8,192 bins
+    over [-2, 2).  The FFT is bound by the FP64 unit; its achieved rate counts
+    the conventional 2.5 M log2 M flops of a real transform of M points over
+    the call's time minus that of generating the same numbers (timed alone)."""
+    from paper_1411_2484_gb300 import workloads
+    N, per, M = 256, 1 << 20, 1 << lgM
+    inst = workloads.workload_instances("plain32_65536x4096x64", N)
+    ctx = ph.phprng_create(32, inst, ph.PHPRNG_REQUIRE_SAFE_PRIME, stream)
+    try:
+        hist = torch.zeros(8192, dtype=torch.int64, device="cuda")
+        ms = timed(torch, stream, lambda: ph.phprng_fourier_test(ctx, 0, N, per, lgM, 8192, 2.0, hist,
+                                                                  None, stream), 4)
+        r = torch.empty(N * per, dtype=torch.float64, device="cuda")
+        ms_gen = timed(torch, stream, lambda: ph.phprng_generate(ctx, 0, N, per, None, r, None, stream), 4)
+    finally:
+        ph.phprng_destroy(ctx)
+    torch.cuda.synchronize()
+    h = hist.cpu().numpy().astype(np.float64)
+    centre = -2.0 + (np.arange(8192) + 0.5) * (4.0 / 8192)
+    var = float((h * centre ** 2).sum() / h.sum() - ((h * centre).sum() / h.sum()) ** 2)
+    flops = 2.5 * M * lgM * (N * per // M)
+    peak = SMS * FP64_FMA_PER_CLK_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    fft_ms = max(ms - ms_gen, 1e-6)
+    achieved = flops / fft_ms / 1e9
+    return {"value": N * per / ms * 1e3, "unit": "PRNs/s", "ms_per_call": ms, "ms_generate_alone": ms_gen,
+            "workload": "256 streams x 2^20 numbers, M = 2^20 (the paper's), 8,192 bins over [-2, 2)",
+            "variance_x24": var * 24,
+            "roofline": {"bound": "fp64", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak,
+                         "peak_source": "152 SMs x 2 FP64 FMA/clk x 2 x 2070 MHz (unit counts x max clock)",
+                         "algorithmic_flops_per_call": flops}}
 
 
 def mode_wide64(ph, torch, stream, peak):
@@ -538,6 +576,7 @@ def main():
                          ("serial", lambda: mode_serial(ph, torch, ctx2, N, per, stream)),
                          ("small_e", lambda: mode_small_e(ph, torch, stream, PEAK_TMULS)),
                          ("pattern", lambda: mode_pattern(ph, torch, stream)),
+                         ("fourier", lambda: mode_fourier(ph, torch, stream)),
                          ("wide64", lambda: mode_wide64(ph, torch, stream, PEAK_TMULS)),
                          ("batched", lambda: mode_batched(ph, torch, stream)),
                          ("served", lambda: mode_served(ph, torch))):

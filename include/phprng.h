@@ -234,6 +234,29 @@ int phprng_collision_test(phprng_ctx *ctx, uint64_t first, uint64_t num_inst, ui
 int phprng_runs_test(phprng_ctx *ctx, uint64_t first, uint64_t num_inst, uint64_t per_inst,
                      int lmax, uint64_t *hist, void *cuda_stream);
 
+/* Fourier test (Tests section): every instance of [first, first + num_inst)
+ * draws per_inst numbers R (Eq. 9), cut into per_inst / M consecutive
+ * sequences of M = 2^log2M; for each sequence x_j = R_j - 1/2 and
+ * xhat_k = M^(-1/2) sum_j x_j exp(+2 pi i j k / M), k = 0 .. M/2 - 1, and the
+ * real and imaginary parts of every xhat_k each add one to
+ * hist[floor((v + w) (nbins / 2w))], clamped to bins 0 and nbins - 1 outside
+ * [-w, w).  For uniform R both parts are close to normal with variance 1/24
+ * (k > 0).  Computed in FP64 on the device (the M real numbers as M/2 complex
+ * points, a four-step FFT of those, and the split into the real transform),
+ * so a coefficient differs from the plain sum by rounding (about 1e-15
+ * relative); a part within that of a bin edge may fall in the neighbouring
+ * bin.  coef_out (nullable, device, 16-byte aligned) receives the
+ * coefficients as (re, im) pairs: sequence q of the call (instances in order,
+ * their sequences in order) at coef_out[2 (q M/2 + k)].  Limits: 32-bit
+ * instances, 2 <= log2M <= 20, per_inst a multiple of M, 1 <= nbins <= 2^24,
+ * w > 0.  hist: device memory, nbins uint64 counters, added to.  Streams
+ * advance by per_inst.  Asynchronous on cuda_stream (scratch comes from the
+ * stream-ordered allocator: at most 2^26 numbers of R, as many bytes of
+ * transform scratch, and about M twiddle factors). */
+int phprng_fourier_test(phprng_ctx *ctx, uint64_t first, uint64_t num_inst, uint64_t per_inst,
+                        uint32_t log2M, uint32_t nbins, double w, uint64_t *hist, double *coef_out,
+                        void *cuda_stream);
+
 /* Full-period D-dimensional pattern of one instance (32-bit n) by
  * enumeration, as the paper derives after Eq. 7: over the whole period
  * n(p-1) the value c0 occurs p-1 times, once with each next skip s in

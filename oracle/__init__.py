@@ -335,9 +335,11 @@ def fourier_coefficients(R, M):
 
 
 def fourier_bin(v, nbins, w):
-    """Histogram bin of a real or imaginary part v: floor((v + w) / (2 w) nbins),
-    clamped to the first and last bins outside [-w, w)."""
-    b = np.floor((np.asarray(v, dtype=np.float64) + w) / (2 * w) * nbins)
+    """Histogram bin of a real or imaginary part v: floor((v + w) (nbins / 2w)),
+    clamped to the first and last bins outside [-w, w) (the two roundings --
+    the sum, then the product with the constant nbins / 2w -- are the ones the
+    library takes, so equal coefficients fall in equal bins)."""
+    b = np.floor((np.asarray(v, dtype=np.float64) + w) * (nbins / (2.0 * w)))
     return np.clip(b, 0, nbins - 1).astype(np.int64)
 
 

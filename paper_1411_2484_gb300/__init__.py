@@ -36,7 +36,7 @@ PHPRNG_ALLOW_SHARED_N = 0x2
 EXPORTED = [
     "phprng_create", "phprng_create_seeded", "phprng_destroy", "phprng_last_error",
     "phprng_status_string", "phprng_generate", "phprng_skip", "phprng_seek", "phprng_serial_test", "phprng_poker_test", "phprng_runs_test", "phprng_collision_test",
-    "phprng_pattern", "phprng_pattern_const",
+    "phprng_fourier_test", "phprng_pattern", "phprng_pattern_const",
     "phprng_get_state",
     "phprng_is_prime", "phprng_validate", "phprng_draw_instances", "phprng_microbench",
     "phprng_plan_create", "phprng_plan_launch", "phprng_plan_launch_graph",
@@ -140,6 +140,7 @@ def _load():
         lib.phprng_runs_test.argtypes = [vp, u64, u64, u64, i32, vp, vp]
         u32 = ctypes.c_uint32
         lib.phprng_collision_test.argtypes = [vp, u64, u64, u64, u32, u32, u32, vp, vp]
+        lib.phprng_fourier_test.argtypes = [vp, u64, u64, u64, u32, u32, ctypes.c_double, vp, vp, vp]
         lib.phprng_pattern.argtypes = [ctypes.POINTER(phprng_instance), u64, u64, i32,
                                        ctypes.c_uint32, vp, vp]
         lib.phprng_pattern_const.argtypes = [ctypes.POINTER(phprng_instance), u64, u64, u64, i32,
@@ -294,6 +295,17 @@ def phprng_runs_test(ctx, first, num_inst, per_inst, lmax, hist, stream=None):
     the device counters `hist` (2*lmax uint64); streams advance by per_inst."""
     _check(_load().phprng_runs_test(ctx, int(first), int(num_inst), int(per_inst), int(lmax),
                                     _ptr(hist), _stream(stream)), ctx)
+
+
+def phprng_fourier_test(ctx, first, num_inst, per_inst, log2M, nbins, w, hist, coef=None,
+                        stream=None):
+    """Adds the real and imaginary parts of the Fourier coefficients of every
+    sequence of 2**log2M numbers to the device counters `hist` (nbins uint64,
+    range [-w, w)); `coef` (device float64, optional) receives them as
+    (re, im) pairs; streams advance by per_inst."""
+    _check(_load().phprng_fourier_test(ctx, int(first), int(num_inst), int(per_inst), int(log2M),
+                                       int(nbins), float(w), _ptr(hist),
+                                       _ptr(coef) if coef is not None else None, _stream(stream)), ctx)
 
 
 def phprng_pattern(n, e, p, a, c_lo, L0, D, nb, hist, stream=None):

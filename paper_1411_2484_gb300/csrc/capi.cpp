@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <functional>
 #include <cstring>
+#include <cmath>
 #include <mutex>
 #include <new>
 #include <string>
@@ -784,6 +785,60 @@ PH_API int phprng_collision_test(phprng_ctx *ctx, uint64_t first, uint64_t num_i
     };
     return run_hist_test(ctx, "phprng_collision_test", first, num_inst, per_inst, 1, 1, hist, cuda_stream,
                          launch);
+}
+
+PH_API int phprng_fourier_test(phprng_ctx *ctx, uint64_t first, uint64_t num_inst, uint64_t per_inst,
+                               uint32_t log2M, uint32_t nbins, double w, uint64_t *hist, double *coef_out,
+                               void *cuda_stream)
+{
+    if (!ctx) return fail(nullptr, PHPRNG_EINVAL, "phprng_fourier_test: ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (ctx->serving) return fail(ctx, PHPRNG_EINVAL, "phprng_fourier_test: a server owns the context");
+    if (first > ctx->count || num_inst > ctx->count - first)
+        return fail(ctx, PHPRNG_EINVAL, "phprng_fourier_test: instance range outside the table");
+    if (log2M < 2 || log2M > 20) return fail(ctx, PHPRNG_EINVAL, "phprng_fourier_test: log2M must be 2..20");
+    const uint64_t M = 1ull << log2M;
+    if (per_inst % M) return fail(ctx, PHPRNG_EINVAL, "phprng_fourier_test: per_inst must be a multiple of M");
+    if (nbins < 1 || nbins > (1u << 24) || !(w > 0.0) || !(w < 1e300))
+        return fail(ctx, PHPRNG_EINVAL, "phprng_fourier_test: need 1 <= nbins <= 2^24 and w > 0");
+    if (!hist || (uintptr_t)hist % 8 || (uintptr_t)coef_out % 16)
+        return fail(ctx, PHPRNG_EINVAL, "phprng_fourier_test: hist NULL or misaligned, or coef_out misaligned");
+    if (num_inst == 0 || per_inst == 0) return PHPRNG_OK;
+    for (uint64_t i = first; i < first + num_inst; ++i)
+        if (ctx->wide[i]) return fail(ctx, PHPRNG_EINVAL, "phprng_fourier_test: defined for 32-bit moduli only");
+    CU(ctx, cudaSetDevice(ctx->device));
+    if (pointer_kind(hist) != 1 || (coef_out && pointer_kind(coef_out) != 1))
+        return fail(ctx, PHPRNG_EINVAL, "phprng_fourier_test: hist and coef_out must be device memory");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    // instances per batch: R scratch of at most 2^26 doubles (512 MiB)
+    const uint64_t batch = std::max<uint64_t>(1, std::min<uint64_t>(num_inst, (1ull << 26) / per_inst));
+    double2 *tw = nullptr, *Z = nullptr;
+    double *R = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&tw, fourier_twiddle_count(log2M) * sizeof(double2), s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&R, batch * per_inst * sizeof(double), s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&Z, batch * per_inst / 2 * sizeof(double2), s);
+    std::string err;
+    int rc = e == cudaSuccess ? PHPRNG_OK : PHPRNG_ENOMEM;
+    if (rc == PHPRNG_OK) rc = launch_twiddles(tw, log2M, s, &err);
+    const double scale2 = 0.5 / std::sqrt((double)M);
+    for (uint64_t b0 = 0; b0 < num_inst && rc == PHPRNG_OK; b0 += batch) {
+        const uint64_t nb = std::min(batch, num_inst - b0);
+        rc = launch_range(ctx, first + b0, nb, per_inst, nullptr, R, nullptr, s, true);   // Eq. 9
+        if (rc != PHPRNG_OK) break;
+        double *cb = coef_out ? coef_out + 2 * (b0 * per_inst / 2) : nullptr;
+        rc = launch_fourier(R, nb * per_inst / M, log2M, tw, Z, nbins, w, scale2, hist, cb, s, &err);
+        if (rc == PHPRNG_OK)
+            for (uint64_t i = first + b0; i < first + b0 + nb; ++i) ctx->pos_host[i] += per_inst;
+    }
+    if (tw) cudaFreeAsync(tw, s);
+    if (R) cudaFreeAsync(R, s);
+    if (Z) cudaFreeAsync(Z, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, PHPRNG_ENOMEM, "phprng_fourier_test: scratch allocation failed");
+    }
+    if (rc != PHPRNG_OK) return err.empty() ? rc : fail(ctx, rc, "phprng_fourier_test: " + err);
+    return PHPRNG_OK;
 }
 
 PH_API int phprng_runs_test(phprng_ctx *ctx, uint64_t first, uint64_t num_inst, uint64_t per_inst,

@@ -7,6 +7,8 @@
 #include <vector>
 
 #include "../../include/phprng.h"
+struct double2;   // vector_types.h (CUDA); pointers only here
+
 #include "arith.cuh"
 
 // Numbers per lane per warp group of the 32-bit and 64-bit generators (the
@@ -165,6 +167,18 @@ int launch_runs(const GenArgs &a, int lmax, unsigned long long *hist, void *stre
 int launch_pattern_const(const DevInst &P, const ExpProg &pg, const DevInst &Pd, const ExpProg &pgd,
                          uint32_t b, uint64_t c_lo, uint64_t L0, int D, uint32_t nb, uint64_t *hist,
                          void *stream, std::string *err);
+// Fourier test (fourier.cu).  Twiddle tables for sequences of M = 2^lgM
+// numbers: fourier_twiddle_count(lgM) double2, filled by launch_twiddles.
+// launch_fourier: for nseq sequences of M doubles R (contiguous), the
+// coefficients k < M/2 of the positive-exponent transform of R - 1/2 times
+// scale2 = 1/(2 sqrt M) twice over (the real-input split halves), real and
+// imaginary parts binned into hist[nbins] over [-w, w) (clamped); Z scratch of
+// nseq M/2 double2; coef (nullable) gets nseq M/2 double2.
+uint64_t fourier_twiddle_count(uint32_t lgM);
+int launch_twiddles(double2 *tw, uint32_t lgM, void *stream, std::string *err);
+int launch_fourier(const double *R, uint64_t nseq, uint32_t lgM, const double2 *tw, double2 *Z,
+                   uint32_t nbins, double w, double scale2, uint64_t *hist, double *coef, void *stream,
+                   std::string *err);
 // Collision-test consumer (serial.cu): segments of S numbers into B bins,
 // collision counts into hist[H]; a persistent grid of `warps` warps (from
 // collision_grid_warps()), each with a zeroed bitmap of ceil(B/32) words.

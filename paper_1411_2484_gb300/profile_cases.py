@@ -10,6 +10,8 @@ CASE is one of
   pattern3  the paper's pattern instance (n = 4294967087, p = 2^31-1,
             e = 9), D = 3, 2^24 volumes, L0 = 4 (2^33 points)       pattern_kernel
   wide64    4,096 64-bit instances x 4,096 numbers, R (128 MiB)      gen64_kernel
+  fourier20 plain32's first 256 instances x 2^20 numbers, Fourier test
+            over sequences of M = 2^20 (the paper's), 8,192 bins       fft_*_kernel
   batched   2,000 instances (80 % 32-bit), lengths log-uniform in
             [1, 2^18], offsets in [0, 2^40), R (about 0.4 GiB)       batch_kernel
 Each case warms up once, then launches its kernel N times (default 3) and
@@ -27,7 +29,7 @@ from paper_1411_2484_gb300 import workloads
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["plain32", "fused32", "small_e", "serial2", "pattern3", "wide64", "batched"])
+    ap.add_argument("case", choices=["plain32", "fused32", "small_e", "serial2", "pattern3", "wide64", "batched", "fourier20"])
     ap.add_argument("--repeat", type=int, default=3)
     args = ap.parse_args()
     s = torch.cuda.current_stream()
@@ -53,6 +55,13 @@ def main():
         else:
             sb = torch.empty(N * ph.STATS_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
             run = lambda: ph.phprng_generate(ctx, 0, N, per, None, None, sb, s)
+        numbers = N * per
+    elif args.case == "fourier20":
+        inst = workloads.workload_instances("plain32_65536x4096x64", 256)
+        N, per = 256, 1 << 20
+        ctx = ph.phprng_create(32, inst, ph.PHPRNG_REQUIRE_SAFE_PRIME, s)
+        hist = torch.zeros(8192, dtype=torch.int64, device="cuda")
+        run = lambda: ph.phprng_fourier_test(ctx, 0, N, per, 20, 8192, 2.0, hist, None, s)
         numbers = N * per
     elif args.case == "small_e":
         inst = workloads.workload_instances("plain32_e9_65536x4096")

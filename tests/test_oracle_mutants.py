@@ -88,3 +88,36 @@ def test_unmutated_copy_passes(tmp_path):
     so = oracle.build(force=True, src=oracle._SRC, out=str(tmp_path / "clean.so"))
     rc, out = _run_pins(so)
     assert rc == 0, out
+
+
+# Mistakes planted in the Python part of the oracle (the Fourier test): the
+# function is re-made from its own source with one change and the pins run
+# against it in this process.
+PY_MUTANTS = {
+    "fourier_negative_exponent": ("fourier_coefficients", "X = np.fft.ifft(x, axis=1) * M",
+                                  "X = np.fft.fft(x, axis=1)"),
+    "fourier_dropped_offset": ("fourier_coefficients", "reshape(seqs, M) - 0.5", "reshape(seqs, M)"),
+    "fourier_scale": ("fourier_coefficients", "/ np.sqrt(M)", "/ M"),
+    "fourier_bin_width": ("fourier_bin", "(nbins / (2.0 * w))", "(nbins / w)"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(PY_MUTANTS))
+def test_planted_python_mistake_is_caught(monkeypatch, name):
+    import inspect
+    import textwrap
+    import test_oracle_pins as pins
+    fn_name, old, new = PY_MUTANTS[name]
+    src = textwrap.dedent(inspect.getsource(getattr(oracle, fn_name)))
+    assert src.count(old) == 1, "mutation anchor missing: " + old
+    ns = dict(vars(oracle))
+    exec(compile(src.replace(old, new), "<mutant>", "exec"), ns)
+    monkeypatch.setattr(oracle, fn_name, ns[fn_name])
+    failed = False
+    for test in (pins.test_fourier_pure_tone_and_parseval, pins.test_fourier_direct_sum_and_bin_edges,
+                 pins.test_fourier_variance_one_over_24):
+        try:
+            test(oracle._default())
+        except AssertionError:
+            failed = True
+    assert failed, "pins did not catch mutant " + name

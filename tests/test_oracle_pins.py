@@ -565,6 +565,28 @@ def test_fourier_pure_tone_and_parseval(oracle_mod):
     assert np.allclose(X, np.conj(full[: M // 2]))
 
 
+def test_fourier_direct_sum_and_bin_edges(oracle_mod):
+    """Brute force on a tiny input: the definition summed term by term with
+    complex exponentials, for two sequences of M = 64; and bin edges: a part
+    exactly at -w + 2w b / nbins falls in bin b."""
+    import cmath
+    import oracle as om
+    M = 64
+    rng = np.random.default_rng(11)
+    R = rng.random(2 * M)
+    X = om.fourier_coefficients(R, M)
+    assert X.shape == (2, M // 2)
+    for s in range(2):
+        for k in range(M // 2):
+            want = sum((R[s * M + j] - 0.5) * cmath.exp(2j * cmath.pi * j * k / M)
+                       for j in range(M)) / M ** 0.5
+            assert abs(X[s, k] - want) < 1e-12
+    for nbins, w in ((64, 1.0), (8, 0.5), (4096, 2.0)):
+        for b in (0, 1, nbins // 2, nbins - 1):
+            assert om.fourier_bin(-w + 2 * w * b / nbins, nbins, w) == b
+            assert om.fourier_bin(-w + 2 * w * (b + 1) / nbins - 1e-9, nbins, w) == b
+
+
 def test_fourier_variance_one_over_24(oracle_mod):
     """Coefficients of the generator's numbers: real and imaginary parts with
     variance 1/24 (within 2 %), mean about zero."""
