@@ -447,6 +447,21 @@ int phprng_server_stats_get(phprng_server *srv, phprng_server_stats *out);
  * (Eq. 7); the arena is freed.  NULL is accepted. */
 int phprng_server_destroy(phprng_server *srv);
 
+/* Sets instance inst's state: its next number is made from message m and skip
+ * s by Eq. 9 as number pos+1 of its stream, and c is kept as the last
+ * ciphertext.  The stream is redefined as the one through (m, s) at position
+ * pos: its seed becomes the state pos steps earlier (Eq. 7 backwards: the
+ * cycle position of s is a discrete logarithm on the host, the sum of the
+ * skips in between comes from the prefix table), so phprng_seek,
+ * phprng_skip, batched requests with offsets and the server all follow the
+ * new stream.  With phprng_get_state this checkpoints and restores streams,
+ * also into another context made from the same instance table (the seed then
+ * comes out unchanged).  Limits: m < n, c < n, 1 <= s <= p-1.  Builds the
+ * prefix table on first use; waits for work queued on cuda_stream and
+ * returns with the state written. */
+int phprng_set_state(phprng_ctx *ctx, uint64_t inst, uint64_t m, uint64_t s, uint64_t c, uint64_t pos,
+                     void *cuda_stream);
+
 /* Copies instance inst's parameters and current state to the host: the
  * returned phprng_instance holds {n, e, p, a, m, s} with m, s the current
  * message and skip; *pos_out (nullable) its stream position and *c_out

@@ -37,7 +37,7 @@ EXPORTED = [
     "phprng_create", "phprng_create_seeded", "phprng_destroy", "phprng_last_error",
     "phprng_status_string", "phprng_generate", "phprng_skip", "phprng_seek", "phprng_serial_test", "phprng_poker_test", "phprng_runs_test", "phprng_collision_test",
     "phprng_fourier_test", "phprng_pattern", "phprng_pattern_const",
-    "phprng_get_state",
+    "phprng_get_state", "phprng_set_state",
     "phprng_is_prime", "phprng_validate", "phprng_draw_instances", "phprng_microbench",
     "phprng_plan_create", "phprng_plan_launch", "phprng_plan_launch_graph",
     "phprng_plan_autotune", "phprng_plan_tuning", "phprng_plan_destroy", "phprng_generate_batch",
@@ -146,6 +146,7 @@ def _load():
         lib.phprng_pattern_const.argtypes = [ctypes.POINTER(phprng_instance), u64, u64, u64, i32,
                                              ctypes.c_uint32, vp, vp]
         lib.phprng_get_state.argtypes = [vp, u64, P_inst, P64, P64, vp]
+        lib.phprng_set_state.argtypes = [vp, u64, u64, u64, u64, u64, vp]
         lib.phprng_is_prime.argtypes = [u64]
         lib.phprng_validate.argtypes = [i32, P_inst, u64, u32, P64]
         lib.phprng_draw_instances.argtypes = [i32, u64, u64, u32, P_inst]
@@ -335,6 +336,12 @@ def phprng_seek(ctx, inst_ids, pos, stream=None):
     P64 = ctypes.POINTER(ctypes.c_uint64)
     _check(_load().phprng_seek(ctx, ids.ctypes.data_as(P64), ps.ctypes.data_as(P64), ids.size,
                                _stream(stream)), ctx)
+
+
+def phprng_set_state(ctx, inst, m, s, c=0, pos=0, stream=None):
+    """Sets instance inst to message m, skip s, last ciphertext c at stream
+    position pos (the stream is redefined through that state)."""
+    _check(_load().phprng_set_state(ctx, int(inst), int(m), int(s), int(c), int(pos), _stream(stream)), ctx)
 
 
 def phprng_get_state(ctx, inst, stream=None):

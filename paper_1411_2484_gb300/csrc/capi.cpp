@@ -633,6 +633,65 @@ int ensure_skip(phprng_ctx *c, cudaStream_t s)
     return PHPRNG_OK;
 }
 
+// Pref(t) = sum_{i=1..t} (a^i mod p), 0 <= t <= p-1, on the host from the
+// device table's checkpoint at floor(t/B) B plus the tail of fewer than B terms.
+static int host_pref(phprng_ctx *c, uint64_t t, uint64_t *out)
+{
+    const uint64_t j = t >> kSkipLog2B;
+    uint64_t T;
+    uint32_t x;
+    cudaError_t e = cudaMemcpy(&T, c->d_T + j, 8, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&x, c->d_P + j, 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "phprng_set_state: prefix table read");
+    uint64_t v = x;
+    for (uint64_t u = j << kSkipLog2B; u < t; ++u) {
+        v = v * c->a % c->p;
+        T += v;
+    }
+    *out = T;
+    return PHPRNG_OK;
+}
+
+PH_API int phprng_set_state(phprng_ctx *ctx, uint64_t inst, uint64_t m, uint64_t s, uint64_t c,
+                            uint64_t pos, void *cuda_stream)
+{
+    if (!ctx) return fail(nullptr, PHPRNG_EINVAL, "phprng_set_state: ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (ctx->serving) return fail(ctx, PHPRNG_EINVAL, "phprng_set_state: a server owns the context");
+    if (inst >= ctx->count) return fail(ctx, PHPRNG_EINVAL, "phprng_set_state: instance out of range");
+    const uint64_t n = ctx->host_inst[inst].n, p = ctx->p, pm1 = p - 1;
+    if (m >= n || c >= n) return fail(ctx, PHPRNG_EINVAL, "phprng_set_state: need m < n and c < n");
+    if (s < 1 || s > pm1) return fail(ctx, PHPRNG_EINVAL, "phprng_set_state: need 1 <= s <= p-1");
+    CU(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int rc = ensure_skip(ctx, st);
+    if (rc != PHPRNG_OK) return rc;
+    // the stream through (m, s) at position pos: cycle position of s, then the
+    // seed pos steps earlier (Eq. 7 backwards: L0 = L - pos, m0 = m - F)
+    uint64_t Ls;
+    if (!discrete_logs(p, ctx->a, &s, 1, &Ls))
+        return fail(ctx, PHPRNG_ESKIP, "phprng_set_state: no discrete log for s");
+    const uint64_t q = pos / pm1, r = pos % pm1;
+    const uint64_t L0 = (Ls + pm1 - r) % pm1;
+    uint64_t P0, P1, W;
+    rc = host_pref(ctx, L0, &P0);
+    if (rc == PHPRNG_OK) rc = host_pref(ctx, L0 + r <= pm1 ? L0 + r : L0 + r - pm1, &P1);
+    if (rc != PHPRNG_OK) return rc;
+    W = L0 + r <= pm1 ? P1 - P0 : ctx->tbl.half - P0 + P1;
+    const uint64_t F = (mulmod(q % n, ctx->tbl.half % n, n) + W % n) % n;
+    const uint64_t m0 = m >= F ? m - F : m + (n - F), s0 = powmod(ctx->a, L0, p);
+    const uint64_t v[4] = {m, s, c, pos};
+    CU(ctx, cudaStreamSynchronize(st));
+    for (int k = 0; k < 4; ++k)
+        CU(ctx, cudaMemcpy(ctx->d_state + (uint64_t)k * ctx->count + inst, &v[k], 8, cudaMemcpyHostToDevice));
+    CU(ctx, cudaMemcpy(ctx->d_L0 + inst, &L0, 8, cudaMemcpyHostToDevice));
+    CU(ctx, cudaMemcpy(ctx->d_m0 + inst, &m0, 8, cudaMemcpyHostToDevice));
+    ctx->host_inst[inst].m0 = m0;
+    ctx->host_inst[inst].s0 = s0;
+    ctx->pos_host[inst] = pos;
+    return PHPRNG_OK;
+}
+
 PH_API int phprng_skip(phprng_ctx *ctx, const uint64_t *inst_ids, const uint64_t *k,
                        uint64_t cnt, void *cuda_stream)
 {

@@ -194,3 +194,85 @@ def test_seek_backward_and_forward(ph, torch, table31, width):
             ph.phprng_seek(ctx, [8], [1])                                # out of range
     finally:
         ph.phprng_destroy(ctx)
+
+
+@pytest.mark.parametrize("width", [32, 64])
+def test_set_state_restores_into_a_fresh_context(ph, torch, table31, width):
+    """Checkpoint and restore: states read from one context and written into a
+    fresh context of the same instance table continue identically, and the
+    restored streams keep their seeds (seeking back to 0 gives m0, s0)."""
+    inst = workloads.draw_instances(6, width=width, seed=60 + width)
+    a = ph.phprng_create(width, inst, 0)
+    b = ph.phprng_create(width, inst, 0)
+    try:
+        gen(ph, torch, a, width, 0, 6, 3001)
+        ph.phprng_skip(a, [2, 4], [10 ** 12, (P31 - 1) * 5 + 3])
+        saved = [ph.phprng_get_state(a, i) for i in range(6)]
+        for i, st in enumerate(saved):
+            ph.phprng_set_state(b, i, st["m"], st["s"], st["c"], st["pos"])
+        for i in range(6):
+            assert ph.phprng_get_state(b, i) == saved[i]
+        ca, ra = gen(ph, torch, a, width, 0, 6, 777)
+        cb, rb = gen(ph, torch, b, width, 0, 6, 777)
+        assert np.array_equal(ca, cb) and np.array_equal(ra.view(np.uint64), rb.view(np.uint64))
+        ph.phprng_seek(b, list(range(6)), [0] * 6)
+        for i in range(6):
+            s = ph.phprng_get_state(b, i)
+            assert (s["m"], s["s"], s["c"], s["pos"]) == (int(inst["m0"][i]), int(inst["s0"][i]), 0, 0)
+    finally:
+        ph.phprng_destroy(a)
+        ph.phprng_destroy(b)
+
+
+@pytest.mark.parametrize("width", [32, 64])
+def test_set_state_arbitrary_against_oracle(ph, torch, table31, width):
+    """An arbitrary (m, s) at an arbitrary position: generation continues by
+    Eq. 9 from it (oracle), seek forward from it equals stepping the oracle,
+    seek back to 0 and forward again returns to it, and a batched request at
+    an offset follows the redefined stream."""
+    inst = workloads.draw_instances(4, width=width, seed=70 + width)
+    ctx = ph.phprng_create(width, inst, 0)
+    rng = np.random.default_rng(width)
+    try:
+        picks = []
+        for i in range(4):
+            n = int(inst["n"][i])
+            m = int(rng.integers(0, n - 1, dtype=np.uint64))
+            s = int(rng.integers(1, P31 - 1))
+            pos = [0, 17, 10 ** 11 + 5, (P31 - 1) * 7 + 1000][i]
+            ph.phprng_set_state(ctx, i, m, s, 12345 % n, pos)
+            picks.append((n, int(inst["e"][i]), m, s, pos))
+        c, r = gen(ph, torch, ctx, width, 0, 4, 1500)
+        for i, (n, e, m, s, pos) in enumerate(picks):
+            cr, rr, st = oracle.generate(n, e, P31, A31, m, s, 1500)
+            assert np.array_equal(c[i], cr) and np.array_equal(r[i].view(np.uint64), rr.view(np.uint64))
+            assert ph.phprng_get_state(ctx, i)["pos"] == pos + 1500
+        # forward by seek: 1500 numbers plus 2 full cycles plus 99 beyond the set state
+        ph.phprng_seek(ctx, list(range(4)), [p[4] + 1500 + 2 * (P31 - 1) + 99 for p in picks])
+        c2, _ = gen(ph, torch, ctx, width, 0, 4, 64)
+        for i, (n, e, m, s, pos) in enumerate(picks):
+            _, _, st = oracle.generate(n, e, P31, A31, m, s, 1500 + 99)
+            # two whole skip cycles add 2 p(p-1)/2 to m and leave s unchanged
+            m2 = (int(st[0]) + 2 * (P31 * (P31 - 1) // 2)) % n
+            cr, _, _ = oracle.generate(n, e, P31, A31, m2, int(st[1]), 64)
+            assert np.array_equal(c2[i], cr), i
+        ph.phprng_seek(ctx, list(range(4)), [0] * 4)
+        ph.phprng_seek(ctx, list(range(4)), [p[4] for p in picks])
+        for i, (n, e, m, s, pos) in enumerate(picks):
+            g = ph.phprng_get_state(ctx, i)
+            assert (g["m"], g["s"], g["pos"]) == (m, s, pos), i
+        # a batched request 250 numbers past the set state
+        reqs = np.zeros(1, dtype=[(k, "<u8") for k in ("inst", "offset", "len", "c_off", "r_off")])
+        reqs[0] = (1, picks[1][4] + 250, 300, 0, 0)
+        rb = torch.empty(300, dtype=torch.float64, device="cuda")
+        ph.phprng_generate_batch(ctx, reqs, None, rb)
+        torch.cuda.synchronize()
+        n, e, m, s, pos = picks[1]
+        _, rr, _ = oracle.generate(n, e, P31, A31, m, s, 550)
+        assert np.array_equal(rb.cpu().numpy().view(np.uint64), rr[250:].view(np.uint64))
+        for bad in ((0, int(inst["n"][0]), 1, 0, 0), (0, 1, 0, 0, 0), (0, 1, P31, 0, 0),
+                    (0, 1, 1, int(inst["n"][0]), 0), (4, 1, 1, 0, 0)):
+            with pytest.raises(ph.PhprngError):
+                ph.phprng_set_state(ctx, *bad)
+    finally:
+        ph.phprng_destroy(ctx)
