@@ -480,7 +480,9 @@ int phprng_get_state(phprng_ctx *ctx, uint64_t inst, phprng_instance *state_out,
  * 0 and 1 make one half, form 2 two), 3 the generator's Montgomery product
  * mod a 32-bit prime, 4 fma.rn.f64, 5 the generator's window exponent
  * programs alone on 65,536 seeded 32-bit instances (Montgomery products per
- * second; draws the instances on the host first).  Allocates and frees small
+ * second; draws the instances on the host first), 6 div.rn.f64 (FP64
+ * division), 7 the generator's correctly rounded R = (c+1)/(n+1) built from
+ * integers (Eq. 9d; numbers per second).  Allocates and frees small
  * device buffers.  The paper has no counterpart: this is the measurement used to
  * state the multiply-bound roofline of Eq. 9c. */
 int phprng_microbench(int which, double *ops_per_s, void *cuda_stream);

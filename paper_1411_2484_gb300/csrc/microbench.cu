@@ -14,6 +14,10 @@
 //      primes, random exponents), one warp per instance, 8 messages per
 //      lane, 16 exponentiations back to back; the rate counts Montgomery
 //      products (table, windows, squarings and the exit product).
+//   6  div.rn.f64              FP64 division, IEEE round to nearest (what
+//                              R = (c+1)/(n+1) costs as a floating division)
+//   7  the generator's R built from integers (Eq. 9d, correctly rounded),
+//      for n = 2^32 - 5: the replacement of form 6
 #include <cuda_runtime.h>
 
 #include <vector>
@@ -27,7 +31,8 @@ static constexpr int kChains = 8, kUnroll = 16;
 
 template <int FORM>
 __global__ void __launch_bounds__(256) microbench_kernel(uint32_t *sink, int iters, uint32_t c,
-                                                         uint32_t n, uint32_t ninv)
+                                                         uint32_t n, uint32_t ninv, uint32_t yN,
+                                                         uint32_t ybits, uint64_t W)
 {
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t x[kChains];
@@ -53,6 +58,12 @@ __global__ void __launch_bounds__(256) microbench_kernel(uint32_t *sink, int ite
                     x[k] = (uint32_t)acc[k];
                 } else if (FORM == 3) {
                     x[k] = mont32(x[k], x[k], n, ninv);   // exact for any inputs < 2^32 here
+                } else if (FORM == 6) {
+                    asm volatile("div.rn.f64 %0, %1, %0;" : "+d"(d[k]) : "d"(1.0000001));
+                } else if (FORM == 7) {
+                    // c < 2^31 <= n - 1; the result's low bits feed the next c
+                    const double R = real32_fast(x[k] & 0x7FFFFFFFu, yN, ybits, W);
+                    x[k] ^= (uint32_t)__double_as_longlong(R);
                 } else {
                     asm volatile("fma.rn.f64 %0, %0, %1, %2;" : "+d"(d[k]) : "d"(0.999999), "d"(1e-7));
                 }
@@ -87,11 +98,16 @@ static int run_one(double *ops_per_s, cudaStream_t s, std::string *err)
     const uint32_t n = 4294967291u;
     uint32_t ninv = n;
     for (int i = 0; i < 5; ++i) ninv *= 2u - n * ninv;
-    int iters = FORM == 4 ? 64 : 256;
+    int iters = FORM == 4 ? 64 : FORM >= 6 ? 16 : 256;
+    // R of form 7 for n = 2^32 - 5, from the host's own derivation
+    const phprng_instance in = {n, 3, 2147483647u, 784588716u, 0, 1};
+    ExpProg pg;
+    const DevInst P = derive_inst(in, 0, &pg);
     float ms = 0.f;
     for (int rep = 0; rep < 3; ++rep) {            // warm-up, then two timed sizes
         cudaEventRecord(e0, s);
-        microbench_kernel<FORM><<<(unsigned)grid, 256, 0, s>>>(sink, iters, 2654435769u, n, ninv);
+        microbench_kernel<FORM><<<(unsigned)grid, 256, 0, s>>>(sink, iters, 2654435769u, n, ninv, P.yN,
+                                                               P.ybits, P.aux);
         cudaEventRecord(e1, s);
         cudaEventSynchronize(e1);
         cudaEventElapsedTime(&ms, e0, e1);
@@ -194,6 +210,8 @@ int run_microbench(int which, double *ops_per_s, void *stream, std::string *err)
     case 3: return run_one<3>(ops_per_s, s, err);
     case 4: return run_one<4>(ops_per_s, s, err);
     case 5: return run_exp(ops_per_s, s, err);
+    case 6: return run_one<6>(ops_per_s, s, err);
+    case 7: return run_one<7>(ops_per_s, s, err);
     default:
         *err = "microbench: unknown form";
         return PHPRNG_EINVAL;

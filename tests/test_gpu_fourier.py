@@ -157,3 +157,31 @@ def test_fourier_argument_errors(ph, torch):
             ph.phprng_fourier_test(ctx, 0, 1, 32, 4, 16, 1.0, hist)
     finally:
         ph.phprng_destroy(ctx)
+
+
+def test_fourier_bench_size_sampled(ph, torch):
+    """The benchmark's launch: the first 256 instances of the plain 32-bit
+    workload x 2^20 numbers at M = 2^20, 8,192 bins over [-2, 2).  Sampled
+    sequences (first, middle, last instance, the last in the fourth 2^26-number
+    batch) equal the oracle's; the histogram holds every part and is the
+    binning of all the library's coefficients."""
+    inst = workloads.workload_instances("plain32_65536x4096x64", 256)
+    N, per, lgM, nbins, w = 256, 1 << 20, 20, 8192, 2.0
+    ctx = ph.phprng_create(32, inst, ph.PHPRNG_REQUIRE_SAFE_PRIME)
+    try:
+        hist = torch.zeros(nbins, dtype=torch.int64, device="cuda")
+        coef = torch.empty(N * per, dtype=torch.float64, device="cuda")
+        ph.phprng_fourier_test(ctx, 0, N, per, lgM, nbins, w, hist, coef)
+        torch.cuda.synchronize()
+        h = hist.cpu().numpy().view(np.uint64)
+        assert int(h.sum()) == N * per
+        X = coef.cpu().numpy().view(np.complex128).reshape(N, per // 2)
+        mine = oracle.fourier_hist(X, nbins, w)
+        assert np.array_equal(h, mine)
+    finally:
+        ph.phprng_destroy(ctx)
+    rows = workloads.instance_rows(inst)
+    for i in (0, 127, 200, 255):
+        _, r, _, _ = oracle.generate_many(rows[i:i + 1], per, threads=1, want_c=False)
+        want = oracle.fourier_coefficients(r[0], 1 << lgM)[0]
+        assert np.max(np.abs(X[i] - want)) < ATOL, i
