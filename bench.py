@@ -154,7 +154,7 @@ def cpu_baseline(inst, per_inst, target_s=12.0):
 
 
 def muls_per_number(e, wide):
-    """32-bit product halves per number (SURVEY-style algorithmic count): the
+    """32-bit product halves per number (the algorithmic count of the roofline): the
     binary method's squarings and multiplications of Eq. 9c plus the skip
     product of Eq. 9a; 4 halves per 32-bit Montgomery product, 20 per 64-bit
     one (full 128-bit product 8, low word of q 4, high word of q n 8)."""
