@@ -77,6 +77,19 @@ PH_HD uint32_t mont32(uint32_t a, uint32_t b, uint32_t n, uint32_t ninv)
     return hi < u ? t + n : t;
 }
 
+// Montgomery product by a constant b with bq = b n^-1 mod 2^32 precomputed:
+// the low word of a b is needed only to form q = lo(a b) n^-1 = a bq mod 2^32,
+// and the subtractive form never reads it otherwise (lo(q n) = lo(a b)), so
+// three multiplies replace four.
+PH_HD uint32_t mont32c(uint32_t a, uint32_t b, uint32_t bq, uint32_t n)
+{
+    const uint32_t hi = umulhi32(a, b);
+    const uint32_t q = a * bq;
+    const uint32_t u = umulhi32(q, n);
+    const uint32_t t = hi - u;
+    return hi < u ? t + n : t;
+}
+
 PH_HD uint64_t mont64(uint64_t a, uint64_t b, uint64_t n, uint64_t ninv)
 {
     uint64_t lo = a * b, hi = umulhi64(a, b);
@@ -153,6 +166,9 @@ struct alignas(16) ExpProg {
 
 PH_HD uint32_t mont(uint32_t a, uint32_t b, uint32_t n, uint32_t ninv) { return mont32(a, b, n, ninv); }
 PH_HD uint64_t mont(uint64_t a, uint64_t b, uint64_t n, uint64_t ninv) { return mont64(a, b, n, ninv); }
+// The exit product x K of an exponentiation (Kq = K n^-1 mod 2^32 on the 32-bit path).
+PH_HD uint32_t mont_exit(uint32_t x, uint32_t K, uint32_t Kq, uint32_t n, uint32_t) { return mont32c(x, K, Kq, n); }
+PH_HD uint64_t mont_exit(uint64_t x, uint64_t K, uint64_t, uint64_t n, uint64_t ninv) { return mont64(x, K, n, ninv); }
 
 // x_u = MP(x_u, y_u) for every u.  The 32-bit form is written phase by phase
 // across the NPT independent products (all full products, then all q, then
@@ -221,11 +237,12 @@ PH_HD void mont_sqr_vec(uint32_t (&x)[NPT], uint32_t n, uint32_t ninv)
 
 // c_u = m_u^e mod n for NPT messages by the exponent's program (Eq. 9c with
 // fewer products than the binary method), closed by one product with the
-// exit constant K the host derived for that program.  All control flow
+// exit constant K the host derived for that program (Kq = K n^-1 mod 2^32 for
+// the 32-bit path, unused on the 64-bit one).  All control flow
 // depends only on the program, so it is uniform across a warp that shares
 // the instance.
 template <int NPT, typename W>
-PH_HD void modexp_prog(W (&x)[NPT], const W (&m)[NPT], const ExpProg &pg, W n, W ninv, W K)
+PH_HD void modexp_prog(W (&x)[NPT], const W (&m)[NPT], const ExpProg &pg, W n, W ninv, W K, W Kq)
 {
     W t3[NPT], t5[NPT], t7[NPT];
     const int tbl = pg.tbl;
@@ -302,7 +319,7 @@ PH_HD void modexp_prog(W (&x)[NPT], const W (&m)[NPT], const ExpProg &pg, W n, W
     }
     for (int sq = pg.tail; sq > 0; --sq) mont_sqr_vec<NPT>(x, n, ninv);
 #pragma unroll
-    for (int u = 0; u < NPT; ++u) x[u] = mont(x[u], K, n, ninv);
+    for (int u = 0; u < NPT; ++u) x[u] = mont_exit(x[u], K, Kq, n, ninv);
 }
 
 PH_HD int clz64(uint64_t x)

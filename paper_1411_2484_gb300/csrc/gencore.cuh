@@ -35,7 +35,7 @@ static constexpr unsigned kFullMask = 0xffffffffu;
 // slower on GB300: it trades two multiplier slots for three ALU operations.)
 __device__ __forceinline__ uint32_t skip_step(const SkipConst &sk, uint32_t s, bool group)
 {
-    return mont32(s, group ? sk.aGM : sk.aM, sk.p, sk.pinv);
+    return group ? mont32c(s, sk.aGM, sk.aGMq, sk.p) : mont32c(s, sk.aM, sk.aMq, sk.p);
 }
 
 // s * a^(c Lc) mod p for a plain skip s: the start skip of chunk c of a
@@ -133,17 +133,17 @@ template <int NPT, typename W>
 __device__ __forceinline__ void encrypt(const DevInst &P, const ExpProg &pg, const W (&msg)[NPT],
                                         W (&x)[NPT])
 {
-    const W n = (W)P.n, ninv = (W)P.ninv, K = (W)P.K;
+    const W n = (W)P.n, ninv = (W)P.ninv, K = (W)P.K, Kq = (W)(P.ninv >> 32);
     if (P.fermat) {
 #pragma unroll
         for (int u = 0; u < NPT; ++u) x[u] = msg[u];
         for (uint32_t q = P.fermat; q > 0; --q) mont_sqr_vec<NPT>(x, n, ninv);
         mont_vec<NPT>(x, msg, n, ninv);
 #pragma unroll
-        for (int u = 0; u < NPT; ++u) x[u] = mont(x[u], K, n, ninv);
+        for (int u = 0; u < NPT; ++u) x[u] = mont_exit(x[u], K, Kq, n, ninv);
         return;
     }
-    modexp_prog<NPT, W>(x, msg, pg, n, ninv, K);
+    modexp_prog<NPT, W>(x, msg, pg, n, ninv, K, Kq);
 }
 template <int NPT>
 __device__ __forceinline__ void encrypt32(const DevInst &P, const ExpProg &pg, const uint32_t (&msg)[NPT],

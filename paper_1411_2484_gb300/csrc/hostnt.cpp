@@ -326,8 +326,9 @@ DevInst derive_inst(const phprng_instance &in, int wide, ExpProg *prog)
     else
         *prog = best_program(in.e);
     if (!wide) {
-        d.ninv = (uint32_t)inv_mod_2_64(in.n);
+        const uint32_t ninv32 = (uint32_t)inv_mod_2_64(in.n);
         d.K = mont_exit_constant(in.n, *prog, 32);
+        d.ninv = ninv32 | (uint64_t)((uint32_t)d.K * ninv32) << 32;
         uint64_t y = in.n + 1;
         d.ybits = (uint32_t)bitlen(y);
         d.yN = (uint32_t)(y << (32 - d.ybits));
@@ -350,6 +351,8 @@ SkipConst derive_skip(uint64_t p, uint64_t a, int npt)
     k.pinv = (uint32_t)inv_mod_2_64(p);
     k.aM = (uint32_t)mulmod(a % p, R, p);
     k.aGM = (uint32_t)mulmod(powmod(a, 32ull * npt, p), R, p);
+    k.aMq = k.aM * k.pinv;
+    k.aGMq = k.aGM * k.pinv;
     for (int j = 0; j < 32; ++j)
         k.lane[j] = (uint32_t)mulmod(powmod(a, (uint64_t)npt * j, p), R, p);
     return k;

@@ -26,7 +26,8 @@ namespace phprng {
 // Derived on the host from {n, e} at creation.
 struct alignas(16) DevInst {
     uint64_t n;      // prime modulus (Eq. 1)
-    uint64_t ninv;   // n^-1 mod 2^32 (32-bit path) or mod 2^64 (64-bit path)
+    uint64_t ninv;   // 32-bit path: n^-1 mod 2^32, and K n^-1 mod 2^32 in the upper word
+                     // (the exit product's constant, mont32c); 64-bit path: n^-1 mod 2^64
     uint64_t K;      // Montgomery exit constant R^(1-alpha) mod n, see mont_exit_constant()
     uint64_t e;      // exponent (its sliding-window program is a separate ExpProg)
     uint64_t V;      // floor(2^84 / yN): reciprocal for the integer-built R (32-bit path)
@@ -46,6 +47,7 @@ struct SkipConst {
     uint32_t p, pinv;      // p, p^-1 mod 2^32
     uint32_t aM;           // a * 2^32 mod p                      (one step, Eq. 9a)
     uint32_t aGM;          // a^(32*NPT) * 2^32 mod p             (one warp group)
+    uint32_t aMq, aGMq;    // aM p^-1, aGM p^-1 mod 2^32 (constant products, mont32c)
     uint32_t lane[32];     // a^(NPT*j) * 2^32 mod p, j = lane    (lane start)
 };
 

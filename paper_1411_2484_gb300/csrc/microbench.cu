@@ -142,7 +142,8 @@ __global__ void __launch_bounds__(256, 2) exp_kernel(const DevInst *inst, const 
 #pragma unroll
     for (int u = 0; u < NPT; ++u) msg[u] = (uint32_t)((w * 977 + lane * 131 + u * 7919) % n);
     for (int r = 0; r < reps; ++r) {
-        modexp_prog<NPT, uint32_t>(x, msg, pg, n, (uint32_t)P.ninv, (uint32_t)P.K);
+        modexp_prog<NPT, uint32_t>(x, msg, pg, n, (uint32_t)P.ninv, (uint32_t)P.K,
+                                   (uint32_t)(P.ninv >> 32));
 #pragma unroll
         for (int u = 0; u < NPT; ++u) {
             msg[u] = x[u];

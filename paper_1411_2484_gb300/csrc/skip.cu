@@ -106,11 +106,11 @@ skip_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, 
         if (!P.wide) {
             uint32_t msg[1] = {(uint32_t)m}, x[1];
             modexp_prog<1, uint32_t>(x, msg, prog[i], (uint32_t)P.n, (uint32_t)P.ninv,
-                                     (uint32_t)P.K);
+                                     (uint32_t)P.K, (uint32_t)(P.ninv >> 32));
             c = x[0];
         } else {
             uint64_t msg[1] = {m}, x[1];
-            modexp_prog<1, uint64_t>(x, msg, prog[i], P.n, P.ninv, P.K);
+            modexp_prog<1, uint64_t>(x, msg, prog[i], P.n, P.ninv, P.K, 0);
             c = x[0];
         }
         st.m[i] = m;

@@ -54,11 +54,12 @@ void h_modexp_many(const uint64_t *m, const uint64_t *e, const uint64_t *n, uint
         DevInst d = derive_inst(in, wide, &pg);
         if (!wide) {
             uint32_t msg[1] = {(uint32_t)m[i]}, x[1];
-            modexp_prog<1, uint32_t>(x, msg, pg, (uint32_t)d.n, (uint32_t)d.ninv, (uint32_t)d.K);
+            modexp_prog<1, uint32_t>(x, msg, pg, (uint32_t)d.n, (uint32_t)d.ninv, (uint32_t)d.K,
+                                     (uint32_t)(d.ninv >> 32));
             out[i] = x[0];
         } else {
             uint64_t msg[1] = {m[i]}, x[1];
-            modexp_prog<1, uint64_t>(x, msg, pg, d.n, d.ninv, d.K);
+            modexp_prog<1, uint64_t>(x, msg, pg, d.n, d.ninv, d.K, 0);
             out[i] = x[0];
         }
     }
@@ -68,14 +69,16 @@ void h_modexp_many(const uint64_t *m, const uint64_t *e, const uint64_t *n, uint
 uint64_t h_skip_step(uint64_t s, uint64_t p, uint64_t a)
 {
     SkipConst k = derive_skip(p, a, 4);
-    return mont32((uint32_t)s, k.aM, k.p, k.pinv);
+    const uint32_t r = mont32c((uint32_t)s, k.aM, k.aMq, k.p);
+    return r == mont32((uint32_t)s, k.aM, k.p, k.pinv) ? r : ~0ull;
 }
 
 // s a^(npt*lane) mod p and s a^(32*npt) mod p from the lane constants.
 uint64_t h_skip_lane(uint64_t s, uint64_t p, uint64_t a, int npt, int lane)
 {
     SkipConst k = derive_skip(p, a, npt);
-    return mont32((uint32_t)s, lane < 32 ? k.lane[lane] : k.aGM, k.p, k.pinv);
+    if (lane == 32) return mont32c((uint32_t)s, k.aGM, k.aGMq, k.p);
+    return mont32((uint32_t)s, k.lane[lane], k.p, k.pinv);
 }
 
 int h_discrete_log(uint64_t p, uint64_t a, uint64_t s, uint64_t *L)
