@@ -148,9 +148,35 @@ def cpu_baseline(inst, per_inst, target_s=12.0):
     t0 = time.perf_counter()
     oracle.generate_many(rows[:count], per_inst, threads=cores, want_c=False)
     dt = time.perf_counter() - t0
+    # one core on a smaller sample (about 2 s)
+    one = max(1, min(len(rows), int(2.0 * count / max(dt, 1e-3) / max(cores, 1))))
+    t0 = time.perf_counter()
+    oracle.generate_many(rows[:one], per_inst, threads=1, want_c=False)
+    dt1 = time.perf_counter() - t0
     return {"value": count * per_inst / dt, "unit": "PRNs/s", "cores": cores, "kind": "oracle",
             "sample": "first %d of the %d instances x %d numbers (R stored), %.1f s"
-                      % (count, len(rows), per_inst, dt)}
+                      % (count, len(rows), per_inst, dt),
+            "value_1core": one * per_inst / dt1, "sample_1core": "first %d instances, %.1f s" % (one, dt1),
+            "cpu_model": cpu_model()}
+
+
+def cpu_model():
+    try:
+        import subprocess
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part", "hardware")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
 
 
 def muls_per_number(e, wide):
