@@ -878,8 +878,8 @@ PH_API int phprng_fourier_test(phprng_ctx *ctx, uint64_t first, uint64_t num_ins
     if (e == cudaSuccess) e = cudaMallocAsync((void **)&Z, batch * per_inst / 2 * sizeof(double2), s);
     std::string err;
     int rc = e == cudaSuccess ? PHPRNG_OK : PHPRNG_ENOMEM;
-    if (rc == PHPRNG_OK) rc = launch_twiddles(tw, log2M, s, &err);
     const double scale2 = 0.5 / std::sqrt((double)M);
+    if (rc == PHPRNG_OK) rc = launch_twiddles(tw, log2M, scale2, s, &err);
     for (uint64_t b0 = 0; b0 < num_inst && rc == PHPRNG_OK; b0 += batch) {
         const uint64_t nb = std::min(batch, num_inst - b0);
         rc = launch_range(ctx, first + b0, nb, per_inst, nullptr, R, nullptr, s, true);   // Eq. 9

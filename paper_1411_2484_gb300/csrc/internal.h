@@ -177,7 +177,7 @@ int launch_pattern_const(const DevInst &P, const ExpProg &pg, const DevInst &Pd,
 // imaginary parts binned into hist[nbins] over [-w, w) (clamped); Z scratch of
 // nseq M/2 double2; coef (nullable) gets nseq M/2 double2.
 uint64_t fourier_twiddle_count(uint32_t lgM);
-int launch_twiddles(double2 *tw, uint32_t lgM, void *stream, std::string *err);
+int launch_twiddles(double2 *tw, uint32_t lgM, double scale2, void *stream, std::string *err);
 int launch_fourier(const double *R, uint64_t nseq, uint32_t lgM, const double2 *tw, double2 *Z,
                    uint32_t nbins, double w, double scale2, uint64_t *hist, double *coef, void *stream,
                    std::string *err);
