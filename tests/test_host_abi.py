@@ -168,3 +168,27 @@ def test_draw_instances_prefix_stable(ph):
 def test_status_strings(ph):
     for s in range(10):
         assert ph.phprng_status_string(s)
+
+
+def test_every_entry_point_rejects_null_handles(ph):
+    """Each call that takes a context, plan, server or output pointer returns
+    PHPRNG_EINVAL when they are NULL (the destroy calls accept NULL and return
+    PHPRNG_OK), without touching a GPU: the checks come before any CUDA call."""
+    import ctypes
+    lib = ph._load()
+    host_only = {"phprng_status_string", "phprng_last_error", "phprng_clock_ns", "phprng_is_prime",
+                 "phprng_validate", "phprng_draw_instances"}
+    for name in ph.EXPORTED:
+        if name in host_only:
+            continue
+        fn = getattr(lib, name)
+        args = []
+        for t in fn.argtypes or []:
+            if t in (ctypes.c_double, ctypes.c_float):
+                args.append(1.0)
+            elif t in (ctypes.c_uint64, ctypes.c_int64, ctypes.c_uint32, ctypes.c_int32, ctypes.c_int):
+                args.append(0)
+            else:
+                args.append(None)
+        want = ph.PHPRNG_OK if name.endswith("_destroy") else ph.PHPRNG_EINVAL
+        assert fn(*args) == want, name
