@@ -174,19 +174,9 @@ PH_HD uint64_t mont_exit(uint64_t x, uint64_t K, uint64_t, uint64_t n, uint64_t 
 // across the NPT independent products (all full products, then all q, then
 // all high halves, then the corrections), so that consecutive multiplies never
 // wait on each other.
-#ifndef PH_MONT_INTERLEAVE
-#define PH_MONT_INTERLEAVE 1
-#endif
-#ifndef PH_SQ_SWITCH
-#define PH_SQ_SWITCH 0
-#endif
-#ifndef PH_PROG_PREFETCH
-#define PH_PROG_PREFETCH 1
-#endif
 template <int NPT>
 PH_HD void mont32_vec(uint32_t (&x)[NPT], const uint32_t (&y)[NPT], uint32_t n, uint32_t ninv)
 {
-#if PH_MONT_INTERLEAVE
     uint32_t lo[NPT], hi[NPT];
 #pragma unroll
     for (int u = 0; u < NPT; ++u) {
@@ -203,10 +193,6 @@ PH_HD void mont32_vec(uint32_t (&x)[NPT], const uint32_t (&y)[NPT], uint32_t n, 
         const uint32_t t = hi[u] - lo[u];
         x[u] = hi[u] < lo[u] ? t + n : t;
     }
-#else
-#pragma unroll
-    for (int u = 0; u < NPT; ++u) x[u] = mont32(x[u], y[u], n, ninv);
-#endif
 }
 
 template <int NPT, typename W>
@@ -280,36 +266,16 @@ PH_HD void modexp_prog(W (&x)[NPT], const W (&m)[NPT], const ExpProg &pg, W n, W
         break;
     }
     const int nent = pg.nent;
-#if PH_PROG_PREFETCH
     int bnext = pg.ent[1];
     for (int k = 1; k < nent; ++k) {
         const int b = bnext;
         bnext = pg.ent[k + 1 < (int)sizeof pg.ent ? k + 1 : k];   // next entry, loaded early
-#else
-    for (int k = 1; k < nent; ++k) {
-        const int b = pg.ent[k];
-#endif
         int sq = b & 63;
-#if PH_SQ_SWITCH
-        for (; sq >= 4; sq -= 4) {
-            mont_sqr_vec<NPT>(x, n, ninv);
-            mont_sqr_vec<NPT>(x, n, ninv);
-            mont_sqr_vec<NPT>(x, n, ninv);
-            mont_sqr_vec<NPT>(x, n, ninv);
-        }
-        switch (sq) {                                   // the remaining 0..3 squarings
-        case 3: mont_sqr_vec<NPT>(x, n, ninv); /* fall through */
-        case 2: mont_sqr_vec<NPT>(x, n, ninv); /* fall through */
-        case 1: mont_sqr_vec<NPT>(x, n, ninv); /* fall through */
-        default: break;
-        }
-#else
         for (; sq >= 2; sq -= 2) {
             mont_sqr_vec<NPT>(x, n, ninv);
             mont_sqr_vec<NPT>(x, n, ninv);
         }
         if (sq) mont_sqr_vec<NPT>(x, n, ninv);
-#endif
         switch (b >> 6) {
         case 0: mont_vec<NPT>(x, m, n, ninv); break;
         case 1: mont_vec<NPT>(x, t3, n, ninv); break;

@@ -25,10 +25,6 @@ namespace phprng {
 
 static constexpr unsigned kFullMask = 0xffffffffu;
 
-#ifndef PH_R_FAST
-#define PH_R_FAST 1
-#endif
-
 // One skip step s -> a s mod p (group = false) or one warp group's advance
 // s -> a^(32 NPT) s mod p (group = true), as a Montgomery product with the
 // constant in Montgomery form.  (A Mersenne fold for p = 2^31 - 1 was measured
@@ -162,11 +158,7 @@ __device__ __forceinline__ void encrypt64(const DevInst &P, const ExpProg &pg, c
 // n, RN(RN(c+1)/RN(n+1)) by the FP64 unit for 64-bit n.
 __device__ __forceinline__ double real_of(const DevInst &P, uint32_t c)
 {
-#if PH_R_FAST
     return real32_fast(c, P.yN, P.ybits, P.aux);
-#else
-    return real32(c, P.yN, P.ybits, P.V);
-#endif
 }
 __device__ __forceinline__ double real_of(const DevInst &P, uint64_t c) { return real64(c, P.n); }
 
