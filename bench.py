@@ -565,9 +565,17 @@ def main():
     for _ in range(steps_e2e):
         ph.phprng_generate(ctx, 0, N, per, None, r_host, None, stream)
     dt = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    # the link's own rate on this host: plain copies of the same bytes into the same buffer
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(4):
+        r_host.copy_(r, non_blocking=True)
+    torch.cuda.synchronize()
+    link = 4 * N * per * 8 / (time.perf_counter() - t0) / 1e9
     e2e = {"value": steps_e2e * N * per * world / dt, "unit": "PRNs/s",
            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": N * per * 8,
-           "steps": steps_e2e}
+           "steps": steps_e2e, "d2h_link_gbs": link,
+           "link_bound_prn_s": link * 1e9 / 8 * world}
 
     ph.phprng_destroy(ctx)
     if rank != 0:
