@@ -478,8 +478,38 @@ def test_argument_errors_on_device(ph, torch):
         with pytest.raises(ph.PhprngError):
             ph.phprng_generate(ctx, 0, 1, 4, None, None)          # no output
         ph.phprng_generate(ctx, 0, 4, 0, None, r)                 # per_inst = 0: no-op
-        assert ph.phprng_get_state(ctx, 0)["pos"] == 0
+        ph.phprng_generate(ctx, 2, 0, 4, None, r)                 # num_inst = 0: no-op
+        ph.phprng_generate(ctx, 4, 0, 4, None, r)                 # empty range at the table's end
+        assert all(ph.phprng_get_state(ctx, i)["pos"] == 0 for i in range(4))
         with pytest.raises(ph.PhprngError):
             ph.phprng_get_state(ctx, 4)
+    finally:
+        ph.phprng_destroy(ctx)
+
+
+def test_maximum_length_single_call(ph, torch):
+    """One stream of 2^32 + 777 numbers in one call (c only, 17 GB): indices
+    past 2^31 and 2^32 inside one launch (split into chunks).  Sampled runs of
+    8 numbers at positions across the call equal the oracle's, each started
+    from the state its own prefix table gives by Eq. 7, and the final state
+    is the oracle's state after 2^32 + 777 steps."""
+    inst = workloads.draw_instances(1, seed=77)
+    n, e, m0, s0 = (int(inst[k][0]) for k in ("n", "e", "m0", "s0"))
+    per = (1 << 32) + 777
+    table = oracle.PrefixTable(P31, A31, 1 << 16)
+    L0 = int(oracle.dlog(P31, A31, [s0])[0])
+    ctx = ph.phprng_create(32, inst, 0)
+    try:
+        c = torch.empty(per, dtype=torch.int32, device="cuda")
+        ph.phprng_generate(ctx, 0, 1, per, c, None)
+        torch.cuda.synchronize()
+        for t in (0, 1, 4095, (1 << 31) - 3, (1 << 31) + 5, (1 << 32) - 5, 1 << 32, per - 8):
+            m_t, s_t = table.state_at(n, m0, L0, t)
+            want, _, _ = oracle.generate(n, e, P31, A31, m_t, s_t, 8)
+            got = c[t:t + 8].cpu().numpy().view(np.uint32).astype(np.uint64)
+            assert np.array_equal(got, want), t
+        st = ph.phprng_get_state(ctx, 0)
+        assert (st["m"], st["s"], st["pos"]) == (*table.state_at(n, m0, L0, per), per)
+        del c
     finally:
         ph.phprng_destroy(ctx)
