@@ -83,6 +83,8 @@ class Oracle:
         lib.or_corr.argtypes = [P64, P64, u64, u64, u64, P64, PD]
         lib.or_serial_hist.restype = None
         lib.or_serial_hist.argtypes = [P64, u64, u64, ctypes.c_int, u64, P64]
+        lib.or_interstream_serial_hist.restype = None
+        lib.or_interstream_serial_hist.argtypes = [P64, P64, u64, u64, ctypes.c_int, u64, P64]
         lib.or_poker_hist.restype = None
         lib.or_poker_hist.argtypes = [P64, u64, u64, P64]
         lib.or_runs_hist.restype = None
@@ -164,6 +166,19 @@ class Oracle:
             hist = np.zeros(B ** D, dtype=np.uint64)
         assert hist.dtype == np.uint64 and hist.size == B ** D and hist.flags.c_contiguous
         self.lib.or_serial_hist(_p64(c), c.size, int(n), int(D), int(B), _p64(hist))
+        return hist
+
+    def interstream_serial_hist(self, c, nmod, D, B, hist=None):
+        """Adds the D-tuples of the streams' numbers in interleaved order (c:
+        uint64[Np, L] instance-major, nmod: the Np moduli) to hist."""
+        c = np.ascontiguousarray(c, dtype=np.uint64)
+        nmod = np.ascontiguousarray(nmod, dtype=np.uint64)
+        Np, L = c.shape
+        assert nmod.size == Np
+        if hist is None:
+            hist = np.zeros(B ** D, dtype=np.uint64)
+        assert hist.dtype == np.uint64 and hist.size == B ** D and hist.flags.c_contiguous
+        self.lib.or_interstream_serial_hist(_p64(c), _p64(nmod), Np, L, int(D), int(B), _p64(hist))
         return hist
 
     def poker_hist(self, c, n, hist=None):
@@ -299,6 +314,10 @@ def generate_many(params, per_inst, threads=1, want_c=True, want_r=True):
 
 def serial_hist(c, n, D, B, hist=None):
     return _default().serial_hist(c, n, D, B, hist)
+
+
+def interstream_serial_hist(c, nmod, D, B, hist=None):
+    return _default().interstream_serial_hist(c, nmod, D, B, hist)
 
 
 def poker_hist(c, n, hist=None):

@@ -291,6 +291,35 @@ void or_serial_hist(const uint64_t *c, uint64_t N, uint64_t n, int D, uint64_t B
     }
 }
 
+/* Interstream serial test (Tests section, interstream correlations): the
+ * numbers of Np streams are taken in the paper's interleaved order -- the
+ * first number of every stream, stream 0 to Np-1, then the second of every
+ * stream, and so on -- and that one sequence S[j Np + a] = R_(j+1) of stream a
+ * is cut into consecutive non-overlapping D-tuples (a remainder of fewer
+ * than D is left out), each adding one to hist[b_1 + B b_2 + ...] with
+ * b = floor(B R).  c holds the streams' ciphertexts instance-major (stream a,
+ * number j at c[a L + j]) and nmod[a] the moduli.
+ * Pinned by: Np = 1 equals or_serial_hist; the sequence built by hand in
+ * Python on small cases; for D = 1 the sum of the streams' own histograms. */
+void or_interstream_serial_hist(const uint64_t *c, const uint64_t *nmod, uint64_t Np, uint64_t L, int D,
+                                uint64_t B, uint64_t *hist)
+{
+    uint64_t total = Np * L;
+    for (uint64_t t = 0; t < total / (uint64_t)D; ++t) {
+        uint64_t idx = 0, scale = 1;
+        for (int d = 0; d < D; ++d) {
+            uint64_t q = t * (uint64_t)D + (uint64_t)d;    /* position in the interleaved sequence */
+            uint64_t a = q % Np, j = q / Np;
+            double R = or_real(c[a * L + j], nmod[a]);
+            uint64_t b = (uint64_t)(R * (double)B);
+            if (b >= B) b = B - 1;
+            idx += b * scale;
+            scale *= B;
+        }
+        hist[idx] += 1;
+    }
+}
+
 /* Poker test (Tests section: five cards, ten denominations).  One stream's
  * numbers in consecutive non-overlapping 5-tuples (a remainder of fewer than
  * five is left out); card k of a hand has denomination floor(10 R_k); the

@@ -47,6 +47,10 @@ MUTANTS = {
     "serial_scale_order": ("scale *= B;", "scale *= B - 1;"),
     "serial_bin_scale": ("uint64_t b = (uint64_t)(R * (double)B);",
                          "uint64_t b = (uint64_t)(R * (double)(B - 1));"),
+    "interstream_transposed": ("double R = or_real(c[a * L + j], nmod[a]);",
+                               "double R = or_real(c[(j * Np + a) % (Np * L)], nmod[a]);"),
+    "interstream_wrong_modulus": ("double R = or_real(c[a * L + j], nmod[a]);",
+                                  "double R = or_real(c[a * L + j], nmod[0]);"),
     "poker_full_house": ("else if (threes && pairs) cat = 4;", "else if (threes) cat = 4;"),
     "poker_denominations": ("int d = (int)(or_real(c[t * 5 + (uint64_t)k], n) * 10.0);",
                             "int d = (int)(or_real(c[t * 5 + (uint64_t)k], n) * 9.0);"),

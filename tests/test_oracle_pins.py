@@ -388,6 +388,49 @@ def test_serial_bin_edges_exact_multiples(oracle_mod):
             assert h[k] == 1 and h[k - 1] == 1
 
 
+# ------------------------------------------------------------ interstream serial test
+def test_interstream_one_stream_is_the_serial_test(oracle_mod):
+    """With Np = 1 the interleaved order is the stream itself."""
+    n = 4294967087
+    c, _, _ = oracle_mod.generate(n, 9, P31, A31, 12345, 77, 3001)
+    for D, B in ((1, 64), (2, 32), (3, 10), (5, 4)):
+        a = oracle_mod.serial_hist(c, n, D, B)
+        b = oracle_mod.interstream_serial_hist(c.reshape(1, -1), [n], D, B)
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("Np,L,D,B", [(2, 7, 2, 4), (3, 5, 2, 3), (5, 8, 3, 4), (7, 9, 4, 2), (4, 6, 1, 8)])
+def test_interstream_against_the_order_built_by_hand(oracle_mod, Np, L, D, B):
+    """The paper's order R_1 of streams 0 .. Np-1, then R_2 of each, and so
+    on, built with Python loops; bins floor(B R) from correctly rounded
+    Python divisions; tuples of D consecutive entries, the tail left out."""
+    rng = random.Random(Np * 100 + L)
+    ns = [4294967087, 4294967291, 2147483659, 3221225473, 4294967029, 2147483693, 3000000019][:Np]
+    c = np.zeros((Np, L), dtype=np.uint64)
+    for a in range(Np):
+        c[a], _, _ = oracle_mod.generate(ns[a], 9, P31, A31, rng.randrange(ns[a]), 1 + a, L)
+    seq = []
+    for j in range(L):
+        for a in range(Np):
+            seq.append(int(B * ((int(c[a, j]) + 1) / (ns[a] + 1))))
+    want = np.zeros(B ** D, dtype=np.uint64)
+    for t in range(len(seq) // D):
+        want[sum(seq[t * D + d] * B ** d for d in range(D))] += 1
+    got = oracle_mod.interstream_serial_hist(c, ns, D, B)
+    assert np.array_equal(got, want)
+
+
+def test_interstream_1d_is_the_sum_of_the_streams(oracle_mod):
+    """Interleaving does not change a one-dimensional histogram."""
+    ns = [4294967087, 4294967291, 2147483659]
+    c = np.stack([oracle_mod.generate(n, 17, P31, A31, 99 + k, 3 + k, 2000)[0] for k, n in enumerate(ns)])
+    h = oracle_mod.interstream_serial_hist(c, ns, 1, 1 << 10)
+    ref = np.zeros(1 << 10, dtype=np.uint64)
+    for k, n in enumerate(ns):
+        oracle_mod.serial_hist(c[k], n, 1, 1 << 10, ref)
+    assert np.array_equal(h, ref)
+
+
 # ------------------------------------------------------------ poker test
 def test_poker_hands_from_chosen_denominations(oracle_mod):
     """n + 1 = 10 t makes floor(10 (c+1)/(n+1)) = d for c = d t (d < 10):
