@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=64)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--modes", default="fused,serial,small_e,pattern,fourier,wide64,batched,served",
+    ap.add_argument("--modes", default="fused,serial,interstream,small_e,pattern,fourier,wide64,batched,served",
                     help="comma-separated extra measurements after the headline, or 'none'")
     return ap.parse_args()
 
@@ -275,6 +275,23 @@ def mode_pattern(ph, torch, stream, L0=128):
     return {"value": points / ms * 1e3, "unit": "points/s", "ms": ms,
             "exponentiations_per_s": 2 * points / ms * 1e3,
             "workload": "paper's pattern instance, D = 3, L0 = 2^7, 2^24 volumes (2^38 points)",
+            "chi2_z": (chi2 - dof) / (2 * dof) ** 0.5}
+
+
+def mode_interstream(ph, torch, ctx, N, per, stream):
+    """The paper's interstream ordering (number 1 of every stream, then
+    number 2 of every stream, ...) over the plain workload's 65,536 streams,
+    pairs of that sequence into 2^20 bins."""
+    D, B = 2, 1 << 10
+    hist = torch.zeros(B ** D, dtype=torch.int64, device="cuda")
+    ms = timed(torch, stream, lambda: ph.phprng_interstream_serial_test(ctx, 0, N, per, D, B, hist, stream), 4)
+    torch.cuda.synchronize()
+    got = hist.cpu().numpy().astype(np.float64)
+    expect = got.sum() / B ** D
+    chi2 = float(((got - expect) ** 2).sum() / expect)
+    dof = B ** D - 1
+    return {"value": N * per / ms * 1e3, "unit": "PRNs/s", "ms_per_call": ms,
+            "workload": "plain32 65,536 streams x 4,096, interleaved order, pairs into 2^20 bins",
             "chi2_z": (chi2 - dof) / (2 * dof) ** 0.5}
 
 
@@ -608,6 +625,7 @@ def main():
         wanted = [] if args.modes == "none" else args.modes.split(",")
         for name, fn in (("fused", lambda: mode_fused(ph, torch, ctx2, N, per, stream, 8)),
                          ("serial", lambda: mode_serial(ph, torch, ctx2, N, per, stream)),
+                         ("interstream", lambda: mode_interstream(ph, torch, ctx2, N, per, stream)),
                          ("small_e", lambda: mode_small_e(ph, torch, stream, PEAK_TMULS)),
                          ("pattern", lambda: mode_pattern(ph, torch, stream)),
                          ("fourier", lambda: mode_fourier(ph, torch, stream)),
@@ -617,7 +635,7 @@ def main():
             if name not in wanted:
                 continue
             try:
-                if name in ("fused", "serial"):
+                if name in ("fused", "serial", "interstream"):
                     ctx2 = ph.phprng_create(32, inst, ph.PHPRNG_REQUIRE_SAFE_PRIME, stream)
                     try:
                         modes[name] = fn()

@@ -234,6 +234,21 @@ int phprng_collision_test(phprng_ctx *ctx, uint64_t first, uint64_t num_inst, ui
 int phprng_runs_test(phprng_ctx *ctx, uint64_t first, uint64_t num_inst, uint64_t per_inst,
                      int lmax, uint64_t *hist, void *cuda_stream);
 
+/* Interstream serial test (Tests section, interstream correlations): the
+ * per_inst numbers that each instance of [first, first + num_inst) draws in
+ * this call (Eq. 9) are taken in the paper's interleaved order -- number 1 of
+ * every instance in order, then number 2 of every instance, and so on -- and
+ * that sequence of num_inst * per_inst numbers is cut into consecutive
+ * non-overlapping D-tuples (the last num_inst * per_inst mod D numbers are left
+ * out); each tuple adds one to hist[b_1 + B b_2 + ... + B^(D-1) b_D], b =
+ * floor(B R).  Limits as phprng_serial_test: 1 <= D <= 8, B a power of two up
+ * to 2^20 or at most 2^16, B^D <= 2^24, 32-bit instances.  hist: device
+ * memory, B^D uint64 counters, added to.  Streams advance by per_inst.
+ * Asynchronous on cuda_stream; scratch of about 2^25 numbers (ciphertexts and
+ * bins) from the stream-ordered allocator. */
+int phprng_interstream_serial_test(phprng_ctx *ctx, uint64_t first, uint64_t num_inst, uint64_t per_inst,
+                                   int D, uint32_t B, uint64_t *hist, void *cuda_stream);
+
 /* Fourier test (Tests section): every instance of [first, first + num_inst)
  * draws per_inst numbers R (Eq. 9), cut into per_inst / M consecutive
  * sequences of M = 2^log2M; for each sequence x_j = R_j - 1/2 and

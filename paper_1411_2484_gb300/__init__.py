@@ -36,7 +36,7 @@ PHPRNG_ALLOW_SHARED_N = 0x2
 EXPORTED = [
     "phprng_create", "phprng_create_seeded", "phprng_destroy", "phprng_last_error",
     "phprng_status_string", "phprng_generate", "phprng_skip", "phprng_seek", "phprng_serial_test", "phprng_poker_test", "phprng_runs_test", "phprng_collision_test",
-    "phprng_fourier_test", "phprng_pattern", "phprng_pattern_const",
+    "phprng_fourier_test", "phprng_interstream_serial_test", "phprng_pattern", "phprng_pattern_const",
     "phprng_get_state", "phprng_set_state",
     "phprng_is_prime", "phprng_validate", "phprng_draw_instances", "phprng_microbench",
     "phprng_plan_create", "phprng_plan_launch", "phprng_plan_launch_graph",
@@ -140,6 +140,7 @@ def _load():
         lib.phprng_runs_test.argtypes = [vp, u64, u64, u64, i32, vp, vp]
         u32 = ctypes.c_uint32
         lib.phprng_collision_test.argtypes = [vp, u64, u64, u64, u32, u32, u32, vp, vp]
+        lib.phprng_interstream_serial_test.argtypes = [vp, u64, u64, u64, i32, u32, vp, vp]
         lib.phprng_fourier_test.argtypes = [vp, u64, u64, u64, u32, u32, ctypes.c_double, vp, vp, vp]
         lib.phprng_pattern.argtypes = [ctypes.POINTER(phprng_instance), u64, u64, i32,
                                        ctypes.c_uint32, vp, vp]
@@ -296,6 +297,14 @@ def phprng_runs_test(ctx, first, num_inst, per_inst, lmax, hist, stream=None):
     the device counters `hist` (2*lmax uint64); streams advance by per_inst."""
     _check(_load().phprng_runs_test(ctx, int(first), int(num_inst), int(per_inst), int(lmax),
                                     _ptr(hist), _stream(stream)), ctx)
+
+
+def phprng_interstream_serial_test(ctx, first, num_inst, per_inst, D, B, hist, stream=None):
+    """Adds the D-tuples of the call's numbers in interleaved order (number 1
+    of every instance, then number 2 of every instance, ...) to the device
+    counters `hist` (B**D uint64); streams advance by per_inst."""
+    _check(_load().phprng_interstream_serial_test(ctx, int(first), int(num_inst), int(per_inst), int(D),
+                                                  int(B), _ptr(hist), _stream(stream)), ctx)
 
 
 def phprng_fourier_test(ctx, first, num_inst, per_inst, log2M, nbins, w, hist, coef=None,

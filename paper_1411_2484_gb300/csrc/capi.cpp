@@ -846,6 +846,62 @@ PH_API int phprng_collision_test(phprng_ctx *ctx, uint64_t first, uint64_t num_i
                          launch);
 }
 
+PH_API int phprng_interstream_serial_test(phprng_ctx *ctx, uint64_t first, uint64_t num_inst,
+                                         uint64_t per_inst, int D, uint32_t B, uint64_t *hist,
+                                         void *cuda_stream)
+{
+    if (!ctx) return fail(nullptr, PHPRNG_EINVAL, "phprng_interstream_serial_test: ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    const char *W = "phprng_interstream_serial_test: ";
+    if (ctx->serving) return fail(ctx, PHPRNG_EINVAL, std::string(W) + "a server owns the context");
+    if (first > ctx->count || num_inst > ctx->count - first)
+        return fail(ctx, PHPRNG_EINVAL, std::string(W) + "instance range outside the table");
+    if (D < 1 || D > 8) return fail(ctx, PHPRNG_EINVAL, std::string(W) + "D must be 1..8");
+    const bool pow2 = B && (B & (B - 1)) == 0;
+    if (B < 1 || (pow2 ? B > (1u << 20) : B > (1u << 16)))
+        return fail(ctx, PHPRNG_EINVAL, std::string(W) + "B must be a power of two up to 2^20 or at most 2^16");
+    uint64_t bins = 1;
+    for (int d = 0; d < D; ++d) bins *= B;
+    if (bins > (1ull << 24)) return fail(ctx, PHPRNG_EINVAL, std::string(W) + "B^D exceeds 2^24");
+    if (!hist || (uintptr_t)hist % 8) return fail(ctx, PHPRNG_EINVAL, std::string(W) + "hist NULL or misaligned");
+    if (num_inst == 0 || per_inst == 0) return PHPRNG_OK;
+    for (uint64_t i = first; i < first + num_inst; ++i)
+        if (ctx->wide[i]) return fail(ctx, PHPRNG_EINVAL, std::string(W) + "defined for 32-bit moduli only");
+    CU(ctx, cudaSetDevice(ctx->device));
+    if (pointer_kind(hist) != 1) return fail(ctx, PHPRNG_EINVAL, std::string(W) + "hist must be device memory");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    // chunks of Lch numbers per stream, a multiple of D so that no tuple of the
+    // interleaved sequence spans two chunks; about 2^25 numbers per chunk
+    uint64_t Lch = (1ull << 25) / num_inst / (uint64_t)D * (uint64_t)D;
+    if (Lch < (uint64_t)D) Lch = (uint64_t)D;
+    if (Lch > kInterMaxChunk) Lch = kInterMaxChunk / (uint64_t)D * (uint64_t)D;
+    if (Lch > per_inst) Lch = per_inst;
+    const int c64 = ctx->width != 32;                   // c's element size as launch_range writes it
+    void *c = nullptr;
+    uint32_t *binsT = nullptr;
+    cudaError_t e = cudaMallocAsync(&c, num_inst * Lch * (c64 ? 8 : 4), s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&binsT, num_inst * Lch * 4, s);
+    std::string err;
+    int rc = e == cudaSuccess ? PHPRNG_OK : PHPRNG_ENOMEM;
+    for (uint64_t j0 = 0; j0 < per_inst && rc == PHPRNG_OK; j0 += Lch) {
+        const uint64_t L = std::min(Lch, per_inst - j0);
+        rc = launch_range(ctx, first, num_inst, L, c, nullptr, nullptr, s, true);   // Eq. 9
+        if (rc != PHPRNG_OK) break;
+        rc = launch_interstream(ctx->d_inst, first, num_inst, L, c, c64, D, B, binsT,
+                                (unsigned long long *)hist, s, &err);
+        if (rc == PHPRNG_OK)
+            for (uint64_t i = first; i < first + num_inst; ++i) ctx->pos_host[i] += L;
+    }
+    if (c) cudaFreeAsync(c, s);
+    if (binsT) cudaFreeAsync(binsT, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, PHPRNG_ENOMEM, std::string(W) + "scratch allocation failed");
+    }
+    if (rc != PHPRNG_OK) return err.empty() ? rc : fail(ctx, rc, std::string(W) + err);
+    return PHPRNG_OK;
+}
+
 PH_API int phprng_fourier_test(phprng_ctx *ctx, uint64_t first, uint64_t num_inst, uint64_t per_inst,
                                uint32_t log2M, uint32_t nbins, double w, uint64_t *hist, double *coef_out,
                                void *cuda_stream)

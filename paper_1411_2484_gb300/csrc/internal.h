@@ -181,6 +181,13 @@ int launch_twiddles(double2 *tw, uint32_t lgM, double scale2, void *stream, std:
 int launch_fourier(const double *R, uint64_t nseq, uint32_t lgM, const double2 *tw, double2 *Z,
                    uint32_t nbins, double w, double scale2, uint64_t *hist, double *coef, void *stream,
                    std::string *err);
+// Interstream serial test (serial.cu): bins of a chunk c (Np streams x L
+// numbers, instance-major) into binsT in interleaved order, then its
+// D-tuples counted into hist (B^D counters).
+static constexpr uint64_t kInterMaxChunk = 65535ull * 32;   // numbers per stream and chunk
+int launch_interstream(const DevInst *inst, uint64_t first, uint64_t Np, uint64_t L, const void *c, int c64,
+                       int D, uint32_t B, uint32_t *binsT, unsigned long long *hist, void *stream,
+                       std::string *err);
 // Collision-test consumer (serial.cu): segments of S numbers into B bins,
 // collision counts into hist[H]; a persistent grid of `warps` warps (from
 // collision_grid_warps()), each with a zeroed bitmap of ceil(B/32) words.

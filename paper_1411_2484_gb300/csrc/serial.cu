@@ -304,6 +304,103 @@ int launch_runs(const GenArgs &a, int lmax, unsigned long long *hist, void *stre
     return PHPRNG_OK;
 }
 
+// Interstream serial test, step 1: bins floor(B R) of a chunk of c (Np
+// streams x L numbers, instance-major; uint64 elements when c64, as a
+// mixed-width context writes them) written in the paper's interleaved
+// order, binsT[j Np + a] for stream a, number j.  A block takes a tile of 32
+// streams x 32 numbers through shared memory so that the reads run along a
+// stream and the writes along the streams.
+__global__ void __launch_bounds__(256)
+inter_bins_kernel(const DevInst *__restrict__ inst, uint64_t first, uint64_t Np, uint64_t L,
+                  const void *__restrict__ c, int c64, uint32_t B, uint32_t *__restrict__ binsT)
+{
+    __shared__ uint32_t tile[32][33];
+    const uint32_t tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const uint64_t a0 = (uint64_t)blockIdx.x * 32, j0 = (uint64_t)blockIdx.y * 32;
+    for (uint32_t r = ty; r < 32; r += 8) {
+        const uint64_t a = a0 + r, j = j0 + tx;
+        if (a < Np) {
+            const DevInst P = inst[first + a];
+            const uint32_t rB = (uint32_t)(((uint64_t)B << 32) / P.yN);
+            if (j < L) {
+                const uint32_t cv = c64 ? (uint32_t)static_cast<const uint64_t *>(c)[a * L + j]
+                                        : static_cast<const uint32_t *>(c)[a * L + j];
+                tile[r][tx] = serial_bin(cv, P.yN, P.ybits, rB, B);
+            }
+        }
+    }
+    __syncthreads();
+    for (uint32_t r = ty; r < 32; r += 8) {
+        const uint64_t j = j0 + r, a = a0 + tx;
+        if (j < L && a < Np) binsT[j * Np + a] = tile[tx][r];
+    }
+}
+
+// Step 2: consecutive non-overlapping D-tuples of the interleaved bins, one
+// count each (per-block shared counters when B^D is at most kInterSmemBins).
+static constexpr uint32_t kInterSmemBins = 8192;
+
+template <bool SMEM>
+__global__ void __launch_bounds__(256)
+inter_hist_kernel(const uint32_t *__restrict__ binsT, uint64_t ntup, int D, uint32_t B, uint32_t nbins,
+                  unsigned long long *__restrict__ hist)
+{
+    __shared__ uint32_t sh[SMEM ? kInterSmemBins : 1];
+    if (SMEM) {
+        for (uint32_t b = threadIdx.x; b < nbins; b += blockDim.x) sh[b] = 0;
+        __syncthreads();
+    }
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ntup;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t idx = 0, scale = 1;
+        for (int d = 0; d < D; ++d) {
+            idx += binsT[t * (uint64_t)D + (uint64_t)d] * scale;
+            scale *= B;
+        }
+        if (SMEM) atomicAdd(sh + idx, 1u);
+        else atomicAdd(hist + idx, 1ull);
+    }
+    if (SMEM) {
+        __syncthreads();
+        for (uint32_t b = threadIdx.x; b < nbins; b += blockDim.x)
+            if (sh[b]) atomicAdd(hist + b, (unsigned long long)sh[b]);
+    }
+}
+
+int launch_interstream(const DevInst *inst, uint64_t first, uint64_t Np, uint64_t L, const void *c, int c64,
+                       int D, uint32_t B, uint32_t *binsT, unsigned long long *hist, void *stream,
+                       std::string *err)
+{
+    if (Np == 0 || L == 0) return PHPRNG_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (L > kInterMaxChunk) {                      // grid.y limit: 65,535 tiles of 32
+        *err = "interstream chunk longer than 65,535 x 32 numbers";
+        return PHPRNG_EINVAL;
+    }
+    const dim3 grid((unsigned)((Np + 31) / 32), (unsigned)((L + 31) / 32));
+    inter_bins_kernel<<<grid, 256, 0, s>>>(inst, first, Np, L, c, c64, B, binsT);
+    uint32_t nbins = 1;
+    for (int d = 0; d < D; ++d) nbins *= B;
+    const uint64_t ntup = Np * L / (uint64_t)D;
+    if (ntup) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const uint64_t want = (ntup + 255) / 256, cap = (uint64_t)sms * 8;
+        const unsigned blocks = (unsigned)(want < cap ? want : cap);
+        if (nbins <= kInterSmemBins)
+            inter_hist_kernel<true><<<blocks, 256, 0, s>>>(binsT, ntup, D, B, nbins, hist);
+        else
+            inter_hist_kernel<false><<<blocks, 256, 0, s>>>(binsT, ntup, D, B, nbins, hist);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        *err = std::string("interstream kernels: ") + cudaGetErrorString(e);
+        return PHPRNG_ECUDA;
+    }
+    return PHPRNG_OK;
+}
+
 int launch_serial(const GenArgs &a, int D, uint32_t B, unsigned long long *hist, void *stream,
                   std::string *err)
 {

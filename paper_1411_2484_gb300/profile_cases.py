@@ -10,6 +10,8 @@ CASE is one of
   pattern3  the paper's pattern instance (n = 4294967087, p = 2^31-1,
             e = 9), D = 3, 2^24 volumes, L0 = 4 (2^33 points)       pattern_kernel
   wide64    4,096 64-bit instances x 4,096 numbers, R (128 MiB)      gen64_kernel
+  inter2    plain32's instances, interleaved order (number 1 of every
+            stream, then number 2 ...), pairs into 2^20 bins          inter_*_kernel
   fourier20 plain32's first 256 instances x 2^20 numbers, Fourier test
             over sequences of M = 2^20 (the paper's), 8,192 bins       fft_*_kernel
   batched   2,000 instances (80 % 32-bit), lengths log-uniform in
@@ -29,7 +31,7 @@ from paper_1411_2484_gb300 import workloads
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["plain32", "fused32", "small_e", "serial2", "pattern3", "wide64", "batched", "fourier20"])
+    ap.add_argument("case", choices=["plain32", "fused32", "small_e", "serial2", "pattern3", "wide64", "batched", "fourier20", "inter2"])
     ap.add_argument("--repeat", type=int, default=3)
     args = ap.parse_args()
     s = torch.cuda.current_stream()
@@ -55,6 +57,13 @@ def main():
         else:
             sb = torch.empty(N * ph.STATS_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
             run = lambda: ph.phprng_generate(ctx, 0, N, per, None, None, sb, s)
+        numbers = N * per
+    elif args.case == "inter2":
+        inst = workloads.workload_instances("plain32_65536x4096x64")
+        N, per = 65536, 4096
+        ctx = ph.phprng_create(32, inst, ph.PHPRNG_REQUIRE_SAFE_PRIME, s)
+        hist = torch.zeros(1 << 20, dtype=torch.int64, device="cuda")
+        run = lambda: ph.phprng_interstream_serial_test(ctx, 0, N, per, 2, 1 << 10, hist, s)
         numbers = N * per
     elif args.case == "fourier20":
         inst = workloads.workload_instances("plain32_65536x4096x64", 256)

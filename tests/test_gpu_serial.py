@@ -223,3 +223,76 @@ def test_collision_mean_at_scale(ph, torch):
         assert abs(mean - expect) < 5 * np.sqrt(expect / segs), (mean, expect)
     finally:
         ph.phprng_destroy(ctx)
+
+
+def _interstream_oracle(rows, per, D, B):
+    c, _, st, _ = oracle.generate_many(rows, per, threads=THREADS, want_r=False)
+    return oracle.interstream_serial_hist(c, rows[:, 0], D, B), st
+
+
+@pytest.mark.parametrize("Np,per,D,B,e", [(1, 1000, 2, 32, None), (3, 1001, 2, 16, None), (37, 777, 3, 10, None),
+                                          (64, 513, 5, 4, None), (5, 2000, 1, 1 << 20, None),
+                                          (1100, 40, 2, 1 << 10, None), (4, 9_000_001, 3, 16, 9)])
+def test_interstream_matches_oracle(ph, torch, Np, per, D, B, e):
+    """Interleaved order over Np streams: ragged tails (Np per mod D != 0),
+    shared-memory and global counters, and 4 x 9,000,001 numbers at D = 3 in
+    four chunks of about 2^25 numbers (a multiple of D per stream, so no
+    tuple spans two chunks); two calls accumulate; the streams continue as
+    after phprng_generate."""
+    inst = workloads.draw_instances(Np, seed=500 + Np, exponent=e)
+    ctx = ph.phprng_create(32, inst, 0)
+    try:
+        rows = workloads.instance_rows(inst).copy()
+        hist = torch.zeros(B ** D, dtype=torch.int64, device="cuda")
+        want = np.zeros(B ** D, dtype=np.uint64)
+        for call in range(2):
+            ph.phprng_interstream_serial_test(ctx, 0, Np, per, D, B, hist)
+            h, st = _interstream_oracle(rows, per, D, B)
+            want += h
+            rows[:, 4:6] = st
+        torch.cuda.synchronize()
+        assert np.array_equal(hist.cpu().numpy().view(np.uint64), want)
+        s = ph.phprng_get_state(ctx, Np - 1)
+        assert (s["m"], s["s"], s["pos"]) == (int(rows[-1, 4]), int(rows[-1, 5]), 2 * per)
+    finally:
+        ph.phprng_destroy(ctx)
+
+
+def test_interstream_large_chunked_and_mixed_context(ph, torch):
+    """A sub-range of 32-bit instances in a mixed-width context (ciphertexts
+    kept as 64-bit words) over more than one chunk; 64-bit instances are
+    rejected."""
+    i32 = workloads.draw_instances(40, seed=511)
+    i64 = workloads.draw_instances(3, width=64, seed=512)
+    inst = workloads.concat_instances(i32, i64)
+    ctx = ph.phprng_create(0, inst, 0)
+    try:
+        hist = torch.zeros(1 << 10, dtype=torch.int64, device="cuda")
+        per = 900_001
+        ph.phprng_interstream_serial_test(ctx, 1, 39, per, 2, 32, hist)
+        want, _ = _interstream_oracle(workloads.instance_rows(i32)[1:], per, 2, 32)
+        torch.cuda.synchronize()
+        assert np.array_equal(hist.cpu().numpy().view(np.uint64), want)
+        with pytest.raises(ph.PhprngError):
+            ph.phprng_interstream_serial_test(ctx, 38, 3, 64, 2, 32, hist)
+    finally:
+        ph.phprng_destroy(ctx)
+
+
+def test_interstream_paper_scale_chi_square(ph, torch):
+    """32,768 streams (one of the paper's groupings) x 8,192 numbers with
+    e = 9, pairs of the interleaved sequence into 2^20 bins: every tuple
+    counted, chi-square unremarkable (|z| < 6)."""
+    inst = workloads.draw_instances(32768, seed=513, exponent=9)
+    ctx = ph.phprng_create(32, inst, 0)
+    try:
+        hist = torch.zeros(1 << 20, dtype=torch.int64, device="cuda")
+        ph.phprng_interstream_serial_test(ctx, 0, 32768, 8192, 2, 1 << 10, hist)
+        torch.cuda.synchronize()
+        got = hist.cpu().numpy().astype(np.float64)
+        assert got.sum() == 32768 * 8192 // 2
+        expect = got.sum() / got.size
+        z = (((got - expect) ** 2).sum() / expect - (got.size - 1)) / (2 * (got.size - 1)) ** 0.5
+        assert abs(z) < 6, z
+    finally:
+        ph.phprng_destroy(ctx)
