@@ -146,9 +146,19 @@ gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
                 const uint64_t my0 = g0 + (uint64_t)NPT * lane;
                 sig_last = sig;
                 g_last = g0;
-                messages32<NPT>(P, sk, lane, my0, len, M, sig, sv, msg);
+                // full groups skip the per-number bounds checks (fewer
+                // instructions and registers; the LIGHT loop keeps one path,
+                // where the split cost a spill)
+                const bool full = g0 + G <= len;             // warp-uniform
+                if (full)
+                    messages32<NPT, true>(P, sk, lane, my0, len, M, sig, sv, msg);
+                else
+                    messages32<NPT>(P, sk, lane, my0, len, M, sig, sv, msg);
                 encrypt32<NPT>(P, pg, msg, x);
-                store_group<NPT, CT, uint32_t>(P, cdst, rdst, my0, len, vec_ok, x);
+                if (full)
+                    store_group<NPT, CT, uint32_t, true>(P, cdst, rdst, my0, len, vec_ok, x);
+                else
+                    store_group<NPT, CT, uint32_t>(P, cdst, rdst, my0, len, vec_ok, x);
             }
         }
         if (wb) write_state_after<NPT, uint32_t, uint32_t>(st, sk, i, lane, g_last, len, pos_after, M,
@@ -157,8 +167,12 @@ gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
     for (uint64_t g0 = 0; g0 < len; g0 += G) {
         uint32_t sv[NPT], msg[NPT], x[NPT];
         const uint64_t my0 = g0 + (uint64_t)NPT * lane;
+        const bool full = g0 + G <= len;                 // block-uniform (lockstep)
         if (active) {
-            messages32<NPT>(P, sk, lane, my0, len, M, sig, sv, msg);
+            if (full)
+                messages32<NPT, true>(P, sk, lane, my0, len, M, sig, sv, msg);
+            else
+                messages32<NPT>(P, sk, lane, my0, len, M, sig, sv, msg);
             if (wb) write_ms_if_last<NPT, uint32_t>(st, i, lane, g0, len, pos_after, sv, msg);
             encrypt32<NPT>(P, pg, msg, x);
             store_group<NPT, CT, uint32_t>(P, cdst, rdst, my0, len, vec_ok, x);
@@ -167,14 +181,25 @@ gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
         if (STATS) {
             uint32_t *cb = smem + ((int)((g0 / G) & 1) * W + warp) * (32 * NPT);
             if (active) {
+                if (full) {
 #pragma unroll
-                for (int u = 0; u < NPT; ++u) {
-                    cb[NPT * lane + u] = x[u];
-                    if (my0 + u < per_inst) {
+                    for (int u = 0; u < NPT; ++u) {
+                        cb[NPT * lane + u] = x[u];
                         const uint64_t v = (uint64_t)x[u] + 1;
                         X += v;
                         Y += (u128)(v * v);
                         atomicAdd(&hist[hist_bin256_int(x[u], P.yN, P.ybits, binr)], 1u);
+                    }
+                } else {
+#pragma unroll
+                    for (int u = 0; u < NPT; ++u) {
+                        cb[NPT * lane + u] = x[u];
+                        if (my0 + u < per_inst) {
+                            const uint64_t v = (uint64_t)x[u] + 1;
+                            X += v;
+                            Y += (u128)(v * v);
+                            atomicAdd(&hist[hist_bin256_int(x[u], P.yN, P.ybits, binr)], 1u);
+                        }
                     }
                 }
                 if (edge && ((warp == W - 1 && has_next) || (warp == 0 && blockIdx.x > 0))) {
@@ -191,7 +216,7 @@ gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
                 const uint32_t *cn = cb + 32 * NPT;              // next warp, same buffer
 #pragma unroll
                 for (int u = 0; u < NPT; ++u)
-                    if (my0 + u < per_inst)
+                    if (full || my0 + u < per_inst)
                         Z += (u128)(((uint64_t)x[u] + 1) * ((uint64_t)cn[NPT * lane + u] + 1));
             }
         }

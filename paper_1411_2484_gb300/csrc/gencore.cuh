@@ -60,7 +60,9 @@ __device__ __forceinline__ uint64_t chunk_message(const SplitArgs &sp, uint64_t 
     return addmod64(h[0], S, n);
 }
 
-template <int NPT>
+// FULL: the whole warp group lies inside the run (no number past len), so
+// the per-number bounds checks are left out.
+template <int NPT, bool FULL = false>
 __device__ __forceinline__ void messages32(const DevInst &P, const SkipConst &sk, int lane,
                                            uint64_t my0, uint64_t len, uint32_t &M, uint32_t &sig,
                                            uint32_t (&sv)[NPT], uint32_t (&msg)[NPT])
@@ -71,7 +73,7 @@ __device__ __forceinline__ void messages32(const DevInst &P, const SkipConst &sk
     for (int u = 0; u < NPT; ++u) {
         t = skip_step(sk, t, false);                             // Eq. 9a
         sv[u] = t;
-        if (my0 + u < len) S = addmod32(S, t, n);
+        if (FULL || my0 + u < len) S = addmod32(S, t, n);
     }
     uint32_t incl = S;
 #pragma unroll
@@ -164,12 +166,12 @@ __device__ __forceinline__ double real_of(const DevInst &P, uint64_t c) { return
 
 // Stores a lane's NPT outputs (16-byte vectors when the whole run of the
 // lane is inside `len` and vec_ok says the addresses are aligned).
-template <int NPT, typename CT, typename XT>
+template <int NPT, typename CT, typename XT, bool FULL = false>
 __device__ __forceinline__ void store_group(const DevInst &P, CT *c_dst, double *r_dst,
                                             uint64_t my0, uint64_t len, bool vec_ok,
                                             const XT (&x)[NPT])
 {
-    const bool full = my0 + NPT <= len;
+    const bool full = FULL || my0 + NPT <= len;
     if (c_dst) {
         CT *dst = c_dst + my0;
         if (full && vec_ok && sizeof(CT) == 4 && NPT % 4 == 0) {
