@@ -23,6 +23,10 @@ namespace phprng {
 static constexpr int kNPT = PH_NPT32;     // numbers per lane per group (32-bit path)
 static constexpr int kNPT64 = PH_NPT64;   // numbers per lane per group (64-bit path)
 static constexpr int kWarpsPerBlock = PH_WPB;
+#ifndef PH_WPB_HEAVY
+#define PH_WPB_HEAVY 10
+#endif
+static constexpr int kWarpsHeavy = PH_WPB_HEAVY;   // warps per block of the plain heavy instantiation (90 registers: 20 warps per SM)
 static constexpr unsigned kFull = kFullMask;
 
 int gen_npt(int wide) { return wide ? kNPT64 : kNPT; }
@@ -64,9 +68,8 @@ __device__ __forceinline__ double u128d(u128 v) { return u128_to_double((uint64_
 // sums, scan, R, stores) dominates, and three resident blocks per SM with
 // the stores of group g placed after group g+1's messages hide it better;
 // for long programs two blocks with in-order stores are faster.
-template <int NPT, typename CT, bool STATS, bool LIGHT>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32,
-                                  STATS ? PH_MINB_STATS : LIGHT ? PH_MINB_LIGHT : PH_MINB32)
+template <int NPT, typename CT, bool STATS, bool LIGHT, int WB>
+__global__ void __launch_bounds__(WB * 32, STATS ? PH_MINB_STATS : LIGHT ? PH_MINB_LIGHT : PH_MINB32)
 gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, DevState st,
              SkipConst sk, uint64_t first, uint64_t num, uint64_t per_inst,
              CT *__restrict__ c_out, double *__restrict__ r_out, int vec_ok,
@@ -74,7 +77,7 @@ gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
              const uint32_t *__restrict__ order, SplitArgs sp)
 {
     extern __shared__ uint32_t smem[];   // STATS: cbuf[2][W][32*NPT] then hist[W][256]
-    constexpr int W = kWarpsPerBlock;
+    constexpr int W = WB;
     constexpr uint64_t G = 32 * NPT;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint64_t w = (uint64_t)blockIdx.x * W + warp;
@@ -391,15 +394,16 @@ int launch_gen32(const GenArgs &a, void *stream, std::string *err)
         return PHPRNG_EINVAL;
     }
     const uint64_t blocks = ((a.num << a.sp.log2K) + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    const uint64_t blocks_heavy = ((a.num << a.sp.log2K) + kWarpsHeavy - 1) / kWarpsHeavy;
     cudaStream_t s = (cudaStream_t)stream;
     if (a.stats) {
         const size_t smem = (2 * kWarpsPerBlock * 32 * kNPT + kWarpsPerBlock * 256) * sizeof(uint32_t);
         if (a.c_is_64)
-            gen32_kernel<kNPT, uint64_t, true, false><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(
+            gen32_kernel<kNPT, uint64_t, true, false, kWarpsPerBlock><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(
                 a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, (uint64_t *)a.c_out, a.r_out,
                 a.vec_ok, a.stats, a.edge, nullptr, a.sp);
         else
-            gen32_kernel<kNPT, uint32_t, true, false><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(
+            gen32_kernel<kNPT, uint32_t, true, false, kWarpsPerBlock><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(
                 a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, (uint32_t *)a.c_out, a.r_out,
                 a.vec_ok, a.stats, a.edge, nullptr, a.sp);
         int rc = check_launch(err, "gen32_kernel (statistics) launch");
@@ -408,16 +412,16 @@ int launch_gen32(const GenArgs &a, void *stream, std::string *err)
             a.inst, a.edge, a.first, a.num, a.per_inst, blocks, a.stats);
         return check_launch(err, "stats_edge_kernel launch");
     }
-#define PH_GEN32_PLAIN(CTY, LT)                                                                     \
-    gen32_kernel<kNPT, CTY, false, LT><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(            \
+#define PH_GEN32_PLAIN(CTY, LT, WB, NB)                                                             \
+    gen32_kernel<kNPT, CTY, false, LT, WB><<<(unsigned)(NB), WB * 32, 0, s>>>(                      \
         a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, (CTY *)a.c_out, a.r_out, a.vec_ok, \
         nullptr, nullptr, a.order, a.sp)
     if (a.c_is_64) {
-        if (a.light) PH_GEN32_PLAIN(uint64_t, true);
-        else PH_GEN32_PLAIN(uint64_t, false);
+        if (a.light) PH_GEN32_PLAIN(uint64_t, true, kWarpsPerBlock, blocks);
+        else PH_GEN32_PLAIN(uint64_t, false, kWarpsHeavy, blocks_heavy);
     } else {
-        if (a.light) PH_GEN32_PLAIN(uint32_t, true);
-        else PH_GEN32_PLAIN(uint32_t, false);
+        if (a.light) PH_GEN32_PLAIN(uint32_t, true, kWarpsPerBlock, blocks);
+        else PH_GEN32_PLAIN(uint32_t, false, kWarpsHeavy, blocks_heavy);
     }
 #undef PH_GEN32_PLAIN
     return check_launch(err, "gen32_kernel launch");
@@ -459,9 +463,9 @@ uint64_t gen_resident_warps()
     if (!cached[dev]) {
         int sms = 0, b = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, gen32_kernel<kNPT, uint32_t, false, false>,
-                                                      kWarpsPerBlock * 32, 0);
-        cached[dev] = (uint64_t)(sms > 0 ? sms : 1) * (b > 0 ? b : 1) * kWarpsPerBlock;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, gen32_kernel<kNPT, uint32_t, false, false, kWarpsHeavy>,
+                                                      kWarpsHeavy * 32, 0);
+        cached[dev] = (uint64_t)(sms > 0 ? sms : 1) * (b > 0 ? b : 1) * kWarpsHeavy;
     }
     return cached[dev];
 }
