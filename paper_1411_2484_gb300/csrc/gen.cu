@@ -26,6 +26,10 @@ static constexpr int kWarpsPerBlock = PH_WPB;
 #ifndef PH_WPB_HEAVY
 #define PH_WPB_HEAVY 10
 #endif
+#ifndef PH_WPB_LIGHT
+#define PH_WPB_LIGHT 8
+#endif
+static constexpr int kWarpsLight = PH_WPB_LIGHT;   // warps per block of the LIGHT instantiation
 static constexpr int kWarpsHeavy = PH_WPB_HEAVY;   // warps per block of the plain heavy instantiation (90 registers: 20 warps per SM)
 static constexpr unsigned kFull = kFullMask;
 
@@ -395,6 +399,7 @@ int launch_gen32(const GenArgs &a, void *stream, std::string *err)
     }
     const uint64_t blocks = ((a.num << a.sp.log2K) + kWarpsPerBlock - 1) / kWarpsPerBlock;
     const uint64_t blocks_heavy = ((a.num << a.sp.log2K) + kWarpsHeavy - 1) / kWarpsHeavy;
+    const uint64_t blocks_light = ((a.num << a.sp.log2K) + kWarpsLight - 1) / kWarpsLight;
     cudaStream_t s = (cudaStream_t)stream;
     if (a.stats) {
         const size_t smem = (2 * kWarpsPerBlock * 32 * kNPT + kWarpsPerBlock * 256) * sizeof(uint32_t);
@@ -417,10 +422,10 @@ int launch_gen32(const GenArgs &a, void *stream, std::string *err)
         a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, (CTY *)a.c_out, a.r_out, a.vec_ok, \
         nullptr, nullptr, a.order, a.sp)
     if (a.c_is_64) {
-        if (a.light) PH_GEN32_PLAIN(uint64_t, true, kWarpsPerBlock, blocks);
+        if (a.light) PH_GEN32_PLAIN(uint64_t, true, kWarpsLight, blocks_light);
         else PH_GEN32_PLAIN(uint64_t, false, kWarpsHeavy, blocks_heavy);
     } else {
-        if (a.light) PH_GEN32_PLAIN(uint32_t, true, kWarpsPerBlock, blocks);
+        if (a.light) PH_GEN32_PLAIN(uint32_t, true, kWarpsLight, blocks_light);
         else PH_GEN32_PLAIN(uint32_t, false, kWarpsHeavy, blocks_heavy);
     }
 #undef PH_GEN32_PLAIN
