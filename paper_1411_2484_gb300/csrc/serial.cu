@@ -53,16 +53,16 @@ __device__ __forceinline__ uint32_t poker_category(const uint32_t *h)
 
 // POKER: hands of five cards, denominations floor(10 R), into 7 category
 // counters (D = 5, B = 10); otherwise the serial test's B^D counters.
-template <int NPT, bool POKER>
-__global__ void __launch_bounds__(256, 2)
+template <int NPT, bool POKER, int WB>
+__global__ void __launch_bounds__(WB * 32, 2)
 serial_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, DevState st,
               SkipConst sk, uint64_t first, uint64_t num, uint64_t per_inst, int D, uint32_t B,
               unsigned long long *__restrict__ hist, const uint32_t *__restrict__ order)
 {
     constexpr uint64_t G = 32 * NPT;
-    __shared__ uint32_t tb[8][32 * NPT + 8];   // per warp: a carried tuple start, then one group
+    __shared__ uint32_t tb[WB][32 * NPT + 8];  // per warp: a carried tuple start, then one group
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint64_t w = (uint64_t)blockIdx.x * 8 + warp;
+    const uint64_t w = (uint64_t)blockIdx.x * WB + warp;
     if (w >= num) return;
     const uint64_t j = order ? order[w] : w;
     const uint64_t i = first + j;
@@ -304,6 +304,11 @@ int launch_runs(const GenArgs &a, int lmax, unsigned long long *hist, void *stre
     return PHPRNG_OK;
 }
 
+#ifndef PH_SERIAL_WARPS
+#define PH_SERIAL_WARPS 10
+#endif
+static constexpr int kSerialWarps = PH_SERIAL_WARPS;   // warps per block of serial_kernel (84 registers, 2 blocks per SM)
+
 // Interstream serial test, step 1: bins floor(B R) of a chunk of c (Np
 // streams x L numbers, instance-major; uint64 elements when c64, as a
 // mixed-width context writes them) written in the paper's interleaved
@@ -405,12 +410,12 @@ int launch_serial(const GenArgs &a, int D, uint32_t B, unsigned long long *hist,
                   std::string *err)
 {
     if (a.num == 0 || a.per_inst == 0) return PHPRNG_OK;
-    const uint64_t blocks = (a.num + 7) / 8;
+    const uint64_t blocks = (a.num + kSerialWarps - 1) / kSerialWarps;
     if (D == 0)                                      // the poker test
-        serial_kernel<8, true><<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(
+        serial_kernel<8, true, kSerialWarps><<<(unsigned)blocks, kSerialWarps * 32, 0, (cudaStream_t)stream>>>(
             a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, 5, 10, hist, a.order);
     else
-        serial_kernel<8, false><<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(
+        serial_kernel<8, false, kSerialWarps><<<(unsigned)blocks, kSerialWarps * 32, 0, (cudaStream_t)stream>>>(
             a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, D, B, hist, a.order);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
