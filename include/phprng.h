@@ -14,8 +14,11 @@
  *
  * Conventions shared by every entry point:
  *  - Every function returns a phprng_status and never throws or aborts.
- *    A failed call leaves the context unchanged; phprng_last_error() gives a
- *    one-line message.
+ *    A call rejected by its argument checks leaves the context unchanged;
+ *    calls that work in chunks (phprng_fourier_test,
+ *    phprng_interstream_serial_test) and fail on the device part-way leave
+ *    the streams advanced by the chunks completed, as phprng_get_state
+ *    reports.  phprng_last_error() gives a one-line message.
  *  - Instance numbers are 0-based indexes into the table given at creation.
  *  - The stream position t of an instance counts the numbers produced so far.
  *    Output j (0-based) of a call is number t+j+1 of the stream, c_{t+j+1}:
