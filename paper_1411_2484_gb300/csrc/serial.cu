@@ -315,9 +315,10 @@ static constexpr int kSerialWarps = PH_SERIAL_WARPS;   // warps per block of ser
 // order, binsT[j Np + a] for stream a, number j.  A block takes a tile of 32
 // streams x 32 numbers through shared memory so that the reads run along a
 // stream and the writes along the streams.
+template <typename BT>
 __global__ void __launch_bounds__(256)
 inter_bins_kernel(const DevInst *__restrict__ inst, uint64_t first, uint64_t Np, uint64_t L,
-                  const void *__restrict__ c, int c64, uint32_t B, uint32_t *__restrict__ binsT)
+                  const void *__restrict__ c, int c64, uint32_t B, BT *__restrict__ binsT)
 {
     __shared__ uint32_t tile[32][33];
     const uint32_t tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
@@ -337,17 +338,18 @@ inter_bins_kernel(const DevInst *__restrict__ inst, uint64_t first, uint64_t Np,
     __syncthreads();
     for (uint32_t r = ty; r < 32; r += 8) {
         const uint64_t j = j0 + r, a = a0 + tx;
-        if (j < L && a < Np) binsT[j * Np + a] = tile[tx][r];
+        if (j < L && a < Np) binsT[j * Np + a] = (BT)tile[tx][r];
     }
 }
 
 // Step 2: consecutive non-overlapping D-tuples of the interleaved bins, one
 // count each (per-block shared counters when B^D is at most kInterSmemBins).
+// Bins are 16-bit words when B <= 2^16 (half the bytes of both passes).
 static constexpr uint32_t kInterSmemBins = 8192;
 
-template <bool SMEM>
+template <bool SMEM, typename BT>
 __global__ void __launch_bounds__(256)
-inter_hist_kernel(const uint32_t *__restrict__ binsT, uint64_t ntup, int D, uint32_t B, uint32_t nbins,
+inter_hist_kernel(const BT *__restrict__ binsT, uint64_t ntup, int D, uint32_t B, uint32_t nbins,
                   unsigned long long *__restrict__ hist)
 {
     __shared__ uint32_t sh[SMEM ? kInterSmemBins : 1];
@@ -359,7 +361,7 @@ inter_hist_kernel(const uint32_t *__restrict__ binsT, uint64_t ntup, int D, uint
          t += (uint64_t)gridDim.x * blockDim.x) {
         uint32_t idx = 0, scale = 1;
         for (int d = 0; d < D; ++d) {
-            idx += binsT[t * (uint64_t)D + (uint64_t)d] * scale;
+            idx += (uint32_t)binsT[t * (uint64_t)D + (uint64_t)d] * scale;
             scale *= B;
         }
         if (SMEM) atomicAdd(sh + idx, 1u);
@@ -383,7 +385,12 @@ int launch_interstream(const DevInst *inst, uint64_t first, uint64_t Np, uint64_
         return PHPRNG_EINVAL;
     }
     const dim3 grid((unsigned)((Np + 31) / 32), (unsigned)((L + 31) / 32));
-    inter_bins_kernel<<<grid, 256, 0, s>>>(inst, first, Np, L, c, c64, B, binsT);
+    const bool narrow = B <= 65536u;                 // bins fit 16 bits
+    uint16_t *bins16 = reinterpret_cast<uint16_t *>(binsT);
+    if (narrow)
+        inter_bins_kernel<uint16_t><<<grid, 256, 0, s>>>(inst, first, Np, L, c, c64, B, bins16);
+    else
+        inter_bins_kernel<uint32_t><<<grid, 256, 0, s>>>(inst, first, Np, L, c, c64, B, binsT);
     uint32_t nbins = 1;
     for (int d = 0; d < D; ++d) nbins *= B;
     const uint64_t ntup = Np * L / (uint64_t)D;
@@ -393,10 +400,17 @@ int launch_interstream(const DevInst *inst, uint64_t first, uint64_t Np, uint64_
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const uint64_t want = (ntup + 255) / 256, cap = (uint64_t)sms * 8;
         const unsigned blocks = (unsigned)(want < cap ? want : cap);
-        if (nbins <= kInterSmemBins)
-            inter_hist_kernel<true><<<blocks, 256, 0, s>>>(binsT, ntup, D, B, nbins, hist);
-        else
-            inter_hist_kernel<false><<<blocks, 256, 0, s>>>(binsT, ntup, D, B, nbins, hist);
+        if (narrow) {
+            if (nbins <= kInterSmemBins)
+                inter_hist_kernel<true, uint16_t><<<blocks, 256, 0, s>>>(bins16, ntup, D, B, nbins, hist);
+            else
+                inter_hist_kernel<false, uint16_t><<<blocks, 256, 0, s>>>(bins16, ntup, D, B, nbins, hist);
+        } else {
+            if (nbins <= kInterSmemBins)
+                inter_hist_kernel<true, uint32_t><<<blocks, 256, 0, s>>>(binsT, ntup, D, B, nbins, hist);
+            else
+                inter_hist_kernel<false, uint32_t><<<blocks, 256, 0, s>>>(binsT, ntup, D, B, nbins, hist);
+        }
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
