@@ -877,23 +877,26 @@ PH_API int phprng_interstream_serial_test(phprng_ctx *ctx, uint64_t first, uint6
     if (Lch > kInterMaxChunk) Lch = kInterMaxChunk / (uint64_t)D * (uint64_t)D;
     if (Lch > per_inst) Lch = per_inst;
     const int c64 = ctx->width != 32;                   // c's element size as launch_range writes it
-    void *c = nullptr;
+    void *c = nullptr, *kc = nullptr;
     uint32_t *binsT = nullptr;
     cudaError_t e = cudaMallocAsync(&c, num_inst * Lch * (c64 ? 8 : 4), s);
     if (e == cudaSuccess) e = cudaMallocAsync((void **)&binsT, num_inst * Lch * 4, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&kc, num_inst * 16, s);
     std::string err;
     int rc = e == cudaSuccess ? PHPRNG_OK : PHPRNG_ENOMEM;
+    if (rc == PHPRNG_OK) rc = launch_inter_consts(ctx->d_inst, first, num_inst, B, kc, s, &err);
     for (uint64_t j0 = 0; j0 < per_inst && rc == PHPRNG_OK; j0 += Lch) {
         const uint64_t L = std::min(Lch, per_inst - j0);
         rc = launch_range(ctx, first, num_inst, L, c, nullptr, nullptr, s, true);   // Eq. 9
         if (rc != PHPRNG_OK) break;
-        rc = launch_interstream(ctx->d_inst, first, num_inst, L, c, c64, D, B, binsT,
+        rc = launch_interstream(kc, num_inst, L, c, c64, D, B, binsT,
                                 (unsigned long long *)hist, s, &err);
         if (rc == PHPRNG_OK)
             for (uint64_t i = first; i < first + num_inst; ++i) ctx->pos_host[i] += L;
     }
     if (c) cudaFreeAsync(c, s);
     if (binsT) cudaFreeAsync(binsT, s);
+    if (kc) cudaFreeAsync(kc, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(ctx, PHPRNG_ENOMEM, std::string(W) + "scratch allocation failed");

@@ -185,7 +185,11 @@ int launch_fourier(const double *R, uint64_t nseq, uint32_t lgM, const double2 *
 // numbers, instance-major) into binsT in interleaved order, then its
 // D-tuples counted into hist (B^D counters).
 static constexpr uint64_t kInterMaxChunk = 65535ull * 32;   // numbers per stream and chunk
-int launch_interstream(const DevInst *inst, uint64_t first, uint64_t Np, uint64_t L, const void *c, int c64,
+// launch_inter_consts: per-stream bin constants k (Np x 16 bytes) of a call,
+// before the chunks; launch_interstream then reads them.
+int launch_inter_consts(const DevInst *inst, uint64_t first, uint64_t Np, uint32_t B, void *k, void *stream,
+                        std::string *err);
+int launch_interstream(const void *k, uint64_t Np, uint64_t L, const void *c, int c64,
                        int D, uint32_t B, uint32_t *binsT, unsigned long long *hist, void *stream,
                        std::string *err);
 // Collision-test consumer (serial.cu): segments of S numbers into B bins,

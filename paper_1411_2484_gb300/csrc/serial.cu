@@ -315,24 +315,32 @@ static constexpr int kSerialWarps = PH_SERIAL_WARPS;   // warps per block of ser
 // order, binsT[j Np + a] for stream a, number j.  A block takes a tile of 32
 // streams x 32 numbers through shared memory so that the reads run along a
 // stream and the writes along the streams.
+// Per-stream bin constants of a call, once: {yN, ybits, floor(B 2^32 / yN)}.
+__global__ void __launch_bounds__(256)
+inter_consts_kernel(const DevInst *__restrict__ inst, uint64_t first, uint64_t Np, uint32_t B,
+                    uint4 *__restrict__ k)
+{
+    const uint64_t a = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= Np) return;
+    const DevInst P = inst[first + a];
+    k[a] = make_uint4(P.yN, P.ybits, (uint32_t)(((uint64_t)B << 32) / P.yN), 0u);
+}
+
 template <typename BT>
 __global__ void __launch_bounds__(256)
-inter_bins_kernel(const DevInst *__restrict__ inst, uint64_t first, uint64_t Np, uint64_t L,
-                  const void *__restrict__ c, int c64, uint32_t B, BT *__restrict__ binsT)
+inter_bins_kernel(const uint4 *__restrict__ kc, uint64_t Np, uint64_t L, const void *__restrict__ c,
+                  int c64, uint32_t B, BT *__restrict__ binsT)
 {
     __shared__ uint32_t tile[32][33];
     const uint32_t tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const uint64_t a0 = (uint64_t)blockIdx.x * 32, j0 = (uint64_t)blockIdx.y * 32;
     for (uint32_t r = ty; r < 32; r += 8) {
         const uint64_t a = a0 + r, j = j0 + tx;
-        if (a < Np) {
-            const DevInst P = inst[first + a];
-            const uint32_t rB = (uint32_t)(((uint64_t)B << 32) / P.yN);
-            if (j < L) {
-                const uint32_t cv = c64 ? (uint32_t)static_cast<const uint64_t *>(c)[a * L + j]
-                                        : static_cast<const uint32_t *>(c)[a * L + j];
-                tile[r][tx] = serial_bin(cv, P.yN, P.ybits, rB, B);
-            }
+        if (a < Np && j < L) {
+            const uint4 k = kc[a];
+            const uint32_t cv = c64 ? (uint32_t)static_cast<const uint64_t *>(c)[a * L + j]
+                                    : static_cast<const uint32_t *>(c)[a * L + j];
+            tile[r][tx] = serial_bin(cv, k.x, k.y, k.z, B);
         }
     }
     __syncthreads();
@@ -374,7 +382,21 @@ inter_hist_kernel(const BT *__restrict__ binsT, uint64_t ntup, int D, uint32_t B
     }
 }
 
-int launch_interstream(const DevInst *inst, uint64_t first, uint64_t Np, uint64_t L, const void *c, int c64,
+int launch_inter_consts(const DevInst *inst, uint64_t first, uint64_t Np, uint32_t B, void *k, void *stream,
+                        std::string *err)
+{
+    if (Np == 0) return PHPRNG_OK;
+    inter_consts_kernel<<<(unsigned)((Np + 255) / 256), 256, 0, (cudaStream_t)stream>>>(inst, first, Np, B,
+                                                                                          (uint4 *)k);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        *err = std::string("inter_consts_kernel launch: ") + cudaGetErrorString(e);
+        return PHPRNG_ECUDA;
+    }
+    return PHPRNG_OK;
+}
+
+int launch_interstream(const void *k, uint64_t Np, uint64_t L, const void *c, int c64,
                        int D, uint32_t B, uint32_t *binsT, unsigned long long *hist, void *stream,
                        std::string *err)
 {
@@ -388,9 +410,9 @@ int launch_interstream(const DevInst *inst, uint64_t first, uint64_t Np, uint64_
     const bool narrow = B <= 65536u;                 // bins fit 16 bits
     uint16_t *bins16 = reinterpret_cast<uint16_t *>(binsT);
     if (narrow)
-        inter_bins_kernel<uint16_t><<<grid, 256, 0, s>>>(inst, first, Np, L, c, c64, B, bins16);
+        inter_bins_kernel<uint16_t><<<grid, 256, 0, s>>>((const uint4 *)k, Np, L, c, c64, B, bins16);
     else
-        inter_bins_kernel<uint32_t><<<grid, 256, 0, s>>>(inst, first, Np, L, c, c64, B, binsT);
+        inter_bins_kernel<uint32_t><<<grid, 256, 0, s>>>((const uint4 *)k, Np, L, c, c64, B, binsT);
     uint32_t nbins = 1;
     for (int d = 0; d < D; ++d) nbins *= B;
     const uint64_t ntup = Np * L / (uint64_t)D;
