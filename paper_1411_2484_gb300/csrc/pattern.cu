@@ -50,10 +50,14 @@ pattern_kernel(DevInst P, ExpProg pg, SkipConst sk, const uint32_t *__restrict__
     const uint32_t p = sk.p, n = (uint32_t)P.n;
     const uint64_t per_c0 = (p - 2 + NPT) / NPT;          // thread items per c0: skips 1 .. p-1
     const uint64_t items = L0 * per_c0;
-    for (uint64_t it = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; it < items;
-         it += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t q = it / per_c0;
-        const uint32_t s0 = (uint32_t)((it - q * per_c0) * NPT) + 1;
+    // item it = q per_c0 + r; the grid stride advances (q, r) without a
+    // division per item (one per thread here)
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t it0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t dq = stride / per_c0, dr = stride - dq * per_c0;
+    uint64_t q = it0 / per_c0, r = it0 - q * per_c0;
+    for (uint64_t it = it0; it < items; it += stride) {
+        const uint32_t s0 = (uint32_t)(r * NPT) + 1;
         const uint32_t m = mtab[q];
         uint32_t t[NPT], acc[NPT], x[NPT], idx[NPT];
 #pragma unroll
@@ -80,6 +84,12 @@ pattern_kernel(DevInst P, ExpProg pg, SkipConst sk, const uint32_t *__restrict__
 #pragma unroll
         for (int u = 0; u < NPT; ++u)
             if (s0 + u < p) atomicAdd((SMEM ? sh : hist) + idx[u], 1u);
+        q += dq;
+        r += dr;
+        if (r >= per_c0) {
+            r -= per_c0;
+            ++q;
+        }
     }
     if (SMEM) {
         __syncthreads();
