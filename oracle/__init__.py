@@ -93,6 +93,10 @@ class Oracle:
         lib.or_pattern_hist.argtypes = [u64, u64, u64, u64, u64, u64, ctypes.c_int, u64, P64]
         lib.or_pattern_const_hist.restype = None
         lib.or_pattern_const_hist.argtypes = [u64, u64, u64, u64, u64, ctypes.c_int, u64, P64]
+        lib.or_pattern_region_hist.restype = None
+        lib.or_pattern_region_hist.argtypes = [u64, u64, u64, u64, u64, u64, ctypes.c_int, u64, u64, P64]
+        lib.or_pattern_const_region_hist.restype = None
+        lib.or_pattern_const_region_hist.argtypes = [u64, u64, u64, u64, u64, ctypes.c_int, u64, u64, P64]
         lib.or_collision_hist.restype = None
         lib.or_collision_hist.argtypes = [P64, u64, u64, u64, u64, u64, P64]
         lib.or_generate_many.restype = u64
@@ -179,6 +183,23 @@ class Oracle:
             hist = np.zeros(B ** D, dtype=np.uint64)
         assert hist.dtype == np.uint64 and hist.size == B ** D and hist.flags.c_contiguous
         self.lib.or_interstream_serial_hist(_p64(c), _p64(nmod), Np, L, int(D), int(B), _p64(hist))
+        return hist
+
+    def pattern_region_hist(self, n, e, p, a, c_lo, L0, D, nb, L1, hist=None):
+        """Full-period pattern of (n, e, p, a) for c0 in [c_lo, c_lo+L0), successors
+        binned by floor(c / L1) and counted only inside [0, nb L1)^(D-1)."""
+        if hist is None:
+            hist = np.zeros(nb ** (D - 1), dtype=np.uint64)
+        assert hist.dtype == np.uint64 and hist.size == nb ** (D - 1)
+        self.lib.or_pattern_region_hist(n, e, p, a, c_lo, L0, D, nb, L1, _p64(hist))
+        return hist
+
+    def pattern_const_region_hist(self, n, e, b, c_lo, L0, D, nb, L1, hist=None):
+        """The same for the constant-skip generator (skip b; b = 1 is the unit skip)."""
+        if hist is None:
+            hist = np.zeros(nb ** (D - 1), dtype=np.uint64)
+        assert hist.dtype == np.uint64 and hist.size == nb ** (D - 1)
+        self.lib.or_pattern_const_region_hist(n, e, b, c_lo, L0, D, nb, L1, _p64(hist))
         return hist
 
     def poker_hist(self, c, n, hist=None):
@@ -370,6 +391,14 @@ def fourier_hist(coefs, nbins, w, hist=None):
     for part in (c.real, c.imag):
         hist += np.bincount(fourier_bin(part, nbins, w), minlength=nbins).astype(np.uint64)
     return hist
+
+
+def pattern_region_hist(n, e, p, a, c_lo, L0, D, nb, L1, hist=None):
+    return _default().pattern_region_hist(n, e, p, a, c_lo, L0, D, nb, L1, hist)
+
+
+def pattern_const_region_hist(n, e, b, c_lo, L0, D, nb, L1, hist=None):
+    return _default().pattern_const_region_hist(n, e, b, c_lo, L0, D, nb, L1, hist)
 
 
 def pattern_const_hist(n, e, b, c_lo, L0, D, nb, hist=None):

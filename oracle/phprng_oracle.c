@@ -453,6 +453,69 @@ void or_pattern_const_hist(uint64_t n, uint64_t e, uint64_t b, uint64_t c_lo, ui
     }
 }
 
+/* Full-period patterns over a region near the origin (the paper's Figs. 2-4:
+ * magnified squares and slabs): as or_pattern_hist and or_pattern_const_hist,
+ * but with the cell width L1 given and only the tuples whose successors all
+ * lie below nb L1 counted (the others are left out), so that hist[b_1 + nb b_2
+ * + ...], b_j = floor(c_(k+j) / L1), covers the region [0, nb L1)^(D-1) of the
+ * successors for the starting values c0 in [c_lo, c_lo + L0).  With
+ * L1 = ceil(n / nb) nothing is left out and the results equal the full-range
+ * functions.  b = 0 in or_pattern_region_hist selects the pseudorandom skip
+ * (p, a); or_pattern_const_region_hist takes the constant skip b.
+ * Pinned by: the full-range reduction; brute-force counts over whole periods
+ * of tiny instances; the paper's Fig. 2 crib pairs for the unit skip; the
+ * Fig. 3 properties (each pair at most once, none on the diagonal). */
+static uint64_t or_inverse_exponent(uint64_t n, uint64_t e)
+{
+    int64_t r0 = (int64_t)(n - 1), r1 = (int64_t)(e % (n - 1)), t0 = 0, t1 = 1;
+    while (r1) {
+        int64_t q = r0 / r1, tmp;
+        tmp = r0 - q * r1; r0 = r1; r1 = tmp;
+        tmp = t0 - q * t1; t0 = t1; t1 = tmp;
+    }
+    return (uint64_t)(t0 < 0 ? t0 + (int64_t)(n - 1) : t0);
+}
+
+void or_pattern_region_hist(uint64_t n, uint64_t e, uint64_t p, uint64_t a, uint64_t c_lo,
+                            uint64_t L0, int D, uint64_t nb, uint64_t L1, uint64_t *hist)
+{
+    uint64_t d = or_inverse_exponent(n, e);
+    for (uint64_t c0 = c_lo; c0 < c_lo + L0; ++c0) {
+        uint64_t m = or_powmod(c0, d, n);
+        for (uint64_t s = 1; s < p; ++s) {
+            uint64_t acc = m, t = s, idx = 0, scale = 1;
+            int inside = 1;
+            for (int j = 1; j < D; ++j) {
+                acc = (uint64_t)(((u128)acc + t) % n);
+                uint64_t c = or_powmod(acc, e, n);
+                if (c / L1 >= nb) inside = 0;
+                idx += (c / L1) * scale;
+                scale *= nb;
+                t = or_mulmod(a, t, p);
+            }
+            if (inside) hist[idx] += 1;
+        }
+    }
+}
+
+void or_pattern_const_region_hist(uint64_t n, uint64_t e, uint64_t b, uint64_t c_lo, uint64_t L0, int D,
+                                  uint64_t nb, uint64_t L1, uint64_t *hist)
+{
+    uint64_t d = or_inverse_exponent(n, e);
+    for (uint64_t c0 = c_lo; c0 < c_lo + L0; ++c0) {
+        uint64_t m = or_powmod(c0, d, n), idx = 0, scale = 1;
+        int inside = 1;
+        for (int j = 1; j < D; ++j) {
+            uint64_t mj = (uint64_t)(((u128)m + (u128)j * (b % n)) % n);
+            uint64_t c = or_powmod(mj, e, n);
+            if (c / L1 >= nb) inside = 0;
+            idx += (c / L1) * scale;
+            scale *= nb;
+        }
+        if (inside) hist[idx] += 1;
+    }
+}
+
 /* Collision test (Tests section: 2^14 numbers into 2^20 bins).  One stream's
  * numbers in consecutive non-overlapping segments of S (a remainder of fewer
  * than S is left out); number k falls in bin floor(B R_k); a number is a

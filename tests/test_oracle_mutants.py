@@ -62,6 +62,14 @@ MUTANTS = {
     "collision_no_reset": ("            seen[b] = 0;\n", "            seen[b] = 1;\n"),
     "pattern_const_offset": ("uint64_t mj = (uint64_t)(((u128)m + (u128)j * (b % n)) % n);",
                              "uint64_t mj = (uint64_t)(((u128)m + (u128)(j + 1) * (b % n)) % n);"),
+    "pattern_region_drops_last_skip": (
+        "uint64_t d = or_inverse_exponent(n, e);\n    for (uint64_t c0 = c_lo; c0 < c_lo + L0; ++c0) {\n"
+        "        uint64_t m = or_powmod(c0, d, n);\n        for (uint64_t s = 1; s < p; ++s) {",
+        "uint64_t d = or_inverse_exponent(n, e);\n    for (uint64_t c0 = c_lo; c0 < c_lo + L0; ++c0) {\n"
+        "        uint64_t m = or_powmod(c0, d, n);\n        for (uint64_t s = 1; s + 1 < p; ++s) {"),
+    "pattern_const_region_encrypts": (
+        "uint64_t m = or_powmod(c0, d, n), idx = 0, scale = 1;\n        int inside = 1;",
+        "uint64_t m = or_powmod(c0, e, n), idx = 0, scale = 1;\n        int inside = 1;"),
     "dlog_index": ("L_out[q] = (i * M + val[h]) % order;", "L_out[q] = (i * M + val[h] + 1) % order;"),
 }
 

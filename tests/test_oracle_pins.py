@@ -645,3 +645,74 @@ def test_fourier_variance_one_over_24(oracle_mod):
     assert int(h.sum()) == 2 * X.size
     assert om.fourier_bin(-1.0, 64, 1.0) == 0 and om.fourier_bin(0.999999, 64, 1.0) == 63
     assert om.fourier_bin(5.0, 64, 1.0) == 63 and om.fourier_bin(-5.0, 64, 1.0) == 0
+
+
+# ------------------------------------------------------------ pattern regions (Figs. 2-4)
+@pytest.mark.parametrize("n,p,e,D,nb", [(23, 11, 3, 2, 4), (47, 23, 5, 3, 3), (1019, 509, 3, 2, 7)])
+def test_pattern_region_full_range_reduction(oracle_mod, n, p, e, D, nb):
+    """With L1 = ceil(n / nb) the region is the whole range: equal to the
+    full-range functions (pseudorandom and unit skip)."""
+    a = primitive_root(p)
+    L1 = -(-n // nb)
+    L0 = min(n, 40)
+    assert np.array_equal(oracle_mod.pattern_region_hist(n, e, p, a, 0, L0, D, nb, L1),
+                          oracle_mod.pattern_hist(n, e, p, a, 0, L0, D, nb))
+    assert np.array_equal(oracle_mod.pattern_const_region_hist(n, e, 1, 0, L0, D, nb, L1),
+                          oracle_mod.pattern_const_hist(n, e, 1, 0, L0, D, nb))
+
+
+@pytest.mark.parametrize("n,p,e,D,nb,L1,c_lo,L0", [(23, 11, 3, 2, 4, 3, 0, 23), (23, 11, 3, 3, 3, 5, 2, 9),
+                                                  (47, 23, 5, 2, 5, 4, 10, 20), (47, 23, 5, 3, 2, 9, 0, 47)])
+def test_pattern_region_equals_full_period_brute_force(oracle_mod, n, p, e, D, nb, L1, c_lo, L0):
+    """Counting, over a whole period n(p-1) of the generator, the D-tuples
+    that start in [c_lo, c_lo+L0) with every successor below nb L1, in cells
+    of width L1."""
+    a = primitive_root(p)
+    P = n * (p - 1)
+    c, _, _ = oracle_mod.generate(n, e, p, a, 4 % n, 3 % p or 1, P)
+    want = np.zeros(nb ** (D - 1), dtype=np.uint64)
+    for k in range(P):
+        if c_lo <= c[k] < c_lo + L0:
+            cells = [int(c[(k + j) % P]) // L1 for j in range(1, D)]
+            if all(b < nb for b in cells):
+                want[sum(b * nb ** i for i, b in enumerate(cells))] += 1
+    assert np.array_equal(oracle_mod.pattern_region_hist(n, e, p, a, c_lo, L0, D, nb, L1), want)
+    cu = [pow((5 + k) % n, e, n) for k in range(n)]          # unit skip, period n
+    want = np.zeros(nb ** (D - 1), dtype=np.uint64)
+    for k in range(n):
+        if c_lo <= cu[k] < c_lo + L0:
+            cells = [cu[(k + j) % n] // L1 for j in range(1, D)]
+            if all(b < nb for b in cells):
+                want[sum(b * nb ** i for i, b in enumerate(cells))] += 1
+    assert np.array_equal(oracle_mod.pattern_const_region_hist(n, e, 1, c_lo, L0, D, nb, L1), want)
+
+
+def test_pattern_region_fig2_cribs_and_cell_counts(oracle_mod):
+    """Fig. 2 (unit skip, n = 2^32 - 5, e = 9): the printed crib pairs (0, 1),
+    (1, 512), (512, 19683), (19683, 262144) are points of the pattern; over the
+    magnified square [0, 2^20)^2 cut into 16 cells of (2^18)^2 the total is
+    close to 2^40 / n (the caption's 16 +- 4 per cell)."""
+    h, rows = read_golden("fig2_unit_skip.txt")
+    n, e = int(h["n"]), int(h["e"])
+    c = [int(r[1]) for r in rows]                          # c for m = 0, 1, 2, 3, 4
+    for c0, c1 in zip(c[:-1], c[1:]):
+        got = oracle_mod.pattern_const_region_hist(n, e, 1, c0, 1, 2, 1 << 20, 1)
+        assert got[c1] == 1 and int(got.sum()) == 1, (c0, c1)
+    cells = np.zeros((4, 4), dtype=np.int64)
+    for i in range(4):
+        cells[i] = oracle_mod.pattern_const_region_hist(n, e, 1, i << 18, 1 << 18, 2, 4, 1 << 18).astype(np.int64)
+    expect = (1 << 40) / n                                # 256 points over the square
+    assert abs(cells.sum() - expect) < 6 * expect ** 0.5
+    assert cells.min() >= 1 and cells.max() <= 16 + 6 * 4
+
+
+@pytest.mark.parametrize("n,p,e", [(23, 11, 3), (47, 23, 5), (107, 53, 3)])
+def test_pattern_region_fig3_each_pair_once_none_on_diagonal(oracle_mod, n, p, e):
+    """Fig. 3's properties of the two-dimensional full-period pattern with
+    cells of width 1: every (c_k, c_(k+1)) pair occurs at most once, and none
+    lies on the diagonal (0 < s < p <= n - 1)."""
+    a = primitive_root(p)
+    for c0 in range(n):
+        row = oracle_mod.pattern_region_hist(n, e, p, a, c0, 1, 2, n, 1)
+        assert row.max() <= 1 and row[c0] == 0
+        assert int(row.sum()) == p - 1
