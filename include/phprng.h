@@ -308,6 +308,23 @@ int phprng_pattern(const phprng_instance *inst, uint64_t c_lo, uint64_t L0, int 
 int phprng_pattern_const(const phprng_instance *inst, uint64_t b, uint64_t c_lo, uint64_t L0, int D,
                          uint32_t nb, uint64_t *hist, void *cuda_stream);
 
+/* The full-period patterns over a region near the origin, as the paper's
+ * Figs. 2-4 show them (magnified squares and slabs): as phprng_pattern and
+ * phprng_pattern_const, but the cells have the given width L1 >= 1 and only
+ * the tuples whose successors all lie below nb L1 are counted, so that
+ * hist[b_1 + nb b_2 + ...], b_j = floor(c_(k+j) / L1), covers the region
+ * [0, nb L1)^(D-1) of the successors of the starting values c0 in
+ * [c_lo, c_lo + L0).  With L1 = ceil(n / nb) they equal the whole-range calls.
+ * Examples: Fig. 3's 2^7 x 2^7 square, one call per c0 in [0, 2^7) with
+ * L0 = 1, D = 2, nb = 2^7, L1 = 1 (each pair appears once or not at all);
+ * Fig. 4's slab 2^9 x 2^16 x 2^16 in 16 subslabs, c_lo = 0, L0 = 2^9, D = 3,
+ * nb = 4, L1 = 2^14.  Limits and errors otherwise those of the whole-range
+ * calls. */
+int phprng_pattern_region(const phprng_instance *inst, uint64_t c_lo, uint64_t L0, int D, uint32_t nb,
+                          uint32_t L1, uint64_t *hist, void *cuda_stream);
+int phprng_pattern_const_region(const phprng_instance *inst, uint64_t b, uint64_t c_lo, uint64_t L0, int D,
+                                uint32_t nb, uint32_t L1, uint64_t *hist, void *cuda_stream);
+
 /* Moves instance inst_ids[i] to absolute stream position pos[i], forward or
  * backward: afterwards its next number is number pos[i]+1 of the stream
  * counted from its seed, and its state (m, s, c) is the one generation would

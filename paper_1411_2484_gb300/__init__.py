@@ -36,7 +36,8 @@ PHPRNG_ALLOW_SHARED_N = 0x2
 EXPORTED = [
     "phprng_create", "phprng_create_seeded", "phprng_destroy", "phprng_last_error",
     "phprng_status_string", "phprng_generate", "phprng_skip", "phprng_seek", "phprng_serial_test", "phprng_poker_test", "phprng_runs_test", "phprng_collision_test",
-    "phprng_fourier_test", "phprng_interstream_serial_test", "phprng_pattern", "phprng_pattern_const",
+    "phprng_fourier_test", "phprng_interstream_serial_test", "phprng_pattern",
+    "phprng_pattern_region", "phprng_pattern_const_region", "phprng_pattern_const",
     "phprng_get_state", "phprng_set_state",
     "phprng_is_prime", "phprng_validate", "phprng_draw_instances", "phprng_microbench",
     "phprng_plan_create", "phprng_plan_launch", "phprng_plan_launch_graph",
@@ -146,6 +147,10 @@ def _load():
                                        ctypes.c_uint32, vp, vp]
         lib.phprng_pattern_const.argtypes = [ctypes.POINTER(phprng_instance), u64, u64, u64, i32,
                                              ctypes.c_uint32, vp, vp]
+        lib.phprng_pattern_region.argtypes = [ctypes.POINTER(phprng_instance), u64, u64, i32,
+                                              ctypes.c_uint32, ctypes.c_uint32, vp, vp]
+        lib.phprng_pattern_const_region.argtypes = [ctypes.POINTER(phprng_instance), u64, u64, u64, i32,
+                                                    ctypes.c_uint32, ctypes.c_uint32, vp, vp]
         lib.phprng_get_state.argtypes = [vp, u64, P_inst, P64, P64, vp]
         lib.phprng_set_state.argtypes = [vp, u64, u64, u64, u64, u64, vp]
         lib.phprng_is_prime.argtypes = [u64]
@@ -325,6 +330,21 @@ def phprng_pattern(n, e, p, a, c_lo, L0, D, nb, hist, stream=None):
     inst = phprng_instance(int(n), int(e), int(p), int(a), 0, 1)
     _check(_load().phprng_pattern(ctypes.byref(inst), int(c_lo), int(L0), int(D), int(nb), _ptr(hist),
                                   _stream(stream)), None)
+
+
+def phprng_pattern_region(n, e, p, a, c_lo, L0, D, nb, L1, hist, stream=None):
+    """phprng_pattern over the region [0, nb*L1)^(D-1) of the successors, cells
+    of width L1 (tuples outside the region left out)."""
+    inst = phprng_instance(int(n), int(e), int(p), int(a), 0, 1)
+    _check(_load().phprng_pattern_region(ctypes.byref(inst), int(c_lo), int(L0), int(D), int(nb), int(L1),
+                                         _ptr(hist), _stream(stream)), None)
+
+
+def phprng_pattern_const_region(n, e, b, c_lo, L0, D, nb, L1, hist, stream=None):
+    """phprng_pattern_const over the region [0, nb*L1)^(D-1), cells of width L1."""
+    inst = phprng_instance(int(n), int(e), 2, 1, 0, 1)
+    _check(_load().phprng_pattern_const_region(ctypes.byref(inst), int(b), int(c_lo), int(L0), int(D),
+                                               int(nb), int(L1), _ptr(hist), _stream(stream)), None)
 
 
 def phprng_pattern_const(n, e, b, c_lo, L0, D, nb, hist, stream=None):

@@ -987,30 +987,31 @@ static uint64_t inverse_mod(uint64_t e, uint64_t m)
     return (uint64_t)(t0 < 0 ? t0 + m : t0);
 }
 
-PH_API int phprng_pattern(const phprng_instance *inst, uint64_t c_lo, uint64_t L0, int D, uint32_t nb,
-                          uint64_t *hist, void *cuda_stream)
+static int pattern_impl(const char *name, const phprng_instance *inst, uint64_t c_lo, uint64_t L0, int D,
+                        uint32_t nb, uint32_t L1, uint64_t *hist, void *cuda_stream)
 {
-    if (!inst) return fail(nullptr, PHPRNG_EINVAL, "phprng_pattern: inst is NULL");
+    const std::string W = std::string(name) + ": ";
+    if (!inst) return fail(nullptr, PHPRNG_EINVAL, W + "inst is NULL");
     phprng_instance in = *inst;
     in.m0 = 0;                                               // the seeds play no part
     in.s0 = 1;
     std::string msg;
     int rc = validate_one(32, in, 0, &msg);
-    if (rc != PHPRNG_OK) return fail(nullptr, rc, "phprng_pattern: " + msg);
+    if (rc != PHPRNG_OK) return fail(nullptr, rc, W + msg);
     inst = &in;
     const uint64_t n = inst->n;
     if (L0 < 1 || L0 > (1ull << 20) || c_lo >= n || L0 > n - c_lo)
         return fail(nullptr, PHPRNG_EINVAL,
-                    "phprng_pattern: need 1 <= L0 <= 2^20 and c_lo + L0 <= n");
-    if (D < 2 || D > 8) return fail(nullptr, PHPRNG_EINVAL, "phprng_pattern: D must be 2..8");
+                    W + "need 1 <= L0 <= 2^20 and c_lo + L0 <= n");
+    if (D < 2 || D > 8) return fail(nullptr, PHPRNG_EINVAL, W + "D must be 2..8");
     uint64_t bins = 1;
     for (int d = 1; d < D && bins <= (1ull << 24); ++d) bins *= nb;
     if (nb < 1 || bins > (1ull << 24))
-        return fail(nullptr, PHPRNG_EINVAL, "phprng_pattern: nb^(D-1) must be 1 .. 2^24");
+        return fail(nullptr, PHPRNG_EINVAL, W + "nb^(D-1) must be 1 .. 2^24");
     if (!hist || (uintptr_t)hist % 8)
-        return fail(nullptr, PHPRNG_EINVAL, "phprng_pattern: hist NULL or not 8-byte aligned");
+        return fail(nullptr, PHPRNG_EINVAL, W + "hist NULL or not 8-byte aligned");
     if (pointer_kind(hist) != 1)
-        return fail(nullptr, PHPRNG_EINVAL, "phprng_pattern: hist must be device memory");
+        return fail(nullptr, PHPRNG_EINVAL, W + "hist must be device memory");
     ExpProg pg;
     const DevInst P = derive_inst(*inst, 0, &pg);
     const SkipConst sk = derive_skip(inst->p, inst->a, 8);
@@ -1019,7 +1020,7 @@ PH_API int phprng_pattern(const phprng_instance *inst, uint64_t c_lo, uint64_t L
     try {
         mtab.resize(L0);
     } catch (const std::bad_alloc &) {
-        return fail(nullptr, PHPRNG_ENOMEM, "phprng_pattern: host allocation failed");
+        return fail(nullptr, PHPRNG_ENOMEM, W + "host allocation failed");
     }
     for (uint64_t q = 0; q < L0; ++q) mtab[q] = (uint32_t)powmod(c_lo + q, d, n);
     cudaStream_t s = (cudaStream_t)cuda_stream;
@@ -1027,22 +1028,36 @@ PH_API int phprng_pattern(const phprng_instance *inst, uint64_t c_lo, uint64_t L
     cudaError_t e = cudaMallocAsync((void **)&d_m, L0 * sizeof(uint32_t), s);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        return fail(nullptr, PHPRNG_ENOMEM, "phprng_pattern: device allocation failed");
+        return fail(nullptr, PHPRNG_ENOMEM, W + "device allocation failed");
     }
     // from pageable memory: staged before the call returns, then ordered on s
     e = cudaMemcpyAsync(d_m, mtab.data(), L0 * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
     std::string err;
-    rc = e == cudaSuccess ? launch_pattern(P, pg, sk, d_m, L0, D, nb, hist, s, &err) : PHPRNG_ECUDA;
+    rc = e == cudaSuccess ? launch_pattern(P, pg, sk, d_m, L0, D, nb, L1, hist, s, &err) : PHPRNG_ECUDA;
     cudaFreeAsync(d_m, s);
-    if (e != cudaSuccess) return cuda_fail(nullptr, e, "phprng_pattern: upload");
-    if (rc != PHPRNG_OK) return fail(nullptr, rc, "phprng_pattern: " + err);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, (W + "upload").c_str());
+    if (rc != PHPRNG_OK) return fail(nullptr, rc, W + err);
     return PHPRNG_OK;
 }
 
-PH_API int phprng_pattern_const(const phprng_instance *inst, uint64_t b, uint64_t c_lo, uint64_t L0,
-                                int D, uint32_t nb, uint64_t *hist, void *cuda_stream)
+PH_API int phprng_pattern(const phprng_instance *inst, uint64_t c_lo, uint64_t L0, int D, uint32_t nb,
+                          uint64_t *hist, void *cuda_stream)
 {
-    if (!inst) return fail(nullptr, PHPRNG_EINVAL, "phprng_pattern_const: inst is NULL");
+    return pattern_impl("phprng_pattern", inst, c_lo, L0, D, nb, 0, hist, cuda_stream);
+}
+
+PH_API int phprng_pattern_region(const phprng_instance *inst, uint64_t c_lo, uint64_t L0, int D, uint32_t nb,
+                                 uint32_t L1, uint64_t *hist, void *cuda_stream)
+{
+    if (L1 < 1) return fail(nullptr, PHPRNG_EINVAL, "phprng_pattern_region: L1 must be at least 1");
+    return pattern_impl("phprng_pattern_region", inst, c_lo, L0, D, nb, L1, hist, cuda_stream);
+}
+
+static int pattern_const_impl(const char *name, const phprng_instance *inst, uint64_t b, uint64_t c_lo,
+                              uint64_t L0, int D, uint32_t nb, uint32_t L1, uint64_t *hist, void *cuda_stream)
+{
+    const std::string W = std::string(name) + ": ";
+    if (!inst) return fail(nullptr, PHPRNG_EINVAL, W + "inst is NULL");
     phprng_instance in = *inst;
     in.p = 3;                                                // only n and e play a part:
     in.a = 2;                                                // a valid stand-in skip generator
@@ -1050,29 +1065,42 @@ PH_API int phprng_pattern_const(const phprng_instance *inst, uint64_t b, uint64_
     in.s0 = 1;
     std::string msg;
     int rc = validate_one(32, in, 0, &msg);
-    if (rc != PHPRNG_OK) return fail(nullptr, rc, "phprng_pattern_const: " + msg);
+    if (rc != PHPRNG_OK) return fail(nullptr, rc, W + msg);
     const uint64_t n = in.n;
-    if (b < 1 || b >= n) return fail(nullptr, PHPRNG_EINVAL, "phprng_pattern_const: need 1 <= b < n");
+    if (b < 1 || b >= n) return fail(nullptr, PHPRNG_EINVAL, W + "need 1 <= b < n");
     if (L0 < 1 || c_lo >= n || L0 > n - c_lo)
-        return fail(nullptr, PHPRNG_EINVAL, "phprng_pattern_const: need L0 >= 1 and c_lo + L0 <= n");
-    if (D < 2 || D > 8) return fail(nullptr, PHPRNG_EINVAL, "phprng_pattern_const: D must be 2..8");
+        return fail(nullptr, PHPRNG_EINVAL, W + "need L0 >= 1 and c_lo + L0 <= n");
+    if (D < 2 || D > 8) return fail(nullptr, PHPRNG_EINVAL, W + "D must be 2..8");
     uint64_t bins = 1;
     for (int d = 1; d < D && bins <= (1ull << 24); ++d) bins *= nb;
     if (nb < 1 || bins > (1ull << 24))
-        return fail(nullptr, PHPRNG_EINVAL, "phprng_pattern_const: nb^(D-1) must be 1 .. 2^24");
+        return fail(nullptr, PHPRNG_EINVAL, W + "nb^(D-1) must be 1 .. 2^24");
     if (!hist || (uintptr_t)hist % 8)
-        return fail(nullptr, PHPRNG_EINVAL, "phprng_pattern_const: hist NULL or not 8-byte aligned");
+        return fail(nullptr, PHPRNG_EINVAL, W + "hist NULL or not 8-byte aligned");
     if (pointer_kind(hist) != 1)
-        return fail(nullptr, PHPRNG_EINVAL, "phprng_pattern_const: hist must be device memory");
+        return fail(nullptr, PHPRNG_EINVAL, W + "hist must be device memory");
     ExpProg pg, pgd;
     const DevInst P = derive_inst(in, 0, &pg);
     phprng_instance dec = in;
     dec.e = inverse_mod(in.e, n - 1);                        // Eq. 2
     const DevInst Pd = derive_inst(dec, 0, &pgd);
     std::string err;
-    rc = launch_pattern_const(P, pg, Pd, pgd, (uint32_t)b, c_lo, L0, D, nb, hist, cuda_stream, &err);
-    if (rc != PHPRNG_OK) return fail(nullptr, rc, "phprng_pattern_const: " + err);
+    rc = launch_pattern_const(P, pg, Pd, pgd, (uint32_t)b, c_lo, L0, D, nb, L1, hist, cuda_stream, &err);
+    if (rc != PHPRNG_OK) return fail(nullptr, rc, W + err);
     return PHPRNG_OK;
+}
+
+PH_API int phprng_pattern_const(const phprng_instance *inst, uint64_t b, uint64_t c_lo, uint64_t L0,
+                                int D, uint32_t nb, uint64_t *hist, void *cuda_stream)
+{
+    return pattern_const_impl("phprng_pattern_const", inst, b, c_lo, L0, D, nb, 0, hist, cuda_stream);
+}
+
+PH_API int phprng_pattern_const_region(const phprng_instance *inst, uint64_t b, uint64_t c_lo, uint64_t L0,
+                                       int D, uint32_t nb, uint32_t L1, uint64_t *hist, void *cuda_stream)
+{
+    if (L1 < 1) return fail(nullptr, PHPRNG_EINVAL, "phprng_pattern_const_region: L1 must be at least 1");
+    return pattern_const_impl("phprng_pattern_const_region", inst, b, c_lo, L0, D, nb, L1, hist, cuda_stream);
 }
 
 PH_API int phprng_seek(phprng_ctx *ctx, const uint64_t *inst_ids, const uint64_t *pos,

@@ -166,9 +166,11 @@ int launch_serial(const GenArgs &a, int D, uint32_t B, unsigned long long *hist,
 int launch_runs(const GenArgs &a, int lmax, unsigned long long *hist, void *stream, std::string *err);
 // Full-period pattern of the constant-skip generator (pattern.cu): P, pg for
 // e and Pd, pgd for d = e^-1 mod n-1; one point per c0 in [c_lo, c_lo+L0).
+// L1 = 0: cells of ceil(n / nb) over the whole range; L1 >= 1: cells of L1,
+// tuples with a successor at or above nb L1 left out (a region near the origin).
 int launch_pattern_const(const DevInst &P, const ExpProg &pg, const DevInst &Pd, const ExpProg &pgd,
-                         uint32_t b, uint64_t c_lo, uint64_t L0, int D, uint32_t nb, uint64_t *hist,
-                         void *stream, std::string *err);
+                         uint32_t b, uint64_t c_lo, uint64_t L0, int D, uint32_t nb, uint32_t L1,
+                         uint64_t *hist, void *stream, std::string *err);
 // Fourier test (fourier.cu).  Twiddle tables for sequences of M = 2^lgM
 // numbers: fourier_twiddle_count(lgM) double2, filled by launch_twiddles.
 // launch_fourier: for nseq sequences of M doubles R (contiguous), the
@@ -201,7 +203,8 @@ int launch_collision(const GenArgs &a, uint32_t S, uint32_t B, uint32_t H, unsig
 // Full-period pattern by enumeration (pattern.cu): mtab[q] = (c_lo+q)^d mod n
 // for q < L0, sk for NPT 8; hist has nb^(D-1) uint64 counters.
 int launch_pattern(const DevInst &P, const ExpProg &pg, const SkipConst &sk, const uint32_t *mtab,
-                   uint64_t L0, int D, uint32_t nb, uint64_t *hist, void *stream, std::string *err);
+                   uint64_t L0, int D, uint32_t nb, uint32_t L1, uint64_t *hist, void *stream,
+                   std::string *err);   // L1 as for launch_pattern_const
 // Split launches: the pre-pass (sk8 = the NPT 8 skip constants) and the
 // number of warps the 32-bit generator keeps resident on the current device.
 int launch_chunk_sums(const GenArgs &a, const SkipConst &sk8, void *stream, std::string *err);

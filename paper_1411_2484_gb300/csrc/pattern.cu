@@ -39,7 +39,7 @@ static constexpr uint32_t kSmemBins = 8192;
 template <int NPT, bool SMEM>
 __global__ void __launch_bounds__(256, 2)
 pattern_kernel(DevInst P, ExpProg pg, SkipConst sk, const uint32_t *__restrict__ mtab, uint64_t L0,
-               int D, uint32_t nb, uint32_t L1, uint32_t rL1, uint32_t bins,
+               int D, uint32_t nb, uint32_t L1, uint32_t rL1, uint64_t lim, uint32_t bins,
                unsigned int *__restrict__ hist)
 {
     extern __shared__ unsigned int sh[];
@@ -60,12 +60,14 @@ pattern_kernel(DevInst P, ExpProg pg, SkipConst sk, const uint32_t *__restrict__
         const uint32_t s0 = (uint32_t)(r * NPT) + 1;
         const uint32_t m = mtab[q];
         uint32_t t[NPT], acc[NPT], x[NPT], idx[NPT];
+        bool inside[NPT];
 #pragma unroll
         for (int u = 0; u < NPT; ++u) {
             // skips past p-1 (the last item of a c0) are computed and not counted
             t[u] = s0 + u < p ? s0 + u : 1u;
             acc[u] = m;
             idx[u] = 0;
+            inside[u] = s0 + u < p;
         }
         uint32_t scale = 1;
         for (int j = 1; j < D; ++j) {
@@ -73,8 +75,10 @@ pattern_kernel(DevInst P, ExpProg pg, SkipConst sk, const uint32_t *__restrict__
             for (int u = 0; u < NPT; ++u) acc[u] = addmod32(acc[u], t[u], n);
             encrypt<NPT, uint32_t>(P, pg, acc, x);                     // Eq. 9c
 #pragma unroll
-            for (int u = 0; u < NPT; ++u)
+            for (int u = 0; u < NPT; ++u) {
                 idx[u] += (L1 == 1 ? x[u] : div_by_width(x[u], L1, rL1)) * scale;
+                inside[u] = inside[u] && x[u] < lim;                    // region [0, nb L1)
+            }
             scale *= nb;
             if (j + 1 < D) {
 #pragma unroll
@@ -83,7 +87,7 @@ pattern_kernel(DevInst P, ExpProg pg, SkipConst sk, const uint32_t *__restrict__
         }
 #pragma unroll
         for (int u = 0; u < NPT; ++u)
-            if (s0 + u < p) atomicAdd((SMEM ? sh : hist) + idx[u], 1u);
+            if (inside[u]) atomicAdd((SMEM ? sh : hist) + idx[u], 1u);
         q += dq;
         r += dr;
         if (r >= per_c0) {
@@ -120,7 +124,7 @@ fold_counts_kernel(unsigned int *__restrict__ h32, unsigned long long *__restric
 template <int NPT, bool SMEM>
 __global__ void __launch_bounds__(256, 2)
 pattern_const_kernel(DevInst P, ExpProg pg, DevInst Pd, ExpProg pgd, uint32_t b, uint64_t c_lo,
-                     uint64_t L0, int D, uint32_t nb, uint32_t L1, uint32_t rL1, uint32_t bins,
+                     uint64_t L0, int D, uint32_t nb, uint32_t L1, uint32_t rL1, uint64_t lim, uint32_t bins,
                      unsigned long long *__restrict__ hist)
 {
     extern __shared__ unsigned int sh[];
@@ -134,10 +138,12 @@ pattern_const_kernel(DevInst P, ExpProg pg, DevInst Pd, ExpProg pgd, uint32_t b,
          it += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t q0 = it * NPT;
         uint32_t c0[NPT], m[NPT], acc[NPT], x[NPT], idx[NPT];
+        bool inside[NPT];
 #pragma unroll
         for (int u = 0; u < NPT; ++u) {
             c0[u] = (uint32_t)(c_lo + (q0 + u < L0 ? q0 + u : 0));   // past L0: computed, not counted
             idx[u] = 0;
+            inside[u] = q0 + u < L0;
         }
         encrypt<NPT, uint32_t>(Pd, pgd, c0, m);                       // m = c0^d (Eq. 2)
         uint32_t scale = 1;
@@ -148,13 +154,15 @@ pattern_const_kernel(DevInst P, ExpProg pg, DevInst Pd, ExpProg pgd, uint32_t b,
             for (int u = 0; u < NPT; ++u) acc[u] = addmod32(acc[u], b, n);
             encrypt<NPT, uint32_t>(P, pg, acc, x);                      // Eq. 9c
 #pragma unroll
-            for (int u = 0; u < NPT; ++u)
+            for (int u = 0; u < NPT; ++u) {
                 idx[u] += (L1 == 1 ? x[u] : div_by_width(x[u], L1, rL1)) * scale;
+                inside[u] = inside[u] && x[u] < lim;                    // region [0, nb L1)
+            }
             scale *= nb;
         }
 #pragma unroll
         for (int u = 0; u < NPT; ++u) {
-            if (q0 + u >= L0) continue;
+            if (!inside[u]) continue;
             if (SMEM)
                 atomicAdd(sh + idx[u], 1u);
             else
@@ -169,12 +177,13 @@ pattern_const_kernel(DevInst P, ExpProg pg, DevInst Pd, ExpProg pgd, uint32_t b,
 }
 
 int launch_pattern_const(const DevInst &P, const ExpProg &pg, const DevInst &Pd, const ExpProg &pgd,
-                         uint32_t b, uint64_t c_lo, uint64_t L0, int D, uint32_t nb, uint64_t *hist,
-                         void *stream, std::string *err)
+                         uint32_t b, uint64_t c_lo, uint64_t L0, int D, uint32_t nb, uint32_t L1r,
+                         uint64_t *hist, void *stream, std::string *err)
 {
     constexpr int NPT = 8;
     const uint32_t n = (uint32_t)P.n;
-    const uint32_t L1 = (uint32_t)((n + (uint64_t)nb - 1) / nb);
+    const uint32_t L1 = L1r ? L1r : (uint32_t)((n + (uint64_t)nb - 1) / nb);
+    const uint64_t lim = (uint64_t)nb * L1;                 // >= n for the whole range
     const uint32_t rL1 = L1 >= 2 ? (uint32_t)((1ull << 32) / L1) : 0u;
     uint32_t bins = 1;
     for (int d = 1; d < D; ++d) bins *= nb;
@@ -192,10 +201,10 @@ int launch_pattern_const(const DevInst &P, const ExpProg &pg, const DevInst &Pd,
     if (grid == 0) return PHPRNG_OK;
     if (smem)
         pattern_const_kernel<NPT, true><<<(unsigned)grid, 256, bins * 4, (cudaStream_t)stream>>>(
-            P, pg, Pd, pgd, b, c_lo, L0, D, nb, L1, rL1, bins, (unsigned long long *)hist);
+            P, pg, Pd, pgd, b, c_lo, L0, D, nb, L1, rL1, lim, bins, (unsigned long long *)hist);
     else
         pattern_const_kernel<NPT, false><<<(unsigned)grid, 256, 0, (cudaStream_t)stream>>>(
-            P, pg, Pd, pgd, b, c_lo, L0, D, nb, L1, rL1, bins, (unsigned long long *)hist);
+            P, pg, Pd, pgd, b, c_lo, L0, D, nb, L1, rL1, lim, bins, (unsigned long long *)hist);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         *err = std::string("pattern_const_kernel launch: ") + cudaGetErrorString(e);
@@ -205,12 +214,14 @@ int launch_pattern_const(const DevInst &P, const ExpProg &pg, const DevInst &Pd,
 }
 
 int launch_pattern(const DevInst &P, const ExpProg &pg, const SkipConst &sk, const uint32_t *mtab,
-                   uint64_t L0, int D, uint32_t nb, uint64_t *hist, void *stream, std::string *err)
+                   uint64_t L0, int D, uint32_t nb, uint32_t L1r, uint64_t *hist, void *stream,
+                   std::string *err)
 {
     constexpr int NPT = 8;
     cudaStream_t s = (cudaStream_t)stream;
     const uint32_t n = (uint32_t)P.n;
-    const uint32_t L1 = (uint32_t)((n + (uint64_t)nb - 1) / nb);
+    const uint32_t L1 = L1r ? L1r : (uint32_t)((n + (uint64_t)nb - 1) / nb);
+    const uint64_t lim = (uint64_t)nb * L1;                 // >= n for the whole range
     const uint32_t rL1 = L1 >= 2 ? (uint32_t)((1ull << 32) / L1) : 0u;
     uint64_t bins = 1;
     for (int d = 1; d < D; ++d) bins *= nb;
@@ -242,10 +253,10 @@ int launch_pattern(const DevInst &P, const ExpProg &pg, const SkipConst &sk, con
         if (grid > cap) grid = cap;
         if (smem)
             pattern_kernel<NPT, true><<<(unsigned)grid, 256, bins * 4, s>>>(P, pg, sk, mtab + q0, lq, D, nb,
-                                                                           L1, rL1, (uint32_t)bins, h32);
+                                                                           L1, rL1, lim, (uint32_t)bins, h32);
         else
             pattern_kernel<NPT, false><<<(unsigned)grid, 256, 0, s>>>(P, pg, sk, mtab + q0, lq, D, nb, L1,
-                                                                     rL1, (uint32_t)bins, h32);
+                                                                     rL1, lim, (uint32_t)bins, h32);
         fold_counts_kernel<<<(unsigned)fold_grid, 256, 0, s>>>(h32, (unsigned long long *)hist, bins);
         e = cudaGetLastError();
     }

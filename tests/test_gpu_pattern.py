@@ -90,3 +90,59 @@ def test_pattern_const_whole_period_unit_skip(ph, torch):
     L1 = -(-n // nb)
     want = np.array([min(L1, n - k * L1) for k in range(nb)], dtype=np.uint64)
     assert np.array_equal(h, want)
+
+
+@pytest.mark.parametrize("n,p,e,D,nb,L1", [(1019, 509, 3, 2, 8, 37), (1031, 103, 7, 3, 5, 100),
+                                           (4294967087, 65537, 9, 2, 64, 1 << 20),
+                                           (4294967087, 65537, 9, 3, 4, 1 << 28)])
+def test_pattern_region_matches_oracle(ph, torch, n, p, e, D, nb, L1):
+    """Regions of cells of width L1 (tuples with a successor at or above
+    nb L1 left out), pseudorandom and unit skip, against the oracle."""
+    from test_gpu_parity import primitive_root
+    a = primitive_root(p)
+    c_lo, L0 = (0, n) if n < 5000 else (77, 24)
+    hist = torch.zeros(nb ** (D - 1), dtype=torch.int64, device="cuda")
+    ph.phprng_pattern_region(n, e, p, a, c_lo, L0, D, nb, L1, hist)
+    torch.cuda.synchronize()
+    assert np.array_equal(hist.cpu().numpy().view(np.uint64),
+                          oracle.pattern_region_hist(n, e, p, a, c_lo, L0, D, nb, L1))
+    hist.zero_()
+    L0c = min(L0 * 50, n - c_lo)
+    ph.phprng_pattern_const_region(n, e, 1, c_lo, L0c, D, nb, L1, hist)
+    torch.cuda.synchronize()
+    assert np.array_equal(hist.cpu().numpy().view(np.uint64),
+                          oracle.pattern_const_region_hist(n, e, 1, c_lo, L0c, D, nb, L1))
+    with pytest.raises(ph.PhprngError):
+        ph.phprng_pattern_region(n, e, p, a, c_lo, L0, D, nb, 0, hist)
+
+
+def test_pattern_region_paper_figures(ph, torch):
+    """The paper's figure regions: Fig. 2's 16 cells of (2^18)^2 for the unit
+    skip with n = 2^32 - 5, e = 9 equal the oracle's; Fig. 3's 2^7 x 2^7
+    square (pseudorandom skip, n = 4294967087, p = 2^31 - 1, e = 9): every
+    pair at most once, none on the diagonal, about half the pairs present;
+    Fig. 4's 2^9 x 2^16 x 2^16 slab in 16 subslabs, each near 16."""
+    n2 = 4294967291
+    h = torch.zeros(4, dtype=torch.int64, device="cuda")
+    for i in range(4):
+        h.zero_()
+        ph.phprng_pattern_const_region(n2, 9, 1, i << 18, 1 << 18, 2, 4, 1 << 18, h)
+        torch.cuda.synchronize()
+        assert np.array_equal(h.cpu().numpy().view(np.uint64),
+                              oracle.pattern_const_region_hist(n2, 9, 1, i << 18, 1 << 18, 2, 4, 1 << 18))
+    n, p, a, e = 4294967087, 2147483647, 784588716, 9
+    sq = np.zeros((128, 128), dtype=np.int64)
+    row = torch.zeros(128, dtype=torch.int64, device="cuda")
+    for c0 in range(128):
+        row.zero_()
+        ph.phprng_pattern_region(n, e, p, a, c0, 1, 2, 128, 1, row)
+        torch.cuda.synchronize()
+        sq[c0] = row.cpu().numpy()
+    assert sq.max() <= 1 and np.trace(sq) == 0
+    rho = (p - 1) / n                                   # about 0.5
+    assert abs(sq.sum() - rho * 128 * 128) < 6 * (rho * (1 - rho) * 128 * 128) ** 0.5
+    slab = torch.zeros(16, dtype=torch.int64, device="cuda")
+    ph.phprng_pattern_region(n, e, p, a, 0, 1 << 9, 3, 4, 1 << 14, slab)
+    torch.cuda.synchronize()
+    cells = slab.cpu().numpy()
+    assert cells.sum() > 0 and abs(cells.mean() - 16) < 6 * 4 / 4 and cells.max() < 16 + 6 * 4
