@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=64)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--modes", default="fused,serial,interstream,small_e,pattern,fourier,wide64,batched,served",
+    ap.add_argument("--modes", default="fused,serial,interstream,small_e,pattern,fourier,figures,wide64,batched,served",
                     help="comma-separated extra measurements after the headline, or 'none'")
     return ap.parse_args()
 
@@ -276,6 +276,39 @@ def mode_pattern(ph, torch, stream, L0=128):
             "exponentiations_per_s": 2 * points / ms * 1e3,
             "workload": "paper's pattern instance, D = 3, L0 = 2^7, 2^24 volumes (2^38 points)",
             "chi2_z": (chi2 - dof) / (2 * dof) ** 0.5}
+
+
+def mode_figures(ph, torch, stream):
+    """The settings of the paper's pattern figures as tables, from the
+    full-period region calls: Fig. 2 (unit skip, n = 2^32 - 5, e = 9; 16 cells
+    of (2^18)^2 near the origin), Fig. 3 (pseudorandom skip, n = 4294967087,
+    p = 2^31 - 1, a = 784588716, e = 9; the 2^7 x 2^7 square: pairs present,
+    most in one cell, on the diagonal) and Fig. 4 (the same instance; the
+    2^9 x 2^16 x 2^16 slab in 16 subslabs)."""
+    t0 = time.perf_counter()
+    fig2 = []
+    h = torch.zeros(4, dtype=torch.int64, device="cuda")
+    for i in range(4):
+        h.zero_()
+        ph.phprng_pattern_const_region(4294967291, 9, 1, i << 18, 1 << 18, 2, 4, 1 << 18, h, stream)
+        torch.cuda.synchronize()
+        fig2.append([int(v) for v in h.cpu().numpy()])
+    n, p, a, e = 4294967087, 2147483647, 784588716, 9
+    sq = torch.zeros((128, 128), dtype=torch.int64, device="cuda")
+    for c0 in range(128):
+        ph.phprng_pattern_region(n, e, p, a, c0, 1, 2, 128, 1, sq[c0], stream)
+    torch.cuda.synchronize()
+    sqn = sq.cpu().numpy()
+    slab = torch.zeros(16, dtype=torch.int64, device="cuda")
+    ph.phprng_pattern_region(n, e, p, a, 0, 1 << 9, 3, 4, 1 << 14, slab, stream)
+    torch.cuda.synchronize()
+    fig4 = slab.cpu().numpy().reshape(4, 4)
+    return {"seconds": time.perf_counter() - t0,
+            "fig2_cells_ck_rows_ck1_cols": fig2,
+            "fig3_pairs_present": int(sqn.sum()), "fig3_max_per_pair": int(sqn.max()),
+            "fig3_on_diagonal": int(np.trace(sqn)), "fig3_expected": 128 * 128 * (p - 1) / n,
+            "fig4_subslabs_ck1_rows_ck2_cols": [[int(v) for v in r] for r in fig4.T],
+            "fig4_expected_per_cell": (1 << 41) / 16 * (p - 1) / n ** 2}
 
 
 def mode_interstream(ph, torch, ctx, N, per, stream):
@@ -629,6 +662,7 @@ def main():
                          ("small_e", lambda: mode_small_e(ph, torch, stream, PEAK_TMULS)),
                          ("pattern", lambda: mode_pattern(ph, torch, stream)),
                          ("fourier", lambda: mode_fourier(ph, torch, stream)),
+                         ("figures", lambda: mode_figures(ph, torch, stream)),
                          ("wide64", lambda: mode_wide64(ph, torch, stream, PEAK_TMULS)),
                          ("batched", lambda: mode_batched(ph, torch, stream)),
                          ("served", lambda: mode_served(ph, torch))):
