@@ -162,8 +162,10 @@ int phprng_generate(phprng_ctx *ctx, uint64_t first, uint64_t num_inst, uint64_t
  * that every device holds while the library is loaded.  Limit:
  * 2 * ceil(num_inst/8) * per_inst <= 2^20, else PHPRNG_EINVAL naming the
  * limit.  stats_out must be device memory (num_inst phprng_stats).  The first
- * call on a device looks up the array's device address once (make that
- * first call before any CUDA stream capture).  All calls share the array and
+ * call on a device looks up the array's device address once and keeps it for
+ * the rest of the process (make that first call before any CUDA stream
+ * capture); the address belongs to the device's primary context, so the
+ * library must not be used on a device after cudaDeviceReset there.  All calls share the array and
  * leave their rows in it; every row is fully written before it is read, so
  * nothing needs clearing, but calls that overlap on the GPU (unordered
  * streams) race on it.  Results, state updates and errors are otherwise
@@ -187,8 +189,12 @@ int phprng_skip(phprng_ctx *ctx, const uint64_t *inst_ids, const uint64_t *k, ui
  * without storing them: each stream's numbers of this call, in order, form
  * consecutive non-overlapping D-tuples (R_{t+1}, ..., R_{t+D}) (a remainder of
  * fewer than D numbers at the end of the call is left out); coordinate d falls
- * in bin b_d = floor(B R) (equal to floor(B (c+1)/(n+1))), and each tuple adds
- * one to hist[b_0 + B b_1 + ... + B^(D-1) b_(D-1)].  hist: device memory,
+ * in bin b_d = floor(B R), R the double of Eq. 9d and B R one IEEE double
+ * product (truncated), and each tuple adds one to
+ * hist[b_0 + B b_1 + ... + B^(D-1) b_(D-1)].  That bin equals the exact
+ * floor(B (c+1)/(n+1)) except where (c+1)/(n+1) is exactly k/B and the double
+ * product falls below k (B = 100: k = 29, 57, 58), where it is k - 1, as the
+ * double arithmetic gives it.  hist: device memory,
  * B^D uint64 counters, added to (clear it first); all streams of the call
  * share it.  The paper's sizes: D = 1, B = 2^20; D = 2, B = 2^10; D = 3,
  * B = 100; D = 4, B = 32; D = 5, B = 16.  Limits: 1 <= D <= 8, B a power of
@@ -213,7 +219,8 @@ int phprng_poker_test(phprng_ctx *ctx, uint64_t first, uint64_t num_inst, uint64
 /* Collision-test consumer (Tests section: 2^14 numbers into 2^20 bins) for
  * 32-bit moduli.  Each stream's numbers of the call form consecutive
  * segments of S numbers (a remainder of fewer than S is left out); in a
- * segment, a number whose bin floor(B R) already holds an earlier number of
+ * segment, a number whose bin floor(B R) (the double product, as in
+ * phprng_serial_test) already holds an earlier number of
  * the segment is a collision, and the segment's collision count C adds one to
  * hist[min(C, H-1)].  Expected count per segment S - B (1 - (1 - 1/B)^S)
  * (about 127.9 at the paper's S = 2^14, B = 2^20).  hist: device memory, H
@@ -244,7 +251,8 @@ int phprng_runs_test(phprng_ctx *ctx, uint64_t first, uint64_t num_inst, uint64_
  * that sequence of num_inst * per_inst numbers is cut into consecutive
  * non-overlapping D-tuples (the last num_inst * per_inst mod D numbers are left
  * out); each tuple adds one to hist[b_1 + B b_2 + ... + B^(D-1) b_D], b =
- * floor(B R).  Limits as phprng_serial_test: 1 <= D <= 8, B a power of two up
+ * floor(B R) (the double product, as in phprng_serial_test).  Limits as
+ * phprng_serial_test: 1 <= D <= 8, B a power of two up
  * to 2^20 or at most 2^16, B^D <= 2^24, 32-bit instances.  hist: device
  * memory, B^D uint64 counters, added to.  Streams advance by per_inst.
  * Asynchronous on cuda_stream; scratch of about 2^25 numbers (ciphertexts and

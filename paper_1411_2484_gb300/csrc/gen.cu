@@ -496,7 +496,9 @@ static std::mutex g_fixed_edge_mu;
 uint64_t gen32_fixed_edge_words() { return kFixedEdgeWords; }
 
 // The host name g_fixed_edge is only a stand-in for the device array: its
-// device address is looked up once per device, with that device current.
+// device address is looked up once per device, with that device current, and
+// kept for the process (it is the primary context's; a cudaDeviceReset of the
+// device would leave it stale, so the library is not used past one).
 static int fixed_edge_address(int dev, uint32_t **out, std::string *err)
 {
     if (dev < 0 || dev >= 64) {

@@ -16,16 +16,34 @@
 
 namespace phprng {
 
-// floor(B (c+1)/(n+1)) for n < 2^32, from integers: with vN = (c+1)
-// 2^(32-ybits) < yN and r = floor(B 2^32 / yN), floor(vN r / 2^32) is the bin or
-// one below it (r is short of B 2^32 / yN by less than 1 and vN < 2^32), and
-// one exact comparison decides.
+// The bin of a number, floor(B R) taken on the double R = RN((c+1)/(n+1))
+// (Eq. 9d) with one IEEE product, RN(R B), then truncation -- what a program
+// binning the generator's doubles computes.  For n < 2^32 and B <= 2^20 this
+// is the exact floor(B (c+1)/(n+1)) except when (c+1)/(n+1) is exactly k/B:
+// otherwise B (c+1)/(n+1) is at least 1/(n+1) >= 2^-32 from an integer, while
+// the two roundings move it by less than B 2^-52 <= 2^-32.  At an exact k/B
+// the double product can land just below k (B = 100: k = 29, 57, 58, where
+// RN(RN(k/100) 100) < k), so that case is decided by the double arithmetic
+// itself.
+//
+// The exact bin from integers: with vN = (c+1) 2^(32-ybits) < yN and
+// r = floor(B 2^32 / yN), floor(vN r / 2^32) is the bin or one below it (r is
+// short of B 2^32 / yN by less than 1 and vN < 2^32), and one exact comparison
+// decides.  The remainder B vN - k yN of the exact quotient k lies in
+// [0, 2 yN) before that correction; its low word is 0 or yN only when it is 0,
+// yN or 2^32, so those two values send the number to the double arithmetic
+// (always correct, about 1 number in 2^31 at random).
 __device__ __forceinline__ uint32_t serial_bin(uint32_t c, uint32_t yN, uint32_t ybits, uint32_t r,
                                                uint32_t B)
 {
     const uint32_t vN = (c + 1) << (32 - ybits);
     uint32_t est = umulhi32(vN, r);
+    const uint32_t rlo = vN * B - est * yN;
     if ((uint64_t)(est + 1) * yN <= (uint64_t)vN * B) ++est;
+    if (rlo == 0u || rlo == yN) {
+        const double R = __ddiv_rn((double)(c + 1), (double)(yN >> (32 - ybits)));
+        est = (uint32_t)__dmul_rn(R, (double)B);
+    }
     return est;
 }
 

@@ -93,6 +93,7 @@ def test_pattern_const_whole_period_unit_skip(ph, torch):
 
 
 @pytest.mark.parametrize("n,p,e,D,nb,L1", [(1019, 509, 3, 2, 8, 37), (1031, 103, 7, 3, 5, 100),
+                                           (1019, 509, 3, 2, 64, 1), (1019, 509, 3, 3, 8, 1),
                                            (4294967087, 65537, 9, 2, 64, 1 << 20),
                                            (4294967087, 65537, 9, 3, 4, 1 << 28)])
 def test_pattern_region_matches_oracle(ph, torch, n, p, e, D, nb, L1):
@@ -146,3 +147,18 @@ def test_pattern_region_paper_figures(ph, torch):
     torch.cuda.synchronize()
     cells = slab.cpu().numpy()
     assert cells.sum() > 0 and abs(cells.mean() - 16) < 6 * 4 / 4 and cells.max() < 16 + 6 * 4
+
+
+def test_pattern_region_three_dimensional_slab_matches_oracle(ph, torch):
+    """Fig. 4's construction (D = 3, c0 in [0, 2^9), the paper's instance
+    n = 4294967087, e = 9) with a skip generator small enough for the oracle
+    (p = 65537, a = 3) and cells of 2^22, so that about 500 points fall in the
+    4 x 4 subslabs: every counter equals the oracle's (the region limit and the
+    cell width of the slab call, checked exactly)."""
+    n, e, p, a = 4294967087, 9, 65537, 3
+    hist = torch.zeros(16, dtype=torch.int64, device="cuda")
+    ph.phprng_pattern_region(n, e, p, a, 0, 1 << 9, 3, 4, 1 << 22, hist)
+    torch.cuda.synchronize()
+    want = oracle.pattern_region_hist(n, e, p, a, 0, 1 << 9, 3, 4, 1 << 22)
+    assert want.sum() > 300
+    assert np.array_equal(hist.cpu().numpy().view(np.uint64), want)

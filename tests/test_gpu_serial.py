@@ -296,3 +296,193 @@ def test_interstream_paper_scale_chi_square(ph, torch):
         assert abs(z) < 6, z
     finally:
         ph.phprng_destroy(ctx)
+
+
+# ------------------------------------------------------------ bins at exact multiples k/B
+# floor(B R) is taken on the double R with one IEEE product; at an exact
+# (c+1)/(n+1) = k/B that product can fall below k (B = 100: k = 29, 57, 58 on
+# n = 2147483999, where n + 1 = 100 * 21474840).  The streams below are seeded
+# so that such ciphertexts come out at chosen positions.
+N100, P31, A31 = 2147483999, 2147483647, 784588716
+
+
+def _is_prime(q):
+    if q < 2:
+        return False
+    for d in (2, 3, 5, 7, 11, 13):
+        if q % d == 0:
+            return q == d
+    d, r = q - 1, 0
+    while d % 2 == 0:
+        d, r = d // 2, r + 1
+    for b in (2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37):
+        x = pow(b, d, q)
+        if x in (1, q - 1):
+            continue
+        for _ in range(r - 1):
+            x = x * x % q
+            if x == q - 1:
+                break
+        else:
+            return False
+    return True
+
+
+def _prime_with_divisor(B, start):
+    n = start + (-1 - start) % B
+    while not _is_prime(n):
+        n += B
+    return n
+
+
+def _coprime_exponent(n, seed):
+    rng = np.random.default_rng(seed)
+    while True:
+        e = int(rng.integers(3, n - 2))
+        if np.gcd(e, n - 1) == 1:
+            return e
+
+
+def _seed_for(n, e, k, c, s0):
+    """m0 such that number k (1-based) of the stream (n, e, P31, A31, m0, s0)
+    is the ciphertext c: m_k = c^d (Eq. 2) = m0 + s_1 + .. + s_k (Eq. 6b)."""
+    d = pow(e, -1, n - 1)
+    ssum, s = 0, s0
+    for _ in range(k):
+        s = A31 * s % P31
+        ssum += s
+    return (pow(c, d, n) - ssum) % n
+
+
+def _seed_pair(n, e, k, c_first, c_second):
+    """(m0, s0) with number k equal to c_first and number k + 1 to c_second:
+    the skip s_(k+1) must be the message difference, so it has to lie in
+    [1, p-1]; returns None when it does not."""
+    d = pow(e, -1, n - 1)
+    delta = (pow(c_second, d, n) - pow(c_first, d, n)) % n
+    if not 1 <= delta < P31:
+        return None
+    s0 = delta * pow(A31, -(k + 1), P31) % P31
+    return _seed_for(n, e, k, c_first, s0), s0
+
+
+def _exact_bins(c, n, B):
+    return (B * (np.asarray(c, dtype=object) + 1)) // (n + 1)
+
+
+def _exact_multiple_instances():
+    """Streams on n = 2147483999 whose numbers at chosen positions (first
+    number, inside a warp group, across a group boundary) are the three
+    ciphertexts with a low double bin, for a straight-chain and a windowed
+    exponent, plus ordinary streams."""
+    rows = []
+    targets = [(21474840 * k - 1) for k in (29, 57, 58)]
+    for e in (3, _coprime_exponent(N100, 7)):
+        for j, (k, c) in enumerate(zip((1, 77, 256), targets)):
+            s0 = 1000 + 17 * j
+            rows.append([N100, e, P31, A31, _seed_for(N100, e, k, c, s0), s0])
+    rows = np.array(rows, dtype=np.uint64)
+    extra = workloads.instance_rows(workloads.draw_instances(5, seed=4242))
+    return np.concatenate([rows, extra])
+
+
+def _ctx_from_rows(ph, rows):
+    return ph.phprng_create(32, rows, ph.PHPRNG_ALLOW_SHARED_N)
+
+
+@pytest.mark.parametrize("D", [1, 3])
+def test_serial_bins_at_exact_multiples_match_oracle(ph, torch, D):
+    """The paper's B = 100 (D = 3 is its three-dimensional serial test) on
+    streams that emit the three low-double-bin ciphertexts: every counter
+    equals the oracle's, which differs from exact-quotient binning."""
+    rows = _exact_multiple_instances()
+    per = 1000
+    ctx = _ctx_from_rows(ph, rows)
+    try:
+        hist = torch.zeros(100 ** D, dtype=torch.int64, device="cuda")
+        ph.phprng_serial_test(ctx, 0, len(rows), per, D, 100, hist)
+        c, _, _, _ = oracle.generate_many(rows, per, threads=THREADS, want_r=False)
+        want = np.zeros(100 ** D, dtype=np.uint64)
+        for k in range(len(rows)):
+            oracle.serial_hist(c[k], int(rows[k, 0]), D, 100, want)
+        # the forced numbers are there, and exact binning would differ
+        assert {int(x) for x in c[:6].ravel()} >= {21474840 * k - 1 for k in (29, 57, 58)}
+        exact = np.zeros(100 ** D, dtype=np.uint64)
+        for k in range(len(rows)):
+            b = _exact_bins(c[k], int(rows[k, 0]), 100)
+            nt = per // D
+            idx = sum(b[d:nt * D:D] * 100 ** d for d in range(D))
+            np.add.at(exact, np.array(idx, dtype=np.int64), 1)
+        assert not np.array_equal(exact, want)
+        torch.cuda.synchronize()
+        assert np.array_equal(hist.cpu().numpy().view(np.uint64), want)
+    finally:
+        ph.phprng_destroy(ctx)
+
+
+def test_interstream_bins_at_exact_multiples_match_oracle(ph, torch):
+    """The interleaved order over the same streams, pairs into 100 x 100 bins."""
+    rows = _exact_multiple_instances()
+    per = 600
+    ctx = _ctx_from_rows(ph, rows)
+    try:
+        for D in (1, 2):
+            hist = torch.zeros(100 ** D, dtype=torch.int64, device="cuda")
+            ph.phprng_interstream_serial_test(ctx, 0, len(rows), per, D, 100, hist)
+            c, _, st, _ = oracle.generate_many(rows, per, threads=THREADS, want_r=False)
+            want = oracle.interstream_serial_hist(c, rows[:, 0], D, 100)
+            torch.cuda.synchronize()
+            assert np.array_equal(hist.cpu().numpy().view(np.uint64), want)
+            rows = rows.copy()
+            rows[:, 4:6] = st
+            if D == 1:
+                exact = np.zeros(100, dtype=np.uint64)
+                for k in range(len(rows)):
+                    np.add.at(exact, np.array(_exact_bins(c[k], int(rows[k, 0]), 100), dtype=np.int64), 1)
+                assert not np.array_equal(exact, want)
+    finally:
+        ph.phprng_destroy(ctx)
+
+
+def test_collision_bins_at_exact_multiples_match_oracle(ph, torch):
+    """Segments of 256 into B = 60000 bins (sparse, so a collision is rare):
+    in each forced stream an earlier number of exact bin k - 1 is followed by
+    the exact multiple k/B whose double product falls to bin k - 1 -- one
+    collision that exact binning would not count."""
+    B = 60000
+    n = _prime_with_divisor(B, 3_000_000_000)
+    t = (n + 1) // B
+    low = [k for k in range(1, B) if (k / B) * B < k][:40]
+    rows = []
+    for e in (3, _coprime_exponent(n, 9)):
+        for pos in (5, 130, 255):                   # the pair inside a group, across lanes, across groups
+            for k in low:
+                found = None
+                for off in range(1, 2000):
+                    found = _seed_pair(n, e, pos, (k - 1) * t + off, k * t - 1)
+                    if found:
+                        break
+                if found:
+                    rows.append([n, e, P31, A31, found[0], found[1]])
+                    break
+    assert len(rows) == 6
+    rows = np.array(rows, dtype=np.uint64)
+    S, H, per = 256, 8, 512
+    ctx = _ctx_from_rows(ph, rows)
+    try:
+        hist = torch.zeros(H, dtype=torch.int64, device="cuda")
+        ph.phprng_collision_test(ctx, 0, len(rows), per, S, B, H, hist)
+        c, _, _, _ = oracle.generate_many(rows, per, threads=THREADS, want_r=False)
+        want = np.zeros(H, dtype=np.uint64)
+        exact = np.zeros(H, dtype=np.uint64)
+        for k in range(len(rows)):
+            oracle.collision_hist(c[k], n, S, B, H, want)
+            b = _exact_bins(c[k], n, B)
+            for g in range(0, per, S):
+                seg = list(b[g:g + S])
+                exact[min(S - len(set(seg)), H - 1)] += 1
+        assert not np.array_equal(exact, want)
+        torch.cuda.synchronize()
+        assert np.array_equal(hist.cpu().numpy().view(np.uint64), want)
+    finally:
+        ph.phprng_destroy(ctx)

@@ -47,6 +47,20 @@ MUTANTS = {
     "serial_scale_order": ("scale *= B;", "scale *= B - 1;"),
     "serial_bin_scale": ("uint64_t b = (uint64_t)(R * (double)B);",
                          "uint64_t b = (uint64_t)(R * (double)(B - 1));"),
+    "serial_exact_integer_bin": (
+        "double R = or_real(c[t * (uint64_t)D + (uint64_t)d], n);\n            uint64_t b = (uint64_t)(R * (double)B);",
+        "double R = or_real(c[t * (uint64_t)D + (uint64_t)d], n);\n"
+        "            uint64_t b = (uint64_t)(((u128)B * (c[t * (uint64_t)D + (uint64_t)d] + 1)) / ((u128)n + 1));"
+        " (void)R;"),
+    "interstream_exact_integer_bin": (
+        "double R = or_real(c[a * L + j], nmod[a]);\n            uint64_t b = (uint64_t)(R * (double)B);",
+        "double R = or_real(c[a * L + j], nmod[a]);\n"
+        "            uint64_t b = (uint64_t)(((u128)B * (c[a * L + j] + 1)) / ((u128)nmod[a] + 1)); (void)R;"),
+    "collision_exact_integer_bin": (
+        "uint64_t b = (uint64_t)(or_real(c[k], n) * (double)B);\n            if (b >= B) b = B - 1;\n"
+        "            if (seen[b]) ++C;",
+        "uint64_t b = (uint64_t)(((u128)B * (c[k] + 1)) / ((u128)n + 1));\n            if (b >= B) b = B - 1;\n"
+        "            if (seen[b]) ++C;"),
     "interstream_transposed": ("double R = or_real(c[a * L + j], nmod[a]);",
                                "double R = or_real(c[(j * Np + a) % (Np * L)], nmod[a]);"),
     "interstream_wrong_modulus": ("double R = or_real(c[a * L + j], nmod[a]);",

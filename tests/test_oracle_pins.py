@@ -337,20 +337,117 @@ def test_generate_many_matches_generate(oracle_mod):
 
 
 # ------------------------------------------------------------ serial tests
+def double_bin(c, n, B):
+    """floor(B R) on the double: R = (c+1)/(n+1) correctly rounded (Python's
+    true division of integers), then one IEEE double product by B, truncated."""
+    return int(((c + 1) / (n + 1)) * B)
+
+
+def low_exact_multiples(B):
+    """k in 1..B-1 whose double product RN(RN(k/B) B) falls below k."""
+    return [k for k in range(1, B) if (k / B) * B < k]
+
+
 @pytest.mark.parametrize("n,p,e", TINY[:6])
 @pytest.mark.parametrize("B", [3, 8, 100])
 def test_serial_1d_full_period(oracle_mod, n, p, e, B):
     """One-dimensional frequency test over a full period: every c appears
-    p-1 times, so bin b holds p-1 times the count of c with floor(B (c+1)/(n+1))
-    = b (exact rationals)."""
+    p-1 times, so bin b holds p-1 times the count of c with floor(B R) = b; for
+    these moduli no (c+1)/(n+1) is an exact k/B below its double product, so
+    the bins are also the exact rationals floor(B (c+1)/(n+1))."""
     a = primitive_root(p)
     P = n * (p - 1)
     c, _, _ = oracle_mod.generate(n, e, p, a, 2 % n, 1, P)
     hist = oracle_mod.serial_hist(c, n, 1, B)
     expect = np.zeros(B, dtype=np.int64)
     for cc in range(n):
+        assert double_bin(cc, n, B) == (B * (cc + 1)) // (n + 1)
         expect[(B * (cc + 1)) // (n + 1)] += p - 1
     assert np.array_equal(hist.astype(np.int64), expect)
+
+
+def test_exact_multiples_whose_double_product_falls_below():
+    """The double product RN(RN(k/B) B) is below k only at a few exact
+    multiples: none for B = 10, 1000 and 3 2^j, k = 29, 57, 58 for the paper's
+    three-dimensional B = 100 (RN(0.29) 100 = 28.999999999999996)."""
+    assert low_exact_multiples(100) == [29, 57, 58]
+    assert (29 / 100) * 100 == 28.999999999999996
+    for B in [10, 1000] + [3 << j for j in range(11)] + [1 << j for j in range(21)]:
+        assert low_exact_multiples(B) == [], B
+
+
+# n = 2147483999 is prime with n + 1 = 100 * 21474840, so (c+1)/(n+1) = k/100
+# exactly for c = 21474840 k - 1.
+N100 = 2147483999
+B100_CASES = [(622770359, 28), (1224065879, 56), (1245540719, 57)]   # k = 29, 57, 58
+
+
+def _prime_with_divisor(B, start):
+    """The first prime n >= start with B dividing n + 1 (Python Rabin-Miller by pow)."""
+    def is_prime(q):
+        if q < 2 or any(q % d == 0 for d in (2, 3, 5, 7, 11, 13)):
+            return q in (2, 3, 5, 7, 11, 13)
+        d, r = q - 1, 0
+        while d % 2 == 0:
+            d //= 2
+            r += 1
+        for b in (2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37):
+            x = pow(b, d, q)
+            if x in (1, q - 1):
+                continue
+            for _ in range(r - 1):
+                x = x * x % q
+                if x == q - 1:
+                    break
+            else:
+                return False
+        return True
+    n = start + (-1 - start) % B
+    while not is_prime(n):
+        n += B
+    return n
+
+
+@pytest.mark.parametrize("B", [10, 100, 1000, 3 << 5, 3 << 10])
+def test_serial_bins_at_exact_multiples_follow_the_double(oracle_mod, B):
+    """Every exact multiple k/B of a prime with B | n + 1, and the number just
+    below it: bin k, except k - 1 where the double product falls below k."""
+    assert N100 == _prime_with_divisor(100, N100)
+    n = N100 if B == 100 else _prime_with_divisor(B, 3_000_000_000)
+    low = set(low_exact_multiples(B))
+    t = (n + 1) // B
+    ks = range(1, B) if B <= 1000 else list(range(1, 40)) + list(range(B - 40, B))
+    cs, want = [], []
+    for k in ks:
+        cs += [k * t - 1, k * t - 2]
+        want += [k - 1 if k in low else k, k - 1]
+    for c, b in zip(cs, want):
+        assert double_bin(c, n, B) == b
+    h = oracle_mod.serial_hist(np.array(cs, dtype=np.uint64), n, 1, B)
+    expect = np.bincount(np.array(want), minlength=B).astype(np.uint64)
+    assert np.array_equal(h, expect)
+
+
+def test_double_bin_cases_of_the_three_dimensional_serial_test(oracle_mod):
+    """The paper's D = 3, B = 100 serial test on n = 2147483999: the three
+    exact multiples with a low double product each fall one bin below the
+    exact quotient, in the serial, interstream and collision binnings."""
+    for c, b in B100_CASES:
+        assert (100 * (c + 1)) % (N100 + 1) == 0 and 100 * (c + 1) // (N100 + 1) == b + 1
+        assert double_bin(c, N100, 100) == b
+        h = oracle_mod.serial_hist(np.array([c], dtype=np.uint64), N100, 1, 100)
+        assert int(h[b]) == 1
+        # a triple: (c, c, 0) -> b + 100 b + 0
+        h3 = oracle_mod.serial_hist(np.array([c, c, 0], dtype=np.uint64), N100, 3, 100)
+        assert int(h3[b + 100 * b]) == 1
+        hi = oracle_mod.interstream_serial_hist(np.array([[c, 5], [7, c]], dtype=np.uint64),
+                                                np.array([N100, N100], dtype=np.uint64), 1, 100)
+        assert int(hi[b]) == 2
+        # collision: c shares its double bin with a number of exact bin b
+        other = b * ((N100 + 1) // 100) + 12345
+        assert (100 * (other + 1)) // (N100 + 1) == b
+        hc = oracle_mod.collision_hist(np.array([other, c], dtype=np.uint64), N100, 2, 100, 3)
+        assert list(hc) == [0, 1, 0]
 
 
 @pytest.mark.parametrize("D,B", [(1, 1 << 20), (2, 1 << 10), (3, 100), (4, 32), (5, 16)])
