@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=64)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--modes", default="fused,serial,interstream,small_e,pattern,fourier,figures,wide64,batched,served",
+    ap.add_argument("--modes", default="fused,serial,interstream,small_e,pattern,fourier,figures,wide64,c0,batched,served",
                     help="comma-separated extra measurements after the headline, or 'none'")
     return ap.parse_args()
 
@@ -69,16 +69,19 @@ def algorithmic_muls(e_values, per_inst):
 
 
 class ClockSampler:
-    """nvidia-smi samples every 200 ms during the timed region."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi samples every 20 ms, started before the warm-up so that its
+    own start-up is over when the timed region begins; stop(t0, t1) keeps the
+    samples whose timestamps fall inside the timed wall-clock window [t0, t1]
+    (the nearest ones when the window is shorter than the sampling period)."""
+    Q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, uuid):
+    def __init__(self, uuid, period_ms=20):
         self.proc = None
         try:
             cmd = ["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
-                   "-lms", "200"]
+                   "-lms", str(period_ms)]
             if uuid:
                 cmd += ["-i", uuid]
             self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
@@ -86,33 +89,56 @@ class ClockSampler:
         except OSError:
             self.proc = None
 
-    def stop(self):
+    @staticmethod
+    def _when(stamp):
+        import datetime
+        try:
+            return datetime.datetime.strptime(stamp.strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
+
+    def stop(self, t0=None, t1=None):
         if not self.proc:
             return None
+        time.sleep(0.05)
         self.proc.terminate()
         try:
             out, _ = self.proc.communicate(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
             out, _ = self.proc.communicate()
-        sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for line in out.splitlines():
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
             try:
-                sm.append(float(f[1]))
-                mx.append(float(f[2]))
+                rows.append((self._when(f[0]), float(f[1]), float(f[2]), f[5:9]))
             except ValueError:
                 continue
-            for nm, v in zip(names, f[5:9]):
+        if not rows:
+            return None
+        inside = [r for r in rows if r[0] is not None and t0 is not None and t0 <= r[0] <= t1]
+        note = "samples inside the timed window"
+        if not inside and t0 is not None:
+            timed_rows = [r for r in rows if r[0] is not None]
+            if timed_rows:
+                mid = 0.5 * (t0 + t1)
+                timed_rows.sort(key=lambda r: abs(r[0] - mid))
+                inside = timed_rows[:2]
+                note = "window shorter than the sampling period: the two samples nearest to it"
+        if not inside:
+            inside, note = rows, "all samples (no timestamps)"
+        reasons = set()
+        for r in inside:
+            for nm, v in zip(names, r[3]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
-        if not sm:
-            return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
-                "samples": len(sm), "reasons": sorted(reasons)}
+        return {"sm_mhz": statistics.median(r[1] for r in inside),
+                "sm_max_mhz": max(r[2] for r in inside),
+                "samples": len(inside), "samples_total": len(rows), "note": note,
+                "reasons": sorted(reasons)}
 
 
 def profile_traffic(kernel):
@@ -238,6 +264,35 @@ def mode_small_e(ph, torch, stream, peak):
     return {"value": prn_s, "unit": "PRNs/s", "ms_per_call": ms,
             "workload": "65,536 safe 32-bit primes, e = 9, x 4,096 numbers per call (R, 2 GiB)",
             "roofline": roof}
+
+
+def mode_c0(ph, torch, stream, peak):
+    """The 4-instance reference workload (4 safe 32-bit primes, random
+    exponents, 2^20 numbers each, c and R stored): four warps' worth of
+    instances, so the call runs as a split launch (every stream cut into
+    chunks after a skip-sum pre-pass, Eq. 6 over chunks)."""
+    from paper_1411_2484_gb300 import workloads
+    name = "pr1_ref_32bit_4x2^20"
+    w = workloads.WORKLOADS[name]
+    inst = workloads.workload_instances(name)
+    N, per = w["instances"], w["per_inst"]
+    ctx = ph.phprng_create(32, inst, ph.PHPRNG_REQUIRE_SAFE_PRIME, stream)
+    try:
+        c = torch.empty(N * per, dtype=torch.int32, device="cuda")
+        r = torch.empty(N * per, dtype=torch.float64, device="cuda")
+        ms = timed(torch, stream, lambda: ph.phprng_generate(ctx, 0, N, per, c, r, None, stream),
+                   20, warmup=3)
+    finally:
+        ph.phprng_destroy(ctx)
+    prn_s = N * per / ms * 1e3
+    muls = algorithmic_muls(inst["e"], per)
+    achieved = muls / (ms * 1e-3) / 1e12
+    return {"value": prn_s, "unit": "PRNs/s", "ms_per_call": ms,
+            "workload": "%s: 4 x 2^20 numbers per call, c (uint32) and R (FP64) stored, "
+                        "split launch (chunk pre-pass + generator)" % name,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T mul32/s",
+                         "frac": achieved / peak, "algorithmic_muls_per_call": muls,
+                         "peak_source": "152 SMs x 64 IMAD/clk x 2070 MHz (unit counts x max clock)"}}
 
 
 def mode_serial(ph, torch, ctx, N, per, stream):
@@ -392,10 +447,11 @@ def mode_wide64(ph, torch, stream, peak):
                          "frac": achieved / peak}}
 
 
-def mode_batched(ph, torch, stream):
+def mode_batched(ph, torch, stream, peak):
     """20,000 instances (16,000 32-bit, 4,000 64-bit), log-uniform lengths in
     [1, 2^20], offsets in [0, 2^40): one graph-replayed persistent launch
-    (autotuned) against one skip+generate launch pair per request."""
+    (autotuned) against one skip+generate launch pair per request, all
+    requests issued back to back on one stream."""
     from paper_1411_2484_gb300 import workloads
     w = workloads.WORKLOADS["batched_20000_mixed"]
     i32 = ph.phprng_draw_instances(32, w["instances32"], w["seed"], ph.PHPRNG_REQUIRE_SAFE_PRIME)
@@ -404,6 +460,14 @@ def mode_batched(ph, torch, stream):
     reqs = workloads.batched_requests(w["instances32"], w["instances64"], w["max_len"],
                                       w["max_offset"], w["seed"] + 2)
     total = int(reqs["len"].sum())
+    # algorithmic multiply halves of the batch (the same count as the plain
+    # launches: binary method + skip, 4 halves per 32-bit product, 20 per
+    # 64-bit one); the skip-ahead to each offset is overhead, not counted
+    e_all = np.concatenate([np.asarray(i32["e"], dtype=np.uint64), np.asarray(i64["e"], dtype=np.uint64)])
+    wide = np.concatenate([np.zeros(len(i32["e"]), bool), np.ones(len(i64["e"]), bool)])
+    muls = 0
+    for (i, off, ln, _, _) in reqs:
+        muls += muls_per_number(int(e_all[int(i)]), bool(wide[int(i)])) * int(ln)
     ctx = ph.phprng_create(0, inst, 0, stream)
     out = {}
     try:
@@ -415,39 +479,59 @@ def mode_batched(ph, torch, stream):
                                                                           ctx=ctx), 5)
         finally:
             ph.phprng_plan_destroy(plan)
+        achieved = muls / (ms * 1e-3) / 1e12
         out = {"value": total / ms * 1e3, "unit": "PRNs/s", "ms_per_launch": ms,
                "numbers": total, "requests": len(reqs), "tuning": tune,
+               "numbers_32bit": int(reqs["len"][~wide[reqs["inst"].astype(np.int64)]].sum()),
+               "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T mul32/s",
+                            "frac": achieved / peak, "algorithmic_muls_per_launch": muls,
+                            "peak_source": "152 SMs x 64 IMAD/clk x 2070 MHz (unit counts x max clock)"},
                "latency_ms": {"p50": ms, "p99": ms,
-                              "note": "all requests are submitted together and complete "
-                                      "within the one launch"}}
+                              "note": "all requests are submitted together; each completes "
+                                      "within the one launch, so completion since submission "
+                                      "is at most the launch time"}}
     finally:
         ph.phprng_destroy(ctx)
-    # one launch per request (skip to the offset, then generate), first 300 requests
+    # one skip + generate launch pair per request, all 20,000 issued back to
+    # back on one stream (no host synchronisation in between); CUDA events
+    # around every pair give each request's own GPU time and its completion
+    # time since the first submission
     ctx = ph.phprng_create(0, inst, 0, stream)
     try:
-        k = 300
-        sub = reqs[:k]
-        r = torch.empty(int(sub["len"].max()), dtype=torch.float64, device="cuda")
-        done = []
+        r = torch.empty(int(reqs["len"].max()), dtype=torch.float64, device="cuda")
+        ph.phprng_skip(ctx, [0], [1], stream)                 # builds the prefix table
         torch.cuda.synchronize()
+        k = len(reqs)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        e0 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
         t0 = time.perf_counter()
-        for (i, off, ln, _, _) in sub:
+        for q, (i, off, ln, _, _) in enumerate(reqs):
+            ev[q][0].record(stream)
             ph.phprng_skip(ctx, [int(i)], [int(off)], stream)
             ph.phprng_generate(ctx, int(i), 1, int(ln), None, r, None, stream)
-            torch.cuda.synchronize()
-            done.append(time.perf_counter() - t0)
-        dt = time.perf_counter() - t0
-        lat = np.array(done) * 1e3
+            ev[q][1].record(stream)
+        issue_s = time.perf_counter() - t0
+        torch.cuda.synchronize()
+        total_ms = e0.elapsed_time(ev[-1][1])
+        own = np.array([a.elapsed_time(b) for a, b in ev])
+        done = np.array([e0.elapsed_time(b) for _, b in ev])
         out["per_instance_launches"] = {
-            "value": float(sub["len"].sum()) / dt, "unit": "PRNs/s", "requests": k,
-            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
-            "note": "first 300 requests, skip + generate per request, issued back to back"}
+            "value": total / total_ms * 1e3, "unit": "PRNs/s", "requests": k,
+            "ms_total": total_ms, "host_issue_s": issue_s,
+            "service_ms": {"p50": float(np.percentile(own, 50)), "p99": float(np.percentile(own, 99))},
+            "completion_since_submit_ms": {"p50": float(np.percentile(done, 50)),
+                                           "p99": float(np.percentile(done, 99))},
+            "note": "all 20,000 requests, skip + generate per request, issued back to back; "
+                    "service = the request's own two launches, completion = since the first "
+                    "submission"}
+        out["batched_over_per_instance"] = out["value"] / out["per_instance_launches"]["value"]
     finally:
         ph.phprng_destroy(ctx)
     return out
 
 
-def mode_served(ph, torch, duration_s=10.0, warm_s=1.0, rate=50000.0, tile=0):
+def mode_served(ph, torch, duration_s=10.0, warm_s=1.0, rate=50000.0, tile=0, capacity=None):
     """1,000,000 32-bit streams, open-loop Poisson arrivals at 50k requests/s,
     sizes min(round(lognormal(ln 4096, 2)), 2^22), admission bounded by 16 GiB
     of outputs; PRNs/s and p50/p99 latency from arrival to completion."""
@@ -488,7 +572,15 @@ def mode_served(ph, torch, duration_s=10.0, warm_s=1.0, rate=50000.0, tile=0):
     meas = (arrivals >= t0 + int(warm_s * 1e9))
     l_ms = lat[meas] / 1e6
     numbers = int(sizes[meas].sum())
+    offered = float(sizes[meas].sum()) / duration_s
     return {"value": numbers / duration_s, "unit": "PRNs/s",
+            "roofline": {"bound": "offered_load", "achieved": numbers / duration_s, "peak": offered,
+                         "unit": "PRNs/s", "frac": numbers / duration_s / offered,
+                         "capacity_prn_s": capacity,
+                         "offered_over_capacity": offered / capacity if capacity else None,
+                         "note": "open-loop arrivals: the server completes what arrives, so its "
+                                 "throughput is the offered load; capacity = the plain launch's "
+                                 "measured rate on the same GPU"},
             "requests": int(meas.sum()), "completed": int(got),
             "latency_ms": {"p50": float(np.percentile(l_ms, 50)),
                            "p99": float(np.percentile(l_ms, 99)),
@@ -585,23 +677,26 @@ def main():
     ctx = ph.phprng_create(32, inst, ph.PHPRNG_REQUIRE_SAFE_PRIME, stream)
     r = torch.empty(N * per, dtype=torch.float64, device="cuda")
 
+    props = torch.cuda.get_device_properties(local)
+    uuid = getattr(props, "uuid", None)
+    sampler = ClockSampler("GPU-" + str(uuid) if uuid else None)
+    time.sleep(0.3)                                   # the sampler's own start-up
     for _ in range(args.warmup):
         ph.phprng_generate(ctx, 0, N, per, None, r, None, stream)
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
-    props = torch.cuda.get_device_properties(local)
-    uuid = getattr(props, "uuid", None)
-    sampler = ClockSampler("GPU-" + str(uuid) if uuid else None)
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    wall0 = time.time()
     start.record(stream)
     for _ in range(args.steps):
         ph.phprng_generate(ctx, 0, N, per, None, r, None, stream)
     end.record(stream)
     torch.cuda.synchronize()
+    wall1 = time.time()
     barrier()
     torch.cuda.synchronize()
-    clocks = sampler.stop()
+    clocks = sampler.stop(wall0, wall1)
     ms = max_over_ranks(start.elapsed_time(end), dist, "cuda")
     numbers = args.steps * N * per * world
     value = numbers / (ms / 1e3)
@@ -664,8 +759,9 @@ def main():
                          ("fourier", lambda: mode_fourier(ph, torch, stream)),
                          ("figures", lambda: mode_figures(ph, torch, stream)),
                          ("wide64", lambda: mode_wide64(ph, torch, stream, PEAK_TMULS)),
-                         ("batched", lambda: mode_batched(ph, torch, stream)),
-                         ("served", lambda: mode_served(ph, torch))):
+                         ("c0", lambda: mode_c0(ph, torch, stream, PEAK_TMULS)),
+                         ("batched", lambda: mode_batched(ph, torch, stream, PEAK_TMULS)),
+                         ("served", lambda: mode_served(ph, torch, capacity=value))):
             if name not in wanted:
                 continue
             try:

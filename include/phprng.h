@@ -63,8 +63,17 @@ typedef enum {
  * n  prime modulus, 5 <= n < 2^32 (width 32) or < 2^64 (width 64, 0)
  * e  exponent, 3 <= e <= n-2, gcd(e, n-1) = 1
  * p  skip-generator prime, 3 <= p < n, p < 2^32; the same (p, a) for every
- *    instance of a context
- * a  primitive root mod p
+ *    instance of a context.  For 64-bit moduli p may reach 2^63 (the
+ *    Implementation section's wide skip generator, period n(p-1) up to
+ *    2^127); a is then checked with the factors of p-1 found by Pollard's
+ *    rho, skip-ahead forms its window sum by parallel stepping (at most 2^40
+ *    steps beyond whole cycles per call), and batched requests and the
+ *    server are not available (their tiles start from the prefix table)
+ * a  primitive root mod p (the pseudorandom skip s_k = a s_(k-1) mod p, Eq. 5),
+ *    or a = 1 for the constant skip s_k = s0 = b of "Message skipping
+ *    algorithms" (Eq. 3; b = 1 is the unit skip, the cipher in counter mode,
+ *    with period n): then p is any prime with 2 <= p < n, p < 2^32 (p = 2 with
+ *    s0 = 1 gives the unit skip), and a skip by k adds k b to the message
  * m0 initial message, 0 <= m0 < n
  * s0 initial skip, 1 <= s0 <= p-1 */
 typedef struct {
@@ -177,7 +186,8 @@ int phprng_generate_stats_noalloc(phprng_ctx *ctx, uint64_t first, uint64_t num_
  * by the closed form Eq. 7 (k = q(p-1) + r: s' = s a^r mod p and
  * m' = m + q p(p-1)/2 + sum_{j=1..r} (s a^j mod p) mod n), with the sum read
  * from an exact prefix-sum table of the skip cycle of (p, a) (built on the
- * device at the first call, then kept).  inst_ids and k are host arrays of
+ * device at the first call, then kept); for the constant skip (a = 1)
+ * m' = m + k s mod n and s' = s (Eq. 3 with s_k = b), with no table.  inst_ids and k are host arrays of
  * cnt entries; an instance may appear more than once (the skips add). */
 int phprng_skip(phprng_ctx *ctx, const uint64_t *inst_ids, const uint64_t *k, uint64_t cnt,
                 void *cuda_stream);
@@ -495,7 +505,8 @@ int phprng_server_destroy(phprng_server *srv);
  * ciphertext.  The stream is redefined as the one through (m, s) at position
  * pos: its seed becomes the state pos steps earlier (Eq. 7 backwards: the
  * cycle position of s is a discrete logarithm on the host, the sum of the
- * skips in between comes from the prefix table), so phprng_seek,
+ * skips in between comes from the prefix table; for the constant skip the
+ * seed is m - pos s mod n with s0 = s), so phprng_seek,
  * phprng_skip, batched requests with offsets and the server all follow the
  * new stream.  With phprng_get_state this checkpoints and restores streams,
  * also into another context made from the same instance table (the seed then
@@ -525,7 +536,11 @@ int phprng_get_state(phprng_ctx *ctx, uint64_t inst, phprng_instance *state_out,
  * programs alone on 65,536 seeded 32-bit instances (Montgomery products per
  * second; draws the instances on the host first), 6 div.rn.f64 (FP64
  * division), 7 the generator's correctly rounded R = (c+1)/(n+1) built from
- * integers (Eq. 9d; numbers per second).  Allocates and frees small
+ * integers (Eq. 9d; numbers per second), 8 mul.wide.u32 (both halves), 9 the
+ * Montgomery product with mul.lo and mul.hi in place of mul.wide, 10 the
+ * Montgomery product by a constant (three multiplies), 11 a product by a
+ * constant mod 2^31 - 1 with a precomputed quotient factor (Shoup's
+ * method).  Allocates and frees small
  * device buffers.  The paper has no counterpart: this is the measurement used to
  * state the multiply-bound roofline of Eq. 9c. */
 int phprng_microbench(int which, double *ops_per_s, void *cuda_stream);

@@ -67,14 +67,37 @@ PH_HD double bits_to_double(uint64_t b)
 #endif
 }
 
+// hi - u, plus n when that borrows: the last step of the subtractive
+// Montgomery reduction (hi, u < n).
+#ifndef PH_FINISH
+#define PH_FINISH 0
+#endif
+PH_HD uint32_t mont_finish32(uint32_t hi, uint32_t u, uint32_t n)
+{
+#if PH_FINISH == 1
+    return hi - u + (hi < u ? n : 0u);
+#elif PH_FINISH == 2 && defined(__CUDA_ARCH__)
+    uint32_t r;
+    asm("{\n\t.reg .u32 t, m;\n\t"
+        "sub.cc.u32 t, %1, %2;\n\t"
+        "subc.u32 m, 0, 0;\n\t"
+        "and.b32 m, m, %3;\n\t"
+        "add.u32 %0, t, m;\n\t}"
+        : "=r"(r) : "r"(hi), "r"(u), "r"(n));
+    return r;
+#else
+    const uint32_t t = hi - u;
+    return hi < u ? t + n : t;
+#endif
+}
+
 PH_HD uint32_t mont32(uint32_t a, uint32_t b, uint32_t n, uint32_t ninv)
 {
     uint64_t T = (uint64_t)a * b;
     uint32_t lo = (uint32_t)T, hi = (uint32_t)(T >> 32);
     uint32_t q = lo * ninv;
     uint32_t u = umulhi32(q, n);
-    uint32_t t = hi - u;
-    return hi < u ? t + n : t;
+    return mont_finish32(hi, u, n);
 }
 
 // Montgomery product by a constant b with bq = b n^-1 mod 2^32 precomputed:
@@ -86,8 +109,7 @@ PH_HD uint32_t mont32c(uint32_t a, uint32_t b, uint32_t bq, uint32_t n)
     const uint32_t hi = umulhi32(a, b);
     const uint32_t q = a * bq;
     const uint32_t u = umulhi32(q, n);
-    const uint32_t t = hi - u;
-    return hi < u ? t + n : t;
+    return mont_finish32(hi, u, n);
 }
 
 PH_HD uint64_t mont64(uint64_t a, uint64_t b, uint64_t n, uint64_t ninv)
@@ -189,10 +211,7 @@ PH_HD void mont32_vec(uint32_t (&x)[NPT], const uint32_t (&y)[NPT], uint32_t n, 
 #pragma unroll
     for (int u = 0; u < NPT; ++u) lo[u] = umulhi32(lo[u], n);    // hi(q n)
 #pragma unroll
-    for (int u = 0; u < NPT; ++u) {
-        const uint32_t t = hi[u] - lo[u];
-        x[u] = hi[u] < lo[u] ? t + n : t;
-    }
+    for (int u = 0; u < NPT; ++u) x[u] = mont_finish32(hi[u], lo[u], n);
 }
 
 template <int NPT, typename W>
@@ -354,6 +373,26 @@ PH_HD uint32_t hist_bin256_int(uint32_t c, uint32_t yN, uint32_t ybits, uint32_t
     return est;
 }
 
+// Funnel shifts of the 64-bit value hi:lo: the high word of (hi:lo) << s and
+// the low word of (hi:lo) >> s, 0 <= s <= 31 (one instruction each on the GPU).
+PH_HD uint32_t funnel_l(uint32_t lo, uint32_t hi, uint32_t s)
+{
+#if defined(__CUDA_ARCH__)
+    return __funnelshift_l(lo, hi, s);
+#else
+    return (uint32_t)(((((uint64_t)hi << 32) | lo) << s) >> 32);
+#endif
+}
+
+PH_HD uint32_t funnel_r(uint32_t lo, uint32_t hi, uint32_t s)
+{
+#if defined(__CUDA_ARCH__)
+    return __funnelshift_r(lo, hi, s);
+#else
+    return (uint32_t)((((uint64_t)hi << 32) | lo) >> s);
+#endif
+}
+
 // The same double, deciding the rounding from an 11-bit fraction: with
 // W = floor((2^95 - 1) / yN), Xf = floor(A W / 2^(32-extra)) is the exact
 // quotient X = A 2^(52+extra) / yN scaled by 2^11 (so Xf < 2^64) and short of
@@ -362,29 +401,40 @@ PH_HD uint32_t hist_bin256_int(uint32_t c, uint32_t yN, uint32_t ybits, uint32_t
 // (X is an integer or not dyadic, as yN < 2^32), so X rounds up exactly when
 // its fraction exceeds 1/2; the 11-bit fraction f of Xf decides that unless
 // 1021 <= f < 1024, where the exact remainder of floor(X) = floor(Xf / 2^11)
-// decides it (about 1 number in 700).
+// decides it (about 1 number in 700).  Outside that band the rounded
+// significand is floor((Xf + 2^10) / 2^11) (Xf + 2^10 < 2^64: X < 2^53 - 2^20).
+// The arithmetic is kept in 32-bit words: Xf from the two partial products by
+// funnel shifts by `extra`, and the high word of the double as
+// ((1022 + E) << 20) + Q_hi with E = 32 - lz - ybits - extra (Q carries the
+// implicit bit, which lifts the exponent field by one to 1023 + E).
 PH_HD double real32_fast(uint32_t c, uint32_t yN, uint32_t ybits, uint64_t W)
 {
     const uint32_t x = c + 1;
-    const int lz = clz32(x);
+    const uint32_t lz = (uint32_t)clz32(x);
     const uint32_t A = x << lz;
     const uint32_t extra = A < yN ? 1u : 0u;
-    const int E = 32 - lz - (int)ybits - (int)extra;
     // Xf = floor(A W / 2^(32 - extra)): H = A w1 + floor(A w0 / 2^32) (< 2^64,
-    // and < 2^63 when extra = 1, as A/yN < 1 then), shifted by extra with the
-    // next bit of A w0 shifted in.
+    // and < 2^63 when extra = 1, as A/yN < 1 then), shifted left by extra
+    // with the next bit of A w0 shifted in.
     const uint64_t P = (uint64_t)A * (uint32_t)W;                        // A * w0
     const uint64_t H = (uint64_t)A * (uint32_t)(W >> 32) + (P >> 32);    // A * w1 + hi
-    const uint64_t Xf = (H << extra) | (uint64_t)(((uint32_t)P >> 31) & extra);
-    uint64_t Q = Xf >> 11;
-    const uint32_t f = (uint32_t)Xf & 0x7FFu;
-    if (f >= 1024u) {
-        ++Q;
-    } else if (f >= 1021u) {
+    const uint32_t Hlo = (uint32_t)H, Hhi = (uint32_t)(H >> 32);
+    const uint32_t Xhi = funnel_l(Hlo, Hhi, extra), Xlo = funnel_l((uint32_t)P, Hlo, extra);
+    const uint32_t f = Xlo & 0x7FFu;
+    uint32_t Qlo, Qhi;
+    if (f - 1021u >= 3u) {
+        const uint64_t Xr = (((uint64_t)Xhi << 32) | Xlo) + 1024u;
+        Qlo = funnel_r((uint32_t)Xr, (uint32_t)(Xr >> 32), 11);
+        Qhi = (uint32_t)(Xr >> 43);
+    } else {
+        uint64_t Q = (((uint64_t)Xhi << 32) | Xlo) >> 11;
         const uint64_t r = ((uint64_t)A << (52 + extra)) - Q * (uint64_t)yN;   // exact, < yN
         Q += (r << 1) > yN ? 1u : 0u;
+        Qlo = (uint32_t)Q;
+        Qhi = (uint32_t)(Q >> 32);
     }
-    return bits_to_double(((uint64_t)(1022 + E) << 52) + Q);
+    const uint32_t hi = ((1054u - ybits - lz - extra) << 20) + Qhi;
+    return bits_to_double(((uint64_t)hi << 32) | Qlo);
 }
 
 PH_HD double real64(uint64_t c, uint64_t n)

@@ -187,10 +187,18 @@ PH_API int phprng_create(phprng_ctx **out, int width, const phprng_instance *ins
         state[i] = inst[i].m0;
         state[count + i] = inst[i].s0;
     }
-    c->sk32 = derive_skip(c->p, c->a, gen_npt(0));
-    c->sk64 = derive_skip(c->p, c->a, gen_npt(1));
-    c->sk32_8 = derive_skip(c->p, c->a, 8);
-    c->sk32_4 = derive_skip(c->p, c->a, 4);
+    if (c->p >= (1ull << 32)) {
+        // the Implementation section's wide skip generator for 64-bit moduli
+        c->wide_skip = true;
+        c->skw64 = phprng::derive_skip64(c->p, c->a, gen_npt(1));
+        const uint64_t R = (uint64_t)((((unsigned __int128)1) << 64) % c->p);
+        c->ainvM = mulmod(powmod(c->a, c->p - 2, c->p), R, c->p);
+    } else {
+        c->sk32 = derive_skip(c->p, c->a, gen_npt(0));
+        c->sk64 = derive_skip(c->p, c->a, gen_npt(1));
+        c->sk32_8 = derive_skip(c->p, c->a, 8);
+        c->sk32_4 = derive_skip(c->p, c->a, 4);
+    }
     cudaStream_t s = (cudaStream_t)cuda_stream;
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_inst, count * sizeof(DevInst));
@@ -275,6 +283,7 @@ static constexpr uint64_t kMinChunk = 1024;
 
 static int prepare_split(phprng_ctx *c, uint64_t num, uint64_t per_inst, GenArgs *g, cudaStream_t s)
 {
+    if (c->wide_skip) return PHPRNG_OK;               // wide skips: never split
     const uint64_t target = 8 * gen_resident_warps();
     uint32_t K = 1, lg = 0;
     while (K < kMaxSplit && num * K < target && per_inst >= 2ull * K * kMinChunk) {
@@ -286,9 +295,10 @@ static int prepare_split(phprng_ctx *c, uint64_t num, uint64_t per_inst, GenArgs
     sp.K = K;
     sp.log2K = lg;
     sp.Lc = ((per_inst + K - 1) / K + 255) / 256 * 256;
-    const uint64_t R = (1ull << 32) % c->p;
+    const uint64_t pm = c->sk32_8.p;                 // the skip products' modulus (3 for the unit skip)
+    const uint64_t R = (1ull << 32) % pm;
     sp.oneM = (uint32_t)R;
-    sp.aLcM = (uint32_t)mulmod(powmod(c->a, sp.Lc, c->p), R, c->p);
+    sp.aLcM = (uint32_t)mulmod(powmod(c->a, sp.Lc, pm), R, pm);
     uint64_t *scr = nullptr;
     cudaError_t e = cudaMallocAsync((void **)&scr, num * (K + 1) * sizeof(uint64_t), s);
     if (e != cudaSuccess) {
@@ -373,6 +383,8 @@ static int launch_range(phprng_ctx *c, uint64_t first, uint64_t num, uint64_t pe
     if (g.edge) cudaFreeAsync(g.edge, s);
     if (rc == PHPRNG_OK && c->any64) {
         g.sk = c->sk64;
+        g.wide_skip = c->wide_skip ? 1 : 0;
+        g.skw = c->skw64;
         rc = launch_gen64(g, s, &err);
     }
     if (g.sp.scratch) cudaFreeAsync((void *)g.sp.scratch, s);
@@ -601,9 +613,26 @@ int ensure_skip(phprng_ctx *c, cudaStream_t s)
         s0[i] = c->host_inst[i].s0;
         m0[i] = c->host_inst[i].m0;
     }
+    SkipTable tb = derive_skip_table(c->p, c->a);
+    if (tb.kind == 1) {
+        // constant skip: the per-instance array holds the constant b = s0;
+        // a skip is the closed form m + k b, so there is no table to build
+        cudaError_t e = cudaMalloc(&c->d_L0, c->count * 8);
+        if (e == cudaSuccess) e = cudaMalloc(&c->d_m0, c->count * 8);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_L0, s0.data(), c->count * 8, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_m0, m0.data(), c->count * 8, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            cudaFree(c->d_L0); cudaFree(c->d_m0);
+            c->d_L0 = c->d_m0 = nullptr;
+            return cuda_fail(c, e, "phprng_skip: seed upload");
+        }
+        c->tbl = tb;
+        c->skip_ready = true;
+        return PHPRNG_OK;
+    }
     if (!discrete_logs(c->p, c->a, s0.data(), c->count, L0.data()))
         return fail(c, PHPRNG_ESKIP, "phprng_skip: no discrete log for a seed s0 (a not a primitive root?)");
-    SkipTable tb = derive_skip_table(c->p, c->a);
     uint64_t *seg = nullptr;
     cudaError_t e = cudaMalloc(&c->d_L0, c->count * 8);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_m0, c->count * 8);
@@ -664,8 +693,32 @@ PH_API int phprng_set_state(phprng_ctx *ctx, uint64_t inst, uint64_t m, uint64_t
     if (s < 1 || s > pm1) return fail(ctx, PHPRNG_EINVAL, "phprng_set_state: need 1 <= s <= p-1");
     CU(ctx, cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)cuda_stream;
+    const uint64_t v[4] = {m, s, c, pos};
+    if (ctx->wide_skip) {
+        // a wide skip prime moves streams by stepping from the current state,
+        // so the state alone defines the stream from here on
+        CU(ctx, cudaStreamSynchronize(st));
+        for (int k = 0; k < 4; ++k)
+            CU(ctx, cudaMemcpy(ctx->d_state + (uint64_t)k * ctx->count + inst, &v[k], 8, cudaMemcpyHostToDevice));
+        ctx->pos_host[inst] = pos;
+        return PHPRNG_OK;
+    }
     int rc = ensure_skip(ctx, st);
     if (rc != PHPRNG_OK) return rc;
+    if (ctx->tbl.kind == 1) {
+        // constant skip through (m, s = b) at pos: seed m0 = m - pos b mod n, s0 = b
+        const uint64_t F = mulmod(pos % n, s % n, n);
+        const uint64_t m0 = m >= F ? m - F : m + (n - F);
+        CU(ctx, cudaStreamSynchronize(st));
+        for (int k = 0; k < 4; ++k)
+            CU(ctx, cudaMemcpy(ctx->d_state + (uint64_t)k * ctx->count + inst, &v[k], 8, cudaMemcpyHostToDevice));
+        CU(ctx, cudaMemcpy(ctx->d_L0 + inst, &s, 8, cudaMemcpyHostToDevice));
+        CU(ctx, cudaMemcpy(ctx->d_m0 + inst, &m0, 8, cudaMemcpyHostToDevice));
+        ctx->host_inst[inst].m0 = m0;
+        ctx->host_inst[inst].s0 = s;
+        ctx->pos_host[inst] = pos;
+        return PHPRNG_OK;
+    }
     // the stream through (m, s) at position pos: cycle position of s, then the
     // seed pos steps earlier (Eq. 7 backwards: L0 = L - pos, m0 = m - F)
     uint64_t Ls;
@@ -680,7 +733,6 @@ PH_API int phprng_set_state(phprng_ctx *ctx, uint64_t inst, uint64_t m, uint64_t
     W = L0 + r <= pm1 ? P1 - P0 : ctx->tbl.half - P0 + P1;
     const uint64_t F = (mulmod(q % n, ctx->tbl.half % n, n) + W % n) % n;
     const uint64_t m0 = m >= F ? m - F : m + (n - F), s0 = powmod(ctx->a, L0, p);
-    const uint64_t v[4] = {m, s, c, pos};
     CU(ctx, cudaStreamSynchronize(st));
     for (int k = 0; k < 4; ++k)
         CU(ctx, cudaMemcpy(ctx->d_state + (uint64_t)k * ctx->count + inst, &v[k], 8, cudaMemcpyHostToDevice));
@@ -689,6 +741,32 @@ PH_API int phprng_set_state(phprng_ctx *ctx, uint64_t inst, uint64_t m, uint64_t
     ctx->host_inst[inst].m0 = m0;
     ctx->host_inst[inst].s0 = s0;
     ctx->pos_host[inst] = pos;
+    return PHPRNG_OK;
+}
+
+// Skip requests of a context with a wide skip prime, one after another: the
+// window sums are formed by stepping, so r = k mod (p-1) is bounded per call.
+static constexpr uint64_t kWideSkipMaxSteps = 1ull << 40;
+
+static int run_wide_skips(phprng_ctx *ctx, const std::vector<SkipReq> &reqs, cudaStream_t s,
+                          const char *what)
+{
+    const std::string w(what);
+    for (const SkipReq &r : reqs)
+        if (r.k % (ctx->p - 1) > kWideSkipMaxSteps)
+            return fail(ctx, PHPRNG_EINVAL, w + ": with a skip prime p >= 2^32 the steps beyond whole "
+                                                "cycles of p-1 are formed one by one; at most 2^40 per call");
+    uint64_t *scratch = nullptr;
+    CU(ctx, cudaMallocAsync((void **)&scratch, (1 + phprng::kWideSkipBlocks) * sizeof(uint64_t), s));
+    std::string err;
+    int rc = PHPRNG_OK;
+    for (const SkipReq &r : reqs) {
+        rc = launch_skip_wide(ctx->d_inst, ctx->d_prog, ctx->st, ctx->skw64, ctx->ainvM, r, scratch, s, &err);
+        if (rc != PHPRNG_OK) break;
+    }
+    cudaError_t e = cudaFreeAsync(scratch, s);
+    if (rc != PHPRNG_OK) return fail(ctx, rc, w + ": " + err);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFreeAsync");
     return PHPRNG_OK;
 }
 
@@ -723,6 +801,12 @@ PH_API int phprng_skip(phprng_ctx *ctx, const uint64_t *inst_ids, const uint64_t
     }
     CU(ctx, cudaSetDevice(ctx->device));
     cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (ctx->wide_skip) {
+        int wrc = run_wide_skips(ctx, reqs, s, "phprng_skip");
+        if (wrc != PHPRNG_OK) return wrc;
+        for (const SkipReq &r : reqs) ctx->pos_host[r.inst] += r.k;
+        return PHPRNG_OK;
+    }
     int rc = ensure_skip(ctx, s);
     if (rc != PHPRNG_OK) return rc;
     SkipReq *d_reqs = nullptr;
@@ -1137,6 +1221,12 @@ PH_API int phprng_seek(phprng_ctx *ctx, const uint64_t *inst_ids, const uint64_t
     }
     CU(ctx, cudaSetDevice(ctx->device));
     cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (ctx->wide_skip) {
+        int wrc = run_wide_skips(ctx, reqs, s, "phprng_seek");
+        if (wrc != PHPRNG_OK) return wrc;
+        for (size_t r = 0; r < reqs.size(); ++r) ctx->pos_host[reqs[r].inst] = target[r];
+        return PHPRNG_OK;
+    }
     int rc = ensure_skip(ctx, s);
     if (rc != PHPRNG_OK) return rc;
     SkipReq *d_reqs = nullptr;
@@ -1269,6 +1359,9 @@ PH_API int phprng_plan_create(phprng_ctx *ctx, const phprng_request *reqs, uint6
     if (!ctx) return fail(nullptr, PHPRNG_EINVAL, "phprng_plan_create: ctx is NULL");
     std::lock_guard<std::mutex> lk(ctx->mu);
     if (ctx->serving) return fail(ctx, PHPRNG_EINVAL, "phprng_plan_create: a server owns the context");
+    if (ctx->wide_skip)
+        return fail(ctx, PHPRNG_EINVAL, "phprng_plan_create: batched tiles start by Eq. 7 from the prefix "
+                                        "table, which a skip prime p >= 2^32 does not have");
     if (nreq && !reqs) return fail(ctx, PHPRNG_EINVAL, "phprng_plan_create: reqs is NULL");
     if (tile == 0) tile = kDefaultTile;
     if (tile > (1u << 30)) return fail(ctx, PHPRNG_EINVAL, "phprng_plan_create: tile above 2^30");

@@ -53,6 +53,12 @@ struct phprng_ctx {
     cudaStream_t copy_stream[kStages] = {};
     cudaEvent_t ev_done[kStages] = {}, ev_copied[kStages] = {};
     bool serving = false;             // a phprng_server owns the context
+    // a wide skip prime (p >= 2^32, 64-bit moduli): skips are stepped in
+    // 64-bit Montgomery arithmetic, skip-ahead sums formed by parallel
+    // stepping (no prefix table), no split launches, no batched offsets
+    bool wide_skip = false;
+    phprng::SkipConst64 skw64{};
+    uint64_t ainvM = 0;               // a^-1 2^64 mod p (going back)
     std::string err;
     std::mutex mu;
 };

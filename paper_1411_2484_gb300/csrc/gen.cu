@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <mutex>
+#include <type_traits>
 
 #include "gencore.cuh"
 
@@ -284,13 +285,16 @@ stats_edge_kernel(const DevInst *__restrict__ inst, const uint32_t *__restrict__
     }
 }
 
-template <int NPT>
+// WSKIP: a wide skip prime (p >= 2^32, SkipConst64 skw, 64-bit skips); such
+// launches are never split.
+template <int NPT, bool WSKIP>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, 2)
 gen64_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, DevState st,
-             SkipConst sk, uint64_t first, uint64_t num, uint64_t per_inst,
+             SkipConst sk, SkipConst64 skw, uint64_t first, uint64_t num, uint64_t per_inst,
              uint64_t *__restrict__ c_out, double *__restrict__ r_out, int vec_ok,
              const uint32_t *__restrict__ order, SplitArgs sp)
 {
+    typedef typename std::conditional<WSKIP, uint64_t, uint32_t>::type SW;
     constexpr uint64_t G = 32 * NPT;
     const int lane = threadIdx.x & 31;
     const uint64_t w = (uint64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
@@ -307,33 +311,47 @@ gen64_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
     const uint64_t len = sp.K == 1 ? per_inst : min(sp.Lc, per_inst - b0);
     const bool wb = b0 + len == per_inst;
     uint64_t M;
-    uint32_t sig;
-    if (sp.K == 1) {
+    SW sig;
+    if constexpr (WSKIP) {
         M = st.m[i];
-        sig = (uint32_t)st.s[i];
+        sig = mont64(st.s[i], skw.lane[lane], skw.p, skw.pinv);
     } else {
-        M = chunk_message(sp, q, cidx, P.n, lane);
-        sig = skip_chunk(sk, sp, (uint32_t)sp.scratch[q * (sp.K + 1) + 1], cidx);
+        uint32_t s0;
+        if (sp.K == 1) {
+            M = st.m[i];
+            s0 = (uint32_t)st.s[i];
+        } else {
+            M = chunk_message(sp, q, cidx, P.n, lane);
+            s0 = skip_chunk(sk, sp, (uint32_t)sp.scratch[q * (sp.K + 1) + 1], cidx);
+        }
+        sig = mont32(s0, sk.lane[lane], sk.p, sk.pinv);
     }
-    sig = mont32(sig, sk.lane[lane], sk.p, sk.pinv);
     const uint64_t pos_after = wb ? st.pos[i] + per_inst : 0;
     uint64_t *cdst = c_out ? c_out + j * per_inst + b0 : nullptr;
     double *rdst = r_out ? r_out + j * per_inst + b0 : nullptr;
     uint64_t x[NPT];
-    uint32_t sig_last = sig;
+    SW sig_last = sig;
     uint64_t g_last = 0;
     for (uint64_t g0 = 0; g0 < len; g0 += G) {
-        uint32_t sv[NPT];
+        SW sv[NPT];
         uint64_t msg[NPT];
         const uint64_t my0 = g0 + (uint64_t)NPT * lane;
         sig_last = sig;
         g_last = g0;
-        messages64<NPT>(P, sk, lane, my0, len, M, sig, sv, msg);
+        if constexpr (WSKIP)
+            messages64<NPT, SkipConst64, uint64_t>(P, skw, lane, my0, len, M, sig, sv, msg);
+        else
+            messages64<NPT>(P, sk, lane, my0, len, M, sig, sv, msg);
         encrypt64<NPT>(P, pg, msg, x);
         store_group<NPT, uint64_t, uint64_t>(P, cdst, rdst, my0, len, vec_ok, x);
     }
-    if (wb) write_state_after<NPT, uint64_t, uint64_t>(st, sk, i, lane, g_last, len, pos_after, M, sig_last,
-                                                       x);
+    if (wb) {
+        if constexpr (WSKIP)
+            write_state_after<NPT, uint64_t, uint64_t, SkipConst64, uint64_t>(st, skw, i, lane, g_last, len,
+                                                                              pos_after, M, sig_last, x);
+        else
+            write_state_after<NPT, uint64_t, uint64_t>(st, sk, i, lane, g_last, len, pos_after, M, sig_last, x);
+    }
 }
 
 // Pre-pass of a split launch: warp w sums the skips of chunk w % K of slot
@@ -442,9 +460,19 @@ int launch_gen64(const GenArgs &a, void *stream, std::string *err)
 {
     if (a.num == 0 || a.per_inst == 0) return PHPRNG_OK;
     const uint64_t blocks = ((a.num << a.sp.log2K) + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    gen64_kernel<kNPT64><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, (cudaStream_t)stream>>>(
-        a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, (uint64_t *)a.c_out, a.r_out, a.vec_ok,
-        a.order, a.sp);
+    if (a.wide_skip) {
+        if (a.sp.K != 1) {
+            *err = "gen64_kernel: launches with a wide skip prime are never split";
+            return PHPRNG_EINVAL;
+        }
+        gen64_kernel<kNPT64, true><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, (cudaStream_t)stream>>>(
+            a.inst, a.prog, a.st, a.sk, a.skw, a.first, a.num, a.per_inst, (uint64_t *)a.c_out, a.r_out,
+            a.vec_ok, a.order, a.sp);
+    } else {
+        gen64_kernel<kNPT64, false><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, (cudaStream_t)stream>>>(
+            a.inst, a.prog, a.st, a.sk, a.skw, a.first, a.num, a.per_inst, (uint64_t *)a.c_out, a.r_out,
+            a.vec_ok, a.order, a.sp);
+    }
     return check_launch(err, "gen64_kernel launch");
 }
 

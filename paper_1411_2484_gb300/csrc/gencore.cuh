@@ -34,6 +34,12 @@ __device__ __forceinline__ uint32_t skip_step(const SkipConst &sk, uint32_t s, b
     return group ? mont32c(s, sk.aGM, sk.aGMq, sk.p) : mont32c(s, sk.aM, sk.aMq, sk.p);
 }
 
+// The same for a wide skip prime p < 2^63 (Montgomery products mod p, R = 2^64).
+__device__ __forceinline__ uint64_t skip_step(const SkipConst64 &sk, uint64_t s, bool group)
+{
+    return mont64(s, group ? sk.aGM : sk.aM, sk.p, sk.pinv);
+}
+
 // s * a^(c Lc) mod p for a plain skip s: the start skip of chunk c of a
 // split launch (square-and-multiply on a^Lc in Montgomery form).
 __device__ __forceinline__ uint32_t skip_chunk(const SkipConst &sk, const SplitArgs &sp, uint32_t s,
@@ -92,14 +98,16 @@ __device__ __forceinline__ void messages32(const DevInst &P, const SkipConst &sk
     sig = skip_step(sk, sig, true);
 }
 
-template <int NPT>
-__device__ __forceinline__ void messages64(const DevInst &P, const SkipConst &sk, int lane,
-                                           uint64_t my0, uint64_t len, uint64_t &M, uint32_t &sig,
-                                           uint32_t (&sv)[NPT], uint64_t (&msg)[NPT])
+// SK, SW: SkipConst and uint32_t skips (p < 2^32), or SkipConst64 and
+// uint64_t skips (a wide skip prime).
+template <int NPT, typename SK = SkipConst, typename SW = uint32_t>
+__device__ __forceinline__ void messages64(const DevInst &P, const SK &sk, int lane,
+                                           uint64_t my0, uint64_t len, uint64_t &M, SW &sig,
+                                           SW (&sv)[NPT], uint64_t (&msg)[NPT])
 {
     const uint64_t n = P.n;
     uint64_t S = 0;
-    uint32_t t = sig;
+    SW t = sig;
 #pragma unroll
     for (int u = 0; u < NPT; ++u) {
         t = skip_step(sk, t, false);
@@ -251,14 +259,14 @@ __device__ __forceinline__ void write_c_if_last(DevState st, uint64_t i, int lan
 // the run's last number: M (the message after the last group, which is the
 // last number's message), that number's skip -- sig_group (the lane's skip
 // entering the last group, g0) stepped ul+1 times -- and its ciphertext.
-template <int NPT, typename XT, typename MT>
-__device__ __forceinline__ void write_state_after(DevState st, const SkipConst &sk, uint64_t i, int lane,
+template <int NPT, typename XT, typename MT, typename SK = SkipConst, typename SW = uint32_t>
+__device__ __forceinline__ void write_state_after(DevState st, const SK &sk, uint64_t i, int lane,
                                                   uint64_t g0, uint64_t len, uint64_t pos_after, MT M,
-                                                  uint32_t sig_group, const XT (&x)[NPT])
+                                                  SW sig_group, const XT (&x)[NPT])
 {
     int ul;
     if (!owns_last<NPT>(lane, g0, len, &ul)) return;
-    uint32_t s = sig_group;
+    SW s = sig_group;
     for (int u = 0; u <= ul; ++u) s = skip_step(sk, s, false);
     XT c = x[0];
 #pragma unroll

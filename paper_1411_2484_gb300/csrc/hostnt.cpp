@@ -97,16 +97,68 @@ bool is_prime(uint64_t n)
     return true;
 }
 
+// A nontrivial factor of the odd composite x: Pollard's rho with Brent's
+// cycle detection (R. P. Brent, "An improved Monte Carlo factorization
+// algorithm", BIT 20, 1980), iterating y -> y^2 + c mod x and taking gcds of
+// products of |x_i - y| over batches of 128 steps; a new c when a batch
+// collapses to x.
+static uint64_t rho_factor(uint64_t x)
+{
+    for (uint64_t c = 1;; ++c) {
+        uint64_t y = 2, g = 1, q = 1, ys = 2, xs = 2;
+        for (uint64_t r = 1; g == 1; r <<= 1) {
+            xs = y;
+            for (uint64_t i = 0; i < r; ++i) y = (mulmod(y, y, x) + c) % x;
+            for (uint64_t k = 0; k < r && g == 1; k += 128) {
+                ys = y;
+                for (uint64_t i = 0; i < 128 && i < r - k; ++i) {
+                    y = (mulmod(y, y, x) + c) % x;
+                    q = mulmod(q, xs > y ? xs - y : y - xs, x);
+                }
+                g = gcd64(q, x);
+            }
+        }
+        if (g == x) {                              // the batch overshot: step singly
+            do {
+                ys = (mulmod(ys, ys, x) + c) % x;
+                g = gcd64(xs > ys ? xs - ys : ys - xs, x);
+            } while (g == 1);
+        }
+        if (g != x) return g;
+    }
+}
+
+static void factor_into(uint64_t x, std::vector<uint64_t> &f)
+{
+    if (x == 1) return;
+    if (is_prime(x)) {
+        f.push_back(x);
+        return;
+    }
+    const uint64_t d = rho_factor(x);
+    factor_into(d, f);
+    factor_into(x / d, f);
+}
+
+// The distinct prime factors of x, ascending: trial division by the primes
+// below 2^16 (by odd numbers), then Pollard's rho on what remains, so that
+// p - 1 of a 63-bit skip prime factors in well under a second.
 std::vector<uint64_t> prime_factors(uint64_t x)
 {
     std::vector<uint64_t> f;
-    for (uint64_t d = 2; d * d <= x; d += (d == 2 ? 1 : 2)) {
+    for (uint64_t d = 2; d < 65536 && d * d <= x; d += (d == 2 ? 1 : 2)) {
         if (x % d == 0) {
             f.push_back(d);
             while (x % d == 0) x /= d;
         }
     }
-    if (x > 1) f.push_back(x);
+    if (x > 1) {
+        std::vector<uint64_t> big;
+        factor_into(x, big);
+        f.insert(f.end(), big.begin(), big.end());
+    }
+    std::sort(f.begin(), f.end());
+    f.erase(std::unique(f.begin(), f.end()), f.end());
     return f;
 }
 
@@ -346,6 +398,10 @@ DevInst derive_inst(const phprng_instance &in, int wide, ExpProg *prog)
 SkipConst derive_skip(uint64_t p, uint64_t a, int npt)
 {
     SkipConst k;
+    // The constant skip (a = 1) keeps s_k = s0 for any odd modulus above s0;
+    // p = 2 (the unit skip, s0 = 1) is even, and the Montgomery products run
+    // modulo 3 instead, with the same values.
+    if (a == 1 && p == 2) p = 3;
     uint64_t R = (1ull << 32) % p;
     k.p = (uint32_t)p;
     k.pinv = (uint32_t)inv_mod_2_64(p);
@@ -358,10 +414,28 @@ SkipConst derive_skip(uint64_t p, uint64_t a, int npt)
     return k;
 }
 
+SkipConst64 derive_skip64(uint64_t p, uint64_t a, int npt)
+{
+    SkipConst64 k;
+    const uint64_t R = (uint64_t)((((u128)1) << 64) % p);
+    k.p = p;
+    k.pinv = inv_mod_2_64(p);
+    k.aM = mulmod(a % p, R, p);
+    k.aGM = mulmod(powmod(a, 32ull * npt, p), R, p);
+    k.oneM = R;
+    for (int j = 0; j < 32; ++j) k.lane[j] = mulmod(powmod(a, (uint64_t)npt * j, p), R, p);
+    return k;
+}
+
 SkipTable derive_skip_table(uint64_t p, uint64_t a)
 {
     SkipTable t;
     memset(&t, 0, sizeof t);
+    if (a == 1) {                                  // constant skip: no cycle, no table
+        t.kind = 1;
+        t.p = (uint32_t)p;
+        return t;
+    }
     uint64_t R = (1ull << 32) % p;
     t.p = (uint32_t)p;
     t.pinv = (uint32_t)inv_mod_2_64(p);
@@ -401,13 +475,24 @@ int validate_one(int width, const phprng_instance &in, uint32_t flags, std::stri
         *msg = fmt_inst("e must satisfy 3 <= e <= n-2 and gcd(e, n-1) = 1", in);
         return PHPRNG_EEXPONENT;
     }
-    if (in.p < 3 || in.p >= in.n || in.p >= (1ull << 32) || !is_prime(in.p)) {
-        *msg = fmt_inst("p must be a prime with 3 <= p < n and p < 2^32", in);
-        return PHPRNG_ESKIP;
-    }
-    if (in.a < 1 || in.a >= in.p || !is_primitive_root(in.a, in.p)) {
-        *msg = fmt_inst("a is not a primitive root mod p", in);
-        return PHPRNG_ESKIP;
+    if (in.a == 1) {
+        // the constant skip s_k = s0 (Eq. 3 with s_k = b; b = 1, p = 2: the unit skip)
+        if (in.p < 2 || in.p >= in.n || in.p >= (1ull << 32) || !is_prime(in.p)) {
+            *msg = fmt_inst("constant skip (a = 1): p must be a prime with 2 <= p < n and p < 2^32", in);
+            return PHPRNG_ESKIP;
+        }
+    } else {
+        // p < 2^32, or for 64-bit moduli a wide skip prime up to 2^63 (the
+        // Implementation section's 63-bit skip generator for 64-bit n)
+        const uint64_t pmax = in.n >= (1ull << 32) ? (1ull << 63) : (1ull << 32);
+        if (in.p < 3 || in.p >= in.n || in.p >= pmax || !is_prime(in.p)) {
+            *msg = fmt_inst("p must be a prime with 3 <= p < n, and p < 2^32 (p < 2^63 when n >= 2^32)", in);
+            return PHPRNG_ESKIP;
+        }
+        if (in.a < 1 || in.a >= in.p || !is_primitive_root(in.a, in.p)) {
+            *msg = fmt_inst("a is not a primitive root mod p (a = 1 selects the constant skip)", in);
+            return PHPRNG_ESKIP;
+        }
     }
     if (in.s0 < 1 || in.s0 >= in.p) {
         *msg = fmt_inst("s0 must lie in [1, p-1]", in);

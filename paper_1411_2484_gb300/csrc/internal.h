@@ -51,6 +51,16 @@ struct SkipConst {
     uint32_t lane[32];     // a^(NPT*j) * 2^32 mod p, j = lane    (lane start)
 };
 
+// The same for a wide skip prime p < 2^63 (64-bit moduli only): Montgomery
+// products modulo p with R = 2^64, values in Montgomery form carrying 2^64.
+struct SkipConst64 {
+    uint64_t p, pinv;      // p, p^-1 mod 2^64
+    uint64_t aM;           // a * 2^64 mod p                      (one step, Eq. 9a)
+    uint64_t aGM;          // a^(32*NPT) * 2^64 mod p             (one warp group)
+    uint64_t oneM;         // 2^64 mod p (1 in Montgomery form)
+    uint64_t lane[32];     // a^(NPT*j) * 2^64 mod p, j = lane    (lane start)
+};
+
 // Generator state, structure of arrays in device memory, one entry per
 // instance: the message m, the skip s, the last ciphertext c (the three
 // values of the seven-integer state that change) and the stream position.
@@ -92,6 +102,10 @@ struct GenArgs {
     const uint32_t *order = nullptr;
     SplitArgs sp;                      // K = 1: no split
     int light = 0;                     // short exponent programs: the LIGHT instantiation
+    // a wide skip prime (p >= 2^32, 64-bit moduli): the 64-bit generator
+    // steps its skips with skw instead of sk (never split)
+    int wide_skip = 0;
+    SkipConst64 skw{};
 };
 
 // Exact prefix table of the skip generator's cycle (Eq. 7): with
@@ -101,7 +115,12 @@ struct GenArgs {
 static constexpr uint32_t kSkipLog2B = 10;
 static constexpr uint32_t kSkipB = 1u << kSkipLog2B;
 
+// kind 0: a primitive root mod p (the pseudorandom skip, Eq. 5) with the
+// prefix table; kind 1: a = 1, the constant skip s_k = s0 = b of Eq. 3 (b = 1
+// is the unit skip), where a skip of k adds k b to the message and the per-
+// instance array that holds cycle positions for kind 0 holds b instead.
 struct SkipTable {
+    uint32_t kind;         // 0 prefix table, 1 constant skip
     const uint64_t *T;     // prefix sums (exact, < 2^64 because p < 2^32)
     const uint32_t *P;     // checkpoint powers
     uint64_t nT;           // entries: (p-1)/B + 1
@@ -217,6 +236,18 @@ int launch_build_skip_table(uint64_t p, uint64_t a, uint64_t *T, uint32_t *P, ui
 int launch_skip(const DevInst *inst, const ExpProg *prog, DevState st, const uint64_t *L0,
                 SkipTable tbl, const SkipReq *reqs, uint64_t cnt, void *stream, std::string *err);
 
+// Wide skip primes (p >= 2^32): Eq. 7 with the window sum formed by parallel
+// stepping (no prefix table: the cycle has p - 1 > 2^32 terms).  One request
+// advances instance `inst` by k (or goes back by k), using `scratch` (at least
+// 1 + kWideSkipBlocks uint64 words, device memory) for the partial sums.
+// The request is cut into pieces of at most kWideSkipPiece steps (one short
+// launch sequence each); q = floor(k/(p-1)) full cycles add q p(p-1)/2 in
+// closed form (Eq. 7), so only r = k mod (p-1) steps are formed.
+static constexpr uint32_t kWideSkipBlocks = 1024;
+static constexpr uint64_t kWideSkipPiece = 1ull << 34;
+int launch_skip_wide(const DevInst *inst, const ExpProg *prog, DevState st, const SkipConst64 &skw,
+                     uint64_t ainvM, const SkipReq &req, uint64_t *scratch, void *stream, std::string *err);
+
 // ---- measurement (microbench.cu) ------------------------------------------
 int run_microbench(int which, double *ops_per_s, void *stream, std::string *err);
 
@@ -235,6 +266,7 @@ uint64_t mont_exit_constant(uint64_t n, const ExpProg &pg, int rbits);
 DevInst derive_inst(const phprng_instance &in, int wide, ExpProg *prog);
 int program_products(const ExpProg &pg);   // Montgomery products of one run, K included
 SkipConst derive_skip(uint64_t p, uint64_t a, int npt);
+SkipConst64 derive_skip64(uint64_t p, uint64_t a, int npt);
 int validate_one(int width, const phprng_instance &in, uint32_t flags, std::string *msg);
 int validate_all(int width, const phprng_instance *inst, uint64_t count, uint32_t flags,
                  uint64_t *bad, std::string *msg);

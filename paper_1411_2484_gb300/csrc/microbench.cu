@@ -18,6 +18,13 @@
 //                              R = (c+1)/(n+1) costs as a floating division)
 //   7  the generator's R built from integers (Eq. 9d, correctly rounded),
 //      for n = 2^32 - 5: the replacement of form 6
+//   8  mul.wide.u32               both halves of a 32x32 product
+//   9  Montgomery product with the low and high halves of a b taken by
+//      mul.lo and mul.hi instead of one mul.wide
+//  10  Montgomery product by a constant (three multiplies, the constant's
+//      q factor precomputed: the generator's exit and skip products)
+//  11  product by a constant mod p < 2^31 with a precomputed quotient factor
+//      (Shoup): q = hi(x w), x b - q p, one conditional subtraction
 #include <cuda_runtime.h>
 
 #include <vector>
@@ -60,6 +67,28 @@ __global__ void __launch_bounds__(256) microbench_kernel(uint32_t *sink, int ite
                     x[k] = mont32(x[k], x[k], n, ninv);   // exact for any inputs < 2^32 here
                 } else if (FORM == 6) {
                     asm volatile("div.rn.f64 %0, %1, %0;" : "+d"(d[k]) : "d"(1.0000001));
+                } else if (FORM == 8) {
+                    uint64_t t;
+                    asm volatile("mul.wide.u32 %0, %1, %2;" : "=l"(t) : "r"(x[k]), "r"(c));
+                    x[k] = (uint32_t)t ^ (uint32_t)(t >> 32);
+                } else if (FORM == 9) {
+                    uint32_t lo, hi, q, u;
+                    asm volatile("mul.lo.u32 %0, %1, %1;" : "=r"(lo) : "r"(x[k]));
+                    asm volatile("mul.hi.u32 %0, %1, %1;" : "=r"(hi) : "r"(x[k]));
+                    asm volatile("mul.lo.u32 %0, %1, %2;" : "=r"(q) : "r"(lo), "r"(ninv));
+                    asm volatile("mul.hi.u32 %0, %1, %2;" : "=r"(u) : "r"(q), "r"(n));
+                    const uint32_t t = hi - u;
+                    x[k] = hi < u ? t + n : t;
+                } else if (FORM == 10) {
+                    x[k] = mont32c(x[k], c, c * ninv, n);
+                } else if (FORM == 11) {
+                    // p = 2^31 - 1, b = c mod p, w = floor(b 2^32 / p); x < p
+                    const uint32_t p = 2147483647u, b = c % p;
+                    const uint32_t w = (uint32_t)(((uint64_t)b << 32) / p);
+                    const uint32_t xx = x[k] & 0x7FFFFFFFu;
+                    const uint32_t q = umulhi32(xx, w);
+                    uint32_t r = xx * b - q * p;
+                    x[k] = r >= p ? r - p : r;
                 } else if (FORM == 7) {
                     // c < 2^31 <= n - 1; the result's low bits feed the next c
                     const double R = real32_fast(x[k] & 0x7FFFFFFFu, yN, ybits, W);
@@ -98,7 +127,7 @@ static int run_one(double *ops_per_s, cudaStream_t s, std::string *err)
     const uint32_t n = 4294967291u;
     uint32_t ninv = n;
     for (int i = 0; i < 5; ++i) ninv *= 2u - n * ninv;
-    int iters = FORM == 4 ? 64 : FORM >= 6 ? 16 : 256;
+    int iters = FORM == 4 ? 64 : (FORM == 6 || FORM == 7) ? 16 : 256;
     // R of form 7 for n = 2^32 - 5, from the host's own derivation
     const phprng_instance in = {n, 3, 2147483647u, 784588716u, 0, 1};
     ExpProg pg;
@@ -213,6 +242,10 @@ int run_microbench(int which, double *ops_per_s, void *stream, std::string *err)
     case 5: return run_exp(ops_per_s, s, err);
     case 6: return run_one<6>(ops_per_s, s, err);
     case 7: return run_one<7>(ops_per_s, s, err);
+    case 8: return run_one<8>(ops_per_s, s, err);
+    case 9: return run_one<9>(ops_per_s, s, err);
+    case 10: return run_one<10>(ops_per_s, s, err);
+    case 11: return run_one<11>(ops_per_s, s, err);
     default:
         *err = "microbench: unknown form";
         return PHPRNG_EINVAL;

@@ -29,18 +29,21 @@ namespace phprng {
 // The exact bin from integers: with vN = (c+1) 2^(32-ybits) < yN and
 // r = floor(B 2^32 / yN), floor(vN r / 2^32) is the bin or one below it (r is
 // short of B 2^32 / yN by less than 1 and vN < 2^32), and one exact comparison
-// decides.  The remainder B vN - k yN of the exact quotient k lies in
-// [0, 2 yN) before that correction; its low word is 0 or yN only when it is 0,
-// yN or 2^32, so those two values send the number to the double arithmetic
-// (always correct, about 1 number in 2^31 at random).
+// decides.  The final remainder B vN - k yN lies in [0, yN), below 2^32, so it
+// is zero exactly when its low word is, and that word comes from the two
+// products of the comparison: lo(B vN) - lo((est+1) yN), plus yN when est was
+// not raised.  A zero remainder -- an exact k/B, about 1 number in 2^31 at
+// random -- sends the number to the double arithmetic.
 __device__ __forceinline__ uint32_t serial_bin(uint32_t c, uint32_t yN, uint32_t ybits, uint32_t r,
                                                uint32_t B)
 {
     const uint32_t vN = (c + 1) << (32 - ybits);
     uint32_t est = umulhi32(vN, r);
-    const uint32_t rlo = vN * B - est * yN;
-    if ((uint64_t)(est + 1) * yN <= (uint64_t)vN * B) ++est;
-    if (rlo == 0u || rlo == yN) {
+    const uint64_t P1 = (uint64_t)(est + 1) * yN, P2 = (uint64_t)vN * B;
+    const bool up = P1 <= P2;
+    est += up ? 1u : 0u;
+    const uint32_t d = (uint32_t)P2 - (uint32_t)P1;
+    if (d == (up ? 0u : 0u - yN)) {
         const double R = __ddiv_rn((double)(c + 1), (double)(yN >> (32 - ybits)));
         est = (uint32_t)__dmul_rn(R, (double)B);
     }

@@ -323,6 +323,9 @@ PH_API int phprng_server_create(phprng_ctx *ctx, const phprng_server_config *cfg
     if (!ctx || !cfg) return fail(ctx, PHPRNG_EINVAL, "phprng_server_create: NULL argument");
     std::lock_guard<std::mutex> lk(ctx->mu);
     if (ctx->serving) return fail(ctx, PHPRNG_EINVAL, "phprng_server_create: context already served");
+    if (ctx->wide_skip)
+        return fail(ctx, PHPRNG_EINVAL, "phprng_server_create: served tiles start by Eq. 7 from the prefix "
+                                        "table, which a skip prime p >= 2^32 does not have");
     if (ctx->count > kTileInstMask)
         return fail(ctx, PHPRNG_EINVAL, "phprng_server_create: more than 2^30 instances");
     phprng_server *s = new (std::nothrow) phprng_server;

@@ -10,6 +10,8 @@
 // L = (L0 + pos) mod (p-1), L0 the discrete log of s0 found on the host.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "skipdev.cuh"
 
 namespace phprng {
@@ -81,12 +83,19 @@ skip_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, 
     const DevInst P = inst[i];
     const uint64_t pm1 = tb.p - 1;
     const uint64_t pos = st.pos[i];
-    const uint64_t L = (L0[i] + pos % pm1) % pm1;
+    // kind 0: the cycle position of the current skip; kind 1: the constant b
+    const uint64_t L = tb.kind == 1 ? L0[i] : (L0[i] + pos % pm1) % pm1;
     uint64_t m;
     uint32_t s;
     uint64_t Lnew;
     if (!q.back) {
         skip_state_warp(tb, P, st.m[i], L, q.k, &m, &s, &Lnew);
+    } else if (tb.kind == 1) {
+        // backward by k over a constant skip: m' = m - k b mod n, s' = b
+        uint64_t F, Lf;
+        skip_state_warp(tb, P, 0, L, q.k, &F, &s, &Lf);
+        const uint64_t mc = st.m[i];
+        m = mc >= F ? mc - F : mc + (P.n - F);
     } else {
         // Backward by k: the state k steps earlier sits at cycle position
         // L' = L - k mod (p-1), and going forward k steps from it adds F =
@@ -120,6 +129,92 @@ skip_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, 
     }
 }
 
+// ---- wide skip primes (p >= 2^32): window sums by parallel stepping ----------
+
+// base^k in Montgomery form from baseM = base 2^64 mod p (square-and-multiply).
+__device__ __forceinline__ uint64_t pow64M(const SkipConst64 &sk, uint64_t baseM, uint64_t k)
+{
+    uint64_t x = sk.oneM;
+    for (int b = 63 - __clzll((long long)(k | 1)); b >= 0; --b) {
+        x = mont64(x, x, sk.p, sk.pinv);
+        if ((k >> b) & 1ull) x = mont64(x, baseM, sk.p, sk.pinv);
+    }
+    return x;
+}
+
+// scratch[0] = the skip the window starts from: s, or s a^-r going back r.
+__global__ void wide_skip_prep(DevState st, SkipConst64 sk, uint64_t ainvM, uint64_t inst, uint64_t r,
+                               uint64_t back, uint64_t *scratch)
+{
+    if (threadIdx.x != 0) return;
+    const uint64_t s = st.s[inst];
+    scratch[0] = back ? mont64(s, pow64M(sk, ainvM, r), sk.p, sk.pinv) : s;
+}
+
+// sum_{j=1..r} (sb a^j mod p) mod n, cut into one contiguous run of terms per
+// thread (each starts at sb a^(j0+1) by square-and-multiply), reduced per
+// block into scratch[1 + block].
+__global__ void __launch_bounds__(256)
+wide_skip_sum(const DevInst *__restrict__ inst, SkipConst64 sk, uint64_t i, uint64_t r, uint64_t *scratch)
+{
+    __shared__ uint64_t part[8];
+    const uint64_t n = inst[i].n;
+    const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t per = (r + T - 1) / T;
+    const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t j0 = t * per;
+    uint64_t sum = 0;
+    if (j0 < r) {
+        const uint64_t sb = scratch[0];
+        uint64_t v = mont64(sb, pow64M(sk, sk.aM, j0 + 1), sk.p, sk.pinv);   // sb a^(j0+1)
+        const uint64_t cnt = min(per, r - j0);
+        for (uint64_t u = 0; u < cnt; ++u) {
+            sum = addmod64(sum, v, n);                                     // v < p < n
+            v = mont64(v, sk.aM, sk.p, sk.pinv);
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) sum = addmod64(sum, __shfl_xor_sync(0xffffffffu, sum, off), n);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint64_t b = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = addmod64(b, part[w], n);
+        scratch[1 + blockIdx.x] = b;
+    }
+}
+
+// The state after the piece: F = q p(p-1)/2 + window sum (mod n), m' = m + F
+// or m - F, s' = sb a^r or sb, c' = m'^e (0 at position 0), pos' = pos +- k.
+__global__ void wide_skip_final(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, DevState st,
+                                SkipConst64 sk, uint64_t i, uint64_t q, uint64_t r, uint64_t k, uint64_t back,
+                                uint64_t nblocks, const uint64_t *scratch)
+{
+    const int lane = threadIdx.x & 31;
+    const DevInst P = inst[i];
+    const uint64_t n = P.n;
+    uint64_t F = 0;
+    for (uint64_t b = lane; b < nblocks; b += 32) F = addmod64(F, scratch[1 + b], n);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) F = addmod64(F, __shfl_xor_sync(0xffffffffu, F, off), n);
+    if (lane != 0) return;
+    if (q) {
+        typedef unsigned __int128 u128;
+        const uint64_t half = (uint64_t)((((u128)sk.p * (sk.p - 1)) >> 1) % n);
+        F = addmod64(F, (uint64_t)(((u128)(q % n) * half) % n), n);
+    }
+    const uint64_t sb = scratch[0], m = st.m[i];
+    const uint64_t m2 = back ? (m >= F ? m - F : m + (n - F)) : addmod64(m, F, n);
+    const uint64_t s2 = back ? sb : mont64(sb, pow64M(sk, sk.aM, r), sk.p, sk.pinv);
+    const uint64_t pos2 = back ? st.pos[i] - k : st.pos[i] + k;
+    uint64_t msg[1] = {m2}, x[1];
+    modexp_prog<1, uint64_t>(x, msg, prog[i], n, P.ninv, P.K, 0);
+    st.m[i] = m2;
+    st.s[i] = s2;
+    st.c[i] = pos2 ? x[0] : 0;
+    st.pos[i] = pos2;
+}
+
 static int check(std::string *err, const char *what)
 {
     cudaError_t e = cudaGetLastError();
@@ -150,6 +245,41 @@ int launch_skip(const DevInst *inst, const ExpProg *prog, DevState st, const uin
     skip_kernel<<<(unsigned)((cnt + 7) / 8), 256, 0, (cudaStream_t)stream>>>(inst, prog, st, L0,
                                                                                tbl, reqs, cnt);
     return check(err, "skip_kernel launch");
+}
+
+}  // namespace phprng
+
+namespace phprng {
+
+// One wide-skip request: r = k mod (p-1) steps in pieces of at most
+// kWideSkipPiece, the q full cycles added with the first piece.
+int launch_skip_wide(const DevInst *inst, const ExpProg *prog, DevState st, const SkipConst64 &skw,
+                     uint64_t ainvM, const SkipReq &req, uint64_t *scratch, void *stream, std::string *err)
+{
+    if (req.k == 0) return PHPRNG_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint64_t pm1 = skw.p - 1;
+    const uint64_t q = req.k / pm1, r = req.k % pm1;
+    uint64_t done = 0;
+    bool first = true;
+    do {
+        const uint64_t piece = std::min<uint64_t>(r - done, kWideSkipPiece);
+        const uint64_t k_piece = first ? q * pm1 + piece : piece;   // positions this piece moves
+        const uint64_t blocks = std::max<uint64_t>(1, std::min<uint64_t>(kWideSkipBlocks, (piece + 255) / 256));
+        wide_skip_prep<<<1, 32, 0, s>>>(st, skw, ainvM, req.inst, piece, req.back, scratch);
+        int rc = check(err, "wide_skip_prep launch");
+        if (rc != PHPRNG_OK) return rc;
+        wide_skip_sum<<<(unsigned)blocks, 256, 0, s>>>(inst, skw, req.inst, piece, scratch);
+        rc = check(err, "wide_skip_sum launch");
+        if (rc != PHPRNG_OK) return rc;
+        wide_skip_final<<<1, 32, 0, s>>>(inst, prog, st, skw, req.inst, first ? q : 0, piece, k_piece,
+                                         req.back, blocks, scratch);
+        rc = check(err, "wide_skip_final launch");
+        if (rc != PHPRNG_OK) return rc;
+        done += piece;
+        first = false;
+    } while (done < r);
+    return PHPRNG_OK;
 }
 
 }  // namespace phprng

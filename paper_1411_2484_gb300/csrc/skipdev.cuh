@@ -70,11 +70,28 @@ __device__ __forceinline__ void window_warp(const SkipTable &tb, uint64_t L, uin
 
 // State k steps after (m, s = a^L) by Eq. 7.  The message update is exact:
 // q mod n times p(p-1)/2 mod n, plus the window sum mod n, all mod n.
+// For the constant skip (kind 1) L carries b = s0: m' = m + k b mod n, s' = b
+// (Eq. 3 with s_k = b: the k messages after m are m + b, m + 2b, ...).
 __device__ __forceinline__ void skip_state_warp(const SkipTable &tb, const DevInst &P,
                                                 uint64_t m, uint64_t L, uint64_t k,
                                                 uint64_t *m_out, uint32_t *s_out,
                                                 uint64_t *L_out)
 {
+    if (tb.kind == 1) {
+        const uint64_t n = P.n, b = L;
+        uint64_t add;
+        if (!P.wide) {
+            add = ((k % n) * b) % n;                               // b < 2^32 > n: fits 64 bits
+            *m_out = (m + add) % n;
+        } else {
+            const uint64_t t = mont64(k % n, b % n, n, P.ninv);     // k b R^-1
+            add = mont64(t, P.aux, n, P.ninv);                     // k b mod n
+            *m_out = addmod64(m, add, n);
+        }
+        *s_out = (uint32_t)b;
+        *L_out = b;
+        return;
+    }
     const uint64_t pm1 = tb.p - 1;
     const uint64_t q = k / pm1, r = k - q * pm1;
     uint64_t W;

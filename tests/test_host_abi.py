@@ -115,6 +115,10 @@ def _one(n=4294967087, e=9, p=P31, a=A31, m0=5, s0=7):
     (_one() + _one(m0=9), 32, 0, 5),                 # duplicate modulus
     (_one() + [(4294967291, 9, 11, 2, 0, 1)], 0, 0, 4),   # two skip generators in one context
     (_one(), 48, 0, 1),                              # bad width
+    (_one(p=2, a=1, s0=2), 32, 0, 4),                # constant skip: s0 >= p
+    (_one(p=65535, a=1, s0=3), 32, 0, 4),            # constant skip: p composite
+    (_one(p=1, a=1, s0=1), 32, 0, 4),                # constant skip: p < 2
+    (_one(n=23, e=3, p=23, a=1, s0=1, m0=0), 32, 0, 4),   # constant skip: p >= n
 ])
 def test_validation_errors(ph, inst, width, flags, status):
     rc, bad, msg = ph.phprng_validate(width, inst, flags)
@@ -131,6 +135,109 @@ def test_validation_accepts_paper_parameters(ph):
     assert ph.phprng_validate(32, _one() + _one(m0=9), 2)[0] == 0       # shared n allowed
     assert ph.phprng_validate(64, [(18446744073709551557, 3, P31, A31, 0, 1)], 0)[0] == 0
     assert ph.phprng_validate(0, _one() + [(18446744073709551557, 5, P31, A31, 1, 1)], 0)[0] == 0
+
+
+def test_validation_accepts_constant_skips(ph):
+    """a = 1 selects the constant skip s_k = s0 (Eq. 3 with s_k = b): the unit
+    skip with p = 2, s0 = 1 (the paper's Fig. 2 generator) and any b < p."""
+    assert ph.phprng_validate(32, _one(p=2, a=1, s0=1), 0)[0] == 0
+    assert ph.phprng_validate(32, _one(p=65537, a=1, s0=12345), 1)[0] == 0
+    assert ph.phprng_validate(64, [(18446744073709551557, 3, 2, 1, 0, 1)], 0)[0] == 0
+    assert ph.phprng_validate(32, _one(p=2, a=1, s0=1) + _one(n=4294967291, p=2, a=1, s0=1), 0)[0] == 0
+
+
+N64 = 18446744073709551557          # a prime above 2^63
+
+
+def _pr_factors(x):
+    """Distinct prime factors by trial division and Pollard's rho (plain Python)."""
+    import math as _m
+
+    def is_p(q):
+        if q < 2:
+            return False
+        for d in (2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37):
+            if q % d == 0:
+                return q == d
+        d, r = q - 1, 0
+        while d % 2 == 0:
+            d, r = d // 2, r + 1
+        for b in (2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37):
+            y = pow(b, d, q)
+            if y in (1, q - 1):
+                continue
+            for _ in range(r - 1):
+                y = y * y % q
+                if y == q - 1:
+                    break
+            else:
+                return False
+        return True
+
+    def rho(q):
+        for c in range(1, 100):
+            xx = yy = 2
+            g = 1
+            while g == 1:
+                xx = (xx * xx + c) % q
+                yy = (yy * yy + c) % q
+                yy = (yy * yy + c) % q
+                g = _m.gcd(abs(xx - yy), q)
+            if g != q:
+                return g
+        raise AssertionError("no factor")
+
+    out, stack = set(), [x]
+    while stack:
+        q = stack.pop()
+        if q == 1:
+            continue
+        for d in range(2, 1000):
+            while q % d == 0:
+                out.add(d)
+                q //= d
+        if q == 1:
+            continue
+        if is_p(q):
+            out.add(q)
+        else:
+            g = rho(q)
+            stack += [g, q // g]
+    return out
+
+
+def _is_primitive_root(a, p):
+    return all(pow(a, (p - 1) // q, p) != 1 for q in _pr_factors(p - 1))
+
+
+@pytest.mark.parametrize("p,a", [(9223372036854771239, 11), (3094861432531188877, 6),
+                                 (8708977279037121833, 3), (6944567280899478719, 11),
+                                 (2606314051492085141, 2), (4294967311, 3)])
+def test_validation_of_wide_skip_primes(ph, p, a):
+    """Skip primes between 2^32 and 2^63 for 64-bit moduli (the paper's 63-bit
+    skip generator): a primitive root is accepted and a quadratic residue (a^2)
+    refused -- the library factors p - 1 (Pollard's rho; here p - 1 has prime
+    factors up to 2^62) and agrees with plain Python throughout."""
+    assert workloads.is_prime(p) and _is_primitive_root(a, p)
+    assert ph.phprng_validate(64, [(N64, 3, p, a, 5, 7)], 0)[0] == 0
+    assert ph.phprng_validate(0, [(N64, 3, p, a, 5, 7)], 0)[0] == 0
+    sq = a * a % p
+    assert not _is_primitive_root(sq, p)
+    assert ph.phprng_validate(64, [(N64, 3, p, sq, 5, 7)], 0)[0] == 4
+
+
+def test_validation_refuses_bad_wide_skips(ph):
+    p = 9223372036854771239
+    composite = p + 2
+    assert not workloads.is_prime(composite)
+    assert ph.phprng_validate(64, [(N64, 3, composite, 11, 5, 7)], 0)[0] == 4
+    big = (1 << 63) + 29                                   # a prime at or above 2^63
+    while not workloads.is_prime(big):
+        big += 2
+    assert ph.phprng_validate(64, [(N64, 3, big, 2, 5, 7)], 0)[0] == 4
+    assert ph.phprng_validate(64, [(N64, 3, p, 11, 5, p)], 0)[0] == 4     # s0 = p
+    # a 32-bit modulus cannot take a skip prime above 2^32 (p < n)
+    assert ph.phprng_validate(32, [(4294967087, 9, 4294967311, 3, 5, 7)], 0)[0] == 4
 
 
 def test_validation_reports_first_bad_index(ph):
