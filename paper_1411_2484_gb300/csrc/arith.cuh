@@ -133,6 +133,15 @@ PH_HD uint64_t addmod64(uint64_t a, uint64_t b, uint64_t n)
     return (t < a || t >= n) ? t - n : t;
 }
 
+// a + b reduced only when it wraps past 2^32, for any a < 2^32 and b < n: the
+// result is below 2^32 and congruent to a + b mod n (a wrapped sum exceeds n,
+// and a + b - n < 2^32 because b < n), not necessarily below n.
+PH_HD uint32_t addmod32_lazy(uint32_t a, uint32_t b, uint32_t n)
+{
+    const uint32_t t = a + b;
+    return t < b ? t - n : t;
+}
+
 // (a - b) mod n for a, b < n.
 PH_HD uint32_t submod32(uint32_t a, uint32_t b, uint32_t n)
 {

@@ -140,8 +140,14 @@ gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
                 const uint64_t my0 = g0 + (uint64_t)NPT * lane;
                 sig_last = sig;
                 g_last = g0;
-                messages32<NPT>(P, sk, lane, my0, len, M, sig, sv, msg);
-                if (g0) store_group<NPT, CT, uint32_t>(P, cdst, rdst, myp, len, vec_ok, xp);
+                // every group but the last is full: the messages of a full
+                // group and the stores of the previous group skip the
+                // per-number bounds checks
+                if (g0 + G <= len)
+                    messages32<NPT, true>(P, sk, lane, my0, len, M, sig, sv, msg);
+                else
+                    messages32<NPT>(P, sk, lane, my0, len, M, sig, sv, msg);
+                if (g0) store_group<NPT, CT, uint32_t, true>(P, cdst, rdst, myp, len, vec_ok, xp);
                 encrypt32<NPT>(P, pg, msg, x);
 #pragma unroll
                 for (int u = 0; u < NPT; ++u) xp[u] = x[u];
@@ -155,8 +161,7 @@ gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
                 sig_last = sig;
                 g_last = g0;
                 // full groups skip the per-number bounds checks (fewer
-                // instructions and registers; the LIGHT loop keeps one path,
-                // where the split cost a spill)
+                // instructions and registers)
                 const bool full = g0 + G <= len;             // warp-uniform
                 if (full)
                     messages32<NPT, true>(P, sk, lane, my0, len, M, sig, sv, msg);
@@ -181,7 +186,7 @@ gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
                 messages32<NPT, true>(P, sk, lane, my0, len, M, sig, sv, msg);
             else
                 messages32<NPT>(P, sk, lane, my0, len, M, sig, sv, msg);
-            if (wb) write_ms_if_last<NPT, uint32_t>(st, i, lane, g0, len, pos_after, sv, msg);
+            if (wb) write_ms_if_last<NPT, uint32_t>(st, i, lane, g0, len, pos_after, sv, msg, P.n);
             encrypt32<NPT>(P, pg, msg, x);
             store_group<NPT, CT, uint32_t>(P, cdst, rdst, my0, len, vec_ok, x);
             if (wb) write_c_if_last<NPT, uint32_t>(st, i, lane, g0, len, x);

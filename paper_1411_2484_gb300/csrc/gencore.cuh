@@ -68,6 +68,13 @@ __device__ __forceinline__ uint64_t chunk_message(const SplitArgs &sp, uint64_t 
 
 // FULL: the whole warp group lies inside the run (no number past len), so
 // the per-number bounds checks are left out.
+//
+// The lane's skip sum and its messages are formed with lazy additions (a
+// skip is below p < n): the sum is reduced once before the scan (one
+// subtraction when n > 2^31, where every 32-bit value is below 2n), and each
+// msg_u is the message mod n up to a multiple of n, a value below 2^32 --
+// which the Montgomery products of the encryption accept (their outputs stay
+// below 2^32, and the exit product by K < n returns c < n).  M stays reduced.
 template <int NPT, bool FULL = false>
 __device__ __forceinline__ void messages32(const DevInst &P, const SkipConst &sk, int lane,
                                            uint64_t my0, uint64_t len, uint32_t &M, uint32_t &sig,
@@ -79,8 +86,9 @@ __device__ __forceinline__ void messages32(const DevInst &P, const SkipConst &sk
     for (int u = 0; u < NPT; ++u) {
         t = skip_step(sk, t, false);                             // Eq. 9a
         sv[u] = t;
-        if (FULL || my0 + u < len) S = addmod32(S, t, n);
+        if (FULL || my0 + u < len) S = addmod32_lazy(S, t, n);
     }
+    S = (n >> 31) ? (S >= n ? S - n : S) : S % n;
     uint32_t incl = S;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
@@ -91,7 +99,7 @@ __device__ __forceinline__ void messages32(const DevInst &P, const SkipConst &sk
     uint32_t mm = addmod32(M, submod32(incl, S, n), n);
 #pragma unroll
     for (int u = 0; u < NPT; ++u) {
-        mm = addmod32(mm, sv[u], n);                              // Eq. 9b
+        mm = addmod32_lazy(mm, sv[u], n);                         // Eq. 9b (mod n up to a multiple of n)
         msg[u] = mm;
     }
     M = addmod32(M, total, n);
@@ -229,14 +237,15 @@ __device__ __forceinline__ bool owns_last(int lane, uint64_t g0, uint64_t len, i
 template <int NPT, typename MT>
 __device__ __forceinline__ void write_ms_if_last(DevState st, uint64_t i, int lane, uint64_t g0,
                                                  uint64_t len, uint64_t pos_after,
-                                                 const uint32_t (&sv)[NPT], const MT (&msg)[NPT])
+                                                 const uint32_t (&sv)[NPT], const MT (&msg)[NPT],
+                                                 uint64_t n)
 {
     int ul;
     if (!owns_last<NPT>(lane, g0, len, &ul)) return;
 #pragma unroll
     for (int u = 0; u < NPT; ++u) {
         if (u == ul) {
-            st.m[i] = msg[u];
+            st.m[i] = (uint64_t)msg[u] % (uint64_t)n;           // 32-bit messages are lazy
             st.s[i] = sv[u];
         }
     }

@@ -16,6 +16,10 @@ CASE is one of
             over sequences of M = 2^20 (the paper's), 8,192 bins       fft_*_kernel
   batched   2,000 instances (80 % 32-bit), lengths log-uniform in
             [1, 2^18], offsets in [0, 2^40), R (about 0.4 GiB)       batch_kernel
+  batched20k  the batched bench workload's 20,000 instances (16,000
+            32-bit, 4,000 64-bit) and offsets, lengths log-uniform in
+            [1, 2^20] (--max-len, default the bench's 2^20: 12 GiB of R;
+            2^15 gives 0.5 GiB for multi-pass captures)              batch_kernel
 Each case warms up once, then launches its kernel N times (default 3) and
 prints the CUDA-event time per launch.  Inputs are the seeded workloads of
 paper_1411_2484_gb300.workloads.
@@ -31,8 +35,10 @@ from paper_1411_2484_gb300 import workloads
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["plain32", "fused32", "small_e", "serial2", "pattern3", "wide64", "batched", "fourier20", "inter2"])
+    ap.add_argument("case", choices=["plain32", "fused32", "small_e", "serial2", "pattern3", "wide64", "batched",
+                                     "batched20k", "fourier20", "inter2"])
     ap.add_argument("--repeat", type=int, default=3)
+    ap.add_argument("--max-len", type=int, default=1 << 20)
     args = ap.parse_args()
     s = torch.cuda.current_stream()
     ctx, plan = None, None
@@ -86,6 +92,18 @@ def main():
         r = torch.empty(N * per, dtype=torch.float64, device="cuda")
         run = lambda: ph.phprng_generate(ctx, 0, N, per, None, r, None, s)
         numbers = N * per
+    elif args.case == "batched20k":
+        w = workloads.WORKLOADS["batched_20000_mixed"]
+        i32 = ph.phprng_draw_instances(32, w["instances32"], w["seed"], ph.PHPRNG_REQUIRE_SAFE_PRIME)
+        i64 = ph.phprng_draw_instances(64, w["instances64"], w["seed"] + 1, ph.PHPRNG_REQUIRE_SAFE_PRIME)
+        inst = workloads.concat_instances(i32, i64)
+        reqs = workloads.batched_requests(w["instances32"], w["instances64"], args.max_len, w["max_offset"],
+                                          w["seed"] + 2)
+        numbers = int(reqs["len"].sum())
+        ctx = ph.phprng_create(0, inst, 0, s)
+        r = torch.empty(numbers, dtype=torch.float64, device="cuda")
+        plan = ph.phprng_plan_create(ctx, reqs, 0, s)
+        run = lambda: ph.phprng_plan_launch(plan, None, r, s, ctx=ctx)
     else:
         i32 = workloads.draw_instances(1600, seed=0x5EED0005)
         i64 = workloads.draw_instances(400, width=64, seed=0x5EED0006)

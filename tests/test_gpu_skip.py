@@ -146,16 +146,17 @@ def test_skip_after_generate_and_c_state(ph, torch):
 
 
 def test_microbench_rates(ph, torch):
-    rates = [ph.phprng_microbench(w) for w in range(8)]
+    rates = [ph.phprng_microbench(w) for w in range(12)]
     assert all(r > 1e9 for r in rates), rates
     # the exponent programs run Montgomery products no faster than a bare chain
     assert rates[5] < 1.05 * rates[3], rates
     # R from integers outruns the FP64 division it replaces (GB300's FP64 rate)
     assert rates[7] > rates[6], rates
     print("mul.lo %.3g mad.hi %.3g mad.wide %.3g mont32 %.3g dfma %.3g programs %.3g "
-          "div.f64 %.3g R-int %.3g per s" % tuple(rates))
+          "div.f64 %.3g R-int %.3g mul.wide %.3g mont32(lo,hi) %.3g mont32c %.3g shoup %.3g per s"
+          % tuple(rates))
     with pytest.raises(ph.PhprngError):
-        ph.phprng_microbench(8)
+        ph.phprng_microbench(12)
 
 
 @pytest.mark.parametrize("width", [32, 64])
