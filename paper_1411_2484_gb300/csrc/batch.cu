@@ -26,7 +26,7 @@ namespace phprng {
 template <int NPT, typename CT>
 __device__ __forceinline__ void run_tile32(const BatchArgs &a, const DevInst &P, const ExpProg &pg,
                                            uint64_t i, int lane, uint32_t m, uint32_t s,
-                                           const Tile &T, bool wb, bool vec_ok)
+                                           const Tile &T, bool wb, bool vec_ok, uint4 *etb)
 {
     constexpr uint64_t G = 32 * NPT;
     const SkipConst &sk = NPT == 8 ? a.sk32_8 : a.sk32_4;
@@ -43,7 +43,7 @@ __device__ __forceinline__ void run_tile32(const BatchArgs &a, const DevInst &P,
         sig_last = sig;
         g_last = g0;
         messages32<NPT>(P, sk, lane, my0, len, M, sig, sv, msg);
-        encrypt32<NPT>(P, pg, msg, x);
+        encrypt32_tb<NPT>(P, pg, msg, x, etb, lane);
         store_group<NPT, CT, uint32_t>(P, cdst, rdst, my0, len, vec_ok, x);
     }
     if (wb) write_state_after<NPT, uint32_t, uint32_t>(a.st, sk, i, lane, g_last, len, T.start + len, M,
@@ -53,7 +53,7 @@ __device__ __forceinline__ void run_tile32(const BatchArgs &a, const DevInst &P,
 template <int NPT>
 __device__ __forceinline__ void run_tile64(const BatchArgs &a, const DevInst &P, const ExpProg &pg,
                                            uint64_t i, int lane, uint64_t m, uint32_t s,
-                                           const Tile &T, bool wb, bool vec_ok)
+                                           const Tile &T, bool wb, bool vec_ok, uint4 *etb)
 {
     constexpr uint64_t G = 32 * NPT;
     const SkipConst &sk = a.sk64;
@@ -72,7 +72,7 @@ __device__ __forceinline__ void run_tile64(const BatchArgs &a, const DevInst &P,
         sig_last = sig;
         g_last = g0;
         messages64<NPT>(P, sk, lane, my0, len, M, sig, sv, msg);
-        encrypt64<NPT>(P, pg, msg, x);
+        encrypt_tb<NPT, uint64_t>(P, pg, msg, x, etb, lane);
         store_group<NPT, uint64_t, uint64_t>(P, cdst, rdst, my0, len, vec_ok, x);
     }
     if (wb) write_state_after<NPT, uint64_t, uint64_t>(a.st, sk, i, lane, g_last, len, T.start + len, M,
@@ -82,6 +82,10 @@ __device__ __forceinline__ void run_tile64(const BatchArgs &a, const DevInst &P,
 template <int NPT32, typename CT>
 __global__ void __launch_bounds__(256, PH_BATCH_MINB) batch_kernel(BatchArgs a)
 {
+    // per warp: the exponent program's odd powers (32-bit tiles: NPT32 words
+    // per entry and lane, 64-bit tiles: PH_NPT64 double words)
+    constexpr int kRows = NPT32 / 4 > PH_NPT64 / 2 ? NPT32 / 4 : PH_NPT64 / 2;
+    __shared__ uint4 etb[8][4 * kRows * 32];
     const int lane = threadIdx.x & 31;
     for (;;) {
         unsigned long long t = 0;
@@ -97,10 +101,10 @@ __global__ void __launch_bounds__(256, PH_BATCH_MINB) batch_kernel(BatchArgs a)
         skip_state_warp(a.tb, P, a.m0[i], a.L0[i], T.start, &m, &s, &L);   // Eq. 7
         const bool vec_ok = a.vec_ok && (T.c_off % (16 / sizeof(CT)) == 0) && (T.r_off % 2 == 0);
         if (!wide)
-            run_tile32<NPT32, CT>(a, P, a.prog[i], i, lane, (uint32_t)m, s, T, wb, vec_ok);
+            run_tile32<NPT32, CT>(a, P, a.prog[i], i, lane, (uint32_t)m, s, T, wb, vec_ok, etb[threadIdx.x >> 5]);
         else
             run_tile64<PH_NPT64>(a, P, a.prog[i], i, lane, m, s, T, wb,
-                          a.vec_ok && (T.c_off % 2 == 0) && (T.r_off % 2 == 0));
+                          a.vec_ok && (T.c_off % 2 == 0) && (T.r_off % 2 == 0), etb[threadIdx.x >> 5]);
     }
 }
 

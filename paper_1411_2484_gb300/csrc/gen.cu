@@ -16,7 +16,7 @@
 namespace phprng {
 
 #ifndef PH_MINB32
-#define PH_MINB32 2
+#define PH_MINB32 3
 #endif
 #ifndef PH_WPB
 #define PH_WPB 8
@@ -25,14 +25,18 @@ static constexpr int kNPT = PH_NPT32;     // numbers per lane per group (32-bit 
 static constexpr int kNPT64 = PH_NPT64;   // numbers per lane per group (64-bit path)
 static constexpr int kWarpsPerBlock = PH_WPB;
 #ifndef PH_WPB_HEAVY
-#define PH_WPB_HEAVY 10
+#define PH_WPB_HEAVY 8
 #endif
 #ifndef PH_WPB_LIGHT
 #define PH_WPB_LIGHT 8
 #endif
 static constexpr int kWarpsLight = PH_WPB_LIGHT;   // warps per block of the LIGHT instantiation
-static constexpr int kWarpsHeavy = PH_WPB_HEAVY;   // warps per block of the plain heavy instantiation (90 registers: 20 warps per SM)
+static constexpr int kWarpsHeavy = PH_WPB_HEAVY;   // warps per block of the plain heavy instantiation (3 blocks of 8 warps per SM, exponent tables in shared memory)
 static constexpr unsigned kFull = kFullMask;
+// shared memory of one warp's exponent table in the heavy plain launch
+static constexpr size_t kTableBytes = 4 * (kNPT / 4) * 32 * sizeof(uint4);
+// ... and of a block of the 64-bit launch (kWarpsPerBlock warps, NPT64 values of 8 bytes)
+static constexpr size_t kTable64Bytes = (size_t)kWarpsPerBlock * 4 * (kNPT64 / 2) * 32 * sizeof(uint4);
 
 int gen_npt(int wide) { return wide ? kNPT64 : kNPT; }
 
@@ -61,7 +65,7 @@ __device__ __forceinline__ double u128d(u128 v) { return u128_to_double((uint64_
 // leave their ciphertexts in `edge` so stats_edge_kernel can pair instances
 // that straddle two blocks.
 #ifndef PH_MINB_STATS
-#define PH_MINB_STATS 2
+#define PH_MINB_STATS 3
 #endif
 
 #ifndef PH_MINB_LIGHT
@@ -81,7 +85,7 @@ gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
              phprng_stats *__restrict__ stats, uint32_t *__restrict__ edge,
              const uint32_t *__restrict__ order, SplitArgs sp)
 {
-    extern __shared__ uint32_t smem[];   // STATS: cbuf[2][W][32*NPT] then hist[W][256]
+    extern __shared__ __align__(16) uint32_t smem[];   // STATS: cbuf[2][W][32*NPT], hist[W][256], exponent tables; heavy plain: exponent tables
     constexpr int W = WB;
     constexpr uint64_t G = 32 * NPT;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -155,6 +159,9 @@ gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
             }
             store_group<NPT, CT, uint32_t>(P, cdst, rdst, myp, len, vec_ok, xp);
         } else {
+            // the exponent program's table of odd powers lives in shared
+            // memory (dynamic, kTableBytes per warp)
+            uint4 *tb = reinterpret_cast<uint4 *>(smem) + warp * (NPT / 4) * 4 * 32;
             for (uint64_t g0 = 0; g0 < len; g0 += G) {
                 uint32_t sv[NPT], msg[NPT];
                 const uint64_t my0 = g0 + (uint64_t)NPT * lane;
@@ -167,7 +174,7 @@ gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
                     messages32<NPT, true>(P, sk, lane, my0, len, M, sig, sv, msg);
                 else
                     messages32<NPT>(P, sk, lane, my0, len, M, sig, sv, msg);
-                encrypt32<NPT>(P, pg, msg, x);
+                encrypt32_tb<NPT>(P, pg, msg, x, tb, lane);
                 if (full)
                     store_group<NPT, CT, uint32_t, true>(P, cdst, rdst, my0, len, vec_ok, x);
                 else
@@ -187,7 +194,10 @@ gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
             else
                 messages32<NPT>(P, sk, lane, my0, len, M, sig, sv, msg);
             if (wb) write_ms_if_last<NPT, uint32_t>(st, i, lane, g0, len, pos_after, sv, msg, P.n);
-            encrypt32<NPT>(P, pg, msg, x);
+            encrypt32_tb<NPT>(P, pg, msg, x,
+                              reinterpret_cast<uint4 *>(smem + 2 * W * (32 * NPT) + W * 256) +
+                                  warp * (NPT / 4) * 4 * 32,
+                              lane);
             store_group<NPT, CT, uint32_t>(P, cdst, rdst, my0, len, vec_ok, x);
             if (wb) write_c_if_last<NPT, uint32_t>(st, i, lane, g0, len, x);
         }
@@ -292,14 +302,18 @@ stats_edge_kernel(const DevInst *__restrict__ inst, const uint32_t *__restrict__
 
 // WSKIP: a wide skip prime (p >= 2^32, SkipConst64 skw, 64-bit skips); such
 // launches are never split.
+#ifndef PH_MINB64
+#define PH_MINB64 3
+#endif
 template <int NPT, bool WSKIP>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, 2)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, PH_MINB64)
 gen64_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, DevState st,
              SkipConst sk, SkipConst64 skw, uint64_t first, uint64_t num, uint64_t per_inst,
              uint64_t *__restrict__ c_out, double *__restrict__ r_out, int vec_ok,
              const uint32_t *__restrict__ order, SplitArgs sp)
 {
     typedef typename std::conditional<WSKIP, uint64_t, uint32_t>::type SW;
+    extern __shared__ uint4 tb64[];                   // per warp: the exponent program's odd powers
     constexpr uint64_t G = 32 * NPT;
     const int lane = threadIdx.x & 31;
     const uint64_t w = (uint64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
@@ -347,7 +361,7 @@ gen64_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
             messages64<NPT, SkipConst64, uint64_t>(P, skw, lane, my0, len, M, sig, sv, msg);
         else
             messages64<NPT>(P, sk, lane, my0, len, M, sig, sv, msg);
-        encrypt64<NPT>(P, pg, msg, x);
+        encrypt_tb<NPT, uint64_t>(P, pg, msg, x, tb64 + (threadIdx.x >> 5) * (NPT / 2) * 4 * 32, lane);
         store_group<NPT, uint64_t, uint64_t>(P, cdst, rdst, my0, len, vec_ok, x);
     }
     if (wb) {
@@ -425,7 +439,14 @@ int launch_gen32(const GenArgs &a, void *stream, std::string *err)
     const uint64_t blocks_light = ((a.num << a.sp.log2K) + kWarpsLight - 1) / kWarpsLight;
     cudaStream_t s = (cudaStream_t)stream;
     if (a.stats) {
-        const size_t smem = (2 * kWarpsPerBlock * 32 * kNPT + kWarpsPerBlock * 256) * sizeof(uint32_t);
+        const size_t smem = (2 * kWarpsPerBlock * 32 * kNPT + kWarpsPerBlock * 256) * sizeof(uint32_t) +
+                            kWarpsPerBlock * kTableBytes;
+        if (smem > 48 * 1024) {                         // above the default 48 KiB (current device)
+            cudaFuncSetAttribute(gen32_kernel<kNPT, uint32_t, true, false, kWarpsPerBlock>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(gen32_kernel<kNPT, uint64_t, true, false, kWarpsPerBlock>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        }
         if (a.c_is_64)
             gen32_kernel<kNPT, uint64_t, true, false, kWarpsPerBlock><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(
                 a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, (uint64_t *)a.c_out, a.r_out,
@@ -441,9 +462,17 @@ int launch_gen32(const GenArgs &a, void *stream, std::string *err)
         return check_launch(err, "stats_edge_kernel launch");
     }
 #define PH_GEN32_PLAIN(CTY, LT, WB, NB)                                                             \
-    gen32_kernel<kNPT, CTY, false, LT, WB><<<(unsigned)(NB), WB * 32, 0, s>>>(                      \
+    gen32_kernel<kNPT, CTY, false, LT, WB><<<(unsigned)(NB), WB * 32, LT ? 0 : WB * kTableBytes, s>>>(     \
         a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, (CTY *)a.c_out, a.r_out, a.vec_ok, \
         nullptr, nullptr, a.order, a.sp)
+    if (!a.light && kWarpsHeavy * kTableBytes > 48 * 1024) {
+        // exponent tables above the default 48 KiB of dynamic shared memory
+        // need the kernel's explicit limit (on the current device)
+        cudaFuncSetAttribute(gen32_kernel<kNPT, uint32_t, false, false, kWarpsHeavy>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kWarpsHeavy * kTableBytes));
+        cudaFuncSetAttribute(gen32_kernel<kNPT, uint64_t, false, false, kWarpsHeavy>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kWarpsHeavy * kTableBytes));
+    }
     if (a.c_is_64) {
         if (a.light) PH_GEN32_PLAIN(uint64_t, true, kWarpsLight, blocks_light);
         else PH_GEN32_PLAIN(uint64_t, false, kWarpsHeavy, blocks_heavy);
@@ -470,11 +499,11 @@ int launch_gen64(const GenArgs &a, void *stream, std::string *err)
             *err = "gen64_kernel: launches with a wide skip prime are never split";
             return PHPRNG_EINVAL;
         }
-        gen64_kernel<kNPT64, true><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, (cudaStream_t)stream>>>(
+        gen64_kernel<kNPT64, true><<<(unsigned)blocks, kWarpsPerBlock * 32, kTable64Bytes, (cudaStream_t)stream>>>(
             a.inst, a.prog, a.st, a.sk, a.skw, a.first, a.num, a.per_inst, (uint64_t *)a.c_out, a.r_out,
             a.vec_ok, a.order, a.sp);
     } else {
-        gen64_kernel<kNPT64, false><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, (cudaStream_t)stream>>>(
+        gen64_kernel<kNPT64, false><<<(unsigned)blocks, kWarpsPerBlock * 32, kTable64Bytes, (cudaStream_t)stream>>>(
             a.inst, a.prog, a.st, a.sk, a.skw, a.first, a.num, a.per_inst, (uint64_t *)a.c_out, a.r_out,
             a.vec_ok, a.order, a.sp);
     }
@@ -502,7 +531,7 @@ uint64_t gen_resident_warps()
         int sms = 0, b = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, gen32_kernel<kNPT, uint32_t, false, false, kWarpsHeavy>,
-                                                      kWarpsHeavy * 32, 0);
+                                                      kWarpsHeavy * 32, kWarpsHeavy * kTableBytes);
         cached[dev] = (uint64_t)(sms > 0 ? sms : 1) * (b > 0 ? b : 1) * kWarpsHeavy;
     }
     return cached[dev];

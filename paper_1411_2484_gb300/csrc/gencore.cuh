@@ -149,9 +149,26 @@ __device__ __forceinline__ void encrypt(const DevInst &P, const ExpProg &pg, con
 {
     const W n = (W)P.n, ninv = (W)P.ninv, K = (W)P.K, Kq = (W)(P.ninv >> 32);
     if (P.fermat) {
+        // the first squaring reads the messages directly; the paper's
+        // e = 9 and 17 (t = 3, 4) and e = 3, 5 run unrolled chains
 #pragma unroll
-        for (int u = 0; u < NPT; ++u) x[u] = msg[u];
-        for (uint32_t q = P.fermat; q > 0; --q) mont_sqr_vec<NPT>(x, n, ninv);
+        for (int u = 0; u < NPT; ++u) x[u] = mont(msg[u], msg[u], n, ninv);
+        switch (P.fermat) {
+        case 1: break;
+        case 2: mont_sqr_vec<NPT>(x, n, ninv); break;
+        case 3:
+            mont_sqr_vec<NPT>(x, n, ninv);
+            mont_sqr_vec<NPT>(x, n, ninv);
+            break;
+        case 4:
+            mont_sqr_vec<NPT>(x, n, ninv);
+            mont_sqr_vec<NPT>(x, n, ninv);
+            mont_sqr_vec<NPT>(x, n, ninv);
+            break;
+        default:
+            for (uint32_t q = P.fermat; q > 1; --q) mont_sqr_vec<NPT>(x, n, ninv);
+            break;
+        }
         mont_vec<NPT>(x, msg, n, ninv);
 #pragma unroll
         for (int u = 0; u < NPT; ++u) x[u] = mont_exit(x[u], K, Kq, n, ninv);
@@ -170,6 +187,107 @@ __device__ __forceinline__ void encrypt64(const DevInst &P, const ExpProg &pg, c
                                           uint64_t (&x)[NPT])
 {
     encrypt<NPT, uint64_t>(P, pg, msg, x);
+}
+
+// The window program of Eq. 9c with its table of odd powers m, m^3, m^5, m^7
+// in shared memory instead of registers: per warp 4 entries x NPT values per
+// lane, laid out [entry][row][lane] as uint4 rows (four 32-bit or two 64-bit
+// values), so that each access of a warp is one conflict-free 512-byte row; a
+// lane reads back only its own words, so no synchronisation is needed.  Frees
+// 3 NPT values' registers (more resident warps hide the products' latency
+// better) for 16-byte loads per window.
+template <int NPT, typename W>
+__device__ __forceinline__ void put_row(uint4 *__restrict__ tb, int e, int lane, const W (&v)[NPT])
+{
+    constexpr int Q = NPT * (int)sizeof(W) / 16;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        uint4 w;
+        if (sizeof(W) == 4)
+            w = make_uint4((uint32_t)v[4 * q], (uint32_t)v[4 * q + 1], (uint32_t)v[4 * q + 2], (uint32_t)v[4 * q + 3]);
+        else
+            w = make_uint4((uint32_t)v[2 * q], (uint32_t)((uint64_t)v[2 * q] >> 32),
+                           (uint32_t)v[2 * q + 1], (uint32_t)((uint64_t)v[2 * q + 1] >> 32));
+        tb[(e * Q + q) * 32 + lane] = w;
+    }
+}
+
+template <int NPT, typename W>
+__device__ __forceinline__ void get_row(const uint4 *__restrict__ tb, int e, int lane, W (&v)[NPT])
+{
+    constexpr int Q = NPT * (int)sizeof(W) / 16;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const uint4 w = tb[(e * Q + q) * 32 + lane];
+        if (sizeof(W) == 4) {
+            v[4 * q] = w.x; v[4 * q + 1] = w.y; v[4 * q + 2] = w.z; v[4 * q + 3] = w.w;
+        } else {
+            v[2 * q] = (W)(((uint64_t)w.y << 32) | w.x);
+            v[2 * q + 1] = (W)(((uint64_t)w.w << 32) | w.z);
+        }
+    }
+}
+
+template <int NPT, typename W>
+__device__ __forceinline__ void modexp_prog_smem(W (&x)[NPT], const W (&m)[NPT], const ExpProg &pg, W n, W ninv,
+                                                 W K, W Kq, uint4 *__restrict__ tb, int lane)
+{
+    static_assert(NPT * sizeof(W) % 16 == 0, "table rows are 16 bytes");
+    const int tbl = pg.tbl;
+    put_row<NPT, W>(tb, 0, lane, m);
+    if (tbl >= 2) {
+        W m2[NPT], t[NPT];
+#pragma unroll
+        for (int u = 0; u < NPT; ++u) m2[u] = mont(m[u], m[u], n, ninv);          // m^2
+#pragma unroll
+        for (int u = 0; u < NPT; ++u) t[u] = mont(m2[u], m[u], n, ninv);          // m^3
+        put_row<NPT, W>(tb, 1, lane, t);
+        if (tbl == 4) {
+            mont_vec<NPT>(t, m2, n, ninv);                                         // m^5
+            put_row<NPT, W>(tb, 2, lane, t);
+            mont_vec<NPT>(t, m2, n, ninv);                                         // m^7
+            put_row<NPT, W>(tb, 3, lane, t);
+        }
+    }
+    get_row<NPT, W>(tb, pg.ent[0] >> 6, lane, x);
+    const int nent = pg.nent;
+    int bnext = pg.ent[1];
+    for (int k = 1; k < nent; ++k) {
+        const int b = bnext;
+        bnext = pg.ent[k + 1 < (int)sizeof pg.ent ? k + 1 : k];   // next entry, loaded early
+        int sq = b & 63;
+        for (; sq >= 2; sq -= 2) {
+            mont_sqr_vec<NPT>(x, n, ninv);
+            mont_sqr_vec<NPT>(x, n, ninv);
+        }
+        if (sq) mont_sqr_vec<NPT>(x, n, ninv);
+        W y[NPT];
+        get_row<NPT, W>(tb, b >> 6, lane, y);
+        mont_vec<NPT>(x, y, n, ninv);
+    }
+    for (int sq = pg.tail; sq > 0; --sq) mont_sqr_vec<NPT>(x, n, ninv);
+#pragma unroll
+    for (int u = 0; u < NPT; ++u) x[u] = mont_exit(x[u], K, Kq, n, ninv);
+}
+
+// Eq. 9c with the program's table in shared memory (tb: 4 NPT sizeof(W) * 32
+// bytes per warp, 16-byte aligned); straight chains need no table.
+template <int NPT, typename W>
+__device__ __forceinline__ void encrypt_tb(const DevInst &P, const ExpProg &pg, const W (&msg)[NPT], W (&x)[NPT],
+                                           uint4 *tb, int lane)
+{
+    if (P.fermat) {
+        encrypt<NPT, W>(P, pg, msg, x);
+        return;
+    }
+    modexp_prog_smem<NPT, W>(x, msg, pg, (W)P.n, (W)P.ninv, (W)P.K, (W)(P.ninv >> 32), tb, lane);
+}
+
+template <int NPT>
+__device__ __forceinline__ void encrypt32_tb(const DevInst &P, const ExpProg &pg, const uint32_t (&msg)[NPT],
+                                             uint32_t (&x)[NPT], uint4 *tb, int lane)
+{
+    encrypt_tb<NPT, uint32_t>(P, pg, msg, x, tb, lane);
 }
 
 // R = (c+1)/(n+1) (Eq. 9d): integer-built and correctly rounded for 32-bit

@@ -16,6 +16,10 @@
 
 namespace phprng {
 
+#ifndef PH_SERIAL_MINB
+#define PH_SERIAL_MINB 3
+#endif
+
 // The bin of a number, floor(B R) taken on the double R = RN((c+1)/(n+1))
 // (Eq. 9d) with one IEEE product, RN(R B), then truncation -- what a program
 // binning the generator's doubles computes.  For n < 2^32 and B <= 2^20 this
@@ -75,13 +79,14 @@ __device__ __forceinline__ uint32_t poker_category(const uint32_t *h)
 // POKER: hands of five cards, denominations floor(10 R), into 7 category
 // counters (D = 5, B = 10); otherwise the serial test's B^D counters.
 template <int NPT, bool POKER, int WB>
-__global__ void __launch_bounds__(WB * 32, 2)
+__global__ void __launch_bounds__(WB * 32, PH_SERIAL_MINB)
 serial_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, DevState st,
               SkipConst sk, uint64_t first, uint64_t num, uint64_t per_inst, int D, uint32_t B,
               unsigned long long *__restrict__ hist, const uint32_t *__restrict__ order)
 {
     constexpr uint64_t G = 32 * NPT;
     __shared__ uint32_t tb[WB][32 * NPT + 8];  // per warp: a carried tuple start, then one group
+    __shared__ uint4 etb[WB][4 * (NPT / 4) * 32];   // per warp: the exponent program's odd powers
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint64_t w = (uint64_t)blockIdx.x * WB + warp;
     if (w >= num) return;
@@ -103,7 +108,7 @@ serial_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog
         sig_last = sig;
         g_last = g0;
         messages32<NPT>(P, sk, lane, my0, per_inst, M, sig, sv, msg);
-        encrypt32<NPT>(P, pg, msg, x);
+        encrypt32_tb<NPT>(P, pg, msg, x, etb[warp], lane);
 #pragma unroll
         for (int u = 0; u < NPT; ++u)
             if (my0 + u < per_inst) buf[carry + NPT * lane + u] = serial_bin(x[u], P.yN, P.ybits, r, B);
@@ -326,9 +331,9 @@ int launch_runs(const GenArgs &a, int lmax, unsigned long long *hist, void *stre
 }
 
 #ifndef PH_SERIAL_WARPS
-#define PH_SERIAL_WARPS 10
+#define PH_SERIAL_WARPS 8
 #endif
-static constexpr int kSerialWarps = PH_SERIAL_WARPS;   // warps per block of serial_kernel (84 registers, 2 blocks per SM)
+static constexpr int kSerialWarps = PH_SERIAL_WARPS;   // warps per block of serial_kernel (3 blocks per SM, exponent tables in shared memory)
 
 // Interstream serial test, step 1: bins floor(B R) of a chunk of c (Np
 // streams x L numbers, instance-major; uint64 elements when c64, as a
