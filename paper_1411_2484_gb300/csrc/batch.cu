@@ -20,7 +20,7 @@
 namespace phprng {
 
 #ifndef PH_BATCH_MINB
-#define PH_BATCH_MINB 2
+#define PH_BATCH_MINB 3
 #endif
 
 template <int NPT, typename CT>
