@@ -279,7 +279,10 @@ static int pointer_kind(const void *p)
 // so the grid still fills the GPU; the chunk starts cost one extra skip product
 // per number (the pre-pass) and a short sum per warp.
 static constexpr uint32_t kMaxSplit = 4096;
-static constexpr uint64_t kMinChunk = 1024;
+#ifndef PH_MIN_CHUNK
+#define PH_MIN_CHUNK 1024
+#endif
+static constexpr uint64_t kMinChunk = PH_MIN_CHUNK;
 
 static int prepare_split(phprng_ctx *c, uint64_t num, uint64_t per_inst, GenArgs *g, cudaStream_t s)
 {
