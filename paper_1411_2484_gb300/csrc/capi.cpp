@@ -957,6 +957,47 @@ PH_API int phprng_interstream_serial_test(phprng_ctx *ctx, uint64_t first, uint6
     CU(ctx, cudaSetDevice(ctx->device));
     if (pointer_kind(hist) != 1) return fail(ctx, PHPRNG_EINVAL, std::string(W) + "hist must be device memory");
     cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (ctx->width == 32 && B <= (1u << 16) && 32 % D == 0 && num_inst % (uint64_t)D == 0) {
+        // Direct form: every tuple of the interleaved sequence holds D streams'
+        // numbers of one index, so the bins are written in stream order by the
+        // generator itself and counted from there (chunks of about 2^25
+        // numbers, rows padded to a multiple of 8 bins)
+        uint64_t Lch = std::max<uint64_t>(256, (1ull << 25) / num_inst / 256 * 256);
+        if (Lch > per_inst) Lch = per_inst;
+        const uint64_t Lrow = (Lch + 7) / 8 * 8;
+        uint16_t *binsI = nullptr;
+        cudaError_t e = cudaMallocAsync((void **)&binsI, num_inst * Lrow * sizeof(uint16_t), s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, PHPRNG_ENOMEM, std::string(W) + "scratch allocation failed");
+        }
+        GenArgs g;
+        g.inst = ctx->d_inst;
+        g.prog = ctx->d_prog;
+        g.st = ctx->st;
+        g.sk = ctx->sk32_8;
+        g.first = first;
+        g.num = num_inst;
+        g.c_out = nullptr;
+        g.r_out = nullptr;
+        g.stats = nullptr;
+        g.edge = nullptr;
+        g.c_is_64 = 0;
+        g.vec_ok = 0;
+        int rc = PHPRNG_OK;
+        if (num_inst >= kOrderMinInstances && num_inst < (1ull << 32))
+            g.order = instance_order(ctx, first, num_inst, s, &rc);
+        std::string err;
+        for (uint64_t j0 = 0; j0 < per_inst && rc == PHPRNG_OK; j0 += Lch) {
+            g.per_inst = std::min(Lch, per_inst - j0);
+            rc = launch_inter_direct(g, Lrow, D, B, binsI, (unsigned long long *)hist, s, &err);
+            if (rc == PHPRNG_OK)
+                for (uint64_t i = first; i < first + num_inst; ++i) ctx->pos_host[i] += g.per_inst;
+        }
+        cudaFreeAsync(binsI, s);
+        if (rc != PHPRNG_OK) return err.empty() ? rc : fail(ctx, rc, std::string(W) + err);
+        return PHPRNG_OK;
+    }
     // chunks of Lch numbers per stream, a multiple of D so that no tuple of the
     // interleaved sequence spans two chunks; about 2^25 numbers per chunk
     uint64_t Lch = (1ull << 25) / num_inst / (uint64_t)D * (uint64_t)D;

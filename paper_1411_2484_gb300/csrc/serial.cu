@@ -408,6 +408,137 @@ inter_hist_kernel(const BT *__restrict__ binsT, uint64_t ntup, int D, uint32_t B
     }
 }
 
+// Interstream serial test, direct form for D | 32 and D | Np with B <= 2^16:
+// every tuple of the interleaved sequence then holds D streams' numbers of one
+// index j (stream a a multiple of D), so the tuples can be counted from the
+// bins in stream order without forming the interleaved sequence.
+//   inter_gen_kernel: Eq. 9 for one chunk (L numbers per stream) with each
+//     number's bin written at once as a 16-bit word, binsI[a Lrow + j] (Lrow
+//     a multiple of 8, so every lane stores its 8 bins as one 16-byte vector)
+//   inter_count_kernel: tiles of 32 streams x 64 indices through shared
+//     memory, each of the tile's 32/D tuples per index counted
+template <int NPT>
+__global__ void __launch_bounds__(kSerialWarps * 32, PH_SERIAL_MINB)
+inter_gen_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, DevState st,
+                 SkipConst sk, uint64_t first, uint64_t num, uint64_t len, uint64_t Lrow, uint32_t B,
+                 uint16_t *__restrict__ binsI, const uint32_t *__restrict__ order)
+{
+    constexpr int WB = kSerialWarps;
+    constexpr uint64_t G = 32 * NPT;
+    __shared__ uint4 etb[WB][4 * (NPT / 4) * 32];   // per warp: the exponent program's odd powers
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t w = (uint64_t)blockIdx.x * WB + warp;
+    if (w >= num) return;
+    const uint64_t j = order ? order[w] : w;
+    const uint64_t i = first + j;
+    const DevInst P = inst[i];
+    const ExpProg &pg = prog[i];
+    const uint32_t r = (uint32_t)(((uint64_t)B << 32) / P.yN);
+    uint32_t M = (uint32_t)st.m[i];
+    uint32_t sig = mont32((uint32_t)st.s[i], sk.lane[lane], sk.p, sk.pinv);
+    const uint64_t pos_after = st.pos[i] + len;
+    uint16_t *row = binsI + j * Lrow;
+    uint32_t x[NPT], sig_last = sig;
+    uint64_t g_last = 0;
+    for (uint64_t g0 = 0; g0 < len; g0 += G) {
+        uint32_t sv[NPT], msg[NPT];
+        const uint64_t my0 = g0 + (uint64_t)NPT * lane;
+        sig_last = sig;
+        g_last = g0;
+        const bool full = g0 + G <= len;                 // warp-uniform
+        if (full)
+            messages32<NPT, true>(P, sk, lane, my0, len, M, sig, sv, msg);
+        else
+            messages32<NPT>(P, sk, lane, my0, len, M, sig, sv, msg);
+        encrypt32_tb<NPT>(P, pg, msg, x, etb[warp], lane);
+        uint32_t b[NPT];
+#pragma unroll
+        for (int u = 0; u < NPT; ++u) b[u] = serial_bin(x[u], P.yN, P.ybits, r, B);
+        if (full && NPT == 8) {
+            *reinterpret_cast<uint4 *>(row + my0) =
+                make_uint4(b[0] | b[1] << 16, b[2] | b[3] << 16, b[4] | b[5] << 16, b[6] | b[7] << 16);
+        } else {
+#pragma unroll
+            for (int u = 0; u < NPT; ++u)
+                if (my0 + u < len) row[my0 + u] = (uint16_t)b[u];
+        }
+    }
+    write_state_after<NPT, uint32_t, uint32_t>(st, sk, i, lane, g_last, len, pos_after, M, sig_last, x);
+}
+
+static constexpr uint32_t kCountTileJ = 64;
+
+template <bool SMEM>
+__global__ void __launch_bounds__(256)
+inter_count_kernel(const uint16_t *__restrict__ binsI, uint64_t Np, uint64_t L, uint64_t Lrow, int D,
+                   uint32_t B, uint32_t nbins, unsigned long long *__restrict__ hist)
+{
+    __shared__ uint16_t tile[32][kCountTileJ + 2];
+    __shared__ uint32_t sh[SMEM ? kInterSmemBins : 1];
+    if (SMEM) {
+        for (uint32_t b = threadIdx.x; b < nbins; b += blockDim.x) sh[b] = 0;
+    }
+    const uint64_t a0 = (uint64_t)blockIdx.x * 32, j0 = (uint64_t)blockIdx.y * kCountTileJ;
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // rows of the tile: one stream each, kCountTileJ consecutive indices (two per lane)
+    for (uint32_t rr = warp; rr < 32; rr += 8) {
+        const uint64_t a = a0 + rr;
+        const uint64_t jj = j0 + 2 * lane;
+        if (a < Np && jj < L) {
+            tile[rr][2 * lane] = binsI[a * Lrow + jj];
+            if (jj + 1 < L) tile[rr][2 * lane + 1] = binsI[a * Lrow + jj + 1];
+        }
+    }
+    __syncthreads();
+    const uint32_t tpr = 32 / (uint32_t)D;                 // tuples per index in the tile
+    const uint32_t ntile = tpr * kCountTileJ;
+    for (uint32_t k = threadIdx.x; k < ntile; k += blockDim.x) {
+        const uint32_t jt = k / tpr, t = k - jt * tpr;
+        const uint64_t a = a0 + (uint64_t)t * D;
+        if (j0 + jt >= L || a + (uint64_t)D > Np) continue;
+        uint32_t idx = 0, scale = 1;
+        for (int d = 0; d < D; ++d) {
+            idx += (uint32_t)tile[t * D + d][jt] * scale;
+            scale *= B;
+        }
+        if (SMEM) atomicAdd(sh + idx, 1u);
+        else atomicAdd(hist + idx, 1ull);
+    }
+    if (SMEM) {
+        __syncthreads();
+        for (uint32_t b = threadIdx.x; b < nbins; b += blockDim.x)
+            if (sh[b]) atomicAdd(hist + b, (unsigned long long)sh[b]);
+    }
+}
+
+int launch_inter_direct(const GenArgs &a, uint64_t Lrow, int D, uint32_t B, uint16_t *binsI,
+                        unsigned long long *hist, void *stream, std::string *err)
+{
+    if (a.num == 0 || a.per_inst == 0) return PHPRNG_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint64_t blocks = (a.num + kSerialWarps - 1) / kSerialWarps;
+    inter_gen_kernel<8><<<(unsigned)blocks, kSerialWarps * 32, 0, s>>>(
+        a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, Lrow, B, binsI, a.order);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        *err = std::string("inter_gen_kernel launch: ") + cudaGetErrorString(e);
+        return PHPRNG_ECUDA;
+    }
+    uint32_t nbins = 1;
+    for (int d = 0; d < D; ++d) nbins *= B;
+    const dim3 grid((unsigned)((a.num + 31) / 32), (unsigned)((a.per_inst + kCountTileJ - 1) / kCountTileJ));
+    if (nbins <= kInterSmemBins)
+        inter_count_kernel<true><<<grid, 256, 0, s>>>(binsI, a.num, a.per_inst, Lrow, D, B, nbins, hist);
+    else
+        inter_count_kernel<false><<<grid, 256, 0, s>>>(binsI, a.num, a.per_inst, Lrow, D, B, nbins, hist);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        *err = std::string("inter_count_kernel launch: ") + cudaGetErrorString(e);
+        return PHPRNG_ECUDA;
+    }
+    return PHPRNG_OK;
+}
+
 int launch_inter_consts(const DevInst *inst, uint64_t first, uint64_t Np, uint32_t B, void *k, void *stream,
                         std::string *err)
 {
