@@ -141,9 +141,10 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
-def profile_traffic(kernel):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source (else None)."""
+def profile_entry(kernel):
+    """The committed ncu record of a kernel (DRAM bytes per launch, pipe
+    instruction counts per number), if it was taken on the current kernel
+    source (else None)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
@@ -157,7 +158,12 @@ def profile_traffic(kernel):
         h.update(open(os.path.join(ROOT, f), "rb").read())
     if h.hexdigest() != d.get("sha256"):
         return None
-    return d.get("bytes_per_launch")
+    return d
+
+
+def profile_traffic(kernel):
+    d = profile_entry(kernel)
+    return d.get("bytes_per_launch") if d else None
 
 
 def cpu_baseline(inst, per_inst, target_s=12.0):
@@ -741,6 +747,8 @@ def main():
                      "unit": "T mul32/s", "frac": achieved / PEAK_TMULS,
                      "traffic": profile_traffic("gen32_kernel"),
                      "kernel": "gen32_kernel",
+                     "ncu_inst_per_number": (profile_entry("gen32_kernel") or {}).get("ncu_inst_per_number"),
+                     "algorithmic_muls_per_number": muls / (N * per),
                      "peak_source": "152 SMs x 64 IMAD/clk x 2070 MHz (unit counts x max clock)",
                      "algorithmic_muls_per_launch": muls},
         "e2e": e2e,

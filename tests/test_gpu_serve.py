@@ -149,3 +149,43 @@ def test_mixed_width_serving(ph, torch, table31):
     finally:
         ph.phprng_server_destroy(srv)
         ph.phprng_destroy(ctx)
+
+
+def test_served_unit_and_constant_skip_streams_match_oracle(ph, torch):
+    """A server over constant-skip streams (a = 1: s_k = s0 = b for every k;
+    b = 1 is the unit skip): each served request starts at m0 + start b
+    (Eq. 3 summed) and equals the oracle's Eq. 9 from there, and the streams'
+    states after shutdown follow."""
+    inst = workloads.draw_instances(12, seed=611)
+    rows = workloads.instance_rows(inst).copy()
+    rows[:, 2], rows[:, 3] = 65537, 1                  # one skip generator per context
+    rows[:, 5] = np.arange(1, 13) * 5000
+    rows[:6, 5] = 1                                    # unit skip (b = 1) for the first six
+    ctx = ph.phprng_create(32, rows, ph.PHPRNG_ALLOW_SHARED_N)
+    srv = ph.phprng_server_create(ctx, 16 << 20, inflight=2, tile=0, want_c=1)
+    try:
+        rng = np.random.default_rng(9)
+        n = 60
+        streams = rng.integers(0, 12, n)
+        lens = rng.integers(1, 3000, n)
+        t0 = ph.phprng_clock_ns() + 2_000_000
+        arrivals = t0 + np.sort(rng.integers(0, 20_000_000, n))
+        ph.phprng_server_submit(srv, streams, lens, np.arange(n), arrivals)
+        got = drain(ph, srv, n)
+    finally:
+        ph.phprng_server_destroy(srv)
+    try:
+        for g in got:
+            n_, e, p, a, m0, b = (int(x) for x in rows[g["inst"]])
+            oc, orr, _ = oracle.generate(n_, e, p, a, (m0 + g["start"] * b) % n_, b, g["len"])
+            assert np.array_equal(g["c"].astype(np.uint64), oc)
+            assert np.array_equal(g["r"].view(np.uint64), orr.view(np.uint64))
+        total = {}
+        for k in range(n):
+            total[int(streams[k])] = total.get(int(streams[k]), 0) + int(lens[k])
+        for i, t in total.items():
+            s = ph.phprng_get_state(ctx, i)
+            n_, b, m0 = int(rows[i, 0]), int(rows[i, 5]), int(rows[i, 4])
+            assert s["pos"] == t and s["m"] == (m0 + t * b) % n_ and s["s"] == b
+    finally:
+        ph.phprng_destroy(ctx)
