@@ -138,8 +138,18 @@ PH_HD uint64_t addmod64(uint64_t a, uint64_t b, uint64_t n)
 // and a + b - n < 2^32 because b < n), not necessarily below n.
 PH_HD uint32_t addmod32_lazy(uint32_t a, uint32_t b, uint32_t n)
 {
+#if defined(__CUDA_ARCH__)
+    // both sums as separate PTX additions (a + b and (a + b) - n), chosen by
+    // the carry of the first: measured one instruction shorter than the
+    // conditional subtraction written in C
+    uint32_t t, r;
+    asm("add.u32 %0, %1, %2;" : "=r"(t) : "r"(a), "r"(b));
+    asm("sub.u32 %0, %1, %2;" : "=r"(r) : "r"(t), "r"(n));
+    return t < b ? r : t;
+#else
     const uint32_t t = a + b;
     return t < b ? t - n : t;
+#endif
 }
 
 // (a - b) mod n for a, b < n.
