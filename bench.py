@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=64)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--modes", default="fused,serial,interstream,small_e,pattern,fourier,figures,wide64,c0,batched,served",
+    ap.add_argument("--modes", default="fused,serial,interstream,consumers,small_e,pattern,fourier,figures,wide64,c0,batched,served",
                     help="comma-separated extra measurements after the headline, or 'none'")
     return ap.parse_args()
 
@@ -387,6 +387,37 @@ def mode_interstream(ph, torch, ctx, N, per, stream):
     return {"value": N * per / ms * 1e3, "unit": "PRNs/s", "ms_per_call": ms,
             "workload": "plain32 65,536 streams x 4,096, interleaved order, pairs into 2^20 bins",
             "chi2_z": (chi2 - dof) / (2 * dof) ** 0.5}
+
+
+def mode_consumers(ph, torch, ctx, N, per, stream):
+    """The poker, runs and collision tests of the Tests section, each fused on
+    the generator over 2^28 numbers: poker on the plain workload's 65,536 x
+    4,096 (hands of five numbers, ten denominations), runs on the same streams
+    (lengths to 32), collision on 16,384 of its instances x 16,384 numbers (the
+    paper's segments of 2^14 numbers into 2^20 bins).  Only the counters are
+    written."""
+    out = {}
+    hist = torch.zeros(7, dtype=torch.int64, device="cuda")
+    ms = timed(torch, stream, lambda: ph.phprng_poker_test(ctx, 0, N, per, hist, stream), 4)
+    out["poker"] = {"value": N * per / ms * 1e3, "unit": "PRNs/s", "ms_per_call": ms,
+                    "workload": "plain32 65,536 x 4,096, hands of five into 7 categories"}
+    lmax = 32
+    hist = torch.zeros(2 * lmax, dtype=torch.int64, device="cuda")
+    ms = timed(torch, stream, lambda: ph.phprng_runs_test(ctx, 0, N, per, lmax, hist, stream), 4)
+    out["runs"] = {"value": N * per / ms * 1e3, "unit": "PRNs/s", "ms_per_call": ms,
+                   "workload": "plain32 65,536 x 4,096, runs of R <= 1/2 and R > 1/2, lengths capped at 32"}
+    Nc, pc = N // 4, per * 4
+    S, B, H = 1 << 14, 1 << 20, 256
+    hist = torch.zeros(H, dtype=torch.int64, device="cuda")
+    ms = timed(torch, stream, lambda: ph.phprng_collision_test(ctx, 0, Nc, pc, S, B, H, hist, stream), 4)
+    torch.cuda.synchronize()
+    got = hist.cpu().numpy()
+    mean = float((got * np.arange(H)).sum() / max(got.sum(), 1))
+    out["collision"] = {"value": Nc * pc / ms * 1e3, "unit": "PRNs/s", "ms_per_call": ms,
+                        "workload": "plain32 first 16,384 instances x 16,384, segments of 2^14 into 2^20 bins",
+                        "mean_collisions": mean,
+                        "expected_mean": S - B * (1.0 - (1.0 - 1.0 / B) ** S)}
+    return out
 
 
 def measured_hbm_gbs():
@@ -762,6 +793,7 @@ def main():
         for name, fn in (("fused", lambda: mode_fused(ph, torch, ctx2, N, per, stream, 8)),
                          ("serial", lambda: mode_serial(ph, torch, ctx2, N, per, stream)),
                          ("interstream", lambda: mode_interstream(ph, torch, ctx2, N, per, stream)),
+                         ("consumers", lambda: mode_consumers(ph, torch, ctx2, N, per, stream)),
                          ("small_e", lambda: mode_small_e(ph, torch, stream, PEAK_TMULS)),
                          ("pattern", lambda: mode_pattern(ph, torch, stream)),
                          ("fourier", lambda: mode_fourier(ph, torch, stream)),
@@ -773,7 +805,7 @@ def main():
             if name not in wanted:
                 continue
             try:
-                if name in ("fused", "serial", "interstream"):
+                if name in ("fused", "serial", "interstream", "consumers"):
                     ctx2 = ph.phprng_create(32, inst, ph.PHPRNG_REQUIRE_SAFE_PRIME, stream)
                     try:
                         modes[name] = fn()

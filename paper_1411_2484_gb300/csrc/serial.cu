@@ -76,6 +76,39 @@ __device__ __forceinline__ uint32_t poker_category(const uint32_t *h)
     }
 }
 
+// Shared counters of one warp: with POKER, 7 categories x 32 lanes, each lane
+// counting its own hands (no atomics); otherwise the serial test's bins when
+// there are at most kLocalBins of them, counted with shared atomics.  Either
+// way they are added to the device histogram at the end of the call, and
+// every 2^23 groups before that, so no 32-bit counter can overflow (a lane
+// counts at most 2 hands of a 256-number group, a warp at most 256 tuples).
+constexpr uint32_t kLocalBins = 7 * 32;
+constexpr uint64_t kLocalFlushGroups = 1ull << 23;
+
+template <bool POKER>
+__device__ __forceinline__ void flush_local(uint32_t *cnt, uint32_t nbins, int lane,
+                                            unsigned long long *hist)
+{
+    __syncwarp();
+    if (POKER) {
+#pragma unroll
+        for (int c = 0; c < 7; ++c) {
+            uint32_t v = cnt[c * 32 + lane];
+            cnt[c * 32 + lane] = 0;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFullMask, v, off);
+            if (lane == 0 && v) atomicAdd(hist + c, (unsigned long long)v);
+        }
+    } else {
+        for (uint32_t b = lane; b < nbins; b += 32) {
+            const uint32_t v = cnt[b];
+            cnt[b] = 0;
+            if (v) atomicAdd(hist + b, (unsigned long long)v);
+        }
+    }
+    __syncwarp();
+}
+
 // POKER: hands of five cards, denominations floor(10 R), into 7 category
 // counters (D = 5, B = 10); otherwise the serial test's B^D counters.
 template <int NPT, bool POKER, int WB>
@@ -87,6 +120,7 @@ serial_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog
     constexpr uint64_t G = 32 * NPT;
     __shared__ uint32_t tb[WB][32 * NPT + 8];  // per warp: a carried tuple start, then one group
     __shared__ uint4 etb[WB][4 * (NPT / 4) * 32];   // per warp: the exponent program's odd powers
+    __shared__ uint32_t lc[WB][kLocalBins];         // per warp: shared counters (flush_local)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint64_t w = (uint64_t)blockIdx.x * WB + warp;
     if (w >= num) return;
@@ -95,6 +129,12 @@ serial_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog
     const DevInst P = inst[i];
     const ExpProg &pg = prog[i];
     const uint32_t r = (uint32_t)(((uint64_t)B << 32) / P.yN);
+    uint32_t nbins = 1;
+    for (int d = 0; d < D && nbins <= kLocalBins; ++d) nbins *= B;
+    const bool local = POKER || nbins <= kLocalBins;
+    uint32_t *cnt = lc[warp];
+    if (local)
+        for (uint32_t b = lane; b < kLocalBins; b += 32) cnt[b] = 0;
     uint32_t M = (uint32_t)st.m[i];
     uint32_t sig = mont32((uint32_t)st.s[i], sk.lane[lane], sk.p, sk.pinv);
     const uint64_t pos_after = st.pos[i] + per_inst;
@@ -118,15 +158,20 @@ serial_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog
         for (uint32_t t = lane; t < ntup; t += 32) {
             uint32_t idx = 0, scale = 1;
             if (POKER) {
-                idx = poker_category(buf + t * 5);
-            } else {
-                for (int d = 0; d < D; ++d) {
-                    idx += buf[t * D + d] * scale;
-                    scale *= B;
-                }
+                cnt[poker_category(buf + t * 5) * 32 + lane] += 1u;
+                continue;
             }
-            atomicAdd(hist + idx, 1ull);
+            for (int d = 0; d < D; ++d) {
+                idx += buf[t * D + d] * scale;
+                scale *= B;
+            }
+            if (local)
+                atomicAdd(cnt + idx, 1u);
+            else
+                atomicAdd(hist + idx, 1ull);
         }
+        if (local && (g0 / G) % kLocalFlushGroups == kLocalFlushGroups - 1)
+            flush_local<POKER>(cnt, nbins, lane, hist);
         const uint32_t rem = total - ntup * (uint32_t)D;
         const uint32_t keep = (uint32_t)lane < rem ? buf[ntup * D + lane] : 0u;
         __syncwarp();
@@ -134,6 +179,7 @@ serial_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog
         __syncwarp();
         carry = rem;
     }
+    if (local) flush_local<POKER>(cnt, nbins, lane, hist);
     write_state_after<NPT, uint32_t, uint32_t>(st, sk, i, lane, g_last, per_inst, pos_after, M, sig_last,
                                                x);
 }
@@ -149,7 +195,7 @@ serial_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog
 // still open at the group's end is carried; the one open at the call's end is
 // not counted.  Counts go to a per-warp shared histogram, flushed at the end.
 template <int NPT>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, PH_SERIAL_MINB)
 runs_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, DevState st,
             SkipConst sk, uint64_t first, uint64_t num, uint64_t per_inst, int lmax,
             unsigned long long *__restrict__ hist, const uint32_t *__restrict__ order)
@@ -158,6 +204,7 @@ runs_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, 
     constexpr int NW = (int)(G / 32);                    // words of bits per group
     __shared__ uint32_t wb[8][NW], wt[8][NW];
     __shared__ uint32_t wh[8][128];                      // 2 lmax <= 128 counters per warp
+    __shared__ uint4 etb[8][4 * (NPT / 4) * 32];         // per warp: the exponent program's odd powers
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint64_t w = (uint64_t)blockIdx.x * 8 + warp;
     if (w >= num) return;
@@ -180,7 +227,7 @@ runs_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, 
         sig_last = sig;
         g_last = g0;
         messages32<NPT>(P, sk, lane, my0, per_inst, M, sig, sv, msg);
-        encrypt32<NPT>(P, pg, msg, x);
+        encrypt32_tb<NPT>(P, pg, msg, x, etb[warp], lane);
         const uint32_t valid = per_inst - g0 < G ? (uint32_t)(per_inst - g0) : (uint32_t)G;
         uint32_t byte = 0;
 #pragma unroll
@@ -240,7 +287,7 @@ runs_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, 
 // to hist[min(C, H-1)] and clears its bitmap.  The grid is persistent (one
 // bitmap per resident warp, warps walk instances with a stride).
 template <int NPT>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, PH_SERIAL_MINB)
 collision_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, DevState st,
                  SkipConst sk, uint64_t first, uint64_t num, uint64_t per_inst, uint32_t S, uint32_t B,
                  uint32_t H, unsigned long long *__restrict__ hist, uint32_t *__restrict__ bitmaps,
@@ -248,6 +295,7 @@ collision_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ p
 {
     constexpr uint64_t G = 32 * NPT;
     const int lane = threadIdx.x & 31;
+    __shared__ uint4 etb[8][4 * (NPT / 4) * 32];         // per warp: the exponent program's odd powers
     const uint64_t gw = (uint64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     const uint64_t nwarps = (uint64_t)gridDim.x * 8;
     const uint32_t words = (B + 31) / 32;
@@ -270,7 +318,7 @@ collision_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ p
             sig_last = sig;
             g_last = g0;
             messages32<NPT>(P, sk, lane, my0, per_inst, M, sig, sv, msg);
-            encrypt32<NPT>(P, pg, msg, x);
+            encrypt32_tb<NPT>(P, pg, msg, x, etb[threadIdx.x >> 5], lane);
             if (g0 >= counted) continue;                  // the incomplete last segment
 #pragma unroll
             for (int u = 0; u < NPT; ++u) {

@@ -30,10 +30,11 @@ def oracle_hist(_unused, start_rows, per, D, B):
     return h, st
 
 
-@pytest.mark.parametrize("D,B", PAPER_SIZES + [(7, 8), (3, 2)])
+@pytest.mark.parametrize("D,B", PAPER_SIZES + [(7, 8), (3, 2), (1, 10), (2, 14), (1, 224), (1, 225)])
 def test_serial_histograms_match_oracle(ph, torch, D, B):
     """Two consecutive calls (ragged lengths, tuples spanning lanes and warp
-    groups), histograms accumulated on the device, states continued."""
+    groups), histograms accumulated on the device, states continued.  Up to
+    224 bins the kernel counts in shared memory (225: the device histogram)."""
     inst = workloads.draw_instances(37, seed=90 + D)
     ctx = ph.phprng_create(32, inst, 0)
     try:
