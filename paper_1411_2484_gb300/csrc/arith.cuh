@@ -426,7 +426,11 @@ PH_HD uint32_t funnel_r(uint32_t lo, uint32_t hi, uint32_t s)
 // funnel shifts by `extra`, and the high word of the double as
 // ((1022 + E) << 20) + Q_hi with E = 32 - lz - ybits - extra (Q carries the
 // implicit bit, which lifts the exponent field by one to 1023 + E).
-PH_HD double real32_fast(uint32_t c, uint32_t yN, uint32_t ybits, uint64_t W)
+// real32_est is the branch-free part: the double rounded from the 11-bit
+// fraction, with *amb = 1 when f lies in the band; real32_exact forms the same
+// Xf and decides by the exact remainder; real32_fast does both in one, with
+// a branch on the band.
+PH_HD double real32_est(uint32_t c, uint32_t yN, uint32_t ybits, uint64_t W, uint32_t *amb)
 {
     const uint32_t x = c + 1;
     const uint32_t lz = (uint32_t)clz32(x);
@@ -435,6 +439,40 @@ PH_HD double real32_fast(uint32_t c, uint32_t yN, uint32_t ybits, uint64_t W)
     // Xf = floor(A W / 2^(32 - extra)): H = A w1 + floor(A w0 / 2^32) (< 2^64,
     // and < 2^63 when extra = 1, as A/yN < 1 then), shifted left by extra
     // with the next bit of A w0 shifted in.
+    const uint64_t P = (uint64_t)A * (uint32_t)W;                        // A * w0
+    const uint64_t H = (uint64_t)A * (uint32_t)(W >> 32) + (P >> 32);    // A * w1 + hi
+    const uint32_t Hlo = (uint32_t)H, Hhi = (uint32_t)(H >> 32);
+    const uint32_t Xhi = funnel_l(Hlo, Hhi, extra), Xlo = funnel_l((uint32_t)P, Hlo, extra);
+    *amb = (Xlo & 0x7FFu) - 1021u < 3u ? 1u : 0u;
+    const uint64_t Xr = (((uint64_t)Xhi << 32) | Xlo) + 1024u;
+    const uint32_t Qlo = funnel_r((uint32_t)Xr, (uint32_t)(Xr >> 32), 11);
+    const uint32_t Qhi = (uint32_t)(Xr >> 43);
+    const uint32_t hi = ((1054u - ybits - lz - extra) << 20) + Qhi;
+    return bits_to_double(((uint64_t)hi << 32) | Qlo);
+}
+
+PH_HD double real32_exact(uint32_t c, uint32_t yN, uint32_t ybits, uint64_t W)
+{
+    const uint32_t x = c + 1;
+    const uint32_t lz = (uint32_t)clz32(x);
+    const uint32_t A = x << lz;
+    const uint32_t extra = A < yN ? 1u : 0u;
+    const uint64_t P = (uint64_t)A * (uint32_t)W;
+    const uint64_t H = (uint64_t)A * (uint32_t)(W >> 32) + (P >> 32);
+    const uint64_t Xf = (H << extra) | (extra ? (uint64_t)((uint32_t)P >> 31) : 0u);
+    uint64_t Q = Xf >> 11;
+    const uint64_t r = ((uint64_t)A << (52 + extra)) - Q * (uint64_t)yN;   // exact, < yN
+    Q += (r << 1) > yN ? 1u : 0u;
+    const uint32_t hi = ((1054u - ybits - lz - extra) << 20) + (uint32_t)(Q >> 32);
+    return bits_to_double(((uint64_t)hi << 32) | (uint32_t)Q);
+}
+
+PH_HD double real32_fast(uint32_t c, uint32_t yN, uint32_t ybits, uint64_t W)
+{
+    const uint32_t x = c + 1;
+    const uint32_t lz = (uint32_t)clz32(x);
+    const uint32_t A = x << lz;
+    const uint32_t extra = A < yN ? 1u : 0u;
     const uint64_t P = (uint64_t)A * (uint32_t)W;                        // A * w0
     const uint64_t H = (uint64_t)A * (uint32_t)(W >> 32) + (P >> 32);    // A * w1 + hi
     const uint32_t Hlo = (uint32_t)H, Hhi = (uint32_t)(H >> 32);

@@ -68,6 +68,9 @@ __device__ __forceinline__ double u128d(u128 v) { return u128_to_double((uint64_
 #define PH_MINB_STATS 3
 #endif
 
+#ifndef PH_RCHUNK_HEAVY
+#define PH_RCHUNK_HEAVY 2
+#endif
 #ifndef PH_MINB_LIGHT
 #define PH_MINB_LIGHT 3
 #endif
@@ -175,10 +178,11 @@ gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
                 else
                     messages32<NPT>(P, sk, lane, my0, len, M, sig, sv, msg);
                 encrypt32_tb<NPT>(P, pg, msg, x, tb, lane);
+                // R of two numbers at a time (reals_of)
                 if (full)
-                    store_group<NPT, CT, uint32_t, true>(P, cdst, rdst, my0, len, vec_ok, x);
+                    store_group<NPT, CT, uint32_t, true, PH_RCHUNK_HEAVY>(P, cdst, rdst, my0, len, vec_ok, x);
                 else
-                    store_group<NPT, CT, uint32_t>(P, cdst, rdst, my0, len, vec_ok, x);
+                    store_group<NPT, CT, uint32_t, false, PH_RCHUNK_HEAVY>(P, cdst, rdst, my0, len, vec_ok, x);
             }
         }
         if (wb) write_state_after<NPT, uint32_t, uint32_t>(st, sk, i, lane, g_last, len, pos_after, M,

@@ -298,9 +298,36 @@ __device__ __forceinline__ double real_of(const DevInst &P, uint32_t c)
 }
 __device__ __forceinline__ double real_of(const DevInst &P, uint64_t c) { return real64(c, P.n); }
 
+// R of a lane's NPT numbers: every estimate first, without branches (so the
+// NPT computations interleave), then, in a lane where some estimate lies in
+// the rounding band (one number in about 680), the exact decision for those.
+template <int NPT>
+__device__ __forceinline__ void reals_of(const DevInst &P, const uint32_t (&x)[NPT], double (&r)[NPT])
+{
+    uint32_t amb = 0;
+#pragma unroll
+    for (int u = 0; u < NPT; ++u) {
+        uint32_t a;
+        r[u] = real32_est(x[u], P.yN, P.ybits, P.aux, &a);
+        amb |= a << u;
+    }
+    if (amb) {
+#pragma unroll
+        for (int u = 0; u < NPT; ++u)
+            if ((amb >> u) & 1u) r[u] = real32_exact(x[u], P.yN, P.ybits, P.aux);
+    }
+}
+template <int NPT>
+__device__ __forceinline__ void reals_of(const DevInst &P, const uint64_t (&x)[NPT], double (&r)[NPT])
+{
+#pragma unroll
+    for (int u = 0; u < NPT; ++u) r[u] = real64(x[u], P.n);
+}
+
 // Stores a lane's NPT outputs (16-byte vectors when the whole run of the
 // lane is inside `len` and vec_ok says the addresses are aligned).
-template <int NPT, typename CT, typename XT, bool FULL = false>
+// RC: numbers whose R are formed together (reals_of; 1: one at a time).
+template <int NPT, typename CT, typename XT, bool FULL = false, int RC = 1>
 __device__ __forceinline__ void store_group(const DevInst &P, CT *c_dst, double *r_dst,
                                             uint64_t my0, uint64_t len, bool vec_ok,
                                             const XT (&x)[NPT])
@@ -325,7 +352,25 @@ __device__ __forceinline__ void store_group(const DevInst &P, CT *c_dst, double 
     }
     if (r_dst) {
         double *dst = r_dst + my0;
-        if (full && vec_ok && NPT % 2 == 0) {
+        if constexpr (sizeof(XT) == 4 && RC > 1 && NPT % RC == 0) {
+#pragma unroll
+            for (int u0 = 0; u0 < NPT; u0 += RC) {
+                XT xc[RC];
+                double r[RC];
+#pragma unroll
+                for (int u = 0; u < RC; ++u) xc[u] = x[u0 + u];
+                reals_of<RC>(P, xc, r);
+                if (full && vec_ok && RC % 2 == 0) {
+#pragma unroll
+                    for (int u = 0; u < RC; u += 2)
+                        *reinterpret_cast<double2 *>(dst + u0 + u) = make_double2(r[u], r[u + 1]);
+                } else {
+#pragma unroll
+                    for (int u = 0; u < RC; ++u)
+                        if (my0 + u0 + u < len) dst[u0 + u] = r[u];
+                }
+            }
+        } else if (full && vec_ok && NPT % 2 == 0) {
 #pragma unroll
             for (int u = 0; u < NPT; u += 2)
                 *reinterpret_cast<double2 *>(dst + u) =

@@ -28,6 +28,20 @@ void h_real32_fast_many(const uint64_t *n, const uint64_t *c, double *out, uint6
     }
 }
 
+// R by the branch-free estimate and, for inputs it flags, the exact decision
+// (the form the generator uses for two numbers at a time)
+void h_real32_split_many(const uint64_t *n, const uint64_t *c, double *out, uint64_t count)
+{
+    for (uint64_t i = 0; i < count; ++i) {
+        phprng_instance in{n[i], 3, 3, 2, 0, 1};
+        ExpProg pg;
+        DevInst d = derive_inst(in, 0, &pg);
+        uint32_t amb;
+        out[i] = real32_est((uint32_t)c[i], d.yN, d.ybits, d.aux, &amb);
+        if (amb) out[i] = real32_exact((uint32_t)c[i], d.yN, d.ybits, d.aux);
+    }
+}
+
 // fraction bits f of the fast quotient estimate, to find inputs in the band
 // where real32_fast falls back to the exact remainder
 uint32_t h_real32_fast_frac(uint64_t n, uint64_t c)

@@ -38,6 +38,7 @@ def h(tmp_path_factory):
     lib.h_addmod.restype = u64
     lib.h_addmod.argtypes = [u64, u64, u64, ctypes.c_int]
     lib.h_real32_fast_many.argtypes = [P64, P64, ctypes.POINTER(ctypes.c_double), u64]
+    lib.h_real32_split_many.argtypes = [P64, P64, ctypes.POINTER(ctypes.c_double), u64]
     lib.h_real32_fast_frac.restype = ctypes.c_uint32
     lib.h_real32_fast_frac.argtypes = [u64, u64]
     return lib
@@ -207,8 +208,11 @@ def test_hist_bin_integer_equals_floor(h):
     assert bad.size == 0, (n[bad[0]], c[bad[0]], out[bad[0]], ref[bad[0]])
 
 
-def test_real32_fast_equals_ieee_division(h):
-    """The fast rounding decision, and its exact fallback band (forced)."""
+@pytest.mark.parametrize("form", ["h_real32_fast_many", "h_real32_split_many"])
+def test_real32_fast_equals_ieee_division(h, form):
+    """The fast rounding decision, and its exact fallback band (forced); in
+    one function, and as the branch-free estimate plus the exact decision for
+    the inputs it flags."""
     rng = np.random.default_rng(11)
     k = 600000
     n = np.concatenate([rng.integers(3, 1 << 32, k // 2, dtype=np.uint64) | np.uint64(1),
@@ -229,7 +233,7 @@ def test_real32_fast_equals_ieee_division(h):
     n = np.concatenate([n, np.array(band_n, dtype=np.uint64)])
     c = np.concatenate([c, np.array(band_c, dtype=np.uint64)])
     out = np.empty(n.size, dtype=np.float64)
-    h.h_real32_fast_many(_p(n), _p(c), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n.size)
+    getattr(h, form)(_p(n), _p(c), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n.size)
     ref = (c + np.uint64(1)).astype(np.float64) / (n + np.uint64(1)).astype(np.float64)
     assert np.array_equal(out.view(np.uint64), ref.view(np.uint64))
     for nn in (3, 5, 7, 23, 31, 127, 255, 257, 4093, 8191, 2147483647):   # every c, small n
@@ -240,6 +244,6 @@ def test_real32_fast_equals_ieee_division(h):
             cs = np.arange(nn, dtype=np.uint64)
         ns = np.full(cs.size, nn, dtype=np.uint64)
         o = np.empty(cs.size, dtype=np.float64)
-        h.h_real32_fast_many(_p(ns), _p(cs), o.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+        getattr(h, form)(_p(ns), _p(cs), o.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                              cs.size)
         assert all(o[i] == float(Fraction(int(cs[i]) + 1, nn + 1)) for i in range(cs.size))
