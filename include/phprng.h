@@ -233,12 +233,13 @@ int phprng_poker_test(phprng_ctx *ctx, uint64_t first, uint64_t num_inst, uint64
  * phprng_serial_test) already holds an earlier number of
  * the segment is a collision, and the segment's collision count C adds one to
  * hist[min(C, H-1)].  Expected count per segment S - B (1 - (1 - 1/B)^S)
- * (about 127.9 at the paper's S = 2^14, B = 2^20).  hist: device memory, H
+ * (about 127.3 at the paper's S = 2^14, B = 2^20).  hist: device memory, H
  * uint64 counters, added to.  Limits: S a multiple of 256 from 256 to 2^24;
- * B a power of two up to 2^20 or any B up to 2^16; 1 <= H <= 2^16.  Takes a
- * stream-ordered scratch of one B-bit bitmap per resident warp (311 MB at
- * B = 2^20 on GB300) for the call.  Streams advance by per_inst.
- * Asynchronous on cuda_stream. */
+ * B a power of two up to 2^20 or any B up to 2^16; 1 <= H <= 2^16.  The
+ * bins of the complete segments are written to a stream-ordered scratch of
+ * 4 bytes per number, at most 2^28 numbers (1 GiB) at a time (larger calls
+ * run in pieces), and each segment is counted in a B-bit bitmap in shared
+ * memory.  Streams advance by per_inst.  Asynchronous on cuda_stream. */
 int phprng_collision_test(phprng_ctx *ctx, uint64_t first, uint64_t num_inst, uint64_t per_inst,
                           uint32_t S, uint32_t B, uint32_t H, uint64_t *hist, void *cuda_stream);
 

@@ -914,19 +914,21 @@ PH_API int phprng_collision_test(phprng_ctx *ctx, uint64_t first, uint64_t num_i
                     "phprng_collision_test: B must be a power of two up to 2^20 or at most 2^16");
     if (H < 1 || H > (1u << 16)) return fail(ctx, PHPRNG_EINVAL, "phprng_collision_test: H must be 1..2^16");
     auto launch = [&](const GenArgs &g, cudaStream_t s, std::string *err) -> int {
-        const int warps = collision_grid_warps();
-        const size_t bytes = (size_t)warps * ((B + 31) / 32) * sizeof(uint32_t);
-        uint32_t *bm = nullptr;
-        cudaError_t e = cudaMallocAsync((void **)&bm, bytes, s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(bm, 0, bytes, s);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            if (bm) cudaFreeAsync(bm, s);
-            *err = std::string("collision bitmaps: ") + cudaGetErrorString(e);
-            return e == cudaErrorMemoryAllocation ? PHPRNG_ENOMEM : PHPRNG_ECUDA;
+        // scratch for the bins of at most kCollBinsCap numbers at a time
+        const uint64_t counted = per_inst / S * S;
+        const uint64_t want = counted > kCollBinsCap / num_inst ? kCollBinsCap : counted * num_inst;
+        const uint64_t cap = std::max<uint64_t>(S, std::min<uint64_t>(kCollBinsCap, want));
+        uint32_t *bins = nullptr;
+        if (counted) {
+            cudaError_t e = cudaMallocAsync((void **)&bins, cap * sizeof(uint32_t), s);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                *err = std::string("collision bins: ") + cudaGetErrorString(e);
+                return e == cudaErrorMemoryAllocation ? PHPRNG_ENOMEM : PHPRNG_ECUDA;
+            }
         }
-        int rc = launch_collision(g, S, B, H, (unsigned long long *)hist, bm, warps, s, err);
-        cudaFreeAsync(bm, s);
+        int rc = launch_collision(g, S, B, H, (unsigned long long *)hist, bins, cap, s, err);
+        if (bins) cudaFreeAsync(bins, s);
         return rc;
     };
     return run_hist_test(ctx, "phprng_collision_test", first, num_inst, per_inst, 1, 1, hist, cuda_stream,

@@ -220,11 +220,12 @@ int launch_interstream(const void *k, uint64_t Np, uint64_t L, const void *c, in
                        int D, uint32_t B, uint32_t *binsT, unsigned long long *hist, void *stream,
                        std::string *err);
 // Collision-test consumer (serial.cu): segments of S numbers into B bins,
-// collision counts into hist[H]; a persistent grid of `warps` warps (from
-// collision_grid_warps()), each with a zeroed bitmap of ceil(B/32) words.
-int collision_grid_warps();
+// collision counts into hist[H]; `bins` is scratch for `cap` 32-bit bins
+// (cap >= S): the streams' bins are written there in pieces of at most cap
+// numbers and counted per segment before the next piece.
+static constexpr uint64_t kCollBinsCap = 1ull << 28;
 int launch_collision(const GenArgs &a, uint32_t S, uint32_t B, uint32_t H, unsigned long long *hist,
-                     uint32_t *bitmaps, int warps, void *stream, std::string *err);
+                     uint32_t *bins, uint64_t cap, void *stream, std::string *err);
 // Full-period pattern by enumeration (pattern.cu): mtab[q] = (c_lo+q)^d mod n
 // for q < L0, sk for NPT 8; hist has nb^(D-1) uint64 counters.
 int launch_pattern(const DevInst &P, const ExpProg &pg, const SkipConst &sk, const uint32_t *mtab,

@@ -10,6 +10,7 @@
 // launch's streams.  B^D is at most 2^24, so the histogram (<= 128 MiB of
 // 64-bit counters, 8 MiB at the paper's 2^20 bins) stays in or near L2 and
 // the additions are L2 reductions.
+#include <algorithm>
 #include <cuda_runtime.h>
 
 #include "gencore.cuh"
@@ -19,6 +20,10 @@ namespace phprng {
 #ifndef PH_SERIAL_MINB
 #define PH_SERIAL_MINB 3
 #endif
+#ifndef PH_SERIAL_WARPS
+#define PH_SERIAL_WARPS 8
+#endif
+static constexpr int kSerialWarps = PH_SERIAL_WARPS;   // warps per block of serial_kernel (3 blocks per SM, exponent tables in shared memory)
 
 // The bin of a number, floor(B R) taken on the double R = RN((c+1)/(n+1))
 // (Eq. 9d) with one IEEE product, RN(R B), then truncation -- what a program
@@ -279,87 +284,147 @@ runs_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, 
 }
 
 // Collision test (Tests section): each stream's numbers of the call in
-// consecutive segments of S (a multiple of the 256-number warp group, so every
-// group lies in one segment); every number sets its bin floor(B R) in the
-// warp's own bitmap of B bits with an atomic OR, and is a collision when the
-// bit was already set.  The count of a segment is S minus its distinct bins,
-// whatever the order of the ORs.  At the end of a segment the warp adds one
-// to hist[min(C, H-1)] and clears its bitmap.  The grid is persistent (one
-// bitmap per resident warp, warps walk instances with a stride).
+// consecutive segments of S (a multiple of the 256-number warp group); the
+// count of a segment is the number of its numbers whose bin floor(B R) an
+// earlier number of the segment already took, i.e. S minus its distinct bins,
+// whatever the order in which they are seen.  Two kernels:
+//   coll_bins_kernel: Eq. 9 for `len` numbers of the streams of launch slots
+//     [w0, wend), each number's bin written as a 32-bit word in stream order,
+//     bins[(w - w0) len + k] (or nothing when store is 0: the numbers past the
+//     last complete segment, generated only to advance the streams);
+//   coll_count_kernel: one block per segment at a time (persistent), its B
+//     bits in shared memory: cleared, every bin set with a shared atomic OR
+//     that counts the bits already set, then hist[min(C, H-1)] += 1.
+// A B-bit bitmap per segment in shared memory (128 KiB at B = 2^20) replaces
+// one bitmap per resident warp in global memory, whose working set (one per
+// warp of the GPU) exceeds L2 and makes every OR a DRAM read-modify-write.
 template <int NPT>
-__global__ void __launch_bounds__(256, PH_SERIAL_MINB)
-collision_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, DevState st,
-                 SkipConst sk, uint64_t first, uint64_t num, uint64_t per_inst, uint32_t S, uint32_t B,
-                 uint32_t H, unsigned long long *__restrict__ hist, uint32_t *__restrict__ bitmaps,
-                 const uint32_t *__restrict__ order)
+__global__ void __launch_bounds__(kSerialWarps * 32, PH_SERIAL_MINB)
+coll_bins_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, DevState st,
+                 SkipConst sk, uint64_t first, uint64_t w0, uint64_t wend, uint64_t len, int store,
+                 uint32_t B, uint32_t *__restrict__ bins, const uint32_t *__restrict__ order)
 {
+    constexpr int WB = kSerialWarps;
     constexpr uint64_t G = 32 * NPT;
-    const int lane = threadIdx.x & 31;
-    __shared__ uint4 etb[8][4 * (NPT / 4) * 32];         // per warp: the exponent program's odd powers
-    const uint64_t gw = (uint64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-    const uint64_t nwarps = (uint64_t)gridDim.x * 8;
+    __shared__ uint4 etb[WB][4 * (NPT / 4) * 32];   // per warp: the exponent program's odd powers
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t w = w0 + (uint64_t)blockIdx.x * WB + warp;
+    if (w >= wend) return;
+    const uint64_t j = order ? order[w] : w;
+    const uint64_t i = first + j;
+    const DevInst P = inst[i];
+    const ExpProg &pg = prog[i];
+    const uint32_t r = (uint32_t)(((uint64_t)B << 32) / P.yN);
+    uint32_t M = (uint32_t)st.m[i];
+    uint32_t sig = mont32((uint32_t)st.s[i], sk.lane[lane], sk.p, sk.pinv);
+    const uint64_t pos_after = st.pos[i] + len;
+    uint32_t *row = bins + (w - w0) * len;
+    uint32_t x[NPT], sig_last = sig;
+    uint64_t g_last = 0;
+    for (uint64_t g0 = 0; g0 < len; g0 += G) {
+        uint32_t sv[NPT], msg[NPT];
+        const uint64_t my0 = g0 + (uint64_t)NPT * lane;
+        sig_last = sig;
+        g_last = g0;
+        const bool full = g0 + G <= len;                 // warp-uniform
+        if (full)
+            messages32<NPT, true>(P, sk, lane, my0, len, M, sig, sv, msg);
+        else
+            messages32<NPT>(P, sk, lane, my0, len, M, sig, sv, msg);
+        encrypt32_tb<NPT>(P, pg, msg, x, etb[warp], lane);
+        if (!store) continue;                            // (len is then the call's tail)
+        uint32_t b[NPT];
+#pragma unroll
+        for (int u = 0; u < NPT; ++u) b[u] = serial_bin(x[u], P.yN, P.ybits, r, B);
+        // stored lengths are whole segments, so every group is full
+#pragma unroll
+        for (int u = 0; u < NPT; u += 4)
+            *reinterpret_cast<uint4 *>(row + my0 + u) = make_uint4(b[u], b[u + 1], b[u + 2], b[u + 3]);
+    }
+    write_state_after<NPT, uint32_t, uint32_t>(st, sk, i, lane, g_last, len, pos_after, M, sig_last, x);
+}
+
+static constexpr int kCollCountThreads = 1024;
+
+__global__ void __launch_bounds__(kCollCountThreads)
+coll_count_kernel(const uint32_t *__restrict__ bins, uint64_t nseg, uint32_t S, uint32_t B, uint32_t H,
+                  unsigned long long *__restrict__ hist)
+{
+    extern __shared__ uint32_t bm[];                     // ceil(B/32) words
+    __shared__ uint32_t part[kCollCountThreads / 32];
     const uint32_t words = (B + 31) / 32;
-    uint32_t *bm = bitmaps + gw * words;
-    const uint64_t counted = per_inst / S * S;            // numbers in complete segments
-    for (uint64_t w = gw; w < num; w += nwarps) {
-        const uint64_t j = order ? order[w] : w;
-        const uint64_t i = first + j;
-        const DevInst P = inst[i];
-        const ExpProg &pg = prog[i];
-        const uint32_t r = (uint32_t)(((uint64_t)B << 32) / P.yN);
-        uint32_t M = (uint32_t)st.m[i];
-        uint32_t sig = mont32((uint32_t)st.s[i], sk.lane[lane], sk.p, sk.pinv);
-        const uint64_t pos_after = st.pos[i] + per_inst;
-        uint32_t x[NPT], sig_last = sig, C = 0;
-        uint64_t g_last = 0;
-        for (uint64_t g0 = 0; g0 < per_inst; g0 += G) {
-            uint32_t sv[NPT], msg[NPT];
-            const uint64_t my0 = g0 + (uint64_t)NPT * lane;
-            sig_last = sig;
-            g_last = g0;
-            messages32<NPT>(P, sk, lane, my0, per_inst, M, sig, sv, msg);
-            encrypt32_tb<NPT>(P, pg, msg, x, etb[threadIdx.x >> 5], lane);
-            if (g0 >= counted) continue;                  // the incomplete last segment
-#pragma unroll
-            for (int u = 0; u < NPT; ++u) {
-                const uint32_t b = serial_bin(x[u], P.yN, P.ybits, r, B);
-                const uint32_t bit = 1u << (b & 31);
-                if (atomicOr(bm + (b >> 5), bit) & bit) ++C;
-            }
-            if ((g0 + G) % S == 0) {                      // the segment is complete
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) C += __shfl_xor_sync(kFullMask, C, off);
-                if (lane == 0) atomicAdd(hist + (C < H ? C : H - 1), 1ull);
-                C = 0;
-                __syncwarp();
-                for (uint32_t k = lane; k < words; k += 32) bm[k] = 0u;
-                __syncwarp();
-            }
+    const int t = threadIdx.x;
+    for (uint64_t g = blockIdx.x; g < nseg; g += gridDim.x) {
+        for (uint32_t k = t; k < words; k += kCollCountThreads) bm[k] = 0u;
+        __syncthreads();
+        const uint32_t *seg = bins + g * S;
+        uint32_t C = 0;
+        for (uint32_t k = t; k < S; k += kCollCountThreads) {
+            const uint32_t b = seg[k];
+            const uint32_t bit = 1u << (b & 31);
+            C += (atomicOr(bm + (b >> 5), bit) & bit) ? 1u : 0u;
         }
-        write_state_after<NPT, uint32_t, uint32_t>(st, sk, i, lane, g_last, per_inst, pos_after, M,
-                                                   sig_last, x);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) C += __shfl_xor_sync(kFullMask, C, off);
+        if ((t & 31) == 0) part[t >> 5] = C;
+        __syncthreads();
+        if (t < 32) {
+            C = part[t];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) C += __shfl_xor_sync(kFullMask, C, off);
+            if (t == 0) atomicAdd(hist + (C < H ? C : H - 1), 1ull);
+        }
+        __syncthreads();                                 // bm and part are reused
     }
 }
 
-int collision_grid_warps()
-{
-    int dev = 0, sms = 0, b = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, collision_kernel<8>, 256, 0);
-    return (sms > 0 ? sms : 1) * (b > 0 ? b : 1) * 8;
-}
-
 int launch_collision(const GenArgs &a, uint32_t S, uint32_t B, uint32_t H, unsigned long long *hist,
-                     uint32_t *bitmaps, int warps, void *stream, std::string *err)
+                     uint32_t *bins, uint64_t cap, void *stream, std::string *err)
 {
     if (a.num == 0 || a.per_inst == 0) return PHPRNG_OK;
-    collision_kernel<8><<<(unsigned)(warps / 8), 256, 0, (cudaStream_t)stream>>>(
-        a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, S, B, H, hist, bitmaps, a.order);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) {
-        *err = std::string("collision_kernel launch: ") + cudaGetErrorString(e);
-        return PHPRNG_ECUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint64_t counted = a.per_inst / S * S;        // numbers in complete segments
+    const size_t smem = (size_t)((B + 31) / 32) * sizeof(uint32_t);
+    static int attr_dev = -1;
+    int dev = 0, sms = 1, per_sm = 0;
+    cudaGetDevice(&dev);
+    if (smem > 48 * 1024 && attr_dev != dev) {
+        cudaFuncSetAttribute(coll_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024);
+        attr_dev = dev;
+    }
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coll_count_kernel, kCollCountThreads, smem);
+    const uint64_t count_blocks = (uint64_t)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+    // slots per chunk and numbers per piece so that one piece of one chunk
+    // fits the `cap` bins of scratch (at least one segment per slot)
+    const uint64_t cw = counted == 0 ? a.num : std::min<uint64_t>(a.num, std::max<uint64_t>(1, cap / S));
+    const uint64_t Lp = counted == 0 ? 0 : std::min<uint64_t>(counted, std::max<uint64_t>(S, cap / cw / S * S));
+    auto check = [&](const char *what) {
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) *err = std::string(what) + " launch: " + cudaGetErrorString(e);
+        return e == cudaSuccess ? PHPRNG_OK : PHPRNG_ECUDA;
+    };
+    for (uint64_t w0 = 0; w0 < a.num; w0 += cw) {
+        const uint64_t wend = std::min(a.num, w0 + cw);
+        const unsigned blocks = (unsigned)((wend - w0 + kSerialWarps - 1) / kSerialWarps);
+        for (uint64_t p0 = 0; p0 < counted; p0 += Lp) {
+            const uint64_t L = std::min(Lp, counted - p0);
+            coll_bins_kernel<8><<<blocks, kSerialWarps * 32, 0, s>>>(a.inst, a.prog, a.st, a.sk, a.first, w0, wend,
+                                                                    L, 1, B, bins, a.order);
+            int rc = check("coll_bins_kernel");
+            if (rc != PHPRNG_OK) return rc;
+            const uint64_t nseg = (wend - w0) * (L / S);
+            coll_count_kernel<<<(unsigned)std::min(nseg, count_blocks), kCollCountThreads, smem, s>>>(
+                bins, nseg, S, B, H, hist);
+            rc = check("coll_count_kernel");
+            if (rc != PHPRNG_OK) return rc;
+        }
+        if (a.per_inst > counted) {
+            coll_bins_kernel<8><<<blocks, kSerialWarps * 32, 0, s>>>(a.inst, a.prog, a.st, a.sk, a.first, w0, wend,
+                                                                    a.per_inst - counted, 0, B, bins, a.order);
+            const int rc = check("coll_bins_kernel");
+            if (rc != PHPRNG_OK) return rc;
+        }
     }
     return PHPRNG_OK;
 }
@@ -378,10 +443,6 @@ int launch_runs(const GenArgs &a, int lmax, unsigned long long *hist, void *stre
     return PHPRNG_OK;
 }
 
-#ifndef PH_SERIAL_WARPS
-#define PH_SERIAL_WARPS 8
-#endif
-static constexpr int kSerialWarps = PH_SERIAL_WARPS;   // warps per block of serial_kernel (3 blocks per SM, exponent tables in shared memory)
 
 // Interstream serial test, step 1: bins floor(B R) of a chunk of c (Np
 // streams x L numbers, instance-major; uint64 elements when c64, as a

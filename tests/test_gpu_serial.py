@@ -226,6 +226,37 @@ def test_collision_mean_at_scale(ph, torch):
         ph.phprng_destroy(ctx)
 
 
+def test_collision_pieces_equal_separate_calls(ph, torch):
+    """Calls larger than the kernel's 2^28-bin scratch run in pieces: along the
+    streams (512 streams x 2^20 numbers, pieces of 2^19) and across them
+    (20,000 streams x 2^14 + 300 numbers, slots in chunks of 16,384).  Each
+    must give the histogram and the states of the same numbers taken in calls
+    small enough for one piece (which the oracle tests check)."""
+    S, B, H = 1 << 14, 1 << 20, 512
+    for count, per, splits in ((512, 1 << 20, "len"), (20000, (1 << 14) + 300, "slots")):
+        inst = workloads.draw_instances(count, seed=126 if splits == "len" else 127)
+        one = ph.phprng_create(32, inst, 0)
+        two = ph.phprng_create(32, inst, 0)
+        try:
+            h1 = torch.zeros(H, dtype=torch.int64, device="cuda")
+            h2 = torch.zeros(H, dtype=torch.int64, device="cuda")
+            ph.phprng_collision_test(one, 0, count, per, S, B, H, h1)
+            if splits == "len":
+                for _ in range(4):
+                    ph.phprng_collision_test(two, 0, count, per // 4, S, B, H, h2)
+            else:
+                ph.phprng_collision_test(two, 0, 10000, per, S, B, H, h2)
+                ph.phprng_collision_test(two, 10000, 10000, per, S, B, H, h2)
+            torch.cuda.synchronize()
+            assert int(h1.sum()) == count * (per // S)
+            assert torch.equal(h1, h2)
+            for i in (0, count // 2, count - 1):
+                assert ph.phprng_get_state(one, i) == ph.phprng_get_state(two, i)
+        finally:
+            ph.phprng_destroy(one)
+            ph.phprng_destroy(two)
+
+
 def _interstream_oracle(rows, per, D, B):
     c, _, st, _ = oracle.generate_many(rows, per, threads=THREADS, want_r=False)
     return oracle.interstream_serial_hist(c, rows[:, 0], D, B), st
