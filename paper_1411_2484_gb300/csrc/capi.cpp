@@ -273,31 +273,54 @@ static int pointer_kind(const void *p)
     return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) ? 1 : 0;
 }
 
-// Split launches (SplitArgs): a call with fewer instances than about eight
-// times the warps the GPU keeps resident cuts each instance into K chunks
-// (K a power of two, at most kMaxSplit, chunks of at least kMinChunk numbers)
-// so the grid still fills the GPU; the chunk starts cost one extra skip product
-// per number (the pre-pass) and a short sum per warp.
+// Split launches (SplitArgs): a call with fewer instances than eight times
+// the warps the GPU keeps resident may cut each instance into K chunks of Lc
+// numbers (Lc a multiple of 256, at least kMinChunk; K at most kMaxSplit) so
+// the grid fills the GPU.  K is chosen to minimise the estimated time
+// waves * (Lc + kChunkCost): waves = ceil(num K / resident warps), kChunkCost
+// the per-chunk start (its skip power, its start message and its share of the
+// pre-pass) in numbers; K = 1 when no split beats the unsplit launch.  The
+// chunk starts cost one extra skip product per number (the pre-pass) and a
+// short sum per warp.
 static constexpr uint32_t kMaxSplit = 4096;
 #ifndef PH_MIN_CHUNK
 #define PH_MIN_CHUNK 1024
 #endif
 static constexpr uint64_t kMinChunk = PH_MIN_CHUNK;
+static constexpr uint64_t kChunkCost = 128;
+
+// The chunk count of a split launch (1: none) for num instances of per_inst
+// numbers with `resident` warps resident on the GPU; *Lc the chunk length.
+static uint32_t split_chunks(uint64_t num, uint64_t per_inst, uint64_t resident, uint64_t *Lc)
+{
+    *Lc = per_inst;
+    if (num == 0 || resident == 0 || num >= 8 * resident || per_inst < 2 * kMinChunk) return 1;
+    uint64_t best_cost = (num + resident - 1) / resident * (per_inst + kChunkCost);
+    uint32_t best = 1;
+    for (uint32_t K = 2; K <= kMaxSplit; ++K) {
+        const uint64_t L = ((per_inst + K - 1) / K + 255) / 256 * 256;
+        if (L < kMinChunk) break;
+        const uint64_t Ku = (per_inst + L - 1) / L;     // chunks in use (none empty)
+        if (Ku != K) continue;                         // the same split as a smaller K
+        const uint64_t cost = (num * Ku + resident - 1) / resident * (L + kChunkCost);
+        if (cost < best_cost) {
+            best_cost = cost;
+            best = K;
+            *Lc = L;
+        }
+    }
+    return best;
+}
 
 static int prepare_split(phprng_ctx *c, uint64_t num, uint64_t per_inst, GenArgs *g, cudaStream_t s)
 {
     if (c->wide_skip) return PHPRNG_OK;               // wide skips: never split
-    const uint64_t target = 8 * gen_resident_warps();
-    uint32_t K = 1, lg = 0;
-    while (K < kMaxSplit && num * K < target && per_inst >= 2ull * K * kMinChunk) {
-        K *= 2;
-        ++lg;
-    }
+    uint64_t Lc = 0;
+    const uint32_t K = split_chunks(num, per_inst, gen_resident_warps(), &Lc);
     if (K == 1) return PHPRNG_OK;
     SplitArgs &sp = g->sp;
     sp.K = K;
-    sp.log2K = lg;
-    sp.Lc = ((per_inst + K - 1) / K + 255) / 256 * 256;
+    sp.Lc = Lc;
     const uint64_t pm = c->sk32_8.p;                 // the skip products' modulus (3 for the unit skip)
     const uint64_t R = (1ull << 32) % pm;
     sp.oneM = (uint32_t)R;

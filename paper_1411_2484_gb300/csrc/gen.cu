@@ -94,10 +94,11 @@ gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint64_t w = (uint64_t)blockIdx.x * W + warp;
     // statistics launches are never split (sp.K = 1)
-    const bool active = w < (num << sp.log2K);
+    const bool active = w < num * sp.K;
     if (!STATS && !active) return;
-    const uint64_t q = w >> sp.log2K;                  // instance slot
-    const uint32_t cidx = (uint32_t)(w & (sp.K - 1));   // chunk of it
+    uint64_t q;                                        // instance slot
+    uint32_t cidx;                                     // chunk of it
+    split_slot(sp, w, &q, &cidx);
     // the instance this warp runs, relative to `first` (statistics: always w)
     const uint64_t j = !active ? 0 : (!STATS && order) ? order[q] : q;
     const uint64_t i = first + j;
@@ -321,9 +322,10 @@ gen64_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
     constexpr uint64_t G = 32 * NPT;
     const int lane = threadIdx.x & 31;
     const uint64_t w = (uint64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-    if (w >= (num << sp.log2K)) return;
-    const uint64_t q = w >> sp.log2K;
-    const uint32_t cidx = (uint32_t)(w & (sp.K - 1));
+    if (w >= num * sp.K) return;
+    uint64_t q;
+    uint32_t cidx;
+    split_slot(sp, w, &q, &cidx);
     const uint64_t j = order ? order[q] : q;          // instance first + j
     const uint64_t i = first + j;
     const DevInst P = inst[i];
@@ -390,9 +392,10 @@ chunk_sums_kernel(const DevInst *__restrict__ inst, DevState st, SkipConst sk, u
     constexpr uint64_t G = 32 * NPT;
     const int lane = threadIdx.x & 31;
     const uint64_t w = (uint64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-    if (w >= (num << sp.log2K)) return;
-    const uint64_t q = w >> sp.log2K;
-    const uint32_t cidx = (uint32_t)(w & (sp.K - 1));
+    if (w >= num * sp.K) return;
+    uint64_t q;
+    uint32_t cidx;
+    split_slot(sp, w, &q, &cidx);
     const uint64_t i = first + (order ? order[q] : q);
     uint64_t *h = scratch + q * (sp.K + 1);
     const uint32_t s = (uint32_t)st.s[i];
@@ -438,9 +441,9 @@ int launch_gen32(const GenArgs &a, void *stream, std::string *err)
         *err = "gen32_kernel: statistics launches are never split";
         return PHPRNG_EINVAL;
     }
-    const uint64_t blocks = ((a.num << a.sp.log2K) + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    const uint64_t blocks_heavy = ((a.num << a.sp.log2K) + kWarpsHeavy - 1) / kWarpsHeavy;
-    const uint64_t blocks_light = ((a.num << a.sp.log2K) + kWarpsLight - 1) / kWarpsLight;
+    const uint64_t blocks = ((a.num * a.sp.K) + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    const uint64_t blocks_heavy = ((a.num * a.sp.K) + kWarpsHeavy - 1) / kWarpsHeavy;
+    const uint64_t blocks_light = ((a.num * a.sp.K) + kWarpsLight - 1) / kWarpsLight;
     cudaStream_t s = (cudaStream_t)stream;
     if (a.stats) {
         const size_t smem = (2 * kWarpsPerBlock * 32 * kNPT + kWarpsPerBlock * 256) * sizeof(uint32_t) +
@@ -497,7 +500,7 @@ uint64_t gen32_edge_words(uint64_t num, uint64_t per_inst)
 int launch_gen64(const GenArgs &a, void *stream, std::string *err)
 {
     if (a.num == 0 || a.per_inst == 0) return PHPRNG_OK;
-    const uint64_t blocks = ((a.num << a.sp.log2K) + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    const uint64_t blocks = ((a.num * a.sp.K) + kWarpsPerBlock - 1) / kWarpsPerBlock;
     if (a.wide_skip) {
         if (a.sp.K != 1) {
             *err = "gen64_kernel: launches with a wide skip prime are never split";
@@ -517,7 +520,7 @@ int launch_gen64(const GenArgs &a, void *stream, std::string *err)
 int launch_chunk_sums(const GenArgs &a, const SkipConst &sk8, void *stream, std::string *err)
 {
     if (a.num == 0 || a.per_inst == 0 || a.sp.K < 2) return PHPRNG_OK;
-    const uint64_t blocks = ((a.num << a.sp.log2K) + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    const uint64_t blocks = ((a.num * a.sp.K) + kWarpsPerBlock - 1) / kWarpsPerBlock;
     chunk_sums_kernel<<<(unsigned)blocks, kWarpsPerBlock * 32, 0, (cudaStream_t)stream>>>(
         a.inst, a.st, sk8, a.first, a.num, a.per_inst, a.order, a.sp, (uint64_t *)a.sp.scratch);
     return check_launch(err, "chunk_sums_kernel launch");

@@ -53,6 +53,20 @@ __device__ __forceinline__ uint32_t skip_chunk(const SkipConst &sk, const SplitA
     return mont32(s, r, sk.p, sk.pinv);
 }
 
+// Launch slot w of a split launch: instance slot q = w / K, chunk c = w mod K
+// (w < 2^32 whenever K > 1).
+__device__ __forceinline__ void split_slot(const SplitArgs &sp, uint64_t w, uint64_t *q, uint32_t *c)
+{
+    if (sp.K == 1) {
+        *q = w;
+        *c = 0;
+    } else {
+        const uint32_t qq = (uint32_t)w / sp.K;
+        *q = qq;
+        *c = (uint32_t)w - qq * sp.K;
+    }
+}
+
 // Start message of chunk c of slot q: the slot's start message plus the skip
 // sums of chunks 0 .. c-1, mod n (every lane gets it).
 __device__ __forceinline__ uint64_t chunk_message(const SplitArgs &sp, uint64_t q, uint32_t c,

@@ -43,8 +43,8 @@ static constexpr int kSerialWarps = PH_SERIAL_WARPS;   // warps per block of ser
 // products of the comparison: lo(B vN) - lo((est+1) yN), plus yN when est was
 // not raised.  A zero remainder -- an exact k/B, about 1 number in 2^31 at
 // random -- sends the number to the double arithmetic.
-__device__ __forceinline__ uint32_t serial_bin(uint32_t c, uint32_t yN, uint32_t ybits, uint32_t r,
-                                               uint32_t B)
+__device__ __forceinline__ uint32_t serial_bin_int(uint32_t c, uint32_t yN, uint32_t ybits, uint32_t r,
+                                                   uint32_t B, uint32_t *exact_multiple)
 {
     const uint32_t vN = (c + 1) << (32 - ybits);
     uint32_t est = umulhi32(vN, r);
@@ -52,11 +52,46 @@ __device__ __forceinline__ uint32_t serial_bin(uint32_t c, uint32_t yN, uint32_t
     const bool up = P1 <= P2;
     est += up ? 1u : 0u;
     const uint32_t d = (uint32_t)P2 - (uint32_t)P1;
-    if (d == (up ? 0u : 0u - yN)) {
-        const double R = __ddiv_rn((double)(c + 1), (double)(yN >> (32 - ybits)));
-        est = (uint32_t)__dmul_rn(R, (double)B);
-    }
+    *exact_multiple = d == (up ? 0u : 0u - yN) ? 1u : 0u;
     return est;
+}
+
+__device__ __forceinline__ uint32_t serial_bin_double(uint32_t c, uint32_t yN, uint32_t ybits, uint32_t B)
+{
+    const double R = __ddiv_rn((double)(c + 1), (double)(yN >> (32 - ybits)));
+    return (uint32_t)__dmul_rn(R, (double)B);
+}
+
+__device__ __forceinline__ uint32_t serial_bin(uint32_t c, uint32_t yN, uint32_t ybits, uint32_t r,
+                                               uint32_t B)
+{
+    uint32_t em;
+    const uint32_t est = serial_bin_int(c, yN, ybits, r, B, &em);
+    return em ? serial_bin_double(c, yN, ybits, B) : est;
+}
+
+// The bins of a lane's NPT numbers: the integer path for all of them without
+// branches, then the double arithmetic for the exact multiples, in the rare
+// lanes that have one.
+template <int NPT, int C = (NPT % 4 == 0 ? 4 : NPT)>
+__device__ __forceinline__ void serial_bins(const uint32_t (&x)[NPT], uint32_t yN, uint32_t ybits, uint32_t r,
+                                            uint32_t B, uint32_t (&b)[NPT])
+{
+#pragma unroll
+    for (int u0 = 0; u0 < NPT; u0 += C) {                // C numbers at a time (register pressure)
+        uint32_t em = 0;
+#pragma unroll
+        for (int u = u0; u < u0 + C; ++u) {
+            uint32_t e;
+            b[u] = serial_bin_int(x[u], yN, ybits, r, B, &e);
+            em |= e << u;
+        }
+        if (em) {
+#pragma unroll
+            for (int u = u0; u < u0 + C; ++u)
+                if ((em >> u) & 1u) b[u] = serial_bin_double(x[u], yN, ybits, B);
+        }
+    }
 }
 
 // Poker category of five denominations: the sum over the cards of how many
@@ -154,9 +189,13 @@ serial_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog
         g_last = g0;
         messages32<NPT>(P, sk, lane, my0, per_inst, M, sig, sv, msg);
         encrypt32_tb<NPT>(P, pg, msg, x, etb[warp], lane);
+        {
+            uint32_t b[NPT];
+            serial_bins<NPT>(x, P.yN, P.ybits, r, B, b);
 #pragma unroll
-        for (int u = 0; u < NPT; ++u)
-            if (my0 + u < per_inst) buf[carry + NPT * lane + u] = serial_bin(x[u], P.yN, P.ybits, r, B);
+            for (int u = 0; u < NPT; ++u)
+                if (my0 + u < per_inst) buf[carry + NPT * lane + u] = b[u];
+        }
         __syncwarp();
         const uint32_t valid = per_inst - g0 < G ? (uint32_t)(per_inst - g0) : (uint32_t)G;
         const uint32_t total = carry + valid, ntup = total / (uint32_t)D;
@@ -334,8 +373,7 @@ coll_bins_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ p
         encrypt32_tb<NPT>(P, pg, msg, x, etb[warp], lane);
         if (!store) continue;                            // (len is then the call's tail)
         uint32_t b[NPT];
-#pragma unroll
-        for (int u = 0; u < NPT; ++u) b[u] = serial_bin(x[u], P.yN, P.ybits, r, B);
+        serial_bins<NPT>(x, P.yN, P.ybits, r, B, b);
         // stored lengths are whole segments, so every group is full
 #pragma unroll
         for (int u = 0; u < NPT; u += 4)
@@ -561,8 +599,7 @@ inter_gen_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ p
             messages32<NPT>(P, sk, lane, my0, len, M, sig, sv, msg);
         encrypt32_tb<NPT>(P, pg, msg, x, etb[warp], lane);
         uint32_t b[NPT];
-#pragma unroll
-        for (int u = 0; u < NPT; ++u) b[u] = serial_bin(x[u], P.yN, P.ybits, r, B);
+        serial_bins<NPT>(x, P.yN, P.ybits, r, B, b);
         if (full && NPT == 8) {
             *reinterpret_cast<uint4 *>(row + my0) =
                 make_uint4(b[0] | b[1] << 16, b[2] | b[3] << 16, b[4] | b[5] << 16, b[6] | b[7] << 16);
