@@ -320,6 +320,7 @@ static int prepare_split(phprng_ctx *c, uint64_t num, uint64_t per_inst, GenArgs
     if (K == 1) return PHPRNG_OK;
     SplitArgs &sp = g->sp;
     sp.K = K;
+    sp.Kinv = (uint64_t)((((unsigned __int128)1 << 64) + K - 1) / K);
     sp.Lc = Lc;
     const uint64_t pm = c->sk32_8.p;                 // the skip products' modulus (3 for the unit skip)
     const uint64_t R = (1ull << 32) % pm;

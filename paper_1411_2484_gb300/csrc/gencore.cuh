@@ -57,14 +57,11 @@ __device__ __forceinline__ uint32_t skip_chunk(const SkipConst &sk, const SplitA
 // (w < 2^32 whenever K > 1).
 __device__ __forceinline__ void split_slot(const SplitArgs &sp, uint64_t w, uint64_t *q, uint32_t *c)
 {
-    if (sp.K == 1) {
-        *q = w;
-        *c = 0;
-    } else {
-        const uint32_t qq = (uint32_t)w / sp.K;
-        *q = qq;
-        *c = (uint32_t)w - qq * sp.K;
-    }
+    // w / K as the high word of w * ceil(2^64 / K): exact for w < 2^32
+    // (the excess w (Kinv - 2^64/K) / 2^64 stays below 2^-32 < 1/K)
+    const uint64_t qq = sp.K == 1 ? w : __umul64hi(w, sp.Kinv);
+    *q = qq;
+    *c = (uint32_t)(w - qq * sp.K);
 }
 
 // Start message of chunk c of slot q: the slot's start message plus the skip

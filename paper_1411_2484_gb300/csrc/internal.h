@@ -78,6 +78,7 @@ struct DevState {
 // s a^(c Lc) (Eq. 6 over chunks).  K = 1 is the plain launch.
 struct SplitArgs {
     uint32_t K = 1;                    // chunks per instance (num K < 2^32 when K > 1)
+    uint64_t Kinv = 0;                 // ceil(2^64 / K) when K > 1
     uint64_t Lc = 0;                   // a multiple of 256
     uint32_t aLcM = 0;                 // a^Lc * 2^32 mod p
     uint32_t oneM = 0;                 // 2^32 mod p

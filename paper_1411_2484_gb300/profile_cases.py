@@ -4,12 +4,17 @@
 
 CASE is one of
   plain32   65,536 instances x 4,096 numbers, R to HBM (2 GiB)     gen32_kernel
+  c0        4 safe 32-bit instances x 2^20 numbers, c and R stored
+            (a split launch: chunk_sums_kernel, then gen32_kernel)
   fused32   the same instances, statistics only                      gen32_kernel (STATS)
   small_e   65,536 instances with e = 9 x 4,096 numbers, R (2 GiB)   gen32_kernel
   serial2   plain32's instances, pairs into 2^20 bins (serial test)  serial_kernel
   pattern3  the paper's pattern instance (n = 4294967087, p = 2^31-1,
             e = 9), D = 3, 2^24 volumes, L0 = 4 (2^33 points)       pattern_kernel
   wide64    4,096 64-bit instances x 4,096 numbers, R (128 MiB)      gen64_kernel
+  collision plain32's first 16,384 instances x 16,384 numbers, segments
+            of 2^14 into 2^20 bins (the paper's collision test)      coll_bins_kernel,
+                                                                      coll_count_kernel
   inter2    plain32's instances, interleaved order (number 1 of every
             stream, then number 2 ...), pairs into 2^20 bins          inter_*_kernel
   fourier20 plain32's first 256 instances x 2^20 numbers, Fourier test
@@ -35,7 +40,7 @@ from paper_1411_2484_gb300 import workloads
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["plain32", "fused32", "small_e", "serial2", "pattern3", "wide64", "batched",
+    ap.add_argument("case", choices=["plain32", "c0", "collision", "fused32", "small_e", "serial2", "pattern3", "wide64", "batched",
                                      "batched20k", "fourier20", "inter2"])
     ap.add_argument("--repeat", type=int, default=3)
     ap.add_argument("--max-len", type=int, default=1 << 20)
@@ -63,6 +68,22 @@ def main():
         else:
             sb = torch.empty(N * ph.STATS_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
             run = lambda: ph.phprng_generate(ctx, 0, N, per, None, None, sb, s)
+        numbers = N * per
+    elif args.case == "collision":
+        inst = workloads.workload_instances("plain32_65536x4096x64", 16384)
+        N, per = 16384, 16384
+        ctx = ph.phprng_create(32, inst, ph.PHPRNG_REQUIRE_SAFE_PRIME, s)
+        hist = torch.zeros(256, dtype=torch.int64, device="cuda")
+        run = lambda: ph.phprng_collision_test(ctx, 0, N, per, 1 << 14, 1 << 20, 256, hist, s)
+        numbers = N * per
+    elif args.case == "c0":
+        name = "pr1_ref_32bit_4x2^20"
+        inst = workloads.workload_instances(name)
+        N, per = workloads.WORKLOADS[name]["instances"], workloads.WORKLOADS[name]["per_inst"]
+        ctx = ph.phprng_create(32, inst, ph.PHPRNG_REQUIRE_SAFE_PRIME, s)
+        c = torch.empty(N * per, dtype=torch.int32, device="cuda")
+        r = torch.empty(N * per, dtype=torch.float64, device="cuda")
+        run = lambda: ph.phprng_generate(ctx, 0, N, per, c, r, None, s)
         numbers = N * per
     elif args.case == "inter2":
         inst = workloads.workload_instances("plain32_65536x4096x64")
