@@ -277,7 +277,8 @@ static int pointer_kind(const void *p)
 // the warps the GPU keeps resident may cut each instance into K chunks of Lc
 // numbers (Lc a multiple of 256, at least kMinChunk; K at most kMaxSplit) so
 // the grid fills the GPU.  K is chosen to minimise the estimated time
-// waves * (Lc + kChunkCost): waves = ceil(num K / resident warps), kChunkCost
+// waves * (Lc + kChunkCost) over 1 to 64 waves: waves = ceil(num K / resident
+// warps), kChunkCost
 // the per-chunk start (its skip power, its start message and its share of the
 // pre-pass) in numbers; K = 1 when no split beats the unsplit launch.  The
 // chunk starts cost one extra skip product per number (the pre-pass) and a
@@ -297,15 +298,19 @@ static uint32_t split_chunks(uint64_t num, uint64_t per_inst, uint64_t resident,
     if (num == 0 || resident == 0 || num >= 8 * resident || per_inst < 2 * kMinChunk) return 1;
     uint64_t best_cost = (num + resident - 1) / resident * (per_inst + kChunkCost);
     uint32_t best = 1;
-    for (uint32_t K = 2; K <= kMaxSplit; ++K) {
-        const uint64_t L = ((per_inst + K - 1) / K + 255) / 256 * 256;
-        if (L < kMinChunk) break;
-        const uint64_t Ku = (per_inst + L - 1) / L;     // chunks in use (none empty)
-        if (Ku != K) continue;                         // the same split as a smaller K
-        const uint64_t cost = (num * Ku + resident - 1) / resident * (L + kChunkCost);
+    // for each wave count w the cheapest split is the shortest chunk that keeps
+    // num * K within w waves
+    for (uint64_t w = 1; w <= 64; ++w) {
+        const uint64_t Kmax = std::min<uint64_t>(w * resident / num, kMaxSplit);
+        if (Kmax < 2) continue;
+        const uint64_t L = std::max<uint64_t>(((per_inst + Kmax - 1) / Kmax + 255) / 256 * 256,
+                                              (kMinChunk + 255) / 256 * 256);
+        const uint64_t K = (per_inst + L - 1) / L;      // chunks in use (none empty)
+        if (K < 2 || K > kMaxSplit) continue;
+        const uint64_t cost = (num * K + resident - 1) / resident * (L + kChunkCost);
         if (cost < best_cost) {
             best_cost = cost;
-            best = K;
+            best = (uint32_t)K;
             *Lc = L;
         }
     }

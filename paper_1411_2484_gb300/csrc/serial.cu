@@ -397,10 +397,20 @@ coll_count_kernel(const uint32_t *__restrict__ bins, uint64_t nseg, uint32_t S, 
         __syncthreads();
         const uint32_t *seg = bins + g * S;
         uint32_t C = 0;
-        for (uint32_t k = t; k < S; k += kCollCountThreads) {
-            const uint32_t b = seg[k];
-            const uint32_t bit = 1u << (b & 31);
-            C += (atomicOr(bm + (b >> 5), bit) & bit) ? 1u : 0u;
+        // eight loads in flight per thread before their ORs
+        for (uint32_t k0 = t; k0 < S; k0 += 8 * kCollCountThreads) {
+            uint32_t b[8];
+#pragma unroll
+            for (int v = 0; v < 8; ++v) {
+                const uint32_t k = k0 + v * kCollCountThreads;
+                b[v] = k < S ? __ldcs(seg + k) : 0xFFFFFFFFu;
+            }
+#pragma unroll
+            for (int v = 0; v < 8; ++v) {
+                if (b[v] == 0xFFFFFFFFu) continue;
+                const uint32_t bit = 1u << (b[v] & 31);
+                C += (atomicOr(bm + (b[v] >> 5), bit) & bit) ? 1u : 0u;
+            }
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) C += __shfl_xor_sync(kFullMask, C, off);
