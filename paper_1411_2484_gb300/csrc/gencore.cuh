@@ -335,9 +335,9 @@ __device__ __forceinline__ void reals_of(const DevInst &P, const uint64_t (&x)[N
     for (int u = 0; u < NPT; ++u) r[u] = real64(x[u], P.n);
 }
 
-// Two doubles as one 16-byte store of their four 32-bit words (a double2
-// store built from the doubles measured 0.75 against 0.54 ms for 2 GiB of R
-// in this layout).
+// Two doubles as one 16-byte store of their four 32-bit words (in the
+// generators one instruction per number fewer than a double2 built from the
+// doubles).
 __device__ __forceinline__ void store_r2(double *dst, double a, double b)
 {
     const unsigned long long ba = (unsigned long long)__double_as_longlong(a);
