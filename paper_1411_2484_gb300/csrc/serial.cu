@@ -200,19 +200,19 @@ serial_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog
         const uint32_t valid = per_inst - g0 < G ? (uint32_t)(per_inst - g0) : (uint32_t)G;
         const uint32_t total = carry + valid, ntup = total / (uint32_t)D;
         for (uint32_t t = lane; t < ntup; t += 32) {
-            uint32_t idx = 0, scale = 1;
-            if (POKER) {
+            if constexpr (POKER) {
                 cnt[poker_category(buf + t * 5) * 32 + lane] += 1u;
-                continue;
+            } else {
+                uint32_t idx = 0, scale = 1;
+                for (int d = 0; d < D; ++d) {
+                    idx += buf[t * D + d] * scale;
+                    scale *= B;
+                }
+                if (local)
+                    atomicAdd(cnt + idx, 1u);
+                else
+                    atomicAdd(hist + idx, 1ull);
             }
-            for (int d = 0; d < D; ++d) {
-                idx += buf[t * D + d] * scale;
-                scale *= B;
-            }
-            if (local)
-                atomicAdd(cnt + idx, 1u);
-            else
-                atomicAdd(hist + idx, 1ull);
         }
         if (local && (g0 / G) % kLocalFlushGroups == kLocalFlushGroups - 1)
             flush_local<POKER>(cnt, nbins, lane, hist);
@@ -433,13 +433,10 @@ int launch_collision(const GenArgs &a, uint32_t S, uint32_t B, uint32_t H, unsig
     cudaStream_t s = (cudaStream_t)stream;
     const uint64_t counted = a.per_inst / S * S;        // numbers in complete segments
     const size_t smem = (size_t)((B + 31) / 32) * sizeof(uint32_t);
-    static int attr_dev = -1;
     int dev = 0, sms = 1, per_sm = 0;
     cudaGetDevice(&dev);
-    if (smem > 48 * 1024 && attr_dev != dev) {
+    if (smem > 48 * 1024)                              // above the default 48 KiB (current device)
         cudaFuncSetAttribute(coll_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024);
-        attr_dev = dev;
-    }
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coll_count_kernel, kCollCountThreads, smem);
     const uint64_t count_blocks = (uint64_t)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
