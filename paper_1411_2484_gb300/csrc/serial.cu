@@ -384,6 +384,20 @@ coll_bins_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ p
 
 static constexpr int kCollCountThreads = 1024;
 
+// Each thread takes its bins eight at a time; the loads of the next eight
+// (of this segment or of the block's next one) are issued before the ORs of
+// the current eight, so the reads of one segment overlap the counting, the
+// reduction and the bitmap clearing of the previous one.
+__device__ __forceinline__ void coll_load8(const uint32_t *__restrict__ bins, uint64_t nseg, uint32_t S,
+                                           uint64_t g, uint32_t j, int t, uint32_t (&b)[8])
+{
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        const uint32_t k = j * 8 * kCollCountThreads + v * kCollCountThreads + t;
+        b[v] = g < nseg && k < S ? __ldcs(bins + g * S + k) : 0xFFFFFFFFu;   // bins are below 2^20
+    }
+}
+
 __global__ void __launch_bounds__(kCollCountThreads)
 coll_count_kernel(const uint32_t *__restrict__ bins, uint64_t nseg, uint32_t S, uint32_t B, uint32_t H,
                   unsigned long long *__restrict__ hist)
@@ -391,26 +405,28 @@ coll_count_kernel(const uint32_t *__restrict__ bins, uint64_t nseg, uint32_t S, 
     extern __shared__ uint32_t bm[];                     // ceil(B/32) words
     __shared__ uint32_t part[kCollCountThreads / 32];
     const uint32_t words = (B + 31) / 32;
+    const uint32_t nb = (S + 8 * kCollCountThreads - 1) / (8 * kCollCountThreads);   // batches per segment
     const int t = threadIdx.x;
+    uint32_t cur[8];
+    coll_load8(bins, nseg, S, blockIdx.x, 0, t, cur);
     for (uint64_t g = blockIdx.x; g < nseg; g += gridDim.x) {
         for (uint32_t k = t; k < words; k += kCollCountThreads) bm[k] = 0u;
         __syncthreads();
-        const uint32_t *seg = bins + g * S;
         uint32_t C = 0;
-        // eight loads in flight per thread before their ORs
-        for (uint32_t k0 = t; k0 < S; k0 += 8 * kCollCountThreads) {
-            uint32_t b[8];
+        for (uint32_t j = 0; j < nb; ++j) {
+            uint32_t nxt[8];
+            if (j + 1 < nb)
+                coll_load8(bins, nseg, S, g, j + 1, t, nxt);
+            else
+                coll_load8(bins, nseg, S, g + gridDim.x, 0, t, nxt);
 #pragma unroll
             for (int v = 0; v < 8; ++v) {
-                const uint32_t k = k0 + v * kCollCountThreads;
-                b[v] = k < S ? __ldcs(seg + k) : 0xFFFFFFFFu;
+                if (cur[v] == 0xFFFFFFFFu) continue;
+                const uint32_t bit = 1u << (cur[v] & 31);
+                C += (atomicOr(bm + (cur[v] >> 5), bit) & bit) ? 1u : 0u;
             }
 #pragma unroll
-            for (int v = 0; v < 8; ++v) {
-                if (b[v] == 0xFFFFFFFFu) continue;
-                const uint32_t bit = 1u << (b[v] & 31);
-                C += (atomicOr(bm + (b[v] >> 5), bit) & bit) ? 1u : 0u;
-            }
+            for (int v = 0; v < 8; ++v) cur[v] = nxt[v];
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) C += __shfl_xor_sync(kFullMask, C, off);
