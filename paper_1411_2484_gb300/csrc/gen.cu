@@ -94,11 +94,11 @@ gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint64_t w = (uint64_t)blockIdx.x * W + warp;
     // statistics launches are never split (sp.K = 1)
-    const bool active = w < num * sp.K;
+    const bool active = STATS ? w < num : w < num * sp.K;
     if (!STATS && !active) return;
-    uint64_t q;                                        // instance slot
-    uint32_t cidx;                                     // chunk of it
-    split_slot(sp, w, &q, &cidx);
+    uint64_t q = w;                                    // instance slot
+    uint32_t cidx = 0;                                 // chunk of it
+    if (!STATS) split_slot(sp, w, &q, &cidx);
     // the instance this warp runs, relative to `first` (statistics: always w)
     const uint64_t j = !active ? 0 : (!STATS && order) ? order[q] : q;
     const uint64_t i = first + j;

@@ -335,9 +335,10 @@ __device__ __forceinline__ void reals_of(const DevInst &P, const uint64_t (&x)[N
     for (int u = 0; u < NPT; ++u) r[u] = real64(x[u], P.n);
 }
 
-// Two doubles as one 16-byte store of their four 32-bit words (in the
-// generators one instruction per number fewer than a double2 built from the
-// doubles).
+// Two doubles as one 16-byte store of their four 32-bit words: with R formed
+// one number at a time (the LIGHT loop, e = 9: 0.969 -> 0.963 ms) this takes
+// one instruction per number fewer than a double2 built from the doubles; the
+// pairs formed by reals_of are stored as a double2 (3.812 against 3.805 ms).
 __device__ __forceinline__ void store_r2(double *dst, double a, double b)
 {
     const unsigned long long ba = (unsigned long long)__double_as_longlong(a);
@@ -384,7 +385,8 @@ __device__ __forceinline__ void store_group(const DevInst &P, CT *c_dst, double 
                 reals_of<RC>(P, xc, r);
                 if (full && vec_ok && RC % 2 == 0) {
 #pragma unroll
-                    for (int u = 0; u < RC; u += 2) store_r2(dst + u0 + u, r[u], r[u + 1]);
+                    for (int u = 0; u < RC; u += 2)
+                        *reinterpret_cast<double2 *>(dst + u0 + u) = make_double2(r[u], r[u + 1]);
                 } else {
 #pragma unroll
                     for (int u = 0; u < RC; ++u)
