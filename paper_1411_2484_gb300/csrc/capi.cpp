@@ -988,6 +988,44 @@ PH_API int phprng_interstream_serial_test(phprng_ctx *ctx, uint64_t first, uint6
     CU(ctx, cudaSetDevice(ctx->device));
     if (pointer_kind(hist) != 1) return fail(ctx, PHPRNG_EINVAL, std::string(W) + "hist must be device memory");
     cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (ctx->width == 32 && B <= (1u << 16) && D == 2 && num_inst % 2 == 0) {
+        // Pairs: the two streams of each pair as adjacent warps, their pairs
+        // counted as they are generated; pair slots heaviest first (the
+        // heavier of the two exponent programs)
+        const uint64_t np = num_inst / 2;
+        uint32_t *pord = nullptr;
+        if (np >= kOrderMinInstances / 2 && np < (1ull << 32)) {
+            std::vector<uint32_t> ord(np), cnt(513, 0);
+            auto pkey = [&](uint64_t q) {
+                return std::min(ctx->key[first + 2 * q], ctx->key[first + 2 * q + 1]);
+            };
+            for (uint64_t q = 0; q < np; ++q) ++cnt[pkey(q) + 1];
+            for (int k = 1; k <= 512; ++k) cnt[k] += cnt[k - 1];
+            for (uint64_t q = 0; q < np; ++q) ord[cnt[pkey(q)]++] = (uint32_t)q;
+            cudaError_t e = cudaMallocAsync((void **)&pord, np * sizeof(uint32_t), s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(pord, ord.data(), np * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                if (pord) cudaFreeAsync(pord, s);
+                return fail(ctx, PHPRNG_ENOMEM, std::string(W) + "pair order upload failed");
+            }
+        }
+        GenArgs g;
+        g.inst = ctx->d_inst;
+        g.prog = ctx->d_prog;
+        g.st = ctx->st;
+        g.sk = ctx->sk32_8;
+        g.first = first;
+        g.num = num_inst;
+        g.per_inst = per_inst;
+        std::string err;
+        const int rc = launch_inter_pairs(g, B, (unsigned long long *)hist, pord, s, &err);
+        if (pord) cudaFreeAsync(pord, s);
+        if (rc != PHPRNG_OK) return fail(ctx, rc, std::string(W) + err);
+        for (uint64_t i = first; i < first + num_inst; ++i) ctx->pos_host[i] += per_inst;
+        return PHPRNG_OK;
+    }
     if (ctx->width == 32 && B <= (1u << 16) && 32 % D == 0 && num_inst % (uint64_t)D == 0) {
         // Direct form: every tuple of the interleaved sequence holds D streams'
         // numbers of one index, so the bins are written in stream order by the

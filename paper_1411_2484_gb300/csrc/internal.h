@@ -217,6 +217,11 @@ int launch_inter_consts(const DevInst *inst, uint64_t first, uint64_t Np, uint32
 // D-tuples counted into hist from those rows.
 int launch_inter_direct(const GenArgs &a, uint64_t Lrow, int D, uint32_t B, uint16_t *binsI,
                         unsigned long long *hist, void *stream, std::string *err);
+// Interstream serial test for pairs (D = 2, an even number of 32-bit streams,
+// B <= 2^16), fused: adjacent warps generate the two streams of a pair and
+// count its pairs at once (pair_order: pair slots heaviest first, or NULL).
+int launch_inter_pairs(const GenArgs &a, uint32_t B, unsigned long long *hist, const uint32_t *pair_order,
+                       void *stream, std::string *err);
 int launch_interstream(const void *k, uint64_t Np, uint64_t L, const void *c, int c64,
                        int D, uint32_t B, uint32_t *binsT, unsigned long long *hist, void *stream,
                        std::string *err);

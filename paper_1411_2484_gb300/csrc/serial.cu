@@ -635,6 +635,103 @@ inter_gen_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ p
     write_state_after<NPT, uint32_t, uint32_t>(st, sk, i, lane, g_last, len, pos_after, M, sig_last, x);
 }
 
+// Interstream serial test for pairs (D = 2), fused: the interleaved sequence's
+// pairs are (number j of stream 2q, number j of stream 2q+1), so the two
+// streams of a pair run as adjacent warps of one block and meet once per warp
+// group: the odd stream's warp leaves its group's bins in shared memory
+// (double-buffered), the two warps pass a named barrier of their own (64
+// threads; the four pairs of a block never wait on one another), and the even
+// stream's warp counts the group's pairs.  No bins go to HBM and no second
+// kernel runs.  A pair waits at most for its slower stream; pairs run heaviest
+// first (pair_order).  Both warps of a pair run the same number of groups and
+// leave together, so every barrier is reached by both.
+template <int NPT>
+__global__ void __launch_bounds__(kSerialWarps * 32, PH_SERIAL_MINB)
+inter_pairs_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, DevState st,
+                   SkipConst sk, uint64_t first, uint64_t num, uint64_t len, uint32_t B,
+                   unsigned long long *__restrict__ hist, const uint32_t *__restrict__ pair_order)
+{
+    constexpr int WB = kSerialWarps;
+    static_assert(WB % 2 == 0 && NPT == 8, "pairs of warps, 8 bins per lane as one 16-byte row");
+    constexpr uint64_t G = 32 * NPT;
+    __shared__ uint4 etb[WB][4 * (NPT / 4) * 32];      // per warp: the exponent program's odd powers
+    __shared__ uint4 pb[WB / 2][2][32];                 // per pair: the odd stream's bins, two buffers
+    __shared__ uint32_t lc[WB][kLocalBins];            // per warp: shared counters when B^2 <= kLocalBins
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t ps = (uint64_t)blockIdx.x * (WB / 2) + (warp >> 1);   // pair slot
+    if (2 * ps >= num) return;                         // num is even: both warps of the pair leave
+    const uint64_t pq = pair_order ? pair_order[ps] : ps;
+    const bool odd = warp & 1;
+    const uint64_t j = 2 * pq + (odd ? 1 : 0);
+    const uint64_t i = first + j;
+    const DevInst P = inst[i];
+    const ExpProg &pg = prog[i];
+    const uint32_t r = (uint32_t)(((uint64_t)B << 32) / P.yN);
+    const uint32_t nbins = B * B;                      // B <= 2^16
+    const bool local = nbins <= kLocalBins;
+    uint32_t *cnt = lc[warp];
+    if (local)
+        for (uint32_t b = lane; b < kLocalBins; b += 32) cnt[b] = 0;
+    uint32_t M = (uint32_t)st.m[i];
+    uint32_t sig = mont32((uint32_t)st.s[i], sk.lane[lane], sk.p, sk.pinv);
+    const uint64_t pos_after = st.pos[i] + len;
+    const uint32_t bar = 1 + (uint32_t)(warp >> 1);    // the pair's named barrier (0 is __syncthreads)
+    uint32_t x[NPT], sig_last = sig;
+    uint64_t g_last = 0;
+    int buf = 0;
+    for (uint64_t g0 = 0; g0 < len; g0 += G) {
+        uint32_t sv[NPT], msg[NPT];
+        const uint64_t my0 = g0 + (uint64_t)NPT * lane;
+        sig_last = sig;
+        g_last = g0;
+        const bool full = g0 + G <= len;               // pair-uniform
+        if (full)
+            messages32<NPT, true>(P, sk, lane, my0, len, M, sig, sv, msg);
+        else
+            messages32<NPT>(P, sk, lane, my0, len, M, sig, sv, msg);
+        encrypt32_tb<NPT>(P, pg, msg, x, etb[warp], lane);
+        uint32_t b[NPT];
+        serial_bins<NPT>(x, P.yN, P.ybits, r, B, b);
+        uint4 *row = &pb[warp >> 1][buf][lane];
+        if (odd) *row = make_uint4(b[0] | b[1] << 16, b[2] | b[3] << 16, b[4] | b[5] << 16, b[6] | b[7] << 16);
+        asm volatile("bar.sync %0, 64;" ::"r"(bar) : "memory");
+        if (!odd) {
+            const uint4 q = *row;
+            const uint32_t o[NPT] = {q.x & 0xFFFFu, q.x >> 16, q.y & 0xFFFFu, q.y >> 16,
+                                     q.z & 0xFFFFu, q.z >> 16, q.w & 0xFFFFu, q.w >> 16};
+#pragma unroll
+            for (int u = 0; u < NPT; ++u) {
+                if (!full && my0 + u >= len) continue;
+                const uint32_t idx = b[u] + o[u] * B;         // the tuple's first element least significant
+                if (local)
+                    atomicAdd(cnt + idx, 1u);
+                else
+                    atomicAdd(hist + idx, 1ull);
+            }
+            if (local && (g0 / G) % kLocalFlushGroups == kLocalFlushGroups - 1)
+                flush_local<false>(cnt, nbins, lane, hist);
+        }
+        buf ^= 1;
+    }
+    if (local && !odd) flush_local<false>(cnt, nbins, lane, hist);
+    write_state_after<NPT, uint32_t, uint32_t>(st, sk, i, lane, g_last, len, pos_after, M, sig_last, x);
+}
+
+int launch_inter_pairs(const GenArgs &a, uint32_t B, unsigned long long *hist, const uint32_t *pair_order,
+                       void *stream, std::string *err)
+{
+    if (a.num == 0 || a.per_inst == 0) return PHPRNG_OK;
+    const uint64_t blocks = (a.num / 2 + kSerialWarps / 2 - 1) / (kSerialWarps / 2);
+    inter_pairs_kernel<8><<<(unsigned)blocks, kSerialWarps * 32, 0, (cudaStream_t)stream>>>(
+        a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, B, hist, pair_order);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        *err = std::string("inter_pairs_kernel launch: ") + cudaGetErrorString(e);
+        return PHPRNG_ECUDA;
+    }
+    return PHPRNG_OK;
+}
+
 static constexpr uint32_t kCountTileJ = 64;
 
 template <bool SMEM>

@@ -268,7 +268,11 @@ def _interstream_oracle(rows, per, D, B):
                                           # the direct form (D | 32, D | Np, B <= 2^16): ragged
                                           # groups, several chunks, D = 1, 2, 4
                                           (64, 5003, 2, 32, None), (96, 2049, 4, 8, None),
-                                          (128, 3001, 1, 1 << 16, None), (512, 70_001, 2, 1 << 10, None)])
+                                          (128, 3001, 1, 1 << 16, None), (512, 70_001, 2, 1 << 10, None),
+                                          # pairs (D = 2, Np even), fused: shared counters (B^2 <=
+                                          # 224) with pair slots heaviest first, and e = 9
+                                          (2048, 300, 2, 14, None), (64, 3001, 2, 4, None),
+                                          (8, 5000, 2, 16, 9)])
 def test_interstream_matches_oracle(ph, torch, Np, per, D, B, e):
     """Interleaved order over Np streams: ragged tails (Np per mod D != 0),
     shared-memory and global counters, and 4 x 9,000,001 numbers at D = 3 in
