@@ -461,27 +461,31 @@ def test_serial_bins_at_exact_multiples_match_oracle(ph, torch, D):
 
 
 def test_interstream_bins_at_exact_multiples_match_oracle(ph, torch):
-    """The interleaved order over the same streams, pairs into 100 x 100 bins."""
-    rows = _exact_multiple_instances()
+    """The interleaved order over the same streams from their seeds (so the
+    forced ciphertexts come up in every case), single numbers and pairs into
+    100 x 100 bins: all 11 streams (an odd count: the general form for pairs)
+    and the first 10 (the fused pairs kernel)."""
+    rows0 = _exact_multiple_instances()
     per = 600
-    ctx = _ctx_from_rows(ph, rows)
-    try:
-        for D in (1, 2):
+    for D, Np in ((1, len(rows0)), (2, len(rows0)), (2, len(rows0) - 1)):
+        rows = rows0[:Np]
+        ctx = _ctx_from_rows(ph, rows)
+        try:
             hist = torch.zeros(100 ** D, dtype=torch.int64, device="cuda")
-            ph.phprng_interstream_serial_test(ctx, 0, len(rows), per, D, 100, hist)
+            ph.phprng_interstream_serial_test(ctx, 0, Np, per, D, 100, hist)
             c, _, st, _ = oracle.generate_many(rows, per, threads=THREADS, want_r=False)
             want = oracle.interstream_serial_hist(c, rows[:, 0], D, 100)
             torch.cuda.synchronize()
             assert np.array_equal(hist.cpu().numpy().view(np.uint64), want)
-            rows = rows.copy()
-            rows[:, 4:6] = st
             if D == 1:
                 exact = np.zeros(100, dtype=np.uint64)
                 for k in range(len(rows)):
                     np.add.at(exact, np.array(_exact_bins(c[k], int(rows[k, 0]), 100), dtype=np.int64), 1)
                 assert not np.array_equal(exact, want)
-    finally:
-        ph.phprng_destroy(ctx)
+            s = ph.phprng_get_state(ctx, Np - 1)
+            assert (s["m"], s["s"], s["pos"]) == (int(st[-1, 0]), int(st[-1, 1]), per)
+        finally:
+            ph.phprng_destroy(ctx)
 
 
 def test_collision_bins_at_exact_multiples_match_oracle(ph, torch):
