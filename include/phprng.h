@@ -266,14 +266,12 @@ int phprng_runs_test(phprng_ctx *ctx, uint64_t first, uint64_t num_inst, uint64_
  * phprng_serial_test: 1 <= D <= 8, B a power of two up
  * to 2^20 or at most 2^16, B^D <= 2^24, 32-bit instances.  hist: device
  * memory, B^D uint64 counters, added to.  Streams advance by per_inst.
- * Asynchronous on cuda_stream.  Pairs (D = 2) of an even num_inst with
- * B <= 2^16 in a 32-bit context take no scratch: each pair of streams runs
- * as two warps that count their pairs as they generate them (only an order
- * of the pairs, num_inst / 2 words, when there are many).  Otherwise a
- * scratch of about 2^25 numbers (ciphertexts and bins, or only 16-bit bins
- * when D divides 32 and num_inst, B <= 2^16 and the context is 32-bit: then
- * every tuple lies within one index of D consecutive streams and is counted
- * from the bins in stream order) from the stream-ordered allocator. */
+ * Asynchronous on cuda_stream.  In a 32-bit context D = 1 is the frequency
+ * test's kernel, and D = 2, 4 or 8 dividing num_inst with B <= 2^16 takes no
+ * scratch: the D streams of each tuple group run as D warps that count their
+ * tuples as they generate them (only an order of the groups, num_inst / D
+ * words, when there are many).  Otherwise a scratch of about 2^25 numbers
+ * (ciphertexts and bins) from the stream-ordered allocator. */
 int phprng_interstream_serial_test(phprng_ctx *ctx, uint64_t first, uint64_t num_inst, uint64_t per_inst,
                                    int D, uint32_t B, uint64_t *hist, void *cuda_stream);
 

@@ -988,27 +988,51 @@ PH_API int phprng_interstream_serial_test(phprng_ctx *ctx, uint64_t first, uint6
     CU(ctx, cudaSetDevice(ctx->device));
     if (pointer_kind(hist) != 1) return fail(ctx, PHPRNG_EINVAL, std::string(W) + "hist must be device memory");
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    if (ctx->width == 32 && B <= (1u << 16) && D == 2 && num_inst % 2 == 0) {
-        // Pairs: the two streams of each pair as adjacent warps, their pairs
-        // counted as they are generated; pair slots heaviest first (the
-        // heavier of the two exponent programs)
-        const uint64_t np = num_inst / 2;
-        uint32_t *pord = nullptr;
-        if (np >= kOrderMinInstances / 2 && np < (1ull << 32)) {
-            std::vector<uint32_t> ord(np), cnt(513, 0);
-            auto pkey = [&](uint64_t q) {
-                return std::min(ctx->key[first + 2 * q], ctx->key[first + 2 * q + 1]);
+    const bool groups = D == 2 || D == 4 || D == 8;
+    if (ctx->width == 32 && D == 1) {
+        // single numbers: the interleaved order does not change their
+        // histogram, which is the frequency test's (serial kernel, D = 1)
+        GenArgs g;
+        g.inst = ctx->d_inst;
+        g.prog = ctx->d_prog;
+        g.st = ctx->st;
+        g.sk = ctx->sk32_8;
+        g.first = first;
+        g.num = num_inst;
+        g.per_inst = per_inst;
+        int rc = PHPRNG_OK;
+        if (num_inst >= kOrderMinInstances && num_inst < (1ull << 32))
+            g.order = instance_order(ctx, first, num_inst, s, &rc);
+        if (rc != PHPRNG_OK) return rc;
+        std::string err;
+        rc = launch_serial(g, 1, B, (unsigned long long *)hist, s, &err);
+        if (rc != PHPRNG_OK) return fail(ctx, rc, std::string(W) + err);
+        for (uint64_t i = first; i < first + num_inst; ++i) ctx->pos_host[i] += per_inst;
+        return PHPRNG_OK;
+    }
+    if (ctx->width == 32 && B <= (1u << 16) && groups && num_inst % (uint64_t)D == 0) {
+        // Groups of D streams as adjacent warps, their tuples counted as they
+        // are generated; group slots heaviest first (the heaviest of the D
+        // exponent programs)
+        const uint64_t ng = num_inst / (uint64_t)D;
+        uint32_t *gord = nullptr;
+        if (ng >= kOrderMinInstances / (uint64_t)D && ng < (1ull << 32)) {
+            std::vector<uint32_t> ord(ng), cnt(513, 0);
+            auto gkey = [&](uint64_t q) {
+                uint16_t k = ctx->key[first + (uint64_t)D * q];
+                for (int d = 1; d < D; ++d) k = std::min(k, ctx->key[first + (uint64_t)D * q + d]);
+                return k;
             };
-            for (uint64_t q = 0; q < np; ++q) ++cnt[pkey(q) + 1];
+            for (uint64_t q = 0; q < ng; ++q) ++cnt[gkey(q) + 1];
             for (int k = 1; k <= 512; ++k) cnt[k] += cnt[k - 1];
-            for (uint64_t q = 0; q < np; ++q) ord[cnt[pkey(q)]++] = (uint32_t)q;
-            cudaError_t e = cudaMallocAsync((void **)&pord, np * sizeof(uint32_t), s);
+            for (uint64_t q = 0; q < ng; ++q) ord[cnt[gkey(q)]++] = (uint32_t)q;
+            cudaError_t e = cudaMallocAsync((void **)&gord, ng * sizeof(uint32_t), s);
             if (e == cudaSuccess)
-                e = cudaMemcpyAsync(pord, ord.data(), np * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
+                e = cudaMemcpyAsync(gord, ord.data(), ng * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
             if (e != cudaSuccess) {
                 cudaGetLastError();
-                if (pord) cudaFreeAsync(pord, s);
-                return fail(ctx, PHPRNG_ENOMEM, std::string(W) + "pair order upload failed");
+                if (gord) cudaFreeAsync(gord, s);
+                return fail(ctx, PHPRNG_ENOMEM, std::string(W) + "group order upload failed");
             }
         }
         GenArgs g;
@@ -1020,51 +1044,10 @@ PH_API int phprng_interstream_serial_test(phprng_ctx *ctx, uint64_t first, uint6
         g.num = num_inst;
         g.per_inst = per_inst;
         std::string err;
-        const int rc = launch_inter_pairs(g, B, (unsigned long long *)hist, pord, s, &err);
-        if (pord) cudaFreeAsync(pord, s);
+        const int rc = launch_inter_groups(g, D, B, (unsigned long long *)hist, gord, s, &err);
+        if (gord) cudaFreeAsync(gord, s);
         if (rc != PHPRNG_OK) return fail(ctx, rc, std::string(W) + err);
         for (uint64_t i = first; i < first + num_inst; ++i) ctx->pos_host[i] += per_inst;
-        return PHPRNG_OK;
-    }
-    if (ctx->width == 32 && B <= (1u << 16) && 32 % D == 0 && num_inst % (uint64_t)D == 0) {
-        // Direct form: every tuple of the interleaved sequence holds D streams'
-        // numbers of one index, so the bins are written in stream order by the
-        // generator itself and counted from there (chunks of about 2^25
-        // numbers, rows padded to a multiple of 8 bins)
-        uint64_t Lch = std::max<uint64_t>(256, (1ull << 25) / num_inst / 256 * 256);
-        if (Lch > per_inst) Lch = per_inst;
-        const uint64_t Lrow = (Lch + 7) / 8 * 8;
-        uint16_t *binsI = nullptr;
-        cudaError_t e = cudaMallocAsync((void **)&binsI, num_inst * Lrow * sizeof(uint16_t), s);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return fail(ctx, PHPRNG_ENOMEM, std::string(W) + "scratch allocation failed");
-        }
-        GenArgs g;
-        g.inst = ctx->d_inst;
-        g.prog = ctx->d_prog;
-        g.st = ctx->st;
-        g.sk = ctx->sk32_8;
-        g.first = first;
-        g.num = num_inst;
-        g.c_out = nullptr;
-        g.r_out = nullptr;
-        g.stats = nullptr;
-        g.edge = nullptr;
-        g.c_is_64 = 0;
-        g.vec_ok = 0;
-        int rc = PHPRNG_OK;
-        if (num_inst >= kOrderMinInstances && num_inst < (1ull << 32))
-            g.order = instance_order(ctx, first, num_inst, s, &rc);
-        std::string err;
-        for (uint64_t j0 = 0; j0 < per_inst && rc == PHPRNG_OK; j0 += Lch) {
-            g.per_inst = std::min(Lch, per_inst - j0);
-            rc = launch_inter_direct(g, Lrow, D, B, binsI, (unsigned long long *)hist, s, &err);
-            if (rc == PHPRNG_OK)
-                for (uint64_t i = first; i < first + num_inst; ++i) ctx->pos_host[i] += g.per_inst;
-        }
-        cudaFreeAsync(binsI, s);
-        if (rc != PHPRNG_OK) return err.empty() ? rc : fail(ctx, rc, std::string(W) + err);
         return PHPRNG_OK;
     }
     // chunks of Lch numbers per stream, a multiple of D so that no tuple of the

@@ -211,17 +211,12 @@ static constexpr uint64_t kInterMaxChunk = 65535ull * 32;   // numbers per strea
 // before the chunks; launch_interstream then reads them.
 int launch_inter_consts(const DevInst *inst, uint64_t first, uint64_t Np, uint32_t B, void *k, void *stream,
                         std::string *err);
-// Direct form for D | 32, D | Np and B <= 2^16 (serial.cu): Eq. 9 for a chunk
-// of a.per_inst numbers per stream with 16-bit bins written in stream order
-// (binsI[a Lrow + j], Lrow a multiple of 8), then the interleaved sequence's
-// D-tuples counted into hist from those rows.
-int launch_inter_direct(const GenArgs &a, uint64_t Lrow, int D, uint32_t B, uint16_t *binsI,
-                        unsigned long long *hist, void *stream, std::string *err);
-// Interstream serial test for pairs (D = 2, an even number of 32-bit streams,
-// B <= 2^16), fused: adjacent warps generate the two streams of a pair and
-// count its pairs at once (pair_order: pair slots heaviest first, or NULL).
-int launch_inter_pairs(const GenArgs &a, uint32_t B, unsigned long long *hist, const uint32_t *pair_order,
-                       void *stream, std::string *err);
+// Interstream serial test for D = 2, 4 or 8 (D dividing the number of 32-bit
+// streams, B <= 2^16), fused: adjacent warps generate the D streams of a tuple
+// group and count its tuples at once (group_order: group slots heaviest
+// first, or NULL).
+int launch_inter_groups(const GenArgs &a, int D, uint32_t B, unsigned long long *hist,
+                        const uint32_t *group_order, void *stream, std::string *err);
 int launch_interstream(const void *k, uint64_t Np, uint64_t L, const void *c, int c64,
                        int D, uint32_t B, uint32_t *binsT, unsigned long long *hist, void *stream,
                        std::string *err);

@@ -578,96 +578,42 @@ inter_hist_kernel(const BT *__restrict__ binsT, uint64_t ntup, int D, uint32_t B
     }
 }
 
-// Interstream serial test, direct form for D | 32 and D | Np with B <= 2^16:
-// every tuple of the interleaved sequence then holds D streams' numbers of one
-// index j (stream a a multiple of D), so the tuples can be counted from the
-// bins in stream order without forming the interleaved sequence.
-//   inter_gen_kernel: Eq. 9 for one chunk (L numbers per stream) with each
-//     number's bin written at once as a 16-bit word, binsI[a Lrow + j] (Lrow
-//     a multiple of 8, so every lane stores its 8 bins as one 16-byte vector)
-//   inter_count_kernel: tiles of 32 streams x 64 indices through shared
-//     memory, each of the tile's 32/D tuples per index counted
-template <int NPT>
+// Interstream serial test for D = 2, 4 or 8, fused: with D dividing the number
+// of streams, the interleaved sequence's D-tuples are (number j of streams
+// Dq, ..., Dq + D-1), so the D streams of a tuple group run as adjacent warps
+// of one block and meet once per warp group: every warp but the group's first
+// leaves its group's bins in shared memory (double-buffered), the D warps pass
+// a named barrier of their own (D*32 threads; the groups of a block never wait
+// on one another), and the first warp counts the group's tuples.  No bins go
+// to HBM and no second kernel runs.  A group waits at most for its slowest
+// stream; groups run heaviest first (group_order).  All D warps of a group run
+// the same number of warp groups and leave together, so every barrier is
+// reached by all of them.
+template <int NPT, int GD>
 __global__ void __launch_bounds__(kSerialWarps * 32, PH_SERIAL_MINB)
-inter_gen_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, DevState st,
-                 SkipConst sk, uint64_t first, uint64_t num, uint64_t len, uint64_t Lrow, uint32_t B,
-                 uint16_t *__restrict__ binsI, const uint32_t *__restrict__ order)
+inter_groups_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, DevState st,
+                    SkipConst sk, uint64_t first, uint64_t num, uint64_t len, uint32_t B,
+                    unsigned long long *__restrict__ hist, const uint32_t *__restrict__ group_order)
 {
     constexpr int WB = kSerialWarps;
-    constexpr uint64_t G = 32 * NPT;
-    __shared__ uint4 etb[WB][4 * (NPT / 4) * 32];   // per warp: the exponent program's odd powers
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint64_t w = (uint64_t)blockIdx.x * WB + warp;
-    if (w >= num) return;
-    const uint64_t j = order ? order[w] : w;
-    const uint64_t i = first + j;
-    const DevInst P = inst[i];
-    const ExpProg &pg = prog[i];
-    const uint32_t r = (uint32_t)(((uint64_t)B << 32) / P.yN);
-    uint32_t M = (uint32_t)st.m[i];
-    uint32_t sig = mont32((uint32_t)st.s[i], sk.lane[lane], sk.p, sk.pinv);
-    const uint64_t pos_after = st.pos[i] + len;
-    uint16_t *row = binsI + j * Lrow;
-    uint32_t x[NPT], sig_last = sig;
-    uint64_t g_last = 0;
-    for (uint64_t g0 = 0; g0 < len; g0 += G) {
-        uint32_t sv[NPT], msg[NPT];
-        const uint64_t my0 = g0 + (uint64_t)NPT * lane;
-        sig_last = sig;
-        g_last = g0;
-        const bool full = g0 + G <= len;                 // warp-uniform
-        if (full)
-            messages32<NPT, true>(P, sk, lane, my0, len, M, sig, sv, msg);
-        else
-            messages32<NPT>(P, sk, lane, my0, len, M, sig, sv, msg);
-        encrypt32_tb<NPT>(P, pg, msg, x, etb[warp], lane);
-        uint32_t b[NPT];
-        serial_bins<NPT>(x, P.yN, P.ybits, r, B, b);
-        if (full && NPT == 8) {
-            *reinterpret_cast<uint4 *>(row + my0) =
-                make_uint4(b[0] | b[1] << 16, b[2] | b[3] << 16, b[4] | b[5] << 16, b[6] | b[7] << 16);
-        } else {
-#pragma unroll
-            for (int u = 0; u < NPT; ++u)
-                if (my0 + u < len) row[my0 + u] = (uint16_t)b[u];
-        }
-    }
-    write_state_after<NPT, uint32_t, uint32_t>(st, sk, i, lane, g_last, len, pos_after, M, sig_last, x);
-}
-
-// Interstream serial test for pairs (D = 2), fused: the interleaved sequence's
-// pairs are (number j of stream 2q, number j of stream 2q+1), so the two
-// streams of a pair run as adjacent warps of one block and meet once per warp
-// group: the odd stream's warp leaves its group's bins in shared memory
-// (double-buffered), the two warps pass a named barrier of their own (64
-// threads; the four pairs of a block never wait on one another), and the even
-// stream's warp counts the group's pairs.  No bins go to HBM and no second
-// kernel runs.  A pair waits at most for its slower stream; pairs run heaviest
-// first (pair_order).  Both warps of a pair run the same number of groups and
-// leave together, so every barrier is reached by both.
-template <int NPT>
-__global__ void __launch_bounds__(kSerialWarps * 32, PH_SERIAL_MINB)
-inter_pairs_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, DevState st,
-                   SkipConst sk, uint64_t first, uint64_t num, uint64_t len, uint32_t B,
-                   unsigned long long *__restrict__ hist, const uint32_t *__restrict__ pair_order)
-{
-    constexpr int WB = kSerialWarps;
-    static_assert(WB % 2 == 0 && NPT == 8, "pairs of warps, 8 bins per lane as one 16-byte row");
+    static_assert(WB % GD == 0 && GD >= 2 && NPT == 8, "groups of warps, 8 bins per lane as one 16-byte row");
+    constexpr int NG = WB / GD;                        // tuple groups per block
     constexpr uint64_t G = 32 * NPT;
     __shared__ uint4 etb[WB][4 * (NPT / 4) * 32];      // per warp: the exponent program's odd powers
-    __shared__ uint4 pb[WB / 2][2][32];                 // per pair: the odd stream's bins, two buffers
-    __shared__ uint32_t lc[WB][kLocalBins];            // per warp: shared counters when B^2 <= kLocalBins
+    __shared__ uint4 pb[NG][GD - 1][2][32];            // per group: its other streams' bins, two buffers
+    __shared__ uint32_t lc[WB][kLocalBins];            // per warp: shared counters when B^D <= kLocalBins
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint64_t ps = (uint64_t)blockIdx.x * (WB / 2) + (warp >> 1);   // pair slot
-    if (2 * ps >= num) return;                         // num is even: both warps of the pair leave
-    const uint64_t pq = pair_order ? pair_order[ps] : ps;
-    const bool odd = warp & 1;
-    const uint64_t j = 2 * pq + (odd ? 1 : 0);
+    const int gi = warp / GD, member = warp % GD;
+    const uint64_t gs = (uint64_t)blockIdx.x * NG + gi;   // group slot
+    if ((uint64_t)GD * gs >= num) return;              // num is a multiple of GD: the group leaves together
+    const uint64_t gq = group_order ? group_order[gs] : gs;
+    const uint64_t j = (uint64_t)GD * gq + member;
     const uint64_t i = first + j;
     const DevInst P = inst[i];
     const ExpProg &pg = prog[i];
     const uint32_t r = (uint32_t)(((uint64_t)B << 32) / P.yN);
-    const uint32_t nbins = B * B;                      // B <= 2^16
+    uint32_t nbins = 1;
+    for (int d = 0; d < GD && nbins <= kLocalBins; ++d) nbins *= B;
     const bool local = nbins <= kLocalBins;
     uint32_t *cnt = lc[warp];
     if (local)
@@ -675,7 +621,7 @@ inter_pairs_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__
     uint32_t M = (uint32_t)st.m[i];
     uint32_t sig = mont32((uint32_t)st.s[i], sk.lane[lane], sk.p, sk.pinv);
     const uint64_t pos_after = st.pos[i] + len;
-    const uint32_t bar = 1 + (uint32_t)(warp >> 1);    // the pair's named barrier (0 is __syncthreads)
+    const uint32_t bar = 1 + (uint32_t)gi;             // the group's named barrier (0 is __syncthreads)
     uint32_t x[NPT], sig_last = sig;
     uint64_t g_last = 0;
     int buf = 0;
@@ -684,7 +630,7 @@ inter_pairs_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__
         const uint64_t my0 = g0 + (uint64_t)NPT * lane;
         sig_last = sig;
         g_last = g0;
-        const bool full = g0 + G <= len;               // pair-uniform
+        const bool full = g0 + G <= len;               // group-uniform
         if (full)
             messages32<NPT, true>(P, sk, lane, my0, len, M, sig, sv, msg);
         else
@@ -692,114 +638,66 @@ inter_pairs_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__
         encrypt32_tb<NPT>(P, pg, msg, x, etb[warp], lane);
         uint32_t b[NPT];
         serial_bins<NPT>(x, P.yN, P.ybits, r, B, b);
-        uint4 *row = &pb[warp >> 1][buf][lane];
-        if (odd) *row = make_uint4(b[0] | b[1] << 16, b[2] | b[3] << 16, b[4] | b[5] << 16, b[6] | b[7] << 16);
-        asm volatile("bar.sync %0, 64;" ::"r"(bar) : "memory");
-        if (!odd) {
-            const uint4 q = *row;
-            const uint32_t o[NPT] = {q.x & 0xFFFFu, q.x >> 16, q.y & 0xFFFFu, q.y >> 16,
-                                     q.z & 0xFFFFu, q.z >> 16, q.w & 0xFFFFu, q.w >> 16};
+        if (member)
+            pb[gi][member - 1][buf][lane] =
+                make_uint4(b[0] | b[1] << 16, b[2] | b[3] << 16, b[4] | b[5] << 16, b[6] | b[7] << 16);
+        asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(GD * 32) : "memory");
+        if (!member) {
+            uint32_t idx[NPT], scale = 1;
+#pragma unroll
+            for (int u = 0; u < NPT; ++u) idx[u] = b[u];
+#pragma unroll
+            for (int d = 1; d < GD; ++d) {
+                scale *= B;
+                const uint4 q = pb[gi][d - 1][buf][lane];
+                const uint32_t o[NPT] = {q.x & 0xFFFFu, q.x >> 16, q.y & 0xFFFFu, q.y >> 16,
+                                         q.z & 0xFFFFu, q.z >> 16, q.w & 0xFFFFu, q.w >> 16};
+#pragma unroll
+                for (int u = 0; u < NPT; ++u) idx[u] += o[u] * scale;   // the tuple's first element least significant
+            }
 #pragma unroll
             for (int u = 0; u < NPT; ++u) {
                 if (!full && my0 + u >= len) continue;
-                const uint32_t idx = b[u] + o[u] * B;         // the tuple's first element least significant
                 if (local)
-                    atomicAdd(cnt + idx, 1u);
+                    atomicAdd(cnt + idx[u], 1u);
                 else
-                    atomicAdd(hist + idx, 1ull);
+                    atomicAdd(hist + idx[u], 1ull);
             }
             if (local && (g0 / G) % kLocalFlushGroups == kLocalFlushGroups - 1)
                 flush_local<false>(cnt, nbins, lane, hist);
         }
         buf ^= 1;
     }
-    if (local && !odd) flush_local<false>(cnt, nbins, lane, hist);
+    if (local && !member) flush_local<false>(cnt, nbins, lane, hist);
     write_state_after<NPT, uint32_t, uint32_t>(st, sk, i, lane, g_last, len, pos_after, M, sig_last, x);
 }
 
-int launch_inter_pairs(const GenArgs &a, uint32_t B, unsigned long long *hist, const uint32_t *pair_order,
-                       void *stream, std::string *err)
+int launch_inter_groups(const GenArgs &a, int D, uint32_t B, unsigned long long *hist,
+                        const uint32_t *group_order, void *stream, std::string *err)
 {
     if (a.num == 0 || a.per_inst == 0) return PHPRNG_OK;
-    const uint64_t blocks = (a.num / 2 + kSerialWarps / 2 - 1) / (kSerialWarps / 2);
-    inter_pairs_kernel<8><<<(unsigned)blocks, kSerialWarps * 32, 0, (cudaStream_t)stream>>>(
-        a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, B, hist, pair_order);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) {
-        *err = std::string("inter_pairs_kernel launch: ") + cudaGetErrorString(e);
-        return PHPRNG_ECUDA;
-    }
-    return PHPRNG_OK;
-}
-
-static constexpr uint32_t kCountTileJ = 64;
-
-template <bool SMEM>
-__global__ void __launch_bounds__(256)
-inter_count_kernel(const uint16_t *__restrict__ binsI, uint64_t Np, uint64_t L, uint64_t Lrow, int D,
-                   uint32_t B, uint32_t nbins, unsigned long long *__restrict__ hist)
-{
-    __shared__ uint16_t tile[32][kCountTileJ + 2];
-    __shared__ uint32_t sh[SMEM ? kInterSmemBins : 1];
-    if (SMEM) {
-        for (uint32_t b = threadIdx.x; b < nbins; b += blockDim.x) sh[b] = 0;
-    }
-    const uint64_t a0 = (uint64_t)blockIdx.x * 32, j0 = (uint64_t)blockIdx.y * kCountTileJ;
-    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // rows of the tile: one stream each, kCountTileJ consecutive indices (two per lane)
-    for (uint32_t rr = warp; rr < 32; rr += 8) {
-        const uint64_t a = a0 + rr;
-        const uint64_t jj = j0 + 2 * lane;
-        if (a < Np && jj < L) {
-            tile[rr][2 * lane] = binsI[a * Lrow + jj];
-            if (jj + 1 < L) tile[rr][2 * lane + 1] = binsI[a * Lrow + jj + 1];
-        }
-    }
-    __syncthreads();
-    const uint32_t tpr = 32 / (uint32_t)D;                 // tuples per index in the tile
-    const uint32_t ntile = tpr * kCountTileJ;
-    for (uint32_t k = threadIdx.x; k < ntile; k += blockDim.x) {
-        const uint32_t jt = k / tpr, t = k - jt * tpr;
-        const uint64_t a = a0 + (uint64_t)t * D;
-        if (j0 + jt >= L || a + (uint64_t)D > Np) continue;
-        uint32_t idx = 0, scale = 1;
-        for (int d = 0; d < D; ++d) {
-            idx += (uint32_t)tile[t * D + d][jt] * scale;
-            scale *= B;
-        }
-        if (SMEM) atomicAdd(sh + idx, 1u);
-        else atomicAdd(hist + idx, 1ull);
-    }
-    if (SMEM) {
-        __syncthreads();
-        for (uint32_t b = threadIdx.x; b < nbins; b += blockDim.x)
-            if (sh[b]) atomicAdd(hist + b, (unsigned long long)sh[b]);
-    }
-}
-
-int launch_inter_direct(const GenArgs &a, uint64_t Lrow, int D, uint32_t B, uint16_t *binsI,
-                        unsigned long long *hist, void *stream, std::string *err)
-{
-    if (a.num == 0 || a.per_inst == 0) return PHPRNG_OK;
-    cudaStream_t s = (cudaStream_t)stream;
     const uint64_t blocks = (a.num + kSerialWarps - 1) / kSerialWarps;
-    inter_gen_kernel<8><<<(unsigned)blocks, kSerialWarps * 32, 0, s>>>(
-        a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, Lrow, B, binsI, a.order);
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (D) {
+    case 2:
+        inter_groups_kernel<8, 2><<<(unsigned)blocks, kSerialWarps * 32, 0, s>>>(
+            a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, B, hist, group_order);
+        break;
+    case 4:
+        inter_groups_kernel<8, 4><<<(unsigned)blocks, kSerialWarps * 32, 0, s>>>(
+            a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, B, hist, group_order);
+        break;
+    case 8:
+        inter_groups_kernel<8, 8><<<(unsigned)blocks, kSerialWarps * 32, 0, s>>>(
+            a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, B, hist, group_order);
+        break;
+    default:
+        *err = "inter_groups_kernel: D must be 2, 4 or 8";
+        return PHPRNG_EINVAL;
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
-        *err = std::string("inter_gen_kernel launch: ") + cudaGetErrorString(e);
-        return PHPRNG_ECUDA;
-    }
-    uint32_t nbins = 1;
-    for (int d = 0; d < D; ++d) nbins *= B;
-    const dim3 grid((unsigned)((a.num + 31) / 32), (unsigned)((a.per_inst + kCountTileJ - 1) / kCountTileJ));
-    if (nbins <= kInterSmemBins)
-        inter_count_kernel<true><<<grid, 256, 0, s>>>(binsI, a.num, a.per_inst, Lrow, D, B, nbins, hist);
-    else
-        inter_count_kernel<false><<<grid, 256, 0, s>>>(binsI, a.num, a.per_inst, Lrow, D, B, nbins, hist);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) {
-        *err = std::string("inter_count_kernel launch: ") + cudaGetErrorString(e);
+        *err = std::string("inter_groups_kernel launch: ") + cudaGetErrorString(e);
         return PHPRNG_ECUDA;
     }
     return PHPRNG_OK;

@@ -265,14 +265,16 @@ def _interstream_oracle(rows, per, D, B):
 @pytest.mark.parametrize("Np,per,D,B,e", [(1, 1000, 2, 32, None), (3, 1001, 2, 16, None), (37, 777, 3, 10, None),
                                           (64, 513, 5, 4, None), (5, 2000, 1, 1 << 20, None),
                                           (1100, 40, 2, 1 << 10, None), (4, 9_000_001, 3, 16, 9),
-                                          # the direct form (D | 32, D | Np, B <= 2^16): ragged
-                                          # groups, several chunks, D = 1, 2, 4
+                                          # D = 2, 4, 8 dividing Np: groups of D warps counting their
+                                          # tuples as generated (ragged groups, long streams, shared
+                                          # counters when B^D <= 224, group slots heaviest first, e = 9);
+                                          # D = 1: the frequency test's kernel
                                           (64, 5003, 2, 32, None), (96, 2049, 4, 8, None),
                                           (128, 3001, 1, 1 << 16, None), (512, 70_001, 2, 1 << 10, None),
-                                          # pairs (D = 2, Np even), fused: shared counters (B^2 <=
-                                          # 224) with pair slots heaviest first, and e = 9
                                           (2048, 300, 2, 14, None), (64, 3001, 2, 4, None),
-                                          (8, 5000, 2, 16, 9)])
+                                          (8, 5000, 2, 16, 9), (128, 1000, 4, 3, None),
+                                          (1024, 300, 4, 4, None), (64, 2000, 8, 2, None),
+                                          (2048, 257, 8, 3, None), (16, 3333, 8, 2, 17)])
 def test_interstream_matches_oracle(ph, torch, Np, per, D, B, e):
     """Interleaved order over Np streams: ragged tails (Np per mod D != 0),
     shared-memory and global counters, and 4 x 9,000,001 numbers at D = 3 in
