@@ -328,12 +328,6 @@ __device__ __forceinline__ void reals_of(const DevInst &P, const uint32_t (&x)[N
             if ((amb >> u) & 1u) r[u] = real32_exact(x[u], P.yN, P.ybits, P.aux);
     }
 }
-template <int NPT>
-__device__ __forceinline__ void reals_of(const DevInst &P, const uint64_t (&x)[NPT], double (&r)[NPT])
-{
-#pragma unroll
-    for (int u = 0; u < NPT; ++u) r[u] = real64(x[u], P.n);
-}
 
 // Two doubles as one 16-byte store of their four 32-bit words: with R formed
 // one number at a time (the LIGHT loop, e = 9: 0.969 -> 0.963 ms) this takes
