@@ -267,7 +267,7 @@ int phprng_runs_test(phprng_ctx *ctx, uint64_t first, uint64_t num_inst, uint64_
  * to 2^20 or at most 2^16, B^D <= 2^24, 32-bit instances.  hist: device
  * memory, B^D uint64 counters, added to.  Streams advance by per_inst.
  * Asynchronous on cuda_stream.  In a 32-bit context D = 1 is the frequency
- * test's kernel, and D = 2, 4 or 8 dividing num_inst with B <= 2^16 takes no
+ * test's kernel, and D >= 2 dividing num_inst with B <= 2^16 takes no
  * scratch: the D streams of each tuple group run as D warps that count their
  * tuples as they generate them (only an order of the groups, num_inst / D
  * words, when there are many).  Otherwise a scratch of about 2^25 numbers

@@ -988,7 +988,7 @@ PH_API int phprng_interstream_serial_test(phprng_ctx *ctx, uint64_t first, uint6
     CU(ctx, cudaSetDevice(ctx->device));
     if (pointer_kind(hist) != 1) return fail(ctx, PHPRNG_EINVAL, std::string(W) + "hist must be device memory");
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    const bool groups = D == 2 || D == 4 || D == 8;
+    const bool groups = D >= 2;                          // 2 <= D <= 8
     if (ctx->width == 32 && D == 1) {
         // single numbers: the interleaved order does not change their
         // histogram, which is the frequency test's (serial kernel, D = 1)

@@ -211,7 +211,7 @@ static constexpr uint64_t kInterMaxChunk = 65535ull * 32;   // numbers per strea
 // before the chunks; launch_interstream then reads them.
 int launch_inter_consts(const DevInst *inst, uint64_t first, uint64_t Np, uint32_t B, void *k, void *stream,
                         std::string *err);
-// Interstream serial test for D = 2, 4 or 8 (D dividing the number of 32-bit
+// Interstream serial test for 2 <= D <= 8 (D dividing the number of 32-bit
 // streams, B <= 2^16), fused: adjacent warps generate the D streams of a tuple
 // group and count its tuples at once (group_order: group slots heaviest
 // first, or NULL).

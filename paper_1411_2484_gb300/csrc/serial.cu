@@ -578,10 +578,10 @@ inter_hist_kernel(const BT *__restrict__ binsT, uint64_t ntup, int D, uint32_t B
     }
 }
 
-// Interstream serial test for D = 2, 4 or 8, fused: with D dividing the number
+// Interstream serial test for 2 <= D <= 8, fused: with D dividing the number
 // of streams, the interleaved sequence's D-tuples are (number j of streams
 // Dq, ..., Dq + D-1), so the D streams of a tuple group run as adjacent warps
-// of one block and meet once per warp group: every warp but the group's first
+// of one block (floor(8/D) groups per block) and meet once per warp group: every warp but the group's first
 // leaves its group's bins in shared memory (double-buffered), the D warps pass
 // a named barrier of their own (D*32 threads; the groups of a block never wait
 // on one another), and the first warp counts the group's tuples.  No bins go
@@ -590,14 +590,14 @@ inter_hist_kernel(const BT *__restrict__ binsT, uint64_t ntup, int D, uint32_t B
 // the same number of warp groups and leave together, so every barrier is
 // reached by all of them.
 template <int NPT, int GD>
-__global__ void __launch_bounds__(kSerialWarps * 32, PH_SERIAL_MINB)
+__global__ void __launch_bounds__(GD * (kSerialWarps / GD) * 32, PH_SERIAL_MINB)
 inter_groups_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, DevState st,
                     SkipConst sk, uint64_t first, uint64_t num, uint64_t len, uint32_t B,
                     unsigned long long *__restrict__ hist, const uint32_t *__restrict__ group_order)
 {
-    constexpr int WB = kSerialWarps;
-    static_assert(WB % GD == 0 && GD >= 2 && NPT == 8, "groups of warps, 8 bins per lane as one 16-byte row");
-    constexpr int NG = WB / GD;                        // tuple groups per block
+    constexpr int NG = kSerialWarps / GD;             // tuple groups per block
+    constexpr int WB = GD * NG;                        // warps per block (6 for D = 3, 5 for D = 5, ...)
+    static_assert(GD >= 2 && GD <= kSerialWarps && NPT == 8, "groups of warps, 8 bins per lane as one 16-byte row");
     constexpr uint64_t G = 32 * NPT;
     __shared__ uint4 etb[WB][4 * (NPT / 4) * 32];      // per warp: the exponent program's odd powers
     __shared__ uint4 pb[NG][GD - 1][2][32];            // per group: its other streams' bins, two buffers
@@ -672,27 +672,31 @@ inter_groups_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict_
     write_state_after<NPT, uint32_t, uint32_t>(st, sk, i, lane, g_last, len, pos_after, M, sig_last, x);
 }
 
+template <int GD>
+static void launch_groups_d(const GenArgs &a, uint32_t B, unsigned long long *hist, const uint32_t *group_order,
+                            cudaStream_t s)
+{
+    constexpr int WB = GD * (kSerialWarps / GD);
+    const uint64_t blocks = (a.num + WB - 1) / WB;
+    inter_groups_kernel<8, GD><<<(unsigned)blocks, WB * 32, 0, s>>>(
+        a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, B, hist, group_order);
+}
+
 int launch_inter_groups(const GenArgs &a, int D, uint32_t B, unsigned long long *hist,
                         const uint32_t *group_order, void *stream, std::string *err)
 {
     if (a.num == 0 || a.per_inst == 0) return PHPRNG_OK;
-    const uint64_t blocks = (a.num + kSerialWarps - 1) / kSerialWarps;
     cudaStream_t s = (cudaStream_t)stream;
     switch (D) {
-    case 2:
-        inter_groups_kernel<8, 2><<<(unsigned)blocks, kSerialWarps * 32, 0, s>>>(
-            a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, B, hist, group_order);
-        break;
-    case 4:
-        inter_groups_kernel<8, 4><<<(unsigned)blocks, kSerialWarps * 32, 0, s>>>(
-            a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, B, hist, group_order);
-        break;
-    case 8:
-        inter_groups_kernel<8, 8><<<(unsigned)blocks, kSerialWarps * 32, 0, s>>>(
-            a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, B, hist, group_order);
-        break;
+    case 2: launch_groups_d<2>(a, B, hist, group_order, s); break;
+    case 3: launch_groups_d<3>(a, B, hist, group_order, s); break;
+    case 4: launch_groups_d<4>(a, B, hist, group_order, s); break;
+    case 5: launch_groups_d<5>(a, B, hist, group_order, s); break;
+    case 6: launch_groups_d<6>(a, B, hist, group_order, s); break;
+    case 7: launch_groups_d<7>(a, B, hist, group_order, s); break;
+    case 8: launch_groups_d<8>(a, B, hist, group_order, s); break;
     default:
-        *err = "inter_groups_kernel: D must be 2, 4 or 8";
+        *err = "inter_groups_kernel: D must be 2 to 8";
         return PHPRNG_EINVAL;
     }
     cudaError_t e = cudaGetLastError();

@@ -274,7 +274,11 @@ def _interstream_oracle(rows, per, D, B):
                                           (2048, 300, 2, 14, None), (64, 3001, 2, 4, None),
                                           (8, 5000, 2, 16, 9), (128, 1000, 4, 3, None),
                                           (1024, 300, 4, 4, None), (64, 2000, 8, 2, None),
-                                          (2048, 257, 8, 3, None), (16, 3333, 8, 2, 17)])
+                                          (2048, 257, 8, 3, None), (16, 3333, 8, 2, 17),
+                                          # D = 3, 5, 6, 7 dividing Np: groups of 6, 5, 6, 7 warps per block
+                                          (48, 1000, 3, 10, None), (30, 700, 5, 4, None),
+                                          (30, 701, 5, 2, None), (36, 513, 6, 3, None),
+                                          (21, 600, 7, 3, 9), (3 * 1024, 100, 3, 100, None)])
 def test_interstream_matches_oracle(ph, torch, Np, per, D, B, e):
     """Interleaved order over Np streams: ragged tails (Np per mod D != 0),
     shared-memory and global counters, and 4 x 9,000,001 numbers at D = 3 in
