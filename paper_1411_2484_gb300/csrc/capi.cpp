@@ -451,8 +451,9 @@ static int ensure_staging(phprng_ctx *c, size_t bytes)
 // Host outputs: generate blocks (instances x numbers) into kStages device
 // staging buffers in turn and copy each block back on that buffer's own copy
 // stream while later blocks are generated (several copy engines can run at
-// once); every block is one contiguous copy.  Returns once everything is on
-// the host.
+// once); every block is one contiguous copy.  The first block of whole
+// instances is kept to about 2^22 numbers, so that the first copy starts
+// early.  Returns once everything is on the host.
 static int generate_to_host(phprng_ctx *c, uint64_t first, uint64_t num, uint64_t per_inst,
                             void *c_out, double *r_out, cudaStream_t s)
 {
@@ -466,8 +467,9 @@ static int generate_to_host(phprng_ctx *c, uint64_t first, uint64_t num, uint64_
     if (rc != PHPRNG_OK) return rc;
     int k = 0;
     bool used[phprng_ctx::kStages] = {};
-    for (uint64_t i0 = 0; i0 < num; i0 += ninst) {
-        const uint64_t ni = std::min(ninst, num - i0);
+    const uint64_t ninst0 = std::max<uint64_t>(1, std::min<uint64_t>(ninst, (1ull << 22) / piece));
+    for (uint64_t i0 = 0, ni = 0; i0 < num; i0 += ni) {
+        ni = std::min(i0 == 0 ? ninst0 : ninst, num - i0);
         for (uint64_t j0 = 0; j0 < per_inst; j0 += piece) {
             const uint64_t pj = std::min(piece, per_inst - j0);
             char *buf = (char *)c->stage[k];
