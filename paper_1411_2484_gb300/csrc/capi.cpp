@@ -407,11 +407,39 @@ static int launch_range(phprng_ctx *c, uint64_t first, uint64_t num, uint64_t pe
             return fail(c, PHPRNG_ENOMEM, "phprng_generate: statistics scratch allocation failed");
         }
     }
+    // statistics: blocks of consecutive instances (their adjacent-stream
+    // products need them together), launched heaviest block first
+    uint32_t *bord = nullptr;
+    if (stats && num >= kOrderMinInstances && num < (1ull << 32)) {
+        const uint64_t W = gen32_stats_block_warps(), nb = (num + W - 1) / W;
+        std::vector<uint32_t> ord(nb), cnt(513, 0);
+        auto bkey = [&](uint64_t b) {
+            uint16_t k = c->key[first + W * b];
+            for (uint64_t j = W * b + 1; j < std::min<uint64_t>(num, W * b + W); ++j)
+                k = std::min(k, c->key[first + j]);
+            return k;
+        };
+        for (uint64_t b = 0; b < nb; ++b) ++cnt[bkey(b) + 1];
+        for (int k = 1; k <= 512; ++k) cnt[k] += cnt[k - 1];
+        for (uint64_t b = 0; b < nb; ++b) ord[cnt[bkey(b)]++] = (uint32_t)b;
+        // from pageable memory: staged before the call returns
+        cudaError_t e = cudaMallocAsync((void **)&bord, nb * sizeof(uint32_t), s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(bord, ord.data(), nb * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            if (bord) cudaFreeAsync(bord, s);
+            if (g.edge) cudaFreeAsync(g.edge, s);
+            return fail(c, PHPRNG_ENOMEM, "phprng_generate: statistics block order upload failed");
+        }
+        g.order = bord;
+    }
     if (c->any32) {
         g.sk = c->sk32;
         g.light = !stats && light_range(c, first, num);
         rc = launch_gen32(g, s, &err);
     }
+    if (bord) cudaFreeAsync(bord, s);
     if (g.edge) cudaFreeAsync(g.edge, s);
     if (rc == PHPRNG_OK && c->any64) {
         g.sk = c->sk64;

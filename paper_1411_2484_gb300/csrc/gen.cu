@@ -92,7 +92,11 @@ gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
     constexpr int W = WB;
     constexpr uint64_t G = 32 * NPT;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint64_t w = (uint64_t)blockIdx.x * W + warp;
+    // statistics: `order` gives the blocks' launch order (heaviest first); the
+    // block keeps its W consecutive instances, which the adjacent-stream
+    // products need, and its boundary rows go by its own index lb
+    const uint64_t lb = (STATS && order) ? (uint64_t)order[blockIdx.x] : (uint64_t)blockIdx.x;
+    const uint64_t w = lb * W + warp;
     // statistics launches are never split (sp.K = 1)
     const bool active = STATS ? w < num : w < num * sp.K;
     if (!STATS && !active) return;
@@ -230,8 +234,8 @@ gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
                         }
                     }
                 }
-                if (edge && ((warp == W - 1 && has_next) || (warp == 0 && blockIdx.x > 0))) {
-                    uint32_t *row = edge + (2 * (uint64_t)blockIdx.x + (warp == 0 ? 0 : 1)) * per_inst;
+                if (edge && ((warp == W - 1 && has_next) || (warp == 0 && lb > 0))) {
+                    uint32_t *row = edge + (2 * lb + (warp == 0 ? 0 : 1)) * per_inst;
 #pragma unroll
                     for (int u = 0; u < NPT; ++u)
                         if (my0 + u < per_inst) row[my0 + u] = x[u];
@@ -457,11 +461,11 @@ int launch_gen32(const GenArgs &a, void *stream, std::string *err)
         if (a.c_is_64)
             gen32_kernel<kNPT, uint64_t, true, false, kWarpsPerBlock><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(
                 a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, (uint64_t *)a.c_out, a.r_out,
-                a.vec_ok, a.stats, a.edge, nullptr, a.sp);
+                a.vec_ok, a.stats, a.edge, a.order, a.sp);
         else
             gen32_kernel<kNPT, uint32_t, true, false, kWarpsPerBlock><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(
                 a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, (uint32_t *)a.c_out, a.r_out,
-                a.vec_ok, a.stats, a.edge, nullptr, a.sp);
+                a.vec_ok, a.stats, a.edge, a.order, a.sp);
         int rc = check_launch(err, "gen32_kernel (statistics) launch");
         if (rc != PHPRNG_OK || blocks < 2) return rc;
         stats_edge_kernel<<<(unsigned)((blocks - 1 + 7) / 8), 256, 0, s>>>(
@@ -490,6 +494,8 @@ int launch_gen32(const GenArgs &a, void *stream, std::string *err)
 #undef PH_GEN32_PLAIN
     return check_launch(err, "gen32_kernel launch");
 }
+
+uint32_t gen32_stats_block_warps() { return kWarpsPerBlock; }
 
 uint64_t gen32_edge_words(uint64_t num, uint64_t per_inst)
 {

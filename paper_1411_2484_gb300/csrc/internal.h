@@ -173,6 +173,7 @@ int batch_max_blocks_per_sm(int npt32, int c_is_64);
 int gen_npt(int wide);   // numbers per lane per warp group of the 32/64-bit launch
 int launch_gen32(const GenArgs &a, void *stream, std::string *err);
 uint64_t gen32_edge_words(uint64_t num, uint64_t per_inst);
+uint32_t gen32_stats_block_warps();   // instances per block of a statistics launch
 uint64_t gen32_fixed_edge_words();
 int launch_gen32_stats_fixed(const GenArgs &a, int dev, void *stream, std::string *err);
 int launch_gen64(const GenArgs &a, void *stream, std::string *err);
