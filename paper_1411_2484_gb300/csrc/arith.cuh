@@ -205,6 +205,43 @@ struct alignas(16) ExpProg {
     uint8_t ent[28];
 };
 
+// Exponent program of the 32-bit heavy generator: a table of 1 to 8 odd
+// powers m, m^3, .., m^(2 tbl - 1) (shared memory holds it), the table size
+// and the windows chosen per exponent by an exact search (dynamic programming
+// over the exponent's bit positions, for every table size) for the fewest
+// Montgomery products, table included.  x starts as the first window's table
+// entry; each later window is `sq` squarings then one product with its entry
+// (e is odd, so no squarings follow the last window).  K, Kq: this program's
+// exit constant R^(1-alpha) mod n and K n^-1 mod 2^32.
+struct alignas(16) ExpProg8 {
+    uint32_t K, Kq;
+    uint8_t nent;       // windows (>= 1)
+    uint8_t tbl;        // table entries, 1 .. 8
+    uint8_t pad[2];
+    uint16_t ent[32];   // per window: sq in bits 0-7, table index (v-1)/2 in bits 8-10
+};
+static_assert(sizeof(ExpProg8) == 80, "ExpProg8 layout");
+
+// The same program run with the table in an array (host tests, NPT numbers).
+template <int NPT>
+PH_HD void modexp_prog8(uint32_t (&x)[NPT], const uint32_t (&m)[NPT], const ExpProg8 &pg, uint32_t n,
+                        uint32_t ninv)
+{
+    uint32_t t[8][NPT], m2[NPT];
+    for (int u = 0; u < NPT; ++u) t[0][u] = m[u];
+    if (pg.tbl >= 2)
+        for (int u = 0; u < NPT; ++u) m2[u] = mont32(m[u], m[u], n, ninv);
+    for (int k = 1; k < pg.tbl; ++k)
+        for (int u = 0; u < NPT; ++u) t[k][u] = mont32(t[k - 1][u], m2[u], n, ninv);
+    for (int u = 0; u < NPT; ++u) x[u] = t[pg.ent[0] >> 8][u];
+    for (int k = 1; k < pg.nent; ++k) {
+        for (int q = 0; q < (pg.ent[k] & 0xFF); ++q)
+            for (int u = 0; u < NPT; ++u) x[u] = mont32(x[u], x[u], n, ninv);
+        for (int u = 0; u < NPT; ++u) x[u] = mont32(x[u], t[(pg.ent[k] >> 8) & 7][u], n, ninv);
+    }
+    for (int u = 0; u < NPT; ++u) x[u] = mont32c(x[u], pg.K, pg.Kq, n);
+}
+
 PH_HD uint32_t mont(uint32_t a, uint32_t b, uint32_t n, uint32_t ninv) { return mont32(a, b, n, ninv); }
 PH_HD uint64_t mont(uint64_t a, uint64_t b, uint64_t n, uint64_t ninv) { return mont64(a, b, n, ninv); }
 // The exit product x K of an exponentiation (Kq = K n^-1 mod 2^32 on the 32-bit path).

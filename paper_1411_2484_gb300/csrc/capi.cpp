@@ -39,6 +39,7 @@ static void free_ctx(phprng_ctx *c)
     cudaDeviceSynchronize();
     cudaFree(c->d_inst);
     cudaFree(c->d_prog);
+    cudaFree(c->d_prog8);
     cudaFree(c->d_state);
     cudaFree(c->d_order);
     cudaFree(c->d_L0);
@@ -160,6 +161,7 @@ PH_API int phprng_create(phprng_ctx **out, int width, const phprng_instance *ins
     if (!c) return fail(nullptr, PHPRNG_ENOMEM, "phprng_create: host allocation failed");
     std::vector<DevInst> di;
     std::vector<ExpProg> prog;
+    std::vector<ExpProg8> prog8;
     std::vector<uint64_t> state;
     try {
         c->width = width;
@@ -173,6 +175,7 @@ PH_API int phprng_create(phprng_ctx **out, int width, const phprng_instance *ins
         c->key.resize(count);
         di.resize(count);
         prog.resize(count);
+        prog8.resize(count);
         state.assign(4 * count, 0);
     } catch (const std::bad_alloc &) {
         delete c;
@@ -183,6 +186,7 @@ PH_API int phprng_create(phprng_ctx **out, int width, const phprng_instance *ins
         c->wide[i] = (uint8_t)w;
         (w ? c->any64 : c->any32) = true;
         di[i] = derive_inst(inst[i], w, &prog[i]);
+        if (!w) prog8[i] = derive_prog8(inst[i].n, inst[i].e);   // the heavy 32-bit generator's program
         c->key[i] = (uint16_t)(256 * w + 255 - std::min(program_products(prog[i]), 255));
         state[i] = inst[i].m0;
         state[count + i] = inst[i].s0;
@@ -203,10 +207,13 @@ PH_API int phprng_create(phprng_ctx **out, int width, const phprng_instance *ins
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_inst, count * sizeof(DevInst));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_prog, count * sizeof(ExpProg));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_prog8, count * sizeof(ExpProg8));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_state, 4 * count * sizeof(uint64_t));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_order, count * sizeof(uint32_t));
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->d_prog, prog.data(), count * sizeof(ExpProg), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->d_prog8, prog8.data(), count * sizeof(ExpProg8), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->d_inst, di.data(), count * sizeof(DevInst), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
@@ -381,6 +388,7 @@ static int launch_range(phprng_ctx *c, uint64_t first, uint64_t num, uint64_t pe
     }
     g.inst = c->d_inst;
     g.prog = c->d_prog;
+    g.prog8 = c->d_prog8;
     g.st = c->st;
     g.first = first;
     g.num = num;

@@ -14,6 +14,7 @@
 using phprng::DevInst;
 using phprng::DevState;
 using phprng::ExpProg;
+using phprng::ExpProg8;
 using phprng::SkipConst;
 using phprng::SkipTable;
 
@@ -28,6 +29,7 @@ struct phprng_ctx {
     std::vector<uint8_t> wide;
     DevInst *d_inst = nullptr;
     ExpProg *d_prog = nullptr;        // exponent programs, one per instance
+    ExpProg8 *d_prog8 = nullptr;      // the heavy 32-bit generator's programs, one per instance
     uint64_t *d_state = nullptr;      // 4 * count: m | s | c | pos
     DevState st{};
     SkipConst sk32{}, sk64{}, sk32_8{}, sk32_4{};

@@ -35,6 +35,8 @@ static constexpr int kWarpsHeavy = PH_WPB_HEAVY;   // warps per block of the pla
 static constexpr unsigned kFull = kFullMask;
 // shared memory of one warp's exponent table in the heavy plain launch
 static constexpr size_t kTableBytes = 4 * (kNPT / 4) * 32 * sizeof(uint4);
+// per warp of the heavy plain instantiation: tables of up to 8 odd powers
+static constexpr size_t kTable8Bytes = 8 * (kNPT / 4) * 32 * sizeof(uint4);
 // ... and of a block of the 64-bit launch (kWarpsPerBlock warps, NPT64 values of 8 bytes)
 static constexpr size_t kTable64Bytes = (size_t)kWarpsPerBlock * 4 * (kNPT64 / 2) * 32 * sizeof(uint4);
 
@@ -82,7 +84,8 @@ __device__ __forceinline__ double u128d(u128 v) { return u128_to_double((uint64_
 // for long programs two blocks with in-order stores are faster.
 template <int NPT, typename CT, bool STATS, bool LIGHT, int WB>
 __global__ void __launch_bounds__(WB * 32, STATS ? PH_MINB_STATS : LIGHT ? PH_MINB_LIGHT : PH_MINB32)
-gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, DevState st,
+gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
+             const ExpProg8 *__restrict__ prog8, DevState st,
              SkipConst sk, uint64_t first, uint64_t num, uint64_t per_inst,
              CT *__restrict__ c_out, double *__restrict__ r_out, int vec_ok,
              phprng_stats *__restrict__ stats, uint32_t *__restrict__ edge,
@@ -167,9 +170,10 @@ gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
             }
             store_group<NPT, CT, uint32_t>(P, cdst, rdst, myp, len, vec_ok, xp);
         } else {
-            // the exponent program's table of odd powers lives in shared
-            // memory (dynamic, kTableBytes per warp)
-            uint4 *tb = reinterpret_cast<uint4 *>(smem) + warp * (NPT / 4) * 4 * 32;
+            // the exponent program's table of up to 8 odd powers lives in
+            // shared memory (dynamic, kTable8Bytes per warp)
+            uint4 *tb = reinterpret_cast<uint4 *>(smem) + warp * (NPT / 4) * 8 * 32;
+            const ExpProg8 &pg8 = prog8[i];
             for (uint64_t g0 = 0; g0 < len; g0 += G) {
                 uint32_t sv[NPT], msg[NPT];
                 const uint64_t my0 = g0 + (uint64_t)NPT * lane;
@@ -182,7 +186,10 @@ gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
                     messages32<NPT, true>(P, sk, lane, my0, len, M, sig, sv, msg);
                 else
                     messages32<NPT>(P, sk, lane, my0, len, M, sig, sv, msg);
-                encrypt32_tb<NPT>(P, pg, msg, x, tb, lane);
+                if (P.fermat)
+                    encrypt32<NPT>(P, pg, msg, x);
+                else
+                    modexp_prog8_smem<NPT>(x, msg, pg8, (uint32_t)P.n, (uint32_t)P.ninv, tb, lane);
                 // R of two numbers at a time (reals_of)
                 if (full)
                     store_group<NPT, CT, uint32_t, true, PH_RCHUNK_HEAVY>(P, cdst, rdst, my0, len, vec_ok, x);
@@ -460,11 +467,11 @@ int launch_gen32(const GenArgs &a, void *stream, std::string *err)
         }
         if (a.c_is_64)
             gen32_kernel<kNPT, uint64_t, true, false, kWarpsPerBlock><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(
-                a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, (uint64_t *)a.c_out, a.r_out,
+                a.inst, a.prog, a.prog8, a.st, a.sk, a.first, a.num, a.per_inst, (uint64_t *)a.c_out, a.r_out,
                 a.vec_ok, a.stats, a.edge, a.order, a.sp);
         else
             gen32_kernel<kNPT, uint32_t, true, false, kWarpsPerBlock><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(
-                a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, (uint32_t *)a.c_out, a.r_out,
+                a.inst, a.prog, a.prog8, a.st, a.sk, a.first, a.num, a.per_inst, (uint32_t *)a.c_out, a.r_out,
                 a.vec_ok, a.stats, a.edge, a.order, a.sp);
         int rc = check_launch(err, "gen32_kernel (statistics) launch");
         if (rc != PHPRNG_OK || blocks < 2) return rc;
@@ -473,16 +480,16 @@ int launch_gen32(const GenArgs &a, void *stream, std::string *err)
         return check_launch(err, "stats_edge_kernel launch");
     }
 #define PH_GEN32_PLAIN(CTY, LT, WB, NB)                                                             \
-    gen32_kernel<kNPT, CTY, false, LT, WB><<<(unsigned)(NB), WB * 32, LT ? 0 : WB * kTableBytes, s>>>(     \
-        a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, (CTY *)a.c_out, a.r_out, a.vec_ok, \
+    gen32_kernel<kNPT, CTY, false, LT, WB><<<(unsigned)(NB), WB * 32, LT ? 0 : WB * kTable8Bytes, s>>>(    \
+        a.inst, a.prog, a.prog8, a.st, a.sk, a.first, a.num, a.per_inst, (CTY *)a.c_out, a.r_out, a.vec_ok, \
         nullptr, nullptr, a.order, a.sp)
-    if (!a.light && kWarpsHeavy * kTableBytes > 48 * 1024) {
+    if (!a.light && kWarpsHeavy * kTable8Bytes > 48 * 1024) {
         // exponent tables above the default 48 KiB of dynamic shared memory
         // need the kernel's explicit limit (on the current device)
         cudaFuncSetAttribute(gen32_kernel<kNPT, uint32_t, false, false, kWarpsHeavy>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kWarpsHeavy * kTableBytes));
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kWarpsHeavy * kTable8Bytes));
         cudaFuncSetAttribute(gen32_kernel<kNPT, uint64_t, false, false, kWarpsHeavy>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kWarpsHeavy * kTableBytes));
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kWarpsHeavy * kTable8Bytes));
     }
     if (a.c_is_64) {
         if (a.light) PH_GEN32_PLAIN(uint64_t, true, kWarpsLight, blocks_light);
@@ -544,7 +551,7 @@ uint64_t gen_resident_warps()
         int sms = 0, b = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, gen32_kernel<kNPT, uint32_t, false, false, kWarpsHeavy>,
-                                                      kWarpsHeavy * 32, kWarpsHeavy * kTableBytes);
+                                                      kWarpsHeavy * 32, kWarpsHeavy * kTable8Bytes);
         cached[dev] = (uint64_t)(sms > 0 ? sms : 1) * (b > 0 ? b : 1) * kWarpsHeavy;
     }
     return cached[dev];

@@ -281,6 +281,47 @@ __device__ __forceinline__ void modexp_prog_smem(W (&x)[NPT], const W (&m)[NPT],
     for (int u = 0; u < NPT; ++u) x[u] = mont_exit(x[u], K, Kq, n, ninv);
 }
 
+// Eq. 9c by the heavy generator's program (ExpProg8), its table of up to 8
+// odd powers in shared memory (tb: 8 NPT * 4 * 32 bytes per warp, the same
+// [entry][row][lane] layout as modexp_prog_smem).
+template <int NPT>
+__device__ __forceinline__ void modexp_prog8_smem(uint32_t (&x)[NPT], const uint32_t (&m)[NPT],
+                                                  const ExpProg8 &pg, uint32_t n, uint32_t ninv,
+                                                  uint4 *__restrict__ tb, int lane)
+{
+    const int tbl = pg.tbl;
+    put_row<NPT, uint32_t>(tb, 0, lane, m);
+    if (tbl >= 2) {
+        uint32_t m2[NPT], t[NPT];
+#pragma unroll
+        for (int u = 0; u < NPT; ++u) m2[u] = mont32(m[u], m[u], n, ninv);          // m^2
+#pragma unroll
+        for (int u = 0; u < NPT; ++u) t[u] = m[u];
+        for (int k = 1; k < tbl; ++k) {                                              // m^(2k+1)
+            mont_vec<NPT>(t, m2, n, ninv);
+            put_row<NPT, uint32_t>(tb, k, lane, t);
+        }
+    }
+    get_row<NPT, uint32_t>(tb, pg.ent[0] >> 8, lane, x);
+    const int nent = pg.nent;
+    int bnext = pg.ent[1];
+    for (int k = 1; k < nent; ++k) {
+        const int b = bnext;
+        bnext = pg.ent[k + 1 < 32 ? k + 1 : k];                     // next entry, loaded early
+        int sq = b & 0xFF;
+        for (; sq >= 2; sq -= 2) {
+            mont_sqr_vec<NPT>(x, n, ninv);
+            mont_sqr_vec<NPT>(x, n, ninv);
+        }
+        if (sq) mont_sqr_vec<NPT>(x, n, ninv);
+        uint32_t y[NPT];
+        get_row<NPT, uint32_t>(tb, (b >> 8) & 7, lane, y);
+        mont_vec<NPT>(x, y, n, ninv);
+    }
+#pragma unroll
+    for (int u = 0; u < NPT; ++u) x[u] = mont32c(x[u], pg.K, pg.Kq, n);
+}
+
 // Eq. 9c with the program's table in shared memory (tb: 4 NPT sizeof(W) * 32
 // bytes per warp, 16-byte aligned); straight chains need no table.
 template <int NPT, typename W>

@@ -362,6 +362,91 @@ uint64_t mont_exit_constant(uint64_t n, const ExpProg &pg, int rbits)
     return powmod(rmodn, ex, n);
 }
 
+// The heavy generator's program (ExpProg8): for each table size T = 1..8
+// (odd powers up to 2T - 1; building them costs T products, or 0 for T = 1)
+// an exact search over the exponent's bit positions: f[i] is the fewest
+// products that leave x = m^(the top i bits of e); the top i bits start x
+// when they are an odd value in the table (no product), and otherwise x
+// comes from some j < i by i - j squarings and one product with the table
+// entry of the low i - j bits of the prefix, which must be odd and in the
+// table (a window with its leading zeros).  The low bits only grow as j
+// falls, so the search over j stops at the first value above the table.
+// e is odd (coprime to the even n - 1), so the last window ends at bit 0.
+int program8_products(const ExpProg8 &pg)
+{
+    int p = (pg.tbl == 1 ? 0 : pg.tbl) + 1;            // table, exit product
+    for (int k = 1; k < pg.nent; ++k) p += (pg.ent[k] & 0xFF) + 1;
+    return p;
+}
+
+ExpProg8 derive_prog8(uint64_t n, uint64_t e)
+{
+    ExpProg8 best;
+    memset(&best, 0, sizeof best);
+    const int L = bitlen(e);
+    if (L < 1 || L > 32 || !(e & 1)) return best;       // 32-bit exponents only (odd)
+    uint64_t pre[33];
+    for (int i = 0; i <= L; ++i) pre[i] = i ? e >> (L - i) : 0;
+    int best_cost = -1;
+    for (int T = 1; T <= 8; ++T) {
+        const uint64_t maxv = 2 * (uint64_t)T - 1;
+        int f[33], from[33];
+        for (int i = 0; i <= L; ++i) f[i] = -1;
+        for (int i = 1; i <= L; ++i) {
+            if ((pre[i] & 1) && pre[i] <= maxv) {
+                f[i] = 0;
+                from[i] = 0;
+                continue;
+            }
+            for (int j = i - 1; j >= 1; --j) {
+                const uint64_t v = pre[i] & ((1ull << (i - j)) - 1);
+                if (v > maxv) break;
+                if (!(v & 1) || f[j] < 0) continue;
+                const int c = f[j] + (i - j) + 1;
+                if (f[i] < 0 || c < f[i]) {
+                    f[i] = c;
+                    from[i] = j;
+                }
+            }
+        }
+        if (f[L] < 0) continue;
+        const int cost = f[L] + (T == 1 ? 0 : T);
+        if (best_cost >= 0 && cost >= best_cost) continue;
+        // the windows, last to first
+        int cuts[33], nc = 0;
+        for (int i = L; i > 0; i = from[i]) cuts[nc++] = i;
+        if (nc > 32) continue;
+        ExpProg8 pg;
+        memset(&pg, 0, sizeof pg);
+        pg.tbl = (uint8_t)T;
+        pg.nent = (uint8_t)nc;
+        int prev = 0;
+        for (int k = 0; k < nc; ++k) {
+            const int i = cuts[nc - 1 - k];
+            const uint64_t v = k == 0 ? pre[i] : pre[i] & ((1ull << (i - prev)) - 1);
+            pg.ent[k] = (uint16_t)((k == 0 ? 0 : i - prev) | (((v - 1) / 2) << 8));
+            prev = i;
+        }
+        best = pg;
+        best_cost = cost;
+    }
+    // exit constant: table entry k carries R^(-2k) (m^3 = MP(m^2, m), and each
+    // next odd power one more product by m^2 = m^2 R^-1); a squaring takes the
+    // power a to 2a - 1, a product with entry k to a - 2k - 1
+    const uint64_t ord = n - 1;
+    auto sub = [&](uint64_t a, uint64_t k) { return (uint64_t)(((u128)a + ord - k % ord) % ord); };
+    uint64_t alpha = sub(0, 2 * (uint64_t)(best.ent[0] >> 8));
+    for (int k = 1; k < best.nent; ++k) {
+        for (int q = 0; q < (best.ent[k] & 0xFF); ++q) alpha = (uint64_t)(((u128)alpha * 2 + ord - 1) % ord);
+        alpha = sub(alpha, 2 * (uint64_t)((best.ent[k] >> 8) & 7) + 1);
+    }
+    const uint64_t rmodn = (uint64_t)((1ull << 32) % n);
+    const uint64_t ex = (uint64_t)(((u128)ord + 1 - alpha) % ord);
+    best.K = (uint32_t)powmod(rmodn, ex, n);
+    best.Kq = best.K * (uint32_t)inv_mod_2_64(n);
+    return best;
+}
+
 DevInst derive_inst(const phprng_instance &in, int wide, ExpProg *prog)
 {
     DevInst d;

@@ -88,6 +88,7 @@ struct SplitArgs {
 struct GenArgs {
     const DevInst *inst;
     const ExpProg *prog;    // per-instance exponent programs
+    const ExpProg8 *prog8 = nullptr;   // the heavy 32-bit generator's programs (tables of up to 8 odd powers)
     DevState st;
     SkipConst sk;
     uint64_t first, num, per_inst;
@@ -99,7 +100,8 @@ struct GenArgs {
     int vec_ok;             // outputs allow 16-byte vector stores
     // nullable: warp w of the launch runs instance first + order[w] (a
     // permutation of 0 .. num-1, heaviest programs first); NULL = identity.
-    // Never used with statistics, whose pairs need adjacent instances.
+    // With statistics (whose pairs need adjacent instances) it orders the
+    // blocks instead: block b of the launch runs logical block order[b].
     const uint32_t *order = nullptr;
     SplitArgs sp;                      // K = 1: no split
     int light = 0;                     // short exponent programs: the LIGHT instantiation
@@ -274,6 +276,10 @@ bool discrete_logs(uint64_t p, uint64_t a, const uint64_t *s, uint64_t count, ui
 uint64_t mont_exit_constant(uint64_t n, const ExpProg &pg, int rbits);
 DevInst derive_inst(const phprng_instance &in, int wide, ExpProg *prog);
 int program_products(const ExpProg &pg);   // Montgomery products of one run, K included
+// The heavy 32-bit generator's program of exponent e for the 32-bit prime n
+// (products minimised over table sizes 1..8), with its exit constant.
+ExpProg8 derive_prog8(uint64_t n, uint64_t e);
+int program8_products(const ExpProg8 &pg);   // Montgomery products of one run, K included
 SkipConst derive_skip(uint64_t p, uint64_t a, int npt);
 SkipConst64 derive_skip64(uint64_t p, uint64_t a, int npt);
 int validate_one(int width, const phprng_instance &in, uint32_t flags, std::string *msg);

@@ -42,6 +42,25 @@ void h_real32_split_many(const uint64_t *n, const uint64_t *c, double *out, uint
     }
 }
 
+// m^e mod n by the heavy generator's program (tables of up to 8 odd powers);
+// *products_out[i] gets its Montgomery products and std_out[i] those of the
+// standard program, for the comparison
+void h_modexp8_many(const uint64_t *m, const uint64_t *e, const uint64_t *n, uint64_t *out,
+                    int64_t *products8, int64_t *products, uint64_t count)
+{
+    for (uint64_t i = 0; i < count; ++i) {
+        phprng_instance in{n[i], e[i], 3, 2, 0, 1};
+        ExpProg pg;
+        derive_inst(in, 0, &pg);
+        const ExpProg8 p8 = derive_prog8(n[i], e[i]);
+        uint32_t msg[1] = {(uint32_t)m[i]}, x[1];
+        modexp_prog8<1>(x, msg, p8, (uint32_t)n[i], (uint32_t)inv_mod_2_64(n[i]));
+        out[i] = x[0];
+        products8[i] = program8_products(p8);
+        products[i] = program_products(pg);
+    }
+}
+
 // fraction bits f of the fast quotient estimate, to find inputs in the band
 // where real32_fast falls back to the exact remainder
 uint32_t h_real32_fast_frac(uint64_t n, uint64_t c)

@@ -39,6 +39,8 @@ def h(tmp_path_factory):
     lib.h_addmod.argtypes = [u64, u64, u64, ctypes.c_int]
     lib.h_real32_fast_many.argtypes = [P64, P64, ctypes.POINTER(ctypes.c_double), u64]
     lib.h_real32_split_many.argtypes = [P64, P64, ctypes.POINTER(ctypes.c_double), u64]
+    lib.h_modexp8_many.argtypes = [P64, P64, P64, P64, ctypes.POINTER(ctypes.c_int64),
+                                   ctypes.POINTER(ctypes.c_int64), u64]
     lib.h_real32_fast_frac.restype = ctypes.c_uint32
     lib.h_real32_fast_frac.argtypes = [u64, u64]
     return lib
@@ -100,6 +102,41 @@ def test_montgomery_exponentiation_matches_pow(h, wide):
             ms.append(m); es.append(e); nn.append(n); ref.append(pow(m, e, n))
     out = modexp(h, ms, es, nn, wide)
     assert [int(x) for x in out] == ref
+
+
+def test_heavy_programs_match_pow_and_save_products(h):
+    """The heavy generator's programs (exact search over table sizes 1..8)
+    give m^e mod n for random 32-bit primes and exponents, the paper's small
+    exponents and extreme ones, and never need more products than the
+    standard sliding-window program (about 0.6 fewer on average)."""
+    rng = random.Random(31)
+    primes = []
+    while len(primes) < 40:
+        q = rng.randrange((1 << 31) + 1, 1 << 32) | 1
+        if pow(2, q - 1, q) == 1 and pow(3, q - 1, q) == 1 and pow(5, q - 1, q) == 1:
+            primes.append(q)
+    import math
+    ms, es, ns = [], [], []
+    for q in primes:
+        for _ in range(40):
+            e = rng.randrange(3, q - 1)
+            while math.gcd(e, q - 1) != 1:
+                e = rng.randrange(3, q - 1)
+            ms.append(rng.randrange(0, q)); es.append(e); ns.append(q)
+        for e in (3, 5, 7, 9, 17, 65537, 0xFFFFFFFF & (q - 2)):
+            if math.gcd(e, q - 1) == 1 and e < q - 1:
+                for mm in (0, 1, 2, q - 1):
+                    ms.append(mm); es.append(e); ns.append(q)
+    m = np.array(ms, dtype=np.uint64); e = np.array(es, dtype=np.uint64); n = np.array(ns, dtype=np.uint64)
+    out = np.empty_like(m)
+    p8 = np.empty(m.size, dtype=np.int64)
+    p4 = np.empty(m.size, dtype=np.int64)
+    h.h_modexp8_many(_p(m), _p(e), _p(n), _p(out), p8.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                     p4.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), m.size)
+    want = np.array([pow(int(a), int(b), int(c)) for a, b, c in zip(m, e, n)], dtype=np.uint64)
+    assert np.array_equal(out, want)
+    assert np.all(p8 <= p4)
+    assert 0.3 < float((p4 - p8).mean()) < 1.2
 
 
 def test_skip_constants(h):
