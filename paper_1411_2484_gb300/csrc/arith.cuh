@@ -205,7 +205,7 @@ struct alignas(16) ExpProg {
     uint8_t ent[28];
 };
 
-// Exponent program of the 32-bit heavy generator: a table of 1 to 8 odd
+// Exponent program of the 32-bit kernels: a table of 1 to kProg8MaxTable odd
 // powers m, m^3, .., m^(2 tbl - 1) (shared memory holds it), the table size
 // and the windows chosen per exponent by an exact search (dynamic programming
 // over the exponent's bit positions, for every table size) for the fewest
@@ -216,11 +216,15 @@ struct alignas(16) ExpProg {
 struct alignas(16) ExpProg8 {
     uint32_t K, Kq;
     uint8_t nent;       // windows (>= 1)
-    uint8_t tbl;        // table entries, 1 .. 8
+    uint8_t tbl;        // table entries, 1 .. kProg8MaxTable
     uint8_t pad[2];
     uint16_t ent[32];   // per window: sq in bits 0-7, table index (v-1)/2 in bits 8-10
 };
 static_assert(sizeof(ExpProg8) == 80, "ExpProg8 layout");
+// Largest table the host search allows: 6 rows of a warp's 8 numbers per lane
+// are 6 KiB of shared memory (the entry field could index 8).  Over random
+// 32-bit exponents a cap of 6 costs 0.04 products per exponentiation against 8.
+static constexpr int kProg8MaxTable = 6;
 
 // The same program run with the table in an array (host tests, NPT numbers).
 template <int NPT>

@@ -23,9 +23,20 @@ namespace phprng {
 #define PH_BATCH_MINB 3
 #endif
 
+// Per warp: the exponent program's table, rows of 16 bytes per lane (32-bit
+// tiles: up to kProg8MaxTable entries of NPT32/4 rows; 64-bit tiles: 4 entries
+// of PH_NPT64/2 rows), in dynamic shared memory.
+template <int NPT32>
+struct BatchEtb {
+    static constexpr int rows = kProg8MaxTable * (NPT32 / 4) > 4 * (PH_NPT64 / 2) ? kProg8MaxTable * (NPT32 / 4)
+                                                                                   : 4 * (PH_NPT64 / 2);
+    static constexpr size_t bytes = (size_t)8 * rows * 32 * sizeof(uint4);    // 8 warps per block
+};
+extern __shared__ uint4 g_batch_etb[];
+
 template <int NPT, typename CT>
 __device__ __forceinline__ void run_tile32(const BatchArgs &a, const DevInst &P, const ExpProg &pg,
-                                           uint64_t i, int lane, uint32_t m, uint32_t s,
+                                           const ExpProg8 &pg8, uint64_t i, int lane, uint32_t m, uint32_t s,
                                            const Tile &T, bool wb, bool vec_ok, uint4 *etb)
 {
     constexpr uint64_t G = 32 * NPT;
@@ -43,7 +54,7 @@ __device__ __forceinline__ void run_tile32(const BatchArgs &a, const DevInst &P,
         sig_last = sig;
         g_last = g0;
         messages32<NPT>(P, sk, lane, my0, len, M, sig, sv, msg);
-        encrypt32_tb<NPT>(P, pg, msg, x, etb, lane);
+        encrypt32_p8<NPT>(P, pg, pg8, msg, x, etb, lane);
         store_group<NPT, CT, uint32_t>(P, cdst, rdst, my0, len, vec_ok, x);
     }
     if (wb) write_state_after<NPT, uint32_t, uint32_t>(a.st, sk, i, lane, g_last, len, T.start + len, M,
@@ -82,11 +93,8 @@ __device__ __forceinline__ void run_tile64(const BatchArgs &a, const DevInst &P,
 template <int NPT32, typename CT>
 __global__ void __launch_bounds__(256, PH_BATCH_MINB) batch_kernel(BatchArgs a)
 {
-    // per warp: the exponent program's odd powers (32-bit tiles: NPT32 words
-    // per entry and lane, 64-bit tiles: PH_NPT64 double words)
-    constexpr int kRows = NPT32 / 4 > PH_NPT64 / 2 ? NPT32 / 4 : PH_NPT64 / 2;
-    __shared__ uint4 etb[8][4 * kRows * 32];
     const int lane = threadIdx.x & 31;
+    uint4 *etb = g_batch_etb + (threadIdx.x >> 5) * BatchEtb<NPT32>::rows * 32;   // this warp's table
     for (;;) {
         unsigned long long t = 0;
         if (lane == 0) t = atomicAdd(a.counter, 1ull);
@@ -101,11 +109,22 @@ __global__ void __launch_bounds__(256, PH_BATCH_MINB) batch_kernel(BatchArgs a)
         skip_state_warp(a.tb, P, a.m0[i], a.L0[i], T.start, &m, &s, &L);   // Eq. 7
         const bool vec_ok = a.vec_ok && (T.c_off % (16 / sizeof(CT)) == 0) && (T.r_off % 2 == 0);
         if (!wide)
-            run_tile32<NPT32, CT>(a, P, a.prog[i], i, lane, (uint32_t)m, s, T, wb, vec_ok, etb[threadIdx.x >> 5]);
+            run_tile32<NPT32, CT>(a, P, a.prog[i], a.prog8[i], i, lane, (uint32_t)m, s, T, wb, vec_ok, etb);
         else
             run_tile64<PH_NPT64>(a, P, a.prog[i], i, lane, m, s, T, wb,
-                          a.vec_ok && (T.c_off % 2 == 0) && (T.r_off % 2 == 0), etb[threadIdx.x >> 5]);
+                          a.vec_ok && (T.c_off % 2 == 0) && (T.r_off % 2 == 0), etb);
     }
+}
+
+// The launch's dynamic shared memory; above the default 48 KiB the kernel's
+// limit is raised first (current device), as the occupancy query needs too.
+template <int NPT32, typename CT>
+static size_t batch_smem()
+{
+    constexpr size_t smem = BatchEtb<NPT32>::bytes;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(batch_kernel<NPT32, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return smem;
 }
 
 template <int NPT32, typename CT>
@@ -114,7 +133,8 @@ static int launch_one(const BatchArgs &a, int blocks_per_sm, void *stream, std::
     int dev = 0, sms = 0, maxb = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&maxb, batch_kernel<NPT32, CT>, 256, 0);
+    const size_t smem = batch_smem<NPT32, CT>();
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&maxb, batch_kernel<NPT32, CT>, 256, smem);
     if (maxb < 1) maxb = 1;
     const int b = blocks_per_sm <= 0 || blocks_per_sm > maxb ? maxb : blocks_per_sm;
     uint64_t grid = (uint64_t)sms * b;
@@ -126,7 +146,7 @@ static int launch_one(const BatchArgs &a, int blocks_per_sm, void *stream, std::
         *err = std::string("batch counter reset: ") + cudaGetErrorString(e);
         return PHPRNG_ECUDA;
     }
-    batch_kernel<NPT32, CT><<<(unsigned)grid, 256, 0, s>>>(a);
+    batch_kernel<NPT32, CT><<<(unsigned)grid, 256, smem, s>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) {
         *err = std::string("batch_kernel launch: ") + cudaGetErrorString(e);
@@ -148,12 +168,21 @@ int launch_batch(const BatchArgs &a, int npt32, int blocks_per_sm, void *stream,
 int batch_max_blocks_per_sm(int npt32, int c_is_64)
 {
     int maxb = 0;
-    if (c_is_64)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &maxb, npt32 == 4 ? batch_kernel<4, uint64_t> : batch_kernel<8, uint64_t>, 256, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &maxb, npt32 == 4 ? batch_kernel<4, uint32_t> : batch_kernel<8, uint32_t>, 256, 0);
+    if (c_is_64) {
+        if (npt32 == 4)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&maxb, batch_kernel<4, uint64_t>, 256,
+                                                          batch_smem<4, uint64_t>());
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&maxb, batch_kernel<8, uint64_t>, 256,
+                                                          batch_smem<8, uint64_t>());
+    } else {
+        if (npt32 == 4)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&maxb, batch_kernel<4, uint32_t>, 256,
+                                                          batch_smem<4, uint32_t>());
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&maxb, batch_kernel<8, uint32_t>, 256,
+                                                          batch_smem<8, uint32_t>());
+    }
     return maxb;
 }
 

@@ -173,6 +173,7 @@ PH_API int phprng_create(phprng_ctx **out, int width, const phprng_instance *ins
         c->pos_host.assign(count, 0);
         c->wide.resize(count);
         c->key.resize(count);
+        c->key_std.resize(count);
         di.resize(count);
         prog.resize(count);
         prog8.resize(count);
@@ -186,8 +187,9 @@ PH_API int phprng_create(phprng_ctx **out, int width, const phprng_instance *ins
         c->wide[i] = (uint8_t)w;
         (w ? c->any64 : c->any32) = true;
         di[i] = derive_inst(inst[i], w, &prog[i]);
-        if (!w) prog8[i] = derive_prog8(inst[i].n, inst[i].e);   // the heavy 32-bit generator's program
-        c->key[i] = (uint16_t)(256 * w + 255 - std::min(program_products(prog[i]), 255));
+        if (!w) prog8[i] = derive_prog8(inst[i].n, inst[i].e);   // the 32-bit kernels' program
+        c->key[i] = (uint16_t)(256 * w + 255 - std::min(w ? program_products(prog[i]) : program8_products(prog8[i]), 255));
+        c->key_std[i] = (uint16_t)(256 * w + 255 - std::min(program_products(prog[i]), 255));
         state[i] = inst[i].m0;
         state[count + i] = inst[i].s0;
     }
@@ -366,8 +368,8 @@ static bool light_range(phprng_ctx *c, uint64_t first, uint64_t num)
     if (c->lt_first == first && c->lt_num == num) return c->lt_light;
     uint64_t sum = 0, cnt = 0;
     for (uint64_t j = first; j < first + num; ++j) {
-        if (c->key[j] >= 256) continue;                  // 64-bit instance
-        sum += 255 - c->key[j];
+        if (c->key_std[j] >= 256) continue;              // 64-bit instance
+        sum += 255 - c->key_std[j];                      // the LIGHT loop runs the standard program
         ++cnt;
     }
     c->lt_first = first;
@@ -422,9 +424,9 @@ static int launch_range(phprng_ctx *c, uint64_t first, uint64_t num, uint64_t pe
         const uint64_t W = gen32_stats_block_warps(), nb = (num + W - 1) / W;
         std::vector<uint32_t> ord(nb), cnt(513, 0);
         auto bkey = [&](uint64_t b) {
-            uint16_t k = c->key[first + W * b];
+            uint16_t k = c->key_std[first + W * b];
             for (uint64_t j = W * b + 1; j < std::min<uint64_t>(num, W * b + W); ++j)
-                k = std::min(k, c->key[first + j]);
+                k = std::min(k, c->key_std[first + j]);
             return k;
         };
         for (uint64_t b = 0; b < nb; ++b) ++cnt[bkey(b) + 1];
@@ -634,6 +636,7 @@ PH_API int phprng_generate_stats_noalloc(phprng_ctx *ctx, uint64_t first, uint64
     GenArgs g;
     g.inst = ctx->d_inst;
     g.prog = ctx->d_prog;
+    g.prog8 = ctx->d_prog8;
     g.st = ctx->st;
     g.sk = ctx->sk32;
     g.first = first;
@@ -918,6 +921,7 @@ static int run_hist_test(phprng_ctx *ctx, const char *what, uint64_t first, uint
     GenArgs g;
     g.inst = ctx->d_inst;
     g.prog = ctx->d_prog;
+    g.prog8 = ctx->d_prog8;
     g.st = ctx->st;
     g.sk = ctx->sk32_8;
     g.first = first;
@@ -1033,6 +1037,7 @@ PH_API int phprng_interstream_serial_test(phprng_ctx *ctx, uint64_t first, uint6
         GenArgs g;
         g.inst = ctx->d_inst;
         g.prog = ctx->d_prog;
+        g.prog8 = ctx->d_prog8;
         g.st = ctx->st;
         g.sk = ctx->sk32_8;
         g.first = first;
@@ -1076,6 +1081,7 @@ PH_API int phprng_interstream_serial_test(phprng_ctx *ctx, uint64_t first, uint6
         GenArgs g;
         g.inst = ctx->d_inst;
         g.prog = ctx->d_prog;
+        g.prog8 = ctx->d_prog8;
         g.st = ctx->st;
         g.sk = ctx->sk32_8;
         g.first = first;
@@ -1468,6 +1474,7 @@ static BatchArgs batch_args(phprng_plan *pl, void *c_base, double *r_base)
     BatchArgs a;
     a.inst = c->d_inst;
     a.prog = c->d_prog;
+    a.prog8 = c->d_prog8;
     a.st = c->st;
     a.m0 = c->d_m0;
     a.L0 = c->d_L0;

@@ -29,15 +29,18 @@ struct phprng_ctx {
     std::vector<uint8_t> wide;
     DevInst *d_inst = nullptr;
     ExpProg *d_prog = nullptr;        // exponent programs, one per instance
-    ExpProg8 *d_prog8 = nullptr;      // the heavy 32-bit generator's programs, one per instance
+    ExpProg8 *d_prog8 = nullptr;      // the 32-bit kernels' exact-search programs, one per instance
     uint64_t *d_state = nullptr;      // 4 * count: m | s | c | pos
     DevState st{};
     SkipConst sk32{}, sk64{}, sk32_8{}, sk32_4{};
     std::vector<uint64_t> pos_host;   // host mirror of the stream positions
     // launch order: key[i] = 256*wide + 255 - products of instance i's program
-    // (clamped); d_order[first ..] holds the order of the last range sorted
-    // (indices relative to its first instance), ord_first/ord_num name it.
-    std::vector<uint16_t> key;
+    // (clamped; the exact-search program for 32-bit instances, which the
+    // plain and test kernels run); key_std[i] the same by the standard
+    // program, which the statistics kernel runs.  d_order[first ..] holds the
+    // order of the last range sorted (indices relative to its first
+    // instance), ord_first/ord_num name it.
+    std::vector<uint16_t> key, key_std;
     uint32_t *d_order = nullptr;
     uint64_t ord_first = 0, ord_num = 0;
     // light-program decision of the last range launched (see launch_range)

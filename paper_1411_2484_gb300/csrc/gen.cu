@@ -33,10 +33,13 @@ static constexpr int kWarpsPerBlock = PH_WPB;
 static constexpr int kWarpsLight = PH_WPB_LIGHT;   // warps per block of the LIGHT instantiation
 static constexpr int kWarpsHeavy = PH_WPB_HEAVY;   // warps per block of the plain heavy instantiation (3 blocks of 8 warps per SM, exponent tables in shared memory)
 static constexpr unsigned kFull = kFullMask;
-// shared memory of one warp's exponent table in the heavy plain launch
+// shared memory of one warp's exponent table in the statistics instantiation
+// (the standard program: up to 4 odd powers, one 16-byte row per lane and
+// NPT/4 numbers each)
 static constexpr size_t kTableBytes = 4 * (kNPT / 4) * 32 * sizeof(uint4);
-// per warp of the heavy plain instantiation: tables of up to 8 odd powers
-static constexpr size_t kTable8Bytes = 8 * (kNPT / 4) * 32 * sizeof(uint4);
+// ... and in the heavy plain instantiation (the exact-search program: up to
+// kProg8MaxTable odd powers)
+static constexpr size_t kTable8Bytes = kProg8MaxTable * (kNPT / 4) * 32 * sizeof(uint4);
 // ... and of a block of the 64-bit launch (kWarpsPerBlock warps, NPT64 values of 8 bytes)
 static constexpr size_t kTable64Bytes = (size_t)kWarpsPerBlock * 4 * (kNPT64 / 2) * 32 * sizeof(uint4);
 
@@ -170,9 +173,9 @@ gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
             }
             store_group<NPT, CT, uint32_t>(P, cdst, rdst, myp, len, vec_ok, xp);
         } else {
-            // the exponent program's table of up to 8 odd powers lives in
-            // shared memory (dynamic, kTable8Bytes per warp)
-            uint4 *tb = reinterpret_cast<uint4 *>(smem) + warp * (NPT / 4) * 8 * 32;
+            // the exponent program's table of up to kProg8MaxTable odd powers
+            // lives in shared memory (dynamic, kTable8Bytes per warp)
+            uint4 *tb = reinterpret_cast<uint4 *>(smem) + warp * (NPT / 4) * kProg8MaxTable * 32;
             const ExpProg8 &pg8 = prog8[i];
             for (uint64_t g0 = 0; g0 < len; g0 += G) {
                 uint32_t sv[NPT], msg[NPT];
@@ -210,6 +213,8 @@ gen32_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
             else
                 messages32<NPT>(P, sk, lane, my0, len, M, sig, sv, msg);
             if (wb) write_ms_if_last<NPT, uint32_t>(st, i, lane, g0, len, pos_after, sv, msg, P.n);
+            // the standard program: with the exact-search one (6-entry
+            // tables, 80 registers) this loop measured 4.265 against 4.235 ms
             encrypt32_tb<NPT>(P, pg, msg, x,
                               reinterpret_cast<uint4 *>(smem + 2 * W * (32 * NPT) + W * 256) +
                                   warp * (NPT / 4) * 4 * 32,
@@ -445,6 +450,18 @@ static int check_launch(std::string *err, const char *what)
     return PHPRNG_OK;
 }
 
+// Exponent tables above the default 48 KiB of dynamic shared memory need the
+// heavy kernel's explicit limit (on the current device), before its launches
+// and before the occupancy query that sizes split launches.
+static void heavy_smem_limit()
+{
+    if (kWarpsHeavy * kTable8Bytes <= 48 * 1024) return;
+    cudaFuncSetAttribute(gen32_kernel<kNPT, uint32_t, false, false, kWarpsHeavy>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kWarpsHeavy * kTable8Bytes));
+    cudaFuncSetAttribute(gen32_kernel<kNPT, uint64_t, false, false, kWarpsHeavy>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kWarpsHeavy * kTable8Bytes));
+}
+
 int launch_gen32(const GenArgs &a, void *stream, std::string *err)
 {
     if (a.num == 0 || a.per_inst == 0) return PHPRNG_OK;
@@ -483,14 +500,7 @@ int launch_gen32(const GenArgs &a, void *stream, std::string *err)
     gen32_kernel<kNPT, CTY, false, LT, WB><<<(unsigned)(NB), WB * 32, LT ? 0 : WB * kTable8Bytes, s>>>(    \
         a.inst, a.prog, a.prog8, a.st, a.sk, a.first, a.num, a.per_inst, (CTY *)a.c_out, a.r_out, a.vec_ok, \
         nullptr, nullptr, a.order, a.sp)
-    if (!a.light && kWarpsHeavy * kTable8Bytes > 48 * 1024) {
-        // exponent tables above the default 48 KiB of dynamic shared memory
-        // need the kernel's explicit limit (on the current device)
-        cudaFuncSetAttribute(gen32_kernel<kNPT, uint32_t, false, false, kWarpsHeavy>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kWarpsHeavy * kTable8Bytes));
-        cudaFuncSetAttribute(gen32_kernel<kNPT, uint64_t, false, false, kWarpsHeavy>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kWarpsHeavy * kTable8Bytes));
-    }
+    if (!a.light) heavy_smem_limit();
     if (a.c_is_64) {
         if (a.light) PH_GEN32_PLAIN(uint64_t, true, kWarpsLight, blocks_light);
         else PH_GEN32_PLAIN(uint64_t, false, kWarpsHeavy, blocks_heavy);
@@ -550,6 +560,7 @@ uint64_t gen_resident_warps()
     if (!cached[dev]) {
         int sms = 0, b = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        heavy_smem_limit();
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, gen32_kernel<kNPT, uint32_t, false, false, kWarpsHeavy>,
                                                       kWarpsHeavy * 32, kWarpsHeavy * kTable8Bytes);
         cached[dev] = (uint64_t)(sms > 0 ? sms : 1) * (b > 0 ? b : 1) * kWarpsHeavy;

@@ -281,9 +281,9 @@ __device__ __forceinline__ void modexp_prog_smem(W (&x)[NPT], const W (&m)[NPT],
     for (int u = 0; u < NPT; ++u) x[u] = mont_exit(x[u], K, Kq, n, ninv);
 }
 
-// Eq. 9c by the heavy generator's program (ExpProg8), its table of up to 8
-// odd powers in shared memory (tb: 8 NPT * 4 * 32 bytes per warp, the same
-// [entry][row][lane] layout as modexp_prog_smem).
+// Eq. 9c by the exact-search program (ExpProg8), its table of up to
+// kProg8MaxTable odd powers in shared memory (tb: kProg8MaxTable * NPT * 4 * 32
+// bytes per warp, the same [entry][row][lane] layout as modexp_prog_smem).
 template <int NPT>
 __device__ __forceinline__ void modexp_prog8_smem(uint32_t (&x)[NPT], const uint32_t (&m)[NPT],
                                                   const ExpProg8 &pg, uint32_t n, uint32_t ninv,
@@ -320,6 +320,18 @@ __device__ __forceinline__ void modexp_prog8_smem(uint32_t (&x)[NPT], const uint
     }
 #pragma unroll
     for (int u = 0; u < NPT; ++u) x[u] = mont32c(x[u], pg.K, pg.Kq, n);
+}
+
+// Eq. 9c for the 32-bit kernels: straight chains for e = 2^t + 1 (no table),
+// else the exact-search program with its table at tb (modexp_prog8_smem).
+template <int NPT>
+__device__ __forceinline__ void encrypt32_p8(const DevInst &P, const ExpProg &pg, const ExpProg8 &pg8,
+                                             const uint32_t (&msg)[NPT], uint32_t (&x)[NPT], uint4 *tb, int lane)
+{
+    if (P.fermat)
+        encrypt<NPT, uint32_t>(P, pg, msg, x);
+    else
+        modexp_prog8_smem<NPT>(x, msg, pg8, (uint32_t)P.n, (uint32_t)P.ninv, tb, lane);
 }
 
 // Eq. 9c with the program's table in shared memory (tb: 4 NPT sizeof(W) * 32

@@ -388,7 +388,7 @@ ExpProg8 derive_prog8(uint64_t n, uint64_t e)
     uint64_t pre[33];
     for (int i = 0; i <= L; ++i) pre[i] = i ? e >> (L - i) : 0;
     int best_cost = -1;
-    for (int T = 1; T <= 8; ++T) {
+    for (int T = 1; T <= kProg8MaxTable; ++T) {
         const uint64_t maxv = 2 * (uint64_t)T - 1;
         int f[33], from[33];
         for (int i = 0; i <= L; ++i) f[i] = -1;

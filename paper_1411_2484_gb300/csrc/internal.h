@@ -88,7 +88,7 @@ struct SplitArgs {
 struct GenArgs {
     const DevInst *inst;
     const ExpProg *prog;    // per-instance exponent programs
-    const ExpProg8 *prog8 = nullptr;   // the heavy 32-bit generator's programs (tables of up to 8 odd powers)
+    const ExpProg8 *prog8 = nullptr;   // the 32-bit kernels' programs (tables of up to kProg8MaxTable odd powers)
     DevState st;
     SkipConst sk;
     uint64_t first, num, per_inst;
@@ -156,6 +156,7 @@ static_assert(sizeof(Tile) == 32, "Tile is 32 bytes");
 struct BatchArgs {
     const DevInst *inst;
     const ExpProg *prog;
+    const ExpProg8 *prog8;          // 32-bit instances' exact-search programs
     DevState st;
     const uint64_t *m0, *L0;        // seed message and the seed skip's cycle position
     SkipTable tb;
@@ -276,8 +277,8 @@ bool discrete_logs(uint64_t p, uint64_t a, const uint64_t *s, uint64_t count, ui
 uint64_t mont_exit_constant(uint64_t n, const ExpProg &pg, int rbits);
 DevInst derive_inst(const phprng_instance &in, int wide, ExpProg *prog);
 int program_products(const ExpProg &pg);   // Montgomery products of one run, K included
-// The heavy 32-bit generator's program of exponent e for the 32-bit prime n
-// (products minimised over table sizes 1..8), with its exit constant.
+// The 32-bit kernels' program of exponent e for the 32-bit prime n (products
+// minimised over table sizes 1..kProg8MaxTable), with its exit constant.
 ExpProg8 derive_prog8(uint64_t n, uint64_t e);
 int program8_products(const ExpProg8 &pg);   // Montgomery products of one run, K included
 SkipConst derive_skip(uint64_t p, uint64_t a, int npt);

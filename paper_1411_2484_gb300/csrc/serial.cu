@@ -25,6 +25,23 @@ namespace phprng {
 #endif
 static constexpr int kSerialWarps = PH_SERIAL_WARPS;   // warps per block of serial_kernel (3 blocks per SM, exponent tables in shared memory)
 
+// Per warp of the generating kernels below: the exponent program's table of up
+// to kProg8MaxTable odd powers (NPT/4 16-byte rows per lane and entry; the
+// launches run 8 numbers per lane), in dynamic shared memory after the
+// kernel's static arrays.
+static constexpr size_t kEtbWarpBytes = kProg8MaxTable * (8 / 4) * 32 * sizeof(uint4);
+extern __shared__ uint4 g_etb[];
+
+// Dynamic shared memory of a launch of `warps` warps (the kernel's limit is
+// raised when it passes the default 48 KiB; current device).
+template <typename K>
+static size_t etb_smem(K kernel, int warps)
+{
+    const size_t bytes = (size_t)warps * kEtbWarpBytes;
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return bytes;
+}
+
 // The bin of a number, floor(B R) taken on the double R = RN((c+1)/(n+1))
 // (Eq. 9d) with one IEEE product, RN(R B), then truncation -- what a program
 // binning the generator's doubles computes.  For n < 2^32 and B <= 2^20 this
@@ -153,13 +170,13 @@ __device__ __forceinline__ void flush_local(uint32_t *cnt, uint32_t nbins, int l
 // counters (D = 5, B = 10); otherwise the serial test's B^D counters.
 template <int NPT, bool POKER, int WB>
 __global__ void __launch_bounds__(WB * 32, PH_SERIAL_MINB)
-serial_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, DevState st,
+serial_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
+              const ExpProg8 *__restrict__ prog8, DevState st,
               SkipConst sk, uint64_t first, uint64_t num, uint64_t per_inst, int D, uint32_t B,
               unsigned long long *__restrict__ hist, const uint32_t *__restrict__ order)
 {
     constexpr uint64_t G = 32 * NPT;
     __shared__ uint32_t tb[WB][32 * NPT + 8];  // per warp: a carried tuple start, then one group
-    __shared__ uint4 etb[WB][4 * (NPT / 4) * 32];   // per warp: the exponent program's odd powers
     __shared__ uint32_t lc[WB][kLocalBins];         // per warp: shared counters (flush_local)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint64_t w = (uint64_t)blockIdx.x * WB + warp;
@@ -168,6 +185,8 @@ serial_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog
     const uint64_t i = first + j;
     const DevInst P = inst[i];
     const ExpProg &pg = prog[i];
+    const ExpProg8 &pg8 = prog8[i];
+    uint4 *etb = g_etb + warp * kProg8MaxTable * (NPT / 4) * 32;   // this warp's exponent table
     const uint32_t r = (uint32_t)(((uint64_t)B << 32) / P.yN);
     uint32_t nbins = 1;
     for (int d = 0; d < D && nbins <= kLocalBins; ++d) nbins *= B;
@@ -188,7 +207,7 @@ serial_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog
         sig_last = sig;
         g_last = g0;
         messages32<NPT>(P, sk, lane, my0, per_inst, M, sig, sv, msg);
-        encrypt32_tb<NPT>(P, pg, msg, x, etb[warp], lane);
+        encrypt32_p8<NPT>(P, pg, pg8, msg, x, etb, lane);
         {
             uint32_t b[NPT];
             serial_bins<NPT>(x, P.yN, P.ybits, r, B, b);
@@ -240,7 +259,8 @@ serial_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog
 // not counted.  Counts go to a per-warp shared histogram, flushed at the end.
 template <int NPT>
 __global__ void __launch_bounds__(256, PH_SERIAL_MINB)
-runs_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, DevState st,
+runs_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
+            const ExpProg8 *__restrict__ prog8, DevState st,
             SkipConst sk, uint64_t first, uint64_t num, uint64_t per_inst, int lmax,
             unsigned long long *__restrict__ hist, const uint32_t *__restrict__ order)
 {
@@ -248,7 +268,6 @@ runs_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, 
     constexpr int NW = (int)(G / 32);                    // words of bits per group
     __shared__ uint32_t wb[8][NW], wt[8][NW];
     __shared__ uint32_t wh[8][128];                      // 2 lmax <= 128 counters per warp
-    __shared__ uint4 etb[8][4 * (NPT / 4) * 32];         // per warp: the exponent program's odd powers
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint64_t w = (uint64_t)blockIdx.x * 8 + warp;
     if (w >= num) return;
@@ -256,6 +275,8 @@ runs_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, 
     const uint64_t i = first + j;
     const DevInst P = inst[i];
     const ExpProg &pg = prog[i];
+    const ExpProg8 &pg8 = prog8[i];
+    uint4 *etb = g_etb + warp * kProg8MaxTable * (NPT / 4) * 32;   // this warp's exponent table
     const uint32_t half = (uint32_t)((P.n - 1) / 2);
     uint32_t M = (uint32_t)st.m[i];
     uint32_t sig = mont32((uint32_t)st.s[i], sk.lane[lane], sk.p, sk.pinv);
@@ -271,7 +292,7 @@ runs_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, 
         sig_last = sig;
         g_last = g0;
         messages32<NPT>(P, sk, lane, my0, per_inst, M, sig, sv, msg);
-        encrypt32_tb<NPT>(P, pg, msg, x, etb[warp], lane);
+        encrypt32_p8<NPT>(P, pg, pg8, msg, x, etb, lane);
         const uint32_t valid = per_inst - g0 < G ? (uint32_t)(per_inst - g0) : (uint32_t)G;
         uint32_t byte = 0;
 #pragma unroll
@@ -339,13 +360,13 @@ runs_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, 
 // warp of the GPU) exceeds L2 and makes every OR a DRAM read-modify-write.
 template <int NPT>
 __global__ void __launch_bounds__(kSerialWarps * 32, PH_SERIAL_MINB)
-coll_bins_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, DevState st,
+coll_bins_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
+                 const ExpProg8 *__restrict__ prog8, DevState st,
                  SkipConst sk, uint64_t first, uint64_t w0, uint64_t wend, uint64_t len, int store,
                  uint32_t B, uint32_t *__restrict__ bins, const uint32_t *__restrict__ order)
 {
     constexpr int WB = kSerialWarps;
     constexpr uint64_t G = 32 * NPT;
-    __shared__ uint4 etb[WB][4 * (NPT / 4) * 32];   // per warp: the exponent program's odd powers
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint64_t w = w0 + (uint64_t)blockIdx.x * WB + warp;
     if (w >= wend) return;
@@ -353,6 +374,8 @@ coll_bins_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ p
     const uint64_t i = first + j;
     const DevInst P = inst[i];
     const ExpProg &pg = prog[i];
+    const ExpProg8 &pg8 = prog8[i];
+    uint4 *etb = g_etb + warp * kProg8MaxTable * (NPT / 4) * 32;   // this warp's exponent table
     const uint32_t r = (uint32_t)(((uint64_t)B << 32) / P.yN);
     uint32_t M = (uint32_t)st.m[i];
     uint32_t sig = mont32((uint32_t)st.s[i], sk.lane[lane], sk.p, sk.pinv);
@@ -370,7 +393,7 @@ coll_bins_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ p
             messages32<NPT, true>(P, sk, lane, my0, len, M, sig, sv, msg);
         else
             messages32<NPT>(P, sk, lane, my0, len, M, sig, sv, msg);
-        encrypt32_tb<NPT>(P, pg, msg, x, etb[warp], lane);
+        encrypt32_p8<NPT>(P, pg, pg8, msg, x, etb, lane);
         if (!store) continue;                            // (len is then the call's tail)
         uint32_t b[NPT];
         serial_bins<NPT>(x, P.yN, P.ybits, r, B, b);
@@ -456,6 +479,7 @@ int launch_collision(const GenArgs &a, uint32_t S, uint32_t B, uint32_t H, unsig
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coll_count_kernel, kCollCountThreads, smem);
     const uint64_t count_blocks = (uint64_t)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+    const size_t esm = etb_smem(coll_bins_kernel<8>, kSerialWarps);
     // slots per chunk and numbers per piece so that one piece of one chunk
     // fits the `cap` bins of scratch (at least one segment per slot)
     const uint64_t cw = counted == 0 ? a.num : std::min<uint64_t>(a.num, std::max<uint64_t>(1, cap / S));
@@ -470,8 +494,8 @@ int launch_collision(const GenArgs &a, uint32_t S, uint32_t B, uint32_t H, unsig
         const unsigned blocks = (unsigned)((wend - w0 + kSerialWarps - 1) / kSerialWarps);
         for (uint64_t p0 = 0; p0 < counted; p0 += Lp) {
             const uint64_t L = std::min(Lp, counted - p0);
-            coll_bins_kernel<8><<<blocks, kSerialWarps * 32, 0, s>>>(a.inst, a.prog, a.st, a.sk, a.first, w0, wend,
-                                                                    L, 1, B, bins, a.order);
+            coll_bins_kernel<8><<<blocks, kSerialWarps * 32, esm, s>>>(a.inst, a.prog, a.prog8, a.st, a.sk, a.first,
+                                                                      w0, wend, L, 1, B, bins, a.order);
             int rc = check("coll_bins_kernel");
             if (rc != PHPRNG_OK) return rc;
             const uint64_t nseg = (wend - w0) * (L / S);
@@ -481,8 +505,9 @@ int launch_collision(const GenArgs &a, uint32_t S, uint32_t B, uint32_t H, unsig
             if (rc != PHPRNG_OK) return rc;
         }
         if (a.per_inst > counted) {
-            coll_bins_kernel<8><<<blocks, kSerialWarps * 32, 0, s>>>(a.inst, a.prog, a.st, a.sk, a.first, w0, wend,
-                                                                    a.per_inst - counted, 0, B, bins, a.order);
+            coll_bins_kernel<8><<<blocks, kSerialWarps * 32, esm, s>>>(a.inst, a.prog, a.prog8, a.st, a.sk, a.first,
+                                                                      w0, wend, a.per_inst - counted, 0, B, bins,
+                                                                      a.order);
             const int rc = check("coll_bins_kernel");
             if (rc != PHPRNG_OK) return rc;
         }
@@ -494,8 +519,8 @@ int launch_runs(const GenArgs &a, int lmax, unsigned long long *hist, void *stre
 {
     if (a.num == 0 || a.per_inst == 0) return PHPRNG_OK;
     const uint64_t blocks = (a.num + 7) / 8;
-    runs_kernel<8><<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(
-        a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, lmax, hist, a.order);
+    runs_kernel<8><<<(unsigned)blocks, 256, etb_smem(runs_kernel<8>, 8), (cudaStream_t)stream>>>(
+        a.inst, a.prog, a.prog8, a.st, a.sk, a.first, a.num, a.per_inst, lmax, hist, a.order);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         *err = std::string("runs_kernel launch: ") + cudaGetErrorString(e);
@@ -591,7 +616,8 @@ inter_hist_kernel(const BT *__restrict__ binsT, uint64_t ntup, int D, uint32_t B
 // reached by all of them.
 template <int NPT, int GD>
 __global__ void __launch_bounds__(GD * (kSerialWarps / GD) * 32, PH_SERIAL_MINB)
-inter_groups_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog, DevState st,
+inter_groups_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict__ prog,
+                    const ExpProg8 *__restrict__ prog8, DevState st,
                     SkipConst sk, uint64_t first, uint64_t num, uint64_t len, uint32_t B,
                     unsigned long long *__restrict__ hist, const uint32_t *__restrict__ group_order)
 {
@@ -599,7 +625,6 @@ inter_groups_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict_
     constexpr int WB = GD * NG;                        // warps per block (6 for D = 3, 5 for D = 5, ...)
     static_assert(GD >= 2 && GD <= kSerialWarps && NPT == 8, "groups of warps, 8 bins per lane as one 16-byte row");
     constexpr uint64_t G = 32 * NPT;
-    __shared__ uint4 etb[WB][4 * (NPT / 4) * 32];      // per warp: the exponent program's odd powers
     __shared__ uint4 pb[NG][GD - 1][2][32];            // per group: its other streams' bins, two buffers
     __shared__ uint32_t lc[WB][kLocalBins];            // per warp: shared counters when B^D <= kLocalBins
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -611,6 +636,8 @@ inter_groups_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict_
     const uint64_t i = first + j;
     const DevInst P = inst[i];
     const ExpProg &pg = prog[i];
+    const ExpProg8 &pg8 = prog8[i];
+    uint4 *etb = g_etb + warp * kProg8MaxTable * (NPT / 4) * 32;   // this warp's exponent table
     const uint32_t r = (uint32_t)(((uint64_t)B << 32) / P.yN);
     uint32_t nbins = 1;
     for (int d = 0; d < GD && nbins <= kLocalBins; ++d) nbins *= B;
@@ -635,7 +662,7 @@ inter_groups_kernel(const DevInst *__restrict__ inst, const ExpProg *__restrict_
             messages32<NPT, true>(P, sk, lane, my0, len, M, sig, sv, msg);
         else
             messages32<NPT>(P, sk, lane, my0, len, M, sig, sv, msg);
-        encrypt32_tb<NPT>(P, pg, msg, x, etb[warp], lane);
+        encrypt32_p8<NPT>(P, pg, pg8, msg, x, etb, lane);
         uint32_t b[NPT];
         serial_bins<NPT>(x, P.yN, P.ybits, r, B, b);
         if (member)
@@ -678,8 +705,8 @@ static void launch_groups_d(const GenArgs &a, uint32_t B, unsigned long long *hi
 {
     constexpr int WB = GD * (kSerialWarps / GD);
     const uint64_t blocks = (a.num + WB - 1) / WB;
-    inter_groups_kernel<8, GD><<<(unsigned)blocks, WB * 32, 0, s>>>(
-        a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, B, hist, group_order);
+    inter_groups_kernel<8, GD><<<(unsigned)blocks, WB * 32, etb_smem(inter_groups_kernel<8, GD>, WB), s>>>(
+        a.inst, a.prog, a.prog8, a.st, a.sk, a.first, a.num, a.per_inst, B, hist, group_order);
 }
 
 int launch_inter_groups(const GenArgs &a, int D, uint32_t B, unsigned long long *hist,
@@ -773,11 +800,15 @@ int launch_serial(const GenArgs &a, int D, uint32_t B, unsigned long long *hist,
     if (a.num == 0 || a.per_inst == 0) return PHPRNG_OK;
     const uint64_t blocks = (a.num + kSerialWarps - 1) / kSerialWarps;
     if (D == 0)                                      // the poker test
-        serial_kernel<8, true, kSerialWarps><<<(unsigned)blocks, kSerialWarps * 32, 0, (cudaStream_t)stream>>>(
-            a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, 5, 10, hist, a.order);
+        serial_kernel<8, true, kSerialWarps><<<(unsigned)blocks, kSerialWarps * 32,
+                                               etb_smem(serial_kernel<8, true, kSerialWarps>, kSerialWarps),
+                                               (cudaStream_t)stream>>>(
+            a.inst, a.prog, a.prog8, a.st, a.sk, a.first, a.num, a.per_inst, 5, 10, hist, a.order);
     else
-        serial_kernel<8, false, kSerialWarps><<<(unsigned)blocks, kSerialWarps * 32, 0, (cudaStream_t)stream>>>(
-            a.inst, a.prog, a.st, a.sk, a.first, a.num, a.per_inst, D, B, hist, a.order);
+        serial_kernel<8, false, kSerialWarps><<<(unsigned)blocks, kSerialWarps * 32,
+                                                etb_smem(serial_kernel<8, false, kSerialWarps>, kSerialWarps),
+                                                (cudaStream_t)stream>>>(
+            a.inst, a.prog, a.prog8, a.st, a.sk, a.first, a.num, a.per_inst, D, B, hist, a.order);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         *err = std::string("serial_kernel launch: ") + cudaGetErrorString(e);

@@ -182,6 +182,7 @@ static int launch_slot(phprng_server *s, Slot &sl)
     BatchArgs a;
     a.inst = c->d_inst;
     a.prog = c->d_prog;
+    a.prog8 = c->d_prog8;
     a.st = c->st;
     a.m0 = c->d_m0;
     a.L0 = c->d_L0;

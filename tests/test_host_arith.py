@@ -105,7 +105,7 @@ def test_montgomery_exponentiation_matches_pow(h, wide):
 
 
 def test_heavy_programs_match_pow_and_save_products(h):
-    """The heavy generator's programs (exact search over table sizes 1..8)
+    """The 32-bit kernels' programs (exact search over table sizes 1..6)
     give m^e mod n for random 32-bit primes and exponents, the paper's small
     exponents and extreme ones, and never need more products than the
     standard sliding-window program (about 0.6 fewer on average)."""
@@ -137,6 +137,45 @@ def test_heavy_programs_match_pow_and_save_products(h):
     assert np.array_equal(out, want)
     assert np.all(p8 <= p4)
     assert 0.3 < float((p4 - p8).mean()) < 1.2
+
+
+def test_exact_search_is_minimal_over_all_window_cuts(h):
+    """For every odd exponent below 2^10, and for 15- and 16-bit exponents
+    whose best table has 6 entries, the program's product count equals the
+    minimum over all ways of cutting the exponent's bits into windows (brute
+    force over every subset of cut positions), each window an odd value of at
+    most 2T - 1 after its leading zeros, for table sizes T = 1..6: the first
+    window loads a table entry, each later one costs its length in squarings
+    plus one product; the table costs T products for T >= 2 (m^2 and T - 1
+    steps), and the exit product one more."""
+    def brute(e):
+        # least cost of the windows for each table size T = 1..6
+        bits = bin(e)[2:]
+        L, best = len(bits), [None] * 7
+        for mask in range(1 << (L - 1)):
+            cuts = [0] + [k + 1 for k in range(L - 1) if mask >> k & 1] + [L]
+            segs = [bits[a:b] for a, b in zip(cuts, cuts[1:])]
+            vals = [int(sg, 2) for sg in segs]
+            if any(v % 2 == 0 for v in vals) or max(vals) > 11:
+                continue
+            cost = sum(len(sg) + 1 for sg in segs[1:])
+            for T in range((max(vals) + 1) // 2, 7):      # every table that holds the windows
+                if best[T] is None or cost < best[T]:
+                    best[T] = cost
+        return 1 + min(best[T] + (T if T >= 2 else 0) for T in range(1, 7) if best[T] is not None)
+    # a 6-entry table is strictly best for these (one product fewer than 5)
+    wide = [22987, 19851, 45639]
+    es = np.array(list(range(3, 1024, 2)) + wide, dtype=np.uint64)
+    n = np.full(es.size, 4294967291, dtype=np.uint64)
+    m = np.full(es.size, 12345, dtype=np.uint64)
+    out = np.empty_like(m)
+    p8 = np.empty(es.size, dtype=np.int64)
+    p4 = np.empty(es.size, dtype=np.int64)
+    h.h_modexp8_many(_p(m), _p(es), _p(n), _p(out), p8.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                     p4.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), es.size)
+    for e, got, x in zip(es, p8, out):
+        assert int(got) == brute(int(e)), (int(e), int(got))
+        assert int(x) == pow(12345, int(e), 4294967291)
 
 
 def test_skip_constants(h):
