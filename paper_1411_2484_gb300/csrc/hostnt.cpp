@@ -362,8 +362,8 @@ uint64_t mont_exit_constant(uint64_t n, const ExpProg &pg, int rbits)
     return powmod(rmodn, ex, n);
 }
 
-// The heavy generator's program (ExpProg8): for each table size T = 1..8
-// (odd powers up to 2T - 1; building them costs T products, or 0 for T = 1)
+// The 32-bit kernels' program (ExpProg8): for each table size
+// T = 1..kProg8MaxTable (odd powers up to 2T - 1; building them costs T products, or 0 for T = 1)
 // an exact search over the exponent's bit positions: f[i] is the fewest
 // products that leave x = m^(the top i bits of e); the top i bits start x
 // when they are an odd value in the table (no product), and otherwise x

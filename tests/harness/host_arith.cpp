@@ -42,7 +42,7 @@ void h_real32_split_many(const uint64_t *n, const uint64_t *c, double *out, uint
     }
 }
 
-// m^e mod n by the heavy generator's program (tables of up to 8 odd powers);
+// m^e mod n by the exact-search program (tables of up to kProg8MaxTable odd powers);
 // *products_out[i] gets its Montgomery products and std_out[i] those of the
 // standard program, for the comparison
 void h_modexp8_many(const uint64_t *m, const uint64_t *e, const uint64_t *n, uint64_t *out,
