@@ -63,6 +63,20 @@ void h_modexp8_many(const uint64_t *m, const uint64_t *e, const uint64_t *n, uin
 
 // fraction bits f of the fast quotient estimate, to find inputs in the band
 // where real32_fast falls back to the exact remainder
+// The exact-search program of (n, e) as plain words: out[0] table size,
+// out[1] windows, out[2 + k] window k's squarings and out[34 + k] its table
+// index (k < 32), for checks of the layout the kernels index by.
+void h_prog8_words(uint64_t n, uint64_t e, uint32_t *out)
+{
+    const ExpProg8 p8 = derive_prog8(n, e);
+    out[0] = p8.tbl;
+    out[1] = p8.nent;
+    for (int k = 0; k < 32; ++k) {
+        out[2 + k] = p8.ent[k] & 0xFF;
+        out[34 + k] = (p8.ent[k] >> 8) & 0xFF;
+    }
+}
+
 uint32_t h_real32_fast_frac(uint64_t n, uint64_t c)
 {
     phprng_instance in{n, 3, 3, 2, 0, 1};

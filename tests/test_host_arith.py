@@ -42,6 +42,7 @@ def h(tmp_path_factory):
     lib.h_modexp8_many.argtypes = [P64, P64, P64, P64, ctypes.POINTER(ctypes.c_int64),
                                    ctypes.POINTER(ctypes.c_int64), u64]
     lib.h_real32_fast_frac.restype = ctypes.c_uint32
+    lib.h_prog8_words.argtypes = [u64, u64, ctypes.POINTER(ctypes.c_uint32)]
     lib.h_real32_fast_frac.argtypes = [u64, u64]
     return lib
 
@@ -176,6 +177,29 @@ def test_exact_search_is_minimal_over_all_window_cuts(h):
     for e, got, x in zip(es, p8, out):
         assert int(got) == brute(int(e)), (int(e), int(got))
         assert int(x) == pow(12345, int(e), 4294967291)
+
+
+def test_exact_search_programs_index_inside_their_table(h):
+    """Every window of a program reads a table entry the program builds (index
+    below its table size, at most 6 entries: the 6 KiB per warp the kernels
+    reserve), there are 1 to 32 windows, every window after the first has at
+    least one squaring, and the windows' bits add up to the exponent's length:
+    random 32-bit exponents and the extreme ones."""
+    rng = random.Random(77)
+    n = 4294967291
+    es = [3, 5, 9, 17, 65537, 0x55555555, 0xAAAAAAAB, 0xFFFFFFFD, (1 << 31) + 1, n - 2]
+    es += [rng.randrange(3, 1 << 32) | 1 for _ in range(3000)]
+    w = (ctypes.c_uint32 * 66)()
+    for e in es:
+        h.h_prog8_words(n, e, w)
+        tbl, nent = w[0], w[1]
+        assert 1 <= tbl <= 6 and 1 <= nent <= 32, (e, tbl, nent)
+        sq = [w[2 + k] for k in range(nent)]
+        idx = [w[34 + k] for k in range(nent)]
+        assert all(i < tbl for i in idx), (e, tbl, idx)
+        assert all(q >= 1 for q in sq[1:]), (e, sq)
+        first_bits = (2 * idx[0] + 1).bit_length()
+        assert first_bits + sum(sq[1:]) == e.bit_length(), (e, sq, idx)
 
 
 def test_skip_constants(h):
